@@ -1,0 +1,365 @@
+"""FlowRoI oracle: numpy front end over the plain FP64 C oracle.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()``
+and ``bench.py``'s CPU-baseline / reference legs import this module.  It
+shares no code with the CUDA library (``paper_2511_14419_gb300``) and never
+imports it.
+
+Every function below is a thin ctypes marshaller around one stage of
+``flowroi_oracle.c`` (see the comments there for the paper passage each stage
+follows); ``frame`` chains them in the paper's order for one frame pair:
+§Optical flow extraction -> §Region of Interest extraction -> the JPEG2000
+front end of §Implementation details.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "flowroi_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liborc.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE double: no fast-math, no FMA
+    contraction, so x86 and Arm builds round identically)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        _declare(_lib)
+    return _lib
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_F = ctypes.c_float
+
+
+def _declare(L):
+    sig = {
+        "orc_version": (_I, []),
+        "orc_units": (None, [_P, _I, _I, _I64, _P]),
+        "orc_pyr_down": (None, [_P, _I, _I, _P]),
+        "orc_poly_projector": (_I, [_I, _D, _P]),
+        "orc_poly_expand": (_I, [_P, _I, _I, _I, _D, _P]),
+        "orc_flow_upsample": (None, [_P, _I, _I, _I, _I, _P]),
+        "orc_flow_iterate": (None, [_P, _P, _I, _I, _P, _I, _I, _D, _P]),
+        "orc_flow": (_I, [_P, _P, _I, _I, _I, _I, _D, _I, _I, _D, _P]),
+        "orc_saliency": (None, [_P, _I, _I, _D, _P]),
+        "orc_normalise": (None, [_P, _I64, _P]),
+        "orc_quantile_k": (_I64, [_F, _I64]),
+        "orc_threshold": (_D, [_P, _I64, _F, _P]),
+        "orc_threshold_f32": (_F, [_P, _I64, _F, _P]),
+        "orc_erode": (None, [_P, _I, _I, _I, _P]),
+        "orc_dilate": (None, [_P, _I, _I, _I, _P]),
+        "orc_morph": (None, [_P, _I, _I, _I, _I, _P]),
+        "orc_dwt53_1d": (None, [_P, _I, _P]),
+        "orc_idwt53_1d": (None, [_P, _I, _P]),
+        "orc_dwt97_1d": (None, [_P, _I, _P]),
+        "orc_idwt97_1d": (None, [_P, _I, _P]),
+        "orc_dwt53_2d": (None, [_P, _I, _I, _I]),
+        "orc_idwt53_2d": (None, [_P, _I, _I, _I]),
+        "orc_dwt97_2d": (None, [_P, _I, _I, _I]),
+        "orc_idwt97_2d": (None, [_P, _I, _I, _I]),
+        "orc_dc_shift": (None, [_P, _I, _I, _I64, _P]),
+        "orc_subband_index": (_I, [_I, _I, _I, _I, _I]),
+        "orc_delta_table": (_I, [_I, _I, _D, _P, _P, _P, _P]),
+        "orc_quantise_f32": (None, [_P, _I, _I, _I, _P, _P]),
+        "orc_quantise_f64": (None, [_P, _I, _I, _I, _P, _P]),
+        "orc_wavelet_mask": (None, [_P, _I, _I, _I, _I, _P]),
+        "orc_roi_shift": (_I, [_P, _P, _I64, _I]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def _c(a, dtype):
+    """Contiguous array of the given dtype (copied only when needed)."""
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---------------------------------------------------------------- stages --
+
+def units(raw: np.ndarray, bit_depth: int) -> np.ndarray:
+    raw = np.ascontiguousarray(raw)
+    out = np.empty(raw.shape, np.float64)
+    lib().orc_units(_ptr(raw), raw.dtype.itemsize, bit_depth, raw.size, _ptr(out))
+    return out
+
+
+def pyr_down(img: np.ndarray) -> np.ndarray:
+    img = _c(img, np.float64)
+    h, w = img.shape
+    out = np.empty(((h + 1) // 2, (w + 1) // 2), np.float64)
+    lib().orc_pyr_down(_ptr(img), w, h, _ptr(out))
+    return out
+
+
+def poly_projector(n_half: int, sigma: float) -> np.ndarray:
+    m = 2 * n_half + 1
+    P = np.empty((6, m * m), np.float64)
+    if lib().orc_poly_projector(n_half, sigma, _ptr(P)) != 0:
+        raise ValueError("singular Gram matrix")
+    return P
+
+
+def poly_expand(img: np.ndarray, n_half: int, sigma: float) -> np.ndarray:
+    """(5, h, w): A11, A12, A22, b1, b2."""
+    img = _c(img, np.float64)
+    h, w = img.shape
+    out = np.empty((5, h, w), np.float64)
+    if lib().orc_poly_expand(_ptr(img), w, h, n_half, sigma, _ptr(out)) != 0:
+        raise ValueError("singular Gram matrix")
+    return out
+
+
+def flow_upsample(dc: np.ndarray, w: int, h: int) -> np.ndarray:
+    dc = _c(dc, np.float64)
+    out = np.empty((2, h, w), np.float64)
+    lib().orc_flow_upsample(_ptr(dc), dc.shape[2], dc.shape[1], w, h, _ptr(out))
+    return out
+
+
+def flow_iterate(f1, f2, dprior, iters: int, win_r: int, lam: float) -> np.ndarray:
+    f1 = _c(f1, np.float64)
+    f2 = _c(f2, np.float64)
+    dprior = _c(dprior, np.float64)
+    _, h, w = f1.shape
+    out = np.empty((2, h, w), np.float64)
+    lib().orc_flow_iterate(_ptr(f1), _ptr(f2), w, h, _ptr(dprior), iters, win_r, lam, _ptr(out))
+    return out
+
+
+def flow(cur: np.ndarray, prev: np.ndarray, levels: int, n_half: int = 2, sigma: float = 1.1,
+         iters: int = 3, win_r: int = 7, lam: float = 1e-3) -> np.ndarray:
+    """(2, h, w) flow (dx, dy) on the grid of `cur`; f1 = cur, f2 = prev."""
+    cur = _c(cur, np.float64)
+    prev = _c(prev, np.float64)
+    h, w = cur.shape
+    out = np.empty((2, h, w), np.float64)
+    if lib().orc_flow(_ptr(cur), _ptr(prev), w, h, levels, n_half, sigma, iters, win_r, lam, _ptr(out)) != 0:
+        raise ValueError("bad flow arguments")
+    return out
+
+
+def saliency(d: np.ndarray, alpha: float) -> np.ndarray:
+    d = _c(d, np.float64)
+    _, h, w = d.shape
+    out = np.empty((h, w), np.float64)
+    lib().orc_saliency(_ptr(d), w, h, alpha, _ptr(out))
+    return out
+
+
+def normalise(S: np.ndarray) -> np.ndarray:
+    S = _c(S, np.float64)
+    out = np.empty_like(S)
+    lib().orc_normalise(_ptr(S), S.size, _ptr(out))
+    return out
+
+
+def quantile_k(q: float, n: int) -> int:
+    return int(lib().orc_quantile_k(q, n))
+
+
+def threshold(Sh: np.ndarray, q: float):
+    """(mask0 uint8, t) on double values."""
+    Sh = _c(Sh, np.float64)
+    m = np.empty(Sh.shape, np.uint8)
+    t = lib().orc_threshold(_ptr(Sh), Sh.size, q, _ptr(m))
+    return m, float(t)
+
+
+def threshold_f32(Sh: np.ndarray, q: float):
+    """(mask0 uint8, t) decided on single-precision values."""
+    Sh = _c(Sh, np.float32)
+    m = np.empty(Sh.shape, np.uint8)
+    t = lib().orc_threshold_f32(_ptr(Sh), Sh.size, q, _ptr(m))
+    return m, np.float32(t)
+
+
+def erode(m: np.ndarray, r: int) -> np.ndarray:
+    m = _c(m, np.uint8)
+    out = np.empty_like(m)
+    lib().orc_erode(_ptr(m), m.shape[1], m.shape[0], r, _ptr(out))
+    return out
+
+
+def dilate(m: np.ndarray, r: int) -> np.ndarray:
+    m = _c(m, np.uint8)
+    out = np.empty_like(m)
+    lib().orc_dilate(_ptr(m), m.shape[1], m.shape[0], r, _ptr(out))
+    return out
+
+
+def morph(m: np.ndarray, r_open: int, r_close: int) -> np.ndarray:
+    m = _c(m, np.uint8)
+    out = np.empty_like(m)
+    lib().orc_morph(_ptr(m), m.shape[1], m.shape[0], r_open, r_close, _ptr(out))
+    return out
+
+
+def dwt1d(x: np.ndarray, wavelet: int, inverse: bool = False) -> np.ndarray:
+    if wavelet == 53:
+        a = _c(x, np.int32).copy()
+        tmp = np.empty_like(a)
+        (lib().orc_idwt53_1d if inverse else lib().orc_dwt53_1d)(_ptr(a), a.size, _ptr(tmp))
+    else:
+        a = _c(x, np.float64).copy()
+        tmp = np.empty_like(a)
+        (lib().orc_idwt97_1d if inverse else lib().orc_dwt97_1d)(_ptr(a), a.size, _ptr(tmp))
+    return a
+
+
+def dwt2d(x: np.ndarray, wavelet: int, levels: int, inverse: bool = False) -> np.ndarray:
+    h, w = x.shape
+    if wavelet == 53:
+        a = _c(x, np.int32).copy()
+        (lib().orc_idwt53_2d if inverse else lib().orc_dwt53_2d)(_ptr(a), w, h, levels)
+    else:
+        a = _c(x, np.float64).copy()
+        (lib().orc_idwt97_2d if inverse else lib().orc_dwt97_2d)(_ptr(a), w, h, levels)
+    return a
+
+
+def dc_shift(raw: np.ndarray, bit_depth: int) -> np.ndarray:
+    raw = np.ascontiguousarray(raw)
+    out = np.empty(raw.shape, np.int32)
+    lib().orc_dc_shift(_ptr(raw), raw.dtype.itemsize, bit_depth, raw.size, _ptr(out))
+    return out
+
+
+def subband_index(x: int, y: int, w: int, h: int, levels: int) -> int:
+    return int(lib().orc_subband_index(x, y, w, h, levels))
+
+
+def delta_table(levels: int, bit_depth: int, delta_base: float = 1.0):
+    """(G, delta float32, eps, mu), each of length 3*levels+1."""
+    nb = 3 * levels + 1
+    G = np.empty(nb, np.float64)
+    d = np.empty(nb, np.float32)
+    e = np.empty(nb, np.int32)
+    m = np.empty(nb, np.int32)
+    if lib().orc_delta_table(levels, bit_depth, delta_base, _ptr(G), _ptr(d), _ptr(e), _ptr(m)) != 0:
+        raise ValueError("quantisation step exponent out of range")
+    return G, d, e, m
+
+
+def quantise_f32(y: np.ndarray, levels: int, delta: np.ndarray) -> np.ndarray:
+    y = _c(y, np.float32)
+    d = _c(delta, np.float32)
+    h, w = y.shape
+    q = np.empty((h, w), np.int32)
+    lib().orc_quantise_f32(_ptr(y), w, h, levels, _ptr(d), _ptr(q))
+    return q
+
+
+def quantise_f64(y: np.ndarray, levels: int, delta: np.ndarray) -> np.ndarray:
+    y = _c(y, np.float64)
+    d = _c(delta, np.float32)
+    h, w = y.shape
+    q = np.empty((h, w), np.int32)
+    lib().orc_quantise_f64(_ptr(y), w, h, levels, _ptr(d), _ptr(q))
+    return q
+
+
+def wavelet_mask(pix: np.ndarray, levels: int, wavelet: int) -> np.ndarray:
+    pix = _c(pix, np.uint8)
+    h, w = pix.shape
+    out = np.empty_like(pix)
+    lib().orc_wavelet_mask(_ptr(pix), w, h, levels, wavelet, _ptr(out))
+    return out
+
+
+def roi_shift(q: np.ndarray, cmask: np.ndarray, s: int) -> np.ndarray:
+    a = _c(q, np.int32).copy()
+    m = _c(cmask, np.uint8)
+    if lib().orc_roi_shift(_ptr(a), _ptr(m), a.size, s) != 0:
+        raise OverflowError("RoI up-shift overflows int32")
+    return a
+
+
+# ------------------------------------------------------------- pipeline --
+
+@dataclass
+class Params:
+    """Method parameters (the paper's Table 1 plus the estimator constants it
+    leaves unstated)."""
+    pyr_levels: int = 3
+    iters: int = 3
+    win_r: int = 7
+    poly_n_half: int = 2
+    poly_sigma: float = 1.1
+    lam: float = 1e-3
+    sal_weight: float = 0.7
+    roi_q: float = 0.2
+    r_open: int = 1
+    r_close: int = 2
+    wavelet: int = 53
+    dwt_levels: int = 3
+    scale_shift: int = 5
+    delta_base: float = 1.0
+
+
+def frame(prev_raw, cur_raw, bit_depth: int, p: Params, y_f32=None):
+    """Whole hot path for one frame pair (prev_raw = frame t-1 or None).
+
+    Returns a dict: flow (2,h,w) f64, S, Sh (f64), t, mask0, mask (uint8),
+    y (DWT coefficients: int32 for 5/3, f64 for 9/7), cmask (wavelet-domain
+    mask), q (quantised), coeffs (int32 after the RoI up-shift).  With no
+    predecessor the mask is empty (the first frame of a stream has no flow).
+
+    For 9/7, `y_f32` may carry single-precision DWT coefficients computed
+    elsewhere: quantisation then decides on those values (same precision as
+    a single-precision transform) instead of on the oracle's f64 values.
+    """
+    h, w = cur_raw.shape
+    out = {}
+    if prev_raw is not None:
+        I1 = units(cur_raw, bit_depth)
+        I2 = units(prev_raw, bit_depth)
+        d = flow(I1, I2, p.pyr_levels, p.poly_n_half, p.poly_sigma, p.iters, p.win_r, p.lam)
+        S = saliency(d, p.sal_weight)
+        Sh = normalise(S)
+        mask0, t = threshold(Sh, p.roi_q)
+        mask = morph(mask0, p.r_open, p.r_close)
+        out.update(flow=d, S=S, Sh=Sh, t=t, mask0=mask0)
+    else:
+        mask = np.zeros((h, w), np.uint8)
+    out["mask"] = mask
+    x = dc_shift(cur_raw, bit_depth)
+    cm = wavelet_mask(mask, p.dwt_levels, p.wavelet)
+    if p.wavelet == 53:
+        y = dwt2d(x, 53, p.dwt_levels)
+        q = y
+    else:
+        y = dwt2d(x.astype(np.float64), 97, p.dwt_levels)
+        _, delta, _, _ = delta_table(p.dwt_levels, bit_depth, p.delta_base)
+        q = quantise_f32(y_f32, p.dwt_levels, delta) if y_f32 is not None else quantise_f64(y, p.dwt_levels, delta)
+        out["delta"] = delta
+    out.update(y=y, cmask=cm, q=q, coeffs=roi_shift(q, cm, p.scale_shift))
+    return out
