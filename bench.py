@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Throughput of the FlowRoI hot path (flow -> RoI mask -> JPEG2000 front
+end) on GB300, through the library's C ABI.
+
+One step = one batch holding the next frame of every stream (16 streams of
+2048x2048 12-bit frames by default), i.e. one pass of the whole hot path:
+pyramid + expansion, coarse-to-fine displacement, saliency, exact quantile,
+opening/closing, 9/7 DWT with quantisation and RoI up-shift.
+
+Printed (one JSON line, rank 0):
+  value      frames/s with inputs resident in HBM (CUDA events on the
+             library's compute stream around K steps, max over ranks);
+  e2e        the same through host buffers: every step copies its frames
+             from pinned host memory and reads every mask and coefficient
+             plane back to pinned host memory;
+  plain_fps  the plain per-frame path (each frame launched alone, no graph);
+  latency    p50/p99 submit -> result-ready of the e2e run;
+  roofline   the dominant kernel (level-0 displacement) vs measured HBM
+             bandwidth, from per-kernel CUDA events;
+  cpu_baseline  the oracle on this host's cores on a bounded crop sample.
+`--impl reference` times the oracle alone (rank 0) on crops of the same
+workload and prints the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "frames/s (flow+mask+DWT) at 1 GB300 and p50/p99 frame latency vs plain per-frame path"
+
+WORKLOADS = {
+    # 16 streams (one per lens) x 32 frames of 2048^2 12-bit, 200 migrating
+    # blobs, 5-level pyramid, 9/7 DWT 5 levels in float32.
+    "batched_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                            dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
+    # same workload, pyramid and expansion fields stored in fp16
+    "fp16_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                         dwt_levels=5, wavelet=97, precision=16, seed_base=3000),
+    # one stream of 64 1024^2 12-bit frames, 5/3 DWT (plain method at full size)
+    "stream_1024": dict(streams=1, frames=64, h=1024, w=1024, blobs=80, bit_depth=12, pyr_levels=4,
+                        dwt_levels=5, wavelet=53, precision=32, seed_base=2000),
+}
+
+# Algorithmic bytes per level-0 pixel of one displacement launch (read
+# A1,A12,A22,b1,b2 of the current frame, the same five fields of the
+# previous frame at the warped position, the prior flow; write the flow):
+# 5+5 fields x 4 B + 8 + 8 = 56 B (fp32 storage), 5+5 fields x 2 B + 16 =
+# 36 B (fp16); the first iteration of a level reads the coarse flow (2 B/px).
+FLOW_BYTES = {32: (50.0, 56.0), 16: (30.0, 36.0)}
+# DRAM bytes per level-0 pixel per launch of that kernel measured by ncu on
+# the current kernel (null when not measured for this build).
+FLOW_TRAFFIC_PER_PX = {32: None, 16: None}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "100"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def make_frames(wl, device):
+    import torch
+
+    from synth import sequence_u16
+    frames = []
+    for s in range(wl["streams"]):
+        frames.append(sequence_u16(wl["seed_base"] + s, wl["frames"], wl["h"], wl["w"], wl["blobs"],
+                                   device=device))
+    torch.cuda.synchronize()
+    return frames
+
+
+def frame_index(t, n):
+    """Ping-pong through a sequence of n frames (0..n-1, n-2..0, ...)."""
+    period = 2 * (n - 1)
+    k = t % period
+    return k if k < n else period - k
+
+
+def submit(F, ctx, sid, data, idx, bd):
+    while True:
+        try:
+            return F.flowroi_submit_frame(ctx, sid, data, idx, bd)
+        except F.FlowRoIError as e:
+            if e.code != F.EBUSY:
+                raise
+            time.sleep(50e-6)
+
+
+def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampler_device=None):
+    """Device-resident run: returns dict(time_s, frames, launches, kernel_times, stats, clocks)."""
+    import torch
+    cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
+               precision=wl["precision"], max_batch_frames=64, result_ring=4,
+               flags=F.MANUAL | (F.PLAIN if plain else 0), device=torch.cuda.current_device())
+    S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
+    res = {}
+    with F.Context(**cfg) as ctx:
+        stream = torch.cuda.ExternalStream(F.flowroi_compute_stream(ctx.h))
+        t = 0
+
+        def one_step():
+            nonlocal t
+            i = frame_index(t, n)
+            for s in range(S):
+                submit(F, ctx.h, s, frames[s][i], t, bd)
+            if plain:
+                while F.flowroi_step(ctx.h) > 0:
+                    pass
+            else:
+                F.flowroi_step(ctx.h)
+            t += 1
+
+        one_step()  # first frames: no predecessor
+        for _ in range(warmup):
+            one_step()
+        F.flowroi_flush(ctx.h, -1)
+        torch.cuda.synchronize()
+        l0 = F.flowroi_get_stats(ctx.h)["kernel_launches"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(sampler_device) if sampler_device is not None else None
+        if sampler:
+            sampler.__enter__()
+        e0.record(stream)
+        for _ in range(steps):
+            one_step()
+        e1.record(stream)
+        F.flowroi_flush(ctx.h, -1)
+        e1.synchronize()
+        if sampler:
+            sampler.__exit__(None, None, None)
+            res["clocks"] = sampler.summary()
+        res["time_s"] = e0.elapsed_time(e1) / 1e3
+        res["frames"] = steps * S
+        st = F.flowroi_get_stats(ctx.h)
+        res["launches"] = st["kernel_launches"] - l0
+        res["stats"] = st
+        if profile_steps:
+            F.flowroi_set_profiling(ctx.h, 2)
+            for _ in range(profile_steps):
+                one_step()
+            F.flowroi_flush(ctx.h, -1)
+            res["kernel_times"] = F.flowroi_get_kernel_times(ctx.h)
+            F.flowroi_set_profiling(ctx.h, 0)
+    return res
+
+
+def run_e2e(F, wl, frames, steps, warmup):
+    """Host-buffer run through the public API: pinned host frames in,
+    pinned host masks and coefficients out, every step."""
+    import torch
+    S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
+    nh = min(n, 8)
+    host = [[frames[s][i].cpu().pin_memory() for i in range(nh)] for s in range(S)]
+    h, w = wl["h"], wl["w"]
+    masks = [torch.empty((h, w), dtype=torch.uint8).pin_memory() for _ in range(S)]
+    coefs = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(S)]
+    cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
+               precision=wl["precision"], max_batch_frames=64, result_ring=4, flags=F.MANUAL,
+               device=torch.cuda.current_device())
+    res = {}
+    with F.Context(**cfg) as ctx:
+        t = 0
+
+        def submit_step():
+            nonlocal t
+            i = frame_index(t, nh)
+            for s in range(S):
+                submit(F, ctx.h, s, host[s][i], t, bd)
+            F.flowroi_step(ctx.h)
+            t += 1
+
+        def fetch(step):
+            for s in range(S):
+                F.flowroi_get_mask(ctx.h, s, step, masks[s], -1)
+                F.flowroi_get_coeffs(ctx.h, s, step, coefs[s], -1)
+
+        submit_step()
+        fetch(0)
+        for _ in range(warmup):
+            submit_step()
+            fetch(t - 1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            submit_step()
+            if k:
+                fetch(t - 2)
+        fetch(t - 1)
+        dt = time.perf_counter() - t0
+        st = F.flowroi_get_stats(ctx.h)
+    res["time_s"] = dt
+    res["frames"] = steps * S
+    res["h2d"] = S * h * w * 2
+    res["d2h"] = S * h * w * (1 + 4)
+    res["stats"] = st
+    return res
+
+
+def cpu_sample(wl, frames_cpu, budget_s=12.0, crop=512):
+    """The oracle (as it stands, single-threaded) on crop pairs of the
+    workload; returns (frames/s scaled to full frames, seconds, crops)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    p = O.Params(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"])
+    h, w = wl["h"], wl["w"]
+    done, t0, k = 0, time.perf_counter(), 0
+    while True:
+        s = k % len(frames_cpu)
+        a, b = frames_cpu[s]
+        y0 = (k * 389) % (h - crop + 1) // 32 * 32
+        x0 = (k * 613) % (w - crop + 1) // 32 * 32
+        O.frame(np.ascontiguousarray(a[y0:y0 + crop, x0:x0 + crop]), np.ascontiguousarray(b[y0:y0 + crop, x0:x0 + crop]),
+                wl["bit_depth"], p)
+        done += 1
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s and done >= 2:
+            break
+    px_per_s = done * crop * crop / el
+    return px_per_s / (h * w), el, done
+
+
+def reference_arm(args, wl, ws, rank):
+    """The oracle as the reference implementation (rank 0 only)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    from oracle import oracle as O
+    from synth import sequence_u16
+    crop = 256
+    seqs = [sequence_u16(wl["seed_base"] + s, 2, wl["h"], wl["w"], wl["blobs"], device="cpu")
+            for s in range(min(2, wl["streams"]))]
+    pairs = [(q[0].numpy().view(np.uint16), q[1].numpy().view(np.uint16)) for q in seqs]
+    p = O.Params(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"])
+
+    def step(k):
+        a, b = pairs[k % len(pairs)]
+        y0 = (k * 389) % (wl["h"] - crop + 1) // 32 * 32
+        x0 = (k * 613) % (wl["w"] - crop + 1) // 32 * 32
+        O.frame(np.ascontiguousarray(a[y0:y0 + crop, x0:x0 + crop]), np.ascontiguousarray(b[y0:y0 + crop, x0:x0 + crop]),
+                wl["bit_depth"], p)
+
+    for k in range(args.warmup):
+        step(k)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        step(args.warmup + k)
+    dt = time.perf_counter() - t0
+    fps = args.steps * crop * crop / dt / (wl["h"] * wl["w"])
+    line = {"impl": "reference", "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(args.workload, wl),
+            "cpu_baseline": {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} crops of {crop}x{crop} from the workload's frame pairs, "
+                                       f"time scaled to {wl['w']}x{wl['h']} frames by pixel count"},
+            "e2e": {"value": fps, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(name, wl):
+    return {"workload": name, "streams": wl["streams"], "frame": f"{wl['w']}x{wl['h']} u16 ({wl['bit_depth']}-bit)",
+            "frames_per_stream": wl["frames"], "blobs": wl["blobs"], "batch_frames": wl["streams"],
+            "pyr_levels": wl["pyr_levels"], "dwt": f"{wl['wavelet'] // 10}/{wl['wavelet'] % 10} x{wl['dwt_levels']}",
+            "storage": "fp16" if wl["precision"] == 16 else "fp32",
+            "l2": "inputs larger than L2 (each step touches ~2.5 GB of frames and fields)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--workload", default="batched_16x2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        reference_arm(args, wl, ws, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_14419_gb300 import build
+    from paper_2511_14419_gb300 import flowroi as F
+    build()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    frames = make_frames(wl, f"cuda:{local}")
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    barrier()
+    dev = run_device(F, wl, frames, args.steps, args.warmup, profile_steps=min(args.steps, 10), sampler_device=local)
+    barrier()
+    t_max = max_over_ranks(dev["time_s"])
+    value = dev["frames"] * ws / t_max
+
+    plain = None
+    if not args.no_plain:
+        ps = max(3, min(args.steps, 20))
+        pr = run_device(F, wl, frames, ps, args.warmup, plain=True)
+        barrier()
+        plain = pr["frames"] * ws / max_over_ranks(pr["time_s"])
+
+    e2e = None
+    if not args.no_e2e:
+        es = max(3, min(args.steps, 20))
+        er = run_e2e(F, wl, frames, es, args.warmup)
+        barrier()
+        e2e = {"value": er["frames"] * ws / max_over_ranks(er["time_s"]), "unit": "frames/s",
+               "h2d_bytes_per_step": er["h2d"], "d2h_bytes_per_step": er["d2h"]}
+        latency = {"p50_ms": er["stats"]["lat_p50_ms"], "p99_ms": er["stats"]["lat_p99_ms"],
+                   "source": "e2e run, submit -> result ready"}
+    else:
+        latency = None
+
+    # roofline of the dominant kernel: level-0 displacement iterations
+    peak, peak_kind = peaks()
+    kt = dev.get("kernel_times") or []
+    tot = sum(k["total_ms"] for k in kt) or 1.0
+    flow0 = [k for k in kt if k["name"] == "flow" and k["level"] == 0]
+    px = wl["h"] * wl["w"] * wl["streams"]
+    b_first, b_rest = FLOW_BYTES[wl["precision"]]
+    roof = None
+    if flow0:
+        byts = sum((b_first if k["iter"] == 0 else b_rest) * px * k["launches"] for k in flow0)
+        ms = sum(k["total_ms"] for k in flow0)
+        nl = sum(k["launches"] for k in flow0)
+        achieved = byts / (ms / 1e3) / 1e9
+        tr = FLOW_TRAFFIC_PER_PX[wl["precision"]]
+        roof = {"kernel": "k_flow level 0 (update+window+solve)", "bound": "hbm", "achieved": achieved,
+                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                "traffic": (tr * px) if tr else None, "algorithmic_bytes_per_launch": byts / nl,
+                "avg_launch_ms": ms / nl, "share_of_step": ms / tot}
+    kernels = {}
+    for k in kt:
+        key = k["name"] + ("" if k["level"] < 0 else f"[{k['level']}]")
+        kernels[key] = round(kernels.get(key, 0.0) + k["total_ms"] / max(1, k["launches"]), 4)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        import numpy as np
+        fc = [(frames[s][0].cpu().numpy().view(np.uint16), frames[s][1].cpu().numpy().view(np.uint16))
+              for s in range(min(2, wl["streams"]))]
+        fps_cpu, el, nc = cpu_sample(wl, fc)
+        cpu = {"value": fps_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nc} crops of 512x512 from the workload's first frame pairs ({el:.1f} s), "
+                         f"time scaled to {wl['w']}x{wl['h']} frames by pixel count; host has {os.cpu_count()} cores"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": config_of(args.workload, wl), "e2e": e2e, "gpu_launches": dev["launches"],
+                "plain_fps": plain, "latency": latency, "clocks": dev.get("clocks"), "roofline": roof,
+                "cpu_baseline": cpu, "kernel_avg_ms": kernels}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

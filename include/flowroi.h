@@ -1,0 +1,270 @@
+/*
+ * flowroi.h: C ABI of the GB300 (sm_103a) FlowRoI hot-path library.
+ *
+ * FlowRoI ("FlowRoI: A Fast Optical-Flow-Driven Region-of-Interest
+ * Extraction Framework for High-Throughput Image Compression in Immune Cell
+ * Migration Analysis", arXiv 2511.14419) turns a stream of grey frames into,
+ * per frame, a binary region-of-interest mask and the JPEG2000 wavelet
+ * coefficients that a scaling-based RoI encoder codes:
+ *
+ *   §Method / §Optical flow extraction: dense two-frame Farneback optical
+ *       flow between the frame and its predecessor (Gaussian pyramid,
+ *       polynomial expansion, iterated windowed displacement solve, coarse
+ *       to fine);
+ *   §Region of Interest extraction: saliency from the flow magnitude and
+ *       its spatial gradient (weight 0.7), min-max normalisation, a
+ *       quantile cut keeping the top "RoI threshold" fraction, opening and
+ *       closing;
+ *   §Implementation details + Table 1: JPEG2000 scaling-based RoI coding
+ *       of the raw frame under that mask: DC level shift, lifting DWT
+ *       (reversible 5/3 or irreversible 9/7), quantisation, and the up-shift
+ *       of RoI coefficients by the scaling factor.
+ *
+ * EBCOT / rate control / codestream assembly are downstream consumers of
+ * the coefficients and are not part of this library.
+ *
+ * Every step runs in this library's CUDA kernels on one GPU; the host side
+ * only validates, copies and schedules.  The library owns its device
+ * memory (one allocation per admitted stream, from the CUDA stream-ordered
+ * allocator) and its CUDA streams.
+ *
+ * Conventions
+ *   - Every int-returning call returns FLOWROI_OK (0) or a negative status.
+ *   - Pointers are plain host or device pointers; whether a data pointer is
+ *     on the device is stated by an explicit flag next to it.  Device
+ *     pointers must belong to the context's device.
+ *   - Images are row-major, x (columns) fastest.  Flow is stored as
+ *     interleaved (dx, dy) float pairs.
+ *   - Strings returned by flowroi_last_error stay valid until the next call
+ *     on the same context from the same thread.
+ *   - A context is safe to use from several host threads.
+ */
+#ifndef FLOWROI_H
+#define FLOWROI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLOWROI_ABI_VERSION 1
+
+/* Exported symbols (the library is built with hidden default visibility). */
+#if defined(__GNUC__)
+#define FLOWROI_API __attribute__((visibility("default")))
+#else
+#define FLOWROI_API
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FLOWROI_OK 0
+#define FLOWROI_EINVAL (-1)     /* bad argument, descriptor, size or frame order */
+#define FLOWROI_ENOSTREAM (-2)  /* unknown stream, or frame never submitted */
+#define FLOWROI_EBUSY (-3)      /* retry later: HBM budget (stream not admitted yet) or
+                                   the stream's frame ring is full of unfinished frames */
+#define FLOWROI_ENOMEM (-4)     /* device or host allocation failed */
+#define FLOWROI_ETIMEDOUT (-5)  /* a bounded wait expired; nothing was copied */
+#define FLOWROI_EDEVICE (-6)    /* a CUDA error was seen; the context is poisoned */
+#define FLOWROI_EGONE (-7)      /* result overwritten: the stream's result ring wrapped */
+#define FLOWROI_ENOTKEPT (-8)   /* intermediate requested without FLOWROI_KEEP_INTERMEDIATES */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define FLOWROI_U8 1            /* 8-bit unsigned samples */
+#define FLOWROI_U16 2           /* 16-bit unsigned samples (e.g. 12-bit data) */
+#define FLOWROI_W53 53          /* reversible integer 5/3 lifting DWT (no quantisation) */
+#define FLOWROI_W97 97          /* irreversible 9/7 lifting DWT, single precision, quantised */
+#define FLOWROI_FP32 32         /* pyramid and expansion fields stored in float */
+#define FLOWROI_FP16 16         /* ... stored in half, all arithmetic in float */
+
+/* flowroi_config.flags */
+#define FLOWROI_KEEP_INTERMEDIATES 0x1u /* keep flow, saliency, pre-morphology mask and
+                                           (9/7) float coefficients per result slot */
+#define FLOWROI_PLAIN 0x2u              /* plain per-frame path: each frame runs alone,
+                                           one grid per frame, no CUDA graphs */
+#define FLOWROI_MANUAL 0x4u             /* no scheduler thread: the caller launches batches
+                                           with flowroi_step (deterministic batch makeup) */
+
+/* flowroi_get_intermediate: `which` */
+#define FLOWROI_I_FLOW 1        /* float[2*W*H]: level-0 flow (dx, dy) interleaved */
+#define FLOWROI_I_SALIENCY 2    /* float[W*H]: normalised saliency S^ in [0, 1] */
+#define FLOWROI_I_MASK0 3       /* uint8[W*H]: mask before opening/closing (0/1) */
+#define FLOWROI_I_COEFF_F32 4   /* float[W*H]: 9/7 coefficients before quantisation, Mallat */
+#define FLOWROI_I_THRESHOLD 5   /* float[1]: the cut t on S^ (mask0 = S^ > t) */
+
+/* ---- configuration ----------------------------------------------------- */
+/* Method parameters.  Table 1 of the paper names the user parameters (RoI
+ * threshold, scaling factor; denoise and adjacent factor are not on this
+ * path; compression rate acts downstream).  The estimator constants are not
+ * given by the paper; the defaults are the values this library documents
+ * (pyramid 5 levels, 3 iterations, 15x15 box window, 5x5 expansion with
+ * sigma 1.1, lambda 1e-3 in 8-bit units, opening radius 1, closing
+ * radius 2). */
+typedef struct flowroi_config {
+    uint32_t struct_size;      /* = sizeof(flowroi_config) */
+    float roi_q;               /* RoI threshold q in (0,1): keep at most floor(q*W*H) pixels (0.2) */
+    int32_t scale_shift;       /* scaling factor s in [0, 15]: RoI coefficients times 2^s (5) */
+    int32_t wavelet;           /* FLOWROI_W53 or FLOWROI_W97 */
+    int32_t dwt_levels;        /* D in [1, 8] */
+    int32_t pyr_levels;        /* L in [1, 8] */
+    int32_t iters;             /* displacement iterations per pyramid level, [1, 8] (3) */
+    int32_t win_r;             /* box window radius r in [1, 12]: side 2r+1 (7) */
+    int32_t poly_n_half;       /* expansion radius n in {2, 3}: side 2n+1 (2) */
+    float poly_sigma;          /* applicability sigma (1.1) */
+    float lambda;              /* solve regulariser, added to det (1e-3) */
+    float sal_weight;          /* alpha: S = alpha*|d| + (1-alpha)*|grad|d|| (0.7) */
+    int32_t r_open;            /* opening radius in [0, 8] (1) */
+    int32_t r_close;           /* closing radius in [0, 8] (2) */
+    int32_t precision;         /* FLOWROI_FP32 or FLOWROI_FP16 */
+    float delta_base;          /* 9/7: base quantisation step (1.0) */
+    int32_t max_batch_frames;  /* frames per batched launch, [1, 64] (64) */
+    int32_t result_ring;       /* frames kept per stream (input and result slots), [2, 16] (4) */
+    uint32_t flags;            /* FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL */
+    int32_t device;            /* CUDA device ordinal (0) */
+    uint64_t hbm_budget_bytes; /* admission budget for all streams' device state;
+                                  0 = 80% of the device memory free at create */
+} flowroi_config;
+
+/* One input frame.  Frames of a stream keep their width, height, dtype and
+ * bit depth; frame_idx strictly increases.  width and height must be
+ * multiples of 2^max(dwt_levels, pyr_levels - 1) and at least 16. */
+typedef struct flowroi_frame {
+    uint32_t struct_size;      /* = sizeof(flowroi_frame) */
+    int32_t width, height;
+    int32_t pitch_bytes;       /* row pitch of `data`; 0 = width * sample size */
+    int32_t dtype;             /* FLOWROI_U8 or FLOWROI_U16 */
+    int32_t bit_depth;         /* significant bits B: 1..8 (U8) or 1..16 (U16) */
+    int64_t frame_idx;
+    const void *data;          /* samples; host or device (see data_on_device) */
+    int32_t data_on_device;    /* 1: `data` is a device pointer */
+} flowroi_frame;
+
+typedef struct flowroi_stats {
+    uint32_t struct_size;      /* = sizeof(flowroi_stats) */
+    int64_t frames_submitted, frames_done, batches;
+    int64_t streams_admitted;  /* streams currently holding device state */
+    int64_t admissions_refused;
+    uint64_t bytes_admitted, budget_bytes;
+    double lat_p50_ms, lat_p99_ms, lat_mean_ms; /* submit -> result ready, frames done so far */
+    int64_t kernel_launches;   /* this library's kernels launched so far (graph nodes counted) */
+} flowroi_stats;
+
+/* Opaque context: one GPU, its streams, its scheduler. */
+typedef struct flowroi_ctx flowroi_ctx;
+
+/* Fill *cfg with the documented defaults (5/3, D = 3, L = 3, FP32,
+ * scheduler thread on). */
+FLOWROI_API void flowroi_default_config(flowroi_config *cfg);
+
+/* Create a context on cfg->device.  Every field is validated
+ * (FLOWROI_EINVAL; flowroi_last_error(NULL) names the field).  Starts the
+ * scheduler thread unless FLOWROI_MANUAL.  *out receives the context,
+ * owned by the caller until flowroi_destroy.  No device memory is held
+ * until the first stream is admitted. */
+FLOWROI_API int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out);
+
+/* Submit frame `f` of stream `stream_id` (§Method: the image sequence of
+ * one well/lens).  A new stream_id creates a stream on its first frame and
+ * is admitted only if its device state fits the HBM budget; otherwise
+ * FLOWROI_EBUSY (nothing kept; retry after other streams end).  The frame
+ * is copied before the call returns (host data: host-to-device copy
+ * completed; device data: device-to-device copy ordered before its use), so
+ * the caller keeps ownership of f->data.  FLOWROI_EBUSY too when the
+ * stream already has result_ring frames not yet processed.  The first frame
+ * of a stream has no predecessor: its mask is empty and its coefficients
+ * are the plain (unshifted) JPEG2000 front end. */
+FLOWROI_API int flowroi_submit_frame(flowroi_ctx *ctx, int64_t stream_id, const flowroi_frame *f);
+
+/* Launch one batch now: for every stream with a pending frame, its oldest
+ * one, at most max_batch_frames frames (FLOWROI_PLAIN: one frame per
+ * launch sequence, still all pending streams).  Returns the number of
+ * frames launched (>= 0) or a negative status.  Needed only with
+ * FLOWROI_MANUAL; harmless otherwise. */
+FLOWROI_API int flowroi_step(flowroi_ctx *ctx);
+
+/* Copy out the RoI mask of (stream_id, frame_idx): W*H bytes, 0 or 1,
+ * row-major, into caller-owned `out` (device memory if out_on_device).
+ * Waits at most timeout_ms (< 0: no limit) for the frame to finish, then
+ * copies; FLOWROI_ETIMEDOUT if it did not finish in time (nothing copied).
+ * FLOWROI_EGONE if the stream's result ring has since been overwritten. */
+FLOWROI_API int flowroi_get_mask(flowroi_ctx *ctx, int64_t stream_id, int64_t frame_idx, uint8_t *out,
+                     int out_on_device, int timeout_ms);
+
+/* Copy out the wavelet coefficients of (stream_id, frame_idx): W*H int32,
+ * Mallat layout (per level the low-low band top-left, HL right of it, LH
+ * below, HH diagonal), after quantisation (9/7) and the RoI up-shift
+ * q <- sign(q) * (|q| << s) of every coefficient whose synthesis support
+ * meets the mask (§Implementation details, scaling-based RoI).  Same
+ * waiting, ownership and errors as flowroi_get_mask. */
+FLOWROI_API int flowroi_get_coeffs(flowroi_ctx *ctx, int64_t stream_id, int64_t frame_idx, int32_t *out,
+                       int out_on_device, int timeout_ms);
+
+/* Copy out an intermediate of (stream_id, frame_idx) (`which`: one of
+ * FLOWROI_I_*, sizes as listed there) for inspection and tests.  Needs
+ * FLOWROI_KEEP_INTERMEDIATES (else FLOWROI_ENOTKEPT).  A first frame has
+ * no flow: its flow and saliency are zero and its threshold is +inf. */
+FLOWROI_API int flowroi_get_intermediate(flowroi_ctx *ctx, int64_t stream_id, int64_t frame_idx, int which,
+                             void *out, int out_on_device, int timeout_ms);
+
+/* Launch everything pending and wait (at most timeout_ms, < 0: no limit)
+ * until every submitted frame has finished. */
+FLOWROI_API int flowroi_flush(flowroi_ctx *ctx, int timeout_ms);
+
+/* End a stream: waits for its frames in flight, then frees its device
+ * state and returns its bytes to the admission budget.  Later frames with
+ * the same id start a new stream. */
+FLOWROI_API int flowroi_end_stream(flowroi_ctx *ctx, int64_t stream_id);
+
+/* Counters and latency percentiles since create. */
+FLOWROI_API int flowroi_get_stats(flowroi_ctx *ctx, flowroi_stats *out);
+
+/* Stop the scheduler, wait for the device, free everything.  NULL is a
+ * no-op. */
+FLOWROI_API void flowroi_destroy(flowroi_ctx *ctx);
+
+/* Human-readable reason for the last failing call of this thread on ctx
+ * (ctx may be NULL for flowroi_create failures). */
+FLOWROI_API const char *flowroi_last_error(flowroi_ctx *ctx);
+
+/* The 9/7 quantisation steps (§Implementation details: quantisation of the
+ * irreversible path; the paper gives no step sizes).  For subband b the step
+ * is delta_base / sqrt(G_b), G_b the squared norm of b's 2-D synthesis basis
+ * function, written in the JPEG2000 form 2^(R_b - eps) * (1 + mu / 2^11)
+ * with R_b = bit_depth + gain_b (gain 0 LL, 1 HL/LH, 2 HH).  Output arrays
+ * (caller-owned host memory, length 3*levels + 1) are indexed
+ * 3*(level-1) + orientation (0 HL, 1 LH, 2 HH) and 3*levels for the final
+ * low-low band; any of them may be NULL.  Host-only, no device use. */
+FLOWROI_API int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps,
+                        int32_t *mu, double *gain_norm);
+
+/* The CUDA stream (cudaStream_t, as void*) on which every batch of ctx
+ * runs, for callers that time or order work against it (e.g. record CUDA
+ * events around steps).  Owned by the context; do not destroy. */
+FLOWROI_API int flowroi_compute_stream(flowroi_ctx *ctx, void **out);
+
+/* Per-kernel timing (tracing).  With profiling on, batches launch their
+ * kernels directly (no graph replay) with a CUDA event pair around every
+ * launch on the compute stream.  flowroi_get_kernel_times waits for the
+ * device, folds the recorded pairs into per-(kernel, level) totals and
+ * copies at most `cap` rows into caller-owned `out`; returns the number of
+ * rows (or a negative status).  Turning profiling off keeps the totals;
+ * flowroi_set_profiling(ctx, 2) clears them and turns profiling on. */
+typedef struct flowroi_kernel_time {
+    char name[24];       /* "expand", "flow", "saliency", "select_pass", "select_find",
+                            "morph", "dwt", "frame_init" */
+    int32_t level;       /* pyramid level (expand, flow), DWT level (dwt), digit pass, or -1 */
+    int32_t iter;        /* displacement iteration (flow), else -1 */
+    int64_t launches;
+    double total_ms;
+} flowroi_kernel_time;
+FLOWROI_API int flowroi_set_profiling(flowroi_ctx *ctx, int on);
+FLOWROI_API int flowroi_get_kernel_times(flowroi_ctx *ctx, flowroi_kernel_time *out, int cap);
+
+/* Library ABI version (FLOWROI_ABI_VERSION). */
+FLOWROI_API int flowroi_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,143 @@
+// Device-visible descriptors and small device helpers shared by the
+// FlowRoI kernels and the runtime that fills them.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace flowroi {
+
+constexpr int kMaxLevels = 8;    // pyramid and DWT levels
+constexpr int kMaxBatch = 64;    // frames per batched launch
+constexpr int kHistBins = 2048;  // radix-select digit of 11 bits
+constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
+
+// Tile shapes (output pixels per block) of each kernel family.
+constexpr int kExpTW = 64, kExpTH = 16;   // pyramid + polynomial expansion
+constexpr int kFlowTW = 32, kFlowTH = 32; // displacement update + window + solve
+constexpr int kSalTW = 64, kSalTH = 16;   // saliency, radix-select passes
+constexpr int kMorTW = 64, kMorTH = 32;   // threshold + opening + closing
+constexpr int kDwtTW = 32, kDwtTH = 16;   // DWT: band coefficients per block (per band)
+
+// Per-frame reduction block (device), one per frame slot.
+//   [0] min of S (float bits), [1] max of S, [2] select prefix,
+//   [3] remaining rank, [4] t_S bits, [5] t_hat bits,
+//   [kRedHist .. +kHistBins) histogram of the current radix digit.
+constexpr int kRedMin = 0, kRedMax = 1, kRedPrefix = 2, kRedRank = 3, kRedTS = 4, kRedTHat = 5;
+constexpr int kRedHist = 8;
+constexpr int kRedWords = kRedHist + kHistBins;
+
+// Method constants of a context (passed by value to every kernel).
+struct MethodConsts {
+    // polynomial expansion: 1-D applicability a(u), u = -n..n, and the
+    // closed-form projection constants of the separable fit.
+    int n_half;
+    float app[7];
+    float inv_s0s2;   // r_u = <u,f> / (s0 s2), r_v likewise
+    float inv_s2s2;   // r_uv = <uv,f> / s2^2
+    float m_uu[3];    // r_uu = m_uu . (<1,f>, <u^2,f>, <v^2,f>)
+    float m_vv[3];    // r_vv likewise
+    // displacement
+    int pyr_levels, iters, win_r;
+    float lambda;
+    // saliency / threshold / morphology
+    float alpha;      // weight of |d|
+    float q;          // RoI threshold
+    int r_open, r_close;
+    // JPEG2000 front end
+    int wavelet, dwt_levels, shift;
+    float delta[kMaxSubbands];
+};
+
+// One frame of a batch.  Level geometry: lw/lh = level size, lp = pitch in
+// elements.  All planes of the previous frame of the same stream are read
+// through fq_prev / fb_prev.
+struct FrameDesc {
+    int W, H, bpp, bit_depth;
+    int has_prev, keep, raw_pitch, dc_off;  // raw_pitch in bytes; dc_off = 2^(B-1)
+    float unit_scale;                        // 255 / (2^B - 1)
+    int pad0, pad1, pad2;
+    const void *raw;
+    int lw[kMaxLevels], lh[kMaxLevels], lp[kMaxLevels];
+    void *pyr[kMaxLevels];          // level images 1..L-1 (storage type)
+    void *fq_cur[kMaxLevels];       // A11, A12, A22, b1 (4 x storage type per pixel)
+    void *fb_cur[kMaxLevels];       // b2 (storage type per pixel)
+    const void *fq_prev[kMaxLevels];
+    const void *fb_prev[kMaxLevels];
+    float2 *flow[2];                // ping-pong flow buffers, level-0 capacity
+    float *S;                       // saliency, pitch lp[0]
+    unsigned *red;                  // reduction block (kRedWords)
+    uint8_t *mask;                  // result mask, W*H
+    int32_t *coeffs;                // result coefficients, W*H (Mallat)
+    float2 *dbg_flow;               // keep: level-0 flow, W*H (else null)
+    float *dbg_shat;                // keep: normalised saliency, W*H
+    uint8_t *dbg_mask0;             // keep: mask before morphology, W*H
+    float *dbg_yf;                  // keep + 9/7: float coefficients, W*H
+    float *dbg_thr;                 // keep: threshold on S^ (1 float)
+    void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
+    uint8_t *llm[2];                // their RoI masks
+};
+
+// A batch: per kernel family and level, an exclusive prefix over frames of
+// their tile counts (blocks binary-search it to find their frame).
+struct BatchDesc {
+    int nframes;
+    int final_flow_buf;             // ping-pong index holding the level-0 flow
+    int pad[2];
+    int exp_off[kMaxLevels][kMaxBatch + 1];
+    int flow_off[kMaxLevels][kMaxBatch + 1];
+    int dwt_off[kMaxLevels][kMaxBatch + 1];
+    int sal_off[kMaxBatch + 1];     // frames with a predecessor only
+    int mor_off[kMaxBatch + 1];     // every frame
+    int frm_off[kMaxBatch + 1];     // one unit per frame (init / select-find)
+    FrameDesc f[kMaxBatch];
+};
+
+#ifdef __CUDACC__
+// Frame owning global tile t: largest i with off[i] <= t (off[0] = 0).
+__device__ __forceinline__ int find_frame(const int *off, int nframes, int t)
+{
+    int lo = 0, hi = nframes - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(off + mid) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+// Storage conversions.
+template <typename T> struct Store;
+template <> struct Store<float> {
+    using T4 = float4;
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ float4 ld4(const float4 *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void st4(float4 *p, float a, float b, float c, float d) { *p = make_float4(a, b, c, d); }
+    static __device__ __forceinline__ float4 f4(float4 v) { return v; }
+};
+template <> struct Store<__half> {
+    using T4 = uint2;  // four halves
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ uint2 ld4(const uint2 *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void st4(uint2 *p, float a, float b, float c, float d)
+    {
+        __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+        uint2 u;
+        u.x = *reinterpret_cast<unsigned *>(&lo);
+        u.y = *reinterpret_cast<unsigned *>(&hi);
+        *p = u;
+    }
+    static __device__ __forceinline__ float4 f4(uint2 u)
+    {
+        __half2 lo = *reinterpret_cast<__half2 *>(&u.x), hi = *reinterpret_cast<__half2 *>(&u.y);
+        float2 a = __half22float2(lo), b = __half22float2(hi);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+#endif
+
+}  // namespace flowroi

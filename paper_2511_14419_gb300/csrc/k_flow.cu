@@ -1,0 +1,254 @@
+// Farneback displacement estimation: one iteration at one pyramid level,
+// fused (update, box window, 2x2 solve) in one pass over a tile.
+//
+// Paper: §Optical flow extraction (dense Farneback flow between adjacent
+// frames).  With f1 = the current frame and f2 = its predecessor, and a
+// prior displacement d~ (the coarser level's flow, bilinearly upsampled at
+// (x/2, y/2) and doubled, at the first iteration of a level; the previous
+// iteration's flow after that):
+//     A  = (A1(x) + A2(x + d~)) / 2             (A2, b2 read bilinearly,
+//     db = -(b2(x + d~) - b1(x)) / 2 + A d~      position clamped to the image)
+//     G  = A^T A,  h = A^T db
+//     G_, h_ = means over the (2r+1)^2 box around x (clipped to the image)
+//     d  = adj(G_) h_ / (det G_ + lambda)
+//
+// Tile scheme: a block owns kFlowTW x kFlowTH output pixels.  Phase 1
+// computes G, h (5 floats) for the tile plus an r-pixel apron into shared
+// memory; phase 2 sums every column over 2r+1 rows; phase 3 sums every row
+// over 2r+1 columns; phase 4 solves.  Phases 2-3 keep a column (row) in
+// registers and add it as a tree of power-of-two partial sums (no running
+// sums: every window is a fresh sum of its own 2r+1 terms).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace flowroi {
+
+namespace {
+
+// out[i] = v[i] + ... + v[i + WN - 1] for i < N - WN + 1, as a tree of
+// power-of-two partial sums (all indices compile-time after unrolling).
+template <int N, int WN>
+__device__ __forceinline__ void box_sums(const float (&v)[N], float (&out)[N - WN + 1])
+{
+    constexpr int M = N - WN + 1;
+    float p2[N], p4[N], p8[N], p16[N];
+#pragma unroll
+    for (int i = 0; i + 1 < N; i++) p2[i] = v[i] + v[i + 1];
+#pragma unroll
+    for (int i = 0; i + 3 < N; i++) p4[i] = p2[i] + p2[i + 2];
+#pragma unroll
+    for (int i = 0; i + 7 < N; i++) p8[i] = p4[i] + p4[i + 4];
+#pragma unroll
+    for (int i = 0; i + 15 < N; i++) p16[i] = p8[i] + p8[i + 8];
+#pragma unroll
+    for (int i = 0; i < M; i++) {
+        float s = 0.f;
+        int o = 0;
+        bool any = false;
+        if (WN & 16) { s = p16[i]; o += 16; any = true; }
+        if (WN & 8) { s = any ? s + p8[i + o] : p8[i + o]; o += 8; any = true; }
+        if (WN & 4) { s = any ? s + p4[i + o] : p4[i + o]; o += 4; any = true; }
+        if (WN & 2) { s = any ? s + p2[i + o] : p2[i + o]; o += 2; any = true; }
+        if (WN & 1) { s = any ? s + v[i + o] : v[i + o]; }
+        out[i] = s;
+    }
+}
+
+// a*b - c*d with one rounding error at most a few ulps (FMA error-free
+// transformation of c*d).
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d)
+{
+    const float cd = c * d;
+    const float err = fmaf(-c, d, cd);
+    const float dop = fmaf(a, b, -cd);
+    return dop + err;
+}
+
+}  // namespace
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256, 2)
+    k_flow(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int iter, int src, int dst)
+{
+    constexpr int TW = kFlowTW, TH = kFlowTH;
+    constexpr int EW = TW + 2 * R, EH = TH + 2 * R, WN = 2 * R + 1;
+    constexpr int SEG = 16;  // outputs per thread in the horizontal pass
+    extern __shared__ float smem[];
+    float *gh = smem;                // [5][EH][EW]; later [5][TH][TW] horizontal sums
+    float *vs = smem + 5 * EH * EW;  // [5][TH][EW] vertical sums
+    using ST = Store<T>;
+    using T4 = typename ST::T4;
+
+    const int nfr = bd->nframes;
+    const int *off = bd->flow_off[level];
+    const int total = __ldg(off + nfr);
+    const bool top = level == mc.pyr_levels - 1;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int fi = find_frame(off, nfr, t);
+        const FrameDesc &F = bd->f[fi];
+        const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
+        const int ntx = (w + TW - 1) / TW;
+        const int lt = t - __ldg(off + fi);
+        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
+        const T4 *q1 = static_cast<const T4 *>(F.fq_cur[level]);
+        const T *b1p = static_cast<const T *>(F.fb_cur[level]);
+        const T4 *q2 = static_cast<const T4 *>(F.fq_prev[level]);
+        const T *b2p = static_cast<const T *>(F.fb_prev[level]);
+        const float2 *fsrc = F.flow[src];
+
+        // ---- phase 1: G, h on the tile plus apron
+        for (int i = threadIdx.x; i < EH * EW; i += blockDim.x) {
+            const int ey = i / EW, ex = i - ey * EW;
+            const int gx = x0 - R + ex, gy = y0 - R + ey;
+            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f, o4 = 0.f;
+            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
+                float ddx = 0.f, ddy = 0.f;
+                if (iter > 0) {
+                    const float2 v = fsrc[(size_t)gy * p + gx];
+                    ddx = v.x;
+                    ddy = v.y;
+                } else if (!top) {
+                    const int wc = F.lw[level + 1], hc = F.lh[level + 1], pc = F.lp[level + 1];
+                    const int cx = gx >> 1, cy = gy >> 1;
+                    const int cx1 = min(cx + 1, wc - 1), cy1 = min(cy + 1, hc - 1);
+                    const float fx = (gx & 1) ? 0.5f : 0.f, fy = (gy & 1) ? 0.5f : 0.f;
+                    const float2 a = fsrc[(size_t)cy * pc + cx], b = fsrc[(size_t)cy * pc + cx1];
+                    const float2 c = fsrc[(size_t)cy1 * pc + cx], d = fsrc[(size_t)cy1 * pc + cx1];
+                    ddx = 2.f * ((1.f - fy) * ((1.f - fx) * a.x + fx * b.x) + fy * ((1.f - fx) * c.x + fx * d.x));
+                    ddy = 2.f * ((1.f - fy) * ((1.f - fx) * a.y + fx * b.y) + fy * ((1.f - fx) * c.y + fx * d.y));
+                }
+                // Sample position x + d~ split into integer and fraction so
+                // the fraction keeps full precision; clamped to the image.
+                const float flx = floorf(ddx), fly = floorf(ddy);
+                int ix = gx + (int)flx, iy = gy + (int)fly;
+                float fx = ddx - flx, fy = ddy - fly;
+                if (ix < 0) { ix = 0; fx = 0.f; } else if (ix >= w - 1) { ix = w - 1; fx = 0.f; }
+                if (iy < 0) { iy = 0; fy = 0.f; } else if (iy >= h - 1) { iy = h - 1; fy = 0.f; }
+                const int ix1 = min(ix + 1, w - 1), iy1 = min(iy + 1, h - 1);
+                const size_t r0 = (size_t)iy * p, r1 = (size_t)iy1 * p;
+                const float4 qa = ST::f4(ST::ld4(q2 + r0 + ix)), qb = ST::f4(ST::ld4(q2 + r0 + ix1));
+                const float4 qc = ST::f4(ST::ld4(q2 + r1 + ix)), qd = ST::f4(ST::ld4(q2 + r1 + ix1));
+                const float ba = ST::ld(b2p + r0 + ix), bb = ST::ld(b2p + r0 + ix1);
+                const float bc = ST::ld(b2p + r1 + ix), bdd = ST::ld(b2p + r1 + ix1);
+                const float A11b = ((1.f - fy) * ((1.f - fx) * qa.x + fx * qb.x) + fy * ((1.f - fx) * qc.x + fx * qd.x));
+                const float A12b = ((1.f - fy) * ((1.f - fx) * qa.y + fx * qb.y) + fy * ((1.f - fx) * qc.y + fx * qd.y));
+                const float A22b = ((1.f - fy) * ((1.f - fx) * qa.z + fx * qb.z) + fy * ((1.f - fx) * qc.z + fx * qd.z));
+                const float b1b = ((1.f - fy) * ((1.f - fx) * qa.w + fx * qb.w) + fy * ((1.f - fx) * qc.w + fx * qd.w));
+                const float b2b = ((1.f - fy) * ((1.f - fx) * ba + fx * bb) + fy * ((1.f - fx) * bc + fx * bdd));
+                const size_t o = (size_t)gy * p + gx;
+                const float4 qs = ST::f4(ST::ld4(q1 + o));
+                const float b2a = ST::ld(b1p + o);
+                const float a11 = 0.5f * (qs.x + A11b), a12 = 0.5f * (qs.y + A12b), a22 = 0.5f * (qs.z + A22b);
+                const float db1 = -0.5f * (b1b - qs.w) + (a11 * ddx + a12 * ddy);
+                const float db2 = -0.5f * (b2b - b2a) + (a12 * ddx + a22 * ddy);
+                o0 = a11 * a11 + a12 * a12;
+                o1 = a11 * a12 + a12 * a22;
+                o2 = a12 * a12 + a22 * a22;
+                o3 = a11 * db1 + a12 * db2;
+                o4 = a12 * db1 + a22 * db2;
+            }
+            gh[0 * EH * EW + i] = o0;
+            gh[1 * EH * EW + i] = o1;
+            gh[2 * EH * EW + i] = o2;
+            gh[3 * EH * EW + i] = o3;
+            gh[4 * EH * EW + i] = o4;
+        }
+        __syncthreads();
+
+        // ---- phase 2: vertical window sums, one (field, column) per item
+        for (int it = threadIdx.x; it < 5 * EW; it += blockDim.x) {
+            const int k = it / EW, ex = it - k * EW;
+            float v[EH], s[TH];
+#pragma unroll
+            for (int j = 0; j < EH; j++) v[j] = gh[k * EH * EW + j * EW + ex];
+            box_sums<EH, WN>(v, s);
+#pragma unroll
+            for (int j = 0; j < TH; j++) vs[k * TH * EW + j * EW + ex] = s[j];
+        }
+        __syncthreads();
+
+        // ---- phase 3: horizontal window sums, one (field, row, segment) per item
+        for (int it = threadIdx.x; it < 5 * TH * (TW / SEG); it += blockDim.x) {
+            const int k = it / (TH * (TW / SEG));
+            const int rem = it - k * TH * (TW / SEG);
+            const int row = rem / (TW / SEG), sg = rem - row * (TW / SEG);
+            float v[SEG + 2 * R], s[SEG];
+#pragma unroll
+            for (int j = 0; j < SEG + 2 * R; j++) v[j] = vs[k * TH * EW + row * EW + sg * SEG + j];
+            box_sums<SEG + 2 * R, WN>(v, s);
+#pragma unroll
+            for (int j = 0; j < SEG; j++) gh[k * TH * TW + row * TW + sg * SEG + j] = s[j];
+        }
+        __syncthreads();
+
+        // ---- phase 4: means and 2x2 solve
+        float2 *fdst = F.flow[dst];
+        for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
+            const int r = i / TW, c = i - r * TW;
+            const int gx = x0 + c, gy = y0 + r;
+            if (gx >= w || gy >= h) continue;
+            const int cnt = (min(gx + R, w - 1) - max(gx - R, 0) + 1) * (min(gy + R, h - 1) - max(gy - R, 0) + 1);
+            const float fc = (float)cnt;
+            const float g11 = gh[0 * TH * TW + i] / fc, g12 = gh[1 * TH * TW + i] / fc, g22 = gh[2 * TH * TW + i] / fc;
+            const float h1 = gh[3 * TH * TW + i] / fc, h2 = gh[4 * TH * TW + i] / fc;
+            const float det = diff_of_products(g11, g22, g12, g12) + mc.lambda;
+            const float nx = diff_of_products(g22, h1, g12, h2);
+            const float ny = diff_of_products(g11, h2, g12, h1);
+            fdst[(size_t)gy * p + gx] = make_float2(nx / det, ny / det);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int R>
+static void launch_flow_t(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, int dst, int grid,
+                          cudaStream_t s)
+{
+    constexpr int EW = kFlowTW + 2 * R, EH = kFlowTH + 2 * R;
+    const size_t sm = sizeof(float) * (5 * EH * EW + 5 * kFlowTH * EW);
+    // The dynamic shared-memory limit was raised by occ_flow_t at set-up.
+    k_flow<T, R><<<grid, 256, sm, s>>>(bd, mc, level, iter, src, dst);
+}
+
+template <typename T, int R>
+static int occ_flow_t()
+{
+    constexpr int EW = kFlowTW + 2 * R, EH = kFlowTH + 2 * R;
+    const size_t sm = sizeof(float) * (5 * EH * EW + 5 * kFlowTH * EW);
+    cudaFuncSetAttribute(k_flow<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flow<T, R>, 256, sm);
+    return b;
+}
+
+#define FLOWROI_FLOW_RADII(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
+
+void launch_flow(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, int dst, bool half,
+                 int grid, cudaStream_t s)
+{
+    switch (mc.win_r) {
+#define CASE(RR)                                                                           \
+    case RR:                                                                               \
+        if (half) launch_flow_t<__half, RR>(bd, mc, level, iter, src, dst, grid, s);       \
+        else launch_flow_t<float, RR>(bd, mc, level, iter, src, dst, grid, s);             \
+        break;
+        FLOWROI_FLOW_RADII(CASE)
+#undef CASE
+    default: break;
+    }
+}
+
+int occupancy_flow(bool half, int win_r)
+{
+    switch (win_r) {
+#define CASE(RR) \
+    case RR: return half ? occ_flow_t<__half, RR>() : occ_flow_t<float, RR>();
+        FLOWROI_FLOW_RADII(CASE)
+#undef CASE
+    default: return 0;
+    }
+}
+
+bool flow_radius_supported(int r) { return r >= 2 && r <= 10; }
+
+}  // namespace flowroi

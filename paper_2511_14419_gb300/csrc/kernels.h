@@ -1,0 +1,35 @@
+// Host-side launchers of the FlowRoI kernels (one translation unit per
+// kernel family).  `grid` is the number of blocks; every kernel walks its
+// tiles with a grid-stride loop, so any grid >= 1 is correct.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace flowroi {
+
+void launch_expand(const BatchDesc *bd, const MethodConsts &mc, int level, bool half, int grid, cudaStream_t s);
+void launch_flow(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, int dst, bool half,
+                 int grid, cudaStream_t s);
+void launch_frame_init(const BatchDesc *bd, int grid, cudaStream_t s);
+void launch_saliency(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
+void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s);
+void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
+void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
+void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
+
+// Resident blocks per SM (also sets any shared-memory attribute the kernel
+// needs; call once per device before the first launch).
+int occupancy_expand(bool half, int n_half);
+int occupancy_flow(bool half, int win_r);
+int occupancy_mask_kernels();
+int occupancy_dwt(int wavelet);
+
+bool flow_radius_supported(int r);
+bool morph_radius_supported(int r);
+
+// 9/7 quantisation steps (host, double precision); see flowroi_quant_steps.
+int quant_steps(int levels, int bit_depth, double delta_base, float *delta, int *eps, int *mu, double *gain);
+
+}  // namespace flowroi

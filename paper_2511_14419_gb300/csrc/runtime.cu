@@ -1,0 +1,1093 @@
+// FlowRoI runtime and C ABI (see include/flowroi.h for the contract).
+//
+// One context = one GPU.  Every stream (one microscope well / lens, the
+// paper's "image sequence") owns one device block, allocated on admission
+// from the stream-ordered allocator and sized from its frame geometry:
+//   - a ring of R input frames and R result slots (mask, coefficients,
+//     optional intermediates);
+//   - two sets of polynomial-expansion fields (this frame's and the
+//     previous frame's, alternating by frame parity): the previous
+//     frame's expansion stays resident, so each frame expands only itself;
+//   - the per-frame temporaries of one frame in flight (pyramid, flow
+//     ping-pong, saliency, reduction block, DWT low-low planes).
+// Streams are admitted while the sum of their blocks fits the HBM budget.
+//
+// Batches: a scheduler thread (or flowroi_step in manual mode) takes, for
+// every stream, its oldest pending frame, fills a batch descriptor (frames,
+// per-kernel tile prefixes) in pinned memory, copies it to the device and
+// replays a CUDA graph of the whole hot path whose kernels read the
+// descriptor.  Every kernel loops over (frame, tile) work with a fixed
+// persistent grid, so one captured graph serves any batch makeup: streams
+// of different resolutions are continuously batched without recapture.
+// At most two batches are in flight; a host function after each batch
+// stamps completion times.  The plain path (FLOWROI_PLAIN) runs each frame
+// alone with exact grids and direct launches, for comparison.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "../../include/flowroi.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace flowroi;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+double now_ms()
+{
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+enum EntryState { E_EMPTY = 0, E_PENDING = 2, E_LAUNCHED = 3, E_DONE = 4 };
+
+struct Entry {
+    int64_t frame_idx = -1;
+    int64_t seq = -1;
+    std::atomic<int> state{E_EMPTY};
+    bool has_prev = false;
+    double t_submit = 0.0, t_done = 0.0;
+    int readers = 0;
+    cudaEvent_t uploaded = nullptr;
+    void *raw = nullptr;
+    uint8_t *mask = nullptr;
+    int32_t *coeffs = nullptr;
+    float2 *dbg_flow = nullptr;
+    float *dbg_shat = nullptr;
+    uint8_t *dbg_mask0 = nullptr;
+    float *dbg_yf = nullptr;
+    float *dbg_thr = nullptr;
+};
+
+struct Stream {
+    int64_t id = 0;
+    int W = 0, H = 0, bpp = 0, bit_depth = 0;
+    size_t bytes = 0;
+    char *block = nullptr;
+    int64_t next_seq = 0;
+    int64_t last_frame_idx = 0;
+    bool any_frame = false;
+    int64_t launched_seq = -1;
+    bool ending = false;
+    std::vector<std::unique_ptr<Entry>> ring;
+    int lw[kMaxLevels] = {}, lh[kMaxLevels] = {}, lp[kMaxLevels] = {};
+    void *fq[2][kMaxLevels] = {};
+    void *fb[2][kMaxLevels] = {};
+    void *pyr[kMaxLevels] = {};
+    float2 *flow[2] = {};
+    float *S = nullptr;
+    unsigned *red = nullptr;
+    void *ll[2] = {};
+    uint8_t *llm[2] = {};
+};
+
+struct BatchRec;
+
+}  // namespace
+
+struct flowroi_ctx {
+    flowroi_config cfg{};
+    MethodConsts mc{};
+    int device = 0, num_sms = 0;
+    bool half = false, plain = false, keep = false, manual = false;
+    cudaStream_t s_comp = nullptr, s_copy = nullptr, s_d2h = nullptr, s_cap = nullptr;
+    std::mutex mu;       // host state: streams, entries, descriptors
+    std::mutex d2h_mu;   // serialises copies out on s_d2h
+    std::mutex cmu;      // completion state + scheduler wake-ups (never held across CUDA calls)
+    std::condition_variable ccv;
+    std::map<int64_t, std::unique_ptr<Stream>> streams;
+    int64_t rr_cursor = INT64_MIN;
+    uint64_t budget = 0, admitted = 0;
+    static constexpr int kDesc = 3;
+    BatchDesc *desc_host[kDesc] = {};
+    BatchDesc *desc_dev[kDesc] = {};
+    cudaEvent_t desc_ev[kDesc] = {};
+    cudaGraphExec_t graph[kDesc] = {};
+    int graph_launches = 0;
+    int desc_next = 0;
+    int grid_exp = 0, grid_flow = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0;
+    int inflight = 0;               // guarded by cmu
+    int max_inflight = 2;
+    bool work_flag = false;         // guarded by cmu
+    bool shutdown = false;          // guarded by cmu
+    std::thread sched;
+    std::atomic<bool> poisoned{false};
+    std::string poison_msg;
+    int64_t frames_submitted = 0, frames_cancelled = 0;  // guarded by mu
+    int64_t frames_done = 0;                              // guarded by cmu
+    std::atomic<int64_t> batches{0}, refused{0}, launches{0};
+    std::vector<double> lat_ms;                           // guarded by cmu
+    // per-kernel event timing (guarded by mu)
+    bool profiling = false;
+    struct ProfRec { int kid, level, iter; cudaEvent_t a, b; };
+    std::vector<ProfRec> prof_pending;
+    std::map<std::tuple<int, int, int>, std::pair<int64_t, double>> prof_tot;
+};
+
+namespace {
+
+struct BatchRec {
+    flowroi_ctx *ctx;
+    std::vector<Entry *> entries;
+};
+
+int cuda_fail(flowroi_ctx *c, cudaError_t e, const char *what)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s", what, cudaGetErrorString(e));
+    if (c) {
+        c->poisoned = true;
+        c->poison_msg = buf;
+    }
+    g_err = buf;
+    return FLOWROI_EDEVICE;
+}
+
+#define CK(ctx, call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+// ------------------------------------------------------------ validation --
+int validate_config(const flowroi_config *c)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "config is NULL");
+    if (c->struct_size != sizeof(flowroi_config)) return fail(FLOWROI_EINVAL, "config.struct_size mismatch");
+    if (!(c->roi_q > 0.f && c->roi_q < 1.f)) return fail(FLOWROI_EINVAL, "config.roi_q must be in (0,1)");
+    if (c->scale_shift < 0 || c->scale_shift > 15) return fail(FLOWROI_EINVAL, "config.scale_shift must be in [0,15]");
+    if (c->wavelet != FLOWROI_W53 && c->wavelet != FLOWROI_W97) return fail(FLOWROI_EINVAL, "config.wavelet must be 53 or 97");
+    if (c->dwt_levels < 1 || c->dwt_levels > kMaxLevels) return fail(FLOWROI_EINVAL, "config.dwt_levels must be in [1,8]");
+    if (c->pyr_levels < 1 || c->pyr_levels > kMaxLevels) return fail(FLOWROI_EINVAL, "config.pyr_levels must be in [1,8]");
+    if (c->iters < 1 || c->iters > 8) return fail(FLOWROI_EINVAL, "config.iters must be in [1,8]");
+    if (!flow_radius_supported(c->win_r)) return fail(FLOWROI_EINVAL, "config.win_r must be in [2,10]");
+    if (c->poly_n_half != 2 && c->poly_n_half != 3) return fail(FLOWROI_EINVAL, "config.poly_n_half must be 2 or 3");
+    if (!(c->poly_sigma > 0.f)) return fail(FLOWROI_EINVAL, "config.poly_sigma must be > 0");
+    if (!(c->lambda > 0.f)) return fail(FLOWROI_EINVAL, "config.lambda must be > 0");
+    if (!(c->sal_weight >= 0.f && c->sal_weight <= 1.f)) return fail(FLOWROI_EINVAL, "config.sal_weight must be in [0,1]");
+    if (!morph_radius_supported(c->r_open) || !morph_radius_supported(c->r_close))
+        return fail(FLOWROI_EINVAL, "config.r_open/r_close must be in [0,4]");
+    if (c->precision != FLOWROI_FP32 && c->precision != FLOWROI_FP16) return fail(FLOWROI_EINVAL, "config.precision must be 32 or 16");
+    if (!(c->delta_base > 0.f)) return fail(FLOWROI_EINVAL, "config.delta_base must be > 0");
+    if (c->max_batch_frames < 1 || c->max_batch_frames > kMaxBatch) return fail(FLOWROI_EINVAL, "config.max_batch_frames must be in [1,64]");
+    if (c->result_ring < 2 || c->result_ring > 16) return fail(FLOWROI_EINVAL, "config.result_ring must be in [2,16]");
+    if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL)) return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
+    return FLOWROI_OK;
+}
+
+// Closed-form constants of the separable polynomial expansion.
+void expansion_consts(int n, double sigma, MethodConsts &mc)
+{
+    double a[7] = {}, s0 = 0, s2 = 0, s4 = 0;
+    for (int u = -n; u <= n; u++) {
+        a[u + n] = std::exp(-(double)(u * u) / (2.0 * sigma * sigma));
+        s0 += a[u + n];
+        s2 += a[u + n] * u * u;
+        s4 += a[u + n] * u * u * u * u;
+    }
+    for (int i = 0; i < 7; i++) mc.app[i] = (float)a[i];
+    mc.n_half = n;
+    mc.inv_s0s2 = (float)(1.0 / (s0 * s2));
+    mc.inv_s2s2 = (float)(1.0 / (s2 * s2));
+    // M = [[s0^2, s0 s2, s0 s2], [s0 s2, s0 s4, s2^2], [s0 s2, s2^2, s0 s4]]
+    // acting on (r_1, r_uu, r_vv); rows 1 and 2 of its inverse by cofactors.
+    double M[3][3] = {{s0 * s0, s0 * s2, s0 * s2}, {s0 * s2, s0 * s4, s2 * s2}, {s0 * s2, s2 * s2, s0 * s4}};
+    double det = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                 M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+    double inv[3][3];
+    for (int i = 0; i < 3; i++)
+        for (int j = 0; j < 3; j++) {
+            int r0 = (j + 1) % 3, r1 = (j + 2) % 3, c0 = (i + 1) % 3, c1 = (i + 2) % 3;
+            inv[i][j] = (M[r0][c0] * M[r1][c1] - M[r0][c1] * M[r1][c0]) / det;
+        }
+    for (int j = 0; j < 3; j++) {
+        mc.m_uu[j] = (float)inv[1][j];
+        mc.m_vv[j] = (float)inv[2][j];
+    }
+}
+
+int tiles(int w, int h, int tw, int th) { return ((w + tw - 1) / tw) * ((h + th - 1) / th); }
+
+int64_t stream_is_launchable(Stream *s)
+{
+    if (s->ending) return -1;
+    const int64_t next = s->launched_seq + 1;
+    if (next >= s->next_seq) return -1;
+    Entry *e = s->ring[next % (int64_t)s->ring.size()].get();
+    // (Readers never block a launch: a reader of this slot waits for this very
+    // frame; submit refuses to reuse a slot that is being read.)
+    if (e->seq != next || e->state.load() != E_PENDING) return -1;
+    return next;
+}
+
+// Byte plan of a stream's device block (carves pointers when base != null).
+size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
+{
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        off = align_up(off, 256);
+        char *p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const int L = c->cfg.pyr_levels, R = c->cfg.result_ring;
+    const size_t esz = c->half ? 2 : 4;
+    const size_t npx = (size_t)s->W * s->H;
+    for (int l = 0; l < L; l++) {
+        s->lw[l] = s->W >> l;
+        s->lh[l] = s->H >> l;
+        s->lp[l] = (int)align_up((size_t)s->lw[l], 32);
+    }
+    for (int k = 0; k < 2; k++)
+        for (int l = 0; l < L; l++) {
+            s->fq[k][l] = take((size_t)s->lp[l] * s->lh[l] * 4 * esz);
+            s->fb[k][l] = take((size_t)s->lp[l] * s->lh[l] * esz);
+        }
+    for (int l = 1; l < L; l++) s->pyr[l] = take((size_t)s->lp[l] * s->lh[l] * esz);
+    for (int k = 0; k < 2; k++) s->flow[k] = reinterpret_cast<float2 *>(take((size_t)s->lp[0] * s->H * sizeof(float2)));
+    s->S = reinterpret_cast<float *>(take((size_t)s->lp[0] * s->H * sizeof(float)));
+    s->red = reinterpret_cast<unsigned *>(take(kRedWords * sizeof(unsigned)));
+    for (int k = 0; k < 2; k++) {
+        s->ll[k] = take((npx / 4) * 4);
+        s->llm[k] = reinterpret_cast<uint8_t *>(take(npx / 4));
+    }
+    for (int r = 0; r < R; r++) {
+        Entry *e = s->ring[r].get();
+        e->raw = take(npx * s->bpp);
+        e->mask = reinterpret_cast<uint8_t *>(take(npx));
+        e->coeffs = reinterpret_cast<int32_t *>(take(npx * 4));
+        if (c->keep) {
+            e->dbg_flow = reinterpret_cast<float2 *>(take(npx * sizeof(float2)));
+            e->dbg_shat = reinterpret_cast<float *>(take(npx * 4));
+            e->dbg_mask0 = reinterpret_cast<uint8_t *>(take(npx));
+            e->dbg_yf = c->cfg.wavelet == FLOWROI_W97 ? reinterpret_cast<float *>(take(npx * 4)) : nullptr;
+            e->dbg_thr = reinterpret_cast<float *>(take(sizeof(float)));
+        }
+    }
+    return align_up(off, 256);
+}
+
+void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
+{
+    std::memset(&F, 0, sizeof F);
+    F.W = s->W;
+    F.H = s->H;
+    F.bpp = s->bpp;
+    F.bit_depth = s->bit_depth;
+    F.has_prev = e->has_prev ? 1 : 0;
+    F.keep = c->keep ? 1 : 0;
+    F.raw_pitch = s->W * s->bpp;
+    F.dc_off = 1 << (s->bit_depth - 1);
+    F.unit_scale = (float)(255.0 / (double)((1 << s->bit_depth) - 1));
+    F.raw = e->raw;
+    const int cur = (int)(e->seq & 1), prv = cur ^ 1;
+    for (int l = 0; l < c->cfg.pyr_levels; l++) {
+        F.lw[l] = s->lw[l];
+        F.lh[l] = s->lh[l];
+        F.lp[l] = s->lp[l];
+        F.pyr[l] = s->pyr[l];
+        F.fq_cur[l] = s->fq[cur][l];
+        F.fb_cur[l] = s->fb[cur][l];
+        F.fq_prev[l] = s->fq[prv][l];
+        F.fb_prev[l] = s->fb[prv][l];
+    }
+    F.flow[0] = s->flow[0];
+    F.flow[1] = s->flow[1];
+    F.S = s->S;
+    F.red = s->red;
+    F.mask = e->mask;
+    F.coeffs = e->coeffs;
+    F.dbg_flow = e->dbg_flow;
+    F.dbg_shat = e->dbg_shat;
+    F.dbg_mask0 = e->dbg_mask0;
+    F.dbg_yf = e->dbg_yf;
+    F.dbg_thr = e->dbg_thr;
+    F.ll[0] = s->ll[0];
+    F.ll[1] = s->ll[1];
+    F.llm[0] = s->llm[0];
+    F.llm[1] = s->llm[1];
+}
+
+// Prefix tables of the batch (also the exact grids of the plain path).
+void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
+{
+    const int n = bd.nframes;
+    const int L = c->cfg.pyr_levels, D = c->cfg.dwt_levels;
+    for (int l = 0; l < kMaxLevels; l++) {
+        bd.exp_off[l][0] = bd.flow_off[l][0] = bd.dwt_off[l][0] = 0;
+    }
+    bd.sal_off[0] = bd.mor_off[0] = bd.frm_off[0] = 0;
+    for (int i = 0; i < n; i++) {
+        const FrameDesc &F = bd.f[i];
+        for (int l = 0; l < L; l++) {
+            bd.exp_off[l][i + 1] = bd.exp_off[l][i] + tiles(F.lw[l], F.lh[l], kExpTW, kExpTH);
+            bd.flow_off[l][i + 1] = bd.flow_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kFlowTW, kFlowTH) : 0);
+        }
+        for (int l = 1; l <= D; l++)
+            bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH);
+        bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
+        bd.mor_off[i + 1] = bd.mor_off[i] + tiles(F.W, F.H, kMorTW, kMorTH);
+        bd.frm_off[i + 1] = i + 1;
+    }
+}
+
+const char *const kKernelNames[] = {"frame_init", "expand", "flow", "saliency", "select_find", "select_pass", "morph", "dwt"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_FLOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT };
+
+// Runs one launch, bracketed by an event pair when profiling.
+template <class Fn>
+void timed(flowroi_ctx *c, cudaStream_t st, bool prof, int kid, int level, int iter, Fn fn)
+{
+    if (!prof) {
+        fn();
+        return;
+    }
+    flowroi_ctx::ProfRec r{kid, level, iter, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, st);
+    fn();
+    cudaEventRecord(r.b, st);
+    c->prof_pending.push_back(r);
+}
+
+// The hot path for one batch descriptor.  `hd` (host copy) gives exact grids
+// on the plain path; the batched path uses fixed persistent grids.
+int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, cudaStream_t st, int *nlaunch, bool prof)
+{
+    const MethodConsts &mc = c->mc;
+    const int L = c->cfg.pyr_levels, D = c->cfg.dwt_levels, I = c->cfg.iters;
+    const int n = hd->nframes;
+    const bool pl = c->plain;
+    auto g = [&](int exact, int persistent) { return pl ? std::max(exact, 1) : persistent; };
+    int cnt = 0;
+    const bool any_prev = !pl || hd->sal_off[n] > 0;
+    timed(c, st, prof, K_INIT, -1, -1, [&] { launch_frame_init(dd, g(n, c->grid_frames), st); });
+    cnt++;
+    for (int l = 0; l < L; l++) {
+        timed(c, st, prof, K_EXPAND, l, -1, [&] { launch_expand(dd, mc, l, c->half, g(hd->exp_off[l][n], c->grid_exp), st); });
+        cnt++;
+    }
+    if (any_prev) {
+        int k = 0;
+        for (int l = L - 1; l >= 0; l--)
+            for (int it = 0; it < I; it++, k++) {
+                const int dst = k & 1;
+                timed(c, st, prof, K_FLOW, l, it, [&] {
+                    launch_flow(dd, mc, l, it, dst ^ 1, dst, c->half, g(hd->flow_off[l][n], c->grid_flow), st);
+                });
+                cnt++;
+            }
+        timed(c, st, prof, K_SAL, -1, -1, [&] { launch_saliency(dd, mc, g(hd->sal_off[n], c->grid_mask), st); });
+        for (int pass = 0; pass < 3; pass++) {
+            if (pass > 0)
+                timed(c, st, prof, K_PASS, pass, -1, [&] { launch_select_pass(dd, pass, g(hd->sal_off[n], c->grid_mask), st); });
+            timed(c, st, prof, K_FIND, pass, -1, [&] { launch_select_find(dd, mc, pass, g(n, c->grid_frames), st); });
+        }
+        cnt += 6;
+    }
+    timed(c, st, prof, K_MORPH, -1, -1, [&] { launch_morph(dd, mc, g(hd->mor_off[n], c->grid_mask), st); });
+    cnt++;
+    for (int l = 1; l <= D; l++) {
+        timed(c, st, prof, K_DWT, l, -1, [&] { launch_dwt(dd, mc, l, g(hd->dwt_off[l - 1][n], c->grid_dwt), st); });
+        cnt++;
+    }
+    *nlaunch = cnt;
+    return FLOWROI_OK;
+}
+
+void CUDART_CB on_batch_done(void *p)
+{
+    BatchRec *r = static_cast<BatchRec *>(p);
+    flowroi_ctx *c = r->ctx;
+    const double t = now_ms();
+    {
+        std::lock_guard<std::mutex> lk(c->cmu);
+        for (Entry *e : r->entries) {
+            e->t_done = t;
+            e->state.store(E_DONE);
+            c->lat_ms.push_back(t - e->t_submit);
+            c->frames_done++;
+        }
+        c->inflight--;
+    }
+    c->ccv.notify_all();
+    delete r;
+}
+
+// Launch one batch (mu held).  Returns frames launched or a negative status.
+int step_locked(flowroi_ctx *c)
+{
+    if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+    const int maxb = c->plain ? 1 : c->cfg.max_batch_frames;
+    std::vector<std::pair<Stream *, Entry *>> sel;
+    // Round-robin over streams, starting after the last one served.
+    auto it = c->streams.upper_bound(c->rr_cursor);
+    for (size_t visited = 0; visited < c->streams.size() && (int)sel.size() < maxb; visited++) {
+        if (it == c->streams.end()) it = c->streams.begin();
+        Stream *s = it->second.get();
+        const int64_t seq = stream_is_launchable(s);
+        if (seq >= 0) sel.emplace_back(s, s->ring[seq % (int64_t)s->ring.size()].get());
+        ++it;
+    }
+    if (sel.empty()) return 0;
+    c->rr_cursor = sel.back().first->id;
+
+    const int k = c->desc_next;
+    c->desc_next = (k + 1) % flowroi_ctx::kDesc;
+    CK(c, cudaEventSynchronize(c->desc_ev[k]));
+    BatchDesc &hd = *c->desc_host[k];
+    hd.nframes = (int)sel.size();
+    const int nflow = c->cfg.pyr_levels * c->cfg.iters;
+    hd.final_flow_buf = (nflow - 1) & 1;
+    for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].first, sel[i].second, hd.f[i]);
+    fill_offsets(c, hd);
+    for (auto &pr : sel) CK(c, cudaStreamWaitEvent(c->s_comp, pr.second->uploaded, 0));
+    const size_t bytes = offsetof(BatchDesc, f) + sizeof(FrameDesc) * sel.size();
+    CK(c, cudaMemcpyAsync(c->desc_dev[k], c->desc_host[k], bytes, cudaMemcpyHostToDevice, c->s_comp));
+    CK(c, cudaEventRecord(c->desc_ev[k], c->s_comp));
+    int nl = 0;
+    if (c->plain || c->profiling) {
+        enqueue_pipeline(c, c->desc_dev[k], &hd, c->s_comp, &nl, c->profiling);
+        CK(c, cudaGetLastError());
+    } else {
+        if (!c->graph[k]) {
+            cudaGraph_t gr = nullptr;
+            CK(c, cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeThreadLocal));
+            enqueue_pipeline(c, c->desc_dev[k], &hd, c->s_cap, &nl, false);
+            cudaError_t e1 = cudaGetLastError();
+            cudaError_t e2 = cudaStreamEndCapture(c->s_cap, &gr);
+            if (e1 != cudaSuccess) return cuda_fail(c, e1, "kernel launch during capture");
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+            cudaError_t e3 = cudaGraphInstantiate(&c->graph[k], gr, 0);
+            cudaGraphDestroy(gr);
+            if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
+            c->graph_launches = nl;
+        }
+        nl = c->graph_launches;
+        CK(c, cudaGraphLaunch(c->graph[k], c->s_comp));
+    }
+    BatchRec *rec = new BatchRec{c, {}};
+    for (auto &pr : sel) {
+        pr.second->state.store(E_LAUNCHED);
+        pr.first->launched_seq = pr.second->seq;
+        rec->entries.push_back(pr.second);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->cmu);
+        c->inflight++;
+    }
+    cudaError_t eh = cudaLaunchHostFunc(c->s_comp, on_batch_done, rec);
+    if (eh != cudaSuccess) {
+        delete rec;
+        return cuda_fail(c, eh, "cudaLaunchHostFunc");
+    }
+    c->batches++;
+    c->launches += nl;
+    return (int)sel.size();
+}
+
+bool any_launchable(flowroi_ctx *c)
+{
+    for (auto &kv : c->streams)
+        if (stream_is_launchable(kv.second.get()) >= 0) return true;
+    return false;
+}
+
+void scheduler_main(flowroi_ctx *c)
+{
+    cudaSetDevice(c->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(c->cmu);
+            c->ccv.wait_for(lk, std::chrono::milliseconds(20),
+                            [&] { return c->shutdown || (c->work_flag && c->inflight < c->max_inflight); });
+            if (c->shutdown) return;
+            if (!(c->work_flag && c->inflight < c->max_inflight)) continue;
+            c->work_flag = false;
+        }
+        std::lock_guard<std::mutex> lk(c->mu);
+        step_locked(c);
+        if (any_launchable(c)) {
+            std::lock_guard<std::mutex> lk2(c->cmu);
+            c->work_flag = true;
+        }
+    }
+}
+
+void wake_scheduler(flowroi_ctx *c)
+{
+    {
+        std::lock_guard<std::mutex> lk(c->cmu);
+        c->work_flag = true;
+    }
+    c->ccv.notify_all();
+}
+
+Entry *find_entry(Stream *s, int64_t frame_idx)
+{
+    for (auto &e : s->ring)
+        if (e->state.load() != E_EMPTY && e->frame_idx == frame_idx) return e.get();
+    return nullptr;
+}
+
+// A device error stops host callbacks from ever running; waits poll the
+// compute stream (non-blocking) so they end with FLOWROI_EDEVICE instead.
+void poll_device(flowroi_ctx *c)
+{
+    const cudaError_t e = cudaStreamQuery(c->s_comp);
+    if (e != cudaSuccess && e != cudaErrorNotReady) cuda_fail(c, e, "device error");
+}
+
+// Waits (bounded) for an entry to be done.
+bool wait_done(flowroi_ctx *c, Entry *e, int timeout_ms)
+{
+    const double t0 = now_ms();
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(c->cmu);
+            c->ccv.wait_for(lk, std::chrono::milliseconds(20), [&] { return e->state.load() == E_DONE || c->poisoned.load(); });
+            if (e->state.load() == E_DONE) return true;
+            if (c->poisoned) return false;
+        }
+        poll_device(c);
+        if (timeout_ms >= 0 && now_ms() - t0 >= timeout_ms) return e->state.load() == E_DONE;
+    }
+}
+
+int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, void *out, int out_on_device,
+               int timeout_ms)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    if (!out) return fail(FLOWROI_EINVAL, "out is NULL");
+    if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+    Entry *e = nullptr;
+    Stream *s = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->streams.find(stream_id);
+        if (it == c->streams.end()) return fail(FLOWROI_ENOSTREAM, "unknown stream %lld", (long long)stream_id);
+        s = it->second.get();
+        e = find_entry(s, frame_idx);
+        if (!e) {
+            if (s->any_frame && frame_idx <= s->last_frame_idx)
+                return fail(FLOWROI_EGONE, "frame %lld of stream %lld is no longer held", (long long)frame_idx,
+                            (long long)stream_id);
+            return fail(FLOWROI_ENOSTREAM, "frame %lld of stream %lld was not submitted", (long long)frame_idx,
+                        (long long)stream_id);
+        }
+        if (which >= FLOWROI_I_FLOW && !c->keep) return fail(FLOWROI_ENOTKEPT, "intermediates not kept (FLOWROI_KEEP_INTERMEDIATES)");
+        if (which == FLOWROI_I_COEFF_F32 && c->cfg.wavelet != FLOWROI_W97)
+            return fail(FLOWROI_EINVAL, "float coefficients exist only for the 9/7 path");
+        e->readers++;
+    }
+    const bool ok = wait_done(c, e, timeout_ms);
+    int rc = FLOWROI_OK;
+    if (!ok) {
+        rc = c->poisoned ? fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str())
+                         : fail(FLOWROI_ETIMEDOUT, "frame %lld not finished within %d ms", (long long)frame_idx, timeout_ms);
+    } else {
+        const size_t npx = (size_t)s->W * s->H;
+        const void *src = nullptr;
+        size_t bytes = 0;
+        switch (which) {
+        case 0: src = e->mask; bytes = npx; break;
+        case -1: src = e->coeffs; bytes = npx * 4; break;
+        case FLOWROI_I_FLOW: src = e->dbg_flow; bytes = npx * 8; break;
+        case FLOWROI_I_SALIENCY: src = e->dbg_shat; bytes = npx * 4; break;
+        case FLOWROI_I_MASK0: src = e->dbg_mask0; bytes = npx; break;
+        case FLOWROI_I_COEFF_F32: src = e->dbg_yf; bytes = npx * 4; break;
+        case FLOWROI_I_THRESHOLD: src = e->dbg_thr; bytes = 4; break;
+        default: rc = fail(FLOWROI_EINVAL, "unknown intermediate %d", which); break;
+        }
+        if (rc == FLOWROI_OK && which >= FLOWROI_I_FLOW && !e->has_prev) {
+            // A first frame has no flow: report zeros and an infinite cut.
+            std::lock_guard<std::mutex> lk(c->d2h_mu);
+            if (which == FLOWROI_I_THRESHOLD) {
+                const float inf = INFINITY;
+                cudaError_t ce = cudaMemcpyAsync(out, &inf, 4, out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, c->s_d2h);
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s_d2h);
+                if (ce != cudaSuccess) rc = cuda_fail(c, ce, "copy out");
+                src = nullptr;
+            } else if (which == FLOWROI_I_FLOW || which == FLOWROI_I_SALIENCY) {
+                cudaError_t ce = out_on_device ? cudaMemsetAsync(out, 0, bytes, c->s_d2h) : cudaSuccess;
+                if (!out_on_device) std::memset(out, 0, bytes);
+                if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s_d2h);
+                if (ce != cudaSuccess) rc = cuda_fail(c, ce, "copy out");
+                src = nullptr;
+            }
+        }
+        if (rc == FLOWROI_OK && src) {
+            std::lock_guard<std::mutex> lk(c->d2h_mu);
+            cudaError_t ce = cudaMemcpyAsync(out, src, bytes, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                             c->s_d2h);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s_d2h);
+            if (ce != cudaSuccess) rc = cuda_fail(c, ce, "copy out");
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        e->readers--;
+    }
+    if (!c->manual) wake_scheduler(c);
+    return rc;
+}
+
+}  // namespace
+
+// ================================================================ C ABI ==
+extern "C" {
+
+int flowroi_abi_version(void) { return FLOWROI_ABI_VERSION; }
+
+void flowroi_default_config(flowroi_config *cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof *cfg);
+    cfg->struct_size = sizeof(flowroi_config);
+    cfg->roi_q = 0.2f;
+    cfg->scale_shift = 5;
+    cfg->wavelet = FLOWROI_W53;
+    cfg->dwt_levels = 3;
+    cfg->pyr_levels = 3;
+    cfg->iters = 3;
+    cfg->win_r = 7;
+    cfg->poly_n_half = 2;
+    cfg->poly_sigma = 1.1f;
+    cfg->lambda = 1e-3f;
+    cfg->sal_weight = 0.7f;
+    cfg->r_open = 1;
+    cfg->r_close = 2;
+    cfg->precision = FLOWROI_FP32;
+    cfg->delta_base = 1.0f;
+    cfg->max_batch_frames = 64;
+    cfg->result_ring = 4;
+    cfg->flags = 0;
+    cfg->device = 0;
+    cfg->hbm_budget_bytes = 0;
+}
+
+int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
+                        double *gain_norm)
+{
+    if (quant_steps(levels, bit_depth, delta_base, delta, eps, mu, gain_norm) != 0)
+        return fail(FLOWROI_EINVAL, "quantisation steps out of range for levels=%d bit_depth=%d", levels, bit_depth);
+    return FLOWROI_OK;
+}
+
+int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
+{
+    if (!out) return fail(FLOWROI_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate_config(cfg);
+    if (rc) return rc;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return cuda_fail(nullptr, e == cudaSuccess ? cudaErrorNoDevice : e, "no CUDA device");
+    if (cfg->device < 0 || cfg->device >= ndev) return fail(FLOWROI_EINVAL, "config.device out of range");
+    std::unique_ptr<flowroi_ctx> c(new flowroi_ctx);
+    c->cfg = *cfg;
+    c->device = cfg->device;
+    c->half = cfg->precision == FLOWROI_FP16;
+    c->plain = (cfg->flags & FLOWROI_PLAIN) != 0;
+    c->keep = (cfg->flags & FLOWROI_KEEP_INTERMEDIATES) != 0;
+    c->manual = (cfg->flags & FLOWROI_MANUAL) != 0;
+    MethodConsts &mc = c->mc;
+    std::memset(&mc, 0, sizeof mc);
+    expansion_consts(cfg->poly_n_half, cfg->poly_sigma, mc);
+    mc.pyr_levels = cfg->pyr_levels;
+    mc.iters = cfg->iters;
+    mc.win_r = cfg->win_r;
+    mc.lambda = cfg->lambda;
+    mc.alpha = cfg->sal_weight;
+    mc.q = cfg->roi_q;
+    mc.r_open = cfg->r_open;
+    mc.r_close = cfg->r_close;
+    mc.wavelet = cfg->wavelet;
+    mc.dwt_levels = cfg->dwt_levels;
+    mc.shift = cfg->scale_shift;
+    for (int b = 0; b < kMaxSubbands; b++) mc.delta[b] = 1.f;
+    if (cfg->wavelet == FLOWROI_W97 && quant_steps(cfg->dwt_levels, 12, cfg->delta_base, mc.delta, nullptr, nullptr, nullptr) != 0)
+        return fail(FLOWROI_EINVAL, "config.delta_base gives quantisation steps out of range");
+
+    flowroi_ctx *cp = c.get();
+    CK(nullptr, cudaSetDevice(c->device));
+    CK(nullptr, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    CK(nullptr, cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking));
+    CK(nullptr, cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
+    CK(nullptr, cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
+    CK(nullptr, cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
+    for (int k = 0; k < flowroi_ctx::kDesc; k++) {
+        CK(nullptr, cudaMallocHost(reinterpret_cast<void **>(&c->desc_host[k]), sizeof(BatchDesc)));
+        CK(nullptr, cudaMalloc(reinterpret_cast<void **>(&c->desc_dev[k]), sizeof(BatchDesc)));
+        CK(nullptr, cudaEventCreateWithFlags(&c->desc_ev[k], cudaEventDisableTiming));
+        std::memset(c->desc_host[k], 0, sizeof(BatchDesc));
+    }
+    const int oe = occupancy_expand(c->half, cfg->poly_n_half);
+    const int of = occupancy_flow(c->half, cfg->win_r);
+    const int om = occupancy_mask_kernels();
+    const int od = occupancy_dwt(cfg->wavelet);
+    CK(nullptr, cudaGetLastError());
+    c->grid_exp = std::max(1, oe) * c->num_sms;
+    c->grid_flow = std::max(1, of) * c->num_sms;
+    c->grid_mask = std::max(1, om) * c->num_sms;
+    c->grid_dwt = std::max(1, od) * c->num_sms;
+    c->grid_frames = kMaxBatch;
+    size_t freeb = 0, totalb = 0;
+    CK(nullptr, cudaMemGetInfo(&freeb, &totalb));
+    c->budget = cfg->hbm_budget_bytes ? cfg->hbm_budget_bytes : (uint64_t)(0.8 * (double)freeb);
+    if (!c->manual) c->sched = std::thread(scheduler_main, cp);
+    *out = c.release();
+    (void)cp;
+    return FLOWROI_OK;
+}
+
+int flowroi_submit_frame(flowroi_ctx *c, int64_t stream_id, const flowroi_frame *f)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    if (!f || f->struct_size != sizeof(flowroi_frame)) return fail(FLOWROI_EINVAL, "frame descriptor NULL or struct_size mismatch");
+    if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+    if (f->dtype != FLOWROI_U8 && f->dtype != FLOWROI_U16) return fail(FLOWROI_EINVAL, "frame.dtype must be U8 or U16");
+    const int bpp = f->dtype == FLOWROI_U8 ? 1 : 2;
+    if (f->bit_depth < 1 || f->bit_depth > 8 * bpp) return fail(FLOWROI_EINVAL, "frame.bit_depth out of range for dtype");
+    const int align = 1 << std::max(c->cfg.dwt_levels, c->cfg.pyr_levels - 1);
+    if (f->width < 16 || f->height < 16 || f->width % align || f->height % align)
+        return fail(FLOWROI_EINVAL, "frame %dx%d: width and height must be >= 16 and multiples of %d", f->width, f->height, align);
+    if ((int64_t)f->width * f->height > (1LL << 28)) return fail(FLOWROI_EINVAL, "frame larger than 2^28 pixels");
+    if (!f->data) return fail(FLOWROI_EINVAL, "frame.data is NULL");
+    const int pitch = f->pitch_bytes ? f->pitch_bytes : f->width * bpp;
+    if (pitch < f->width * bpp) return fail(FLOWROI_EINVAL, "frame.pitch_bytes smaller than a row");
+    cudaSetDevice(c->device);
+
+    Entry *e = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->streams.find(stream_id);
+        Stream *s = nullptr;
+        if (it == c->streams.end()) {
+            std::unique_ptr<Stream> ns(new Stream);
+            ns->id = stream_id;
+            ns->W = f->width;
+            ns->H = f->height;
+            ns->bpp = bpp;
+            ns->bit_depth = f->bit_depth;
+            for (int r = 0; r < c->cfg.result_ring; r++) ns->ring.emplace_back(new Entry);
+            const size_t bytes = plan_stream(c, ns.get(), nullptr);
+            if (c->admitted + bytes > c->budget) {
+                c->refused++;
+                return fail(FLOWROI_EBUSY, "stream %lld needs %zu bytes; %llu of %llu budget in use", (long long)stream_id, bytes,
+                            (unsigned long long)c->admitted, (unsigned long long)c->budget);
+            }
+            if (c->cfg.wavelet == FLOWROI_W97 && quant_steps(c->cfg.dwt_levels, f->bit_depth, c->cfg.delta_base, nullptr, nullptr, nullptr, nullptr) != 0)
+                return fail(FLOWROI_EINVAL, "bit depth %d gives quantisation exponents out of range", f->bit_depth);
+            void *blk = nullptr;
+            cudaError_t ae = cudaMallocAsync(&blk, bytes, c->s_copy);
+            if (ae != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FLOWROI_ENOMEM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(ae));
+            }
+            ns->block = static_cast<char *>(blk);
+            ns->bytes = bytes;
+            plan_stream(c, ns.get(), ns->block);
+            for (auto &en : ns->ring) CK(c, cudaEventCreateWithFlags(&en->uploaded, cudaEventDisableTiming));
+            c->admitted += bytes;
+            s = ns.get();
+            c->streams[stream_id] = std::move(ns);
+        } else {
+            s = it->second.get();
+            if (s->ending) return fail(FLOWROI_EINVAL, "stream %lld is ending", (long long)stream_id);
+            if (s->W != f->width || s->H != f->height || s->bpp != bpp || s->bit_depth != f->bit_depth)
+                return fail(FLOWROI_EINVAL, "stream %lld: frame geometry or format changed", (long long)stream_id);
+            if (s->any_frame && f->frame_idx <= s->last_frame_idx)
+                return fail(FLOWROI_EINVAL, "stream %lld: frame_idx %lld not after %lld", (long long)stream_id,
+                            (long long)f->frame_idx, (long long)s->last_frame_idx);
+        }
+        const int64_t seq = s->next_seq;
+        e = s->ring[seq % (int64_t)s->ring.size()].get();
+        const int st = e->state.load();
+        if ((st != E_EMPTY && st != E_DONE) || e->readers > 0)
+            return fail(FLOWROI_EBUSY, "stream %lld: %zu frames not yet processed or being read", (long long)stream_id, s->ring.size());
+        e->frame_idx = f->frame_idx;
+        e->seq = seq;
+        e->has_prev = seq > 0;
+        e->t_submit = now_ms();
+        e->t_done = 0.0;
+        const cudaMemcpyKind kind = f->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(c, cudaMemcpy2DAsync(e->raw, (size_t)s->W * bpp, f->data, pitch, (size_t)s->W * bpp, s->H, kind, c->s_copy));
+        CK(c, cudaEventRecord(e->uploaded, c->s_copy));
+        e->state.store(E_PENDING);
+        s->next_seq = seq + 1;
+        s->last_frame_idx = f->frame_idx;
+        s->any_frame = true;
+        c->frames_submitted++;
+    }
+    // The caller may reuse its buffer as soon as this returns.
+    CK(c, cudaEventSynchronize(e->uploaded));
+    if (!c->manual) wake_scheduler(c);
+    return FLOWROI_OK;
+}
+
+int flowroi_step(flowroi_ctx *c)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    cudaSetDevice(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    return step_locked(c);
+}
+
+int flowroi_get_mask(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, uint8_t *out, int out_on_device, int timeout_ms)
+{
+    if (c) cudaSetDevice(c->device);
+    return get_common(c, stream_id, frame_idx, 0, out, out_on_device, timeout_ms);
+}
+
+int flowroi_get_coeffs(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int32_t *out, int out_on_device, int timeout_ms)
+{
+    if (c) cudaSetDevice(c->device);
+    return get_common(c, stream_id, frame_idx, -1, out, out_on_device, timeout_ms);
+}
+
+int flowroi_get_intermediate(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, void *out, int out_on_device,
+                             int timeout_ms)
+{
+    if (which < FLOWROI_I_FLOW || which > FLOWROI_I_THRESHOLD) return fail(FLOWROI_EINVAL, "unknown intermediate %d", which);
+    if (c) cudaSetDevice(c->device);
+    return get_common(c, stream_id, frame_idx, which, out, out_on_device, timeout_ms);
+}
+
+int flowroi_flush(flowroi_ctx *c, int timeout_ms)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    cudaSetDevice(c->device);
+    const double t0 = now_ms();
+    int64_t target;
+    for (;;) {
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            if (c->manual) {
+                for (;;) {
+                    int n = step_locked(c);
+                    if (n < 0) return n;
+                    if (n == 0) break;
+                    // two batches in flight at most; let the device drain
+                    std::unique_lock<std::mutex> lk2(c->cmu);
+                    c->ccv.wait_for(lk2, std::chrono::milliseconds(50), [&] { return c->inflight < c->max_inflight; });
+                }
+            }
+            target = c->frames_submitted - c->frames_cancelled;
+        }
+        if (!c->manual) wake_scheduler(c);
+        std::unique_lock<std::mutex> lk(c->cmu);
+        c->ccv.wait_for(lk, std::chrono::milliseconds(10), [&] { return c->frames_done >= target || c->poisoned.load(); });
+        if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+        if (c->frames_done >= target) {
+            lk.unlock();
+            std::lock_guard<std::mutex> lk3(c->mu);
+            if (c->frames_submitted - c->frames_cancelled <= target) return FLOWROI_OK;
+            continue;
+        }
+        lk.unlock();
+        poll_device(c);
+        if (timeout_ms >= 0 && now_ms() - t0 > timeout_ms) return fail(FLOWROI_ETIMEDOUT, "flush did not finish in %d ms", timeout_ms);
+    }
+}
+
+int flowroi_end_stream(flowroi_ctx *c, int64_t stream_id)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    cudaSetDevice(c->device);
+    Stream *s = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        auto it = c->streams.find(stream_id);
+        if (it == c->streams.end()) return fail(FLOWROI_ENOSTREAM, "unknown stream %lld", (long long)stream_id);
+        s = it->second.get();
+        s->ending = true;
+        for (auto &e : s->ring)
+            if (e->state.load() == E_PENDING) {
+                e->state.store(E_EMPTY);
+                c->frames_cancelled++;
+            }
+    }
+    for (;;) {
+        bool busy = false;
+        {
+            std::lock_guard<std::mutex> lk(c->mu);
+            for (auto &e : s->ring)
+                if (e->state.load() == E_LAUNCHED || e->readers > 0) busy = true;
+            if (!busy) {
+                if (c->poisoned) {
+                    // leave the block to flowroi_destroy's device reset path
+                } else {
+                    cudaFreeAsync(s->block, c->s_comp);
+                }
+                for (auto &e : s->ring)
+                    if (e->uploaded) cudaEventDestroy(e->uploaded);
+                c->admitted -= s->bytes;
+                c->streams.erase(stream_id);
+                return FLOWROI_OK;
+            }
+        }
+        {
+            std::unique_lock<std::mutex> lk(c->cmu);
+            c->ccv.wait_for(lk, std::chrono::milliseconds(5));
+        }
+        poll_device(c);
+        if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+    }
+}
+
+int flowroi_get_stats(flowroi_ctx *c, flowroi_stats *out)
+{
+    if (!c || !out) return fail(FLOWROI_EINVAL, "ctx or out is NULL");
+    if (out->struct_size != sizeof(flowroi_stats)) return fail(FLOWROI_EINVAL, "stats.struct_size mismatch");
+    std::vector<double> lat;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        out->frames_submitted = c->frames_submitted;
+        out->streams_admitted = (int64_t)c->streams.size();
+        out->bytes_admitted = c->admitted;
+        out->budget_bytes = c->budget;
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->cmu);
+        out->frames_done = c->frames_done;
+        lat = c->lat_ms;
+    }
+    out->batches = c->batches;
+    out->admissions_refused = c->refused;
+    out->kernel_launches = c->launches;
+    out->lat_p50_ms = out->lat_p99_ms = out->lat_mean_ms = 0.0;
+    if (!lat.empty()) {
+        std::sort(lat.begin(), lat.end());
+        auto pct = [&](double q) {
+            const double pos = q * (double)(lat.size() - 1);
+            const size_t i = (size_t)pos;
+            const double f = pos - (double)i;
+            return i + 1 < lat.size() ? lat[i] * (1 - f) + lat[i + 1] * f : lat[i];
+        };
+        out->lat_p50_ms = pct(0.5);
+        out->lat_p99_ms = pct(0.99);
+        double s = 0;
+        for (double v : lat) s += v;
+        out->lat_mean_ms = s / (double)lat.size();
+    }
+    return FLOWROI_OK;
+}
+
+void flowroi_destroy(flowroi_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    {
+        std::lock_guard<std::mutex> lk(c->cmu);
+        c->shutdown = true;
+    }
+    c->ccv.notify_all();
+    if (c->sched.joinable()) c->sched.join();
+    cudaStreamSynchronize(c->s_comp);
+    cudaStreamSynchronize(c->s_copy);
+    cudaStreamSynchronize(c->s_d2h);
+    for (auto &kv : c->streams) {
+        cudaFreeAsync(kv.second->block, c->s_comp);
+        for (auto &e : kv.second->ring)
+            if (e->uploaded) cudaEventDestroy(e->uploaded);
+    }
+    cudaStreamSynchronize(c->s_comp);
+    for (int k = 0; k < flowroi_ctx::kDesc; k++) {
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+        if (c->desc_host[k]) cudaFreeHost(c->desc_host[k]);
+        if (c->desc_dev[k]) cudaFree(c->desc_dev[k]);
+        if (c->desc_ev[k]) cudaEventDestroy(c->desc_ev[k]);
+    }
+    cudaStreamDestroy(c->s_comp);
+    cudaStreamDestroy(c->s_copy);
+    cudaStreamDestroy(c->s_d2h);
+    cudaStreamDestroy(c->s_cap);
+    delete c;
+}
+
+int flowroi_compute_stream(flowroi_ctx *c, void **out)
+{
+    if (!c || !out) return fail(FLOWROI_EINVAL, "ctx or out is NULL");
+    *out = (void *)c->s_comp;
+    return FLOWROI_OK;
+}
+
+int flowroi_set_profiling(flowroi_ctx *c, int on)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->mu);
+    if (on == 2) c->prof_tot.clear();
+    c->profiling = on != 0;
+    return FLOWROI_OK;
+}
+
+int flowroi_get_kernel_times(flowroi_ctx *c, flowroi_kernel_time *out, int cap)
+{
+    if (!c || (!out && cap > 0)) return fail(FLOWROI_EINVAL, "ctx or out is NULL");
+    cudaSetDevice(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    CK(c, cudaStreamSynchronize(c->s_comp));
+    for (auto &r : c->prof_pending) {
+        float ms = 0.f;
+        CK(c, cudaEventElapsedTime(&ms, r.a, r.b));
+        auto &t = c->prof_tot[std::make_tuple(r.kid, r.level, r.iter)];
+        t.first += 1;
+        t.second += ms;
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    c->prof_pending.clear();
+    int n = 0;
+    for (auto &kv : c->prof_tot) {
+        if (n < cap) {
+            flowroi_kernel_time &o = out[n];
+            std::memset(&o, 0, sizeof o);
+            snprintf(o.name, sizeof o.name, "%s", kKernelNames[std::get<0>(kv.first)]);
+            o.level = std::get<1>(kv.first);
+            o.iter = std::get<2>(kv.first);
+            o.launches = kv.second.first;
+            o.total_ms = kv.second.second;
+        }
+        n++;
+    }
+    return std::min(n, cap);
+}
+
+const char *flowroi_last_error(flowroi_ctx *c)
+{
+    (void)c;
+    return g_err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,256 @@
+"""ctypes binding of the FlowRoI C ABI (include/flowroi.h).
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, converts numpy arrays / torch tensors to plain pointers
+(with the matching on-device flag) and turns a negative status into a
+``FlowRoIError``.  All computation happens in the CUDA library; if it is not
+built, importing this module fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from ._build import LIB
+
+OK = 0
+EINVAL, ENOSTREAM, EBUSY, ENOMEM, ETIMEDOUT, EDEVICE, EGONE, ENOTKEPT = -1, -2, -3, -4, -5, -6, -7, -8
+U8, U16 = 1, 2
+W53, W97 = 53, 97
+FP32, FP16 = 32, 16
+KEEP_INTERMEDIATES, PLAIN, MANUAL = 0x1, 0x2, 0x4
+I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD = 1, 2, 3, 4, 5
+
+EXPORTS = [
+    "flowroi_abi_version", "flowroi_default_config", "flowroi_create", "flowroi_submit_frame",
+    "flowroi_step", "flowroi_get_mask", "flowroi_get_coeffs", "flowroi_get_intermediate",
+    "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
+    "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
+    "flowroi_get_kernel_times",
+]
+
+
+class FlowRoIError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class flowroi_config(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("roi_q", ctypes.c_float), ("scale_shift", ctypes.c_int32),
+        ("wavelet", ctypes.c_int32), ("dwt_levels", ctypes.c_int32), ("pyr_levels", ctypes.c_int32),
+        ("iters", ctypes.c_int32), ("win_r", ctypes.c_int32), ("poly_n_half", ctypes.c_int32),
+        ("poly_sigma", ctypes.c_float), ("lambda_", ctypes.c_float), ("sal_weight", ctypes.c_float),
+        ("r_open", ctypes.c_int32), ("r_close", ctypes.c_int32), ("precision", ctypes.c_int32),
+        ("delta_base", ctypes.c_float), ("max_batch_frames", ctypes.c_int32), ("result_ring", ctypes.c_int32),
+        ("flags", ctypes.c_uint32), ("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
+    ]
+
+
+class flowroi_frame(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+        ("pitch_bytes", ctypes.c_int32), ("dtype", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
+        ("frame_idx", ctypes.c_int64), ("data", ctypes.c_void_p), ("data_on_device", ctypes.c_int32),
+    ]
+
+
+class flowroi_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("level", ctypes.c_int32), ("iter", ctypes.c_int32),
+                ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class flowroi_stats(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32), ("frames_submitted", ctypes.c_int64), ("frames_done", ctypes.c_int64),
+        ("batches", ctypes.c_int64), ("streams_admitted", ctypes.c_int64), ("admissions_refused", ctypes.c_int64),
+        ("bytes_admitted", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64), ("lat_p50_ms", ctypes.c_double),
+        ("lat_p99_ms", ctypes.c_double), ("lat_mean_ms", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
+    ]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise ImportError(f"{LIB} is missing: build the CUDA library first "
+                              "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB)
+        P, I, I64, U32 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint32
+        sigs = {
+            "flowroi_abi_version": (I, []),
+            "flowroi_default_config": (None, [ctypes.POINTER(flowroi_config)]),
+            "flowroi_create": (I, [ctypes.POINTER(flowroi_config), ctypes.POINTER(P)]),
+            "flowroi_submit_frame": (I, [P, I64, ctypes.POINTER(flowroi_frame)]),
+            "flowroi_step": (I, [P]),
+            "flowroi_get_mask": (I, [P, I64, I64, P, I, I]),
+            "flowroi_get_coeffs": (I, [P, I64, I64, P, I, I]),
+            "flowroi_get_intermediate": (I, [P, I64, I64, I, P, I, I]),
+            "flowroi_flush": (I, [P, I]),
+            "flowroi_end_stream": (I, [P, I64]),
+            "flowroi_get_stats": (I, [P, ctypes.POINTER(flowroi_stats)]),
+            "flowroi_destroy": (None, [P]),
+            "flowroi_last_error": (ctypes.c_char_p, [P]),
+            "flowroi_quant_steps": (I, [I, I, ctypes.c_float, P, P, P, P]),
+            "flowroi_compute_stream": (I, [P, ctypes.POINTER(P)]),
+            "flowroi_set_profiling": (I, [P, I]),
+            "flowroi_get_kernel_times": (I, [P, ctypes.POINTER(flowroi_kernel_time), I]),
+        }
+        for name, (res, args) in sigs.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        del U32
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, ctx=None) -> int:
+    if rc < 0:
+        raise FlowRoIError(rc, lib().flowroi_last_error(ctx).decode(errors="replace"))
+    return rc
+
+
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (must be contiguous)."""
+    if hasattr(a, "data_ptr"):  # torch.Tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, 0
+
+
+# ------------------------------------------------------------ entry points --
+
+def flowroi_abi_version() -> int:
+    return lib().flowroi_abi_version()
+
+
+def flowroi_default_config(**overrides) -> flowroi_config:
+    cfg = flowroi_config()
+    lib().flowroi_default_config(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, "lambda_" if k == "lam" else k, v)
+    return cfg
+
+
+def flowroi_create(cfg: flowroi_config) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().flowroi_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def flowroi_submit_frame(ctx, stream_id: int, data, frame_idx: int, bit_depth: int, pitch_bytes: int = 0) -> int:
+    """`data`: (H, W) uint8 or uint16 samples (int16 with the same bit
+    pattern also accepted), numpy (host) or torch (host or CUDA)."""
+    h, w = int(data.shape[0]), int(data.shape[1])
+    esz = data.itemsize if hasattr(data, "itemsize") else data.element_size()
+    p, dev = _ptr(data)
+    f = flowroi_frame(ctypes.sizeof(flowroi_frame), w, h, pitch_bytes, U8 if esz == 1 else U16, bit_depth,
+                      frame_idx, p, dev)
+    return _check(lib().flowroi_submit_frame(ctx, stream_id, ctypes.byref(f)), ctx)
+
+
+def flowroi_step(ctx) -> int:
+    return _check(lib().flowroi_step(ctx), ctx)
+
+
+def flowroi_get_mask(ctx, stream_id: int, frame_idx: int, out, timeout_ms: int = -1) -> int:
+    p, dev = _ptr(out)
+    return _check(lib().flowroi_get_mask(ctx, stream_id, frame_idx, p, dev, timeout_ms), ctx)
+
+
+def flowroi_get_coeffs(ctx, stream_id: int, frame_idx: int, out, timeout_ms: int = -1) -> int:
+    p, dev = _ptr(out)
+    return _check(lib().flowroi_get_coeffs(ctx, stream_id, frame_idx, p, dev, timeout_ms), ctx)
+
+
+def flowroi_get_intermediate(ctx, stream_id: int, frame_idx: int, which: int, out, timeout_ms: int = -1) -> int:
+    p, dev = _ptr(out)
+    return _check(lib().flowroi_get_intermediate(ctx, stream_id, frame_idx, which, p, dev, timeout_ms), ctx)
+
+
+def flowroi_flush(ctx, timeout_ms: int = -1) -> int:
+    return _check(lib().flowroi_flush(ctx, timeout_ms), ctx)
+
+
+def flowroi_end_stream(ctx, stream_id: int) -> int:
+    return _check(lib().flowroi_end_stream(ctx, stream_id), ctx)
+
+
+def flowroi_get_stats(ctx) -> dict:
+    s = flowroi_stats()
+    s.struct_size = ctypes.sizeof(flowroi_stats)
+    _check(lib().flowroi_get_stats(ctx, ctypes.byref(s)), ctx)
+    return {name: getattr(s, name) for name, _ in flowroi_stats._fields_ if name != "struct_size"}
+
+
+def flowroi_destroy(ctx) -> None:
+    lib().flowroi_destroy(ctx)
+
+
+def flowroi_last_error(ctx=None) -> str:
+    return lib().flowroi_last_error(ctx).decode(errors="replace")
+
+
+def flowroi_quant_steps(levels: int, bit_depth: int, delta_base: float = 1.0):
+    """(delta float32[3L+1], eps int32, mu int32, gain float64) as numpy arrays."""
+    import numpy as np
+    nb = 3 * levels + 1
+    d = np.empty(nb, np.float32)
+    e = np.empty(nb, np.int32)
+    m = np.empty(nb, np.int32)
+    g = np.empty(nb, np.float64)
+    _check(lib().flowroi_quant_steps(levels, bit_depth, delta_base, d.ctypes.data, e.ctypes.data, m.ctypes.data,
+                                     g.ctypes.data))
+    return d, e, m, g
+
+
+def flowroi_compute_stream(ctx) -> int:
+    """The context's compute stream handle (cudaStream_t as an int)."""
+    h = ctypes.c_void_p()
+    _check(lib().flowroi_compute_stream(ctx, ctypes.byref(h)), ctx)
+    return h.value or 0
+
+
+def flowroi_set_profiling(ctx, on: int) -> int:
+    return _check(lib().flowroi_set_profiling(ctx, on), ctx)
+
+
+def flowroi_get_kernel_times(ctx, cap: int = 256) -> list:
+    arr = (flowroi_kernel_time * cap)()
+    n = _check(lib().flowroi_get_kernel_times(ctx, arr, cap), ctx)
+    return [dict(name=arr[i].name.decode(), level=arr[i].level, iter=arr[i].iter, launches=arr[i].launches,
+                 total_ms=arr[i].total_ms) for i in range(n)]
+
+
+class Context:
+    """Small owner of a context handle (destroyed on close / exit)."""
+
+    def __init__(self, **cfg):
+        self.cfg = flowroi_default_config(**cfg)
+        self.h = flowroi_create(self.cfg)
+
+    def close(self):
+        if self.h:
+            flowroi_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,144 @@
+"""GPU path vs oracle, element by element, through the C ABI.
+
+Acceptance (stage by stage, each GPU stage checked on the same input as
+the oracle stage; where single precision decides an integer, the oracle
+decides in single precision on the GPU's own values):
+  - flow (float32) vs the float64 oracle: max abs error <= FLOW_TOL px;
+  - normalised saliency from the GPU's flow: abs error <= SAL_TOL;
+  - quantile cut on the GPU's own S^: threshold and mask0 bit-exact;
+  - opening/closing of the GPU's own mask0: bit-exact;
+  - end to end, mask0 differs from the oracle's only where the oracle's
+    S^ lies within 1e-4 of its threshold;
+  - 5/3 coefficients (DC shift, DWT, wavelet mask, RoI shift) given the
+    GPU's mask: bit-exact;
+  - 9/7 float coefficients vs float64: abs error <= 1e-4 + 4e-6*|y|
+    (float32 lifting: ~10 rounded operations per level and dimension on
+    operands up to a few times |y|, D <= 5 levels), quantised + shifted
+    coefficients from the GPU's own float coefficients: bit-exact.
+"""
+import numpy as np
+import pytest
+import torch
+
+from synth import pair_u8, sequence_u16
+from tests._gpu import F, fetch, oracle_params, run_stream, u16
+
+pytestmark = pytest.mark.gpu
+
+FLOW_TOL = 1e-3
+SAL_TOL = 1e-5
+QBAND = 1e-4
+
+
+def _stagewise(orc, prev, cur, bd, g, **cfg):
+    p = oracle_params(orc, **cfg)
+    o = orc.frame(prev, cur, bd, p)
+    h, w = cur.shape
+    d = g["flow"].transpose(2, 0, 1).astype(np.float64)
+    ferr = np.abs(d - o["flow"]).max()
+    assert ferr <= FLOW_TOL, f"flow max abs error {ferr}"
+    Sh = orc.normalise(orc.saliency(d, p.sal_weight))
+    serr = np.abs(g["shat"] - Sh).max()
+    assert serr <= SAL_TOL, f"saliency error {serr}"
+    m0, t = orc.threshold_f32(g["shat"], p.roi_q)
+    assert g["thr"][0] == t
+    assert np.array_equal(m0, g["mask0"])
+    assert np.array_equal(orc.morph(g["mask0"], p.r_open, p.r_close), g["mask"])
+    diff = g["mask0"] != o["mask0"]
+    if diff.any():
+        assert np.abs(o["Sh"][diff] - o["t"]).max() <= QBAND
+    cm = orc.wavelet_mask(g["mask"], p.dwt_levels, p.wavelet)
+    if p.wavelet == 53:
+        y = orc.dwt2d(orc.dc_shift(cur, bd), 53, p.dwt_levels)
+        assert np.array_equal(g["coeffs"], orc.roi_shift(y, cm, p.scale_shift))
+    else:
+        y = orc.dwt2d(orc.dc_shift(cur, bd).astype(np.float64), 97, p.dwt_levels)
+        yerr = np.abs(g["yf"] - y)
+        assert np.all(yerr <= 1e-4 + 4e-6 * np.abs(y)), f"9/7 error {yerr.max()}"
+        _, delta, _, _ = orc.delta_table(p.dwt_levels, bd, p.delta_base)
+        q = orc.quantise_f32(g["yf"], p.dwt_levels, delta)
+        assert np.array_equal(g["coeffs"], orc.roi_shift(q, cm, p.scale_shift))
+    iou = (g["mask"] & o["mask"]).sum() / max(1, (g["mask"] | o["mask"]).sum())
+    return dict(flow_err=ferr, sal_err=serr, mask0_diff=int(diff.sum()), iou=iou)
+
+
+def test_identical_frames_give_zero_flow_and_empty_mask(orc):
+    prev, _ = pair_u8(seed=5, h=64, w=64, n_blobs=3)
+    a = prev.numpy()
+    g0, g1 = run_stream([a, a], 8)
+    assert np.all(g1["flow"] == 0.0)
+    assert g1["mask0"].sum() == 0 and g1["mask"].sum() == 0
+    plain = orc.dwt2d(orc.dc_shift(a, 8), 53, 3)
+    assert np.array_equal(g1["coeffs"], plain) and np.array_equal(g0["coeffs"], plain)
+    assert g0["mask"].sum() == 0 and np.isinf(g0["thr"][0])
+
+
+def test_pair_256_u8_53(orc):
+    prev, cur = pair_u8(seed=1001)
+    g = run_stream([prev.numpy(), cur.numpy()], 8)[1]
+    r = _stagewise(orc, prev.numpy(), cur.numpy(), 8, g)
+    assert r["iou"] > 0.98
+
+
+@pytest.mark.parametrize("h,w", [(48, 64), (80, 48), (16, 16), (72, 40)])
+def test_ragged_sizes(orc, h, w):
+    prev, cur = pair_u8(seed=h * 1000 + w, h=h, w=w, n_blobs=2)
+    levels = dict(pyr_levels=2, dwt_levels=3) if h > 16 else dict(pyr_levels=2, dwt_levels=1)
+    g = run_stream([prev.numpy(), cur.numpy()], 8, **levels)[1]
+    _stagewise(orc, prev.numpy(), cur.numpy(), 8, g, **levels)
+
+
+def test_sequence_1024_u16_53_resident_state(orc):
+    """Three frames of one 12-bit stream: frames 1 and 2 reuse the resident
+    expansion of their predecessor."""
+    seq = u16(sequence_u16(2000, 3, 1024, 1024, 80))
+    cfg = dict(pyr_levels=4, dwt_levels=5)
+    gs = run_stream([seq[0], seq[1], seq[2]], 12, **cfg)
+    for t in (1, 2):
+        _stagewise(orc, seq[t - 1], seq[t], 12, gs[t], **cfg)
+
+
+def test_pair_512_u16_97(orc):
+    seq = u16(sequence_u16(3001, 2, 512, 512, 30))
+    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
+    g = run_stream([seq[0], seq[1]], 12, **cfg)[1]
+    _stagewise(orc, seq[0], seq[1], 12, g, **cfg)
+
+
+def test_full_size_2048_u16_97_batched(orc):
+    """Frame geometry and settings of the 16 x 2048^2 batched workload
+    (5-level pyramid, 9/7 DWT 5 levels), through the batched, graph-replayed
+    path, one pair checked against the oracle at full size."""
+    seq = u16(sequence_u16(3000, 2, 2048, 2048, 200))
+    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
+    g = run_stream([seq[0], seq[1]], 12, **cfg)[1]
+    _stagewise(orc, seq[0], seq[1], 12, g, **cfg)
+
+
+def test_fp16_storage_epe_and_iou(orc):
+    seq = u16(sequence_u16(3002, 2, 512, 512, 30))
+    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
+    g = run_stream([seq[0], seq[1]], 12, precision=F.FP16, **cfg)[1]
+    o = orc.frame(seq[0], seq[1], 12, oracle_params(orc, **cfg))
+    d = g["flow"].transpose(2, 0, 1)
+    epe = np.hypot(d[0] - o["flow"][0], d[1] - o["flow"][1]).mean()
+    iou = (g["mask"] & o["mask"]).sum() / max(1, (g["mask"] | o["mask"]).sum())
+    assert epe < 0.05 and iou > 0.9, (epe, iou)
+    # integer paths stay exact given the GPU's own mask
+    p = oracle_params(orc, **cfg)
+    assert np.array_equal(orc.morph(g["mask0"], p.r_open, p.r_close), g["mask"])
+
+
+def test_device_pointer_io_matches_host_io():
+    prev, cur = pair_u8(seed=77, h=128, w=128, n_blobs=5)
+    host = run_stream([prev.numpy(), cur.numpy()], 8, keep=False)[1]
+    with F.Context(flags=F.MANUAL) as ctx:
+        for i, fr in enumerate((prev, cur)):
+            F.flowroi_submit_frame(ctx.h, 3, fr.cuda().contiguous(), i, 8)
+            F.flowroi_flush(ctx.h, 60000)
+        m = torch.empty((128, 128), dtype=torch.uint8, device="cuda")
+        c = torch.empty((128, 128), dtype=torch.int32, device="cuda")
+        F.flowroi_get_mask(ctx.h, 3, 1, m)
+        F.flowroi_get_coeffs(ctx.h, 3, 1, c)
+    assert np.array_equal(m.cpu().numpy(), host["mask"])
+    assert np.array_equal(c.cpu().numpy(), host["coeffs"])

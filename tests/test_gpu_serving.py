@@ -1,0 +1,136 @@
+"""Serving behaviour of the CUDA library through the C ABI: batch
+invariance (a frame's results are bit-identical alone, in a mixed batch of
+streams of different resolutions, on the plain per-frame path and under the
+continuously batching scheduler thread), admission by HBM budget, result
+ring eviction, bounded waits and argument errors."""
+import numpy as np
+import pytest
+
+from synth import pair_u8, sequence_u16
+from tests._gpu import F, fetch, run_stream, u16
+
+pytestmark = pytest.mark.gpu
+
+
+def _streams():
+    """Four streams of different geometry / format (two frames each)."""
+    out = []
+    for sid, (h, w) in enumerate([(256, 256), (128, 192), (512, 256), (64, 64)]):
+        if sid % 2 == 0:
+            a, b = pair_u8(seed=900 + sid, h=h, w=w, n_blobs=6)
+            out.append((sid, [a.numpy(), b.numpy()], 8))
+        else:
+            s = u16(sequence_u16(950 + sid, 2, h, w, 12))
+            out.append((sid, [s[0], s[1]], 12))
+    return out
+
+
+def _same(a, b):
+    for k in ("mask", "coeffs", "flow", "mask0", "shat", "thr"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+@pytest.mark.parametrize("wavelet", [53, 97])
+def test_batch_invariance_mixed_resolutions(wavelet):
+    cfg = dict(pyr_levels=3, dwt_levels=3, wavelet=wavelet)
+    alone = {sid: run_stream(frames, bd, **cfg)[1] for sid, frames, bd in _streams()}
+    plain = {sid: run_stream(frames, bd, plain=True, **cfg)[1] for sid, frames, bd in _streams()}
+    with F.Context(flags=F.MANUAL | F.KEEP_INTERMEDIATES, **cfg) as ctx:
+        for t in range(2):
+            for sid, frames, bd in _streams():
+                F.flowroi_submit_frame(ctx.h, sid, frames[t], t, bd)
+            assert F.flowroi_step(ctx.h) == 4  # one batch holds every stream's frame
+            F.flowroi_flush(ctx.h, 60000)
+        mixed = {sid: fetch(ctx.h, sid, 1, frames[1].shape[0], frames[1].shape[1], wavelet=wavelet)
+                 for sid, frames, bd in _streams()}
+        st = F.flowroi_get_stats(ctx.h)
+        assert st["batches"] == 2 and st["frames_done"] == 8 and st["kernel_launches"] > 0
+    for sid in alone:
+        _same(alone[sid], mixed[sid])
+        _same(alone[sid], plain[sid])
+
+
+def test_scheduler_thread_matches_manual():
+    streams = _streams()
+    manual = {sid: run_stream(frames, bd, keep=False)[1] for sid, frames, bd in streams}
+    with F.Context() as ctx:  # scheduler thread, continuous batching
+        for t in range(2):
+            for sid, frames, bd in streams:
+                F.flowroi_submit_frame(ctx.h, sid, frames[t], t, bd)
+        for sid, frames, bd in streams:
+            h, w = frames[1].shape
+            got = fetch(ctx.h, sid, 1, h, w, keep=False, timeout_ms=60000)
+            assert np.array_equal(got["mask"], manual[sid]["mask"])
+            assert np.array_equal(got["coeffs"], manual[sid]["coeffs"])
+        st = F.flowroi_get_stats(ctx.h)
+        assert st["frames_done"] == 8 and st["lat_p99_ms"] >= st["lat_p50_ms"] > 0
+
+
+def test_admission_by_hbm_budget():
+    a, _ = pair_u8(seed=1, h=256, w=256)
+    with F.Context(flags=F.MANUAL) as probe:
+        F.flowroi_submit_frame(probe.h, 0, a.numpy(), 0, 8)
+        one = F.flowroi_get_stats(probe.h)["bytes_admitted"]
+    with F.Context(flags=F.MANUAL, hbm_budget_bytes=int(one * 1.5)) as ctx:
+        F.flowroi_submit_frame(ctx.h, 1, a.numpy(), 0, 8)
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_submit_frame(ctx.h, 2, a.numpy(), 0, 8)
+        assert ei.value.code == F.EBUSY
+        F.flowroi_flush(ctx.h, 60000)
+        F.flowroi_end_stream(ctx.h, 1)
+        F.flowroi_submit_frame(ctx.h, 2, a.numpy(), 0, 8)  # admitted once the budget is free
+        st = F.flowroi_get_stats(ctx.h)
+        assert st["admissions_refused"] == 1 and st["streams_admitted"] == 1
+
+
+def test_ring_eviction_timeout_and_order_errors():
+    frames = [pair_u8(seed=s, h=64, w=64)[0].numpy() for s in range(4)]
+    out = np.empty((64, 64), np.uint8)
+    with F.Context(flags=F.MANUAL, result_ring=2) as ctx:
+        for i in range(3):
+            F.flowroi_submit_frame(ctx.h, 5, frames[i], i, 8)
+            F.flowroi_flush(ctx.h, 60000)
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_mask(ctx.h, 5, 0, out, 1000)
+        assert ei.value.code == F.EGONE
+        F.flowroi_get_mask(ctx.h, 5, 2, out, 1000)
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_submit_frame(ctx.h, 5, frames[3], 2, 8)  # not after frame 2
+        assert ei.value.code == F.EINVAL
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_submit_frame(ctx.h, 5, np.zeros((32, 64), np.uint8), 9, 8)  # geometry change
+        assert ei.value.code == F.EINVAL
+        F.flowroi_submit_frame(ctx.h, 5, frames[3], 10, 8)  # submitted, never stepped
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_mask(ctx.h, 5, 10, out, 50)
+        assert ei.value.code == F.ETIMEDOUT
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_mask(ctx.h, 5, 11, out, 50)
+        assert ei.value.code == F.ENOSTREAM
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_intermediate(ctx.h, 5, 2, F.I_FLOW, np.empty((64, 64, 2), np.float32), 50)
+        assert ei.value.code == F.ENOTKEPT
+        F.flowroi_step(ctx.h)
+        F.flowroi_get_mask(ctx.h, 5, 10, out, 60000)
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_submit_frame(ctx.h, 6, np.zeros((64, 60), np.uint8), 0, 8)  # not a multiple of 8
+        assert ei.value.code == F.EINVAL
+
+
+def test_many_streams_and_frames_in_flight():
+    """16 streams x 6 frames under the scheduler thread, results fetched
+    while later frames are queued; each matches its stream run alone."""
+    seqs = [u16(sequence_u16(4000 + s, 6, 128, 128, 8)) for s in range(16)]
+    ref = {s: run_stream([seqs[s][t] for t in range(6)], 12, keep=False) for s in (0, 7, 15)}
+    with F.Context(result_ring=8) as ctx:
+        for t in range(6):
+            for s in range(16):
+                F.flowroi_submit_frame(ctx.h, s, seqs[s][t], t, 12)
+        for s in (0, 7, 15):
+            for t in range(6):
+                got = fetch(ctx.h, s, t, 128, 128, keep=False)
+                assert np.array_equal(got["mask"], ref[s][t]["mask"])
+                assert np.array_equal(got["coeffs"], ref[s][t]["coeffs"])
+        F.flowroi_flush(ctx.h, 60000)
+        st = F.flowroi_get_stats(ctx.h)
+        assert st["frames_done"] == 96 and st["batches"] >= 6
