@@ -45,6 +45,9 @@ WORKLOADS = {
     # same workload, pyramid and expansion fields stored in fp16
     "fp16_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=16, seed_base=3000),
+    # four streams of the batched workload's frames (small case for profiler captures)
+    "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                         dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
     # one stream of 64 1024^2 12-bit frames, 5/3 DWT (plain method at full size)
     "stream_1024": dict(streams=1, frames=64, h=1024, w=1024, blobs=80, bit_depth=12, pyr_levels=4,
                         dwt_levels=5, wavelet=53, precision=32, seed_base=2000),

@@ -15,16 +15,17 @@ constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 
 // Tile shapes (output pixels per block) of each kernel family.
 constexpr int kExpTW = 64, kExpTH = 16;   // pyramid + polynomial expansion
-constexpr int kFlowTW = 32, kFlowTH = 32; // displacement update + window + solve
+constexpr int kFlowTW = 64, kFlowTH = 32; // displacement update + window + solve
 constexpr int kSalTW = 64, kSalTH = 16;   // saliency, radix-select passes
-constexpr int kMorTW = 64, kMorTH = 32;   // threshold + opening + closing
-constexpr int kDwtTW = 32, kDwtTH = 16;   // DWT: band coefficients per block (per band)
+constexpr int kMorTW = 256, kMorTH = 32;  // threshold + opening + closing (8 words x 32 rows)
+constexpr int kDwtTW = 64, kDwtTH = 16;   // DWT: band coefficients per block (per band)
 
 // Per-frame reduction block (device), one per frame slot.
 //   [0] min of S (float bits), [1] max of S, [2] select prefix,
-//   [3] remaining rank, [4] t_S bits, [5] t_hat bits,
+//   [3] remaining rank, [4] t_S bits, [5] t_hat bits, [6] s* bits (the
+//   largest S whose normalised value is <= t_hat: mask0 = S > s*),
 //   [kRedHist .. +kHistBins) histogram of the current radix digit.
-constexpr int kRedMin = 0, kRedMax = 1, kRedPrefix = 2, kRedRank = 3, kRedTS = 4, kRedTHat = 5;
+constexpr int kRedMin = 0, kRedMax = 1, kRedPrefix = 2, kRedRank = 3, kRedTS = 4, kRedTHat = 5, kRedSStar = 6;
 constexpr int kRedHist = 8;
 constexpr int kRedWords = kRedHist + kHistBins;
 

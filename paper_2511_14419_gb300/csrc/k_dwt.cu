@@ -22,10 +22,13 @@
 // Tile scheme: a block owns kDwtTW x kDwtTH coefficients of each of the
 // four bands of the level, i.e. a 2*TW x 2*TH input block plus a 4-sample
 // apron loaded with the symmetric extension (for the 4-step 9/7 cone;
-// 5/3 needs 2).  Lifting runs in place in shared memory over the whole
-// extended tile; outputs come from its centre, which depends only on
-// in-tile samples.  The low-low band goes to a temporary plane for the
-// next level (or, at the last level, quantised into the coefficient plane).
+// 5/3 needs 2).  Each column of the extended tile is lifted in a thread's
+// registers; then each (row, 16-coefficient segment) is lifted in
+// registers from a 40-sample window of that row and its coefficients are
+// quantised, shifted and stored.  Outputs come from window centres, which
+// depend only on in-window samples.  The low-low band goes to a temporary
+// plane for the next level (or, at the last level, into the coefficient
+// plane).
 #include <type_traits>
 
 #include "common.cuh"
@@ -38,11 +41,14 @@ namespace {
 constexpr float kA = -1.586134342059924f, kB = -0.052980118572961f, kG = 0.882911075530934f,
                 kD = 0.443506852043971f, kK = 1.230174104914001f;
 constexpr int kDwtHalo = 4;
-constexpr int kDwtEW = 2 * kDwtTW + 2 * kDwtHalo, kDwtEH = 2 * kDwtTH + 2 * kDwtHalo;
 
-// Whole-sample symmetric extension of index i into [0, n).
+// Whole-sample symmetric extension of index i into [0, n).  One
+// reflection suffices when the apron is shorter than the signal; tiny
+// signals take the periodic form.
 __device__ __forceinline__ int mirror(int i, int n)
 {
+    if (i >= 0 && i < n) return i;
+    if (n > kDwtHalo) return i < 0 ? -i : 2 * (n - 1) - i;
     if (n == 1) return 0;
     const int period = 2 * (n - 1);
     i %= period;
@@ -68,16 +74,66 @@ __device__ __forceinline__ int32_t roi_up(int32_t q, int s) { return q < 0 ? -((
 
 }  // namespace
 
+// One 1-D lifting pass over N register values (x[0] has even parity).
+// Only positions 1..N-2 are updated (their neighbours exist); the caller's
+// apron keeps the outputs it uses away from the stale ends.
+template <int N>
+__device__ __forceinline__ void lift97(float (&x)[N])
+{
+#pragma unroll
+    for (int i = 1; i < N - 1; i += 2) x[i] += kA * (x[i - 1] + x[i + 1]);
+#pragma unroll
+    for (int i = 2; i < N - 1; i += 2) x[i] += kB * (x[i - 1] + x[i + 1]);
+#pragma unroll
+    for (int i = 1; i < N - 1; i += 2) x[i] += kG * (x[i - 1] + x[i + 1]);
+#pragma unroll
+    for (int i = 2; i < N - 1; i += 2) x[i] += kD * (x[i - 1] + x[i + 1]);
+#pragma unroll
+    for (int i = 0; i < N; i++) x[i] = (i & 1) ? x[i] * kK : __fdiv_rn(x[i], kK);
+}
+
+template <int N>
+__device__ __forceinline__ void lift53(int (&x)[N])
+{
+#pragma unroll
+    for (int i = 1; i < N - 1; i += 2) x[i] -= (x[i - 1] + x[i + 1]) >> 1;
+#pragma unroll
+    for (int i = 2; i < N - 1; i += 2) x[i] += (x[i - 1] + x[i + 1] + 2) >> 2;
+}
+
+template <typename V, int N>
+__device__ __forceinline__ void lift(V (&x)[N])
+{
+    if constexpr (std::is_same<V, float>::value) lift97<N>(x);
+    else lift53<N>(x);
+}
+
+// 1-D mask rule on a register window: low k from [2k+lo0, 2k+lo1], high k
+// from [2k+hi0, 2k+hi1] (relative to the window's even sample e = HALO+2k).
+template <int WAV, int N>
+__device__ __forceinline__ void mask_rule(const uint8_t (&m)[N], int e, uint8_t &lo, uint8_t &hi)
+{
+    constexpr int lo0 = WAV == 97 ? -3 : -1, lo1 = WAV == 97 ? 3 : 1;
+    constexpr int hi0 = WAV == 97 ? -3 : -1, hi1 = WAV == 97 ? 5 : 3;
+    uint8_t a = 0, b = 0;
+#pragma unroll
+    for (int d = lo0; d <= lo1; d++) a |= m[e + d];
+#pragma unroll
+    for (int d = hi0; d <= hi1; d++) b |= m[e + d];
+    lo = a;
+    hi = b;
+}
+
 template <int WAV>
 __global__ void __launch_bounds__(256) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
     using V = typename std::conditional<WAV == 97, float, int>::type;
-    constexpr int TW = kDwtTW, TH = kDwtTH, EW = kDwtEW, EH = kDwtEH, HALO = kDwtHalo;
-    constexpr int lo0 = WAV == 97 ? -3 : -1, lo1 = WAV == 97 ? 3 : 1;
-    constexpr int hi0 = WAV == 97 ? -3 : -1, hi1 = WAV == 97 ? 5 : 3;
+    constexpr int TW = kDwtTW, TH = kDwtTH, HALO = kDwtHalo;
+    constexpr int EW = 2 * TW + 2 * HALO, EH = 2 * TH + 2 * HALO;  // 136 x 72
+    constexpr int SEG = 8;                                          // band outputs per row item
+    constexpr int RW = 2 * SEG + 2 * HALO;                          // row window (24)
     __shared__ V s_x[EH][EW + 1];
-    __shared__ uint8_t s_m[EH][EW];
-    __shared__ uint8_t s_mv[2 * TH][EW];
+    __shared__ uint8_t s_m[EH][EW + 4];
 
     const int nfr = bd->nframes;
     const int *off = bd->dwt_off[level - 1];
@@ -95,145 +151,129 @@ __global__ void __launch_bounds__(256) k_dwt(const BatchDesc *__restrict__ bd, M
         const int ix0 = 2 * bx0 - HALO, iy0 = 2 * by0 - HALO;
         const V *llin = static_cast<const V *>(F.ll[level % 2]);
         const uint8_t *mlin = F.llm[level % 2];
-        for (int i = threadIdx.x; i < EH * EW; i += blockDim.x) {
-            const int r = i / EW, c = i - r * EW;
-            const int gy = iy0 + r, gx = ix0 + c;
-            const int my = mirror(gy, ih), mx = mirror(gx, iw);
-            V v;
-            if (level == 1) {
-                const uint8_t *row = static_cast<const uint8_t *>(F.raw) + (size_t)my * F.raw_pitch;
-                const int raw = F.bpp == 1 ? (int)__ldg(row + mx) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + mx);
-                v = (V)(raw - F.dc_off);
-            } else {
-                v = llin[(size_t)my * iw + mx];
+
+        // Load: samples with symmetric extension, mask clipped (0 outside).
+        // Two adjacent columns per thread (ix0 is even, so an in-range pair
+        // is one aligned 2-sample / 2-byte load).
+        const bool xin = ix0 >= 0 && ix0 + EW <= iw;
+        for (int r = threadIdx.x >> 5; r < EH; r += blockDim.x >> 5) {
+            const int gy = iy0 + r, my = mirror(gy, ih);
+            const bool rin = gy >= 0 && gy < ih;
+            const uint8_t *mrow = level == 1 ? F.mask + (size_t)gy * W : mlin + (size_t)gy * iw;
+            for (int c = 2 * (threadIdx.x & 31); c < EW; c += 64) {
+                const int gx = ix0 + c;
+                V v0, v1;
+                if (level == 1) {
+                    const uint8_t *row = static_cast<const uint8_t *>(F.raw) + (size_t)my * F.raw_pitch;
+                    int r0, r1;
+                    if (xin && F.bpp == 2) {
+                        const unsigned pr = __ldg(reinterpret_cast<const unsigned *>(row) + (gx >> 1));
+                        r0 = (int)(pr & 0xffffu);
+                        r1 = (int)(pr >> 16);
+                    } else {
+                        const int m0 = mirror(gx, iw), m1 = mirror(gx + 1, iw);
+                        r0 = F.bpp == 1 ? (int)__ldg(row + m0) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m0);
+                        r1 = F.bpp == 1 ? (int)__ldg(row + m1) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m1);
+                    }
+                    v0 = (V)(r0 - F.dc_off);
+                    v1 = (V)(r1 - F.dc_off);
+                } else {
+                    const V *row = llin + (size_t)my * iw;
+                    if (xin) {
+                        v0 = row[gx];
+                        v1 = row[gx + 1];
+                    } else {
+                        v0 = row[mirror(gx, iw)];
+                        v1 = row[mirror(gx + 1, iw)];
+                    }
+                }
+                s_x[r][c] = v0;
+                s_x[r][c + 1] = v1;
+                uint8_t m0 = 0, m1 = 0;
+                if (rin) {
+                    if (xin) {
+                        const unsigned short mm = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
+                        m0 = (uint8_t)(mm & 0xff);
+                        m1 = (uint8_t)(mm >> 8);
+                    } else {
+                        if (gx >= 0 && gx < iw) m0 = mrow[gx];
+                        if (gx + 1 >= 0 && gx + 1 < iw) m1 = mrow[gx + 1];
+                    }
+                }
+                s_m[r][c] = m0;
+                s_m[r][c + 1] = m1;
             }
-            s_x[r][c] = v;
-            uint8_t m = 0;
-            if (gx >= 0 && gx < iw && gy >= 0 && gy < ih) m = level == 1 ? F.mask[(size_t)gy * W + gx] : mlin[(size_t)gy * iw + gx];
-            s_m[r][c] = m;
         }
         __syncthreads();
 
-        // Vertical lifting (every column), rows of each parity in turn.
-        if constexpr (WAV == 97) {
-            const float cst[4] = {kA, kB, kG, kD};
+        // Vertical: threads [0, EW) lift one column each in registers; the
+        // other threads turn columns of the pixel mask into (low, high) row
+        // masks with the 1-D rule, in place (a column is private to its item).
+        if (threadIdx.x < EW) {
+            const int c = threadIdx.x;
+            V x[EH];
 #pragma unroll
-            for (int s = 0; s < 4; s++) {
-                const int par = (s % 2 == 0) ? 1 : 0;
-                const int nr = (EH - 1 - par) / 2;  // rows par, par+2, ... in [1, EH-1)
-                for (int i = threadIdx.x; i < nr * EW; i += blockDim.x) {
-                    const int k = i / EW, c = i - k * EW;
-                    const int r = par + 2 * k + (par == 0 ? 2 : 0);
-                    if (r < 1 || r >= EH - 1) continue;
-                    s_x[r][c] += cst[s] * (s_x[r - 1][c] + s_x[r + 1][c]);
-                }
-                __syncthreads();
-            }
-            for (int i = threadIdx.x; i < EH * EW; i += blockDim.x) {
-                const int r = i / EW, c = i - r * EW;
-                s_x[r][c] = (r & 1) ? s_x[r][c] * kK : __fdiv_rn(s_x[r][c], kK);
-            }
-            __syncthreads();
+            for (int j = 0; j < EH; j++) x[j] = s_x[j][c];
+            lift<V, EH>(x);
 #pragma unroll
-            for (int s = 0; s < 4; s++) {
-                const int par = (s % 2 == 0) ? 1 : 0;
-                const int nc = (EW - 1 - par) / 2;
-                for (int i = threadIdx.x; i < EH * nc; i += blockDim.x) {
-                    const int r = i / nc, k = i - r * nc;
-                    const int c = par + 2 * k + (par == 0 ? 2 : 0);
-                    if (c < 1 || c >= EW - 1) continue;
-                    s_x[r][c] += cst[s] * (s_x[r][c - 1] + s_x[r][c + 1]);
-                }
-                __syncthreads();
-            }
-            for (int i = threadIdx.x; i < EH * EW; i += blockDim.x) {
-                const int r = i / EW, c = i - r * EW;
-                s_x[r][c] = (c & 1) ? s_x[r][c] * kK : __fdiv_rn(s_x[r][c], kK);
-            }
-            __syncthreads();
+            for (int j = 0; j < EH; j++) s_x[j][c] = x[j];
         } else {
-            for (int i = threadIdx.x; i < (EH / 2) * EW; i += blockDim.x) {
-                const int k = i / EW, c = i - k * EW;
-                const int r = 2 * k + 1;
-                if (r >= EH - 1) continue;
-                s_x[r][c] -= (s_x[r - 1][c] + s_x[r + 1][c]) >> 1;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < (EH / 2) * EW; i += blockDim.x) {
-                const int k = i / EW, c = i - k * EW;
-                const int r = 2 * k;
-                if (r < 1 || r >= EH - 1) continue;
-                s_x[r][c] += (s_x[r - 1][c] + s_x[r + 1][c] + 2) >> 2;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < EH * (EW / 2); i += blockDim.x) {
-                const int r = i / (EW / 2), k = i - r * (EW / 2);
-                const int c = 2 * k + 1;
-                if (c >= EW - 1) continue;
-                s_x[r][c] -= (s_x[r][c - 1] + s_x[r][c + 1]) >> 1;
-            }
-            __syncthreads();
-            for (int i = threadIdx.x; i < EH * (EW / 2); i += blockDim.x) {
-                const int r = i / (EW / 2), k = i - r * (EW / 2);
-                const int c = 2 * k;
-                if (c < 1 || c >= EW - 1) continue;
-                s_x[r][c] += (s_x[r][c - 1] + s_x[r][c + 1] + 2) >> 2;
-            }
-            __syncthreads();
-        }
-
-        // Wavelet-domain mask: vertical rule into s_mv (low rows, then high rows).
-        for (int i = threadIdx.x; i < TH * EW; i += blockDim.x) {
-            const int j = i / EW, c = i - j * EW;
-            const int ce = HALO + 2 * j;
-            uint8_t l = 0, hm = 0;
+            for (int c = threadIdx.x - EW; c < EW; c += blockDim.x - EW) {
+                uint8_t m[EH];
 #pragma unroll
-            for (int d = lo0; d <= lo1; d++) l |= s_m[ce + d][c];
+                for (int j = 0; j < EH; j++) m[j] = s_m[j][c];
 #pragma unroll
-            for (int d = hi0; d <= hi1; d++) hm |= s_m[ce + d][c];
-            s_mv[j][c] = l;
-            s_mv[TH + j][c] = hm;
+                for (int k = 0; k < TH; k++) {
+                    uint8_t lo, hi;
+                    mask_rule<WAV, EH>(m, HALO + 2 * k, lo, hi);
+                    s_m[HALO + 2 * k][c] = lo;       // even rows: low-vertical mask
+                    s_m[HALO + 2 * k + 1][c] = hi;   // odd rows: high-vertical mask
+                }
+            }
         }
         __syncthreads();
 
-        for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
-            const int j = i / TW, k = i - j * TW;
-            const int gi = bx0 + k, gj = by0 + j;
-            if (gi >= bw || gj >= bh) continue;
-            const int er = HALO + 2 * j, ec = HALO + 2 * k;
-            uint8_t mll = 0, mhl = 0, mlh = 0, mhh = 0;
+        // Horizontal: one (output row, 16-coefficient segment) per thread.
+        {
+            const int rr = threadIdx.x / (TW / SEG), sg = threadIdx.x - rr * (TW / SEG);  // rr in [0, 2*TH)
+            const int row = HALO + rr;         // even: low-vertical row, odd: high
+            const int gj = by0 + (rr >> 1);
+            const int c0 = sg * 2 * SEG;       // window start (covers its apron)
+            if (rr < 2 * TH && gj < bh) {
+                V x[RW];
+                uint8_t m[RW];
 #pragma unroll
-            for (int d = lo0; d <= lo1; d++) { mll |= s_mv[j][ec + d]; mlh |= s_mv[TH + j][ec + d]; }
+                for (int j = 0; j < RW; j++) { x[j] = s_x[row][c0 + j]; m[j] = s_m[row][c0 + j]; }
+                lift<V, RW>(x);
+                const bool vhigh = rr & 1;
+                const int b_lo = vhigh ? 3 * (level - 1) + 1 : 3 * mc.dwt_levels;  // LH or LL
+                const int b_hi = vhigh ? 3 * (level - 1) + 2 : 3 * (level - 1);    // HH or HL
+                const float d_lo = mc.delta[b_lo], d_hi = mc.delta[b_hi];
+                const int ylo = vhigh ? bh + gj : gj;
 #pragma unroll
-            for (int d = hi0; d <= hi1; d++) { mhl |= s_mv[j][ec + d]; mhh |= s_mv[TH + j][ec + d]; }
-            const V yll = s_x[er][ec], yhl = s_x[er][ec + 1], ylh = s_x[er + 1][ec], yhh = s_x[er + 1][ec + 1];
-            const int b0 = 3 * (level - 1);
-            const size_t phl = (size_t)gj * W + bw + gi, plh = (size_t)(bh + gj) * W + gi, phh = (size_t)(bh + gj) * W + bw + gi;
-            int32_t q;
-            q = quantise(yhl, mc.delta[b0 + 0], WAV);
-            F.coeffs[phl] = mhl ? roi_up(q, mc.shift) : q;
-            q = quantise(ylh, mc.delta[b0 + 1], WAV);
-            F.coeffs[plh] = mlh ? roi_up(q, mc.shift) : q;
-            q = quantise(yhh, mc.delta[b0 + 2], WAV);
-            F.coeffs[phh] = mhh ? roi_up(q, mc.shift) : q;
-            if constexpr (WAV == 97) {
-                if (F.dbg_yf) {
-                    F.dbg_yf[phl] = yhl;
-                    F.dbg_yf[plh] = ylh;
-                    F.dbg_yf[phh] = yhh;
+                for (int k = 0; k < SEG; k++) {
+                    const int gi = bx0 + sg * SEG + k;
+                    if (gi >= bw) break;
+                    uint8_t mlo, mhi;
+                    mask_rule<WAV, RW>(m, HALO + 2 * k, mlo, mhi);
+                    const V ylo_v = x[HALO + 2 * k], yhi_v = x[HALO + 2 * k + 1];
+                    // high horizontal band (HL or HH)
+                    const size_t ph = (size_t)ylo * W + bw + gi;
+                    int32_t q = quantise(yhi_v, d_hi, WAV);
+                    F.coeffs[ph] = mhi ? roi_up(q, mc.shift) : q;
+                    if constexpr (WAV == 97) { if (F.dbg_yf) F.dbg_yf[ph] = yhi_v; }
+                    // low horizontal band (LL or LH)
+                    if (vhigh || last) {
+                        const size_t pl = (size_t)ylo * W + gi;
+                        q = quantise(ylo_v, d_lo, WAV);
+                        F.coeffs[pl] = mlo ? roi_up(q, mc.shift) : q;
+                        if constexpr (WAV == 97) { if (F.dbg_yf) F.dbg_yf[pl] = ylo_v; }
+                    } else {
+                        V *llout = static_cast<V *>(F.ll[(level - 1) % 2]);
+                        llout[(size_t)gj * bw + gi] = ylo_v;
+                        F.llm[(level - 1) % 2][(size_t)gj * bw + gi] = mlo;
+                    }
                 }
-            }
-            if (last) {
-                const size_t pll = (size_t)gj * W + gi;
-                q = quantise(yll, mc.delta[3 * mc.dwt_levels], WAV);
-                F.coeffs[pll] = mll ? roi_up(q, mc.shift) : q;
-                if constexpr (WAV == 97) {
-                    if (F.dbg_yf) F.dbg_yf[pll] = yll;
-                }
-            } else {
-                V *llout = static_cast<V *>(F.ll[(level - 1) % 2]);
-                llout[(size_t)gj * bw + gi] = yll;
-                F.llm[(level - 1) % 2][(size_t)gj * bw + gi] = mll;
             }
         }
         __syncthreads();

@@ -14,10 +14,12 @@
 //
 // Tile scheme: a block owns kFlowTW x kFlowTH output pixels.  Phase 1
 // computes G, h (5 floats) for the tile plus an r-pixel apron into shared
-// memory; phase 2 sums every column over 2r+1 rows; phase 3 sums every row
-// over 2r+1 columns; phase 4 solves.  Phases 2-3 keep a column (row) in
-// registers and add it as a tree of power-of-two partial sums (no running
-// sums: every window is a fresh sum of its own 2r+1 terms).
+// memory (threads in 32-wide rows, coalesced field loads); phase 2 sums
+// every column over 2r+1 rows in place; phase 3 sums 8 adjacent outputs of
+// a row over 2r+1 columns for all five fields and solves them.  Phases 2-3
+// keep a column (row segment) in registers and add it as a tree of
+// power-of-two partial sums (no running sums: every window is a fresh sum of
+// its own 2r+1 terms, so no cancellation between far-apart values).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -67,17 +69,18 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 }  // namespace
 
 template <typename T, int R>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
     k_flow(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int iter, int src, int dst)
 {
     constexpr int TW = kFlowTW, TH = kFlowTH;
     constexpr int EW = TW + 2 * R, EH = TH + 2 * R, WN = 2 * R + 1;
-    constexpr int SEG = 16;  // outputs per thread in the horizontal pass
+    constexpr int SEG = 8;             // outputs per item in the horizontal pass + solve
+    constexpr int NXS = (EW + 31) / 32; // column strides of the 32-wide thread rows
     extern __shared__ float smem[];
-    float *gh = smem;                // [5][EH][EW]; later [5][TH][TW] horizontal sums
-    float *vs = smem + 5 * EH * EW;  // [5][TH][EW] vertical sums
+    float *gh = smem;  // [5][EH][EW]: G, h; rows [0, TH) then hold the vertical sums
     using ST = Store<T>;
     using T4 = typename ST::T4;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
 
     const int nfr = bd->nframes;
     const int *off = bd->flow_off[level];
@@ -95,106 +98,126 @@ __global__ void __launch_bounds__(256, 2)
         const T4 *q2 = static_cast<const T4 *>(F.fq_prev[level]);
         const T *b2p = static_cast<const T *>(F.fb_prev[level]);
         const float2 *fsrc = F.flow[src];
+        const int wc = top ? 1 : F.lw[level + 1], hc = top ? 1 : F.lh[level + 1], pc = top ? 1 : F.lp[level + 1];
 
-        // ---- phase 1: G, h on the tile plus apron
-        for (int i = threadIdx.x; i < EH * EW; i += blockDim.x) {
-            const int ey = i / EW, ex = i - ey * EW;
-            const int gx = x0 - R + ex, gy = y0 - R + ey;
-            float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f, o4 = 0.f;
-            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-                float ddx = 0.f, ddy = 0.f;
+        // ---- phase 1: G, h on the tile plus apron (thread row ty, column tx)
+        for (int ey = ty; ey < EH; ey += 8) {
+            const int gy = y0 - R + ey;
+            const bool rowin = gy >= 0 && gy < h;
+            float ddx[NXS], ddy[NXS];
+            bool in[NXS];
+#pragma unroll
+            for (int k = 0; k < NXS; k++) {
+                const int ex = tx + 32 * k, gx = x0 - R + ex;
+                in[k] = rowin && ex < EW && gx >= 0 && gx < w;
+                ddx[k] = 0.f;
+                ddy[k] = 0.f;
+                if (!in[k]) continue;
                 if (iter > 0) {
                     const float2 v = fsrc[(size_t)gy * p + gx];
-                    ddx = v.x;
-                    ddy = v.y;
+                    ddx[k] = v.x;
+                    ddy[k] = v.y;
                 } else if (!top) {
-                    const int wc = F.lw[level + 1], hc = F.lh[level + 1], pc = F.lp[level + 1];
                     const int cx = gx >> 1, cy = gy >> 1;
                     const int cx1 = min(cx + 1, wc - 1), cy1 = min(cy + 1, hc - 1);
                     const float fx = (gx & 1) ? 0.5f : 0.f, fy = (gy & 1) ? 0.5f : 0.f;
                     const float2 a = fsrc[(size_t)cy * pc + cx], b = fsrc[(size_t)cy * pc + cx1];
                     const float2 c = fsrc[(size_t)cy1 * pc + cx], d = fsrc[(size_t)cy1 * pc + cx1];
-                    ddx = 2.f * ((1.f - fy) * ((1.f - fx) * a.x + fx * b.x) + fy * ((1.f - fx) * c.x + fx * d.x));
-                    ddy = 2.f * ((1.f - fy) * ((1.f - fx) * a.y + fx * b.y) + fy * ((1.f - fx) * c.y + fx * d.y));
+                    ddx[k] = 2.f * ((1.f - fy) * ((1.f - fx) * a.x + fx * b.x) + fy * ((1.f - fx) * c.x + fx * d.x));
+                    ddy[k] = 2.f * ((1.f - fy) * ((1.f - fx) * a.y + fx * b.y) + fy * ((1.f - fx) * c.y + fx * d.y));
                 }
-                // Sample position x + d~ split into integer and fraction so
-                // the fraction keeps full precision; clamped to the image.
-                const float flx = floorf(ddx), fly = floorf(ddy);
-                int ix = gx + (int)flx, iy = gy + (int)fly;
-                float fx = ddx - flx, fy = ddy - fly;
-                if (ix < 0) { ix = 0; fx = 0.f; } else if (ix >= w - 1) { ix = w - 1; fx = 0.f; }
-                if (iy < 0) { iy = 0; fy = 0.f; } else if (iy >= h - 1) { iy = h - 1; fy = 0.f; }
-                const int ix1 = min(ix + 1, w - 1), iy1 = min(iy + 1, h - 1);
-                const size_t r0 = (size_t)iy * p, r1 = (size_t)iy1 * p;
-                const float4 qa = ST::f4(ST::ld4(q2 + r0 + ix)), qb = ST::f4(ST::ld4(q2 + r0 + ix1));
-                const float4 qc = ST::f4(ST::ld4(q2 + r1 + ix)), qd = ST::f4(ST::ld4(q2 + r1 + ix1));
-                const float ba = ST::ld(b2p + r0 + ix), bb = ST::ld(b2p + r0 + ix1);
-                const float bc = ST::ld(b2p + r1 + ix), bdd = ST::ld(b2p + r1 + ix1);
-                const float A11b = ((1.f - fy) * ((1.f - fx) * qa.x + fx * qb.x) + fy * ((1.f - fx) * qc.x + fx * qd.x));
-                const float A12b = ((1.f - fy) * ((1.f - fx) * qa.y + fx * qb.y) + fy * ((1.f - fx) * qc.y + fx * qd.y));
-                const float A22b = ((1.f - fy) * ((1.f - fx) * qa.z + fx * qb.z) + fy * ((1.f - fx) * qc.z + fx * qd.z));
-                const float b1b = ((1.f - fy) * ((1.f - fx) * qa.w + fx * qb.w) + fy * ((1.f - fx) * qc.w + fx * qd.w));
-                const float b2b = ((1.f - fy) * ((1.f - fx) * ba + fx * bb) + fy * ((1.f - fx) * bc + fx * bdd));
-                const size_t o = (size_t)gy * p + gx;
-                const float4 qs = ST::f4(ST::ld4(q1 + o));
-                const float b2a = ST::ld(b1p + o);
-                const float a11 = 0.5f * (qs.x + A11b), a12 = 0.5f * (qs.y + A12b), a22 = 0.5f * (qs.z + A22b);
-                const float db1 = -0.5f * (b1b - qs.w) + (a11 * ddx + a12 * ddy);
-                const float db2 = -0.5f * (b2b - b2a) + (a12 * ddx + a22 * ddy);
-                o0 = a11 * a11 + a12 * a12;
-                o1 = a11 * a12 + a12 * a22;
-                o2 = a12 * a12 + a22 * a22;
-                o3 = a11 * db1 + a12 * db2;
-                o4 = a12 * db1 + a22 * db2;
             }
-            gh[0 * EH * EW + i] = o0;
-            gh[1 * EH * EW + i] = o1;
-            gh[2 * EH * EW + i] = o2;
-            gh[3 * EH * EW + i] = o3;
-            gh[4 * EH * EW + i] = o4;
+#pragma unroll
+            for (int k = 0; k < NXS; k++) {
+                const int ex = tx + 32 * k, gx = x0 - R + ex;
+                if (ex >= EW) continue;
+                float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f, o4 = 0.f;
+                if (in[k]) {
+                    const float dx = ddx[k], dy = ddy[k];
+                    // Position x + d~ as integer + fraction (full-precision
+                    // fraction), clamped to the image.
+                    const float flx = floorf(dx), fly = floorf(dy);
+                    int ix = gx + (int)flx, iy = gy + (int)fly;
+                    float fx = dx - flx, fy = dy - fly;
+                    if (ix < 0) { ix = 0; fx = 0.f; } else if (ix >= w - 1) { ix = w - 1; fx = 0.f; }
+                    if (iy < 0) { iy = 0; fy = 0.f; } else if (iy >= h - 1) { iy = h - 1; fy = 0.f; }
+                    const int ix1 = min(ix + 1, w - 1), iy1 = min(iy + 1, h - 1);
+                    const size_t r0 = (size_t)iy * p, r1 = (size_t)iy1 * p, o = (size_t)gy * p + gx;
+                    const float4 qa = ST::f4(ST::ld4(q2 + r0 + ix)), qb = ST::f4(ST::ld4(q2 + r0 + ix1));
+                    const float4 qc = ST::f4(ST::ld4(q2 + r1 + ix)), qd = ST::f4(ST::ld4(q2 + r1 + ix1));
+                    const float ba = ST::ld(b2p + r0 + ix), bb = ST::ld(b2p + r0 + ix1);
+                    const float bc = ST::ld(b2p + r1 + ix), bdd = ST::ld(b2p + r1 + ix1);
+                    const float4 qs = ST::f4(ST::ld4(q1 + o));
+                    const float b2a = ST::ld(b1p + o);
+                    const float gx0 = 1.f - fx, gy0 = 1.f - fy;
+                    const float A11b = gy0 * (gx0 * qa.x + fx * qb.x) + fy * (gx0 * qc.x + fx * qd.x);
+                    const float A12b = gy0 * (gx0 * qa.y + fx * qb.y) + fy * (gx0 * qc.y + fx * qd.y);
+                    const float A22b = gy0 * (gx0 * qa.z + fx * qb.z) + fy * (gx0 * qc.z + fx * qd.z);
+                    const float b1b = gy0 * (gx0 * qa.w + fx * qb.w) + fy * (gx0 * qc.w + fx * qd.w);
+                    const float b2b = gy0 * (gx0 * ba + fx * bb) + fy * (gx0 * bc + fx * bdd);
+                    const float a11 = 0.5f * (qs.x + A11b), a12 = 0.5f * (qs.y + A12b), a22 = 0.5f * (qs.z + A22b);
+                    const float db1 = -0.5f * (b1b - qs.w) + (a11 * dx + a12 * dy);
+                    const float db2 = -0.5f * (b2b - b2a) + (a12 * dx + a22 * dy);
+                    o0 = a11 * a11 + a12 * a12;
+                    o1 = a11 * a12 + a12 * a22;
+                    o2 = a12 * a12 + a22 * a22;
+                    o3 = a11 * db1 + a12 * db2;
+                    o4 = a12 * db1 + a22 * db2;
+                }
+                const int i = ey * EW + ex;
+                gh[0 * EH * EW + i] = o0;
+                gh[1 * EH * EW + i] = o1;
+                gh[2 * EH * EW + i] = o2;
+                gh[3 * EH * EW + i] = o3;
+                gh[4 * EH * EW + i] = o4;
+            }
         }
         __syncthreads();
 
-        // ---- phase 2: vertical window sums, one (field, column) per item
+        // ---- phase 2: vertical window sums, in place (a column is private to its item)
         for (int it = threadIdx.x; it < 5 * EW; it += blockDim.x) {
             const int k = it / EW, ex = it - k * EW;
+            float *col = gh + k * EH * EW + ex;
             float v[EH], s[TH];
 #pragma unroll
-            for (int j = 0; j < EH; j++) v[j] = gh[k * EH * EW + j * EW + ex];
+            for (int j = 0; j < EH; j++) v[j] = col[j * EW];
             box_sums<EH, WN>(v, s);
 #pragma unroll
-            for (int j = 0; j < TH; j++) vs[k * TH * EW + j * EW + ex] = s[j];
+            for (int j = 0; j < TH; j++) col[j * EW] = s[j];
         }
         __syncthreads();
 
-        // ---- phase 3: horizontal window sums, one (field, row, segment) per item
-        for (int it = threadIdx.x; it < 5 * TH * (TW / SEG); it += blockDim.x) {
-            const int k = it / (TH * (TW / SEG));
-            const int rem = it - k * TH * (TW / SEG);
-            const int row = rem / (TW / SEG), sg = rem - row * (TW / SEG);
-            float v[SEG + 2 * R], s[SEG];
+        // ---- phase 3: horizontal window sums of 8 outputs, then the solve
+        {
+            const int r = threadIdx.x / (TW / SEG), sg = threadIdx.x - r * (TW / SEG);
+            const int gy = y0 + r, gxs = x0 + sg * SEG;
+            if (r < TH && gy < h && gxs < w) {
+                float acc[5][SEG];
 #pragma unroll
-            for (int j = 0; j < SEG + 2 * R; j++) v[j] = vs[k * TH * EW + row * EW + sg * SEG + j];
-            box_sums<SEG + 2 * R, WN>(v, s);
+                for (int k = 0; k < 5; k++) {
+                    const float *row = gh + k * EH * EW + r * EW + sg * SEG;
+                    float v[SEG + 2 * R], sm[SEG];
 #pragma unroll
-            for (int j = 0; j < SEG; j++) gh[k * TH * TW + row * TW + sg * SEG + j] = s[j];
-        }
-        __syncthreads();
-
-        // ---- phase 4: means and 2x2 solve
-        float2 *fdst = F.flow[dst];
-        for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
-            const int r = i / TW, c = i - r * TW;
-            const int gx = x0 + c, gy = y0 + r;
-            if (gx >= w || gy >= h) continue;
-            const int cnt = (min(gx + R, w - 1) - max(gx - R, 0) + 1) * (min(gy + R, h - 1) - max(gy - R, 0) + 1);
-            const float fc = (float)cnt;
-            const float g11 = gh[0 * TH * TW + i] / fc, g12 = gh[1 * TH * TW + i] / fc, g22 = gh[2 * TH * TW + i] / fc;
-            const float h1 = gh[3 * TH * TW + i] / fc, h2 = gh[4 * TH * TW + i] / fc;
-            const float det = diff_of_products(g11, g22, g12, g12) + mc.lambda;
-            const float nx = diff_of_products(g22, h1, g12, h2);
-            const float ny = diff_of_products(g11, h2, g12, h1);
-            fdst[(size_t)gy * p + gx] = make_float2(nx / det, ny / det);
+                    for (int j = 0; j < SEG + 2 * R; j++) v[j] = row[j];
+                    box_sums<SEG + 2 * R, WN>(v, sm);
+#pragma unroll
+                    for (int j = 0; j < SEG; j++) acc[k][j] = sm[j];
+                }
+                const int cy = min(gy + R, h - 1) - max(gy - R, 0) + 1;
+                float2 *fdst = F.flow[dst] + (size_t)gy * p;
+#pragma unroll
+                for (int j = 0; j < SEG; j++) {
+                    const int gx = gxs + j;
+                    if (gx >= w) break;
+                    const int cx = min(gx + R, w - 1) - max(gx - R, 0) + 1;
+                    const float ic = 1.f / (float)(cx * cy);
+                    const float g11 = acc[0][j] * ic, g12 = acc[1][j] * ic, g22 = acc[2][j] * ic;
+                    const float h1 = acc[3][j] * ic, h2 = acc[4][j] * ic;
+                    const float idet = 1.f / (diff_of_products(g11, g22, g12, g12) + mc.lambda);
+                    fdst[gx] = make_float2(diff_of_products(g22, h1, g12, h2) * idet,
+                                           diff_of_products(g11, h2, g12, h1) * idet);
+                }
+            }
         }
         __syncthreads();
     }
@@ -205,7 +228,7 @@ static void launch_flow_t(const BatchDesc *bd, const MethodConsts &mc, int level
                           cudaStream_t s)
 {
     constexpr int EW = kFlowTW + 2 * R, EH = kFlowTH + 2 * R;
-    const size_t sm = sizeof(float) * (5 * EH * EW + 5 * kFlowTH * EW);
+    const size_t sm = sizeof(float) * (5 * EH * EW);
     // The dynamic shared-memory limit was raised by occ_flow_t at set-up.
     k_flow<T, R><<<grid, 256, sm, s>>>(bd, mc, level, iter, src, dst);
 }
@@ -214,7 +237,7 @@ template <typename T, int R>
 static int occ_flow_t()
 {
     constexpr int EW = kFlowTW + 2 * R, EH = kFlowTH + 2 * R;
-    const size_t sm = sizeof(float) * (5 * EH * EW + 5 * kFlowTH * EW);
+    const size_t sm = sizeof(float) * (5 * EH * EW);
     cudaFuncSetAttribute(k_flow<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flow<T, R>, 256, sm);

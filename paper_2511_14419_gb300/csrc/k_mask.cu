@@ -60,64 +60,107 @@ __global__ void k_frame_init(const BatchDesc *__restrict__ bd)
     }
 }
 
+// Block-private histogram + min/max kept across the consecutive tiles a
+// block takes from the same frame, flushed to the frame's reduction block
+// when the frame changes and at the end (persistent grids give each block a
+// run of tiles, mostly of one frame).
+struct BlockHist {
+    unsigned *hist;  // shared, kHistBins
+    unsigned *mm;    // shared, [0] min, [1] max
+    int frame = -1;
+
+    __device__ void begin(int f)
+    {
+        if (f == frame) return;
+        flush();
+        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) hist[i] = 0u;
+        if (threadIdx.x == 0) { mm[0] = 0x7f800000u; mm[1] = 0u; }
+        frame = f;
+        __syncthreads();
+    }
+    __device__ void flush_to(unsigned *red, bool minmax)
+    {
+        __syncthreads();
+        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
+            if (hist[i]) atomicAdd(red + kRedHist + i, hist[i]);
+        if (minmax && threadIdx.x == 0) {
+            atomicMin(red + kRedMin, mm[0]);
+            atomicMax(red + kRedMax, mm[1]);
+        }
+        __syncthreads();
+    }
+    unsigned *target = nullptr;
+    bool with_minmax = false;
+    __device__ void flush()
+    {
+        if (frame >= 0) flush_to(target, with_minmax);
+    }
+};
+
 // Saliency S, min/max of S, histogram of the first radix digit.
 __global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
     constexpr int TW = kSalTW, TH = kSalTH;
     __shared__ float s_m[TH + 2][TW + 2];
     __shared__ unsigned s_hist[kHistBins];
-    __shared__ unsigned s_mn[8], s_mx[8];
+    __shared__ unsigned s_mm[2];
     const int nfr = bd->nframes;
     const int *off = bd->sal_off;
     const int total = __ldg(off + nfr);
     const int buf = bd->final_flow_buf;
+    BlockHist bh{s_hist, s_mm};
+    bh.with_minmax = true;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
+        bh.begin(fi);
+        bh.target = F.red;
         const int w = F.W, h = F.H, p = F.lp[0];
         const int ntx = (w + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
         const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
         const float2 *fl = F.flow[buf];
-        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) s_hist[i] = 0u;
-        for (int i = threadIdx.x; i < (TH + 2) * (TW + 2); i += blockDim.x) {
-            const int r = i / (TW + 2), c = i - r * (TW + 2);
-            const int gy = clampi(y0 - 1 + r, 0, h - 1), gx = clampi(x0 - 1 + c, 0, w - 1);
-            const float2 d = fl[(size_t)gy * p + gx];
-            s_m[r][c] = sqrtf(d.x * d.x + d.y * d.y);
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+        for (int r = ty; r < TH + 2; r += 8) {
+            const int gy = clampi(y0 - 1 + r, 0, h - 1);
+            const float2 *row = fl + (size_t)gy * p;
+            for (int c = tx; c < TW + 2; c += 32) {
+                const float2 d = row[clampi(x0 - 1 + c, 0, w - 1)];
+                s_m[r][c] = sqrtf(d.x * d.x + d.y * d.y);
+            }
         }
         __syncthreads();
         unsigned mn = 0x7f800000u, mx = 0u;
-        for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
-            const int r = i / TW, c = i - r * TW;
-            const int gx = x0 + c, gy = y0 + r;
-            if (gx >= w || gy >= h) continue;
-            const float gxv = 0.5f * (s_m[r + 1][c + 2] - s_m[r + 1][c]);
-            const float gyv = 0.5f * (s_m[r + 2][c + 1] - s_m[r][c + 1]);
-            const float S = mc.alpha * s_m[r + 1][c + 1] + (1.f - mc.alpha) * sqrtf(gxv * gxv + gyv * gyv);
-            F.S[(size_t)gy * p + gx] = S;
-            if (F.dbg_flow) F.dbg_flow[(size_t)gy * w + gx] = fl[(size_t)gy * p + gx];
-            const unsigned b = __float_as_uint(S);
-            mn = min(mn, b);
-            mx = max(mx, b);
-            atomicAdd(&s_hist[b >> digit_shift(0)], 1u);
+#pragma unroll
+        for (int rr = 0; rr < TH / 8; rr++) {
+            const int r = ty + 8 * rr, gy = y0 + r;
+#pragma unroll
+            for (int cc = 0; cc < TW / 32; cc++) {
+                const int c = tx + 32 * cc, gx = x0 + c;
+                if (gx >= w || gy >= h) continue;
+                const float gxv = 0.5f * (s_m[r + 1][c + 2] - s_m[r + 1][c]);
+                const float gyv = 0.5f * (s_m[r + 2][c + 1] - s_m[r][c + 1]);
+                const float S = mc.alpha * s_m[r + 1][c + 1] + (1.f - mc.alpha) * sqrtf(gxv * gxv + gyv * gyv);
+                F.S[(size_t)gy * p + gx] = S;
+                if (F.dbg_flow) F.dbg_flow[(size_t)gy * w + gx] = fl[(size_t)gy * p + gx];
+                const unsigned b = __float_as_uint(S);
+                mn = min(mn, b);
+                mx = max(mx, b);
+                atomicAdd(&s_hist[b >> digit_shift(0)], 1u);
+            }
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
             mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
-        if ((threadIdx.x & 31) == 0) { s_mn[threadIdx.x >> 5] = mn; s_mx[threadIdx.x >> 5] = mx; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            for (int k = 1; k < (int)(blockDim.x >> 5); k++) { mn = min(mn, s_mn[k]); mx = max(mx, s_mx[k]); }
-            atomicMin(F.red + kRedMin, mn);
-            atomicMax(F.red + kRedMax, mx);
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&s_mm[0], mn);
+            atomicMax(&s_mm[1], mx);
         }
-        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
-            if (s_hist[i]) atomicAdd(F.red + kRedHist + i, s_hist[i]);
         __syncthreads();
     }
+    bh.flush();
 }
 
 // Histogram of radix digit `pass` (1 or 2) over the values whose higher
@@ -126,33 +169,39 @@ __global__ void __launch_bounds__(256) k_select_pass(const BatchDesc *__restrict
 {
     constexpr int TW = kSalTW, TH = kSalTH;
     __shared__ unsigned s_hist[kHistBins];
+    __shared__ unsigned s_mm[2];
     const int nfr = bd->nframes;
     const int *off = bd->sal_off;
     const int total = __ldg(off + nfr);
     const int sh = digit_shift(pass), hi = sh + digit_bits(pass);
     const unsigned dmask = (1u << digit_bits(pass)) - 1u;
+    BlockHist bh{s_hist, s_mm};
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
+        bh.begin(fi);
+        bh.target = F.red;
         const int w = F.W, h = F.H, p = F.lp[0];
         const int ntx = (w + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
         const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
         const unsigned want = __ldg(F.red + kRedPrefix) >> hi;
-        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x) s_hist[i] = 0u;
-        __syncthreads();
-        for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
-            const int r = i / TW, c = i - r * TW;
-            const int gx = x0 + c, gy = y0 + r;
+        // 4 pixels per thread per row (pitch is a multiple of 32 floats, so
+        // every 4-pixel group starting at a multiple of 4 is 16-byte aligned;
+        // the tail beyond the width lies inside the pitch and is masked).
+        constexpr int G = TW / 4;  // groups per row
+        for (int i = threadIdx.x; i < TH * G; i += blockDim.x) {
+            const int r = i / G, c4 = (i % G) * 4;
+            const int gx = x0 + c4, gy = y0 + r;
             if (gx >= w || gy >= h) continue;
-            const unsigned b = __float_as_uint(F.S[(size_t)gy * p + gx]);
-            if ((b >> hi) == want) atomicAdd(&s_hist[(b >> sh) & dmask], 1u);
+            const uint4 b4 = *reinterpret_cast<const uint4 *>(F.S + (size_t)gy * p + gx);
+            const unsigned bb[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (gx + j < w && (bb[j] >> hi) == want) atomicAdd(&s_hist[(bb[j] >> sh) & dmask], 1u);
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < kHistBins; i += blockDim.x)
-            if (s_hist[i]) atomicAdd(F.red + kRedHist + i, s_hist[i]);
-        __syncthreads();
     }
+    bh.flush();
 }
 
 // One block per frame: locate the bin of the current digit that holds the
@@ -207,6 +256,19 @@ __global__ void __launch_bounds__(256) k_select_find(const BatchDesc *__restrict
                 const float th = normalise(__uint_as_float(prefix), mn, mx);
                 red[kRedTS] = prefix;
                 red[kRedTHat] = __float_as_uint(th);
+                // normalise() is monotone in S, so {S : normalise(S) > th} =
+                // {S > s*} with s* the largest value normalising to <= th;
+                // binary search over the float bits in [t_S, max].
+                unsigned lo = prefix, hi = red[kRedMax];
+                if (normalise(__uint_as_float(hi), mn, mx) <= th) {
+                    lo = hi;
+                } else {
+                    while (hi - lo > 1u) {
+                        const unsigned mid = lo + ((hi - lo) >> 1);
+                        if (normalise(__uint_as_float(mid), mn, mx) <= th) lo = mid; else hi = mid;
+                    }
+                }
+                red[kRedSStar] = lo;
                 if (F.dbg_thr) *F.dbg_thr = th;
             }
         }
@@ -214,51 +276,60 @@ __global__ void __launch_bounds__(256) k_select_find(const BatchDesc *__restrict
     }
 }
 
-// Threshold + opening + closing on a tile with an apron of
-// 2*(r_open + r_close) pixels, in bytes in shared memory.
+// Threshold + opening + closing, bit-packed: 32 horizontally adjacent
+// pixels per 32-bit word (bit i = pixel x0 + i).  A block owns a tile of
+// kMorWords words x kMorRows rows and loads an apron of one word on each
+// side (>= the total radius 2*(r_open + r_close) <= 16) and 16 rows above
+// and below.  mask0 is formed with one warp ballot per word from coalesced
+// S reads; erosion / dilation of radius r are shifts and AND / OR across
+// neighbouring words, then across neighbouring rows.  Words and rows at the
+// apron's outer edge see missing neighbours as the neutral element; the
+// error this causes moves inwards by r per operation and never reaches the
+// tile (apron >= total radius).  Out-of-image pixels take no part: before
+// each operation they are set to its neutral element (1 for AND, 0 for OR).
 namespace {
 
 constexpr int kMorMaxR = 4;
-constexpr int kMorHalo = 4 * kMorMaxR;
-constexpr int kMorEW = kMorTW + 2 * kMorHalo, kMorEH = kMorTH + 2 * kMorHalo;
+constexpr int kMorWords = 8, kMorRows = 32;
+constexpr int kMorApron = 4 * kMorMaxR;                  // rows above and below
+constexpr int kMorEW = kMorWords + 2, kMorEH = kMorRows + 2 * kMorApron;
 
-// One separable min (erosion) or max (dilation) of radius r over the valid
-// region [m, E-m) of `a`, result back in `a` (valid region then [m+r, E-m-r)).
-__device__ __forceinline__ void morph_stage(uint8_t (*a)[kMorEW], uint8_t (*b)[kMorEW], int m, int r, bool erode)
+// Bits of word (wx) of row gy that lie inside the image.
+__device__ __forceinline__ unsigned in_image_bits(int wx, int gy, int w, int h)
 {
-    const int y0 = m, y1 = kMorEH - m, xa = m + r, xb = kMorEW - m - r;
-    for (int i = threadIdx.x; i < (y1 - y0) * (xb - xa); i += blockDim.x) {
-        const int y = y0 + i / (xb - xa), x = xa + i % (xb - xa);
-        uint8_t v = a[y][x];
+    if (gy < 0 || gy >= h || wx < 0) return 0u;
+    const int x = wx * 32;
+    if (x >= w) return 0u;
+    const int n = w - x;
+    return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+}
+
+__device__ __forceinline__ void morph_op(unsigned (*a)[kMorEW], unsigned (*b)[kMorEW], int r, bool erode, int wx0,
+                                         int gy0, int w, int h, bool next_erode, int ylo, int yhi)
+{
+    const unsigned neutral = erode ? 0xffffffffu : 0u;
+    const int n = (yhi - ylo) * kMorEW;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int y = ylo + i / kMorEW, x = i % kMorEW;
+        const unsigned m = a[y][x];
+        const unsigned l = x > 0 ? a[y][x - 1] : neutral, rr = x + 1 < kMorEW ? a[y][x + 1] : neutral;
+        unsigned v = m;
         for (int d = 1; d <= r; d++) {
-            const uint8_t l = a[y][x - d], rr = a[y][x + d];
-            v = erode ? (v & l & rr) : (v | l | rr);
+            const unsigned sl = (m << d) | (l >> (32 - d)), sr = (m >> d) | (rr << (32 - d));
+            v = erode ? (v & sl & sr) : (v | sl | sr);
         }
         b[y][x] = v;
     }
     __syncthreads();
-    const int ya = m + r, yb = kMorEH - m - r;
-    for (int i = threadIdx.x; i < (yb - ya) * (xb - xa); i += blockDim.x) {
-        const int y = ya + i / (xb - xa), x = xa + i % (xb - xa);
-        uint8_t v = b[y][x];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int y = ylo + i / kMorEW, x = i % kMorEW;
+        unsigned v = b[y][x];
         for (int d = 1; d <= r; d++) {
-            const uint8_t u = b[y - d][x], dd = b[y + d][x];
-            v = erode ? (v & u & dd) : (v | u | dd);
+            const unsigned up = y - d >= ylo ? b[y - d][x] : neutral, dn = y + d < yhi ? b[y + d][x] : neutral;
+            v = erode ? (v & up & dn) : (v | up | dn);
         }
-        a[y][x] = v;
-    }
-    __syncthreads();
-}
-
-// Out-of-image pixels of the valid region take the neutral value of the
-// next operation (1 before an erosion, 0 before a dilation).
-__device__ __forceinline__ void morph_pad(uint8_t (*a)[kMorEW], int m, int gx0, int gy0, int w, int h, uint8_t neutral)
-{
-    for (int i = threadIdx.x; i < kMorEH * kMorEW; i += blockDim.x) {
-        const int y = i / kMorEW, x = i - y * kMorEW;
-        if (y < m || y >= kMorEH - m || x < m || x >= kMorEW - m) continue;
-        const int gx = gx0 + x, gy = gy0 + y;
-        if (gx < 0 || gx >= w || gy < 0 || gy >= h) a[y][x] = neutral;
+        const unsigned inb = in_image_bits(wx0 + x, gy0 + y, w, h);
+        a[y][x] = (v & inb) | (next_erode ? ~inb : 0u);
     }
     __syncthreads();
 }
@@ -267,78 +338,98 @@ __device__ __forceinline__ void morph_pad(uint8_t (*a)[kMorEW], int m, int gx0, 
 
 __global__ void __launch_bounds__(256) k_morph(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
-    __shared__ uint8_t s_a[kMorEH][kMorEW];
-    __shared__ uint8_t s_b[kMorEH][kMorEW];
+    __shared__ unsigned s_a[kMorEH][kMorEW];
+    __shared__ unsigned s_b[kMorEH][kMorEW];
     const int nfr = bd->nframes;
     const int *off = bd->mor_off;
     const int total = __ldg(off + nfr);
     const int ro = mc.r_open, rc = mc.r_close;
-    const int H0 = kMorHalo - 2 * (ro + rc);  // unused outer margin of the buffers
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
         const int w = F.W, h = F.H, p = F.lp[0];
-        const int ntx = (w + kMorTW - 1) / kMorTW;
+        const int ntx = (w + 32 * kMorWords - 1) / (32 * kMorWords);
         const int lt = t - __ldg(off + fi);
-        const int x0 = (lt % ntx) * kMorTW, y0 = (lt / ntx) * kMorTH;
-        const int gx0 = x0 - kMorHalo, gy0 = y0 - kMorHalo;
+        const int tx = lt % ntx, ty = lt / ntx;
+        const int wx0 = tx * kMorWords - 1;         // global word index of apron column 0
+        const int gy0 = ty * kMorRows - kMorApron;  // global row of apron row 0
         if (!F.has_prev) {
-            for (int i = threadIdx.x; i < kMorTH * kMorTW; i += blockDim.x) {
-                const int r = i / kMorTW, c = i - r * kMorTW;
-                const int gx = x0 + c, gy = y0 + r;
-                if (gx >= w || gy >= h) continue;
-                F.mask[(size_t)gy * w + gx] = 0;
-                if (F.dbg_mask0) F.dbg_mask0[(size_t)gy * w + gx] = 0;
-                if (F.dbg_shat) F.dbg_shat[(size_t)gy * w + gx] = 0.f;
+            // no predecessor: empty mask
+            for (int i = threadIdx.x; i < kMorRows * kMorWords * 8; i += blockDim.x) {
+                const int r = i / (kMorWords * 8), q = i - r * (kMorWords * 8);
+                const int gy = ty * kMorRows + r, gx = (tx * kMorWords) * 32 + q * 4;
+                if (gy >= h) continue;
+                for (int j = 0; j < 4; j++)
+                    if (gx + j < w) {
+                        F.mask[(size_t)gy * w + gx + j] = 0;
+                        if (F.dbg_mask0) F.dbg_mask0[(size_t)gy * w + gx + j] = 0;
+                        if (F.dbg_shat) F.dbg_shat[(size_t)gy * w + gx + j] = 0.f;
+                    }
             }
             continue;
         }
+        const unsigned sstar = F.red[kRedSStar];
+        const bool keep = F.dbg_mask0 != nullptr;
         const float mn = __uint_as_float(F.red[kRedMin]), mx = __uint_as_float(F.red[kRedMax]);
-        const float th = __uint_as_float(F.red[kRedTHat]);
-        // mask0 on the buffer's used region; outside the image: 1 (the
-        // first operation is an erosion, or with r_open = 0 a dilation
-        // that the pad below fixes).
-        for (int i = threadIdx.x; i < kMorEH * kMorEW; i += blockDim.x) {
-            const int y = i / kMorEW, x = i - y * kMorEW;
-            if (y < H0 || y >= kMorEH - H0 || x < H0 || x >= kMorEW - H0) continue;
-            const int gx = gx0 + x, gy = gy0 + y;
-            uint8_t v = 1;
-            if (gx >= 0 && gx < w && gy >= 0 && gy < h) {
-                const float sh = normalise(F.S[(size_t)gy * p + gx], mn, mx);
-                v = sh > th ? 1 : 0;
-                if (y >= kMorHalo && y < kMorHalo + kMorTH && x >= kMorHalo && x < kMorHalo + kMorTW) {
-                    if (F.dbg_mask0) F.dbg_mask0[(size_t)gy * w + gx] = v;
-                    if (F.dbg_shat) F.dbg_shat[(size_t)gy * w + gx] = sh;
-                }
+        // Pack mask0 = (S > s*) one row per warp, each lane loading one pixel
+        // of every word of the row (all loads of the row in flight together).
+        // Out-of-image bits = 1 (the first operation is an erosion; with
+        // r_open = 0 the first is a dilation, padded below).  Rows outside
+        // the apron actually needed (2*(r_open + r_close)) are left unused.
+        const int apron = 2 * (ro + rc);
+        for (int y = kMorApron - apron + warp; y < kMorApron + kMorRows + apron; y += nwarps) {
+            const int gy = gy0 + y;
+            const bool rin = gy >= 0 && gy < h;
+            unsigned bits[kMorEW];
+#pragma unroll
+            for (int x = 0; x < kMorEW; x++) {
+                const int gx = (wx0 + x) * 32 + lane;
+                bits[x] = (rin && gx >= 0 && gx < w) ? __float_as_uint(F.S[(size_t)gy * p + gx]) : 0xffffffffu;
             }
-            s_a[y][x] = v;
+#pragma unroll
+            for (int x = 0; x < kMorEW; x++) {
+                const bool inb = bits[x] != 0xffffffffu;
+                const bool bit = inb ? bits[x] > sstar : true;
+                if (keep && inb && y >= kMorApron && y < kMorApron + kMorRows && x >= 1 && x <= kMorWords) {
+                    const int gx = (wx0 + x) * 32 + lane;
+                    F.dbg_mask0[(size_t)gy * w + gx] = bit ? 1 : 0;
+                    F.dbg_shat[(size_t)gy * w + gx] = normalise(__uint_as_float(bits[x]), mn, mx);
+                }
+                const unsigned word = __ballot_sync(0xffffffffu, bit);
+                if (lane == 0) s_a[y][x] = word;
+            }
         }
         __syncthreads();
-        int m = H0;
+        const int ylo = kMorApron - apron, yhi = kMorApron + kMorRows + apron;
         if (ro > 0) {
-            morph_stage(s_a, s_b, m, ro, true);
-            m += ro;
-        }
-        morph_pad(s_a, m, gx0, gy0, w, h, 0);
-        if (ro > 0) {
-            morph_stage(s_a, s_b, m, ro, false);
-            m += ro;
-            morph_pad(s_a, m, gx0, gy0, w, h, 0);
+            morph_op(s_a, s_b, ro, true, wx0, gy0, w, h, false, ylo, yhi);
+            morph_op(s_a, s_b, ro, false, wx0, gy0, w, h, rc == 0, ylo, yhi);
+        } else {
+            for (int i = threadIdx.x; i < (yhi - ylo) * kMorEW; i += blockDim.x) {
+                const int y = ylo + i / kMorEW, x = i % kMorEW;
+                s_a[y][x] &= in_image_bits(wx0 + x, gy0 + y, w, h);
+            }
+            __syncthreads();
         }
         if (rc > 0) {
-            morph_stage(s_a, s_b, m, rc, false);
-            m += rc;
+            morph_op(s_a, s_b, rc, false, wx0, gy0, w, h, true, ylo, yhi);
+            morph_op(s_a, s_b, rc, true, wx0, gy0, w, h, false, ylo, yhi);
         }
-        morph_pad(s_a, m, gx0, gy0, w, h, 1);
-        if (rc > 0) {
-            morph_stage(s_a, s_b, m, rc, true);
-            m += rc;
-        }
-        for (int i = threadIdx.x; i < kMorTH * kMorTW; i += blockDim.x) {
-            const int r = i / kMorTW, c = i - r * kMorTW;
-            const int gx = x0 + c, gy = y0 + r;
-            if (gx >= w || gy >= h) continue;
-            F.mask[(size_t)gy * w + gx] = s_a[kMorHalo + r][kMorHalo + c];
+        // Unpack the tile: 4 pixels (one byte each) per item.
+        for (int i = threadIdx.x; i < kMorRows * kMorWords * 8; i += blockDim.x) {
+            const int r = i / (kMorWords * 8), q = i - r * (kMorWords * 8);
+            const int gy = ty * kMorRows + r, gx = (tx * kMorWords) * 32 + q * 4;
+            if (gy >= h || gx >= w) continue;
+            const unsigned word = s_a[kMorApron + r][1 + (q >> 3)];
+            const unsigned nib = (word >> ((q & 7) * 4)) & 0xfu;
+            const unsigned bytes = (nib * 0x00204081u) & 0x01010101u;
+            uint8_t *dst = F.mask + (size_t)gy * w + gx;
+            if (gx + 4 <= w && ((((size_t)gy * w + gx) & 3) == 0)) {
+                *reinterpret_cast<unsigned *>(dst) = bytes;
+            } else {
+                for (int j = 0; j < 4 && gx + j < w; j++) dst[j] = (uint8_t)((bytes >> (8 * j)) & 1u);
+            }
         }
         __syncthreads();
     }

@@ -355,7 +355,7 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
         for (int l = 1; l <= D; l++)
             bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH);
         bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
-        bd.mor_off[i + 1] = bd.mor_off[i] + tiles(F.W, F.H, kMorTW, kMorTH);
+        bd.mor_off[i + 1] = bd.mor_off[i] + tiles(F.W, F.H, kMorTW, kMorTH);  // 256 x 32 pixel tiles
         bd.frm_off[i + 1] = i + 1;
     }
 }
@@ -388,7 +388,9 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     const int L = c->cfg.pyr_levels, D = c->cfg.dwt_levels, I = c->cfg.iters;
     const int n = hd->nframes;
     const bool pl = c->plain;
-    auto g = [&](int exact, int persistent) { return pl ? std::max(exact, 1) : persistent; };
+    // Plain path: one frame per launch, the same persistent kernels with a
+    // grid no larger than the frame's tile count.
+    auto g = [&](int exact, int persistent) { return pl ? std::max(1, std::min(exact, persistent)) : persistent; };
     int cnt = 0;
     const bool any_prev = !pl || hd->sal_off[n] > 0;
     timed(c, st, prof, K_INIT, -1, -1, [&] { launch_frame_init(dd, g(n, c->grid_frames), st); });
