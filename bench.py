@@ -53,15 +53,20 @@ WORKLOADS = {
                         dwt_levels=5, wavelet=53, precision=32, seed_base=2000),
 }
 
-# Algorithmic bytes per level-0 pixel of one displacement launch (read
-# A1,A12,A22,b1,b2 of the current frame, the same five fields of the
-# previous frame at the warped position, the prior flow; write the flow):
-# 5+5 fields x 4 B + 8 + 8 = 56 B (fp32 storage), 5+5 fields x 2 B + 16 =
-# 36 B (fp16); the first iteration of a level reads the coarse flow (2 B/px).
-FLOW_BYTES = {32: (50.0, 56.0), 16: (30.0, 36.0)}
-# DRAM bytes per level-0 pixel per launch of that kernel measured by ncu on
-# the current kernel (null when not measured for this build).
-FLOW_TRAFFIC_PER_PX = {32: None, 16: None}
+# Algorithmic bytes per level-0 pixel of one launch of the two displacement
+# kernels (storage 32 = fp32 fields, 16 = fp16), (first iteration, later ones):
+#   update: read the five expansion fields of the current frame and, at the
+#           warped position, of the previous frame, plus the prior flow (the
+#           coarse flow, a quarter of a pixel's 8 B, on the first iteration);
+#           write the five G, h planes:   fp32 5*4+5*4+{2,8}+5*4 = {62, 68} B
+#                                         fp16 5*2+5*2+{2,8}+5*2 = {32, 38} B
+#   window: read the five G, h planes, write the flow: fp32 20+8 = 28 B,
+#           fp16 10+8 = 18 B.
+KERNEL_BYTES = {("update", 32): (62.0, 68.0), ("update", 16): (32.0, 38.0),
+                ("window", 32): (28.0, 28.0), ("window", 16): (18.0, 18.0)}
+# DRAM bytes per level-0 pixel per launch measured by ncu on the current
+# kernels (None until measured for this build).
+KERNEL_TRAFFIC_PER_PX = {}
 
 
 def log(*a):
@@ -420,24 +425,29 @@ def main():
     else:
         latency = None
 
-    # roofline of the dominant kernel: level-0 displacement iterations
+    # roofline of the dominant kernel (by share of the step): the level-0
+    # launches of the two displacement kernels
     peak, peak_kind = peaks()
     kt = dev.get("kernel_times") or []
     tot = sum(k["total_ms"] for k in kt) or 1.0
-    flow0 = [k for k in kt if k["name"] == "flow" and k["level"] == 0]
     px = wl["h"] * wl["w"] * wl["streams"]
-    b_first, b_rest = FLOW_BYTES[wl["precision"]]
-    roof = None
-    if flow0:
-        byts = sum((b_first if k["iter"] == 0 else b_rest) * px * k["launches"] for k in flow0)
-        ms = sum(k["total_ms"] for k in flow0)
-        nl = sum(k["launches"] for k in flow0)
+    roofs = []
+    for name in ("update", "window"):
+        l0 = [k for k in kt if k["name"] == name and k["level"] == 0]
+        if not l0:
+            continue
+        b_first, b_rest = KERNEL_BYTES[(name, wl["precision"])]
+        byts = sum((b_first if k["iter"] == 0 else b_rest) * px * k["launches"] for k in l0)
+        ms = sum(k["total_ms"] for k in l0)
+        nl = sum(k["launches"] for k in l0)
         achieved = byts / (ms / 1e3) / 1e9
-        tr = FLOW_TRAFFIC_PER_PX[wl["precision"]]
-        roof = {"kernel": "k_flow level 0 (update+window+solve)", "bound": "hbm", "achieved": achieved,
-                "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
-                "traffic": (tr * px) if tr else None, "algorithmic_bytes_per_launch": byts / nl,
-                "avg_launch_ms": ms / nl, "share_of_step": ms / tot}
+        tr = KERNEL_TRAFFIC_PER_PX.get((name, wl["precision"]))
+        roofs.append({"kernel": f"k_{name} level 0", "bound": "hbm", "achieved": achieved, "peak": peak,
+                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
+                      "traffic": (tr * px) if tr else None, "algorithmic_bytes_per_launch": byts / nl,
+                      "avg_launch_ms": ms / nl, "share_of_step": ms / tot})
+    roofs.sort(key=lambda r: -r["share_of_step"])
+    roof = roofs[0] if roofs else None
     kernels = {}
     for k in kt:
         key = k["name"] + ("" if k["level"] < 0 else f"[{k['level']}]")
@@ -459,7 +469,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args.workload, wl), "e2e": e2e, "gpu_launches": dev["launches"],
                 "plain_fps": plain, "latency": latency, "clocks": dev.get("clocks"), "roofline": roof,
-                "cpu_baseline": cpu, "kernel_avg_ms": kernels}
+                "cpu_baseline": cpu, "kernel_avg_ms": kernels, "roofline_other": roofs[1:]}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()

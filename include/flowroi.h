@@ -109,13 +109,13 @@ typedef struct flowroi_config {
     int32_t dwt_levels;        /* D in [1, 8] */
     int32_t pyr_levels;        /* L in [1, 8] */
     int32_t iters;             /* displacement iterations per pyramid level, [1, 8] (3) */
-    int32_t win_r;             /* box window radius r in [1, 12]: side 2r+1 (7) */
+    int32_t win_r;             /* box window radius r in [2, 10]: side 2r+1 (7) */
     int32_t poly_n_half;       /* expansion radius n in {2, 3}: side 2n+1 (2) */
     float poly_sigma;          /* applicability sigma (1.1) */
-    float lambda;              /* solve regulariser, added to det (1e-3) */
+    float lambda;              /* solve regulariser (> 0), added to det (1e-3) */
     float sal_weight;          /* alpha: S = alpha*|d| + (1-alpha)*|grad|d|| (0.7) */
-    int32_t r_open;            /* opening radius in [0, 8] (1) */
-    int32_t r_close;           /* closing radius in [0, 8] (2) */
+    int32_t r_open;            /* opening radius in [0, 4] (1) */
+    int32_t r_close;           /* closing radius in [0, 4] (2) */
     int32_t precision;         /* FLOWROI_FP32 or FLOWROI_FP16 */
     float delta_base;          /* 9/7: base quantisation step (1.0) */
     int32_t max_batch_frames;  /* frames per batched launch, [1, 64] (64) */
@@ -251,10 +251,10 @@ FLOWROI_API int flowroi_compute_stream(flowroi_ctx *ctx, void **out);
  * rows (or a negative status).  Turning profiling off keeps the totals;
  * flowroi_set_profiling(ctx, 2) clears them and turns profiling on. */
 typedef struct flowroi_kernel_time {
-    char name[24];       /* "expand", "flow", "saliency", "select_pass", "select_find",
+    char name[24];       /* "expand", "update", "window", "saliency", "select_pass", "select_find",
                             "morph", "dwt", "frame_init" */
-    int32_t level;       /* pyramid level (expand, flow), DWT level (dwt), digit pass, or -1 */
-    int32_t iter;        /* displacement iteration (flow), else -1 */
+    int32_t level;       /* pyramid level (expand, update, window), DWT level (dwt), digit pass, or -1 */
+    int32_t iter;        /* displacement iteration (update, window), else -1 */
     int64_t launches;
     double total_ms;
 } flowroi_kernel_time;

@@ -2,6 +2,7 @@
 // FlowRoI kernels and the runtime that fills them.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -15,7 +16,8 @@ constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 
 // Tile shapes (output pixels per block) of each kernel family.
 constexpr int kExpTW = 64, kExpTH = 16;   // pyramid + polynomial expansion
-constexpr int kFlowTW = 64, kFlowTH = 32; // displacement update + window + solve
+constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
+constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
 constexpr int kSalTW = 64, kSalTH = 16;   // saliency, radix-select passes
 constexpr int kMorTW = 256, kMorTH = 32;  // threshold + opening + closing (8 words x 32 rows)
 constexpr int kDwtTW = 64, kDwtTH = 16;   // DWT: band coefficients per block (per band)
@@ -55,6 +57,8 @@ struct MethodConsts {
 // elements.  All planes of the previous frame of the same stream are read
 // through fq_prev / fb_prev.
 struct FrameDesc {
+    // TMA maps of the five G, h planes per level (3-D: x, y, plane).
+    CUtensorMap gh_map[kMaxLevels];
     int W, H, bpp, bit_depth;
     int has_prev, keep, raw_pitch, dc_off;  // raw_pitch in bytes; dc_off = 2^(B-1)
     float unit_scale;                        // 255 / (2^B - 1)
@@ -64,6 +68,7 @@ struct FrameDesc {
     void *pyr[kMaxLevels];          // level images 1..L-1 (storage type)
     void *fq_cur[kMaxLevels];       // A11, A12, A22, b1 (4 x storage type per pixel)
     void *fb_cur[kMaxLevels];       // b2 (storage type per pixel)
+    void *gh[kMaxLevels];           // G11, G12, G22, h1, h2: five planes (storage type)
     const void *fq_prev[kMaxLevels];
     const void *fb_prev[kMaxLevels];
     float2 *flow[2];                // ping-pong flow buffers, level-0 capacity
@@ -85,9 +90,10 @@ struct FrameDesc {
 struct BatchDesc {
     int nframes;
     int final_flow_buf;             // ping-pong index holding the level-0 flow
-    int pad[2];
+    unsigned *err;                  // error word (mapped host memory); kernels set it on a failed wait
     int exp_off[kMaxLevels][kMaxBatch + 1];
-    int flow_off[kMaxLevels][kMaxBatch + 1];
+    int flow_off[kMaxLevels][kMaxBatch + 1];   // update tiles
+    int win_off[kMaxLevels][kMaxBatch + 1];    // window tiles
     int dwt_off[kMaxLevels][kMaxBatch + 1];
     int sal_off[kMaxBatch + 1];     // frames with a predecessor only
     int mor_off[kMaxBatch + 1];     // every frame

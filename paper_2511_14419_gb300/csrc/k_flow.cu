@@ -12,16 +12,16 @@
 //     G_, h_ = means over the (2r+1)^2 box around x (clipped to the image)
 //     d  = adj(G_) h_ / (det G_ + lambda)
 //
-// Tile scheme: a block owns kFlowTW x kFlowTH output pixels.  Phase 1
-// computes G, h (5 floats) for the tile plus an r-pixel apron into shared
-// memory (threads in 32-wide rows, coalesced field loads); phase 2 sums
-// every column over 2r+1 rows in place; phase 3 sums 8 adjacent outputs of
-// a row over 2r+1 columns for all five fields and solves them.  Phases 2-3
-// keep a column (row segment) in registers and add it as a tree of
-// power-of-two partial sums (no running sums: every window is a fresh sum of
-// its own 2r+1 terms, so no cancellation between far-apart values).
+// Two kernels per iteration: k_update computes G and h per pixel into five
+// planes (no apron recompute, no shared memory: full occupancy hides the
+// gather latency); k_window forms the box means over a shared-memory tile
+// and solves.  Box sums keep a column (row segment) in registers and add it
+// as a tree of power-of-two partial sums (no running sums: every window is
+// a fresh sum of its own 2r+1 terms, so no cancellation between far-apart
+// values).
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 namespace flowroi {
 
@@ -68,20 +68,17 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 
 }  // namespace
 
-template <typename T, int R>
-__global__ void __launch_bounds__(256, 3)
-    k_flow(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int iter, int src, int dst)
+// ---------------------------------------------------------------- update
+// Per pixel G = A^T A and h = A^T db (5 values) into five planes.  One
+// thread owns a column of kUpdRows rows of a 256-wide row band, so its
+// loads for those pixels are in flight together; no shared memory, full
+// occupancy hides the gather latency.
+template <typename T>
+__global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int iter,
+                                              int src)
 {
-    constexpr int TW = kFlowTW, TH = kFlowTH;
-    constexpr int EW = TW + 2 * R, EH = TH + 2 * R, WN = 2 * R + 1;
-    constexpr int SEG = 8;             // outputs per item in the horizontal pass + solve
-    constexpr int NXS = (EW + 31) / 32; // column strides of the 32-wide thread rows
-    extern __shared__ float smem[];
-    float *gh = smem;  // [5][EH][EW]: G, h; rows [0, TH) then hold the vertical sums
     using ST = Store<T>;
     using T4 = typename ST::T4;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-
     const int nfr = bd->nframes;
     const int *off = bd->flow_off[level];
     const int total = __ldg(off + nfr);
@@ -90,104 +87,160 @@ __global__ void __launch_bounds__(256, 3)
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
         const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
-        const int ntx = (w + TW - 1) / TW;
+        const int ntx = (w + kUpdTW - 1) / kUpdTW;
         const int lt = t - __ldg(off + fi);
-        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
+        const int gx = (lt % ntx) * kUpdTW + threadIdx.x, y0 = (lt / ntx) * kUpdRows;
+        if (gx >= w) continue;
         const T4 *q1 = static_cast<const T4 *>(F.fq_cur[level]);
         const T *b1p = static_cast<const T *>(F.fb_cur[level]);
         const T4 *q2 = static_cast<const T4 *>(F.fq_prev[level]);
         const T *b2p = static_cast<const T *>(F.fb_prev[level]);
         const float2 *fsrc = F.flow[src];
-        const int wc = top ? 1 : F.lw[level + 1], hc = top ? 1 : F.lh[level + 1], pc = top ? 1 : F.lp[level + 1];
-
-        // ---- phase 1: G, h on the tile plus apron (thread row ty, column tx)
-        for (int ey = ty; ey < EH; ey += 8) {
-            const int gy = y0 - R + ey;
-            const bool rowin = gy >= 0 && gy < h;
-            float ddx[NXS], ddy[NXS];
-            bool in[NXS];
+        T *gh = static_cast<T *>(F.gh[level]);
+        const size_t plane = (size_t)p * h;
+        float ddx[kUpdRows], ddy[kUpdRows];
 #pragma unroll
-            for (int k = 0; k < NXS; k++) {
-                const int ex = tx + 32 * k, gx = x0 - R + ex;
-                in[k] = rowin && ex < EW && gx >= 0 && gx < w;
-                ddx[k] = 0.f;
-                ddy[k] = 0.f;
-                if (!in[k]) continue;
-                if (iter > 0) {
-                    const float2 v = fsrc[(size_t)gy * p + gx];
-                    ddx[k] = v.x;
-                    ddy[k] = v.y;
-                } else if (!top) {
-                    const int cx = gx >> 1, cy = gy >> 1;
-                    const int cx1 = min(cx + 1, wc - 1), cy1 = min(cy + 1, hc - 1);
-                    const float fx = (gx & 1) ? 0.5f : 0.f, fy = (gy & 1) ? 0.5f : 0.f;
-                    const float2 a = fsrc[(size_t)cy * pc + cx], b = fsrc[(size_t)cy * pc + cx1];
-                    const float2 c = fsrc[(size_t)cy1 * pc + cx], d = fsrc[(size_t)cy1 * pc + cx1];
-                    ddx[k] = 2.f * ((1.f - fy) * ((1.f - fx) * a.x + fx * b.x) + fy * ((1.f - fx) * c.x + fx * d.x));
-                    ddy[k] = 2.f * ((1.f - fy) * ((1.f - fx) * a.y + fx * b.y) + fy * ((1.f - fx) * c.y + fx * d.y));
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < NXS; k++) {
-                const int ex = tx + 32 * k, gx = x0 - R + ex;
-                if (ex >= EW) continue;
-                float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f, o4 = 0.f;
-                if (in[k]) {
-                    const float dx = ddx[k], dy = ddy[k];
-                    // Position x + d~ as integer + fraction (full-precision
-                    // fraction), clamped to the image.
-                    const float flx = floorf(dx), fly = floorf(dy);
-                    int ix = gx + (int)flx, iy = gy + (int)fly;
-                    float fx = dx - flx, fy = dy - fly;
-                    if (ix < 0) { ix = 0; fx = 0.f; } else if (ix >= w - 1) { ix = w - 1; fx = 0.f; }
-                    if (iy < 0) { iy = 0; fy = 0.f; } else if (iy >= h - 1) { iy = h - 1; fy = 0.f; }
-                    const int ix1 = min(ix + 1, w - 1), iy1 = min(iy + 1, h - 1);
-                    const size_t r0 = (size_t)iy * p, r1 = (size_t)iy1 * p, o = (size_t)gy * p + gx;
-                    const float4 qa = ST::f4(ST::ld4(q2 + r0 + ix)), qb = ST::f4(ST::ld4(q2 + r0 + ix1));
-                    const float4 qc = ST::f4(ST::ld4(q2 + r1 + ix)), qd = ST::f4(ST::ld4(q2 + r1 + ix1));
-                    const float ba = ST::ld(b2p + r0 + ix), bb = ST::ld(b2p + r0 + ix1);
-                    const float bc = ST::ld(b2p + r1 + ix), bdd = ST::ld(b2p + r1 + ix1);
-                    const float4 qs = ST::f4(ST::ld4(q1 + o));
-                    const float b2a = ST::ld(b1p + o);
-                    const float gx0 = 1.f - fx, gy0 = 1.f - fy;
-                    const float A11b = gy0 * (gx0 * qa.x + fx * qb.x) + fy * (gx0 * qc.x + fx * qd.x);
-                    const float A12b = gy0 * (gx0 * qa.y + fx * qb.y) + fy * (gx0 * qc.y + fx * qd.y);
-                    const float A22b = gy0 * (gx0 * qa.z + fx * qb.z) + fy * (gx0 * qc.z + fx * qd.z);
-                    const float b1b = gy0 * (gx0 * qa.w + fx * qb.w) + fy * (gx0 * qc.w + fx * qd.w);
-                    const float b2b = gy0 * (gx0 * ba + fx * bb) + fy * (gx0 * bc + fx * bdd);
-                    const float a11 = 0.5f * (qs.x + A11b), a12 = 0.5f * (qs.y + A12b), a22 = 0.5f * (qs.z + A22b);
-                    const float db1 = -0.5f * (b1b - qs.w) + (a11 * dx + a12 * dy);
-                    const float db2 = -0.5f * (b2b - b2a) + (a12 * dx + a22 * dy);
-                    o0 = a11 * a11 + a12 * a12;
-                    o1 = a11 * a12 + a12 * a22;
-                    o2 = a12 * a12 + a22 * a22;
-                    o3 = a11 * db1 + a12 * db2;
-                    o4 = a12 * db1 + a22 * db2;
-                }
-                const int i = ey * EW + ex;
-                gh[0 * EH * EW + i] = o0;
-                gh[1 * EH * EW + i] = o1;
-                gh[2 * EH * EW + i] = o2;
-                gh[3 * EH * EW + i] = o3;
-                gh[4 * EH * EW + i] = o4;
+        for (int j = 0; j < kUpdRows; j++) {
+            const int gy = y0 + j;
+            ddx[j] = 0.f;
+            ddy[j] = 0.f;
+            if (gy >= h) continue;
+            if (iter > 0) {
+                const float2 v = fsrc[(size_t)gy * p + gx];
+                ddx[j] = v.x;
+                ddy[j] = v.y;
+            } else if (!top) {
+                const int wc = F.lw[level + 1], hc = F.lh[level + 1], pc = F.lp[level + 1];
+                const int cx = gx >> 1, cy = gy >> 1;
+                const int cx1 = min(cx + 1, wc - 1), cy1 = min(cy + 1, hc - 1);
+                const float fx = (gx & 1) ? 0.5f : 0.f, fy = (gy & 1) ? 0.5f : 0.f;
+                const float2 a = fsrc[(size_t)cy * pc + cx], b = fsrc[(size_t)cy * pc + cx1];
+                const float2 c = fsrc[(size_t)cy1 * pc + cx], d = fsrc[(size_t)cy1 * pc + cx1];
+                ddx[j] = 2.f * ((1.f - fy) * ((1.f - fx) * a.x + fx * b.x) + fy * ((1.f - fx) * c.x + fx * d.x));
+                ddy[j] = 2.f * ((1.f - fy) * ((1.f - fx) * a.y + fx * b.y) + fy * ((1.f - fx) * c.y + fx * d.y));
             }
         }
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kUpdRows; j++) {
+            const int gy = y0 + j;
+            if (gy >= h) continue;
+            const float dx = ddx[j], dy = ddy[j];
+            // Position x + d~ as integer + fraction (full-precision
+            // fraction), clamped to the image.
+            const float flx = floorf(dx), fly = floorf(dy);
+            int ix = gx + (int)flx, iy = gy + (int)fly;
+            float fx = dx - flx, fy = dy - fly;
+            if (ix < 0) { ix = 0; fx = 0.f; } else if (ix >= w - 1) { ix = w - 1; fx = 0.f; }
+            if (iy < 0) { iy = 0; fy = 0.f; } else if (iy >= h - 1) { iy = h - 1; fy = 0.f; }
+            const int ix1 = min(ix + 1, w - 1), iy1 = min(iy + 1, h - 1);
+            const size_t r0 = (size_t)iy * p, r1 = (size_t)iy1 * p, o = (size_t)gy * p + gx;
+            const float4 qa = ST::f4(ST::ld4(q2 + r0 + ix)), qb = ST::f4(ST::ld4(q2 + r0 + ix1));
+            const float4 qc = ST::f4(ST::ld4(q2 + r1 + ix)), qd = ST::f4(ST::ld4(q2 + r1 + ix1));
+            const float ba = ST::ld(b2p + r0 + ix), bb = ST::ld(b2p + r0 + ix1);
+            const float bc = ST::ld(b2p + r1 + ix), bdd = ST::ld(b2p + r1 + ix1);
+            const float4 qs = ST::f4(ST::ld4(q1 + o));
+            const float b2a = ST::ld(b1p + o);
+            const float gx0 = 1.f - fx, gy0 = 1.f - fy;
+            const float A11b = gy0 * (gx0 * qa.x + fx * qb.x) + fy * (gx0 * qc.x + fx * qd.x);
+            const float A12b = gy0 * (gx0 * qa.y + fx * qb.y) + fy * (gx0 * qc.y + fx * qd.y);
+            const float A22b = gy0 * (gx0 * qa.z + fx * qb.z) + fy * (gx0 * qc.z + fx * qd.z);
+            const float b1b = gy0 * (gx0 * qa.w + fx * qb.w) + fy * (gx0 * qc.w + fx * qd.w);
+            const float b2b = gy0 * (gx0 * ba + fx * bb) + fy * (gx0 * bc + fx * bdd);
+            const float a11 = 0.5f * (qs.x + A11b), a12 = 0.5f * (qs.y + A12b), a22 = 0.5f * (qs.z + A22b);
+            const float db1 = -0.5f * (b1b - qs.w) + (a11 * dx + a12 * dy);
+            const float db2 = -0.5f * (b2b - b2a) + (a12 * dx + a22 * dy);
+            ST::st(gh + 0 * plane + o, a11 * a11 + a12 * a12);
+            ST::st(gh + 1 * plane + o, a11 * a12 + a12 * a22);
+            ST::st(gh + 2 * plane + o, a12 * a12 + a22 * a22);
+            ST::st(gh + 3 * plane + o, a11 * db1 + a12 * db2);
+            ST::st(gh + 4 * plane + o, a12 * db1 + a22 * db2);
+        }
+    }
+}
 
-        // ---- phase 2: vertical window sums, in place (a column is private to its item)
+// ---------------------------------------------------------------- window
+// Box means of G and h over (2r+1)^2 (clipped to the image) and the 2x2
+// solve.  One TMA copy brings the five planes of a kWinTW x kWinTH tile
+// plus its r-pixel apron into shared memory (elements outside the image
+// arrive as zeros, which is exactly the clipped sum); every column is then
+// summed over 2r+1 rows (in place, or into a float buffer for half
+// storage), and 8 adjacent outputs of a row are summed over 2r+1 columns
+// for all five fields and solved.
+template <typename T, int R>
+struct WinGeom {
+    static constexpr int EPC = 16 / sizeof(T);                         // elements per 16 bytes
+    static constexpr int XO = (R + EPC - 1) / EPC * EPC;               // box starts XO left of the tile
+    static constexpr int BW = (kWinTW + XO + R + EPC - 1) / EPC * EPC; // box width (elements)
+    static constexpr int EH = kWinTH + 2 * R;
+    static constexpr int EW = kWinTW + 2 * R;
+    static constexpr size_t box_bytes = (size_t)5 * EH * BW * sizeof(T);
+    // float sums buffer (half storage only)
+    static constexpr size_t sum_bytes = sizeof(T) == 4 ? 0 : (size_t)5 * kWinTH * EW * sizeof(float);
+    static constexpr size_t smem = 128 + box_bytes + sum_bytes;
+};
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256, 3) k_window(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int dst)
+{
+    using G = WinGeom<T, R>;
+    constexpr int TW = kWinTW, TH = kWinTH, EW = G::EW, EH = G::EH, BW = G::BW, WN = 2 * R + 1;
+    constexpr int SEG = 8;
+    constexpr bool kF32 = sizeof(T) == 4;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+    T *box = reinterpret_cast<T *>(smem_raw + 128);                              // [5][EH][BW]
+    float *sums = kF32 ? reinterpret_cast<float *>(box) : reinterpret_cast<float *>(smem_raw + 128 + G::box_bytes);
+    // float view of the column sums: [5][rows][SW]
+    constexpr int SW = kF32 ? BW : EW;
+    constexpr int SR = kF32 ? EH : TH;
+    constexpr int SOFF = kF32 ? (G::XO - R) : 0;  // column of ext col 0 in the sums buffer
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const int nfr = bd->nframes;
+    const int *off = bd->win_off[level];
+    const int total = __ldg(off + nfr);
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int fi = find_frame(off, nfr, t);
+        const FrameDesc &F = bd->f[fi];
+        const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
+        const int ntx = (w + TW - 1) / TW;
+        const int lt = t - __ldg(off + fi);
+        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
+        if (threadIdx.x == 0) {
+            const CUtensorMap *map = &F.gh_map[level];
+            tensormap_acquire(map);
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, (uint32_t)G::box_bytes);
+            tma_load_3d(box, map, x0 - G::XO, y0 - R, 0, bar);
+        }
+        const bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {
+            // Give up: flag the batch, give the copy one more bounded wait, leave.
+            if (threadIdx.x == 0) atomicExch(bd->err, kErrTmaTimeout);
+            mbar_wait(bar, phase);
+            return;
+        }
+        phase ^= 1u;
+
+        // vertical sums of every ext column (rows [0, TH) of the sums view)
         for (int it = threadIdx.x; it < 5 * EW; it += blockDim.x) {
             const int k = it / EW, ex = it - k * EW;
-            float *col = gh + k * EH * EW + ex;
-            float v[EH], s[TH];
+            const T *col = box + k * EH * BW + ex + (G::XO - R);
+            float v[EH], sm[TH];
 #pragma unroll
-            for (int j = 0; j < EH; j++) v[j] = col[j * EW];
-            box_sums<EH, WN>(v, s);
+            for (int j = 0; j < EH; j++) v[j] = (float)col[j * BW];
+            box_sums<EH, WN>(v, sm);
+            float *dcol = sums + k * SR * SW + ex + SOFF;
 #pragma unroll
-            for (int j = 0; j < TH; j++) col[j * EW] = s[j];
+            for (int j = 0; j < TH; j++) dcol[j * SW] = sm[j];
         }
         __syncthreads();
 
-        // ---- phase 3: horizontal window sums of 8 outputs, then the solve
         {
             const int r = threadIdx.x / (TW / SEG), sg = threadIdx.x - r * (TW / SEG);
             const int gy = y0 + r, gxs = x0 + sg * SEG;
@@ -195,7 +248,7 @@ __global__ void __launch_bounds__(256, 3)
                 float acc[5][SEG];
 #pragma unroll
                 for (int k = 0; k < 5; k++) {
-                    const float *row = gh + k * EH * EW + r * EW + sg * SEG;
+                    const float *row = sums + k * SR * SW + r * SW + SOFF + sg * SEG;
                     float v[SEG + 2 * R], sm[SEG];
 #pragma unroll
                     for (int j = 0; j < SEG + 2 * R; j++) v[j] = row[j];
@@ -224,36 +277,52 @@ __global__ void __launch_bounds__(256, 3)
 }
 
 template <typename T, int R>
-static void launch_flow_t(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, int dst, int grid,
-                          cudaStream_t s)
+static void launch_window_t(const BatchDesc *bd, const MethodConsts &mc, int level, int dst, int grid, cudaStream_t s)
 {
-    constexpr int EW = kFlowTW + 2 * R, EH = kFlowTH + 2 * R;
-    const size_t sm = sizeof(float) * (5 * EH * EW);
-    // The dynamic shared-memory limit was raised by occ_flow_t at set-up.
-    k_flow<T, R><<<grid, 256, sm, s>>>(bd, mc, level, iter, src, dst);
+    // The dynamic shared-memory limit was raised by occ_window_t at set-up.
+    k_window<T, R><<<grid, 256, WinGeom<T, R>::smem, s>>>(bd, mc, level, dst);
 }
 
 template <typename T, int R>
-static int occ_flow_t()
+static int occ_window_t()
 {
-    constexpr int EW = kFlowTW + 2 * R, EH = kFlowTH + 2 * R;
-    const size_t sm = sizeof(float) * (5 * EH * EW);
-    cudaFuncSetAttribute(k_flow<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = WinGeom<T, R>::smem;
+    cudaFuncSetAttribute(k_window<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_flow<T, R>, 256, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_window<T, R>, 256, sm);
     return b;
 }
 
 #define FLOWROI_FLOW_RADII(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
-void launch_flow(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, int dst, bool half,
-                 int grid, cudaStream_t s)
+void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int grid,
+                   cudaStream_t s)
+{
+    if (half) k_update<__half><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+    else k_update<float><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+}
+
+int window_box(bool half, int win_r, int *xo, int *bw, int *eh)
+{
+    switch (win_r) {
+#define CASE(RR)                                                                                              \
+    case RR:                                                                                                  \
+        if (half) { *xo = WinGeom<__half, RR>::XO; *bw = WinGeom<__half, RR>::BW; *eh = WinGeom<__half, RR>::EH; } \
+        else { *xo = WinGeom<float, RR>::XO; *bw = WinGeom<float, RR>::BW; *eh = WinGeom<float, RR>::EH; }       \
+        return 0;
+        FLOWROI_FLOW_RADII(CASE)
+#undef CASE
+    default: return -1;
+    }
+}
+
+void launch_window(const BatchDesc *bd, const MethodConsts &mc, int level, int dst, bool half, int grid, cudaStream_t s)
 {
     switch (mc.win_r) {
-#define CASE(RR)                                                                           \
-    case RR:                                                                               \
-        if (half) launch_flow_t<__half, RR>(bd, mc, level, iter, src, dst, grid, s);       \
-        else launch_flow_t<float, RR>(bd, mc, level, iter, src, dst, grid, s);             \
+#define CASE(RR)                                                                 \
+    case RR:                                                                     \
+        if (half) launch_window_t<__half, RR>(bd, mc, level, dst, grid, s);      \
+        else launch_window_t<float, RR>(bd, mc, level, dst, grid, s);            \
         break;
         FLOWROI_FLOW_RADII(CASE)
 #undef CASE
@@ -261,11 +330,19 @@ void launch_flow(const BatchDesc *bd, const MethodConsts &mc, int level, int ite
     }
 }
 
-int occupancy_flow(bool half, int win_r)
+int occupancy_update(bool half)
+{
+    int b = 0;
+    if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half>, 256, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float>, 256, 0);
+    return b;
+}
+
+int occupancy_window(bool half, int win_r)
 {
     switch (win_r) {
 #define CASE(RR) \
-    case RR: return half ? occ_flow_t<__half, RR>() : occ_flow_t<float, RR>();
+    case RR: return half ? occ_window_t<__half, RR>() : occ_window_t<float, RR>();
         FLOWROI_FLOW_RADII(CASE)
 #undef CASE
     default: return 0;

@@ -10,8 +10,9 @@
 namespace flowroi {
 
 void launch_expand(const BatchDesc *bd, const MethodConsts &mc, int level, bool half, int grid, cudaStream_t s);
-void launch_flow(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, int dst, bool half,
-                 int grid, cudaStream_t s);
+void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int grid,
+                   cudaStream_t s);
+void launch_window(const BatchDesc *bd, const MethodConsts &mc, int level, int dst, bool half, int grid, cudaStream_t s);
 void launch_frame_init(const BatchDesc *bd, int grid, cudaStream_t s);
 void launch_saliency(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s);
@@ -22,7 +23,10 @@ void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid
 // Resident blocks per SM (also sets any shared-memory attribute the kernel
 // needs; call once per device before the first launch).
 int occupancy_expand(bool half, int n_half);
-int occupancy_flow(bool half, int win_r);
+int occupancy_update(bool half);
+// TMA box of the window kernel: it starts xo elements left of a tile, bw wide, eh rows.
+int window_box(bool half, int win_r, int *xo, int *bw, int *eh);
+int occupancy_window(bool half, int win_r);
 int occupancy_mask_kernels();
 int occupancy_dwt(int wavelet);
 

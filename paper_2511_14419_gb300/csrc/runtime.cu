@@ -38,9 +38,12 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/flowroi.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "tma.cuh"
 
 using namespace flowroi;
 
@@ -89,6 +92,7 @@ struct Entry {
 };
 
 struct Stream {
+    CUtensorMap gh_map[kMaxLevels];
     int64_t id = 0;
     int W = 0, H = 0, bpp = 0, bit_depth = 0;
     size_t bytes = 0;
@@ -103,6 +107,7 @@ struct Stream {
     void *fq[2][kMaxLevels] = {};
     void *fb[2][kMaxLevels] = {};
     void *pyr[kMaxLevels] = {};
+    void *gh[kMaxLevels] = {};
     float2 *flow[2] = {};
     float *S = nullptr;
     unsigned *red = nullptr;
@@ -134,7 +139,7 @@ struct flowroi_ctx {
     cudaGraphExec_t graph[kDesc] = {};
     int graph_launches = 0;
     int desc_next = 0;
-    int grid_exp = 0, grid_flow = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0;
+    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0;
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -146,6 +151,7 @@ struct flowroi_ctx {
     int64_t frames_done = 0;                              // guarded by cmu
     std::atomic<int64_t> batches{0}, refused{0}, launches{0};
     std::vector<double> lat_ms;                           // guarded by cmu
+    unsigned *err_host = nullptr, *err_dev = nullptr;     // kernel error word (mapped pinned memory)
     // per-kernel event timing (guarded by mu)
     bool profiling = false;
     struct ProfRec { int kid, level, iter; cudaEvent_t a, b; };
@@ -273,6 +279,7 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
             s->fb[k][l] = take((size_t)s->lp[l] * s->lh[l] * esz);
         }
     for (int l = 1; l < L; l++) s->pyr[l] = take((size_t)s->lp[l] * s->lh[l] * esz);
+    for (int l = 0; l < L; l++) s->gh[l] = take((size_t)s->lp[l] * s->lh[l] * 5 * esz);
     for (int k = 0; k < 2; k++) s->flow[k] = reinterpret_cast<float2 *>(take((size_t)s->lp[0] * s->H * sizeof(float2)));
     s->S = reinterpret_cast<float *>(take((size_t)s->lp[0] * s->H * sizeof(float)));
     s->red = reinterpret_cast<unsigned *>(take(kRedWords * sizeof(unsigned)));
@@ -296,9 +303,25 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
     return align_up(off, 256);
 }
 
+// TMA maps of a stream's G, h planes (one 3-D map per pyramid level).
+bool encode_stream_maps(flowroi_ctx *c, Stream *s)
+{
+    int xo = 0, bw = 0, eh = 0;
+    if (window_box(c->half, c->cfg.win_r, &xo, &bw, &eh) != 0) return false;
+    const size_t esz = c->half ? 2 : 4;
+    for (int l = 0; l < c->cfg.pyr_levels; l++) {
+        const uint64_t dims[3] = {(uint64_t)s->lw[l], (uint64_t)s->lh[l], 5};
+        const uint64_t strides[2] = {(uint64_t)s->lp[l] * esz, (uint64_t)s->lp[l] * s->lh[l] * esz};
+        const uint32_t box[3] = {(uint32_t)bw, (uint32_t)eh, 5};
+        if (!tma_encode(&s->gh_map[l], c->half, 3, s->gh[l], dims, strides, box)) return false;
+    }
+    return true;
+}
+
 void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
 {
     std::memset(&F, 0, sizeof F);
+    for (int l = 0; l < c->cfg.pyr_levels; l++) F.gh_map[l] = s->gh_map[l];
     F.W = s->W;
     F.H = s->H;
     F.bpp = s->bpp;
@@ -319,6 +342,7 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
         F.fb_cur[l] = s->fb[cur][l];
         F.fq_prev[l] = s->fq[prv][l];
         F.fb_prev[l] = s->fb[prv][l];
+        F.gh[l] = s->gh[l];
     }
     F.flow[0] = s->flow[0];
     F.flow[1] = s->flow[1];
@@ -343,14 +367,15 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
     const int n = bd.nframes;
     const int L = c->cfg.pyr_levels, D = c->cfg.dwt_levels;
     for (int l = 0; l < kMaxLevels; l++) {
-        bd.exp_off[l][0] = bd.flow_off[l][0] = bd.dwt_off[l][0] = 0;
+        bd.exp_off[l][0] = bd.flow_off[l][0] = bd.win_off[l][0] = bd.dwt_off[l][0] = 0;
     }
     bd.sal_off[0] = bd.mor_off[0] = bd.frm_off[0] = 0;
     for (int i = 0; i < n; i++) {
         const FrameDesc &F = bd.f[i];
         for (int l = 0; l < L; l++) {
             bd.exp_off[l][i + 1] = bd.exp_off[l][i] + tiles(F.lw[l], F.lh[l], kExpTW, kExpTH);
-            bd.flow_off[l][i + 1] = bd.flow_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kFlowTW, kFlowTH) : 0);
+            bd.flow_off[l][i + 1] = bd.flow_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kUpdTW, kUpdRows) : 0);
+            bd.win_off[l][i + 1] = bd.win_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kWinTW, kWinTH) : 0);
         }
         for (int l = 1; l <= D; l++)
             bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH);
@@ -360,8 +385,9 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
     }
 }
 
-const char *const kKernelNames[] = {"frame_init", "expand", "flow", "saliency", "select_find", "select_pass", "morph", "dwt"};
-enum KernelId { K_INIT = 0, K_EXPAND, K_FLOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT };
+const char *const kKernelNames[] = {"frame_init", "expand", "update", "window", "saliency", "select_find", "select_pass",
+                                    "morph", "dwt"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT };
 
 // Runs one launch, bracketed by an event pair when profiling.
 template <class Fn>
@@ -404,10 +430,13 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
         for (int l = L - 1; l >= 0; l--)
             for (int it = 0; it < I; it++, k++) {
                 const int dst = k & 1;
-                timed(c, st, prof, K_FLOW, l, it, [&] {
-                    launch_flow(dd, mc, l, it, dst ^ 1, dst, c->half, g(hd->flow_off[l][n], c->grid_flow), st);
+                timed(c, st, prof, K_UPDATE, l, it, [&] {
+                    launch_update(dd, mc, l, it, dst ^ 1, c->half, g(hd->flow_off[l][n], c->grid_upd), st);
                 });
-                cnt++;
+                timed(c, st, prof, K_WINDOW, l, it, [&] {
+                    launch_window(dd, mc, l, dst, c->half, g(hd->win_off[l][n], c->grid_win), st);
+                });
+                cnt += 2;
             }
         timed(c, st, prof, K_SAL, -1, -1, [&] { launch_saliency(dd, mc, g(hd->sal_off[n], c->grid_mask), st); });
         for (int pass = 0; pass < 3; pass++) {
@@ -432,6 +461,11 @@ void CUDART_CB on_batch_done(void *p)
     BatchRec *r = static_cast<BatchRec *>(p);
     flowroi_ctx *c = r->ctx;
     const double t = now_ms();
+    if (c->err_host && *(volatile unsigned *)c->err_host) {
+        // A kernel gave up a bounded wait: results of this batch are not valid.
+        c->poison_msg = "a kernel's bounded wait for a TMA copy ran out";
+        c->poisoned = true;
+    }
     {
         std::lock_guard<std::mutex> lk(c->cmu);
         for (Entry *e : r->entries) {
@@ -469,6 +503,7 @@ int step_locked(flowroi_ctx *c)
     CK(c, cudaEventSynchronize(c->desc_ev[k]));
     BatchDesc &hd = *c->desc_host[k];
     hd.nframes = (int)sel.size();
+    hd.err = c->err_dev;
     const int nflow = c->cfg.pyr_levels * c->cfg.iters;
     hd.final_flow_buf = (nflow - 1) & 1;
     for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].first, sel[i].second, hd.f[i]);
@@ -666,6 +701,44 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
 
 }  // namespace
 
+// ========================================================= TMA encode ==
+namespace flowroi {
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+bool tma_available()
+{
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return g_encode != nullptr;
+}
+
+bool tma_encode(CUtensorMap *map, bool half, int rank, void *base, const uint64_t *dims, const uint64_t *strides_bytes,
+                const uint32_t *box)
+{
+    if (!tma_available() || rank < 1 || rank > 5) return false;
+    cuuint64_t d[5], st[4];
+    cuuint32_t b[5], es[5];
+    for (int i = 0; i < rank; i++) {
+        d[i] = dims[i];
+        b[i] = box[i];
+        es[i] = 1;
+    }
+    for (int i = 0; i + 1 < rank; i++) st[i] = strides_bytes[i];
+    const CUresult r = g_encode(map, half ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank,
+                                base, d, st, b, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace flowroi
+
 // ================================================================ C ABI ==
 extern "C" {
 
@@ -754,13 +827,19 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
         CK(nullptr, cudaEventCreateWithFlags(&c->desc_ev[k], cudaEventDisableTiming));
         std::memset(c->desc_host[k], 0, sizeof(BatchDesc));
     }
+    CK(nullptr, cudaHostAlloc(reinterpret_cast<void **>(&c->err_host), sizeof(unsigned), cudaHostAllocMapped));
+    *c->err_host = 0u;
+    CK(nullptr, cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->err_dev), c->err_host, 0));
+    if (!tma_available()) return fail(FLOWROI_EDEVICE, "cuTensorMapEncodeTiled is not available from the driver");
     const int oe = occupancy_expand(c->half, cfg->poly_n_half);
-    const int of = occupancy_flow(c->half, cfg->win_r);
+    const int ou = occupancy_update(c->half);
+    const int ow = occupancy_window(c->half, cfg->win_r);
     const int om = occupancy_mask_kernels();
     const int od = occupancy_dwt(cfg->wavelet);
     CK(nullptr, cudaGetLastError());
     c->grid_exp = std::max(1, oe) * c->num_sms;
-    c->grid_flow = std::max(1, of) * c->num_sms;
+    c->grid_upd = std::max(1, ou) * c->num_sms;
+    c->grid_win = std::max(1, ow) * c->num_sms;
     c->grid_mask = std::max(1, om) * c->num_sms;
     c->grid_dwt = std::max(1, od) * c->num_sms;
     c->grid_frames = kMaxBatch;
@@ -820,6 +899,10 @@ int flowroi_submit_frame(flowroi_ctx *c, int64_t stream_id, const flowroi_frame 
             ns->block = static_cast<char *>(blk);
             ns->bytes = bytes;
             plan_stream(c, ns.get(), ns->block);
+            if (!encode_stream_maps(c, ns.get())) {
+                cudaFreeAsync(blk, c->s_copy);
+                return fail(FLOWROI_EDEVICE, "TMA tensor map encoding failed");
+            }
             for (auto &en : ns->ring) CK(c, cudaEventCreateWithFlags(&en->uploaded, cudaEventDisableTiming));
             c->admitted += bytes;
             s = ns.get();
@@ -1031,6 +1114,7 @@ void flowroi_destroy(flowroi_ctx *c)
         if (c->desc_dev[k]) cudaFree(c->desc_dev[k]);
         if (c->desc_ev[k]) cudaEventDestroy(c->desc_ev[k]);
     }
+    if (c->err_host) cudaFreeHost(c->err_host);
     cudaStreamDestroy(c->s_comp);
     cudaStreamDestroy(c->s_copy);
     cudaStreamDestroy(c->s_d2h);
