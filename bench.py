@@ -64,9 +64,11 @@ WORKLOADS = {
 #           fp16 10+8 = 18 B.
 KERNEL_BYTES = {("update", 32): (62.0, 68.0), ("update", 16): (32.0, 38.0),
                 ("window", 32): (28.0, 28.0), ("window", 16): (18.0, 18.0)}
-# DRAM bytes per level-0 pixel per launch measured by ncu on the current
-# kernels (None until measured for this build).
-KERNEL_TRAFFIC_PER_PX = {}
+# DRAM bytes (read + write) per level-0 pixel of one launch, measured by ncu
+# on the current kernels (profiles/k_update_level0_4x2048.md,
+# profiles/k_window_level0_4x2048.md: 4 frames, traffic proportional to
+# pixels); absent = not measured for the current build.
+KERNEL_TRAFFIC_PER_PX = {("update", 32): 66.5, ("window", 32): 26.6}
 
 
 def log(*a):
@@ -158,6 +160,23 @@ def make_frames(wl, device):
                                    device=device))
     torch.cuda.synchronize()
     return frames
+
+
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """Max of a per-rank float over all ranks (host reduction only)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank: int, ws: int, t_max: float) -> float:
+    """Whole-job frames/s: every rank processed frames_per_rank frames; the
+    job took as long as its slowest rank."""
+    return frames_per_rank * ws / t_max
 
 
 def frame_index(t, n):
@@ -393,32 +412,27 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    dev_name = f"cuda:{local}" if ws > 1 and dist.get_backend() == "nccl" else "cpu"
 
     barrier()
     dev = run_device(F, wl, frames, args.steps, args.warmup, profile_steps=min(args.steps, 10), sampler_device=local)
     barrier()
-    t_max = max_over_ranks(dev["time_s"])
-    value = dev["frames"] * ws / t_max
+    t_max = max_over_ranks(dev["time_s"], ws, dev_name)
+    value = job_throughput(dev["frames"], ws, t_max)
 
     plain = None
     if not args.no_plain:
         ps = max(3, min(args.steps, 20))
         pr = run_device(F, wl, frames, ps, args.warmup, plain=True)
         barrier()
-        plain = pr["frames"] * ws / max_over_ranks(pr["time_s"])
+        plain = job_throughput(pr["frames"], ws, max_over_ranks(pr["time_s"], ws, dev_name))
 
     e2e = None
     if not args.no_e2e:
         es = max(3, min(args.steps, 20))
         er = run_e2e(F, wl, frames, es, args.warmup)
         barrier()
-        e2e = {"value": er["frames"] * ws / max_over_ranks(er["time_s"]), "unit": "frames/s",
+        e2e = {"value": job_throughput(er["frames"], ws, max_over_ranks(er["time_s"], ws, dev_name)), "unit": "frames/s",
                "h2d_bytes_per_step": er["h2d"], "d2h_bytes_per_step": er["d2h"]}
         latency = {"p50_ms": er["stats"]["lat_p50_ms"], "p99_ms": er["stats"]["lat_p99_ms"],
                    "source": "e2e run, submit -> result ready"}

@@ -125,7 +125,7 @@ __device__ __forceinline__ void mask_rule(const uint8_t (&m)[N], int e, uint8_t 
 }
 
 template <int WAV>
-__global__ void __launch_bounds__(256) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
+__global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
     using V = typename std::conditional<WAV == 97, float, int>::type;
     constexpr int TW = kDwtTW, TH = kDwtTH, HALO = kDwtHalo;
@@ -149,60 +149,87 @@ __global__ void __launch_bounds__(256) k_dwt(const BatchDesc *__restrict__ bd, M
         const int lt = t - __ldg(off + fi);
         const int bx0 = (lt % ntx) * TW, by0 = (lt / ntx) * TH;
         const int ix0 = 2 * bx0 - HALO, iy0 = 2 * by0 - HALO;
+        // Descriptor fields in registers (the output stores below could
+        // otherwise force their reloads).
         const V *llin = static_cast<const V *>(F.ll[level % 2]);
         const uint8_t *mlin = F.llm[level % 2];
+        const uint8_t *fraw = static_cast<const uint8_t *>(F.raw);
+        const uint8_t *fmask = F.mask;
+        const int raw_pitch = F.raw_pitch, bpp = F.bpp, dc_off = F.dc_off;
+        int32_t *const coeffs = F.coeffs;
+        float *const dbg_yf = F.dbg_yf;
+        V *const llout = static_cast<V *>(F.ll[(level - 1) % 2]);
+        uint8_t *const llmout = F.llm[(level - 1) % 2];
 
         // Load: samples with symmetric extension, mask clipped (0 outside).
-        // Two adjacent columns per thread (ix0 is even, so an in-range pair
-        // is one aligned 2-sample / 2-byte load).
-        const bool xin = ix0 >= 0 && ix0 + EW <= iw;
-        for (int r = threadIdx.x >> 5; r < EH; r += blockDim.x >> 5) {
-            const int gy = iy0 + r, my = mirror(gy, ih);
-            const bool rin = gy >= 0 && gy < ih;
-            const uint8_t *mrow = level == 1 ? F.mask + (size_t)gy * W : mlin + (size_t)gy * iw;
-            for (int c = 2 * (threadIdx.x & 31); c < EW; c += 64) {
-                const int gx = ix0 + c;
-                V v0, v1;
-                if (level == 1) {
-                    const uint8_t *row = static_cast<const uint8_t *>(F.raw) + (size_t)my * F.raw_pitch;
-                    int r0, r1;
-                    if (xin && F.bpp == 2) {
-                        const unsigned pr = __ldg(reinterpret_cast<const unsigned *>(row) + (gx >> 1));
-                        r0 = (int)(pr & 0xffffu);
-                        r1 = (int)(pr >> 16);
+        // Two adjacent columns per item (ix0 is even, so an in-range pair is
+        // one aligned 2-sample / 2-byte load); a thread issues all of its
+        // items' loads before any shared-memory store.
+        {
+            const bool xin = ix0 >= 0 && ix0 + EW <= iw;
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            constexpr int NR = (EH + 7) / 8, NP = (EW / 2 + 31) / 32;
+            V v[NR][NP][2];
+            uint8_t mm[NR][NP][2];
+#pragma unroll
+            for (int i = 0; i < NR; i++) {
+                const int r = warp + 8 * i;
+                const int gy = iy0 + r, my = mirror(gy, ih);
+                const bool rin = gy >= 0 && gy < ih;
+                const uint8_t *mrow = level == 1 ? fmask + (size_t)gy * W : mlin + (size_t)gy * iw;
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    const int c = 2 * (lane + 32 * j), gx = ix0 + c;
+                    v[i][j][0] = v[i][j][1] = (V)0;
+                    mm[i][j][0] = mm[i][j][1] = 0;
+                    if (r >= EH || c >= EW) continue;
+                    if (level == 1) {
+                        const uint8_t *row = fraw + (size_t)my * raw_pitch;
+                        int r0, r1;
+                        if (xin && bpp == 2) {
+                            const unsigned pr = __ldg(reinterpret_cast<const unsigned *>(row) + (gx >> 1));
+                            r0 = (int)(pr & 0xffffu);
+                            r1 = (int)(pr >> 16);
+                        } else {
+                            const int m0 = mirror(gx, iw), m1 = mirror(gx + 1, iw);
+                            r0 = bpp == 1 ? (int)__ldg(row + m0) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m0);
+                            r1 = bpp == 1 ? (int)__ldg(row + m1) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m1);
+                        }
+                        v[i][j][0] = (V)(r0 - dc_off);
+                        v[i][j][1] = (V)(r1 - dc_off);
                     } else {
-                        const int m0 = mirror(gx, iw), m1 = mirror(gx + 1, iw);
-                        r0 = F.bpp == 1 ? (int)__ldg(row + m0) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m0);
-                        r1 = F.bpp == 1 ? (int)__ldg(row + m1) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m1);
+                        const V *row = llin + (size_t)my * iw;
+                        if (xin) {
+                            v[i][j][0] = __ldg(row + gx);
+                            v[i][j][1] = __ldg(row + gx + 1);
+                        } else {
+                            v[i][j][0] = __ldg(row + mirror(gx, iw));
+                            v[i][j][1] = __ldg(row + mirror(gx + 1, iw));
+                        }
                     }
-                    v0 = (V)(r0 - F.dc_off);
-                    v1 = (V)(r1 - F.dc_off);
-                } else {
-                    const V *row = llin + (size_t)my * iw;
-                    if (xin) {
-                        v0 = row[gx];
-                        v1 = row[gx + 1];
-                    } else {
-                        v0 = row[mirror(gx, iw)];
-                        v1 = row[mirror(gx + 1, iw)];
+                    if (rin) {
+                        if (xin) {
+                            const unsigned short m2 = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
+                            mm[i][j][0] = (uint8_t)(m2 & 0xff);
+                            mm[i][j][1] = (uint8_t)(m2 >> 8);
+                        } else {
+                            if (gx >= 0 && gx < iw) mm[i][j][0] = __ldg(mrow + gx);
+                            if (gx + 1 >= 0 && gx + 1 < iw) mm[i][j][1] = __ldg(mrow + gx + 1);
+                        }
                     }
                 }
-                s_x[r][c] = v0;
-                s_x[r][c + 1] = v1;
-                uint8_t m0 = 0, m1 = 0;
-                if (rin) {
-                    if (xin) {
-                        const unsigned short mm = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
-                        m0 = (uint8_t)(mm & 0xff);
-                        m1 = (uint8_t)(mm >> 8);
-                    } else {
-                        if (gx >= 0 && gx < iw) m0 = mrow[gx];
-                        if (gx + 1 >= 0 && gx + 1 < iw) m1 = mrow[gx + 1];
-                    }
-                }
-                s_m[r][c] = m0;
-                s_m[r][c + 1] = m1;
             }
+#pragma unroll
+            for (int i = 0; i < NR; i++)
+#pragma unroll
+                for (int j = 0; j < NP; j++) {
+                    const int r = warp + 8 * i, c = 2 * (lane + 32 * j);
+                    if (r >= EH || c >= EW) continue;
+                    s_x[r][c] = v[i][j][0];
+                    s_x[r][c + 1] = v[i][j][1];
+                    s_m[r][c] = mm[i][j][0];
+                    s_m[r][c + 1] = mm[i][j][1];
+                }
         }
         __syncthreads();
 
@@ -260,18 +287,17 @@ __global__ void __launch_bounds__(256) k_dwt(const BatchDesc *__restrict__ bd, M
                     // high horizontal band (HL or HH)
                     const size_t ph = (size_t)ylo * W + bw + gi;
                     int32_t q = quantise(yhi_v, d_hi, WAV);
-                    F.coeffs[ph] = mhi ? roi_up(q, mc.shift) : q;
-                    if constexpr (WAV == 97) { if (F.dbg_yf) F.dbg_yf[ph] = yhi_v; }
+                    coeffs[ph] = mhi ? roi_up(q, mc.shift) : q;
+                    if constexpr (WAV == 97) { if (dbg_yf) dbg_yf[ph] = yhi_v; }
                     // low horizontal band (LL or LH)
                     if (vhigh || last) {
                         const size_t pl = (size_t)ylo * W + gi;
                         q = quantise(ylo_v, d_lo, WAV);
-                        F.coeffs[pl] = mlo ? roi_up(q, mc.shift) : q;
-                        if constexpr (WAV == 97) { if (F.dbg_yf) F.dbg_yf[pl] = ylo_v; }
+                        coeffs[pl] = mlo ? roi_up(q, mc.shift) : q;
+                        if constexpr (WAV == 97) { if (dbg_yf) dbg_yf[pl] = ylo_v; }
                     } else {
-                        V *llout = static_cast<V *>(F.ll[(level - 1) % 2]);
                         llout[(size_t)gj * bw + gi] = ylo_v;
-                        F.llm[(level - 1) % 2][(size_t)gj * bw + gi] = mlo;
+                        llmout[(size_t)gj * bw + gi] = mlo;
                     }
                 }
             }

@@ -26,20 +26,33 @@ namespace flowroi {
 
 namespace {
 
+// Source of one level, with the descriptor fields it needs held in
+// registers (read once per tile).
 template <typename T>
-__device__ __forceinline__ float read_level(const FrameDesc &F, int level, int x, int y)
-{
-    if (level == 0) {
-        if (F.bpp == 1) {
-            const uint8_t *r = static_cast<const uint8_t *>(F.raw) + (size_t)y * F.raw_pitch;
-            return (float)__ldg(r + x) * F.unit_scale;
-        }
-        const uint16_t *r = reinterpret_cast<const uint16_t *>(static_cast<const uint8_t *>(F.raw) + (size_t)y * F.raw_pitch);
-        return (float)__ldg(r + x) * F.unit_scale;
+struct LevelSrc {
+    const uint8_t *raw;  // level 0: raw samples
+    const T *img;        // level > 0: pyramid image
+    int pitch;           // raw row pitch in bytes, or image pitch in elements
+    int bpp;
+    float scale;
+    __device__ __forceinline__ LevelSrc(const FrameDesc &F, int level)
+    {
+        raw = static_cast<const uint8_t *>(F.raw);
+        img = static_cast<const T *>(F.pyr[level]);
+        bpp = F.bpp;
+        scale = F.unit_scale;
+        pitch = level == 0 ? F.raw_pitch : F.lp[level];
+        if (level > 0) raw = nullptr;
     }
-    const T *p = static_cast<const T *>(F.pyr[level]);
-    return Store<T>::ld(p + (size_t)y * F.lp[level] + x);
-}
+    __device__ __forceinline__ float at(int x, int y) const
+    {
+        if (raw) {
+            if (bpp == 1) return (float)__ldg(raw + (size_t)y * pitch + x) * scale;
+            return (float)__ldg(reinterpret_cast<const uint16_t *>(raw + (size_t)y * pitch) + x) * scale;
+        }
+        return Store<T>::ld(img + (size_t)y * pitch + x);
+    }
+};
 
 }  // namespace
 
@@ -71,11 +84,35 @@ __global__ void __launch_bounds__(256) k_expand(const BatchDesc *__restrict__ bd
         // A per-tile constant is removed before the fit (the fit of a
         // constant is that constant: A and b are unchanged) to keep the
         // single-precision moments small.
-        const float c0 = read_level<T>(F, level, min(x0 + kExpTW / 2, w - 1), min(y0 + kExpTH / 2, h - 1));
-        for (int i = threadIdx.x; i < IH * IW; i += blockDim.x) {
-            const int r = i / IW, c = i - r * IW;
-            const int gy = clampi(y0 - HALO + r, 0, h - 1), gx = clampi(x0 - HALO + c, 0, w - 1);
-            s_in[r][c] = read_level<T>(F, level, gx, gy) - c0;
+        const LevelSrc<T> src(F, level);
+        T4 *fq = static_cast<T4 *>(F.fq_cur[level]);
+        T *fb = static_cast<T *>(F.fb_cur[level]);
+        T *pdst = pyr_next ? static_cast<T *>(F.pyr[level + 1]) : nullptr;
+        const int wn = pyr_next ? F.lw[level + 1] : 0, hn = pyr_next ? F.lh[level + 1] : 0, pn = pyr_next ? F.lp[level + 1] : 0;
+        const float c0 = src.at(min(x0 + kExpTW / 2, w - 1), min(y0 + kExpTH / 2, h - 1));
+        {
+            // All of a thread's loads first (up to 3 rows x 3 columns), then
+            // the shared-memory stores, so the loads are in flight together.
+            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+            float v[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const int r = ty + 8 * i, c = tx + 32 * j;
+                    v[i][j] = 0.f;
+                    if (r < IH && c < IW) {
+                        const int gy = clampi(y0 - HALO + r, 0, h - 1), gx = clampi(x0 - HALO + c, 0, w - 1);
+                        v[i][j] = src.at(gx, gy);
+                    }
+                }
+#pragma unroll
+            for (int i = 0; i < 3; i++)
+#pragma unroll
+                for (int j = 0; j < 3; j++) {
+                    const int r = ty + 8 * i, c = tx + 32 * j;
+                    if (r < IH && c < IW) s_in[r][c] = v[i][j] - c0;
+                }
         }
         __syncthreads();
         for (int i = threadIdx.x; i < RH * kExpTW; i += blockDim.x) {
@@ -101,8 +138,6 @@ __global__ void __launch_bounds__(256) k_expand(const BatchDesc *__restrict__ bd
             }
         }
         __syncthreads();
-        T4 *fq = static_cast<T4 *>(F.fq_cur[level]);
-        T *fb = static_cast<T *>(F.fb_cur[level]);
         for (int i = threadIdx.x; i < kExpTH * kExpTW; i += blockDim.x) {
             const int r = i / kExpTW, c = i - r * kExpTW;
             const int gx = x0 + c, gy = y0 + r;
@@ -127,8 +162,6 @@ __global__ void __launch_bounds__(256) k_expand(const BatchDesc *__restrict__ bd
             ST::st(fb + o, c01 * mc.inv_s0s2);
         }
         if (pyr_next) {
-            T *dst = static_cast<T *>(F.pyr[level + 1]);
-            const int wn = F.lw[level + 1], hn = F.lh[level + 1], pn = F.lp[level + 1];
             for (int i = threadIdx.x; i < (kExpTH / 2) * BW; i += blockDim.x) {
                 const int j = i / BW, k = i - j * BW;
                 const int gx = x0 / 2 + k, gy = y0 / 2 + j;
@@ -136,7 +169,7 @@ __global__ void __launch_bounds__(256) k_expand(const BatchDesc *__restrict__ bd
                 const int r = HALO + 2 * j;
                 const float v = b5[0] * s_blur[r - 2][k] + b5[1] * s_blur[r - 1][k] + b5[2] * s_blur[r][k] +
                                 b5[3] * s_blur[r + 1][k] + b5[4] * s_blur[r + 2][k];
-                ST::st(dst + (size_t)gy * pn + gx, v + c0);
+                ST::st(pdst + (size_t)gy * pn + gx, v + c0);
             }
         }
         __syncthreads();

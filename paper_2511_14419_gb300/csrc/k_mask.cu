@@ -120,14 +120,28 @@ __global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ 
         const int lt = t - __ldg(off + fi);
         const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
         const float2 *fl = F.flow[buf];
+        float *const Sp = F.S;
+        float2 *const dbg_flow = F.dbg_flow;
         const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        for (int r = ty; r < TH + 2; r += 8) {
-            const int gy = clampi(y0 - 1 + r, 0, h - 1);
-            const float2 *row = fl + (size_t)gy * p;
-            for (int c = tx; c < TW + 2; c += 32) {
-                const float2 d = row[clampi(x0 - 1 + c, 0, w - 1)];
-                s_m[r][c] = sqrtf(d.x * d.x + d.y * d.y);
-            }
+        {
+            constexpr int NR = (TH + 2 + 7) / 8, NC = (TW + 2 + 31) / 32;
+            float2 d[NR][NC];
+#pragma unroll
+            for (int i = 0; i < NR; i++)
+#pragma unroll
+                for (int j = 0; j < NC; j++) {
+                    const int r = ty + 8 * i, c = tx + 32 * j;
+                    d[i][j] = make_float2(0.f, 0.f);
+                    if (r < TH + 2 && c < TW + 2)
+                        d[i][j] = fl[(size_t)clampi(y0 - 1 + r, 0, h - 1) * p + clampi(x0 - 1 + c, 0, w - 1)];
+                }
+#pragma unroll
+            for (int i = 0; i < NR; i++)
+#pragma unroll
+                for (int j = 0; j < NC; j++) {
+                    const int r = ty + 8 * i, c = tx + 32 * j;
+                    if (r < TH + 2 && c < TW + 2) s_m[r][c] = sqrtf(d[i][j].x * d[i][j].x + d[i][j].y * d[i][j].y);
+                }
         }
         __syncthreads();
         unsigned mn = 0x7f800000u, mx = 0u;
@@ -141,8 +155,8 @@ __global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ 
                 const float gxv = 0.5f * (s_m[r + 1][c + 2] - s_m[r + 1][c]);
                 const float gyv = 0.5f * (s_m[r + 2][c + 1] - s_m[r][c + 1]);
                 const float S = mc.alpha * s_m[r + 1][c + 1] + (1.f - mc.alpha) * sqrtf(gxv * gxv + gyv * gyv);
-                F.S[(size_t)gy * p + gx] = S;
-                if (F.dbg_flow) F.dbg_flow[(size_t)gy * w + gx] = fl[(size_t)gy * p + gx];
+                Sp[(size_t)gy * p + gx] = S;
+                if (dbg_flow) dbg_flow[(size_t)gy * w + gx] = fl[(size_t)gy * p + gx];
                 const unsigned b = __float_as_uint(S);
                 mn = min(mn, b);
                 mx = max(mx, b);
@@ -371,6 +385,10 @@ __global__ void __launch_bounds__(256) k_morph(const BatchDesc *__restrict__ bd,
         }
         const unsigned sstar = F.red[kRedSStar];
         const bool keep = F.dbg_mask0 != nullptr;
+        const float *const Sp = F.S;
+        uint8_t *const dbg_mask0 = F.dbg_mask0;
+        float *const dbg_shat = F.dbg_shat;
+        uint8_t *const maskp = F.mask;
         const float mn = __uint_as_float(F.red[kRedMin]), mx = __uint_as_float(F.red[kRedMax]);
         // Pack mask0 = (S > s*) one row per warp, each lane loading one pixel
         // of every word of the row (all loads of the row in flight together).
@@ -385,7 +403,7 @@ __global__ void __launch_bounds__(256) k_morph(const BatchDesc *__restrict__ bd,
 #pragma unroll
             for (int x = 0; x < kMorEW; x++) {
                 const int gx = (wx0 + x) * 32 + lane;
-                bits[x] = (rin && gx >= 0 && gx < w) ? __float_as_uint(F.S[(size_t)gy * p + gx]) : 0xffffffffu;
+                bits[x] = (rin && gx >= 0 && gx < w) ? __float_as_uint(Sp[(size_t)gy * p + gx]) : 0xffffffffu;
             }
 #pragma unroll
             for (int x = 0; x < kMorEW; x++) {
@@ -393,8 +411,8 @@ __global__ void __launch_bounds__(256) k_morph(const BatchDesc *__restrict__ bd,
                 const bool bit = inb ? bits[x] > sstar : true;
                 if (keep && inb && y >= kMorApron && y < kMorApron + kMorRows && x >= 1 && x <= kMorWords) {
                     const int gx = (wx0 + x) * 32 + lane;
-                    F.dbg_mask0[(size_t)gy * w + gx] = bit ? 1 : 0;
-                    F.dbg_shat[(size_t)gy * w + gx] = normalise(__uint_as_float(bits[x]), mn, mx);
+                    dbg_mask0[(size_t)gy * w + gx] = bit ? 1 : 0;
+                    dbg_shat[(size_t)gy * w + gx] = normalise(__uint_as_float(bits[x]), mn, mx);
                 }
                 const unsigned word = __ballot_sync(0xffffffffu, bit);
                 if (lane == 0) s_a[y][x] = word;
@@ -424,7 +442,7 @@ __global__ void __launch_bounds__(256) k_morph(const BatchDesc *__restrict__ bd,
             const unsigned word = s_a[kMorApron + r][1 + (q >> 3)];
             const unsigned nib = (word >> ((q & 7) * 4)) & 0xfu;
             const unsigned bytes = (nib * 0x00204081u) & 0x01010101u;
-            uint8_t *dst = F.mask + (size_t)gy * w + gx;
+            uint8_t *dst = maskp + (size_t)gy * w + gx;
             if (gx + 4 <= w && ((((size_t)gy * w + gx) & 3) == 0)) {
                 *reinterpret_cast<unsigned *>(dst) = bytes;
             } else {

@@ -1,0 +1,50 @@
+"""Multi-rank aggregation of bench.py on CPU (gloo, world size 2): every
+rank runs its own replica; the job time is the slowest rank's and the
+throughput counts every rank's frames."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, ws, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    t = bench.max_over_ranks(1.5 + rank, ws, "cpu")  # rank 1 is the slow one
+    q.put((rank, t, bench.job_throughput(100, ws, t)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_job_throughput_gloo():
+    ws = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(ws)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, t, thr in out:
+        assert t == 2.5
+        assert thr == pytest.approx(200 / 2.5)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(3.0, 1, "cpu") == 3.0
+    assert bench.job_throughput(16, 1, 2.0) == 8.0
+    assert [bench.frame_index(t, 4) for t in range(8)] == [0, 1, 2, 3, 2, 1, 0, 1]
