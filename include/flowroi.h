@@ -261,6 +261,50 @@ typedef struct flowroi_kernel_time {
 FLOWROI_API int flowroi_set_profiling(flowroi_ctx *ctx, int on);
 FLOWROI_API int flowroi_get_kernel_times(flowroi_ctx *ctx, flowroi_kernel_time *out, int cap);
 
+/* JPEG2000 front end of one frame that allocates nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (code running inside a fixed, pre-reserved
+ * device budget, plug-ins whose host application owns the device heap,
+ * real-time loops that must not call cudaMalloc, whose latency is unbounded
+ * and which can synchronise the device).  It runs the same DWT kernel as the
+ * streaming path - DC shift, `levels` levels of lifting DWT, quantisation
+ * (9/7), the wavelet-domain RoI mask of `mask` and the up-shift of RoI
+ * coefficients by `scale_shift` bits - on buffers the caller owns, and
+ * calls no cudaMalloc, cudaFree or allocating routine.  The memory it needs
+ * besides the caller's buffers (a one-frame descriptor and the low-low
+ * planes between levels) is one fixed array in the library, about 2.6 MB,
+ * that every GPU which loads the library holds until the process exits.
+ *
+ *   raw          device pointer: width x height samples, rows pitch_bytes
+ *                apart (0 = tight); dtype FLOWROI_U8 or FLOWROI_U16 (then
+ *                raw and pitch 4-byte aligned), bit_depth significant bits
+ *   mask         device pointer: width x height bytes, 0/1, tight rows,
+ *                2-byte aligned (e.g. from flowroi_get_mask with
+ *                out_on_device = 1)
+ *   delta        host array of 3*levels + 1 quantisation steps for 9/7 (from
+ *                flowroi_quant_steps); may be NULL for 5/3
+ *   coeffs       device pointer: width x height int32, Mallat layout (the
+ *                layout of flowroi_get_coeffs), 4-byte aligned
+ *   cuda_stream  cudaStream_t (as void*) the work is queued on; NULL = the
+ *                legacy default stream.  The call returns once the work is
+ *                queued.
+ *
+ * Limits: width * height <= 2^20 pixels (the fixed array holds the low-low
+ * planes of frames that large), width and height >= 16 and multiples of
+ * 2^levels, levels in [1, 8].  Larger or malformed requests return
+ * FLOWROI_EINVAL and queue nothing; a CUDA error returns FLOWROI_EDEVICE.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU (queued on different streams without ordering between them) race
+ * and give undefined coefficients; order them on one stream or with events.
+ * Host threads are serialised by an internal lock. */
+FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, int pitch_bytes, int dtype,
+                                        int bit_depth, const uint8_t *mask, int wavelet, int levels,
+                                        int scale_shift, const float *delta, int32_t *coeffs, void *cuda_stream);
+
 /* Library ABI version (FLOWROI_ABI_VERSION). */
 FLOWROI_API int flowroi_abi_version(void);
 

@@ -26,7 +26,7 @@ EXPORTS = [
     "flowroi_step", "flowroi_get_mask", "flowroi_get_coeffs", "flowroi_get_intermediate",
     "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
-    "flowroi_get_kernel_times",
+    "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc",
 ]
 
 
@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
             "flowroi_compute_stream": (I, [P, ctypes.POINTER(P)]),
             "flowroi_set_profiling": (I, [P, I]),
             "flowroi_get_kernel_times": (I, [P, ctypes.POINTER(flowroi_kernel_time), I]),
+            "flowroi_dwt_roi_noalloc": (I, [P, I, I, I, I, I, P, I, I, I, P, P, P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -229,6 +230,30 @@ def flowroi_get_kernel_times(ctx, cap: int = 256) -> list:
     n = _check(lib().flowroi_get_kernel_times(ctx, arr, cap), ctx)
     return [dict(name=arr[i].name.decode(), level=arr[i].level, iter=arr[i].iter, launches=arr[i].launches,
                  total_ms=arr[i].total_ms) for i in range(n)]
+
+
+def flowroi_dwt_roi_noalloc(raw, bit_depth: int, mask, wavelet: int, levels: int, scale_shift: int, delta,
+                            coeffs, stream: int = 0, pitch_bytes: int = 0) -> int:
+    """JPEG2000 front end of one frame with no allocation (see the C header).
+    raw / mask / coeffs: CUDA tensors (H, W); delta: host float32 array or
+    None (5/3); stream: cudaStream_t handle as an int (0 = default)."""
+    h, w = int(raw.shape[0]), int(raw.shape[1])
+    esz = raw.element_size()
+    rp, rdev = _ptr(raw)
+    mp_, mdev = _ptr(mask)
+    cp, cdev = _ptr(coeffs)
+    if not (rdev and mdev and cdev):
+        raise ValueError("raw, mask and coeffs must be device tensors")
+    dp = None
+    if delta is not None:
+        import numpy as np
+        delta = np.ascontiguousarray(delta, dtype=np.float32)
+        dp = delta.ctypes.data
+    rc = lib().flowroi_dwt_roi_noalloc(rp, w, h, pitch_bytes, U8 if esz == 1 else U16, bit_depth, mp_, wavelet, levels,
+                                       scale_shift, dp, cp, stream or None)
+    if rc < 0:
+        raise FlowRoIError(rc, "flowroi_dwt_roi_noalloc rejected the request" if rc == EINVAL else "CUDA error")
+    return rc
 
 
 class Context:
