@@ -48,6 +48,11 @@ WORKLOADS = {
     # four streams of the batched workload's frames (small case for profiler captures)
     "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
+    # serving: 64 streams (16 each of 512^2, 1024^2, 2048^2, 2048x1536, 12-bit)
+    # through the scheduler thread; Poisson arrivals, then a burst replay
+    "serving_64mixed": dict(streams=64, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                            dwt_levels=5, wavelet=97, precision=32, seed_base=5000,
+                            sizes=[(512, 512), (1024, 1024), (2048, 2048), (1536, 2048)]),
     # one stream of 64 1024^2 12-bit frames, 5/3 DWT (plain method at full size)
     "stream_1024": dict(streams=1, frames=64, h=1024, w=1024, blobs=80, bit_depth=12, pyr_levels=4,
                         dwt_levels=5, wavelet=53, precision=32, seed_base=2000),
@@ -306,6 +311,85 @@ def run_e2e(F, wl, frames, steps, warmup):
     return res
 
 
+def run_serving(F, wl, rate_fps: float, duration_s: float, burst_per_stream: int, seed: int = 7):
+    """Serving through the public API with the scheduler thread: 64 streams
+    of mixed resolution submit frames from pinned host memory, (1) as Poisson
+    processes with `rate_fps` frames/s in aggregate for `duration_s`, then
+    (2) as a burst: every stream submits `burst_per_stream` frames at once.
+    Results are fetched as they complete.  Returns frames/s and latency
+    percentiles (submit -> result ready) of each phase."""
+    import numpy as np
+    import torch
+
+    from synth import sequence_u16
+    rng = np.random.default_rng(seed)
+    S, nf, bd = wl["streams"], wl["frames"], wl["bit_depth"]
+    sizes = [wl["sizes"][s // (S // len(wl["sizes"]))] for s in range(S)]
+    host = []
+    for s in range(S):
+        h, w = sizes[s]
+        fr = sequence_u16(wl["seed_base"] + s, nf, h, w, max(8, wl["blobs"] * h * w // (2048 * 2048)), device="cuda")
+        host.append([fr[i].cpu().pin_memory() for i in range(nf)])
+    torch.cuda.synchronize()
+    cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
+               precision=wl["precision"], max_batch_frames=64, result_ring=8, device=torch.cuda.current_device())
+    out = {}
+    masks = {sz: torch.empty(sz, dtype=torch.uint8).pin_memory() for sz in set(sizes)}
+    coefs = {sz: torch.empty(sz, dtype=torch.int32).pin_memory() for sz in set(sizes)}
+    with F.Context(**cfg) as ctx:
+        nxt = [0] * S
+        pending = []  # (stream, frame index)
+
+        def submit_one(s):
+            i = nxt[s]
+            submit(F, ctx.h, s, host[s][frame_index(i, nf)], i, bd)
+            pending.append((s, i))
+            nxt[s] += 1
+
+        def drain(block: bool):
+            keep = []
+            for s, i in pending:
+                sz = sizes[s]
+                try:
+                    F.flowroi_get_mask(ctx.h, s, i, masks[sz], -1 if block else 0)
+                    F.flowroi_get_coeffs(ctx.h, s, i, coefs[sz], -1)
+                except F.FlowRoIError as e:
+                    if e.code != F.ETIMEDOUT:
+                        raise
+                    keep.append((s, i))
+            pending[:] = keep
+
+        for s in range(S):  # first frames (no predecessor), not measured
+            submit_one(s)
+        F.flowroi_flush(ctx.h, -1)
+        drain(True)
+        for phase in ("poisson", "burst"):
+            st0 = F.flowroi_get_stats(ctx.h)
+            n0 = st0["frames_done"]
+            F.flowroi_reset_stats(ctx.h)
+            t0 = time.perf_counter()
+            if phase == "poisson":
+                arrivals = np.sort(rng.uniform(0.0, duration_s, size=rng.poisson(rate_fps * duration_s)))
+                who = rng.integers(0, S, size=arrivals.size)
+                for ta, s in zip(arrivals, who):
+                    while time.perf_counter() - t0 < ta:
+                        drain(False)
+                        time.sleep(0.0005)
+                    submit_one(int(s))
+            else:
+                for _ in range(burst_per_stream):
+                    for s in range(S):
+                        submit_one(s)
+            F.flowroi_flush(ctx.h, -1)
+            dt = time.perf_counter() - t0
+            drain(True)
+            st = F.flowroi_get_stats(ctx.h)
+            out[phase] = {"frames": st["frames_done"] - n0, "seconds": dt,
+                          "frames_per_s": (st["frames_done"] - n0) / dt,
+                          "p50_ms": st["lat_p50_ms"], "p99_ms": st["lat_p99_ms"], "batches": st["batches"]}
+    return out
+
+
 def cpu_sample(wl, frames_cpu, budget_s=12.0, crop=512):
     """The oracle (as it stands, single-threaded) on crop pairs of the
     workload; returns (frames/s scaled to full frames, seconds, crops)."""
@@ -388,6 +472,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--serving-rate", type=float, default=8.0,
+                    help="serving workload: aggregate Poisson arrival rate, frames/s (8 = 64 wells x 1 frame / 8 s)")
+    ap.add_argument("--serving-seconds", type=float, default=20.0)
+    ap.add_argument("--burst", type=int, default=4, help="serving workload: frames per stream in the burst replay")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -405,6 +493,15 @@ def main():
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if "sizes" in wl:
+        # serving measurement: its own JSON line (rank 0), not the throughput line
+        res = run_serving(F, wl, args.serving_rate, args.serving_seconds, args.burst)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "workload": args.workload, "n_gpus": ws, "data": "synthetic",
+                              "streams": wl["streams"], "sizes": wl["sizes"],
+                              "poisson_rate_fps": args.serving_rate, "poisson_seconds": args.serving_seconds,
+                              "burst_frames_per_stream": args.burst, "phases": res}), flush=True)
+        return
     frames = make_frames(wl, f"cuda:{local}")
 
     def barrier():

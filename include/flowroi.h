@@ -219,6 +219,10 @@ FLOWROI_API int flowroi_end_stream(flowroi_ctx *ctx, int64_t stream_id);
 /* Counters and latency percentiles since create. */
 FLOWROI_API int flowroi_get_stats(flowroi_ctx *ctx, flowroi_stats *out);
 
+/* Forget the latency samples collected so far (counters keep counting),
+ * so that flowroi_get_stats reports percentiles of a measurement window. */
+FLOWROI_API int flowroi_reset_stats(flowroi_ctx *ctx);
+
 /* Stop the scheduler, wait for the device, free everything.  NULL is a
  * no-op. */
 FLOWROI_API void flowroi_destroy(flowroi_ctx *ctx);

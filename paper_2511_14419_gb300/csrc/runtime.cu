@@ -1089,6 +1089,14 @@ int flowroi_get_stats(flowroi_ctx *c, flowroi_stats *out)
     return FLOWROI_OK;
 }
 
+int flowroi_reset_stats(flowroi_ctx *c)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    std::lock_guard<std::mutex> lk(c->cmu);
+    c->lat_ms.clear();
+    return FLOWROI_OK;
+}
+
 void flowroi_destroy(flowroi_ctx *c)
 {
     if (!c) return;

@@ -26,7 +26,7 @@ EXPORTS = [
     "flowroi_step", "flowroi_get_mask", "flowroi_get_coeffs", "flowroi_get_intermediate",
     "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
-    "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc",
+    "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc", "flowroi_reset_stats",
 ]
 
 
@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
             "flowroi_set_profiling": (I, [P, I]),
             "flowroi_get_kernel_times": (I, [P, ctypes.POINTER(flowroi_kernel_time), I]),
             "flowroi_dwt_roi_noalloc": (I, [P, I, I, I, I, I, P, I, I, I, P, P, P]),
+            "flowroi_reset_stats": (I, [P]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -191,6 +192,10 @@ def flowroi_get_stats(ctx) -> dict:
     s.struct_size = ctypes.sizeof(flowroi_stats)
     _check(lib().flowroi_get_stats(ctx, ctypes.byref(s)), ctx)
     return {name: getattr(s, name) for name, _ in flowroi_stats._fields_ if name != "struct_size"}
+
+
+def flowroi_reset_stats(ctx) -> int:
+    return _check(lib().flowroi_reset_stats(ctx), ctx)
 
 
 def flowroi_destroy(ctx) -> None:

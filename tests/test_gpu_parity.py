@@ -148,3 +148,24 @@ def test_device_pointer_io_matches_host_io():
         F.flowroi_get_coeffs(ctx.h, 3, 1, c)
     assert np.array_equal(m.cpu().numpy(), host["mask"])
     assert np.array_equal(c.cpu().numpy(), host["coeffs"])
+
+
+def test_fp16_storage_2048_epe_and_iou_vs_fp64(orc):
+    """fp16 storage of pyramid, expansion fields and G, h (float arithmetic,
+    float 2x2 solve) on a full-size 2048x2048 pair: flow EPE and mask IoU
+    against the float64 oracle, beside the float32 storage path."""
+    seq = u16(sequence_u16(3000, 2, 2048, 2048, 200))
+    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
+    o = orc.frame(seq[0], seq[1], 12, oracle_params(orc, **cfg))
+    res = {}
+    for name, prec in (("fp32", F.FP32), ("fp16", F.FP16)):
+        g = run_stream([seq[0], seq[1]], 12, precision=prec, **cfg)[1]
+        d = g["flow"].transpose(2, 0, 1).astype(np.float64)
+        epe = float(np.hypot(d[0] - o["flow"][0], d[1] - o["flow"][1]).mean())
+        mx = float(np.abs(d - o["flow"]).max())
+        iou = float((g["mask"] & o["mask"]).sum() / max(1, (g["mask"] | o["mask"]).sum()))
+        res[name] = (epe, mx, iou)
+    print(f"\n2048^2 pair vs float64 oracle: fp32 EPE {res['fp32'][0]:.3e} max {res['fp32'][1]:.3e} IoU {res['fp32'][2]:.5f}; "
+          f"fp16 EPE {res['fp16'][0]:.3e} max {res['fp16'][1]:.3e} IoU {res['fp16'][2]:.5f}")
+    assert res["fp32"][1] <= FLOW_TOL
+    assert res["fp16"][0] < 0.05 and res["fp16"][2] > 0.9
