@@ -15,10 +15,10 @@
 // Two kernels per iteration: k_update computes G and h per pixel into five
 // planes (no apron recompute, no shared memory: full occupancy hides the
 // gather latency); k_window forms the box means over a shared-memory tile
-// and solves.  Box sums keep a column (row segment) in registers and add it
-// as a tree of power-of-two partial sums (no running sums: every window is
-// a fresh sum of its own 2r+1 terms, so no cancellation between far-apart
-// values).
+// and solves.  Box sums keep a column (row segment) in registers and form
+// every window from a block suffix sum and a block prefix sum (no running
+// sums: every window is a fresh sum of its own 2r+1 terms, so no
+// cancellation between far-apart values).
 #include "common.cuh"
 #include "kernels.h"
 #include "tma.cuh"
@@ -27,33 +27,32 @@ namespace flowroi {
 
 namespace {
 
-// out[i] = v[i] + ... + v[i + WN - 1] for i < N - WN + 1, as a tree of
-// power-of-two partial sums (all indices compile-time after unrolling).
+// out[i] = v[i] + ... + v[i + WN - 1] for i < N - WN + 1.  The column is
+// cut into blocks of WN starting at 0; a window starting at i either is
+// one whole block (i a multiple of WN) or ends in the next block, so it is
+// the suffix sum of i's block from i plus the prefix sum of the next block
+// up to i + WN - 1 (the van Herk / Gil-Werman decomposition, here for sums
+// instead of extrema).  About three additions per output instead of
+// log2(WN) per output plus the partial-sum pyramid, and each window is
+// still a fresh sum of its own WN terms.  All indices are compile-time
+// after unrolling; sums nothing reads are removed by the compiler.
 template <int N, int WN>
 __device__ __forceinline__ void box_sums(const float (&v)[N], float (&out)[N - WN + 1])
 {
     constexpr int M = N - WN + 1;
-    float p2[N], p4[N], p8[N], p16[N];
+    float suf[N], pre[N];
 #pragma unroll
-    for (int i = 0; i + 1 < N; i++) p2[i] = v[i] + v[i + 1];
-#pragma unroll
-    for (int i = 0; i + 3 < N; i++) p4[i] = p2[i] + p2[i + 2];
-#pragma unroll
-    for (int i = 0; i + 7 < N; i++) p8[i] = p4[i] + p4[i + 4];
-#pragma unroll
-    for (int i = 0; i + 15 < N; i++) p16[i] = p8[i] + p8[i + 8];
-#pragma unroll
-    for (int i = 0; i < M; i++) {
-        float s = 0.f;
-        int o = 0;
-        bool any = false;
-        if (WN & 16) { s = p16[i]; o += 16; any = true; }
-        if (WN & 8) { s = any ? s + p8[i + o] : p8[i + o]; o += 8; any = true; }
-        if (WN & 4) { s = any ? s + p4[i + o] : p4[i + o]; o += 4; any = true; }
-        if (WN & 2) { s = any ? s + p2[i + o] : p2[i + o]; o += 2; any = true; }
-        if (WN & 1) { s = any ? s + v[i + o] : v[i + o]; }
-        out[i] = s;
+    for (int j = N - 1; j >= 0; j--) {
+        if (j % WN == WN - 1 || j == N - 1) suf[j] = v[j];
+        else suf[j] = v[j] + suf[j + 1];
     }
+#pragma unroll
+    for (int j = 0; j < N; j++) {
+        if (j % WN == 0) pre[j] = v[j];
+        else pre[j] = pre[j - 1] + v[j];
+    }
+#pragma unroll
+    for (int i = 0; i < M; i++) out[i] = (i % WN == 0) ? suf[i] : suf[i] + pre[i + WN - 1];
 }
 
 // a*b - c*d with one rounding error at most a few ulps (FMA error-free
@@ -162,10 +161,14 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
 // Box means of G and h over (2r+1)^2 (clipped to the image) and the 2x2
 // solve.  One TMA copy brings the five planes of a kWinTW x kWinTH tile
 // plus its r-pixel apron into shared memory (elements outside the image
-// arrive as zeros, which is exactly the clipped sum); every column is then
-// summed over 2r+1 rows (in place, or into a float buffer for half
-// storage), and 8 adjacent outputs of a row are summed over 2r+1 columns
-// for all five fields and solved.
+// arrive as zeros, which is exactly the clipped sum).  Every column is then
+// summed over 2r+1 rows, fields 0-2 in a first round of threads and fields
+// 3-4 in a second; each round sums its columns in registers before any
+// thread writes, so the sums can be packed in place (fp32) at a row stride
+// SW with SW/4 odd.  Then each thread sums 8 adjacent outputs of a row over
+// 2r+1 columns for all five fields, reading its row segment as 16-byte
+// words: the 8 threads of a quarter-warp take 8 different rows, whose
+// words fall in 8 different bank groups, so the reads are conflict-free.
 template <typename T, int R>
 struct WinGeom {
     static constexpr int EPC = 16 / sizeof(T);                         // elements per 16 bytes
@@ -173,10 +176,17 @@ struct WinGeom {
     static constexpr int BW = (kWinTW + XO + R + EPC - 1) / EPC * EPC; // box width (elements)
     static constexpr int EH = kWinTH + 2 * R;
     static constexpr int EW = kWinTW + 2 * R;
+    static constexpr int SEG = 8;                                      // outputs per thread in a row
+    static constexpr int SV = (SEG + 2 * R + 3) / 4;                   // float4 words a thread reads per row
+    static constexpr int SW0 = EW > kWinTW - SEG + 4 * SV ? (EW + 3) / 4 * 4 : kWinTW - SEG + 4 * SV;
+    static constexpr int SW = (SW0 / 4) % 2 ? SW0 : SW0 + 4;           // sums row stride (floats)
     static constexpr size_t box_bytes = (size_t)5 * EH * BW * sizeof(T);
-    // float sums buffer (half storage only)
-    static constexpr size_t sum_bytes = sizeof(T) == 4 ? 0 : (size_t)5 * kWinTH * EW * sizeof(float);
+    // float sums buffer (half storage only; fp32 packs the sums in place)
+    static constexpr size_t sum_bytes = sizeof(T) == 4 ? 0 : (size_t)5 * kWinTH * SW * sizeof(float);
     static constexpr size_t smem = 128 + box_bytes + sum_bytes;
+    static_assert(sizeof(T) != 4 || kWinTH * SW <= EH * BW, "packed sums fit each field's box");
+    static_assert(3 * EW <= 256, "a round of three fields' columns fits the block");
+    static_assert(kWinTW % SEG == 0 && (kWinTW / SEG) * kWinTH == 256, "one row segment per thread");
 };
 
 template <typename T, int R>
@@ -184,16 +194,18 @@ __global__ void __launch_bounds__(256, 3) k_window(const BatchDesc *__restrict__
 {
     using G = WinGeom<T, R>;
     constexpr int TW = kWinTW, TH = kWinTH, EW = G::EW, EH = G::EH, BW = G::BW, WN = 2 * R + 1;
-    constexpr int SEG = 8;
+    constexpr int SEG = G::SEG, SW = G::SW, SV = G::SV;
     constexpr bool kF32 = sizeof(T) == 4;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-    T *box = reinterpret_cast<T *>(smem_raw + 128);                              // [5][EH][BW]
+    T *box = reinterpret_cast<T *>(smem_raw + 128);  // [5][EH][BW]
+    // field k's column sums: [TH][SW] at sums + k * SFS
     float *sums = kF32 ? reinterpret_cast<float *>(box) : reinterpret_cast<float *>(smem_raw + 128 + G::box_bytes);
-    // float view of the column sums: [5][rows][SW]
-    constexpr int SW = kF32 ? BW : EW;
-    constexpr int SR = kF32 ? EH : TH;
-    constexpr int SOFF = kF32 ? (G::XO - R) : 0;  // column of ext col 0 in the sums buffer
+    constexpr int SFS = kF32 ? EH * BW : TH * SW;
+
+    // row-segment owner of this thread: quarter-warps span 8 rows
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int r = (wp & 3) * 8 + (lane & 7), sg = (wp >> 2) * 4 + (lane >> 3);
 
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -227,48 +239,76 @@ __global__ void __launch_bounds__(256, 3) k_window(const BatchDesc *__restrict__
         }
         phase ^= 1u;
 
-        // vertical sums of every ext column (rows [0, TH) of the sums view)
-        for (int it = threadIdx.x; it < 5 * EW; it += blockDim.x) {
-            const int k = it / EW, ex = it - k * EW;
-            const T *col = box + k * EH * BW + ex + (G::XO - R);
-            float v[EH], sm[TH];
+        // vertical sums of every ext column, two rounds of fields
 #pragma unroll
-            for (int j = 0; j < EH; j++) v[j] = (float)col[j * BW];
-            box_sums<EH, WN>(v, sm);
-            float *dcol = sums + k * SR * SW + ex + SOFF;
+        for (int round = 0; round < 2; round++) {
+            const int k0 = round ? 3 : 0, nk = round ? 2 : 3;
+            const int k = k0 + (int)threadIdx.x / EW, ex = (int)threadIdx.x % EW;
+            const bool mine = (int)threadIdx.x < nk * EW;
+            float sm[TH];
+            if (mine) {
+                const T *col = box + k * EH * BW + ex + (G::XO - R);
+                float v[EH];
 #pragma unroll
-            for (int j = 0; j < TH; j++) dcol[j * SW] = sm[j];
+                for (int j = 0; j < EH; j++) v[j] = (float)col[j * BW];
+                box_sums<EH, WN>(v, sm);
+            }
+            if (kF32) __syncthreads();  // every column of the round is read before the packed sums overwrite it
+            if (mine) {
+                float *dcol = sums + k * SFS + ex;
+#pragma unroll
+                for (int j = 0; j < TH; j++) dcol[j * SW] = sm[j];
+            }
         }
         __syncthreads();
 
         {
-            const int r = threadIdx.x / (TW / SEG), sg = threadIdx.x - r * (TW / SEG);
             const int gy = y0 + r, gxs = x0 + sg * SEG;
-            if (r < TH && gy < h && gxs < w) {
+            if (gy < h && gxs < w) {
                 float acc[5][SEG];
 #pragma unroll
                 for (int k = 0; k < 5; k++) {
-                    const float *row = sums + k * SR * SW + r * SW + SOFF + sg * SEG;
-                    float v[SEG + 2 * R], sm[SEG];
+                    const float4 *row = reinterpret_cast<const float4 *>(sums + k * SFS + r * SW + sg * SEG);
+                    float v[4 * SV], sm[SEG];
 #pragma unroll
-                    for (int j = 0; j < SEG + 2 * R; j++) v[j] = row[j];
-                    box_sums<SEG + 2 * R, WN>(v, sm);
+                    for (int q = 0; q < SV; q++) {
+                        const float4 u = row[q];
+                        v[4 * q] = u.x;
+                        v[4 * q + 1] = u.y;
+                        v[4 * q + 2] = u.z;
+                        v[4 * q + 3] = u.w;
+                    }
+                    const float(&vv)[SEG + 2 * R] = *reinterpret_cast<const float(*)[SEG + 2 * R]>(v);
+                    box_sums<SEG + 2 * R, WN>(vv, sm);
 #pragma unroll
                     for (int j = 0; j < SEG; j++) acc[k][j] = sm[j];
                 }
+                // With c = the window's in-image pixel count, G_ = S_G / c and
+                // h_ = S_h / c, so adj(G_) h_ / (det G_ + lambda) =
+                // adj(S_G) S_h / (det S_G + lambda c^2): one division.
                 const int cy = min(gy + R, h - 1) - max(gy - R, 0) + 1;
-                float2 *fdst = F.flow[dst] + (size_t)gy * p;
+                float2 *frow = F.flow[dst] + (size_t)gy * p + gxs;
+                const bool whole = gxs + SEG <= w;
 #pragma unroll
-                for (int j = 0; j < SEG; j++) {
-                    const int gx = gxs + j;
-                    if (gx >= w) break;
-                    const int cx = min(gx + R, w - 1) - max(gx - R, 0) + 1;
-                    const float ic = 1.f / (float)(cx * cy);
-                    const float g11 = acc[0][j] * ic, g12 = acc[1][j] * ic, g22 = acc[2][j] * ic;
-                    const float h1 = acc[3][j] * ic, h2 = acc[4][j] * ic;
-                    const float idet = 1.f / (diff_of_products(g11, g22, g12, g12) + mc.lambda);
-                    fdst[gx] = make_float2(diff_of_products(g22, h1, g12, h2) * idet,
-                                           diff_of_products(g11, h2, g12, h1) * idet);
+                for (int j = 0; j < SEG; j += 2) {
+                    float d[4];
+#pragma unroll
+                    for (int e = 0; e < 2; e++) {
+                        const int gx = gxs + j + e;
+                        const int cx = min(gx + R, w - 1) - max(gx - R, 0) + 1;
+                        const float c = (float)(cx * cy);
+                        const float g11 = acc[0][j + e], g12 = acc[1][j + e], g22 = acc[2][j + e];
+                        const float h1 = acc[3][j + e], h2 = acc[4][j + e];
+                        const float idet = 1.f / (diff_of_products(g11, g22, g12, g12) + mc.lambda * c * c);
+                        d[2 * e] = diff_of_products(g22, h1, g12, h2) * idet;
+                        d[2 * e + 1] = diff_of_products(g11, h2, g12, h1) * idet;
+                    }
+                    if (whole) {
+                        *reinterpret_cast<float4 *>(frow + j) = make_float4(d[0], d[1], d[2], d[3]);
+                    } else {
+                        if (gxs + j < w) frow[j] = make_float2(d[0], d[1]);
+                        if (gxs + j + 1 < w) frow[j + 1] = make_float2(d[2], d[3]);
+                    }
                 }
             }
         }
