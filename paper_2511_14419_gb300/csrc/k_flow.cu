@@ -159,16 +159,34 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
 
 // ---------------------------------------------------------------- window
 // Box means of G and h over (2r+1)^2 (clipped to the image) and the 2x2
-// solve.  One TMA copy brings the five planes of a kWinTW x kWinTH tile
-// plus its r-pixel apron into shared memory (elements outside the image
-// arrive as zeros, which is exactly the clipped sum).  Every column is then
-// summed over 2r+1 rows, fields 0-2 in a first round of threads and fields
-// 3-4 in a second; each round sums its columns in registers before any
-// thread writes, so the sums can be packed in place (fp32) at a row stride
-// SW with SW/4 odd.  Then each thread sums 8 adjacent outputs of a row over
-// 2r+1 columns for all five fields, reading its row segment as 16-byte
-// words: the 8 threads of a quarter-warp take 8 different rows, whose
-// words fall in 8 different bank groups, so the reads are conflict-free.
+// solve, over kWinTW x kWinTH tiles.  Warp-specialised, plane by plane: a
+// producer warp streams each tile's five G, h planes (each with the r-pixel
+// apron, one TMA copy per plane) through a ring of NS shared-memory slots
+// guarded by full / empty mbarriers.  NS is more than a tile's five planes,
+// so the next tile's planes are in flight while the current tile is
+// summed.  Elements outside the image arrive as zeros, which is exactly the
+// clipped sum.  Per plane, eight consumer warps sum every column over 2r+1
+// rows (kWinChunks row chunks per column, so that 3(64 + 2r) items keep the
+// warps busy) into one of two sums buffers and release the slot; after a
+// barrier each consumer thread sums 8 adjacent outputs of a row over 2r+1
+// columns into registers.  After the fifth plane it solves.  The sums rows
+// are an odd number of 16-byte words apart and the 8 threads of a
+// quarter-warp take 8 different rows, so the float4 row reads are
+// conflict-free.  Sums buffer (plane i mod 2) is rewritten two planes
+// later, after the barrier that follows every warp's reads of it.
+//
+// Ordering: every consumer warp takes the planes in load order and waits
+// for each, so when it waits for a slot's n-th fill it has seen the
+// (n-1)-th complete (the parity waits cannot alias); the producer refills a
+// slot only after all eight warps arrived on its empty barrier.  Every wait
+// is bounded: a consumer whose wait runs out skips the work, the consumers
+// agree at the next barrier and leave with the batch error word set, and
+// the producer waits (bounded) for the copies it issued before it leaves.
+constexpr int kWinConsumers = 256;
+constexpr int kWinThreads = kWinConsumers + 32;
+constexpr int kWinChunks = 3;
+constexpr size_t kWinSmemBlock = 112 * 1024;  // two blocks per SM
+
 template <typename T, int R>
 struct WinGeom {
     static constexpr int EPC = 16 / sizeof(T);                         // elements per 16 bytes
@@ -176,143 +194,173 @@ struct WinGeom {
     static constexpr int BW = (kWinTW + XO + R + EPC - 1) / EPC * EPC; // box width (elements)
     static constexpr int EH = kWinTH + 2 * R;
     static constexpr int EW = kWinTW + 2 * R;
+    static constexpr int CH = (kWinTH + kWinChunks - 1) / kWinChunks;  // outputs per column chunk
     static constexpr int SEG = 8;                                      // outputs per thread in a row
     static constexpr int SV = (SEG + 2 * R + 3) / 4;                   // float4 words a thread reads per row
     static constexpr int SW0 = EW > kWinTW - SEG + 4 * SV ? (EW + 3) / 4 * 4 : kWinTW - SEG + 4 * SV;
     static constexpr int SW = (SW0 / 4) % 2 ? SW0 : SW0 + 4;           // sums row stride (floats)
-    static constexpr size_t box_bytes = (size_t)5 * EH * BW * sizeof(T);
-    // float sums buffer (half storage only; fp32 packs the sums in place)
-    static constexpr size_t sum_bytes = sizeof(T) == 4 ? 0 : (size_t)5 * kWinTH * SW * sizeof(float);
-    static constexpr size_t smem = 128 + box_bytes + sum_bytes;
-    static_assert(sizeof(T) != 4 || kWinTH * SW <= EH * BW, "packed sums fit each field's box");
-    static_assert(3 * EW <= 256, "a round of three fields' columns fits the block");
-    static_assert(kWinTW % SEG == 0 && (kWinTW / SEG) * kWinTH == 256, "one row segment per thread");
+    static constexpr size_t plane_bytes = (size_t)EH * BW * sizeof(T); // one TMA copy
+    static constexpr size_t slot_stride = (plane_bytes + 127) / 128 * 128;
+    static constexpr size_t sums_bytes = (size_t)kWinTH * SW * sizeof(float);
+    static constexpr size_t fixed = 128 + 2 * sums_bytes;
+    static constexpr int NS0 = (int)((kWinSmemBlock - fixed) / slot_stride);
+    static constexpr int NS = NS0 > 8 ? 8 : NS0;                       // ring slots
+    static constexpr size_t slots_off = 128;
+    static constexpr size_t sums_off = slots_off + NS * slot_stride;
+    static constexpr size_t smem = sums_off + 2 * sums_bytes;
+    static_assert(NS >= 5, "a whole tile's planes in flight");
+    static_assert(kWinChunks * EW <= kWinConsumers, "one column chunk per consumer thread");
+    static_assert((kWinTW / SEG) * kWinTH == kWinConsumers, "one row segment per consumer thread");
+    static_assert(kWinConsumers == 256, "row-segment thread map assumes 8 warps");
 };
 
 template <typename T, int R>
-__global__ void __launch_bounds__(256, 3) k_window(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int dst)
+__global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__restrict__ bd, MethodConsts mc, int level,
+                                                          int dst)
 {
     using G = WinGeom<T, R>;
-    constexpr int TW = kWinTW, TH = kWinTH, EW = G::EW, EH = G::EH, BW = G::BW, WN = 2 * R + 1;
-    constexpr int SEG = G::SEG, SW = G::SW, SV = G::SV;
-    constexpr bool kF32 = sizeof(T) == 4;
+    constexpr int TW = kWinTW, TH = kWinTH, EW = G::EW, BW = G::BW, WN = 2 * R + 1;
+    constexpr int SEG = G::SEG, SW = G::SW, SV = G::SV, CH = G::CH, NS = G::NS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-    T *box = reinterpret_cast<T *>(smem_raw + 128);  // [5][EH][BW]
-    // field k's column sums: [TH][SW] at sums + k * SFS
-    float *sums = kF32 ? reinterpret_cast<float *>(box) : reinterpret_cast<float *>(smem_raw + 128 + G::box_bytes);
-    constexpr int SFS = kF32 ? EH * BW : TH * SW;
-
-    // row-segment owner of this thread: quarter-warps span 8 rows
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int r = (wp & 3) * 8 + (lane & 7), sg = (wp >> 2) * 4 + (lane >> 3);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
+    uint64_t *empty = full + NS;
+    unsigned char *slots = smem_raw + G::slots_off;
+    float *sums = reinterpret_cast<float *>(smem_raw + G::sums_off);  // [2][TH][SW]
 
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        for (int b = 0; b < NS; b++) {
+            mbar_init(&full[b], 1);
+            mbar_init(&empty[b], kWinConsumers / 32);
+        }
         fence_mbar_init();
     }
     __syncthreads();
-    uint32_t phase = 0;
     const int nfr = bd->nframes;
     const int *off = bd->win_off[level];
     const int total = __ldg(off + nfr);
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    const int mine = total > (int)blockIdx.x ? (total - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+
+    if (threadIdx.x >= kWinConsumers) {
+        // ---- producer: one lane issues the plane copies in order
+        if (threadIdx.x == kWinConsumers) {
+            int i = 0;
+            bool ok = true;
+            for (int j = 0; j < mine && ok; j++) {
+                const int t = blockIdx.x + j * gridDim.x;
+                const int fi = find_frame(off, nfr, t);
+                const FrameDesc &F = bd->f[fi];
+                const int ntx = (F.lw[level] + TW - 1) / TW;
+                const int lt = t - __ldg(off + fi);
+                const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
+                const CUtensorMap *map = &F.gh_map[level];
+                tensormap_acquire(map);
+                for (int k = 0; k < 5; k++, i++) {
+                    const int slot = i % NS;
+                    if (i >= NS && !mbar_wait(&empty[slot], (uint32_t)((i / NS - 1) & 1))) {
+                        atomicExch(bd->err, kErrTmaTimeout);
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async_smem();
+                    mbar_expect_tx(&full[slot], (uint32_t)G::plane_bytes);
+                    tma_load_3d(slots + slot * G::slot_stride, map, x0 - G::XO, y0 - R, k, &full[slot]);
+                }
+            }
+            // No copy may still be writing shared memory when the block leaves.
+            for (int q = i - NS < 0 ? 0 : i - NS; q < i; q++) mbar_wait(&full[q % NS], (uint32_t)((q / NS) & 1));
+        }
+        return;
+    }
+
+    // ---- consumers
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    // column-sum item: chunk cc of ext column ex
+    const int cc = tid / EW, ex = tid - cc * EW;
+    const bool has_item = cc < kWinChunks;
+    const int cs = min(cc * CH, TH - CH);  // first output row of the chunk (the last one may overlap)
+    const int cw = cc * CH;                // rows below this are another chunk's to write
+    // row-segment owner: quarter-warps span 8 rows
+    const int r = (wp & 3) * 8 + (lane & 7), sg = (wp >> 2) * 4 + (lane >> 3);
+    int i = 0;
+    for (int j = 0; j < mine; j++) {
+        const int t = blockIdx.x + j * gridDim.x;
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
         const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
         const int ntx = (w + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
         const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
-        if (threadIdx.x == 0) {
-            const CUtensorMap *map = &F.gh_map[level];
-            tensormap_acquire(map);
-            fence_proxy_async_smem();
-            mbar_expect_tx(bar, (uint32_t)G::box_bytes);
-            tma_load_3d(box, map, x0 - G::XO, y0 - R, 0, bar);
-        }
-        const bool ok = mbar_wait(bar, phase);
-        if (__syncthreads_or(!ok)) {
-            // Give up: flag the batch, give the copy one more bounded wait, leave.
-            if (threadIdx.x == 0) atomicExch(bd->err, kErrTmaTimeout);
-            mbar_wait(bar, phase);
-            return;
-        }
-        phase ^= 1u;
 
-        // vertical sums of every ext column, two rounds of fields
+        float acc[5][SEG];
 #pragma unroll
-        for (int round = 0; round < 2; round++) {
-            const int k0 = round ? 3 : 0, nk = round ? 2 : 3;
-            const int k = k0 + (int)threadIdx.x / EW, ex = (int)threadIdx.x % EW;
-            const bool mine = (int)threadIdx.x < nk * EW;
-            float sm[TH];
-            if (mine) {
-                const T *col = box + k * EH * BW + ex + (G::XO - R);
-                float v[EH];
+        for (int k = 0; k < 5; k++, i++) {
+            const int slot = i % NS;
+            float *sb = sums + (i & 1) * (TH * SW);
+            const bool ok = mbar_wait(&full[slot], (uint32_t)((i / NS) & 1));
+            if (ok && has_item) {
+                const T *col = reinterpret_cast<const T *>(slots + slot * G::slot_stride) + cs * BW + ex + (G::XO - R);
+                float v[CH + 2 * R], sm[CH];
 #pragma unroll
-                for (int j = 0; j < EH; j++) v[j] = (float)col[j * BW];
-                box_sums<EH, WN>(v, sm);
+                for (int q = 0; q < CH + 2 * R; q++) v[q] = (float)col[q * BW];
+                box_sums<CH + 2 * R, WN>(v, sm);
+                float *dcol = sb + cs * SW + ex;
+#pragma unroll
+                for (int q = 0; q < CH; q++)
+                    if (cs + q >= cw) dcol[q * SW] = sm[q];
             }
-            if (kF32) __syncthreads();  // every column of the round is read before the packed sums overwrite it
-            if (mine) {
-                float *dcol = sums + k * SFS + ex;
-#pragma unroll
-                for (int j = 0; j < TH; j++) dcol[j * SW] = sm[j];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+            if (named_sync_or(1, kWinConsumers, !ok)) {
+                if (tid == 0) atomicExch(bd->err, kErrTmaTimeout);
+                return;
             }
+            // horizontal sums of this plane for the thread's 8 outputs
+            const float4 *row = reinterpret_cast<const float4 *>(sb + r * SW + sg * SEG);
+            float v[4 * SV], sm[SEG];
+#pragma unroll
+            for (int q = 0; q < SV; q++) {
+                const float4 u = row[q];
+                v[4 * q] = u.x;
+                v[4 * q + 1] = u.y;
+                v[4 * q + 2] = u.z;
+                v[4 * q + 3] = u.w;
+            }
+            const float(&vv)[SEG + 2 * R] = *reinterpret_cast<const float(*)[SEG + 2 * R]>(v);
+            box_sums<SEG + 2 * R, WN>(vv, sm);
+#pragma unroll
+            for (int q = 0; q < SEG; q++) acc[k][q] = sm[q];
         }
-        __syncthreads();
 
-        {
-            const int gy = y0 + r, gxs = x0 + sg * SEG;
-            if (gy < h && gxs < w) {
-                float acc[5][SEG];
+        const int gy = y0 + r, gxs = x0 + sg * SEG;
+        if (gy < h && gxs < w) {
+            // With c = the window's in-image pixel count, G_ = S_G / c and
+            // h_ = S_h / c, so adj(G_) h_ / (det G_ + lambda) =
+            // adj(S_G) S_h / (det S_G + lambda c^2): one division.
+            const int cy = min(gy + R, h - 1) - max(gy - R, 0) + 1;
+            float2 *frow = F.flow[dst] + (size_t)gy * p + gxs;
+            const bool whole = gxs + SEG <= w;
 #pragma unroll
-                for (int k = 0; k < 5; k++) {
-                    const float4 *row = reinterpret_cast<const float4 *>(sums + k * SFS + r * SW + sg * SEG);
-                    float v[4 * SV], sm[SEG];
+            for (int q = 0; q < SEG; q += 2) {
+                float d[4];
 #pragma unroll
-                    for (int q = 0; q < SV; q++) {
-                        const float4 u = row[q];
-                        v[4 * q] = u.x;
-                        v[4 * q + 1] = u.y;
-                        v[4 * q + 2] = u.z;
-                        v[4 * q + 3] = u.w;
-                    }
-                    const float(&vv)[SEG + 2 * R] = *reinterpret_cast<const float(*)[SEG + 2 * R]>(v);
-                    box_sums<SEG + 2 * R, WN>(vv, sm);
-#pragma unroll
-                    for (int j = 0; j < SEG; j++) acc[k][j] = sm[j];
+                for (int e = 0; e < 2; e++) {
+                    const int gx = gxs + q + e;
+                    const int cx = min(gx + R, w - 1) - max(gx - R, 0) + 1;
+                    const float c = (float)(cx * cy);
+                    const float g11 = acc[0][q + e], g12 = acc[1][q + e], g22 = acc[2][q + e];
+                    const float h1 = acc[3][q + e], h2 = acc[4][q + e];
+                    const float idet = 1.f / (diff_of_products(g11, g22, g12, g12) + mc.lambda * c * c);
+                    d[2 * e] = diff_of_products(g22, h1, g12, h2) * idet;
+                    d[2 * e + 1] = diff_of_products(g11, h2, g12, h1) * idet;
                 }
-                // With c = the window's in-image pixel count, G_ = S_G / c and
-                // h_ = S_h / c, so adj(G_) h_ / (det G_ + lambda) =
-                // adj(S_G) S_h / (det S_G + lambda c^2): one division.
-                const int cy = min(gy + R, h - 1) - max(gy - R, 0) + 1;
-                float2 *frow = F.flow[dst] + (size_t)gy * p + gxs;
-                const bool whole = gxs + SEG <= w;
-#pragma unroll
-                for (int j = 0; j < SEG; j += 2) {
-                    float d[4];
-#pragma unroll
-                    for (int e = 0; e < 2; e++) {
-                        const int gx = gxs + j + e;
-                        const int cx = min(gx + R, w - 1) - max(gx - R, 0) + 1;
-                        const float c = (float)(cx * cy);
-                        const float g11 = acc[0][j + e], g12 = acc[1][j + e], g22 = acc[2][j + e];
-                        const float h1 = acc[3][j + e], h2 = acc[4][j + e];
-                        const float idet = 1.f / (diff_of_products(g11, g22, g12, g12) + mc.lambda * c * c);
-                        d[2 * e] = diff_of_products(g22, h1, g12, h2) * idet;
-                        d[2 * e + 1] = diff_of_products(g11, h2, g12, h1) * idet;
-                    }
-                    if (whole) {
-                        *reinterpret_cast<float4 *>(frow + j) = make_float4(d[0], d[1], d[2], d[3]);
-                    } else {
-                        if (gxs + j < w) frow[j] = make_float2(d[0], d[1]);
-                        if (gxs + j + 1 < w) frow[j + 1] = make_float2(d[2], d[3]);
-                    }
+                if (whole) {
+                    *reinterpret_cast<float4 *>(frow + q) = make_float4(d[0], d[1], d[2], d[3]);
+                } else {
+                    if (gxs + q < w) frow[q] = make_float2(d[0], d[1]);
+                    if (gxs + q + 1 < w) frow[q + 1] = make_float2(d[2], d[3]);
                 }
             }
         }
-        __syncthreads();
     }
 }
 
@@ -320,7 +368,7 @@ template <typename T, int R>
 static void launch_window_t(const BatchDesc *bd, const MethodConsts &mc, int level, int dst, int grid, cudaStream_t s)
 {
     // The dynamic shared-memory limit was raised by occ_window_t at set-up.
-    k_window<T, R><<<grid, 256, WinGeom<T, R>::smem, s>>>(bd, mc, level, dst);
+    k_window<T, R><<<grid, kWinThreads, WinGeom<T, R>::smem, s>>>(bd, mc, level, dst);
 }
 
 template <typename T, int R>
@@ -329,7 +377,7 @@ static int occ_window_t()
     const size_t sm = WinGeom<T, R>::smem;
     cudaFuncSetAttribute(k_window<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_window<T, R>, 256, sm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_window<T, R>, kWinThreads, sm);
     return b;
 }
 

@@ -312,7 +312,7 @@ bool encode_stream_maps(flowroi_ctx *c, Stream *s)
     for (int l = 0; l < c->cfg.pyr_levels; l++) {
         const uint64_t dims[3] = {(uint64_t)s->lw[l], (uint64_t)s->lh[l], 5};
         const uint64_t strides[2] = {(uint64_t)s->lp[l] * esz, (uint64_t)s->lp[l] * s->lh[l] * esz};
-        const uint32_t box[3] = {(uint32_t)bw, (uint32_t)eh, 5};
+        const uint32_t box[3] = {(uint32_t)bw, (uint32_t)eh, 1};  // one plane per copy
         if (!tma_encode(&s->gh_map[l], c->half, 3, s->gh[l], dims, strides, box)) return false;
     }
     return true;

@@ -49,6 +49,29 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const void *map, int c0, 
         : "memory");
 }
 
+// Plain arrival (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier over `nthreads` threads only (named barrier `id`, a multiple of
+// 32 threads), and the same barrier with an OR reduction of a predicate.
+__device__ __forceinline__ void named_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred pi, po;\n setp.ne.u32 pi, %1, 0;\n bar.red.or.pred po, %2, %3, pi;\n selp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
 // Bounded wait for phase `parity` of the mbarrier; true when it completed.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 {
