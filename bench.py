@@ -201,11 +201,24 @@ def submit(F, ctx, sid, data, idx, bd):
             time.sleep(50e-6)
 
 
+def submit_all(F, ctx, items):
+    """Submit (stream, data, frame_idx, bit_depth) items as one batch,
+    retrying the tail while a stream's ring is still busy."""
+    while items:
+        k, st = F.flowroi_submit_frames(ctx, items)
+        items = items[k:]
+        if not items:
+            return
+        if st != F.EBUSY:
+            raise F.FlowRoIError(st, F.flowroi_last_error(ctx))
+        time.sleep(50e-6)
+
+
 def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampler_device=None):
     """Device-resident run: returns dict(time_s, frames, launches, kernel_times, stats, clocks)."""
     import torch
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
-               precision=wl["precision"], max_batch_frames=64, result_ring=4,
+               precision=wl["precision"], max_batch_frames=64, result_ring=8,
                flags=F.MANUAL | (F.PLAIN if plain else 0), device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     res = {}
@@ -216,8 +229,7 @@ def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampl
         def one_step():
             nonlocal t
             i = frame_index(t, n)
-            for s in range(S):
-                submit(F, ctx.h, s, frames[s][i], t, bd)
+            submit_all(F, ctx.h, [(s, frames[s][i], t, bd) for s in range(S)])
             if plain:
                 while F.flowroi_step(ctx.h) > 0:
                     pass
@@ -270,7 +282,7 @@ def run_e2e(F, wl, frames, steps, warmup):
     masks = [torch.empty((h, w), dtype=torch.uint8).pin_memory() for _ in range(S)]
     coefs = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(S)]
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
-               precision=wl["precision"], max_batch_frames=64, result_ring=4, flags=F.MANUAL,
+               precision=wl["precision"], max_batch_frames=64, result_ring=8, flags=F.MANUAL,
                device=torch.cuda.current_device())
     res = {}
     with F.Context(**cfg) as ctx:
@@ -279,8 +291,7 @@ def run_e2e(F, wl, frames, steps, warmup):
         def submit_step():
             nonlocal t
             i = frame_index(t, nh)
-            for s in range(S):
-                submit(F, ctx.h, s, host[s][i], t, bd)
+            submit_all(F, ctx.h, [(s, host[s][i], t, bd) for s in range(S)])
             F.flowroi_step(ctx.h)
             t += 1
 

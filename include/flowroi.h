@@ -176,6 +176,19 @@ FLOWROI_API int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out);
  * are the plain (unshifted) JPEG2000 front end. */
 FLOWROI_API int flowroi_submit_frame(flowroi_ctx *ctx, int64_t stream_id, const flowroi_frame *f);
 
+/* Submit n frames, frames[k] to stream stream_ids[k], in order, with the
+ * rules of flowroi_submit_frame for each; the copies are queued back to
+ * back and waited for once (one wait per batch of wells instead of one per
+ * frame).  Returns the number of frames accepted, k <= n: frames [0, k)
+ * are submitted and their buffers may be reused; when k < n, frames[k] was
+ * refused with *status (if status is not NULL: FLOWROI_EBUSY,
+ * FLOWROI_EINVAL, ...) and flowroi_last_error says why, and frames after
+ * it were not looked at.  Negative on a NULL ctx, n < 0 or a NULL array
+ * (FLOWROI_EINVAL), with nothing submitted.  *status is FLOWROI_OK when
+ * all n were accepted. */
+FLOWROI_API int flowroi_submit_frames(flowroi_ctx *ctx, int n, const int64_t *stream_ids, const flowroi_frame *frames,
+                                      int *status);
+
 /* Launch one batch now: for every stream with a pending frame, its oldest
  * one, at most max_batch_frames frames (FLOWROI_PLAIN: one frame per
  * launch sequence, still all pending streams).  Returns the number of

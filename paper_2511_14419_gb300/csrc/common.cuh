@@ -15,7 +15,7 @@ constexpr int kHistBins = 2048;  // radix-select digit of 11 bits
 constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 
 // Tile shapes (output pixels per block) of each kernel family.
-constexpr int kExpTW = 64, kExpTH = 16;   // pyramid + polynomial expansion
+constexpr int kExpTW = 256, kExpTH = 16;   // pyramid + polynomial expansion
 constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
 constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
 constexpr int kSalTW = 64, kSalTH = 16;   // saliency, radix-select passes

@@ -23,9 +23,9 @@
 // four bands of the level, i.e. a 2*TW x 2*TH input block plus a 4-sample
 // apron loaded with the symmetric extension (for the 4-step 9/7 cone;
 // 5/3 needs 2).  Each column of the extended tile is lifted in a thread's
-// registers; then each (row, 16-coefficient segment) is lifted in
-// registers from a 40-sample window of that row and its coefficients are
-// quantised, shifted and stored.  Outputs come from window centres, which
+// registers; then each (row, 16-sample segment) is lifted in registers
+// from a 24-sample window of that row and its 8 low and 8 high
+// coefficients are quantised, shifted and stored.  Outputs come from window centres, which
 // depend only on in-window samples.  The low-low band goes to a temporary
 // plane for the next level (or, at the last level, into the coefficient
 // plane).
@@ -40,6 +40,9 @@ namespace {
 
 constexpr float kA = -1.586134342059924f, kB = -0.052980118572961f, kG = 0.882911075530934f,
                 kD = 0.443506852043971f, kK = 1.230174104914001f;
+// 1/K rounded to float: low samples are scaled by a product (one more
+// rounding than a division, far inside the 9/7 coefficient tolerance).
+constexpr float kInvK = (float)(1.0 / 1.230174104914001);
 constexpr int kDwtHalo = 4;
 
 // Whole-sample symmetric extension of index i into [0, n).  One
@@ -72,6 +75,14 @@ __device__ __forceinline__ int32_t quantise(V y, float delta, int wav)
 
 __device__ __forceinline__ int32_t roi_up(int32_t q, int s) { return q < 0 ? -((-q) << s) : (q << s); }
 
+// The low-low plane's 32-bit words as the level's sample type.
+template <typename V>
+__device__ __forceinline__ V __int_as_float_or_int(uint32_t u)
+{
+    if constexpr (std::is_same<V, float>::value) return __uint_as_float(u);
+    else return (V)u;
+}
+
 }  // namespace
 
 // One 1-D lifting pass over N register values (x[0] has even parity).
@@ -89,7 +100,7 @@ __device__ __forceinline__ void lift97(float (&x)[N])
 #pragma unroll
     for (int i = 2; i < N - 1; i += 2) x[i] += kD * (x[i - 1] + x[i + 1]);
 #pragma unroll
-    for (int i = 0; i < N; i++) x[i] = (i & 1) ? x[i] * kK : __fdiv_rn(x[i], kK);
+    for (int i = 0; i < N; i++) x[i] *= (i & 1) ? kK : kInvK;
 }
 
 template <int N>
@@ -110,12 +121,13 @@ __device__ __forceinline__ void lift(V (&x)[N])
 
 // 1-D mask rule on a register window: low k from [2k+lo0, 2k+lo1], high k
 // from [2k+hi0, 2k+hi1] (relative to the window's even sample e = HALO+2k).
-template <int WAV, int N>
-__device__ __forceinline__ void mask_rule(const uint8_t (&m)[N], int e, uint8_t &lo, uint8_t &hi)
+// Applied to 0/1 bytes, or to words of four such bytes (four columns).
+template <int WAV, typename M, int N>
+__device__ __forceinline__ void mask_rule(const M (&m)[N], int e, M &lo, M &hi)
 {
     constexpr int lo0 = WAV == 97 ? -3 : -1, lo1 = WAV == 97 ? 3 : 1;
     constexpr int hi0 = WAV == 97 ? -3 : -1, hi1 = WAV == 97 ? 5 : 3;
-    uint8_t a = 0, b = 0;
+    M a = 0, b = 0;
 #pragma unroll
     for (int d = lo0; d <= lo1; d++) a |= m[e + d];
 #pragma unroll
@@ -124,12 +136,12 @@ __device__ __forceinline__ void mask_rule(const uint8_t (&m)[N], int e, uint8_t 
     hi = b;
 }
 
-template <int WAV>
+template <int WAV, bool L1>
 __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
     using V = typename std::conditional<WAV == 97, float, int>::type;
     constexpr int TW = kDwtTW, TH = kDwtTH, HALO = kDwtHalo;
-    constexpr int EW = 2 * TW + 2 * HALO, EH = 2 * TH + 2 * HALO;  // 136 x 72
+    constexpr int EW = 2 * TW + 2 * HALO, EH = 2 * TH + 2 * HALO;  // 136 x 40
     constexpr int SEG = 8;                                          // band outputs per row item
     constexpr int RW = 2 * SEG + 2 * HALO;                          // row window (24)
     __shared__ V s_x[EH][EW + 1];
@@ -164,57 +176,57 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         // Load: samples with symmetric extension, mask clipped (0 outside).
         // Two adjacent columns per item (ix0 is even, so an in-range pair is
         // one aligned 2-sample / 2-byte load); a thread issues all of its
-        // items' loads before any shared-memory store.
+        // items' loads before any shared-memory store, holding level-1 sample
+        // pairs packed in one word and every mask pair as two 0/1 bytes.
         {
             const bool xin = ix0 >= 0 && ix0 + EW <= iw;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             constexpr int NR = (EH + 7) / 8, NP = (EW / 2 + 31) / 32;
-            V v[NR][NP][2];
-            uint8_t mm[NR][NP][2];
+            constexpr int NV = L1 ? 1 : 2;  // registers per sample pair
+            uint32_t sv[NR][NP][NV];
+            uint32_t mm[NR][NP];
 #pragma unroll
             for (int i = 0; i < NR; i++) {
                 const int r = warp + 8 * i;
                 const int gy = iy0 + r, my = mirror(gy, ih);
                 const bool rin = gy >= 0 && gy < ih;
-                const uint8_t *mrow = level == 1 ? fmask + (size_t)gy * W : mlin + (size_t)gy * iw;
+                const uint8_t *mrow = L1 ? fmask + (size_t)gy * W : mlin + (size_t)gy * iw;
 #pragma unroll
                 for (int j = 0; j < NP; j++) {
                     const int c = 2 * (lane + 32 * j), gx = ix0 + c;
-                    v[i][j][0] = v[i][j][1] = (V)0;
-                    mm[i][j][0] = mm[i][j][1] = 0;
+#pragma unroll
+                    for (int e = 0; e < NV; e++) sv[i][j][e] = 0u;
+                    mm[i][j] = 0u;
                     if (r >= EH || c >= EW) continue;
-                    if (level == 1) {
+                    if constexpr (L1) {
                         const uint8_t *row = fraw + (size_t)my * raw_pitch;
-                        int r0, r1;
                         if (xin && bpp == 2) {
-                            const unsigned pr = __ldg(reinterpret_cast<const unsigned *>(row) + (gx >> 1));
-                            r0 = (int)(pr & 0xffffu);
-                            r1 = (int)(pr >> 16);
+                            sv[i][j][0] = __ldg(reinterpret_cast<const unsigned *>(row) + (gx >> 1));
                         } else {
                             const int m0 = mirror(gx, iw), m1 = mirror(gx + 1, iw);
-                            r0 = bpp == 1 ? (int)__ldg(row + m0) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m0);
-                            r1 = bpp == 1 ? (int)__ldg(row + m1) : (int)__ldg(reinterpret_cast<const uint16_t *>(row) + m1);
+                            const uint32_t r0 = bpp == 1 ? __ldg(row + m0) : __ldg(reinterpret_cast<const uint16_t *>(row) + m0);
+                            const uint32_t r1 = bpp == 1 ? __ldg(row + m1) : __ldg(reinterpret_cast<const uint16_t *>(row) + m1);
+                            sv[i][j][0] = r0 | (r1 << 16);
                         }
-                        v[i][j][0] = (V)(r0 - dc_off);
-                        v[i][j][1] = (V)(r1 - dc_off);
                     } else {
-                        const V *row = llin + (size_t)my * iw;
+                        const uint32_t *row = reinterpret_cast<const uint32_t *>(llin) + (size_t)my * iw;
                         if (xin) {
-                            v[i][j][0] = __ldg(row + gx);
-                            v[i][j][1] = __ldg(row + gx + 1);
+                            const uint2 pr = __ldg(reinterpret_cast<const uint2 *>(row + gx));
+                            sv[i][j][0] = pr.x;
+                            sv[i][j][1] = pr.y;
                         } else {
-                            v[i][j][0] = __ldg(row + mirror(gx, iw));
-                            v[i][j][1] = __ldg(row + mirror(gx + 1, iw));
+                            sv[i][j][0] = __ldg(row + mirror(gx, iw));
+                            sv[i][j][1] = __ldg(row + mirror(gx + 1, iw));
                         }
                     }
                     if (rin) {
                         if (xin) {
-                            const unsigned short m2 = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
-                            mm[i][j][0] = (uint8_t)(m2 & 0xff);
-                            mm[i][j][1] = (uint8_t)(m2 >> 8);
+                            const uint32_t m2 = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
+                            mm[i][j] = ((m2 & 0xffu) != 0) | (((m2 >> 8) != 0) << 8);
                         } else {
-                            if (gx >= 0 && gx < iw) mm[i][j][0] = __ldg(mrow + gx);
-                            if (gx + 1 >= 0 && gx + 1 < iw) mm[i][j][1] = __ldg(mrow + gx + 1);
+                            const uint32_t m0 = gx >= 0 && gx < iw ? __ldg(mrow + gx) : 0;
+                            const uint32_t m1 = gx + 1 >= 0 && gx + 1 < iw ? __ldg(mrow + gx + 1) : 0;
+                            mm[i][j] = (m0 != 0) | ((m1 != 0) << 8);
                         }
                     }
                 }
@@ -225,17 +237,22 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
                 for (int j = 0; j < NP; j++) {
                     const int r = warp + 8 * i, c = 2 * (lane + 32 * j);
                     if (r >= EH || c >= EW) continue;
-                    s_x[r][c] = v[i][j][0];
-                    s_x[r][c + 1] = v[i][j][1];
-                    s_m[r][c] = mm[i][j][0];
-                    s_m[r][c + 1] = mm[i][j][1];
+                    if constexpr (L1) {
+                        s_x[r][c] = (V)((int)(sv[i][j][0] & 0xffffu) - dc_off);
+                        s_x[r][c + 1] = (V)((int)(sv[i][j][0] >> 16) - dc_off);
+                    } else {
+                        s_x[r][c] = __int_as_float_or_int<V>(sv[i][j][0]);
+                        s_x[r][c + 1] = __int_as_float_or_int<V>(sv[i][j][1]);
+                    }
+                    *reinterpret_cast<uint16_t *>(&s_m[r][c]) = (uint16_t)mm[i][j];
                 }
         }
         __syncthreads();
 
         // Vertical: threads [0, EW) lift one column each in registers; the
-        // other threads turn columns of the pixel mask into (low, high) row
-        // masks with the 1-D rule, in place (a column is private to its item).
+        // next EW/4 threads turn four columns of the pixel mask at a time
+        // (the byte lanes of a word) into (low, high) row masks with the 1-D
+        // rule, in place (the columns are private to their item).
         if (threadIdx.x < EW) {
             const int c = threadIdx.x;
             V x[EH];
@@ -244,60 +261,97 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
             lift<V, EH>(x);
 #pragma unroll
             for (int j = 0; j < EH; j++) s_x[j][c] = x[j];
-        } else {
-            for (int c = threadIdx.x - EW; c < EW; c += blockDim.x - EW) {
-                uint8_t m[EH];
+        } else if (threadIdx.x < EW + EW / 4) {
+            const int c = 4 * (threadIdx.x - EW);
+            uint32_t m[EH];
 #pragma unroll
-                for (int j = 0; j < EH; j++) m[j] = s_m[j][c];
+            for (int j = 0; j < EH; j++) m[j] = *reinterpret_cast<const uint32_t *>(&s_m[j][c]);
 #pragma unroll
-                for (int k = 0; k < TH; k++) {
-                    uint8_t lo, hi;
-                    mask_rule<WAV, EH>(m, HALO + 2 * k, lo, hi);
-                    s_m[HALO + 2 * k][c] = lo;       // even rows: low-vertical mask
-                    s_m[HALO + 2 * k + 1][c] = hi;   // odd rows: high-vertical mask
-                }
+            for (int k = 0; k < TH; k++) {
+                uint32_t lo, hi;
+                mask_rule<WAV>(m, HALO + 2 * k, lo, hi);
+                *reinterpret_cast<uint32_t *>(&s_m[HALO + 2 * k][c]) = lo;      // even rows: low-vertical mask
+                *reinterpret_cast<uint32_t *>(&s_m[HALO + 2 * k + 1][c]) = hi;  // odd rows: high-vertical mask
             }
         }
         __syncthreads();
 
-        // Horizontal: one (output row, 16-coefficient segment) per thread.
+        // Horizontal: one (output row, 16-sample segment) per thread.
         {
-            const int rr = threadIdx.x / (TW / SEG), sg = threadIdx.x - rr * (TW / SEG);  // rr in [0, 2*TH)
+            // a warp takes 16 consecutive rows x 2 segments: with the odd row
+            // stride of s_x its 32 window reads fall in 32 different banks
+            static_assert(2 * TH == 32 && TW / SEG == 8, "row-item map");
+            const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+            const int rr = (wq & 1) * 16 + (lane & 15), sg = (wq >> 1) * 2 + (lane >> 4);  // rr in [0, 2*TH)
             const int row = HALO + rr;         // even: low-vertical row, odd: high
             const int gj = by0 + (rr >> 1);
             const int c0 = sg * 2 * SEG;       // window start (covers its apron)
             if (rr < 2 * TH && gj < bh) {
                 V x[RW];
-                uint8_t m[RW];
 #pragma unroll
-                for (int j = 0; j < RW; j++) { x[j] = s_x[row][c0 + j]; m[j] = s_m[row][c0 + j]; }
+                for (int j = 0; j < RW; j++) x[j] = s_x[row][c0 + j];
+                // the RW mask bytes (0/1) of the window as bits 0..RW-1
+                uint32_t mb = 0;
+#pragma unroll
+                for (int q = 0; q < RW / 4; q++) {
+                    const uint32_t wq = *reinterpret_cast<const uint32_t *>(&s_m[row][c0 + 4 * q]);
+                    mb |= ((wq * 0x01020408u) >> 24 & 0xfu) << (4 * q);
+                }
                 lift<V, RW>(x);
                 const bool vhigh = rr & 1;
                 const int b_lo = vhigh ? 3 * (level - 1) + 1 : 3 * mc.dwt_levels;  // LH or LL
                 const int b_hi = vhigh ? 3 * (level - 1) + 2 : 3 * (level - 1);    // HH or HL
                 const float d_lo = mc.delta[b_lo], d_hi = mc.delta[b_hi];
                 const int ylo = vhigh ? bh + gj : gj;
+                // the 1-D rule on bits: low k <- [e+lo0, e+lo1], high k <- [e+hi0, e+hi1], e = HALO+2k
+                constexpr int lo0 = WAV == 97 ? -3 : -1, lo1 = WAV == 97 ? 3 : 1;
+                constexpr int hi0 = WAV == 97 ? -3 : -1, hi1 = WAV == 97 ? 5 : 3;
+                constexpr uint32_t lom = (1u << (lo1 - lo0 + 1)) - 1u, him = (1u << (hi1 - hi0 + 1)) - 1u;
+                int32_t qh[SEG], ql[SEG];
 #pragma unroll
                 for (int k = 0; k < SEG; k++) {
-                    const int gi = bx0 + sg * SEG + k;
-                    if (gi >= bw) break;
-                    uint8_t mlo, mhi;
-                    mask_rule<WAV, RW>(m, HALO + 2 * k, mlo, mhi);
+                    const bool mlo = (mb >> (HALO + 2 * k + lo0)) & lom;
+                    const bool mhi = (mb >> (HALO + 2 * k + hi0)) & him;
                     const V ylo_v = x[HALO + 2 * k], yhi_v = x[HALO + 2 * k + 1];
-                    // high horizontal band (HL or HH)
-                    const size_t ph = (size_t)ylo * W + bw + gi;
-                    int32_t q = quantise(yhi_v, d_hi, WAV);
-                    coeffs[ph] = mhi ? roi_up(q, mc.shift) : q;
-                    if constexpr (WAV == 97) { if (dbg_yf) dbg_yf[ph] = yhi_v; }
-                    // low horizontal band (LL or LH)
-                    if (vhigh || last) {
-                        const size_t pl = (size_t)ylo * W + gi;
-                        q = quantise(ylo_v, d_lo, WAV);
-                        coeffs[pl] = mlo ? roi_up(q, mc.shift) : q;
-                        if constexpr (WAV == 97) { if (dbg_yf) dbg_yf[pl] = ylo_v; }
-                    } else {
-                        llout[(size_t)gj * bw + gi] = ylo_v;
-                        llmout[(size_t)gj * bw + gi] = mlo;
+                    const int32_t a = quantise(yhi_v, d_hi, WAV);
+                    qh[k] = mhi ? roi_up(a, mc.shift) : a;
+                    const int32_t b = quantise(ylo_v, d_lo, WAV);
+                    ql[k] = mlo ? roi_up(b, mc.shift) : b;
+                }
+                const int gi0 = bx0 + sg * SEG;
+                const bool lo_band = vhigh || last;  // low horizontal band to the coefficients (LH or LL)
+                int32_t *const ph = coeffs + (size_t)ylo * W + bw + gi0;
+                int32_t *const pl = coeffs + (size_t)ylo * W + gi0;
+                if (gi0 + SEG <= bw && (bw & 3) == 0) {
+#pragma unroll
+                    for (int k = 0; k < SEG; k += 4) {
+                        *reinterpret_cast<int4 *>(ph + k) = make_int4(qh[k], qh[k + 1], qh[k + 2], qh[k + 3]);
+                        if (lo_band) *reinterpret_cast<int4 *>(pl + k) = make_int4(ql[k], ql[k + 1], ql[k + 2], ql[k + 3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < SEG; k++) {
+                        if (gi0 + k >= bw) break;
+                        ph[k] = qh[k];
+                        if (lo_band) pl[k] = ql[k];
+                    }
+                }
+                if (!lo_band) {
+#pragma unroll
+                    for (int k = 0; k < SEG; k++) {
+                        if (gi0 + k >= bw) break;
+                        llout[(size_t)gj * bw + gi0 + k] = x[HALO + 2 * k];
+                        llmout[(size_t)gj * bw + gi0 + k] = (mb >> (HALO + 2 * k + lo0)) & lom ? 1 : 0;
+                    }
+                }
+                if constexpr (WAV == 97) {
+                    if (dbg_yf) {
+#pragma unroll
+                        for (int k = 0; k < SEG; k++) {
+                            if (gi0 + k >= bw) break;
+                            dbg_yf[(size_t)ylo * W + bw + gi0 + k] = x[HALO + 2 * k + 1];
+                            if (lo_band) dbg_yf[(size_t)ylo * W + gi0 + k] = x[HALO + 2 * k];
+                        }
                     }
                 }
             }
@@ -308,16 +362,28 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
 
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s)
 {
-    if (mc.wavelet == 97) k_dwt<97><<<grid, 256, 0, s>>>(bd, mc, level);
-    else k_dwt<53><<<grid, 256, 0, s>>>(bd, mc, level);
+    if (mc.wavelet == 97) {
+        if (level == 1) k_dwt<97, true><<<grid, 256, 0, s>>>(bd, mc, level);
+        else k_dwt<97, false><<<grid, 256, 0, s>>>(bd, mc, level);
+    } else {
+        if (level == 1) k_dwt<53, true><<<grid, 256, 0, s>>>(bd, mc, level);
+        else k_dwt<53, false><<<grid, 256, 0, s>>>(bd, mc, level);
+    }
 }
 
 int occupancy_dwt(int wavelet)
 {
-    int b = 0;
-    if (wavelet == 97) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97>, 256, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53>, 256, 0);
-    return b;
+    // the level-1 and later-level kernels have the same shared memory and
+    // register bound; take the smaller occupancy of the two
+    int a = 0, b = 0;
+    if (wavelet == 97) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false>, 256, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false>, 256, 0);
+    }
+    return a < b ? a : b;
 }
 
 }  // namespace flowroi

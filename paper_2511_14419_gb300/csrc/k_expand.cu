@@ -56,120 +56,146 @@ struct LevelSrc {
 
 }  // namespace
 
+// One block per kExpTW x kExpTH tile (kExpTW = the block's 256 threads):
+// the tile plus a HALO apron (replicate border) is staged in shared memory
+// once; then each thread walks down its column, forming the three row
+// moments of each row from 2n+1 neighbours and, from a sliding window of
+// 2n+1 rows of them, the six window moments of each output pixel, all in
+// registers.  The applicability is even, so both passes fold the taps in
+// symmetric pairs (sums for the even moments, differences for the odd).
+// The next pyramid level's even samples are blurred from the same staged
+// tile: a row pass at even columns into a second buffer, then a column
+// pass at even rows.
 template <typename T, int NH>
-__global__ void __launch_bounds__(256) k_expand(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
+__global__ void __launch_bounds__(256, 4) k_expand(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
+    constexpr int TW = kExpTW, TH = kExpTH;
     constexpr int HALO = NH > 2 ? NH : 2;
-    constexpr int IW = kExpTW + 2 * HALO, IH = kExpTH + 2 * HALO;
-    constexpr int RH = kExpTH + 2 * NH;  // rows the column pass needs
-    constexpr int BW = kExpTW / 2;
-    __shared__ float s_in[IH][IW + 1];
-    __shared__ float s_g[3][RH][kExpTW + 1];
-    __shared__ float s_blur[IH][BW + 1];
+    constexpr int IW = TW + 2 * HALO, IH = TH + 2 * HALO;
+    constexpr int BW = TW / 2, HR = IH / 2;
+    constexpr int NLD = (IH * IW + TW - 1) / TW;  // staged elements per thread
+    static_assert(TW == 256 && IW % 2 == 0 && IH % 2 == 0, "tile geometry");
+    __shared__ __align__(16) float s_in[IH][IW];
+    __shared__ float s_hb[IH][BW];
     using ST = Store<T>;
     using T4 = typename ST::T4;
-    const float b5[5] = {1.f / 16, 4.f / 16, 6.f / 16, 4.f / 16, 1.f / 16};
+
+    // applicability taps a(u) and their first / second moments, u = 1..n
+    float a0 = mc.app[NH], au[NH + 1], au1[NH + 1], au2[NH + 1];
+#pragma unroll
+    for (int u = 1; u <= NH; u++) {
+        au[u] = mc.app[NH + u];
+        au1[u] = (float)u * au[u];
+        au2[u] = (float)(u * u) * au[u];
+    }
 
     const int nfr = bd->nframes;
     const int *off = bd->exp_off[level];
     const int total = __ldg(off + nfr);
     const bool pyr_next = level + 1 < mc.pyr_levels;
+    const int tid = threadIdx.x;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
         const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
-        const int ntx = (w + kExpTW - 1) / kExpTW;
+        const int ntx = (w + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
-        const int x0 = (lt % ntx) * kExpTW, y0 = (lt / ntx) * kExpTH;
+        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
         // A per-tile constant is removed before the fit (the fit of a
         // constant is that constant: A and b are unchanged) to keep the
         // single-precision moments small.
         const LevelSrc<T> src(F, level);
         T4 *fq = static_cast<T4 *>(F.fq_cur[level]);
         T *fb = static_cast<T *>(F.fb_cur[level]);
-        T *pdst = pyr_next ? static_cast<T *>(F.pyr[level + 1]) : nullptr;
-        const int wn = pyr_next ? F.lw[level + 1] : 0, hn = pyr_next ? F.lh[level + 1] : 0, pn = pyr_next ? F.lp[level + 1] : 0;
-        const float c0 = src.at(min(x0 + kExpTW / 2, w - 1), min(y0 + kExpTH / 2, h - 1));
+        const float c0 = src.at(min(x0 + TW / 2, w - 1), min(y0 + TH / 2, h - 1));
         {
-            // All of a thread's loads first (up to 3 rows x 3 columns), then
-            // the shared-memory stores, so the loads are in flight together.
-            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-            float v[3][3];
+            // every load of the thread first, then the shared-memory stores
+            float v[NLD];
 #pragma unroll
-            for (int i = 0; i < 3; i++)
+            for (int i = 0; i < NLD; i++) {
+                const int e = i * TW + tid, r = e / IW, cc = e - r * IW;
+                v[i] = 0.f;
+                if (e < IH * IW) {
+                    const int gy = clampi(y0 - HALO + r, 0, h - 1), gx = clampi(x0 - HALO + cc, 0, w - 1);
+                    v[i] = src.at(gx, gy);
+                }
+            }
 #pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    const int r = ty + 8 * i, c = tx + 32 * j;
-                    v[i][j] = 0.f;
-                    if (r < IH && c < IW) {
-                        const int gy = clampi(y0 - HALO + r, 0, h - 1), gx = clampi(x0 - HALO + c, 0, w - 1);
-                        v[i][j] = src.at(gx, gy);
+            for (int i = 0; i < NLD; i++) {
+                const int e = i * TW + tid, r = e / IW, cc = e - r * IW;
+                if (e < IH * IW) s_in[r][cc] = v[i] - c0;
+            }
+        }
+        __syncthreads();
+
+        // expansion: thread = column, walking down the rows
+        {
+            const int gx = x0 + tid;
+            float m0[IH], m1[IH], m2[IH];  // row moments (only a sliding window stays live)
+#pragma unroll
+            for (int r = HALO - NH; r < HALO + TH + NH; r++) {
+                const float *row = &s_in[r][tid + HALO];
+                float g0 = a0 * row[0], g1 = 0.f, g2 = 0.f;
+#pragma unroll
+                for (int u = 1; u <= NH; u++) {
+                    const float xp = row[u], xm = row[-u];
+                    const float su = xp + xm, du = xp - xm;
+                    g0 = fmaf(au[u], su, g0);
+                    g1 = fmaf(au1[u], du, g1);
+                    g2 = fmaf(au2[u], su, g2);
+                }
+                m0[r] = g0;
+                m1[r] = g1;
+                m2[r] = g2;
+                const int j = r - HALO - NH;  // output row completed by this row
+                if (j >= 0) {
+                    const int cr = HALO + j;
+                    float c00 = a0 * m0[cr], c01 = 0.f, c02 = 0.f, c10 = a0 * m1[cr], c11 = 0.f, c20 = a0 * m2[cr];
+#pragma unroll
+                    for (int q = 1; q <= NH; q++) {
+                        const float s0 = m0[cr + q] + m0[cr - q], d0 = m0[cr + q] - m0[cr - q];
+                        const float s1 = m1[cr + q] + m1[cr - q], d1 = m1[cr + q] - m1[cr - q];
+                        const float s2 = m2[cr + q] + m2[cr - q];
+                        c00 = fmaf(au[q], s0, c00);
+                        c01 = fmaf(au1[q], d0, c01);
+                        c02 = fmaf(au2[q], s0, c02);
+                        c10 = fmaf(au[q], s1, c10);
+                        c11 = fmaf(au1[q], d1, c11);
+                        c20 = fmaf(au[q], s2, c20);
+                    }
+                    const int gy = y0 + j;
+                    if (gx < w && gy < h) {
+                        const float ruu = mc.m_uu[0] * c00 + mc.m_uu[1] * c20 + mc.m_uu[2] * c02;
+                        const float rvv = mc.m_vv[0] * c00 + mc.m_vv[1] * c20 + mc.m_vv[2] * c02;
+                        const float ruv = c11 * mc.inv_s2s2;
+                        const size_t o = (size_t)gy * p + gx;
+                        ST::st4(fq + o, ruu, 0.5f * ruv, rvv, c10 * mc.inv_s0s2);
+                        ST::st(fb + o, c01 * mc.inv_s0s2);
                     }
                 }
-#pragma unroll
-            for (int i = 0; i < 3; i++)
-#pragma unroll
-                for (int j = 0; j < 3; j++) {
-                    const int r = ty + 8 * i, c = tx + 32 * j;
-                    if (r < IH && c < IW) s_in[r][c] = v[i][j] - c0;
-                }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < RH * kExpTW; i += blockDim.x) {
-            const int r = i / kExpTW, c = i - r * kExpTW;
-            const float *row = &s_in[r + HALO - NH][c + HALO - NH];
-            float g0 = 0.f, g1 = 0.f, g2 = 0.f;
-#pragma unroll
-            for (int u = -NH; u <= NH; u++) {
-                const float av = mc.app[u + NH] * row[u + NH];
-                g0 += av;
-                g1 += (float)u * av;
-                g2 += (float)(u * u) * av;
             }
-            s_g[0][r][c] = g0;
-            s_g[1][r][c] = g1;
-            s_g[2][r][c] = g2;
         }
+
         if (pyr_next) {
-            for (int i = threadIdx.x; i < IH * BW; i += blockDim.x) {
-                const int r = i / BW, k = i - r * BW;
-                const float *row = &s_in[r][HALO + 2 * k - 2];
-                s_blur[r][k] = b5[0] * row[0] + b5[1] * row[1] + b5[2] * row[2] + b5[3] * row[3] + b5[4] * row[4];
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < kExpTH * kExpTW; i += blockDim.x) {
-            const int r = i / kExpTW, c = i - r * kExpTW;
-            const int gx = x0 + c, gy = y0 + r;
-            if (gx >= w || gy >= h) continue;
-            float c00 = 0.f, c01 = 0.f, c02 = 0.f, c10 = 0.f, c11 = 0.f, c20 = 0.f;
+            // [1 4 6 4 1]/16 along rows at even columns (half the rows per thread)
+            const int k = tid & (BW - 1), r0 = (tid / BW) * HR;
 #pragma unroll
-            for (int v = -NH; v <= NH; v++) {
-                const float a = mc.app[v + NH];
-                const float g0 = s_g[0][r + v + NH][c], g1 = s_g[1][r + v + NH][c], g2 = s_g[2][r + v + NH][c];
-                c00 += a * g0;
-                c01 += (a * (float)v) * g0;
-                c02 += (a * (float)(v * v)) * g0;
-                c10 += a * g1;
-                c11 += (a * (float)v) * g1;
-                c20 += a * g2;
+            for (int i = 0; i < HR; i++) {
+                const float *row = &s_in[r0 + i][HALO + 2 * k];
+                s_hb[r0 + i][k] = (6.f * row[0] + 4.f * (row[-1] + row[1]) + (row[-2] + row[2])) * (1.f / 16.f);
             }
-            const float ruu = mc.m_uu[0] * c00 + mc.m_uu[1] * c20 + mc.m_uu[2] * c02;
-            const float rvv = mc.m_vv[0] * c00 + mc.m_vv[1] * c20 + mc.m_vv[2] * c02;
-            const float ruv = c11 * mc.inv_s2s2;
-            const size_t o = (size_t)gy * p + gx;
-            ST::st4(fq + o, ruu, 0.5f * ruv, rvv, c10 * mc.inv_s0s2);
-            ST::st(fb + o, c01 * mc.inv_s0s2);
-        }
-        if (pyr_next) {
-            for (int i = threadIdx.x; i < (kExpTH / 2) * BW; i += blockDim.x) {
-                const int j = i / BW, k = i - j * BW;
-                const int gx = x0 / 2 + k, gy = y0 / 2 + j;
-                if (gx >= wn || gy >= hn) continue;
-                const int r = HALO + 2 * j;
-                const float v = b5[0] * s_blur[r - 2][k] + b5[1] * s_blur[r - 1][k] + b5[2] * s_blur[r][k] +
-                                b5[3] * s_blur[r + 1][k] + b5[4] * s_blur[r + 2][k];
-                ST::st(pdst + (size_t)gy * pn + gx, v + c0);
+            __syncthreads();
+            // ... and along columns at even rows
+            T *pdst = static_cast<T *>(F.pyr[level + 1]);
+            const int wn = F.lw[level + 1], hn = F.lh[level + 1], pn = F.lp[level + 1];
+            const int gi = x0 / 2 + k;
+#pragma unroll
+            for (int q = 0; q < TH / 4; q++) {
+                const int jj = (tid / BW) * (TH / 4) + q, gj = y0 / 2 + jj;
+                const int cr = HALO + 2 * jj;
+                const float vv = (6.f * s_hb[cr][k] + 4.f * (s_hb[cr - 1][k] + s_hb[cr + 1][k]) +
+                                  (s_hb[cr - 2][k] + s_hb[cr + 2][k])) * (1.f / 16.f);
+                if (gi < wn && gj < hn) ST::st(pdst + (size_t)gj * pn + gi, vv + c0);
             }
         }
         __syncthreads();

@@ -349,9 +349,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
                     const float c = (float)(cx * cy);
                     const float g11 = acc[0][q + e], g12 = acc[1][q + e], g22 = acc[2][q + e];
                     const float h1 = acc[3][q + e], h2 = acc[4][q + e];
-                    const float idet = 1.f / (diff_of_products(g11, g22, g12, g12) + mc.lambda * c * c);
-                    d[2 * e] = diff_of_products(g22, h1, g12, h2) * idet;
-                    d[2 * e + 1] = diff_of_products(g11, h2, g12, h1) * idet;
+                    // det + lambda c^2 >= lambda > 0 (G_ is a sum of A^T A), far
+                    // below the range where the fast reciprocal flushes
+                    const float idet = __fdividef(1.f, diff_of_products(g11, g22, g12, g12) + mc.lambda * c * c);
+                    d[2 * e] = fmaf(g22, h1, -g12 * h2) * idet;
+                    d[2 * e + 1] = fmaf(g11, h2, -g12 * h1) * idet;
                 }
                 if (whole) {
                     *reinterpret_cast<float4 *>(frow + q) = make_float4(d[0], d[1], d[2], d[3]);

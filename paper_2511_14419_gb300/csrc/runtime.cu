@@ -132,7 +132,10 @@ struct flowroi_ctx {
     std::map<int64_t, std::unique_ptr<Stream>> streams;
     int64_t rr_cursor = INT64_MIN;
     uint64_t budget = 0, admitted = 0;
-    static constexpr int kDesc = 3;
+    // Descriptor slots: the host can enqueue this many batches ahead of the
+    // device, so a host stall shorter than that many batch times does not
+    // leave the device idle.
+    static constexpr int kDesc = 8;
     BatchDesc *desc_host[kDesc] = {};
     BatchDesc *desc_dev[kDesc] = {};
     cudaEvent_t desc_ev[kDesc] = {};
@@ -518,17 +521,23 @@ int step_locked(flowroi_ctx *c)
         CK(c, cudaGetLastError());
     } else {
         if (!c->graph[k]) {
-            cudaGraph_t gr = nullptr;
-            CK(c, cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeThreadLocal));
-            enqueue_pipeline(c, c->desc_dev[k], &hd, c->s_cap, &nl, false);
-            cudaError_t e1 = cudaGetLastError();
-            cudaError_t e2 = cudaStreamEndCapture(c->s_cap, &gr);
-            if (e1 != cudaSuccess) return cuda_fail(c, e1, "kernel launch during capture");
-            if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
-            cudaError_t e3 = cudaGraphInstantiate(&c->graph[k], gr, 0);
-            cudaGraphDestroy(gr);
-            if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
-            c->graph_launches = nl;
+            // Capture every slot's graph at once (the graphs differ only in
+            // the descriptor they read), so no later step pays for a capture.
+            for (int g = 0; g < flowroi_ctx::kDesc; g++) {
+                if (c->graph[g]) continue;
+                cudaGraph_t gr = nullptr;
+                int ng = 0;
+                CK(c, cudaStreamBeginCapture(c->s_cap, cudaStreamCaptureModeThreadLocal));
+                enqueue_pipeline(c, c->desc_dev[g], &hd, c->s_cap, &ng, false);
+                cudaError_t e1 = cudaGetLastError();
+                cudaError_t e2 = cudaStreamEndCapture(c->s_cap, &gr);
+                if (e1 != cudaSuccess) return cuda_fail(c, e1, "kernel launch during capture");
+                if (e2 != cudaSuccess) return cuda_fail(c, e2, "cudaStreamEndCapture");
+                cudaError_t e3 = cudaGraphInstantiate(&c->graph[g], gr, 0);
+                cudaGraphDestroy(gr);
+                if (e3 != cudaSuccess) return cuda_fail(c, e3, "cudaGraphInstantiate");
+                c->graph_launches = ng;
+            }
         }
         nl = c->graph_launches;
         CK(c, cudaGraphLaunch(c->graph[k], c->s_comp));
@@ -852,9 +861,10 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     return FLOWROI_OK;
 }
 
-int flowroi_submit_frame(flowroi_ctx *c, int64_t stream_id, const flowroi_frame *f)
+// Validates frame f of stream_id and enqueues its copy into the stream's
+// ring (mu taken inside); *ev receives the copy's completion event.
+static int submit_enqueue(flowroi_ctx *c, int64_t stream_id, const flowroi_frame *f, cudaEvent_t *ev)
 {
-    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
     if (!f || f->struct_size != sizeof(flowroi_frame)) return fail(FLOWROI_EINVAL, "frame descriptor NULL or struct_size mismatch");
     if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
     if (f->dtype != FLOWROI_U8 && f->dtype != FLOWROI_U16) return fail(FLOWROI_EINVAL, "frame.dtype must be U8 or U16");
@@ -927,7 +937,10 @@ int flowroi_submit_frame(flowroi_ctx *c, int64_t stream_id, const flowroi_frame 
         e->t_submit = now_ms();
         e->t_done = 0.0;
         const cudaMemcpyKind kind = f->data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        CK(c, cudaMemcpy2DAsync(e->raw, (size_t)s->W * bpp, f->data, pitch, (size_t)s->W * bpp, s->H, kind, c->s_copy));
+        if (pitch == s->W * bpp)  // contiguous rows: one linear copy
+            CK(c, cudaMemcpyAsync(e->raw, f->data, (size_t)s->W * bpp * s->H, kind, c->s_copy));
+        else
+            CK(c, cudaMemcpy2DAsync(e->raw, (size_t)s->W * bpp, f->data, pitch, (size_t)s->W * bpp, s->H, kind, c->s_copy));
         CK(c, cudaEventRecord(e->uploaded, c->s_copy));
         e->state.store(E_PENDING);
         s->next_seq = seq + 1;
@@ -935,10 +948,50 @@ int flowroi_submit_frame(flowroi_ctx *c, int64_t stream_id, const flowroi_frame 
         s->any_frame = true;
         c->frames_submitted++;
     }
+    *ev = e->uploaded;
+    return FLOWROI_OK;
+}
+
+int flowroi_submit_frame(flowroi_ctx *c, int64_t stream_id, const flowroi_frame *f)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    cudaEvent_t ev = nullptr;
+    const int rc = submit_enqueue(c, stream_id, f, &ev);
+    if (rc != FLOWROI_OK) return rc;
     // The caller may reuse its buffer as soon as this returns.
-    CK(c, cudaEventSynchronize(e->uploaded));
+    CK(c, cudaEventSynchronize(ev));
     if (!c->manual) wake_scheduler(c);
     return FLOWROI_OK;
+}
+
+int flowroi_submit_frames(flowroi_ctx *c, int n, const int64_t *stream_ids, const flowroi_frame *frames, int *status)
+{
+    if (status) *status = FLOWROI_OK;
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    if (n < 0 || (n > 0 && (!stream_ids || !frames))) return fail(FLOWROI_EINVAL, "n < 0 or a NULL array");
+    cudaEvent_t last = nullptr;
+    int k = 0;
+    for (; k < n; k++) {
+        cudaEvent_t ev = nullptr;
+        const int rc = submit_enqueue(c, stream_ids[k], &frames[k], &ev);
+        if (rc != FLOWROI_OK) {
+            if (status) *status = rc;
+            break;
+        }
+        last = ev;
+    }
+    // Every accepted copy is on the one copy stream: the last one's event
+    // covers them all.  The caller may reuse those buffers once this returns.
+    if (last) {
+        const cudaError_t e = cudaEventSynchronize(last);
+        if (e != cudaSuccess) {
+            cuda_fail(c, e, "cudaEventSynchronize");
+            if (status) *status = FLOWROI_EDEVICE;
+            return k;
+        }
+    }
+    if (k > 0 && !c->manual) wake_scheduler(c);
+    return k;  // k < n: frames[k] failed with *status, flowroi_last_error says why
 }
 
 int flowroi_step(flowroi_ctx *c)

@@ -22,7 +22,7 @@ KEEP_INTERMEDIATES, PLAIN, MANUAL = 0x1, 0x2, 0x4
 I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD = 1, 2, 3, 4, 5
 
 EXPORTS = [
-    "flowroi_abi_version", "flowroi_default_config", "flowroi_create", "flowroi_submit_frame",
+    "flowroi_abi_version", "flowroi_default_config", "flowroi_create", "flowroi_submit_frame", "flowroi_submit_frames",
     "flowroi_step", "flowroi_get_mask", "flowroi_get_coeffs", "flowroi_get_intermediate",
     "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
@@ -87,6 +87,8 @@ def lib() -> ctypes.CDLL:
             "flowroi_default_config": (None, [ctypes.POINTER(flowroi_config)]),
             "flowroi_create": (I, [ctypes.POINTER(flowroi_config), ctypes.POINTER(P)]),
             "flowroi_submit_frame": (I, [P, I64, ctypes.POINTER(flowroi_frame)]),
+            "flowroi_submit_frames": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(flowroi_frame),
+                                          ctypes.POINTER(I)]),
             "flowroi_step": (I, [P]),
             "flowroi_get_mask": (I, [P, I64, I64, P, I, I]),
             "flowroi_get_coeffs": (I, [P, I64, I64, P, I, I]),
@@ -158,6 +160,28 @@ def flowroi_submit_frame(ctx, stream_id: int, data, frame_idx: int, bit_depth: i
     f = flowroi_frame(ctypes.sizeof(flowroi_frame), w, h, pitch_bytes, U8 if esz == 1 else U16, bit_depth,
                       frame_idx, p, dev)
     return _check(lib().flowroi_submit_frame(ctx, stream_id, ctypes.byref(f)), ctx)
+
+
+def _frame(data, frame_idx: int, bit_depth: int, pitch_bytes: int = 0) -> "flowroi_frame":
+    h, w = int(data.shape[0]), int(data.shape[1])
+    esz = data.itemsize if hasattr(data, "itemsize") else data.element_size()
+    p, dev = _ptr(data)
+    return flowroi_frame(ctypes.sizeof(flowroi_frame), w, h, pitch_bytes, U8 if esz == 1 else U16, bit_depth,
+                         frame_idx, p, dev)
+
+
+def flowroi_submit_frames(ctx, items) -> tuple:
+    """`items`: sequence of (stream_id, data, frame_idx, bit_depth).
+    Returns (accepted, status): frames [0, accepted) were submitted; when
+    accepted < len(items), status is the refusal code of the next one."""
+    n = len(items)
+    ids = (ctypes.c_int64 * max(n, 1))(*[int(it[0]) for it in items])
+    frs = (flowroi_frame * max(n, 1))(*[_frame(it[1], it[2], it[3]) for it in items])
+    st = ctypes.c_int(0)
+    k = lib().flowroi_submit_frames(ctx, n, ids, frs, ctypes.byref(st))
+    if k < 0:
+        _check(k, ctx)
+    return k, st.value
 
 
 def flowroi_step(ctx) -> int:

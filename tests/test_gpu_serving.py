@@ -50,6 +50,30 @@ def test_batch_invariance_mixed_resolutions(wavelet):
         _same(alone[sid], plain[sid])
 
 
+def test_batch_submit_matches_per_frame_submit_and_stops_at_a_refusal():
+    cfg = dict(pyr_levels=3, dwt_levels=3, wavelet=53)
+    streams = _streams()
+    alone = {sid: run_stream(frames, bd, **cfg)[1] for sid, frames, bd in streams}
+    with F.Context(flags=F.MANUAL | F.KEEP_INTERMEDIATES, result_ring=2, **cfg) as ctx:
+        for t in range(2):
+            k, st = F.flowroi_submit_frames(ctx.h, [(sid, frames[t], t, bd) for sid, frames, bd in streams])
+            assert (k, st) == (4, F.OK)
+            assert F.flowroi_step(ctx.h) == 4
+            F.flowroi_flush(ctx.h, 60000)
+        for sid, frames, bd in streams:
+            _same(alone[sid], fetch(ctx.h, sid, 1, frames[1].shape[0], frames[1].shape[1], wavelet=53))
+        # frame 2 of stream 0 and 1 fit; a frame index that does not
+        # increase is refused and nothing after it is looked at
+        sid0, fr0, bd0 = streams[0]
+        sid1, fr1, bd1 = streams[1]
+        k, st = F.flowroi_submit_frames(ctx.h, [(sid0, fr0[0], 2, bd0), (sid1, fr1[0], 1, bd1), (sid1, fr1[0], 3, bd1)])
+        assert (k, st) == (1, F.EINVAL)
+        assert "not after" in F.flowroi_last_error(ctx.h)
+        # an empty batch is a no-op; a negative count is an argument error
+        assert F.flowroi_submit_frames(ctx.h, []) == (0, F.OK)
+        assert F.lib().flowroi_submit_frames(ctx.h, -1, None, None, None) == F.EINVAL
+
+
 def test_scheduler_thread_matches_manual():
     streams = _streams()
     manual = {sid: run_stream(frames, bd, keep=False)[1] for sid, frames, bd in streams}
