@@ -18,8 +18,8 @@ constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 constexpr int kExpTW = 256, kExpTH = 16;   // pyramid + polynomial expansion
 constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
 constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
-constexpr int kSalTW = 64, kSalTH = 16;   // saliency, radix-select passes
-constexpr int kMorTW = 256, kMorTH = 32;  // threshold + opening + closing (8 words x 32 rows)
+constexpr int kSalTW = 256, kSalTH = 32;   // saliency, radix-select passes
+constexpr int kMorTW = 256, kMorTH = 64;  // threshold + opening + closing (8 words x 64 rows)
 constexpr int kDwtTW = 64, kDwtTH = 16;   // DWT: band coefficients per block (per band)
 
 // Per-frame reduction block (device), one per frame slot.

@@ -29,6 +29,7 @@
 // depend only on in-window samples.  The low-low band goes to a temporary
 // plane for the next level (or, at the last level, into the coefficient
 // plane).
+#include <mutex>
 #include <type_traits>
 
 #include "common.cuh"
@@ -74,6 +75,8 @@ __device__ __forceinline__ int32_t quantise(V y, float delta, int wav)
 }
 
 __device__ __forceinline__ int32_t roi_up(int32_t q, int s) { return q < 0 ? -((-q) << s) : (q << s); }
+
+__device__ __forceinline__ uint32_t smem_u32_dwt(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // The low-low plane's 32-bit words as the level's sample type.
 template <typename V>
@@ -136,22 +139,98 @@ __device__ __forceinline__ void mask_rule(const M (&m)[N], int e, M &lo, M &hi)
     hi = b;
 }
 
+// Shared-memory plan of k_dwt: the vertically lifted tile s_x [EH][EW+1]
+// (sample type), the mask rows [NB][EH][MW] bytes and, at level 1, the
+// staged raw samples [2][EH][EW] (u16).  Level 1 double-buffers the mask
+// and samples so the next tile's copies run during this tile's lifting.
+template <int WAV, bool L1>
+struct DwtSmem {
+    using V = typename std::conditional<WAV == 97, float, int>::type;
+    static constexpr int EW = 2 * kDwtTW + 2 * kDwtHalo, EH = 2 * kDwtTH + 2 * kDwtHalo;  // 136 x 40
+    static constexpr int MW = EW + 4;                                                    // mask row stride
+    static constexpr int NB = L1 ? 2 : 1;
+    static constexpr size_t x_bytes = (size_t)EH * (EW + 1) * sizeof(V);
+    static constexpr size_t m_off = (x_bytes + 15) / 16 * 16;
+    static constexpr size_t r_off = (m_off + (size_t)NB * EH * MW + 15) / 16 * 16;
+    static constexpr size_t bytes = r_off + (L1 ? (size_t)2 * EH * EW * sizeof(uint16_t) : 0);
+};
+
+__device__ __forceinline__ void cp_async8(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32_dwt(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32_dwt(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 template <int WAV, bool L1>
 __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
-    using V = typename std::conditional<WAV == 97, float, int>::type;
+    using SM = DwtSmem<WAV, L1>;
+    using V = typename SM::V;
     constexpr int TW = kDwtTW, TH = kDwtTH, HALO = kDwtHalo;
-    constexpr int EW = 2 * TW + 2 * HALO, EH = 2 * TH + 2 * HALO;  // 136 x 40
-    constexpr int SEG = 8;                                          // band outputs per row item
-    constexpr int RW = 2 * SEG + 2 * HALO;                          // row window (24)
-    __shared__ V s_x[EH][EW + 1];
-    __shared__ uint8_t s_m[EH][EW + 4];
+    constexpr int EW = SM::EW, EH = SM::EH, MW = SM::MW;
+    constexpr int SEG = 8;                  // band outputs per row item
+    constexpr int RW = 2 * SEG + 2 * HALO;  // row window (24)
+    extern __shared__ __align__(16) unsigned char dsm[];
+    V (*s_x)[EW + 1] = reinterpret_cast<V (*)[EW + 1]>(dsm);
+    uint8_t *const s_mb = dsm + SM::m_off;                                  // [NB][EH][MW]
+    uint16_t *const s_rb = reinterpret_cast<uint16_t *>(dsm + SM::r_off);  // [2][EH][EW] (level 1)
 
     const int nfr = bd->nframes;
     const int *off = bd->dwt_off[level - 1];
     const int total = __ldg(off + nfr);
     const bool last = level == mc.dwt_levels;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+
+    // Level 1: the raw samples and mask bytes of an interior tile (no
+    // symmetric extension, no clipping) are copied to the staging buffers
+    // with cp.async, 8 and 4 bytes per copy.
+    auto interior_async = [&](const FrameDesc &F, int ix0, int iy0) {
+        if (!L1 || F.bpp != 2) return false;
+        if (ix0 < 0 || iy0 < 0 || ix0 + EW > F.W || iy0 + EH > F.H) return false;
+        return ((reinterpret_cast<uintptr_t>(F.raw) | (uintptr_t)F.raw_pitch) & 7) == 0 &&
+               ((reinterpret_cast<uintptr_t>(F.mask) | (uintptr_t)F.W) & 3) == 0;
+    };
+    auto tile_origin = [&](int t, int &fi, int &ix0, int &iy0) {
+        fi = find_frame(off, nfr, t);
+        const FrameDesc &F = bd->f[fi];
+        const int bw = (F.W >> (level - 1)) >> 1;
+        const int ntx = (bw + TW - 1) / TW;
+        const int lt = t - __ldg(off + fi);
+        ix0 = 2 * ((lt % ntx) * TW) - HALO;
+        iy0 = 2 * ((lt / ntx) * TH) - HALO;
+    };
+    auto issue_async = [&](const FrameDesc &F, int ix0, int iy0, int buf) {
+        constexpr int NQ = EW / 4;  // 8-byte sample chunks (and 4-byte mask chunks) per row
+        const uint8_t *raw = static_cast<const uint8_t *>(F.raw) + (size_t)iy0 * F.raw_pitch + (size_t)ix0 * 2;
+        const uint8_t *msk = F.mask + (size_t)iy0 * F.W + ix0;
+        uint16_t *rb = s_rb + (size_t)buf * EH * EW;
+        uint8_t *mb = s_mb + (size_t)buf * EH * MW;
+        for (int i = threadIdx.x; i < EH * NQ; i += blockDim.x) {
+            const int r = i / NQ, q = i - r * NQ;
+            cp_async8(rb + r * EW + 4 * q, raw + (size_t)r * F.raw_pitch + 8 * q);
+            cp_async4(mb + r * MW + 4 * q, msk + (size_t)r * F.W + 4 * q);
+        }
+    };
+    if (L1) {
+        // prologue: the block's first tile
+        if ((int)blockIdx.x < total) {
+            int fi, ix0, iy0;
+            tile_origin(blockIdx.x, fi, ix0, iy0);
+            if (interior_async(bd->f[fi], ix0, iy0)) issue_async(bd->f[fi], ix0, iy0, 0);
+        }
+        cp_async_commit();
+    }
+
+    int k = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, k++) {
+        const int cur = L1 ? (k & 1) : 0;
+        uint8_t *const s_m = s_mb + (size_t)cur * EH * MW;
+        uint16_t *const s_r = s_rb + (size_t)cur * EH * EW;
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
         const int W = F.W;
@@ -172,13 +251,26 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         float *const dbg_yf = F.dbg_yf;
         V *const llout = static_cast<V *>(F.ll[(level - 1) % 2]);
         uint8_t *const llmout = F.llm[(level - 1) % 2];
+        const bool staged = L1 && interior_async(F, ix0, iy0);
 
-        // Load: samples with symmetric extension, mask clipped (0 outside).
-        // Two adjacent columns per item (ix0 is even, so an in-range pair is
-        // one aligned 2-sample / 2-byte load); a thread issues all of its
-        // items' loads before any shared-memory store, holding level-1 sample
-        // pairs packed in one word and every mask pair as two 0/1 bytes.
-        {
+        if (L1) {
+            // start the next tile's copies into the other buffers (their last
+            // reader, the previous tile's vertical pass, is behind a barrier)
+            const int tn = t + gridDim.x;
+            if (tn < total) {
+                int fn, nx0, ny0;
+                tile_origin(tn, fn, nx0, ny0);
+                if (interior_async(bd->f[fn], nx0, ny0)) issue_async(bd->f[fn], nx0, ny0, cur ^ 1);
+            }
+            cp_async_commit();
+        }
+
+        if (!staged) {
+            // Samples with symmetric extension, mask clipped (0 outside).
+            // Two adjacent columns per item (ix0 is even, so an in-range pair
+            // is one aligned 2-sample / 2-byte load); a thread issues all of
+            // its items' loads before any shared-memory store, holding level-1
+            // sample pairs packed in one word and every mask pair in one word.
             const bool xin = ix0 >= 0 && ix0 + EW <= iw;
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             constexpr int NR = (EH + 7) / 8, NP = (EW / 2 + 31) / 32;
@@ -221,12 +313,11 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
                     }
                     if (rin) {
                         if (xin) {
-                            const uint32_t m2 = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
-                            mm[i][j] = ((m2 & 0xffu) != 0) | (((m2 >> 8) != 0) << 8);
+                            mm[i][j] = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
                         } else {
                             const uint32_t m0 = gx >= 0 && gx < iw ? __ldg(mrow + gx) : 0;
                             const uint32_t m1 = gx + 1 >= 0 && gx + 1 < iw ? __ldg(mrow + gx + 1) : 0;
-                            mm[i][j] = (m0 != 0) | ((m1 != 0) << 8);
+                            mm[i][j] = m0 | (m1 << 8);
                         }
                     }
                 }
@@ -238,26 +329,30 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
                     const int r = warp + 8 * i, c = 2 * (lane + 32 * j);
                     if (r >= EH || c >= EW) continue;
                     if constexpr (L1) {
-                        s_x[r][c] = (V)((int)(sv[i][j][0] & 0xffffu) - dc_off);
-                        s_x[r][c + 1] = (V)((int)(sv[i][j][0] >> 16) - dc_off);
+                        *reinterpret_cast<uint32_t *>(s_r + r * EW + c) = sv[i][j][0];
                     } else {
                         s_x[r][c] = __int_as_float_or_int<V>(sv[i][j][0]);
                         s_x[r][c + 1] = __int_as_float_or_int<V>(sv[i][j][1]);
                     }
-                    *reinterpret_cast<uint16_t *>(&s_m[r][c]) = (uint16_t)mm[i][j];
+                    *reinterpret_cast<uint16_t *>(s_m + r * MW + c) = (uint16_t)mm[i][j];
                 }
         }
+        if (L1) cp_async_wait_prior();  // this tile's staged copies have landed
         __syncthreads();
 
-        // Vertical: threads [0, EW) lift one column each in registers; the
-        // next EW/4 threads turn four columns of the pixel mask at a time
-        // (the byte lanes of a word) into (low, high) row masks with the 1-D
+        // Vertical: threads [0, EW) lift one column each in registers (level
+        // 1 from the staged samples, with the DC shift); the next EW/4
+        // threads turn four columns of the mask at a time (the byte lanes of
+        // a word, made 0/1 first) into (low, high) row masks with the 1-D
         // rule, in place (the columns are private to their item).
         if (threadIdx.x < EW) {
             const int c = threadIdx.x;
             V x[EH];
 #pragma unroll
-            for (int j = 0; j < EH; j++) x[j] = s_x[j][c];
+            for (int j = 0; j < EH; j++) {
+                if constexpr (L1) x[j] = (V)((int)s_r[j * EW + c] - dc_off);
+                else x[j] = s_x[j][c];
+            }
             lift<V, EH>(x);
 #pragma unroll
             for (int j = 0; j < EH; j++) s_x[j][c] = x[j];
@@ -265,13 +360,14 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
             const int c = 4 * (threadIdx.x - EW);
             uint32_t m[EH];
 #pragma unroll
-            for (int j = 0; j < EH; j++) m[j] = *reinterpret_cast<const uint32_t *>(&s_m[j][c]);
+            for (int j = 0; j < EH; j++)
+                m[j] = __vcmpne4(*reinterpret_cast<const uint32_t *>(s_m + j * MW + c), 0u) & 0x01010101u;
 #pragma unroll
-            for (int k = 0; k < TH; k++) {
+            for (int kk = 0; kk < TH; kk++) {
                 uint32_t lo, hi;
-                mask_rule<WAV>(m, HALO + 2 * k, lo, hi);
-                *reinterpret_cast<uint32_t *>(&s_m[HALO + 2 * k][c]) = lo;      // even rows: low-vertical mask
-                *reinterpret_cast<uint32_t *>(&s_m[HALO + 2 * k + 1][c]) = hi;  // odd rows: high-vertical mask
+                mask_rule<WAV>(m, HALO + 2 * kk, lo, hi);
+                *reinterpret_cast<uint32_t *>(s_m + (HALO + 2 * kk) * MW + c) = lo;      // even rows: low-vertical mask
+                *reinterpret_cast<uint32_t *>(s_m + (HALO + 2 * kk + 1) * MW + c) = hi;  // odd rows: high-vertical mask
             }
         }
         __syncthreads();
@@ -294,7 +390,7 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
                 uint32_t mb = 0;
 #pragma unroll
                 for (int q = 0; q < RW / 4; q++) {
-                    const uint32_t wq = *reinterpret_cast<const uint32_t *>(&s_m[row][c0 + 4 * q]);
+                    const uint32_t wq = *reinterpret_cast<const uint32_t *>(&s_m[row * MW + c0 + 4 * q]);
                     mb |= ((wq * 0x01020408u) >> 24 & 0xfu) << (4 * q);
                 }
                 lift<V, RW>(x);
@@ -358,30 +454,59 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         }
         __syncthreads();
     }
+    if (L1) cp_async_wait_all();
 }
+
+namespace {
+
+// The kernels take more than the default 48 KB of dynamic shared memory:
+// raise their limit once per device.
+template <int WAV, bool L1>
+void dwt_attr()
+{
+    cudaFuncSetAttribute(k_dwt<WAV, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DwtSmem<WAV, L1>::bytes);
+}
+
+void ensure_dwt_attrs()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    dwt_attr<97, true>();
+    dwt_attr<97, false>();
+    dwt_attr<53, true>();
+    dwt_attr<53, false>();
+    done[dev] = true;
+}
+
+}  // namespace
 
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s)
 {
+    ensure_dwt_attrs();
     if (mc.wavelet == 97) {
-        if (level == 1) k_dwt<97, true><<<grid, 256, 0, s>>>(bd, mc, level);
-        else k_dwt<97, false><<<grid, 256, 0, s>>>(bd, mc, level);
+        if (level == 1) k_dwt<97, true><<<grid, 256, DwtSmem<97, true>::bytes, s>>>(bd, mc, level);
+        else k_dwt<97, false><<<grid, 256, DwtSmem<97, false>::bytes, s>>>(bd, mc, level);
     } else {
-        if (level == 1) k_dwt<53, true><<<grid, 256, 0, s>>>(bd, mc, level);
-        else k_dwt<53, false><<<grid, 256, 0, s>>>(bd, mc, level);
+        if (level == 1) k_dwt<53, true><<<grid, 256, DwtSmem<53, true>::bytes, s>>>(bd, mc, level);
+        else k_dwt<53, false><<<grid, 256, DwtSmem<53, false>::bytes, s>>>(bd, mc, level);
     }
 }
 
 int occupancy_dwt(int wavelet)
 {
-    // the level-1 and later-level kernels have the same shared memory and
-    // register bound; take the smaller occupancy of the two
+    // the level-1 kernel (staging buffers) bounds the occupancy
+    ensure_dwt_attrs();
     int a = 0, b = 0;
     if (wavelet == 97) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true>, 256, DwtSmem<97, true>::bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false>, 256, DwtSmem<97, false>::bytes);
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true>, 256, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false>, 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true>, 256, DwtSmem<53, true>::bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false>, 256, DwtSmem<53, false>::bytes);
     }
     return a < b ? a : b;
 }

@@ -97,22 +97,49 @@ struct BlockHist {
     }
 };
 
-// Saliency S, min/max of S, histogram of the first radix digit.
+// sqrt(x) for x >= 0 as x * rsqrt(x) (relative error a few 1e-7, far inside
+// the saliency tolerance; the exact cut is taken on these same values).
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// Saliency S, min/max of S, histogram of the first radix digit.  One
+// thread per column of a kSalTW x kSalTH tile walks down its rows, keeping
+// M = |d| of the rows above, at and below in registers (the next row's
+// flow is read one row ahead); the horizontal neighbours come from the
+// adjacent lanes, and the first and last lane of each warp read their
+// outer neighbour themselves.  Columns past the right edge repeat the last
+// column, rows above and below repeat the edge rows (replicate border).
 __global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
     constexpr int TW = kSalTW, TH = kSalTH;
-    __shared__ float s_m[TH + 2][TW + 2];
+    static_assert(TW == 256, "one thread per tile column");
     __shared__ unsigned s_hist[kHistBins];
     __shared__ unsigned s_mm[2];
     const int nfr = bd->nframes;
     const int *off = bd->sal_off;
     const int total = __ldg(off + nfr);
     const int buf = bd->final_flow_buf;
+    const int lane = threadIdx.x & 31;
+    const float wm = mc.alpha, wg = 1.f - mc.alpha;
     BlockHist bh{s_hist, s_mm};
     bh.with_minmax = true;
+    unsigned mn = 0x7f800000u, mx = 0u;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
+        if (fi != bh.frame) {
+            // this thread's extrema belong to the frame being left
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+                mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            }
+            if (lane == 0 && bh.frame >= 0) {
+                atomicMin(&s_mm[0], mn);
+                atomicMax(&s_mm[1], mx);
+            }
+            mn = 0x7f800000u;
+            mx = 0u;
+        }
         bh.begin(fi);
         bh.target = F.red;
         const int w = F.W, h = F.H, p = F.lp[0];
@@ -122,63 +149,65 @@ __global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ 
         const float2 *fl = F.flow[buf];
         float *const Sp = F.S;
         float2 *const dbg_flow = F.dbg_flow;
-        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-        {
-            constexpr int NR = (TH + 2 + 7) / 8, NC = (TW + 2 + 31) / 32;
-            float2 d[NR][NC];
+        const int gx = x0 + (int)threadIdx.x;
+        const int cx = min(gx, w - 1);
+        // the outer neighbour column of the warp's first / last lane
+        const int ex = lane == 0 ? max(cx - 1, 0) : min(cx + 1, w - 1);
+        const bool edge = lane == 0 || lane == 31;
+        auto mag = [&](int x, int y) {
+            const float2 v = __ldg(fl + (size_t)y * p + x);
+            return fast_sqrt(v.x * v.x + v.y * v.y);
+        };
+        float Mp = mag(cx, max(y0 - 1, 0)), Mc = mag(cx, y0);
+        float Ec = edge ? mag(ex, y0) : 0.f;
+        constexpr int RB = 8;  // rows whose flow is read ahead together
+        static_assert(TH % RB == 0, "row batches");
 #pragma unroll
-            for (int i = 0; i < NR; i++)
+        for (int j0 = 0; j0 < TH; j0 += RB) {
+            float Mn[RB], En[RB];
 #pragma unroll
-                for (int j = 0; j < NC; j++) {
-                    const int r = ty + 8 * i, c = tx + 32 * j;
-                    d[i][j] = make_float2(0.f, 0.f);
-                    if (r < TH + 2 && c < TW + 2)
-                        d[i][j] = fl[(size_t)clampi(y0 - 1 + r, 0, h - 1) * p + clampi(x0 - 1 + c, 0, w - 1)];
+            for (int k = 0; k < RB; k++) {
+                const int yn = min(y0 + j0 + k + 1, h - 1);
+                Mn[k] = mag(cx, yn);
+                En[k] = edge ? mag(ex, yn) : 0.f;
+            }
+#pragma unroll
+            for (int k = 0; k < RB; k++) {
+                const int gy = y0 + j0 + k;
+                float Ml = __shfl_up_sync(0xffffffffu, Mc, 1), Mr = __shfl_down_sync(0xffffffffu, Mc, 1);
+                if (lane == 0) Ml = Ec;
+                if (lane == 31) Mr = Ec;
+                if (gx < w && gy < h) {
+                    const float gxv = 0.5f * (Mr - Ml), gyv = 0.5f * (Mn[k] - Mp);
+                    const float S = wm * Mc + wg * fast_sqrt(gxv * gxv + gyv * gyv);
+                    Sp[(size_t)gy * p + gx] = S;
+                    if (dbg_flow) dbg_flow[(size_t)gy * w + gx] = __ldg(fl + (size_t)gy * p + gx);
+                    const unsigned b = __float_as_uint(S);
+                    mn = min(mn, b);
+                    mx = max(mx, b);
+                    atomicAdd(&s_hist[b >> digit_shift(0)], 1u);
                 }
-#pragma unroll
-            for (int i = 0; i < NR; i++)
-#pragma unroll
-                for (int j = 0; j < NC; j++) {
-                    const int r = ty + 8 * i, c = tx + 32 * j;
-                    if (r < TH + 2 && c < TW + 2) s_m[r][c] = sqrtf(d[i][j].x * d[i][j].x + d[i][j].y * d[i][j].y);
-                }
-        }
-        __syncthreads();
-        unsigned mn = 0x7f800000u, mx = 0u;
-#pragma unroll
-        for (int rr = 0; rr < TH / 8; rr++) {
-            const int r = ty + 8 * rr, gy = y0 + r;
-#pragma unroll
-            for (int cc = 0; cc < TW / 32; cc++) {
-                const int c = tx + 32 * cc, gx = x0 + c;
-                if (gx >= w || gy >= h) continue;
-                const float gxv = 0.5f * (s_m[r + 1][c + 2] - s_m[r + 1][c]);
-                const float gyv = 0.5f * (s_m[r + 2][c + 1] - s_m[r][c + 1]);
-                const float S = mc.alpha * s_m[r + 1][c + 1] + (1.f - mc.alpha) * sqrtf(gxv * gxv + gyv * gyv);
-                Sp[(size_t)gy * p + gx] = S;
-                if (dbg_flow) dbg_flow[(size_t)gy * w + gx] = fl[(size_t)gy * p + gx];
-                const unsigned b = __float_as_uint(S);
-                mn = min(mn, b);
-                mx = max(mx, b);
-                atomicAdd(&s_hist[b >> digit_shift(0)], 1u);
+                Mp = Mc;
+                Mc = Mn[k];
+                Ec = En[k];
             }
         }
+    }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            atomicMin(&s_mm[0], mn);
-            atomicMax(&s_mm[1], mx);
-        }
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    if (lane == 0 && bh.frame >= 0) {
+        atomicMin(&s_mm[0], mn);
+        atomicMax(&s_mm[1], mx);
     }
     bh.flush();
 }
 
 // Histogram of radix digit `pass` (1 or 2) over the values whose higher
-// bits equal the prefix selected so far.
+// bits equal the prefix selected so far.  One thread per tile column: all
+// of its kSalTH loads are issued before any is tested.
 __global__ void __launch_bounds__(256) k_select_pass(const BatchDesc *__restrict__ bd, int pass)
 {
     constexpr int TW = kSalTW, TH = kSalTH;
@@ -200,20 +229,16 @@ __global__ void __launch_bounds__(256) k_select_pass(const BatchDesc *__restrict
         const int lt = t - __ldg(off + fi);
         const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
         const unsigned want = __ldg(F.red + kRedPrefix) >> hi;
-        // 4 pixels per thread per row (pitch is a multiple of 32 floats, so
-        // every 4-pixel group starting at a multiple of 4 is 16-byte aligned;
-        // the tail beyond the width lies inside the pitch and is masked).
-        constexpr int G = TW / 4;  // groups per row
-        for (int i = threadIdx.x; i < TH * G; i += blockDim.x) {
-            const int r = i / G, c4 = (i % G) * 4;
-            const int gx = x0 + c4, gy = y0 + r;
-            if (gx >= w || gy >= h) continue;
-            const uint4 b4 = *reinterpret_cast<const uint4 *>(F.S + (size_t)gy * p + gx);
-            const unsigned bb[4] = {b4.x, b4.y, b4.z, b4.w};
+        const int gx = x0 + (int)threadIdx.x;
+        if (gx >= w) continue;
+        const unsigned *col = reinterpret_cast<const unsigned *>(F.S) + (size_t)y0 * p + gx;
+        const int nr = min(TH, h - y0);
+        unsigned v[TH];
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (gx + j < w && (bb[j] >> hi) == want) atomicAdd(&s_hist[(bb[j] >> sh) & dmask], 1u);
-        }
+        for (int j = 0; j < TH; j++) v[j] = j < nr ? __ldg(col + (size_t)j * p) : 0u;
+#pragma unroll
+        for (int j = 0; j < TH; j++)
+            if (j < nr && (v[j] >> hi) == want) atomicAdd(&s_hist[(v[j] >> sh) & dmask], 1u);
     }
     bh.flush();
 }
@@ -304,7 +329,7 @@ __global__ void __launch_bounds__(256) k_select_find(const BatchDesc *__restrict
 namespace {
 
 constexpr int kMorMaxR = 4;
-constexpr int kMorWords = 8, kMorRows = 32;
+constexpr int kMorWords = kMorTW / 32, kMorRows = kMorTH;
 constexpr int kMorApron = 4 * kMorMaxR;                  // rows above and below
 constexpr int kMorEW = kMorWords + 2, kMorEH = kMorRows + 2 * kMorApron;
 

@@ -383,7 +383,7 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
         for (int l = 1; l <= D; l++)
             bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH);
         bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
-        bd.mor_off[i + 1] = bd.mor_off[i] + tiles(F.W, F.H, kMorTW, kMorTH);  // 256 x 32 pixel tiles
+        bd.mor_off[i + 1] = bd.mor_off[i] + tiles(F.W, F.H, kMorTW, kMorTH);
         bd.frm_off[i + 1] = i + 1;
     }
 }
