@@ -51,6 +51,8 @@ def oracle_params(orc, **cfg):
     p.wavelet = cfg.get("wavelet", 53)
     p.iters = cfg.get("iters", 3)
     p.win_r = cfg.get("win_r", 7)
+    p.poly_n_half = cfg.get("poly_n_half", 2)
+    p.poly_sigma = cfg.get("poly_sigma", 1.1)
     p.roi_q = cfg.get("roi_q", 0.2)
     p.scale_shift = cfg.get("scale_shift", 5)
     p.r_open = cfg.get("r_open", 1)

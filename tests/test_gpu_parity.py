@@ -94,6 +94,21 @@ def test_ragged_sizes(orc, h, w):
     _stagewise(orc, prev.numpy(), cur.numpy(), 8, g, **levels)
 
 
+@pytest.mark.parametrize("cfg", [
+    dict(win_r=2),
+    dict(win_r=10, poly_n_half=3, poly_sigma=1.5),
+    dict(win_r=5, r_open=0, r_close=4, iters=1),
+    dict(win_r=9, r_open=2, r_close=0, roi_q=0.05, pyr_levels=4),
+], ids=["win5", "win21_poly7", "win11_close4_iter1", "win19_open2_q005"])
+def test_method_settings(orc, cfg):
+    """Other window sizes (each a separately compiled box-sum kernel with its
+    own plane-ring depth), the 7-tap expansion, one iteration and other
+    morphology radii, against the oracle with the same settings."""
+    prev, cur = pair_u8(seed=4100 + cfg["win_r"], h=192, w=256, n_blobs=8)
+    g = run_stream([prev.numpy(), cur.numpy()], 8, **cfg)[1]
+    _stagewise(orc, prev.numpy(), cur.numpy(), 8, g, **cfg)
+
+
 def test_sequence_1024_u16_53_resident_state(orc):
     """Three frames of one 12-bit stream: frames 1 and 2 reuse the resident
     expansion of their predecessor."""
