@@ -65,6 +65,59 @@ void orc_units(const void *raw, int bytes_per_px, int bit_depth, int64_t n, doub
     }
 }
 
+/* ------------------------------------------------------------ f1 (opt) --
+ * Denoising of the flow input (§Optical flow extraction: a two-step
+ * denoising, median filtering then bilateral filtering, before the flow;
+ * Table 1 "Denoise": on or off).  The paper gives no sizes; the readings:
+ *   - median over the 3x3 neighbourhood, replicate border;
+ *   - bilateral over the (2*rb+1)^2 square of the median image, replicate
+ *     border, weight of neighbour q of pixel p
+ *         exp(-|q - p|^2 / (2 sigma_s^2)) * exp(-(I(q) - I(p))^2 / (2 sigma_r^2)),
+ *     output = sum(w I(q)) / sum(w), in 8-bit units.
+ * The JPEG2000 front end still codes the raw frame. */
+static int cmp_d(const void *a, const void *b)
+{
+    double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+void orc_median3(const double *in, int w, int h, double *out)
+{
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            double v[9];
+            int k = 0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) v[k++] = in[(size_t)clampi(y + dy, 0, h - 1) * w + clampi(x + dx, 0, w - 1)];
+            qsort(v, 9, sizeof(double), cmp_d);
+            out[(size_t)y * w + x] = v[4];
+        }
+}
+
+void orc_bilateral(const double *in, int w, int h, int rb, double sigma_s, double sigma_r, double *out)
+{
+    for (int y = 0; y < h; y++)
+        for (int x = 0; x < w; x++) {
+            const double c = in[(size_t)y * w + x];
+            double num = 0.0, den = 0.0;
+            for (int dy = -rb; dy <= rb; dy++)
+                for (int dx = -rb; dx <= rb; dx++) {
+                    const double q = in[(size_t)clampi(y + dy, 0, h - 1) * w + clampi(x + dx, 0, w - 1)];
+                    const double wgt = exp(-(double)(dx * dx + dy * dy) / (2.0 * sigma_s * sigma_s)) *
+                                       exp(-(q - c) * (q - c) / (2.0 * sigma_r * sigma_r));
+                    num += wgt * q;
+                    den += wgt;
+                }
+            out[(size_t)y * w + x] = num / den;
+        }
+}
+
+void orc_denoise(const double *in, int w, int h, int rb, double sigma_s, double sigma_r, double *tmp, double *out)
+{
+    orc_median3(in, w, h, tmp);
+    orc_bilateral(tmp, w, h, rb, sigma_s, sigma_r, out);
+}
+
 /* ------------------------------------------------------------------ a2 --
  * One Gaussian-pyramid reduction: 5x5 binomial blur (outer product of
  * [1 4 6 4 1]/16), replicate border, sample at even coordinates.  The

@@ -59,6 +59,9 @@ def _declare(L):
         "orc_version": (_I, []),
         "orc_units": (None, [_P, _I, _I, _I64, _P]),
         "orc_pyr_down": (None, [_P, _I, _I, _P]),
+        "orc_median3": (None, [_P, _I, _I, _P]),
+        "orc_bilateral": (None, [_P, _I, _I, _I, _D, _D, _P]),
+        "orc_denoise": (None, [_P, _I, _I, _I, _D, _D, _P, _P]),
         "orc_poly_projector": (_I, [_I, _D, _P]),
         "orc_poly_expand": (_I, [_P, _I, _I, _I, _D, _P]),
         "orc_flow_upsample": (None, [_P, _I, _I, _I, _I, _P]),
@@ -109,6 +112,33 @@ def units(raw: np.ndarray, bit_depth: int) -> np.ndarray:
     raw = np.ascontiguousarray(raw)
     out = np.empty(raw.shape, np.float64)
     lib().orc_units(_ptr(raw), raw.dtype.itemsize, bit_depth, raw.size, _ptr(out))
+    return out
+
+
+def median3(img: np.ndarray) -> np.ndarray:
+    """3x3 median, replicate border (§Optical flow extraction, denoising)."""
+    img = _c(img, np.float64)
+    h, w = img.shape
+    out = np.empty_like(img)
+    lib().orc_median3(_ptr(img), w, h, _ptr(out))
+    return out
+
+
+def bilateral(img: np.ndarray, rb: int, sigma_s: float, sigma_r: float) -> np.ndarray:
+    """Bilateral filter over a (2rb+1)^2 square, replicate border."""
+    img = _c(img, np.float64)
+    h, w = img.shape
+    out = np.empty_like(img)
+    lib().orc_bilateral(_ptr(img), w, h, rb, sigma_s, sigma_r, _ptr(out))
+    return out
+
+
+def denoise(img: np.ndarray, rb: int, sigma_s: float, sigma_r: float) -> np.ndarray:
+    """Median 3x3, then bilateral (the paper's two-step denoising)."""
+    img = _c(img, np.float64)
+    h, w = img.shape
+    tmp, out = np.empty_like(img), np.empty_like(img)
+    lib().orc_denoise(_ptr(img), w, h, rb, sigma_s, sigma_r, _ptr(tmp), _ptr(out))
     return out
 
 
@@ -323,6 +353,10 @@ class Params:
     dwt_levels: int = 3
     scale_shift: int = 5
     delta_base: float = 1.0
+    denoise: int = 0           # Table 1 "Denoise" (off: a valid setting)
+    den_radius: int = 2        # bilateral square radius (reading)
+    den_sigma_s: float = 2.0   # bilateral spatial sigma, px (reading)
+    den_sigma_r: float = 20.0  # bilateral range sigma, 8-bit units (reading)
 
 
 def frame(prev_raw, cur_raw, bit_depth: int, p: Params, y_f32=None):
@@ -342,6 +376,10 @@ def frame(prev_raw, cur_raw, bit_depth: int, p: Params, y_f32=None):
     if prev_raw is not None:
         I1 = units(cur_raw, bit_depth)
         I2 = units(prev_raw, bit_depth)
+        if p.denoise:
+            I1 = denoise(I1, p.den_radius, p.den_sigma_s, p.den_sigma_r)
+            I2 = denoise(I2, p.den_radius, p.den_sigma_s, p.den_sigma_r)
+            out["denoised"] = I1
         d = flow(I1, I2, p.pyr_levels, p.poly_n_half, p.poly_sigma, p.iters, p.win_r, p.lam)
         S = saliency(d, p.sal_weight)
         Sh = normalise(S)
