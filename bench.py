@@ -45,6 +45,10 @@ WORKLOADS = {
     # same workload, pyramid and expansion fields stored in fp16
     "fp16_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=16, seed_base=3000),
+    # same workload with the optional denoising of the flow input (median 3x3,
+    # bilateral 5x5) on
+    "denoise_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                            dwt_levels=5, wavelet=97, precision=32, seed_base=3000, denoise=1),
     # four streams of the batched workload's frames (small case for profiler captures)
     "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
@@ -218,7 +222,7 @@ def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampl
     """Device-resident run: returns dict(time_s, frames, launches, kernel_times, stats, clocks)."""
     import torch
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
-               precision=wl["precision"], max_batch_frames=64, result_ring=8,
+               precision=wl["precision"], max_batch_frames=64, result_ring=8, denoise=wl.get("denoise", 0),
                flags=F.MANUAL | (F.PLAIN if plain else 0), device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     res = {}
@@ -282,7 +286,8 @@ def run_e2e(F, wl, frames, steps, warmup):
     masks = [torch.empty((h, w), dtype=torch.uint8).pin_memory() for _ in range(S)]
     coefs = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(S)]
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
-               precision=wl["precision"], max_batch_frames=64, result_ring=8, flags=F.MANUAL,
+               precision=wl["precision"], max_batch_frames=64, result_ring=8, denoise=wl.get("denoise", 0),
+               flags=F.MANUAL,
                device=torch.cuda.current_device())
     res = {}
     with F.Context(**cfg) as ctx:
@@ -469,7 +474,7 @@ def config_of(name, wl):
     return {"workload": name, "streams": wl["streams"], "frame": f"{wl['w']}x{wl['h']} u16 ({wl['bit_depth']}-bit)",
             "frames_per_stream": wl["frames"], "blobs": wl["blobs"], "batch_frames": wl["streams"],
             "pyr_levels": wl["pyr_levels"], "dwt": f"{wl['wavelet'] // 10}/{wl['wavelet'] % 10} x{wl['dwt_levels']}",
-            "storage": "fp16" if wl["precision"] == 16 else "fp32",
+            "storage": "fp16" if wl["precision"] == 16 else "fp32", "denoise": bool(wl.get("denoise", 0)),
             "l2": "inputs larger than L2 (each step touches ~2.5 GB of frames and fields)"}
 
 

@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define FLOWROI_ABI_VERSION 1
+#define FLOWROI_ABI_VERSION 2
 
 /* Exported symbols (the library is built with hidden default visibility). */
 #if defined(__GNUC__)
@@ -92,10 +92,11 @@ extern "C" {
 #define FLOWROI_I_MASK0 3       /* uint8[W*H]: mask before opening/closing (0/1) */
 #define FLOWROI_I_COEFF_F32 4   /* float[W*H]: 9/7 coefficients before quantisation, Mallat */
 #define FLOWROI_I_THRESHOLD 5   /* float[1]: the cut t on S^ (mask0 = S^ > t) */
+#define FLOWROI_I_DENOISED 6    /* float[W*H]: denoised flow input in 8-bit units (config.denoise = 1) */
 
 /* ---- configuration ----------------------------------------------------- */
 /* Method parameters.  Table 1 of the paper names the user parameters (RoI
- * threshold, scaling factor; denoise and adjacent factor are not on this
+ * threshold, scaling factor, denoise; the adjacent factor is not on this
  * path; compression rate acts downstream).  The estimator constants are not
  * given by the paper; the defaults are the values this library documents
  * (pyramid 5 levels, 3 iterations, 15x15 box window, 5x5 expansion with
@@ -124,6 +125,13 @@ typedef struct flowroi_config {
     int32_t device;            /* CUDA device ordinal (0) */
     uint64_t hbm_budget_bytes; /* admission budget for all streams' device state;
                                   0 = 80% of the device memory free at create */
+    /* Table 1 "Denoise" (§Optical flow extraction: median filtering, then
+     * bilateral filtering, of the flow input; the JPEG2000 front end still
+     * codes the raw frame).  Sizes are not given by the paper. */
+    int32_t denoise;           /* 0 = off (a valid setting of the paper), 1 = on (0) */
+    int32_t den_radius;        /* bilateral square radius rb in [1, 3]: side 2rb+1 (2) */
+    float den_sigma_s;         /* bilateral spatial sigma in pixels, > 0 (2.0) */
+    float den_sigma_r;         /* bilateral range sigma in 8-bit units, > 0 (20.0) */
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and

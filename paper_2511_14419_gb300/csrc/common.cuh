@@ -15,6 +15,7 @@ constexpr int kHistBins = 2048;  // radix-select digit of 11 bits
 constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 
 // Tile shapes (output pixels per block) of each kernel family.
+constexpr int kDenMaxR = 3;                // largest bilateral radius of the optional denoising
 constexpr int kExpTW = 256, kExpTH = 16;   // pyramid + polynomial expansion
 constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
 constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
@@ -51,6 +52,13 @@ struct MethodConsts {
     // JPEG2000 front end
     int wavelet, dwt_levels, shift;
     float delta[kMaxSubbands];
+    // optional denoising of the flow input: bilateral radius; the weights
+    // as powers of two, w = 2^-(den_ls[offset] + den_lr * (I(q) - I(p))^2),
+    // den_ls = -log2 of the spatial weight over the (2 kDenMaxR + 1)^2
+    // square (row-major, centred), den_lr = log2(e) / (2 sigma_r^2)
+    int denoise, den_r;
+    float den_ls[(2 * kDenMaxR + 1) * (2 * kDenMaxR + 1)];
+    float den_lr;
 };
 
 // One frame of a batch.  Level geometry: lw/lh = level size, lp = pitch in
@@ -81,6 +89,7 @@ struct FrameDesc {
     uint8_t *dbg_mask0;             // keep: mask before morphology, W*H
     float *dbg_yf;                  // keep + 9/7: float coefficients, W*H
     float *dbg_thr;                 // keep: threshold on S^ (1 float)
+    float *dbg_den;                 // keep + denoise: denoised flow input, W*H
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
     uint8_t *llm[2];                // their RoI masks
 };

@@ -16,7 +16,8 @@
 // separable [1 4 6 4 1]/16 blur with replicate border, even samples.
 //
 // Level 0 reads the raw u8/u16 frame and converts to 8-bit units on the
-// fly; level l > 0 reads the pyramid image written by level l-1.
+// fly (or reads the denoised frame when denoising is on); level l > 0 reads
+// the pyramid image written by level l-1.
 // Storage type T (float or __half) holds pyramid images and fields; every
 // arithmetic operation is in float.
 #include "common.cuh"
@@ -37,12 +38,12 @@ struct LevelSrc {
     float scale;
     __device__ __forceinline__ LevelSrc(const FrameDesc &F, int level)
     {
-        raw = static_cast<const uint8_t *>(F.raw);
+        // level 0 is the raw frame, or its denoised image when one exists
         img = static_cast<const T *>(F.pyr[level]);
+        raw = img ? nullptr : static_cast<const uint8_t *>(F.raw);
         bpp = F.bpp;
         scale = F.unit_scale;
-        pitch = level == 0 ? F.raw_pitch : F.lp[level];
-        if (level > 0) raw = nullptr;
+        pitch = raw ? F.raw_pitch : F.lp[level];
     }
     __device__ __forceinline__ float at(int x, int y) const
     {

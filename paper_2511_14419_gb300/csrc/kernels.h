@@ -19,6 +19,8 @@ void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s)
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
 void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
+// Optional denoising of the flow input (level-0 tiles of the expansion).
+void launch_denoise(const BatchDesc *bd, const MethodConsts &mc, bool half, int grid, cudaStream_t s);
 
 // Resident blocks per SM (also sets any shared-memory attribute the kernel
 // needs; call once per device before the first launch).
@@ -29,9 +31,11 @@ int window_box(bool half, int win_r, int *xo, int *bw, int *eh);
 int occupancy_window(bool half, int win_r);
 int occupancy_mask_kernels();
 int occupancy_dwt(int wavelet);
+int occupancy_denoise(bool half, int radius);
 
 bool flow_radius_supported(int r);
 bool morph_radius_supported(int r);
+bool denoise_radius_supported(int r);
 
 // 9/7 quantisation steps (host, double precision); see flowroi_quant_steps.
 int quant_steps(int levels, int bit_depth, double delta_base, float *delta, int *eps, int *mu, double *gain);

@@ -89,6 +89,7 @@ struct Entry {
     uint8_t *dbg_mask0 = nullptr;
     float *dbg_yf = nullptr;
     float *dbg_thr = nullptr;
+    float *dbg_den = nullptr;
 };
 
 struct Stream {
@@ -142,7 +143,7 @@ struct flowroi_ctx {
     cudaGraphExec_t graph[kDesc] = {};
     int graph_launches = 0;
     int desc_next = 0;
-    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0;
+    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0;
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -210,6 +211,9 @@ int validate_config(const flowroi_config *c)
     if (c->max_batch_frames < 1 || c->max_batch_frames > kMaxBatch) return fail(FLOWROI_EINVAL, "config.max_batch_frames must be in [1,64]");
     if (c->result_ring < 2 || c->result_ring > 16) return fail(FLOWROI_EINVAL, "config.result_ring must be in [2,16]");
     if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL)) return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
+    if (c->denoise != 0 && c->denoise != 1) return fail(FLOWROI_EINVAL, "config.denoise must be 0 or 1");
+    if (!denoise_radius_supported(c->den_radius)) return fail(FLOWROI_EINVAL, "config.den_radius must be in [1,3]");
+    if (!(c->den_sigma_s > 0.f) || !(c->den_sigma_r > 0.f)) return fail(FLOWROI_EINVAL, "config.den_sigma_s/den_sigma_r must be > 0");
     return FLOWROI_OK;
 }
 
@@ -281,7 +285,8 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
             s->fq[k][l] = take((size_t)s->lp[l] * s->lh[l] * 4 * esz);
             s->fb[k][l] = take((size_t)s->lp[l] * s->lh[l] * esz);
         }
-    for (int l = 1; l < L; l++) s->pyr[l] = take((size_t)s->lp[l] * s->lh[l] * esz);
+    // level 0 is read from the raw frame unless the flow input is denoised
+    for (int l = c->cfg.denoise ? 0 : 1; l < L; l++) s->pyr[l] = take((size_t)s->lp[l] * s->lh[l] * esz);
     for (int l = 0; l < L; l++) s->gh[l] = take((size_t)s->lp[l] * s->lh[l] * 5 * esz);
     for (int k = 0; k < 2; k++) s->flow[k] = reinterpret_cast<float2 *>(take((size_t)s->lp[0] * s->H * sizeof(float2)));
     s->S = reinterpret_cast<float *>(take((size_t)s->lp[0] * s->H * sizeof(float)));
@@ -301,6 +306,7 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
             e->dbg_mask0 = reinterpret_cast<uint8_t *>(take(npx));
             e->dbg_yf = c->cfg.wavelet == FLOWROI_W97 ? reinterpret_cast<float *>(take(npx * 4)) : nullptr;
             e->dbg_thr = reinterpret_cast<float *>(take(sizeof(float)));
+            e->dbg_den = c->cfg.denoise ? reinterpret_cast<float *>(take(npx * 4)) : nullptr;
         }
     }
     return align_up(off, 256);
@@ -358,6 +364,7 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
     F.dbg_mask0 = e->dbg_mask0;
     F.dbg_yf = e->dbg_yf;
     F.dbg_thr = e->dbg_thr;
+    F.dbg_den = e->dbg_den;
     F.ll[0] = s->ll[0];
     F.ll[1] = s->ll[1];
     F.llm[0] = s->llm[0];
@@ -389,8 +396,8 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
 }
 
 const char *const kKernelNames[] = {"frame_init", "expand", "update", "window", "saliency", "select_find", "select_pass",
-                                    "morph", "dwt"};
-enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT };
+                                    "morph", "dwt", "denoise"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE };
 
 // Runs one launch, bracketed by an event pair when profiling.
 template <class Fn>
@@ -424,6 +431,11 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     const bool any_prev = !pl || hd->sal_off[n] > 0;
     timed(c, st, prof, K_INIT, -1, -1, [&] { launch_frame_init(dd, g(n, c->grid_frames), st); });
     cnt++;
+    if (mc.denoise) {
+        // the flow input of every frame (its expansion is the next frame's predecessor)
+        timed(c, st, prof, K_DENOISE, -1, -1, [&] { launch_denoise(dd, mc, c->half, g(hd->exp_off[0][n], c->grid_den), st); });
+        cnt++;
+    }
     for (int l = 0; l < L; l++) {
         timed(c, st, prof, K_EXPAND, l, -1, [&] { launch_expand(dd, mc, l, c->half, g(hd->exp_off[l][n], c->grid_exp), st); });
         cnt++;
@@ -654,6 +666,7 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
         if (which >= FLOWROI_I_FLOW && !c->keep) return fail(FLOWROI_ENOTKEPT, "intermediates not kept (FLOWROI_KEEP_INTERMEDIATES)");
         if (which == FLOWROI_I_COEFF_F32 && c->cfg.wavelet != FLOWROI_W97)
             return fail(FLOWROI_EINVAL, "float coefficients exist only for the 9/7 path");
+        if (which == FLOWROI_I_DENOISED && !c->cfg.denoise) return fail(FLOWROI_EINVAL, "denoising is off (config.denoise)");
         e->readers++;
     }
     const bool ok = wait_done(c, e, timeout_ms);
@@ -673,6 +686,7 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
         case FLOWROI_I_MASK0: src = e->dbg_mask0; bytes = npx; break;
         case FLOWROI_I_COEFF_F32: src = e->dbg_yf; bytes = npx * 4; break;
         case FLOWROI_I_THRESHOLD: src = e->dbg_thr; bytes = 4; break;
+        case FLOWROI_I_DENOISED: src = e->dbg_den; bytes = npx * 4; break;
         default: rc = fail(FLOWROI_EINVAL, "unknown intermediate %d", which); break;
         }
         if (rc == FLOWROI_OK && which >= FLOWROI_I_FLOW && !e->has_prev) {
@@ -778,6 +792,10 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->flags = 0;
     cfg->device = 0;
     cfg->hbm_budget_bytes = 0;
+    cfg->denoise = 0;
+    cfg->den_radius = 2;
+    cfg->den_sigma_s = 2.0f;
+    cfg->den_sigma_r = 20.0f;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -819,6 +837,14 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     mc.wavelet = cfg->wavelet;
     mc.dwt_levels = cfg->dwt_levels;
     mc.shift = cfg->scale_shift;
+    mc.denoise = cfg->denoise;
+    mc.den_r = cfg->den_radius;
+    const double log2e = 1.4426950408889634;
+    for (int dy = -cfg->den_radius; dy <= cfg->den_radius; dy++)
+        for (int dx = -cfg->den_radius; dx <= cfg->den_radius; dx++)
+            mc.den_ls[(dy + kDenMaxR) * (2 * kDenMaxR + 1) + dx + kDenMaxR] =
+                (float)(log2e * (double)(dx * dx + dy * dy) / (2.0 * (double)cfg->den_sigma_s * cfg->den_sigma_s));
+    mc.den_lr = (float)(log2e / (2.0 * (double)cfg->den_sigma_r * cfg->den_sigma_r));
     for (int b = 0; b < kMaxSubbands; b++) mc.delta[b] = 1.f;
     if (cfg->wavelet == FLOWROI_W97 && quant_steps(cfg->dwt_levels, 12, cfg->delta_base, mc.delta, nullptr, nullptr, nullptr) != 0)
         return fail(FLOWROI_EINVAL, "config.delta_base gives quantisation steps out of range");
@@ -851,6 +877,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     c->grid_win = std::max(1, ow) * c->num_sms;
     c->grid_mask = std::max(1, om) * c->num_sms;
     c->grid_dwt = std::max(1, od) * c->num_sms;
+    c->grid_den = cfg->denoise ? std::max(1, occupancy_denoise(c->half, cfg->den_radius)) * c->num_sms : 0;
     c->grid_frames = kMaxBatch;
     size_t freeb = 0, totalb = 0;
     CK(nullptr, cudaMemGetInfo(&freeb, &totalb));
@@ -1017,7 +1044,7 @@ int flowroi_get_coeffs(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int
 int flowroi_get_intermediate(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, void *out, int out_on_device,
                              int timeout_ms)
 {
-    if (which < FLOWROI_I_FLOW || which > FLOWROI_I_THRESHOLD) return fail(FLOWROI_EINVAL, "unknown intermediate %d", which);
+    if (which < FLOWROI_I_FLOW || which > FLOWROI_I_DENOISED) return fail(FLOWROI_EINVAL, "unknown intermediate %d", which);
     if (c) cudaSetDevice(c->device);
     return get_common(c, stream_id, frame_idx, which, out, out_on_device, timeout_ms);
 }

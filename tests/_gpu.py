@@ -58,4 +58,8 @@ def oracle_params(orc, **cfg):
     p.r_open = cfg.get("r_open", 1)
     p.r_close = cfg.get("r_close", 2)
     p.sal_weight = cfg.get("sal_weight", 0.7)
+    p.denoise = cfg.get("denoise", 0)
+    p.den_radius = cfg.get("den_radius", 2)
+    p.den_sigma_s = cfg.get("den_sigma_s", 2.0)
+    p.den_sigma_r = cfg.get("den_sigma_r", 20.0)
     return p
