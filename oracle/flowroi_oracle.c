@@ -492,6 +492,44 @@ void orc_morph(const uint8_t *in, int w, int h, int r_open, int r_close, uint8_t
     free(b);
 }
 
+/* ------------------------------------------------------------ f2 (opt) --
+ * Removal of small connected components (§Region of Interest extraction:
+ * after opening and closing, residual small connected components are
+ * removed by an area criterion).  Readings: 8-connectivity; a component
+ * with fewer than min_area pixels is removed; min_area = 0 or 1 keeps
+ * every component.  Flood fill with an explicit stack, in place. */
+void orc_remove_small(uint8_t *m, int w, int h, int min_area)
+{
+    int64_t n = (int64_t)w * h;
+    if (min_area <= 1 || n == 0) return;
+    int32_t *comp = (int32_t *)malloc(n * sizeof(int32_t)); /* pixels of the current component */
+    uint8_t *seen = (uint8_t *)calloc(n, 1);
+    for (int64_t s = 0; s < n; s++) {
+        if (!m[s] || seen[s]) continue;
+        int64_t top = 0, len = 0;
+        comp[len++] = (int32_t)s;
+        seen[s] = 1;
+        while (top < len) {
+            int64_t p = comp[top++];
+            int x = (int)(p % w), y = (int)(p / w);
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    int xx = x + dx, yy = y + dy;
+                    if ((dx == 0 && dy == 0) || xx < 0 || yy < 0 || xx >= w || yy >= h) continue;
+                    int64_t q = (int64_t)yy * w + xx;
+                    if (m[q] && !seen[q]) {
+                        seen[q] = 1;
+                        comp[len++] = (int32_t)q;
+                    }
+                }
+        }
+        if (len < min_area)
+            for (int64_t i = 0; i < len; i++) m[comp[i]] = 0;
+    }
+    free(comp);
+    free(seen);
+}
+
 /* ------------------------------------------------------------------ a8 --
  * JPEG2000 lifting DWT, one dimension, whole-sample symmetric extension
  * (x[-i] = x[i], x[n-1+i] = x[n-1-i]).  A signal of length 1 is left as it

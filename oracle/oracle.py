@@ -60,6 +60,7 @@ def _declare(L):
         "orc_units": (None, [_P, _I, _I, _I64, _P]),
         "orc_pyr_down": (None, [_P, _I, _I, _P]),
         "orc_median3": (None, [_P, _I, _I, _P]),
+        "orc_remove_small": (None, [_P, _I, _I, _I]),
         "orc_bilateral": (None, [_P, _I, _I, _I, _D, _D, _P]),
         "orc_denoise": (None, [_P, _I, _I, _I, _D, _D, _P, _P]),
         "orc_poly_projector": (_I, [_I, _D, _P]),
@@ -112,6 +113,14 @@ def units(raw: np.ndarray, bit_depth: int) -> np.ndarray:
     raw = np.ascontiguousarray(raw)
     out = np.empty(raw.shape, np.float64)
     lib().orc_units(_ptr(raw), raw.dtype.itemsize, bit_depth, raw.size, _ptr(out))
+    return out
+
+
+def remove_small(mask: np.ndarray, min_area: int) -> np.ndarray:
+    """Mask without its 8-connected components of fewer than min_area pixels."""
+    out = np.ascontiguousarray(mask, dtype=np.uint8).copy()
+    h, w = out.shape
+    lib().orc_remove_small(_ptr(out), w, h, int(min_area))
     return out
 
 
@@ -353,6 +362,7 @@ class Params:
     dwt_levels: int = 3
     scale_shift: int = 5
     delta_base: float = 1.0
+    min_area: int = 0          # components below this many pixels removed (0: off; reading)
     denoise: int = 0           # Table 1 "Denoise" (off: a valid setting)
     den_radius: int = 2        # bilateral square radius (reading)
     den_sigma_s: float = 2.0   # bilateral spatial sigma, px (reading)
@@ -385,6 +395,9 @@ def frame(prev_raw, cur_raw, bit_depth: int, p: Params, y_f32=None):
         Sh = normalise(S)
         mask0, t = threshold(Sh, p.roi_q)
         mask = morph(mask0, p.r_open, p.r_close)
+        if p.min_area > 1:
+            out["mask_morph"] = mask
+            mask = remove_small(mask, p.min_area)
         out.update(flow=d, S=S, Sh=Sh, t=t, mask0=mask0)
     else:
         mask = np.zeros((h, w), np.uint8)
