@@ -132,6 +132,9 @@ typedef struct flowroi_config {
     int32_t den_radius;        /* bilateral square radius rb in [1, 3]: side 2rb+1 (2) */
     float den_sigma_s;         /* bilateral spatial sigma in pixels, > 0 (2.0) */
     float den_sigma_r;         /* bilateral range sigma in 8-bit units, > 0 (20.0) */
+    /* §Region of Interest extraction: residual small connected components
+     * removed by area after opening and closing (8-connectivity). */
+    int32_t min_area;          /* components with fewer pixels are removed; 0 = off, [0, 2^20] (0) */
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and

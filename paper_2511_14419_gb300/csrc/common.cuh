@@ -56,6 +56,7 @@ struct MethodConsts {
     // as powers of two, w = 2^-(den_ls[offset] + den_lr * (I(q) - I(p))^2),
     // den_ls = -log2 of the spatial weight over the (2 kDenMaxR + 1)^2
     // square (row-major, centred), den_lr = log2(e) / (2 sigma_r^2)
+    int min_area;  // components of the final mask below this many pixels removed (<= 1: off)
     int denoise, den_r;
     float den_ls[(2 * kDenMaxR + 1) * (2 * kDenMaxR + 1)];
     float den_lr;
@@ -90,6 +91,7 @@ struct FrameDesc {
     float *dbg_yf;                  // keep + 9/7: float coefficients, W*H
     float *dbg_thr;                 // keep: threshold on S^ (1 float)
     float *dbg_den;                 // keep + denoise: denoised flow input, W*H
+    int *cc_lab, *cc_cnt, *cc_area; // min_area > 1: component labels, local-root counts, areas (W*H each)
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
     uint8_t *llm[2];                // their RoI masks
 };

@@ -19,6 +19,8 @@ void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s)
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
 void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
+// Removal of small connected components of the final mask (four launches).
+void launch_cc(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 // Optional denoising of the flow input (level-0 tiles of the expansion).
 void launch_denoise(const BatchDesc *bd, const MethodConsts &mc, bool half, int grid, cudaStream_t s);
 
@@ -32,6 +34,7 @@ int occupancy_window(bool half, int win_r);
 int occupancy_mask_kernels();
 int occupancy_dwt(int wavelet);
 int occupancy_denoise(bool half, int radius);
+int occupancy_cc();
 
 bool flow_radius_supported(int r);
 bool morph_radius_supported(int r);

@@ -110,6 +110,7 @@ struct Stream {
     void *pyr[kMaxLevels] = {};
     void *gh[kMaxLevels] = {};
     float2 *flow[2] = {};
+    int *cc[3] = {};  // component labels, local-root counts, areas (min_area > 1)
     float *S = nullptr;
     unsigned *red = nullptr;
     void *ll[2] = {};
@@ -143,7 +144,7 @@ struct flowroi_ctx {
     cudaGraphExec_t graph[kDesc] = {};
     int graph_launches = 0;
     int desc_next = 0;
-    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0;
+    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0;
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -211,6 +212,7 @@ int validate_config(const flowroi_config *c)
     if (c->max_batch_frames < 1 || c->max_batch_frames > kMaxBatch) return fail(FLOWROI_EINVAL, "config.max_batch_frames must be in [1,64]");
     if (c->result_ring < 2 || c->result_ring > 16) return fail(FLOWROI_EINVAL, "config.result_ring must be in [2,16]");
     if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL)) return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
+    if (c->min_area < 0 || c->min_area > (1 << 20)) return fail(FLOWROI_EINVAL, "config.min_area must be in [0, 2^20]");
     if (c->denoise != 0 && c->denoise != 1) return fail(FLOWROI_EINVAL, "config.denoise must be 0 or 1");
     if (!denoise_radius_supported(c->den_radius)) return fail(FLOWROI_EINVAL, "config.den_radius must be in [1,3]");
     if (!(c->den_sigma_s > 0.f) || !(c->den_sigma_r > 0.f)) return fail(FLOWROI_EINVAL, "config.den_sigma_s/den_sigma_r must be > 0");
@@ -291,6 +293,8 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
     for (int k = 0; k < 2; k++) s->flow[k] = reinterpret_cast<float2 *>(take((size_t)s->lp[0] * s->H * sizeof(float2)));
     s->S = reinterpret_cast<float *>(take((size_t)s->lp[0] * s->H * sizeof(float)));
     s->red = reinterpret_cast<unsigned *>(take(kRedWords * sizeof(unsigned)));
+    if (c->cfg.min_area > 1)
+        for (int k = 0; k < 3; k++) s->cc[k] = reinterpret_cast<int *>(take(npx * sizeof(int)));
     for (int k = 0; k < 2; k++) {
         s->ll[k] = take((npx / 4) * 4);
         s->llm[k] = reinterpret_cast<uint8_t *>(take(npx / 4));
@@ -365,6 +369,9 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
     F.dbg_yf = e->dbg_yf;
     F.dbg_thr = e->dbg_thr;
     F.dbg_den = e->dbg_den;
+    F.cc_lab = s->cc[0];
+    F.cc_cnt = s->cc[1];
+    F.cc_area = s->cc[2];
     F.ll[0] = s->ll[0];
     F.ll[1] = s->ll[1];
     F.llm[0] = s->llm[0];
@@ -396,8 +403,8 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
 }
 
 const char *const kKernelNames[] = {"frame_init", "expand", "update", "window", "saliency", "select_find", "select_pass",
-                                    "morph", "dwt", "denoise"};
-enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE };
+                                    "morph", "dwt", "denoise", "components"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC };
 
 // Runs one launch, bracketed by an event pair when profiling.
 template <class Fn>
@@ -463,6 +470,10 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     }
     timed(c, st, prof, K_MORPH, -1, -1, [&] { launch_morph(dd, mc, g(hd->mor_off[n], c->grid_mask), st); });
     cnt++;
+    if (mc.min_area > 1 && any_prev) {
+        timed(c, st, prof, K_CC, -1, -1, [&] { launch_cc(dd, mc, g(hd->sal_off[n], c->grid_cc), st); });
+        cnt += 4;
+    }
     for (int l = 1; l <= D; l++) {
         timed(c, st, prof, K_DWT, l, -1, [&] { launch_dwt(dd, mc, l, g(hd->dwt_off[l - 1][n], c->grid_dwt), st); });
         cnt++;
@@ -477,8 +488,10 @@ void CUDART_CB on_batch_done(void *p)
     flowroi_ctx *c = r->ctx;
     const double t = now_ms();
     if (c->err_host && *(volatile unsigned *)c->err_host) {
-        // A kernel gave up a bounded wait: results of this batch are not valid.
-        c->poison_msg = "a kernel's bounded wait for a TMA copy ran out";
+        // A kernel gave up a bounded wait or loop: results of this batch are not valid.
+        const unsigned code = *(volatile unsigned *)c->err_host;
+        c->poison_msg = code == 1u ? "a kernel's bounded wait for a TMA copy ran out"
+                                   : "a kernel's bounded union-find loop ran out";
         c->poisoned = true;
     }
     {
@@ -796,6 +809,7 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->den_radius = 2;
     cfg->den_sigma_s = 2.0f;
     cfg->den_sigma_r = 20.0f;
+    cfg->min_area = 0;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -837,6 +851,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     mc.wavelet = cfg->wavelet;
     mc.dwt_levels = cfg->dwt_levels;
     mc.shift = cfg->scale_shift;
+    mc.min_area = cfg->min_area;
     mc.denoise = cfg->denoise;
     mc.den_r = cfg->den_radius;
     const double log2e = 1.4426950408889634;
@@ -878,6 +893,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     c->grid_mask = std::max(1, om) * c->num_sms;
     c->grid_dwt = std::max(1, od) * c->num_sms;
     c->grid_den = cfg->denoise ? std::max(1, occupancy_denoise(c->half, cfg->den_radius)) * c->num_sms : 0;
+    c->grid_cc = cfg->min_area > 1 ? std::max(1, occupancy_cc()) * c->num_sms : 0;
     c->grid_frames = kMaxBatch;
     size_t freeb = 0, totalb = 0;
     CK(nullptr, cudaMemGetInfo(&freeb, &totalb));
