@@ -124,6 +124,21 @@ def remove_small(mask: np.ndarray, min_area: int) -> np.ndarray:
     return out
 
 
+def adjacent_merge(own_masks, k: int):
+    """§Region of Interest extraction: masks of neighbouring frames
+    incorporated (Table 1 "Adjacent factor").  Reading: the RoI mask of
+    frame j is the union of the per-frame masks of frames j-k .. j+k that
+    exist (the window is cut at both ends of the sequence)."""
+    n = len(own_masks)
+    out = []
+    for j in range(n):
+        m = np.zeros_like(own_masks[j])
+        for i in range(max(0, j - k), min(n - 1, j + k) + 1):
+            m = m | own_masks[i]
+        out.append(m)
+    return out
+
+
 def median3(img: np.ndarray) -> np.ndarray:
     """3x3 median, replicate border (§Optical flow extraction, denoising)."""
     img = _c(img, np.float64)
@@ -363,6 +378,7 @@ class Params:
     scale_shift: int = 5
     delta_base: float = 1.0
     min_area: int = 0          # components below this many pixels removed (0: off; reading)
+    adjacent: int = 0          # Table 1 "Adjacent factor" k (sequence() merges masks of j-k..j+k)
     denoise: int = 0           # Table 1 "Denoise" (off: a valid setting)
     den_radius: int = 2        # bilateral square radius (reading)
     den_sigma_s: float = 2.0   # bilateral spatial sigma, px (reading)
@@ -414,3 +430,25 @@ def frame(prev_raw, cur_raw, bit_depth: int, p: Params, y_f32=None):
         out["delta"] = delta
     out.update(y=y, cmask=cm, q=q, coeffs=roi_shift(q, cm, p.scale_shift))
     return out
+
+
+def sequence(raw_frames, bit_depth: int, p: Params):
+    """Whole hot path for a finished sequence of frames of one stream: each
+    frame's own mask from frame() (flow against its predecessor), then the
+    adjacent-factor merge, then the JPEG2000 front end of every frame with
+    its merged mask.  Returns a list of dicts (own_mask, mask, coeffs, ...)."""
+    outs = [frame(raw_frames[t - 1] if t > 0 else None, raw_frames[t], bit_depth, p) for t in range(len(raw_frames))]
+    merged = adjacent_merge([o["mask"] for o in outs], p.adjacent)
+    for o, m, raw in zip(outs, merged, raw_frames):
+        o["own_mask"] = o["mask"]
+        o["mask"] = m
+        x = dc_shift(raw, bit_depth)
+        cm = wavelet_mask(m, p.dwt_levels, p.wavelet)
+        if p.wavelet == 53:
+            q = dwt2d(x, 53, p.dwt_levels)
+        else:
+            y = dwt2d(x.astype(np.float64), 97, p.dwt_levels)
+            _, delta, _, _ = delta_table(p.dwt_levels, bit_depth, p.delta_base)
+            q = quantise_f64(y, p.dwt_levels, delta)
+        o.update(cmask=cm, q=q, coeffs=roi_shift(q, cm, p.scale_shift))
+    return outs
