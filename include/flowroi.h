@@ -96,8 +96,8 @@ extern "C" {
 
 /* ---- configuration ----------------------------------------------------- */
 /* Method parameters.  Table 1 of the paper names the user parameters (RoI
- * threshold, scaling factor, denoise; the adjacent factor is not on this
- * path; compression rate acts downstream).  The estimator constants are not
+ * threshold, scaling factor, denoise, adjacent factor; compression rate
+ * acts downstream).  The estimator constants are not
  * given by the paper; the defaults are the values this library documents
  * (pyramid 5 levels, 3 iterations, 15x15 box window, 5x5 expansion with
  * sigma 1.1, lambda 1e-3 in 8-bit units, opening radius 1, closing
@@ -135,6 +135,14 @@ typedef struct flowroi_config {
     /* §Region of Interest extraction: residual small connected components
      * removed by area after opening and closing (8-connectivity). */
     int32_t min_area;          /* components with fewer pixels are removed; 0 = off, [0, 2^20] (0) */
+    /* Table 1 "Adjacent factor" (§Region of Interest extraction: masks of
+     * neighbouring frames incorporated).  The RoI mask of frame j is the
+     * union of the per-frame masks of frames j-k .. j+k, so frame j's mask
+     * and coefficients are ready once frame j+k has been processed, or
+     * after flowroi_flush / flowroi_end_stream, which finish the last k
+     * frames of a stream with the frames there are.  Needs
+     * result_ring >= 2k + 2. */
+    int32_t adjacent;          /* k in [0, 4] (0) */
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and
@@ -232,7 +240,9 @@ FLOWROI_API int flowroi_get_intermediate(flowroi_ctx *ctx, int64_t stream_id, in
                              void *out, int out_on_device, int timeout_ms);
 
 /* Launch everything pending and wait (at most timeout_ms, < 0: no limit)
- * until every submitted frame has finished. */
+ * until every submitted frame has finished.  With an adjacent factor k > 0
+ * this also finishes the last k frames of every stream, merging only the
+ * neighbours submitted so far. */
 FLOWROI_API int flowroi_flush(flowroi_ctx *ctx, int timeout_ms);
 
 /* End a stream: waits for its frames in flight, then frees its device

@@ -16,6 +16,7 @@ constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 
 // Tile shapes (output pixels per block) of each kernel family.
 constexpr int kDenMaxR = 3;                // largest bilateral radius of the optional denoising
+constexpr int kMaxAdj = 4;                 // largest adjacent factor (masks of frames t-k..t+k merged)
 constexpr int kExpTW = 256, kExpTH = 16;   // pyramid + polynomial expansion
 constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
 constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
@@ -92,6 +93,16 @@ struct FrameDesc {
     float *dbg_thr;                 // keep: threshold on S^ (1 float)
     float *dbg_den;                 // keep + denoise: denoised flow input, W*H
     int *cc_lab, *cc_cnt, *cc_area; // min_area > 1: component labels, local-root counts, areas (W*H each)
+    // JPEG2000 front end of this entry: the frame it codes (the flow frame
+    // itself, or with an adjacent factor k > 0 the frame k earlier), its
+    // samples, RoI mask and outputs
+    const void *dwt_raw;
+    uint8_t *dwt_mask;
+    int32_t *dwt_coeffs;
+    float *dwt_yf;                  // keep + 9/7: float coefficients of that frame
+    int do_flow, do_dwt;
+    int n_adj;                      // per-frame masks ORed into dwt_mask (0: none, dwt_mask is the frame's own)
+    const uint8_t *adj[2 * kMaxAdj + 1];
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
     uint8_t *llm[2];                // their RoI masks
 };
@@ -107,8 +118,9 @@ struct BatchDesc {
     int win_off[kMaxLevels][kMaxBatch + 1];    // window tiles
     int dwt_off[kMaxLevels][kMaxBatch + 1];
     int sal_off[kMaxBatch + 1];     // frames with a predecessor only
-    int mor_off[kMaxBatch + 1];     // every frame
+    int mor_off[kMaxBatch + 1];     // every flow frame
     int frm_off[kMaxBatch + 1];     // one unit per frame (init / select-find)
+    int mrg_off[kMaxBatch + 1];     // adjacent-mask merge: 4096-byte units of entries with n_adj > 0
     FrameDesc f[kMaxBatch];
 };
 

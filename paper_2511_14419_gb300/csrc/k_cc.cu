@@ -34,12 +34,16 @@ constexpr int kCcN = kCcTW * kCcTH;
 constexpr unsigned kErrCcLoop = 2u;  // error word: a union-find loop ran out
 constexpr int kCcLimit = 1 << 24;
 
-__device__ __forceinline__ int find_s(const int *P, int x, bool &bad)
+// Root of x, halving the path on the way (a non-root's parent may be
+// replaced by any ancestor: roots are only ever linked, never unlinked).
+__device__ __forceinline__ int find_s(int *P, int x, bool &bad)
 {
     for (int k = 0; k < kCcLimit; k++) {
         const int p = P[x];
         if (p == x) return x;
-        x = p;
+        const int gp = P[p];
+        if (gp != p) P[x] = gp;
+        x = gp;
     }
     bad = true;
     return x;
@@ -67,8 +71,23 @@ __device__ __forceinline__ void union_s(int *P, int a, int b, bool &bad)
 // other blocks link roots concurrently).
 __device__ __forceinline__ int find_g(int *L, int x, bool &bad)
 {
+    volatile int *V = L;
     for (int k = 0; k < kCcLimit; k++) {
-        const int p = *reinterpret_cast<volatile int *>(L + x);
+        const int p = V[x];
+        if (p == x) return x;
+        const int gp = V[p];
+        if (gp != p) V[x] = gp;
+        x = gp;
+    }
+    bad = true;
+    return x;
+}
+
+// Root of x once no union runs any more (read-only path).
+__device__ __forceinline__ int find_ro(const int *L, int x, bool &bad)
+{
+    for (int k = 0; k < kCcLimit; k++) {
+        const int p = __ldg(L + x);
         if (p == x) return x;
         x = p;
     }
@@ -117,12 +136,10 @@ __device__ __forceinline__ CcTile cc_tile(const BatchDesc *bd, int t)
 
 }  // namespace
 
-// 1. tile-local labelling (dynamic shared memory: parents and counts)
+// 1. tile-local labelling (shared memory: parents, then the counts)
 __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ bd)
 {
-    extern __shared__ int sm_cc[];
-    int *P = sm_cc;          // [kCcN] parent (local index), -1 = background
-    int *cnt = sm_cc + kCcN; // [kCcN] pixel count of each local root
+    __shared__ int P[kCcN];  // parent (local index), -1 = background; then the count of each local root
     const int total = __ldg(bd->sal_off + bd->nframes);
     const int c = threadIdx.x;
     bool bad = false;
@@ -130,24 +147,30 @@ __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ 
         const CcTile T = cc_tile(bd, t);
         const uint8_t *mask = T.F->mask;
         const int gx = T.x0 + c;
-#pragma unroll 4
+#pragma unroll 8
         for (int r = 0; r < kCcTH; r++) {
             const int gy = T.y0 + r, i = r * kCcTW + c;
             const bool fg = gx < T.w && gy < T.h && mask[(size_t)gy * T.w + gx] != 0;
             P[i] = fg ? i : -1;
-            cnt[i] = 0;
         }
         __syncthreads();
+        // Raster-earlier neighbours, with the unions other pixels make
+        // anyway left out: the north pixel, when set, is 8-adjacent to the
+        // west and both diagonal ones (their own unions join them to it);
+        // otherwise the west pixel, when set, covers the north-west one.
         for (int r = 0; r < kCcTH; r++) {
             const int i = r * kCcTW + c;
             if (P[i] < 0) continue;
-            if (c > 0 && P[i - 1] >= 0) union_s(P, i, i - 1, bad);
-            if (r > 0) {
-                const int u = i - kCcTW;
-                if (c > 0 && P[u - 1] >= 0) union_s(P, i, u - 1, bad);
-                if (P[u] >= 0) union_s(P, i, u, bad);
-                if (c + 1 < kCcTW && P[u + 1] >= 0) union_s(P, i, u + 1, bad);
+            const int u = i - kCcTW;
+            const bool n = r > 0 && P[u] >= 0;
+            const bool wst = c > 0 && P[i - 1] >= 0;
+            if (n) {
+                union_s(P, i, u, bad);
+                continue;
             }
+            if (wst) union_s(P, i, i - 1, bad);
+            else if (r > 0 && c > 0 && P[u - 1] >= 0) union_s(P, i, u - 1, bad);
+            if (r > 0 && c + 1 < kCcTW && P[u + 1] >= 0) union_s(P, i, u + 1, bad);
         }
         __syncthreads();
         int root[kCcTH];
@@ -156,14 +179,25 @@ __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ 
             const int i = r * kCcTW + c;
             root[r] = P[i] >= 0 ? find_s(P, i, bad) : -1;
         }
-        __syncthreads();  // every find is done before counts and compression
+        __syncthreads();  // every find is done: the parents are not needed any more
 #pragma unroll
-        for (int r = 0; r < kCcTH; r++)
-            if (root[r] >= 0) {
-                // one atomic per distinct root in the warp
-                const unsigned grp = __match_any_sync(__activemask(), root[r]);
-                if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&cnt[root[r]], __popc(grp));
+        for (int r = 0; r < kCcTH; r++) P[r * kCcTW + c] = 0;
+        __syncthreads();
+        // counts: one atomic per run of equal roots down the column
+        {
+            int cur = -1, run = 0;
+#pragma unroll
+            for (int r = 0; r < kCcTH; r++) {
+                if (root[r] == cur) {
+                    run++;
+                } else {
+                    if (cur >= 0) atomicAdd(&P[cur], run);
+                    cur = root[r];
+                    run = 1;
+                }
             }
+            if (cur >= 0) atomicAdd(&P[cur], run);
+        }
         __syncthreads();
         int *L = T.F->cc_lab, *C = T.F->cc_cnt, *A = T.F->cc_area;
         if (gx < T.w) {
@@ -176,7 +210,7 @@ __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ 
                 // frame index of the local root (same raster order as the local index)
                 const int lab = ro < 0 ? -1 : (T.y0 + ro / kCcTW) * T.w + T.x0 + ro % kCcTW;
                 L[g] = lab;
-                C[g] = ro == i ? cnt[i] : 0;
+                C[g] = ro == i ? P[i] : 0;
                 if (ro == i) A[g] = 0;
             }
         }
@@ -226,69 +260,118 @@ __global__ void __launch_bounds__(256) k_cc_merge(const BatchDesc *__restrict__ 
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(bd->err, kErrCcLoop);
 }
 
-// 3. areas of the final components
+// 3. areas of the final components (each local root adds its count; the
+// column's counts are all read before any root is looked up)
 __global__ void __launch_bounds__(256) k_cc_count(const BatchDesc *__restrict__ bd)
 {
     const int total = __ldg(bd->sal_off + bd->nframes);
     bool bad = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const CcTile T = cc_tile(bd, t);
-        int *L = T.F->cc_lab, *C = T.F->cc_cnt, *A = T.F->cc_area;
+        int *L = T.F->cc_lab, *A = T.F->cc_area;
+        const int *C = T.F->cc_cnt;
         const int gx = T.x0 + threadIdx.x;
         if (gx >= T.w) continue;
-        for (int r = 0; r < kCcTH; r++) {
-            const int gy = T.y0 + r;
-            if (gy >= T.h) break;
-            const int g = gy * T.w + gx;
-            const int n = C[g];
-            if (n == 0) continue;
+        const int nr = min(kCcTH, T.h - T.y0);
+        static_assert(kCcTH <= 32, "rows of a column as bits");
+        unsigned rows = 0u;  // rows holding a local root
+#pragma unroll
+        for (int r = 0; r < kCcTH; r++)
+            if (r < nr && __ldg(C + (size_t)(T.y0 + r) * T.w + gx) != 0) rows |= 1u << r;
+        while (rows) {
+            const int r = __ffs(rows) - 1;
+            rows &= rows - 1u;
+            const int g = (T.y0 + r) * T.w + gx;
             const int root = find_g(L, g, bad);
-            L[g] = root;  // shortcut for the filter (root <= g)
-            atomicAdd(A + root, n);
+            L[g] = root;  // the filter reaches the root in one step (root <= g)
+            atomicAdd(A + root, __ldg(C + g));
         }
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(bd->err, kErrCcLoop);
 }
 
-// 4. clear the pixels of components below min_area
+// 4. clear the pixels of components below min_area.  After step 3 a pixel's
+// label is its local root, whose label is the final root: the column's
+// labels, roots and areas are read in three batches.
 __global__ void __launch_bounds__(256) k_cc_filter(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
     const int total = __ldg(bd->sal_off + bd->nframes);
     bool bad = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const CcTile T = cc_tile(bd, t);
-        int *L = T.F->cc_lab, *A = T.F->cc_area;
+        const int *L = T.F->cc_lab, *A = T.F->cc_area;
         uint8_t *mask = T.F->mask;
         const int gx = T.x0 + threadIdx.x;
         if (gx >= T.w) continue;
-        for (int r = 0; r < kCcTH; r++) {
-            const int gy = T.y0 + r;
-            if (gy >= T.h) break;
-            const int g = gy * T.w + gx;
-            const int lab = L[g];
-            if (lab < 0) continue;
-            const int root = find_g(L, lab, bad);
-            if (__ldg(A + root) < mc.min_area) mask[g] = 0;
-        }
+        const int nr = min(kCcTH, T.h - T.y0);
+        int rt[kCcTH];
+#pragma unroll
+        for (int r = 0; r < kCcTH; r++) rt[r] = r < nr ? __ldg(L + (size_t)(T.y0 + r) * T.w + gx) : -1;
+#pragma unroll
+        for (int r = 0; r < kCcTH; r++)
+            if (rt[r] >= 0) rt[r] = __ldg(L + rt[r]);
+#pragma unroll
+        for (int r = 0; r < kCcTH; r++)
+            if (rt[r] >= 0 && __ldg(L + rt[r]) != rt[r]) rt[r] = find_ro(L, rt[r], bad);  // not expected
+#pragma unroll
+        for (int r = 0; r < kCcTH; r++)
+            if (rt[r] >= 0 && __ldg(A + rt[r]) < mc.min_area) mask[(size_t)(T.y0 + r) * T.w + gx] = 0;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicExch(bd->err, kErrCcLoop);
 }
 
-void launch_cc(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s)
+// Adjacent-factor merge (paper: §Region of Interest extraction, masks of
+// neighbouring frames incorporated; Table 1 "Adjacent factor").  Reading:
+// the RoI mask of frame j is the union (OR) of the per-frame masks of
+// frames j-k .. j+k that exist.  16 bytes per thread, 4096-byte units.
+__global__ void __launch_bounds__(256) k_merge(const BatchDesc *__restrict__ bd)
 {
-    static const size_t smem = 2 * kCcN * sizeof(int);
-    k_cc_local<<<grid, 256, smem, s>>>(bd);
-    k_cc_merge<<<grid, 256, 0, s>>>(bd);
-    k_cc_count<<<grid, 256, 0, s>>>(bd);
-    k_cc_filter<<<grid, 256, 0, s>>>(bd, mc);
+    const int nfr = bd->nframes;
+    const int *off = bd->mrg_off;
+    const int total = __ldg(off + nfr);
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int fi = find_frame(off, nfr, t);
+        const FrameDesc &F = bd->f[fi];
+        const size_t npx = (size_t)F.W * F.H;
+        const size_t o = (size_t)(t - __ldg(off + fi)) * 4096 + threadIdx.x * 16;
+        if (o >= npx) continue;
+        const int n = F.n_adj;
+        if (o + 16 <= npx) {
+            uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+            for (int j = 0; j < n; j++) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4 *>(F.adj[j] + o));
+                acc.x |= v.x;
+                acc.y |= v.y;
+                acc.z |= v.z;
+                acc.w |= v.w;
+            }
+            *reinterpret_cast<uint4 *>(F.dwt_mask + o) = acc;
+        } else {
+            for (size_t q = o; q < npx; q++) {
+                uint8_t a = 0;
+                for (int j = 0; j < n; j++) a |= F.adj[j][q];
+                F.dwt_mask[q] = a;
+            }
+        }
+    }
+}
+
+void launch_merge(const BatchDesc *bd, int grid, cudaStream_t s) { k_merge<<<grid, 256, 0, s>>>(bd); }
+
+void launch_cc(const BatchDesc *bd, const MethodConsts &mc, int step, int grid, cudaStream_t s)
+{
+    switch (step) {
+    case 0: k_cc_local<<<grid, 256, 0, s>>>(bd); break;
+    case 1: k_cc_merge<<<grid, 256, 0, s>>>(bd); break;
+    case 2: k_cc_count<<<grid, 256, 0, s>>>(bd); break;
+    default: k_cc_filter<<<grid, 256, 0, s>>>(bd, mc); break;
+    }
 }
 
 int occupancy_cc()
 {
-    const size_t smem = 2 * kCcN * sizeof(int);
-    cudaFuncSetAttribute(k_cc_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int a = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cc_local, 256, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_cc_local, 256, 0);
     return a;
 }
 

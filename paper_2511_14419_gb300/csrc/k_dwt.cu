@@ -28,7 +28,9 @@
 // coefficients are quantised, shifted and stored.  Outputs come from window centres, which
 // depend only on in-window samples.  The low-low band goes to a temporary
 // plane for the next level (or, at the last level, into the coefficient
-// plane).
+// plane).  A batch entry's DWT codes the frame named by its dwt_* fields
+// (with an adjacent factor, an earlier frame than the one whose flow the
+// entry computes).
 #include <mutex>
 #include <type_traits>
 
@@ -192,8 +194,8 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
     auto interior_async = [&](const FrameDesc &F, int ix0, int iy0) {
         if (!L1 || F.bpp != 2) return false;
         if (ix0 < 0 || iy0 < 0 || ix0 + EW > F.W || iy0 + EH > F.H) return false;
-        return ((reinterpret_cast<uintptr_t>(F.raw) | (uintptr_t)F.raw_pitch) & 7) == 0 &&
-               ((reinterpret_cast<uintptr_t>(F.mask) | (uintptr_t)F.W) & 3) == 0;
+        return ((reinterpret_cast<uintptr_t>(F.dwt_raw) | (uintptr_t)F.raw_pitch) & 7) == 0 &&
+               ((reinterpret_cast<uintptr_t>(F.dwt_mask) | (uintptr_t)F.W) & 3) == 0;
     };
     auto tile_origin = [&](int t, int &fi, int &ix0, int &iy0) {
         fi = find_frame(off, nfr, t);
@@ -206,8 +208,8 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
     };
     auto issue_async = [&](const FrameDesc &F, int ix0, int iy0, int buf) {
         constexpr int NQ = EW / 4;  // 8-byte sample chunks (and 4-byte mask chunks) per row
-        const uint8_t *raw = static_cast<const uint8_t *>(F.raw) + (size_t)iy0 * F.raw_pitch + (size_t)ix0 * 2;
-        const uint8_t *msk = F.mask + (size_t)iy0 * F.W + ix0;
+        const uint8_t *raw = static_cast<const uint8_t *>(F.dwt_raw) + (size_t)iy0 * F.raw_pitch + (size_t)ix0 * 2;
+        const uint8_t *msk = F.dwt_mask + (size_t)iy0 * F.W + ix0;
         uint16_t *rb = s_rb + (size_t)buf * EH * EW;
         uint8_t *mb = s_mb + (size_t)buf * EH * MW;
         for (int i = threadIdx.x; i < EH * NQ; i += blockDim.x) {
@@ -244,11 +246,11 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         // otherwise force their reloads).
         const V *llin = static_cast<const V *>(F.ll[level % 2]);
         const uint8_t *mlin = F.llm[level % 2];
-        const uint8_t *fraw = static_cast<const uint8_t *>(F.raw);
-        const uint8_t *fmask = F.mask;
+        const uint8_t *fraw = static_cast<const uint8_t *>(F.dwt_raw);
+        const uint8_t *fmask = F.dwt_mask;
         const int raw_pitch = F.raw_pitch, bpp = F.bpp, dc_off = F.dc_off;
-        int32_t *const coeffs = F.coeffs;
-        float *const dbg_yf = F.dbg_yf;
+        int32_t *const coeffs = F.dwt_coeffs;
+        float *const dbg_yf = F.dwt_yf;
         V *const llout = static_cast<V *>(F.ll[(level - 1) % 2]);
         uint8_t *const llmout = F.llm[(level - 1) % 2];
         const bool staged = L1 && interior_async(F, ix0, iy0);

@@ -19,8 +19,11 @@ void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s)
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
 void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
-// Removal of small connected components of the final mask (four launches).
-void launch_cc(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
+// Adjacent-factor merge of per-frame masks (entries with n_adj > 0).
+void launch_merge(const BatchDesc *bd, int grid, cudaStream_t s);
+// Removal of small connected components of the final mask: steps 0-3
+// (local labels, border unions, areas, filter), one launch each.
+void launch_cc(const BatchDesc *bd, const MethodConsts &mc, int step, int grid, cudaStream_t s);
 // Optional denoising of the flow input (level-0 tiles of the expansion).
 void launch_denoise(const BatchDesc *bd, const MethodConsts &mc, bool half, int grid, cudaStream_t s);
 

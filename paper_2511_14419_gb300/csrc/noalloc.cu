@@ -126,6 +126,10 @@ extern "C" int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, i
     F.raw = raw;
     F.mask = const_cast<uint8_t *>(mask);
     F.coeffs = coeffs;
+    F.dwt_raw = raw;
+    F.dwt_mask = const_cast<uint8_t *>(mask);
+    F.dwt_coeffs = coeffs;
+    F.do_dwt = 1;
     F.ll[0] = base + kNaDescBytes;
     F.ll[1] = base + kNaDescBytes + kNaLLBytes;
     F.llm[0] = base + kNaDescBytes + 2 * kNaLLBytes;

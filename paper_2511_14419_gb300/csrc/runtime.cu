@@ -82,7 +82,8 @@ struct Entry {
     int readers = 0;
     cudaEvent_t uploaded = nullptr;
     void *raw = nullptr;
-    uint8_t *mask = nullptr;
+    uint8_t *mask = nullptr;       // the delivered RoI mask (merged with neighbours' when adjacent > 0)
+    uint8_t *mask_own = nullptr;   // adjacent > 0: this frame's own mask (after morphology / components)
     int32_t *coeffs = nullptr;
     float2 *dbg_flow = nullptr;
     float *dbg_shat = nullptr;
@@ -101,7 +102,9 @@ struct Stream {
     int64_t next_seq = 0;
     int64_t last_frame_idx = 0;
     bool any_frame = false;
-    int64_t launched_seq = -1;
+    int64_t launched_seq = -1;     // last frame whose flow was launched
+    int64_t dwt_seq = 0;           // next frame whose JPEG2000 front end is not launched yet
+    bool draining = false;         // finish the last frames' merges with the frames there are
     bool ending = false;
     std::vector<std::unique_ptr<Entry>> ring;
     int lw[kMaxLevels] = {}, lh[kMaxLevels] = {}, lp[kMaxLevels] = {};
@@ -144,7 +147,7 @@ struct flowroi_ctx {
     cudaGraphExec_t graph[kDesc] = {};
     int graph_launches = 0;
     int desc_next = 0;
-    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0;
+    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0, grid_mrg = 0;
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -213,6 +216,9 @@ int validate_config(const flowroi_config *c)
     if (c->result_ring < 2 || c->result_ring > 16) return fail(FLOWROI_EINVAL, "config.result_ring must be in [2,16]");
     if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL)) return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
     if (c->min_area < 0 || c->min_area > (1 << 20)) return fail(FLOWROI_EINVAL, "config.min_area must be in [0, 2^20]");
+    if (c->adjacent < 0 || c->adjacent > kMaxAdj) return fail(FLOWROI_EINVAL, "config.adjacent must be in [0,4]");
+    if (c->result_ring < 2 * c->adjacent + 2)
+        return fail(FLOWROI_EINVAL, "config.result_ring must be at least 2*adjacent + 2");
     if (c->denoise != 0 && c->denoise != 1) return fail(FLOWROI_EINVAL, "config.denoise must be 0 or 1");
     if (!denoise_radius_supported(c->den_radius)) return fail(FLOWROI_EINVAL, "config.den_radius must be in [1,3]");
     if (!(c->den_sigma_s > 0.f) || !(c->den_sigma_r > 0.f)) return fail(FLOWROI_EINVAL, "config.den_sigma_s/den_sigma_r must be > 0");
@@ -264,6 +270,26 @@ int64_t stream_is_launchable(Stream *s)
     return next;
 }
 
+// The frame whose JPEG2000 front end runs with flow frame `seq` of s: the
+// same frame, or with adjacent factor k the frame seq - k once it exists
+// (its window d-k..d+k is then complete); -1 if none.
+int64_t dwt_target_with_flow(flowroi_ctx *c, Stream *s, int64_t seq)
+{
+    const int k = c->cfg.adjacent;
+    if (k == 0) return seq;
+    const int64_t d = seq - k;
+    return d >= 0 && d >= s->dwt_seq ? d : -1;
+}
+
+// A drain entry of s (no flow frame): the next frame whose front end has
+// not run, when s is draining (flush, end of stream) and has no flow frame
+// to launch; its window is cut at the last frame with a flow.
+int64_t stream_drain_target(flowroi_ctx *c, Stream *s)
+{
+    if (c->cfg.adjacent == 0 || !s->draining || stream_is_launchable(s) >= 0) return -1;
+    return s->dwt_seq <= s->launched_seq ? s->dwt_seq : -1;
+}
+
 // Byte plan of a stream's device block (carves pointers when base != null).
 size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
 {
@@ -303,6 +329,7 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
         Entry *e = s->ring[r].get();
         e->raw = take(npx * s->bpp);
         e->mask = reinterpret_cast<uint8_t *>(take(npx));
+        e->mask_own = c->cfg.adjacent > 0 ? reinterpret_cast<uint8_t *>(take(npx)) : nullptr;
         e->coeffs = reinterpret_cast<int32_t *>(take(npx * 4));
         if (c->keep) {
             e->dbg_flow = reinterpret_cast<float2 *>(take(npx * sizeof(float2)));
@@ -331,7 +358,11 @@ bool encode_stream_maps(flowroi_ctx *c, Stream *s)
     return true;
 }
 
-void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
+// One batch entry of stream s: the flow (and mask) of frame `e` if not
+// null, and the JPEG2000 front end of frame `d` if not null (the same frame
+// when adjacent = 0; with adjacent = k, frame e's seq - k, or during a drain
+// an earlier frame alone), with the per-frame masks of d's window.
+void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
 {
     std::memset(&F, 0, sizeof F);
     for (int l = 0; l < c->cfg.pyr_levels; l++) F.gh_map[l] = s->gh_map[l];
@@ -339,13 +370,13 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
     F.H = s->H;
     F.bpp = s->bpp;
     F.bit_depth = s->bit_depth;
-    F.has_prev = e->has_prev ? 1 : 0;
+    F.do_flow = e ? 1 : 0;
+    F.has_prev = e && e->has_prev ? 1 : 0;
     F.keep = c->keep ? 1 : 0;
     F.raw_pitch = s->W * s->bpp;
     F.dc_off = 1 << (s->bit_depth - 1);
     F.unit_scale = (float)(255.0 / (double)((1 << s->bit_depth) - 1));
-    F.raw = e->raw;
-    const int cur = (int)(e->seq & 1), prv = cur ^ 1;
+    const int cur = e ? (int)(e->seq & 1) : 0, prv = cur ^ 1;
     for (int l = 0; l < c->cfg.pyr_levels; l++) {
         F.lw[l] = s->lw[l];
         F.lh[l] = s->lh[l];
@@ -361,14 +392,6 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
     F.flow[1] = s->flow[1];
     F.S = s->S;
     F.red = s->red;
-    F.mask = e->mask;
-    F.coeffs = e->coeffs;
-    F.dbg_flow = e->dbg_flow;
-    F.dbg_shat = e->dbg_shat;
-    F.dbg_mask0 = e->dbg_mask0;
-    F.dbg_yf = e->dbg_yf;
-    F.dbg_thr = e->dbg_thr;
-    F.dbg_den = e->dbg_den;
     F.cc_lab = s->cc[0];
     F.cc_cnt = s->cc[1];
     F.cc_area = s->cc[2];
@@ -376,6 +399,33 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, FrameDesc &F)
     F.ll[1] = s->ll[1];
     F.llm[0] = s->llm[0];
     F.llm[1] = s->llm[1];
+    if (e) {
+        F.raw = e->raw;
+        F.mask = c->cfg.adjacent > 0 ? e->mask_own : e->mask;
+        F.coeffs = e->coeffs;
+        F.dbg_flow = e->dbg_flow;
+        F.dbg_shat = e->dbg_shat;
+        F.dbg_mask0 = e->dbg_mask0;
+        F.dbg_thr = e->dbg_thr;
+        F.dbg_den = e->dbg_den;
+    }
+    if (d) {
+        F.do_dwt = 1;
+        F.dwt_raw = d->raw;
+        F.dwt_mask = d->mask;
+        F.dwt_coeffs = d->coeffs;
+        F.dwt_yf = d->dbg_yf;
+        const int k = c->cfg.adjacent;
+        if (k > 0) {
+            // own masks of frames d-k .. d+k that exist and have their flow launched
+            const int64_t last = e ? e->seq : s->launched_seq;
+            const int64_t R = (int64_t)s->ring.size();
+            for (int64_t m = std::max<int64_t>(0, d->seq - k); m <= std::min(last, d->seq + k); m++) {
+                Entry *o = s->ring[m % R].get();
+                if (o->seq == m) F.adj[F.n_adj++] = o->mask_own;
+            }
+        }
+    }
 }
 
 // Prefix tables of the batch (also the exact grids of the plain path).
@@ -386,25 +436,26 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
     for (int l = 0; l < kMaxLevels; l++) {
         bd.exp_off[l][0] = bd.flow_off[l][0] = bd.win_off[l][0] = bd.dwt_off[l][0] = 0;
     }
-    bd.sal_off[0] = bd.mor_off[0] = bd.frm_off[0] = 0;
+    bd.sal_off[0] = bd.mor_off[0] = bd.frm_off[0] = bd.mrg_off[0] = 0;
     for (int i = 0; i < n; i++) {
         const FrameDesc &F = bd.f[i];
         for (int l = 0; l < L; l++) {
-            bd.exp_off[l][i + 1] = bd.exp_off[l][i] + tiles(F.lw[l], F.lh[l], kExpTW, kExpTH);
+            bd.exp_off[l][i + 1] = bd.exp_off[l][i] + (F.do_flow ? tiles(F.lw[l], F.lh[l], kExpTW, kExpTH) : 0);
             bd.flow_off[l][i + 1] = bd.flow_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kUpdTW, kUpdRows) : 0);
             bd.win_off[l][i + 1] = bd.win_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kWinTW, kWinTH) : 0);
         }
         for (int l = 1; l <= D; l++)
-            bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH);
+            bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + (F.do_dwt ? tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH) : 0);
         bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
-        bd.mor_off[i + 1] = bd.mor_off[i] + tiles(F.W, F.H, kMorTW, kMorTH);
+        bd.mor_off[i + 1] = bd.mor_off[i] + (F.do_flow ? tiles(F.W, F.H, kMorTW, kMorTH) : 0);
+        bd.mrg_off[i + 1] = bd.mrg_off[i] + (F.n_adj > 0 ? (int)(((size_t)F.W * F.H + 4095) / 4096) : 0);
         bd.frm_off[i + 1] = i + 1;
     }
 }
 
 const char *const kKernelNames[] = {"frame_init", "expand", "update", "window", "saliency", "select_find", "select_pass",
-                                    "morph", "dwt", "denoise", "components"};
-enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC };
+                                    "morph", "dwt", "denoise", "components", "merge"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC, K_MERGE };
 
 // Runs one launch, bracketed by an event pair when profiling.
 template <class Fn>
@@ -471,8 +522,14 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     timed(c, st, prof, K_MORPH, -1, -1, [&] { launch_morph(dd, mc, g(hd->mor_off[n], c->grid_mask), st); });
     cnt++;
     if (mc.min_area > 1 && any_prev) {
-        timed(c, st, prof, K_CC, -1, -1, [&] { launch_cc(dd, mc, g(hd->sal_off[n], c->grid_cc), st); });
-        cnt += 4;
+        for (int step = 0; step < 4; step++) {
+            timed(c, st, prof, K_CC, step, -1, [&] { launch_cc(dd, mc, step, g(hd->sal_off[n], c->grid_cc), st); });
+            cnt++;
+        }
+    }
+    if (c->cfg.adjacent > 0) {
+        timed(c, st, prof, K_MERGE, -1, -1, [&] { launch_merge(dd, g(hd->mrg_off[n], c->grid_mrg), st); });
+        cnt++;
     }
     for (int l = 1; l <= D; l++) {
         timed(c, st, prof, K_DWT, l, -1, [&] { launch_dwt(dd, mc, l, g(hd->dwt_off[l - 1][n], c->grid_dwt), st); });
@@ -513,18 +570,30 @@ int step_locked(flowroi_ctx *c)
 {
     if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
     const int maxb = c->plain ? 1 : c->cfg.max_batch_frames;
-    std::vector<std::pair<Stream *, Entry *>> sel;
+    struct Pick {
+        Stream *s;
+        Entry *e;  // flow frame (null: drain entry)
+        Entry *d;  // frame whose JPEG2000 front end runs (null: none yet)
+    };
+    std::vector<Pick> sel;
     // Round-robin over streams, starting after the last one served.
     auto it = c->streams.upper_bound(c->rr_cursor);
     for (size_t visited = 0; visited < c->streams.size() && (int)sel.size() < maxb; visited++) {
         if (it == c->streams.end()) it = c->streams.begin();
         Stream *s = it->second.get();
+        const int64_t R = (int64_t)s->ring.size();
         const int64_t seq = stream_is_launchable(s);
-        if (seq >= 0) sel.emplace_back(s, s->ring[seq % (int64_t)s->ring.size()].get());
+        if (seq >= 0) {
+            const int64_t j = dwt_target_with_flow(c, s, seq);
+            sel.push_back({s, s->ring[seq % R].get(), j >= 0 ? s->ring[j % R].get() : nullptr});
+        } else {
+            const int64_t j = stream_drain_target(c, s);
+            if (j >= 0) sel.push_back({s, nullptr, s->ring[j % R].get()});
+        }
         ++it;
     }
     if (sel.empty()) return 0;
-    c->rr_cursor = sel.back().first->id;
+    c->rr_cursor = sel.back().s->id;
 
     const int k = c->desc_next;
     c->desc_next = (k + 1) % flowroi_ctx::kDesc;
@@ -534,9 +603,10 @@ int step_locked(flowroi_ctx *c)
     hd.err = c->err_dev;
     const int nflow = c->cfg.pyr_levels * c->cfg.iters;
     hd.final_flow_buf = (nflow - 1) & 1;
-    for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].first, sel[i].second, hd.f[i]);
+    for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].s, sel[i].e, sel[i].d, hd.f[i]);
     fill_offsets(c, hd);
-    for (auto &pr : sel) CK(c, cudaStreamWaitEvent(c->s_comp, pr.second->uploaded, 0));
+    for (auto &pk : sel)
+        if (pk.e) CK(c, cudaStreamWaitEvent(c->s_comp, pk.e->uploaded, 0));
     const size_t bytes = offsetof(BatchDesc, f) + sizeof(FrameDesc) * sel.size();
     CK(c, cudaMemcpyAsync(c->desc_dev[k], c->desc_host[k], bytes, cudaMemcpyHostToDevice, c->s_comp));
     CK(c, cudaEventRecord(c->desc_ev[k], c->s_comp));
@@ -568,10 +638,16 @@ int step_locked(flowroi_ctx *c)
         CK(c, cudaGraphLaunch(c->graph[k], c->s_comp));
     }
     BatchRec *rec = new BatchRec{c, {}};
-    for (auto &pr : sel) {
-        pr.second->state.store(E_LAUNCHED);
-        pr.first->launched_seq = pr.second->seq;
-        rec->entries.push_back(pr.second);
+    for (auto &pk : sel) {
+        if (pk.e) {
+            pk.e->state.store(E_LAUNCHED);
+            pk.s->launched_seq = pk.e->seq;
+        }
+        if (pk.d) {
+            // the frame is complete once this batch's front end has run
+            pk.s->dwt_seq = pk.d->seq + 1;
+            rec->entries.push_back(pk.d);
+        }
     }
     {
         std::lock_guard<std::mutex> lk(c->cmu);
@@ -590,7 +666,7 @@ int step_locked(flowroi_ctx *c)
 bool any_launchable(flowroi_ctx *c)
 {
     for (auto &kv : c->streams)
-        if (stream_is_launchable(kv.second.get()) >= 0) return true;
+        if (stream_is_launchable(kv.second.get()) >= 0 || stream_drain_target(c, kv.second.get()) >= 0) return true;
     return false;
 }
 
@@ -810,6 +886,7 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->den_sigma_s = 2.0f;
     cfg->den_sigma_r = 20.0f;
     cfg->min_area = 0;
+    cfg->adjacent = 0;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -894,6 +971,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     c->grid_dwt = std::max(1, od) * c->num_sms;
     c->grid_den = cfg->denoise ? std::max(1, occupancy_denoise(c->half, cfg->den_radius)) * c->num_sms : 0;
     c->grid_cc = cfg->min_area > 1 ? std::max(1, occupancy_cc()) * c->num_sms : 0;
+    c->grid_mrg = 8 * c->num_sms;
     c->grid_frames = kMaxBatch;
     size_t freeb = 0, totalb = 0;
     CK(nullptr, cudaMemGetInfo(&freeb, &totalb));
@@ -986,6 +1064,7 @@ static int submit_enqueue(flowroi_ctx *c, int64_t stream_id, const flowroi_frame
             CK(c, cudaMemcpy2DAsync(e->raw, (size_t)s->W * bpp, f->data, pitch, (size_t)s->W * bpp, s->H, kind, c->s_copy));
         CK(c, cudaEventRecord(e->uploaded, c->s_copy));
         e->state.store(E_PENDING);
+        s->draining = false;
         s->next_seq = seq + 1;
         s->last_frame_idx = f->frame_idx;
         s->any_frame = true;
@@ -1074,6 +1153,8 @@ int flowroi_flush(flowroi_ctx *c, int timeout_ms)
     for (;;) {
         {
             std::lock_guard<std::mutex> lk(c->mu);
+            // the last adjacent-factor frames of every stream finish with the frames there are
+            for (auto &kv : c->streams) kv.second->draining = true;
             if (c->manual) {
                 for (;;) {
                     int n = step_locked(c);
@@ -1113,6 +1194,7 @@ int flowroi_end_stream(flowroi_ctx *c, int64_t stream_id)
         if (it == c->streams.end()) return fail(FLOWROI_ENOSTREAM, "unknown stream %lld", (long long)stream_id);
         s = it->second.get();
         s->ending = true;
+        s->draining = true;
         for (auto &e : s->ring)
             if (e->state.load() == E_PENDING) {
                 e->state.store(E_EMPTY);
@@ -1136,6 +1218,16 @@ int flowroi_end_stream(flowroi_ctx *c, int64_t stream_id)
                 c->admitted -= s->bytes;
                 c->streams.erase(stream_id);
                 return FLOWROI_OK;
+            }
+        }
+        if (c->cfg.adjacent > 0) {
+            // frames still waiting for their merged mask: run their drain steps
+            if (c->manual) {
+                std::lock_guard<std::mutex> lk(c->mu);
+                const int n = step_locked(c);
+                if (n < 0) return n;
+            } else {
+                wake_scheduler(c);
             }
         }
         {

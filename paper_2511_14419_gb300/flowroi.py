@@ -46,7 +46,7 @@ class flowroi_config(ctypes.Structure):
         ("delta_base", ctypes.c_float), ("max_batch_frames", ctypes.c_int32), ("result_ring", ctypes.c_int32),
         ("flags", ctypes.c_uint32), ("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
         ("denoise", ctypes.c_int32), ("den_radius", ctypes.c_int32), ("den_sigma_s", ctypes.c_float),
-        ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32),
+        ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32), ("adjacent", ctypes.c_int32),
     ]
 
 
