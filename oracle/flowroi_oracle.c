@@ -268,8 +268,19 @@ void orc_flow_upsample(const double *dc, int wc, int hc, int w, int h, double *d
  * then G and h are averaged over a (2r+1)^2 box clipped to the image (mean
  * over the in-image samples) and d = adj(G) h / (det G + lambda); d becomes
  * the next iteration's d~.  dprior and d: dx plane then dy plane. */
+void orc_flow_iterate_off(const double *f1, const double *f2, int w, int h, const double *dprior,
+                          int iters, int win_r, double lambda, double ox, double oy, double *d);
+
 void orc_flow_iterate(const double *f1, const double *f2, int w, int h, const double *dprior,
                       int iters, int win_r, double lambda, double *d)
+{
+    orc_flow_iterate_off(f1, f2, w, h, dprior, iters, win_r, lambda, 0.0, 0.0, d);
+}
+
+/* The same with the second expansion translated by (-ox, -oy): it is read
+ * at x + d~ + (ox, oy).  Registration aligns the predecessor this way. */
+void orc_flow_iterate_off(const double *f1, const double *f2, int w, int h, const double *dprior,
+                          int iters, int win_r, double lambda, double ox, double oy, double *d)
 {
     int64_t n = (int64_t)w * h;
     const double *A11a = f1, *A12a = f1 + n, *A22a = f1 + 2 * n, *b1a = f1 + 3 * n, *b2a = f1 + 4 * n;
@@ -282,7 +293,7 @@ void orc_flow_iterate(const double *f1, const double *f2, int w, int h, const do
             for (int x = 0; x < w; x++) {
                 int64_t p = (int64_t)y * w + x;
                 double ddx = cur[p], ddy = cur[n + p];
-                double xs = x + ddx, ys = y + ddy;
+                double xs = x + ddx + ox, ys = y + ddy + oy;
                 double a11 = 0.5 * (A11a[p] + bilinear(A11b, w, h, xs, ys));
                 double a12 = 0.5 * (A12a[p] + bilinear(A12b, w, h, xs, ys));
                 double a22 = 0.5 * (A22a[p] + bilinear(A22b, w, h, xs, ys));
@@ -326,8 +337,14 @@ void orc_flow_iterate(const double *f1, const double *f2, int w, int h, const do
 /* Full coarse-to-fine flow between the current image f1 and the previous
  * image f2 (both in 8-bit units, w x h), `levels` pyramid levels.  The
  * coarsest level starts from d~ = 0.  Output d: dx plane then dy plane. */
-int orc_flow(const double *cur, const double *prev, int w, int h, int levels, int poly_n_half,
-             double sigma, int iters, int win_r, double lambda, double *d)
+/* Coarse-to-fine flow of the current image against the previous image
+ * registered to it: the previous frame translated by the drift (sx, sy)
+ * (level-0 pixels; cur(x) ~ prev(x - s)), i.e. at level l its expansion
+ * read at x + d~ - s / 2^l.  The expansion is a linear shift-invariant
+ * filter, so this is the expansion of the translated frame away from the
+ * border.  orc_flow is the zero drift. */
+int orc_flow_reg(const double *cur, const double *prev, int w, int h, int levels, int poly_n_half,
+                 double sigma, int iters, int win_r, double lambda, double sx, double sy, double *d)
 {
     if (levels < 1) return -1;
     int lw[32], lh[32];
@@ -356,7 +373,8 @@ int orc_flow(const double *cur, const double *prev, int w, int h, int levels, in
         orc_poly_expand(p1[l], lw[l], lh[l], poly_n_half, sigma, f1);
         orc_poly_expand(p2[l], lw[l], lh[l], poly_n_half, sigma, f2);
         if (dc) orc_flow_upsample(dc, wc, hc, lw[l], lh[l], dp);
-        orc_flow_iterate(f1, f2, lw[l], lh[l], dp, iters, win_r, lambda, dl);
+        const double sc = 1.0 / (double)(1 << l);
+        orc_flow_iterate_off(f1, f2, lw[l], lh[l], dp, iters, win_r, lambda, -sx * sc, -sy * sc, dl);
         free(f1); free(f2); free(dp); free(dc);
         dc = dl; wc = lw[l]; hc = lh[l];
     }
@@ -364,6 +382,12 @@ int orc_flow(const double *cur, const double *prev, int w, int h, int levels, in
     free(dc);
     for (int l = 0; l < levels; l++) { free(p1[l]); free(p2[l]); }
     return 0;
+}
+
+int orc_flow(const double *cur, const double *prev, int w, int h, int levels, int poly_n_half,
+             double sigma, int iters, int win_r, double lambda, double *d)
+{
+    return orc_flow_reg(cur, prev, w, h, levels, poly_n_half, sigma, iters, win_r, lambda, 0.0, 0.0, d);
 }
 
 /* ------------------------------------------------------------------ a5 --

@@ -68,6 +68,7 @@ def _declare(L):
         "orc_flow_upsample": (None, [_P, _I, _I, _I, _I, _P]),
         "orc_flow_iterate": (None, [_P, _P, _I, _I, _P, _I, _I, _D, _P]),
         "orc_flow": (_I, [_P, _P, _I, _I, _I, _I, _D, _I, _I, _D, _P]),
+        "orc_flow_reg": (_I, [_P, _P, _I, _I, _I, _I, _D, _I, _I, _D, _D, _D, _P]),
         "orc_saliency": (None, [_P, _I, _I, _D, _P]),
         "orc_normalise": (None, [_P, _I64, _P]),
         "orc_quantile_k": (_I64, [_F, _I64]),
@@ -219,6 +220,78 @@ def flow(cur: np.ndarray, prev: np.ndarray, levels: int, n_half: int = 2, sigma:
     if lib().orc_flow(_ptr(cur), _ptr(prev), w, h, levels, n_half, sigma, iters, win_r, lam, _ptr(out)) != 0:
         raise ValueError("bad flow arguments")
     return out
+
+
+def flow_reg(cur: np.ndarray, prev: np.ndarray, levels: int, n_half: int, sigma: float, iters: int,
+             win_r: int, lam: float, drift) -> np.ndarray:
+    """flow() against the previous frame registered to the current one by
+    the drift s = (sx, sy) (cur(x) ~ prev(x - s)): the flow that is left
+    after the drift."""
+    cur = _c(cur, np.float64)
+    prev = _c(prev, np.float64)
+    h, w = cur.shape
+    out = np.empty((2, h, w), np.float64)
+    if lib().orc_flow_reg(_ptr(cur), _ptr(prev), w, h, levels, n_half, sigma, iters, win_r, lam,
+                          float(drift[0]), float(drift[1]), _ptr(out)) != 0:
+        raise ValueError("bad flow arguments")
+    return out
+
+
+def _next_pow2(n: int) -> int:
+    return 1 << max(0, (int(n) - 1).bit_length())
+
+
+def phase_correlate(prev_img: np.ndarray, cur_img: np.ndarray):
+    """§Optical flow extraction: each frame is registered to its predecessor
+    by phase correlation (global translational drift).  Readings: both
+    images Hann-windowed (symmetric, over the image size) and zero-padded to
+    the next power of two per axis, each after its mean is removed (else
+    the window's own, unshifted, spectrum dominates); X = F_cur conj(F_prev),
+    R = X / (|X| + 0.01 max|X|) (the normalised cross-power spectrum, with
+    frequencies that carry almost no energy kept from dominating through
+    their noise); r = real(IFFT(R)); the first
+    maximum of r (row-major) gives the integer shift, wrapped to
+    (-N/2, N/2]; each axis refined by the vertex of the parabola through r
+    at the peak and its two circular neighbours (when that parabola opens
+    downwards; clamped to +-0.5).  Returns (sx, sy): the content moved by
+    +s from prev to cur, cur(x) ~ prev(x - s)."""
+    a = _c(prev_img, np.float64)
+    b = _c(cur_img, np.float64)
+    h, w = a.shape
+    wy = np.hanning(h) if h > 1 else np.ones(1)
+    wx = np.hanning(w) if w > 1 else np.ones(1)
+    win = np.outer(wy, wx)
+    ny, nx = _next_pow2(h), _next_pow2(w)
+    A = np.fft.fft2((a - a.mean()) * win, s=(ny, nx))
+    B = np.fft.fft2((b - b.mean()) * win, s=(ny, nx))
+    X = B * np.conj(A)
+    mag = np.abs(X)
+    R = X / (mag + 0.01 * mag.max()) if mag.max() > 0 else X
+    r = np.real(np.fft.ifft2(R))
+    k = int(np.argmax(r))
+    ky, kx = divmod(k, nx)
+
+    def sub(c0, cm, cp):
+        den = cm - 2.0 * c0 + cp
+        if den >= 0.0:
+            return 0.0
+        return float(np.clip((cm - cp) / (2.0 * den), -0.5, 0.5))
+
+    dx = sub(r[ky, kx], r[ky, (kx - 1) % nx], r[ky, (kx + 1) % nx])
+    dy = sub(r[ky, kx], r[(ky - 1) % ny, kx], r[(ky + 1) % ny, kx])
+    sx = (kx - nx if kx > nx // 2 else kx) + dx
+    sy = (ky - ny if ky > ny // 2 else ky) + dy
+    return sx, sy
+
+
+def register(prev_img: np.ndarray, cur_img: np.ndarray, level: int):
+    """Global drift (level-0 pixels) from phase correlation of the level-`level`
+    pyramid images of the two flow inputs."""
+    a, b = _c(prev_img, np.float64), _c(cur_img, np.float64)
+    for _ in range(level):
+        a, b = pyr_down(a), pyr_down(b)
+    sx, sy = phase_correlate(a, b)
+    return sx * (1 << level), sy * (1 << level)
 
 
 def saliency(d: np.ndarray, alpha: float) -> np.ndarray:
@@ -379,6 +452,8 @@ class Params:
     delta_base: float = 1.0
     min_area: int = 0          # components below this many pixels removed (0: off; reading)
     adjacent: int = 0          # Table 1 "Adjacent factor" k (sequence() merges masks of j-k..j+k)
+    register: int = 0          # registration of each frame to its predecessor (phase correlation)
+    reg_level: int = 2         # pyramid level the phase correlation runs on (reading)
     denoise: int = 0           # Table 1 "Denoise" (off: a valid setting)
     den_radius: int = 2        # bilateral square radius (reading)
     den_sigma_s: float = 2.0   # bilateral spatial sigma, px (reading)
@@ -406,7 +481,14 @@ def frame(prev_raw, cur_raw, bit_depth: int, p: Params, y_f32=None):
             I1 = denoise(I1, p.den_radius, p.den_sigma_s, p.den_sigma_r)
             I2 = denoise(I2, p.den_radius, p.den_sigma_s, p.den_sigma_r)
             out["denoised"] = I1
-        d = flow(I1, I2, p.pyr_levels, p.poly_n_half, p.poly_sigma, p.iters, p.win_r, p.lam)
+        if p.register:
+            # flow of the pair after the predecessor is registered to the
+            # current frame by the drift s (cur(x) ~ prev(x - s))
+            s = register(I2, I1, p.reg_level)
+            d = flow_reg(I1, I2, p.pyr_levels, p.poly_n_half, p.poly_sigma, p.iters, p.win_r, p.lam, s)
+            out["drift"] = s
+        else:
+            d = flow(I1, I2, p.pyr_levels, p.poly_n_half, p.poly_sigma, p.iters, p.win_r, p.lam)
         S = saliency(d, p.sal_weight)
         Sh = normalise(S)
         mask0, t = threshold(Sh, p.roi_q)
