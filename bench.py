@@ -53,6 +53,10 @@ WORKLOADS = {
     # (8-connected components under 500 pixels removed)
     "components_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                                dwt_levels=5, wavelet=97, precision=32, seed_base=3000, min_area=500),
+    # same workload with each frame registered to its predecessor by phase
+    # correlation of pyramid level 2 (512x512 FFTs)
+    "register_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                             dwt_levels=5, wavelet=97, precision=32, seed_base=3000, register_frames=1, reg_level=2),
     # four streams of the batched workload's frames (small case for profiler captures)
     "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
@@ -227,7 +231,8 @@ def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampl
     import torch
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
                precision=wl["precision"], max_batch_frames=64, result_ring=8, denoise=wl.get("denoise", 0),
-               min_area=wl.get("min_area", 0), flags=F.MANUAL | (F.PLAIN if plain else 0), device=torch.cuda.current_device())
+               min_area=wl.get("min_area", 0), register_frames=wl.get("register_frames", 0),
+               reg_level=wl.get("reg_level", 2), flags=F.MANUAL | (F.PLAIN if plain else 0), device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     res = {}
     with F.Context(**cfg) as ctx:
@@ -291,7 +296,8 @@ def run_e2e(F, wl, frames, steps, warmup):
     coefs = [torch.empty((h, w), dtype=torch.int32).pin_memory() for _ in range(S)]
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
                precision=wl["precision"], max_batch_frames=64, result_ring=8, denoise=wl.get("denoise", 0),
-               min_area=wl.get("min_area", 0), flags=F.MANUAL,
+               min_area=wl.get("min_area", 0), register_frames=wl.get("register_frames", 0),
+               reg_level=wl.get("reg_level", 2), flags=F.MANUAL,
                device=torch.cuda.current_device())
     res = {}
     with F.Context(**cfg) as ctx:
@@ -479,7 +485,7 @@ def config_of(name, wl):
             "frames_per_stream": wl["frames"], "blobs": wl["blobs"], "batch_frames": wl["streams"],
             "pyr_levels": wl["pyr_levels"], "dwt": f"{wl['wavelet'] // 10}/{wl['wavelet'] % 10} x{wl['dwt_levels']}",
             "storage": "fp16" if wl["precision"] == 16 else "fp32", "denoise": bool(wl.get("denoise", 0)),
-            "min_area": wl.get("min_area", 0),
+            "min_area": wl.get("min_area", 0), "register": bool(wl.get("register_frames", 0)),
             "l2": "inputs larger than L2 (each step touches ~2.5 GB of frames and fields)"}
 
 

@@ -93,6 +93,7 @@ extern "C" {
 #define FLOWROI_I_COEFF_F32 4   /* float[W*H]: 9/7 coefficients before quantisation, Mallat */
 #define FLOWROI_I_THRESHOLD 5   /* float[1]: the cut t on S^ (mask0 = S^ > t) */
 #define FLOWROI_I_DENOISED 6    /* float[W*H]: denoised flow input in 8-bit units (config.denoise = 1) */
+#define FLOWROI_I_DRIFT 7       /* float[2]: registration drift (sx, sy), level-0 pixels (config.register_frames = 1) */
 
 /* ---- configuration ----------------------------------------------------- */
 /* Method parameters.  Table 1 of the paper names the user parameters (RoI
@@ -143,6 +144,12 @@ typedef struct flowroi_config {
      * frames of a stream with the frames there are.  Needs
      * result_ring >= 2k + 2. */
     int32_t adjacent;          /* k in [0, 4] (0) */
+    /* §Optical flow extraction: each frame registered to its predecessor
+     * by phase correlation (global translational drift); the flow is that
+     * of the registered pair.  The correlation runs on pyramid level
+     * reg_level, whose padded size must be at most 1024 per side. */
+    int32_t register_frames;   /* 0 = off, 1 = on (0) */
+    int32_t reg_level;         /* in [1, pyr_levels - 1] (2) */
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and

@@ -31,7 +31,11 @@ constexpr int kDwtTW = 64, kDwtTH = 16;   // DWT: band coefficients per block (p
 //   [kRedHist .. +kHistBins) histogram of the current radix digit.
 constexpr int kRedMin = 0, kRedMax = 1, kRedPrefix = 2, kRedRank = 3, kRedTS = 4, kRedTHat = 5, kRedSStar = 6;
 constexpr int kRedHist = 8;
-constexpr int kRedWords = kRedHist + kHistBins;
+//   [kRedReg ..) registration: the level image's sum (double), max |X|
+//   (float bits), the correlation peak key (u64) and the drift (2 floats).
+constexpr int kRedReg = kRedHist + kHistBins;
+constexpr int kRedRegSum = kRedReg, kRedRegXMax = kRedReg + 2, kRedRegPeak = kRedReg + 4, kRedRegDrift = kRedReg + 6;
+constexpr int kRedWords = kRedReg + 8;
 
 // Method constants of a context (passed by value to every kernel).
 struct MethodConsts {
@@ -58,6 +62,7 @@ struct MethodConsts {
     // den_ls = -log2 of the spatial weight over the (2 kDenMaxR + 1)^2
     // square (row-major, centred), den_lr = log2(e) / (2 sigma_r^2)
     int min_area;  // components of the final mask below this many pixels removed (<= 1: off)
+    int reg_on, reg_level;  // registration to the predecessor by phase correlation of pyramid level reg_level
     int denoise, den_r;
     float den_ls[(2 * kDenMaxR + 1) * (2 * kDenMaxR + 1)];
     float den_lr;
@@ -92,6 +97,7 @@ struct FrameDesc {
     float *dbg_yf;                  // keep + 9/7: float coefficients, W*H
     float *dbg_thr;                 // keep: threshold on S^ (1 float)
     float *dbg_den;                 // keep + denoise: denoised flow input, W*H
+    float *dbg_drift;               // keep + registration: the drift (2 floats)
     int *cc_lab, *cc_cnt, *cc_area; // min_area > 1: component labels, local-root counts, areas (W*H each)
     // JPEG2000 front end of this entry: the frame it codes (the flow frame
     // itself, or with an adjacent factor k > 0 the frame k earlier), its
@@ -101,6 +107,11 @@ struct FrameDesc {
     int32_t *dwt_coeffs;
     float *dwt_yf;                  // keep + 9/7: float coefficients of that frame
     int do_flow, do_dwt;
+    // registration (do_reg): padded FFT size 2^reg_lnx x 2^reg_lny of the
+    // level image, this frame's spectrum (kept for the next frame), the
+    // predecessor's, and the correlation work plane
+    int do_reg, reg_lnx, reg_lny;
+    float2 *reg_cur, *reg_prev, *reg_work;
     int n_adj;                      // per-frame masks ORed into dwt_mask (0: none, dwt_mask is the frame's own)
     const uint8_t *adj[2 * kMaxAdj + 1];
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
@@ -121,6 +132,9 @@ struct BatchDesc {
     int mor_off[kMaxBatch + 1];     // every flow frame
     int frm_off[kMaxBatch + 1];     // one unit per frame (init / select-find)
     int mrg_off[kMaxBatch + 1];     // adjacent-mask merge: 4096-byte units of entries with n_adj > 0
+    int reg_row_off[kMaxBatch + 1]; // registration: padded rows, 8-column groups, 4096-element units
+    int reg_col_off[kMaxBatch + 1];
+    int reg_el_off[kMaxBatch + 1];
     FrameDesc f[kMaxBatch];
 };
 

@@ -96,6 +96,13 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
         const T *b2p = static_cast<const T *>(F.fb_prev[level]);
         const float2 *fsrc = F.flow[src];
         T *gh = static_cast<T *>(F.gh[level]);
+        // registration: the predecessor translated by the drift s is read at x + d~ - s / 2^level
+        float ox = 0.f, oy = 0.f;
+        if (mc.reg_on) {
+            const float sc = -ldexpf(1.f, -level);
+            ox = __uint_as_float(__ldg(F.red + kRedRegDrift)) * sc;
+            oy = __uint_as_float(__ldg(F.red + kRedRegDrift + 1)) * sc;
+        }
         const size_t plane = (size_t)p * h;
         float ddx[kUpdRows], ddy[kUpdRows];
 #pragma unroll
@@ -124,11 +131,12 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
             const int gy = y0 + j;
             if (gy >= h) continue;
             const float dx = ddx[j], dy = ddy[j];
-            // Position x + d~ as integer + fraction (full-precision
-            // fraction), clamped to the image.
-            const float flx = floorf(dx), fly = floorf(dy);
+            // Position x + d~ (+ the registration offset) as integer +
+            // fraction (full-precision fraction), clamped to the image.
+            const float px = dx + ox, py = dy + oy;
+            const float flx = floorf(px), fly = floorf(py);
             int ix = gx + (int)flx, iy = gy + (int)fly;
-            float fx = dx - flx, fy = dy - fly;
+            float fx = px - flx, fy = py - fly;
             if (ix < 0) { ix = 0; fx = 0.f; } else if (ix >= w - 1) { ix = w - 1; fx = 0.f; }
             if (iy < 0) { iy = 0; fy = 0.f; } else if (iy >= h - 1) { iy = h - 1; fy = 0.f; }
             const int ix1 = min(ix + 1, w - 1), iy1 = min(iy + 1, h - 1);

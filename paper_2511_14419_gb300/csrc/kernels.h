@@ -19,6 +19,13 @@ void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s)
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
 void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
+// Registration to the predecessor: steps 0-7 (level-image sum, row and
+// column FFTs, cross-power spectrum, inverse FFTs, peak, drift).
+void launch_register(const BatchDesc *bd, const MethodConsts &mc, bool half, int step, int grid, cudaStream_t s);
+int occupancy_register();
+int register_max_log();  // padded FFT sizes up to 2^this
+int register_cols();     // columns per block of the column FFTs
+int register_unit();     // elements per block-unit of the element-wise steps
 // Adjacent-factor merge of per-frame masks (entries with n_adj > 0).
 void launch_merge(const BatchDesc *bd, int grid, cudaStream_t s);
 // Removal of small connected components of the final mask: steps 0-3

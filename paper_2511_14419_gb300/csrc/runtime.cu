@@ -91,6 +91,7 @@ struct Entry {
     float *dbg_yf = nullptr;
     float *dbg_thr = nullptr;
     float *dbg_den = nullptr;
+    float *dbg_drift = nullptr;
 };
 
 struct Stream {
@@ -114,6 +115,8 @@ struct Stream {
     void *gh[kMaxLevels] = {};
     float2 *flow[2] = {};
     int *cc[3] = {};  // component labels, local-root counts, areas (min_area > 1)
+    int reg_lnx = 0, reg_lny = 0;                  // registration: log2 of the padded FFT size
+    float2 *reg_spec[2] = {}, *reg_work = nullptr; // spectra (by frame parity) and the correlation plane
     float *S = nullptr;
     unsigned *red = nullptr;
     void *ll[2] = {};
@@ -147,7 +150,7 @@ struct flowroi_ctx {
     cudaGraphExec_t graph[kDesc] = {};
     int graph_launches = 0;
     int desc_next = 0;
-    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0, grid_mrg = 0;
+    int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0, grid_mrg = 0, grid_reg = 0;
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -217,6 +220,9 @@ int validate_config(const flowroi_config *c)
     if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL)) return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
     if (c->min_area < 0 || c->min_area > (1 << 20)) return fail(FLOWROI_EINVAL, "config.min_area must be in [0, 2^20]");
     if (c->adjacent < 0 || c->adjacent > kMaxAdj) return fail(FLOWROI_EINVAL, "config.adjacent must be in [0,4]");
+    if (c->register_frames != 0 && c->register_frames != 1) return fail(FLOWROI_EINVAL, "config.register_frames must be 0 or 1");
+    if (c->register_frames && (c->reg_level < 1 || c->reg_level >= c->pyr_levels))
+        return fail(FLOWROI_EINVAL, "config.reg_level must be in [1, pyr_levels - 1]");
     if (c->result_ring < 2 * c->adjacent + 2)
         return fail(FLOWROI_EINVAL, "config.result_ring must be at least 2*adjacent + 2");
     if (c->denoise != 0 && c->denoise != 1) return fail(FLOWROI_EINVAL, "config.denoise must be 0 or 1");
@@ -321,6 +327,15 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
     s->red = reinterpret_cast<unsigned *>(take(kRedWords * sizeof(unsigned)));
     if (c->cfg.min_area > 1)
         for (int k = 0; k < 3; k++) s->cc[k] = reinterpret_cast<int *>(take(npx * sizeof(int)));
+    if (c->cfg.register_frames) {
+        const int rl = c->cfg.reg_level;
+        auto lg = [](int n) { int k = 0; while ((1 << k) < n) k++; return k; };
+        s->reg_lnx = lg(s->lw[rl]);
+        s->reg_lny = lg(s->lh[rl]);
+        const size_t nsp = (size_t)1 << (s->reg_lnx + s->reg_lny);
+        for (int k = 0; k < 2; k++) s->reg_spec[k] = reinterpret_cast<float2 *>(take(nsp * sizeof(float2)));
+        s->reg_work = reinterpret_cast<float2 *>(take(nsp * sizeof(float2)));
+    }
     for (int k = 0; k < 2; k++) {
         s->ll[k] = take((npx / 4) * 4);
         s->llm[k] = reinterpret_cast<uint8_t *>(take(npx / 4));
@@ -338,6 +353,7 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
             e->dbg_yf = c->cfg.wavelet == FLOWROI_W97 ? reinterpret_cast<float *>(take(npx * 4)) : nullptr;
             e->dbg_thr = reinterpret_cast<float *>(take(sizeof(float)));
             e->dbg_den = c->cfg.denoise ? reinterpret_cast<float *>(take(npx * 4)) : nullptr;
+            e->dbg_drift = c->cfg.register_frames ? reinterpret_cast<float *>(take(2 * sizeof(float))) : nullptr;
         }
     }
     return align_up(off, 256);
@@ -399,6 +415,14 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
     F.ll[1] = s->ll[1];
     F.llm[0] = s->llm[0];
     F.llm[1] = s->llm[1];
+    if (e && c->cfg.register_frames) {
+        F.do_reg = 1;
+        F.reg_lnx = s->reg_lnx;
+        F.reg_lny = s->reg_lny;
+        F.reg_cur = s->reg_spec[cur];
+        F.reg_prev = s->reg_spec[prv];
+        F.reg_work = s->reg_work;
+    }
     if (e) {
         F.raw = e->raw;
         F.mask = c->cfg.adjacent > 0 ? e->mask_own : e->mask;
@@ -408,6 +432,7 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
         F.dbg_mask0 = e->dbg_mask0;
         F.dbg_thr = e->dbg_thr;
         F.dbg_den = e->dbg_den;
+        F.dbg_drift = e->dbg_drift;
     }
     if (d) {
         F.do_dwt = 1;
@@ -437,6 +462,7 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
         bd.exp_off[l][0] = bd.flow_off[l][0] = bd.win_off[l][0] = bd.dwt_off[l][0] = 0;
     }
     bd.sal_off[0] = bd.mor_off[0] = bd.frm_off[0] = bd.mrg_off[0] = 0;
+    bd.reg_row_off[0] = bd.reg_col_off[0] = bd.reg_el_off[0] = 0;
     for (int i = 0; i < n; i++) {
         const FrameDesc &F = bd.f[i];
         for (int l = 0; l < L; l++) {
@@ -449,13 +475,17 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
         bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
         bd.mor_off[i + 1] = bd.mor_off[i] + (F.do_flow ? tiles(F.W, F.H, kMorTW, kMorTH) : 0);
         bd.mrg_off[i + 1] = bd.mrg_off[i] + (F.n_adj > 0 ? (int)(((size_t)F.W * F.H + 4095) / 4096) : 0);
+        const int rnx = F.do_reg ? 1 << F.reg_lnx : 0, rny = F.do_reg ? 1 << F.reg_lny : 0;
+        bd.reg_row_off[i + 1] = bd.reg_row_off[i] + rny;
+        bd.reg_col_off[i + 1] = bd.reg_col_off[i] + (rnx + register_cols() - 1) / register_cols();
+        bd.reg_el_off[i + 1] = bd.reg_el_off[i] + (rnx * rny + register_unit() - 1) / register_unit();
         bd.frm_off[i + 1] = i + 1;
     }
 }
 
 const char *const kKernelNames[] = {"frame_init", "expand", "update", "window", "saliency", "select_find", "select_pass",
-                                    "morph", "dwt", "denoise", "components", "merge"};
-enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC, K_MERGE };
+                                    "morph", "dwt", "denoise", "components", "merge", "register"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC, K_MERGE, K_REG };
 
 // Runs one launch, bracketed by an event pair when profiling.
 template <class Fn>
@@ -497,6 +527,16 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     for (int l = 0; l < L; l++) {
         timed(c, st, prof, K_EXPAND, l, -1, [&] { launch_expand(dd, mc, l, c->half, g(hd->exp_off[l][n], c->grid_exp), st); });
         cnt++;
+    }
+    if (mc.reg_on) {
+        // registration to the predecessor (its spectrum is kept for the next frame)
+        const int units[8] = {hd->reg_el_off[n], hd->reg_row_off[n], hd->reg_col_off[n], hd->reg_el_off[n],
+                              hd->reg_row_off[n], hd->reg_col_off[n], hd->reg_el_off[n], 1};
+        for (int step = 0; step < 8; step++) {
+            timed(c, st, prof, K_REG, step, -1,
+                  [&] { launch_register(dd, mc, c->half, step, step == 7 ? 1 : g(units[step], c->grid_reg), st); });
+            cnt++;
+        }
     }
     if (any_prev) {
         int k = 0;
@@ -756,6 +796,8 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
         if (which == FLOWROI_I_COEFF_F32 && c->cfg.wavelet != FLOWROI_W97)
             return fail(FLOWROI_EINVAL, "float coefficients exist only for the 9/7 path");
         if (which == FLOWROI_I_DENOISED && !c->cfg.denoise) return fail(FLOWROI_EINVAL, "denoising is off (config.denoise)");
+        if (which == FLOWROI_I_DRIFT && !c->cfg.register_frames)
+            return fail(FLOWROI_EINVAL, "registration is off (config.register_frames)");
         e->readers++;
     }
     const bool ok = wait_done(c, e, timeout_ms);
@@ -776,6 +818,7 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
         case FLOWROI_I_COEFF_F32: src = e->dbg_yf; bytes = npx * 4; break;
         case FLOWROI_I_THRESHOLD: src = e->dbg_thr; bytes = 4; break;
         case FLOWROI_I_DENOISED: src = e->dbg_den; bytes = npx * 4; break;
+        case FLOWROI_I_DRIFT: src = e->dbg_drift; bytes = 2 * sizeof(float); break;
         default: rc = fail(FLOWROI_EINVAL, "unknown intermediate %d", which); break;
         }
         if (rc == FLOWROI_OK && which >= FLOWROI_I_FLOW && !e->has_prev) {
@@ -787,7 +830,7 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
                 if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s_d2h);
                 if (ce != cudaSuccess) rc = cuda_fail(c, ce, "copy out");
                 src = nullptr;
-            } else if (which == FLOWROI_I_FLOW || which == FLOWROI_I_SALIENCY) {
+            } else if (which == FLOWROI_I_FLOW || which == FLOWROI_I_SALIENCY || which == FLOWROI_I_DRIFT) {
                 cudaError_t ce = out_on_device ? cudaMemsetAsync(out, 0, bytes, c->s_d2h) : cudaSuccess;
                 if (!out_on_device) std::memset(out, 0, bytes);
                 if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s_d2h);
@@ -887,6 +930,8 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->den_sigma_r = 20.0f;
     cfg->min_area = 0;
     cfg->adjacent = 0;
+    cfg->register_frames = 0;
+    cfg->reg_level = 2;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -929,6 +974,8 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     mc.dwt_levels = cfg->dwt_levels;
     mc.shift = cfg->scale_shift;
     mc.min_area = cfg->min_area;
+    mc.reg_on = cfg->register_frames;
+    mc.reg_level = cfg->reg_level;
     mc.denoise = cfg->denoise;
     mc.den_r = cfg->den_radius;
     const double log2e = 1.4426950408889634;
@@ -972,6 +1019,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     c->grid_den = cfg->denoise ? std::max(1, occupancy_denoise(c->half, cfg->den_radius)) * c->num_sms : 0;
     c->grid_cc = cfg->min_area > 1 ? std::max(1, occupancy_cc()) * c->num_sms : 0;
     c->grid_mrg = 8 * c->num_sms;
+    c->grid_reg = cfg->register_frames ? std::max(1, occupancy_register()) * c->num_sms : 0;
     c->grid_frames = kMaxBatch;
     size_t freeb = 0, totalb = 0;
     CK(nullptr, cudaMemGetInfo(&freeb, &totalb));
@@ -1014,6 +1062,9 @@ static int submit_enqueue(flowroi_ctx *c, int64_t stream_id, const flowroi_frame
             ns->bit_depth = f->bit_depth;
             for (int r = 0; r < c->cfg.result_ring; r++) ns->ring.emplace_back(new Entry);
             const size_t bytes = plan_stream(c, ns.get(), nullptr);
+            if (c->cfg.register_frames && (ns->reg_lnx > register_max_log() || ns->reg_lny > register_max_log()))
+                return fail(FLOWROI_EINVAL, "frame %dx%d: pyramid level %d exceeds %d pixels per side for registration",
+                            f->width, f->height, c->cfg.reg_level, 1 << register_max_log());
             if (c->admitted + bytes > c->budget) {
                 c->refused++;
                 return fail(FLOWROI_EBUSY, "stream %lld needs %zu bytes; %llu of %llu budget in use", (long long)stream_id, bytes,
@@ -1139,7 +1190,7 @@ int flowroi_get_coeffs(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int
 int flowroi_get_intermediate(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, void *out, int out_on_device,
                              int timeout_ms)
 {
-    if (which < FLOWROI_I_FLOW || which > FLOWROI_I_DENOISED) return fail(FLOWROI_EINVAL, "unknown intermediate %d", which);
+    if (which < FLOWROI_I_FLOW || which > FLOWROI_I_DRIFT) return fail(FLOWROI_EINVAL, "unknown intermediate %d", which);
     if (c) cudaSetDevice(c->device);
     return get_common(c, stream_id, frame_idx, which, out, out_on_device, timeout_ms);
 }

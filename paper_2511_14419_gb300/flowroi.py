@@ -19,7 +19,7 @@ U8, U16 = 1, 2
 W53, W97 = 53, 97
 FP32, FP16 = 32, 16
 KEEP_INTERMEDIATES, PLAIN, MANUAL = 0x1, 0x2, 0x4
-I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD, I_DENOISED = 1, 2, 3, 4, 5, 6
+I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD, I_DENOISED, I_DRIFT = 1, 2, 3, 4, 5, 6, 7
 
 EXPORTS = [
     "flowroi_abi_version", "flowroi_default_config", "flowroi_create", "flowroi_submit_frame", "flowroi_submit_frames",
@@ -47,6 +47,7 @@ class flowroi_config(ctypes.Structure):
         ("flags", ctypes.c_uint32), ("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
         ("denoise", ctypes.c_int32), ("den_radius", ctypes.c_int32), ("den_sigma_s", ctypes.c_float),
         ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32), ("adjacent", ctypes.c_int32),
+        ("register_frames", ctypes.c_int32), ("reg_level", ctypes.c_int32),
     ]
 
 
