@@ -29,6 +29,7 @@
 #include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -39,6 +40,8 @@
 #include <vector>
 
 #include <cudaTypedefs.h>
+#include <nvtx3/nvToolsExt.h>
+#include <nvtx3/nvToolsExtCudaRt.h>
 
 #include "../../include/flowroi.h"
 #include "common.cuh"
@@ -52,6 +55,29 @@ namespace {
 thread_local std::string g_err;
 
 int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+// stderr logging, on when the environment variable FLOWROI_LOG is set (to
+// anything but "0"): refusals and errors, admissions, context life.
+bool log_on()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("FLOWROI_LOG");
+        return v && *v && std::strcmp(v, "0") != 0;
+    }();
+    return on;
+}
+
+void logf(const char *fmt, ...) __attribute__((format(printf, 1, 2)));
+void logf(const char *fmt, ...)
+{
+    if (!log_on()) return;
+    va_list ap;
+    va_start(ap, fmt);
+    std::fputs("[flowroi] ", stderr);
+    std::vfprintf(stderr, fmt, ap);
+    std::fputc('\n', stderr);
+    va_end(ap);
+}
+
 int fail(int code, const char *fmt, ...)
 {
     char buf[512];
@@ -60,8 +86,15 @@ int fail(int code, const char *fmt, ...)
     vsnprintf(buf, sizeof buf, fmt, ap);
     va_end(ap);
     g_err = buf;
+    logf("status %d: %s", code, buf);
     return code;
 }
+
+// NVTX range for the duration of a scope (no cost without a profiler attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 double now_ms()
 {
@@ -186,6 +219,7 @@ int cuda_fail(flowroi_ctx *c, cudaError_t e, const char *what)
         c->poison_msg = buf;
     }
     g_err = buf;
+    logf("device error, context poisoned: %s", buf);
     return FLOWROI_EDEVICE;
 }
 
@@ -590,6 +624,7 @@ void CUDART_CB on_batch_done(void *p)
         c->poison_msg = code == 1u ? "a kernel's bounded wait for a TMA copy ran out"
                                    : "a kernel's bounded union-find loop ran out";
         c->poisoned = true;
+        logf("context poisoned: %s", c->poison_msg.c_str());
     }
     {
         std::lock_guard<std::mutex> lk(c->cmu);
@@ -608,6 +643,7 @@ void CUDART_CB on_batch_done(void *p)
 // Launch one batch (mu held).  Returns frames launched or a negative status.
 int step_locked(flowroi_ctx *c)
 {
+    NvtxRange range("flowroi.step");
     if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
     const int maxb = c->plain ? 1 : c->cfg.max_batch_frames;
     struct Pick {
@@ -992,6 +1028,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     CK(nullptr, cudaSetDevice(c->device));
     CK(nullptr, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
     CK(nullptr, cudaStreamCreateWithFlags(&c->s_comp, cudaStreamNonBlocking));
+    nvtxNameCudaStreamA(c->s_comp, "flowroi.compute");
     CK(nullptr, cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking));
     CK(nullptr, cudaStreamCreateWithFlags(&c->s_d2h, cudaStreamNonBlocking));
     CK(nullptr, cudaStreamCreateWithFlags(&c->s_cap, cudaStreamNonBlocking));
@@ -1034,6 +1071,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
 // ring (mu taken inside); *ev receives the copy's completion event.
 static int submit_enqueue(flowroi_ctx *c, int64_t stream_id, const flowroi_frame *f, cudaEvent_t *ev)
 {
+    NvtxRange range("flowroi.submit");
     if (!f || f->struct_size != sizeof(flowroi_frame)) return fail(FLOWROI_EINVAL, "frame descriptor NULL or struct_size mismatch");
     if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
     if (f->dtype != FLOWROI_U8 && f->dtype != FLOWROI_U16) return fail(FLOWROI_EINVAL, "frame.dtype must be U8 or U16");
@@ -1087,6 +1125,8 @@ static int submit_enqueue(flowroi_ctx *c, int64_t stream_id, const flowroi_frame
             }
             for (auto &en : ns->ring) CK(c, cudaEventCreateWithFlags(&en->uploaded, cudaEventDisableTiming));
             c->admitted += bytes;
+            logf("stream %lld admitted: %dx%d, %zu bytes (%llu of %llu in use)", (long long)stream_id, f->width,
+                 f->height, bytes, (unsigned long long)c->admitted, (unsigned long long)c->budget);
             s = ns.get();
             c->streams[stream_id] = std::move(ns);
         } else {

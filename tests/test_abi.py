@@ -81,3 +81,18 @@ def test_null_context_is_rejected(F):
     L.flowroi_destroy(None)
     assert isinstance(L.flowroi_last_error(None), bytes)
     del ctypes
+
+
+def test_log_env_reports_refusals_on_stderr():
+    """FLOWROI_LOG=1 logs every refusal (here a config error, which needs no
+    GPU) to stderr; without it the library is silent."""
+    import subprocess
+    import sys
+    code = ("from paper_2511_14419_gb300 import flowroi as F\n"
+            "try:\n    F.Context(roi_q=2.0)\nexcept F.FlowRoIError:\n    pass\n")
+    env = dict(os.environ, FLOWROI_LOG="1")
+    on = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert "[flowroi] status -1: config.roi_q" in on.stderr, on.stderr
+    env.pop("FLOWROI_LOG")
+    off = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT, timeout=120)
+    assert "[flowroi]" not in off.stderr
