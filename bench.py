@@ -85,7 +85,7 @@ KERNEL_BYTES = {("update", 32): (62.0, 68.0), ("update", 16): (32.0, 38.0),
 # on the current kernels (profiles/k_update_level0_4x2048.md,
 # profiles/k_window_level0_4x2048.md: 4 frames, traffic proportional to
 # pixels); absent = not measured for the current build.
-KERNEL_TRAFFIC_PER_PX = {("update", 32): 66.5, ("window", 32): 26.5}
+KERNEL_TRAFFIC_PER_PX = {("update", 32): 66.5, ("window", 32): 27.0}
 
 
 def log(*a):

@@ -167,59 +167,86 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
 
 // ---------------------------------------------------------------- window
 // Box means of G and h over (2r+1)^2 (clipped to the image) and the 2x2
-// solve, over kWinTW x kWinTH tiles.  Warp-specialised, plane by plane: a
-// producer warp streams each tile's five G, h planes (each with the r-pixel
-// apron, one TMA copy per plane) through a ring of NS shared-memory slots
-// guarded by full / empty mbarriers.  NS is more than a tile's five planes,
-// so the next tile's planes are in flight while the current tile is
-// summed.  Elements outside the image arrive as zeros, which is exactly the
-// clipped sum.  Per plane, eight consumer warps sum every column over 2r+1
-// rows (kWinChunks row chunks per column, so that 3(64 + 2r) items keep the
-// warps busy) into one of two sums buffers and release the slot; after a
-// barrier each consumer thread sums 8 adjacent outputs of a row over 2r+1
-// columns into registers.  After the fifth plane it solves.  The sums rows
-// are an odd number of 16-byte words apart and the 8 threads of a
-// quarter-warp take 8 different rows, so the float4 row reads are
-// conflict-free.  Sums buffer (plane i mod 2) is rewritten two planes
-// later, after the barrier that follows every warp's reads of it.
+// solve, over kWinTW x kWinTH tiles.  Warp-specialised: a producer warp
+// streams each tile's five G, h planes (each with the r-pixel apron, one
+// TMA copy per plane) through a ring of NS >= 5 shared-memory slots
+// guarded by full / empty mbarriers, so the next tile's planes are in
+// flight while the current tile is summed.  Elements outside the image
+// arrive as zeros, which is exactly the clipped sum.
 //
-// Ordering: every consumer warp takes the planes in load order and waits
-// for each, so when it waits for a slot's n-th fill it has seen the
-// (n-1)-th complete (the parity waits cannot alias); the producer refills a
-// slot only after all eight warps arrived on its empty barrier.  Every wait
-// is bounded: a consumer whose wait runs out skips the work, the consumers
-// agree at the next barrier and leave with the batch error word set, and
-// the producer waits (bounded) for the copies it issued before it leaves.
+// Per tile, each plane's 64 + 2r extended columns are cut into three
+// warp-sized pieces (the last one partial), and the 15 pieces are dealt to
+// the eight consumer warps, two rounds; each lane sums its whole column
+// over 2r+1 rows in one pass (every slot value is read once).  A warp's
+// piece lies in one plane, so its lanes take 32 different banks.  With fp32 planes the column sums overwrite the column
+// they came from (each column has one owner, and it has read the column
+// before it writes it), so the slot itself holds the plane's sums; with
+// fp16 planes each slot has a separate fp32 sums area.  After one barrier
+// every consumer thread sums 8 adjacent outputs of a row over 2r+1
+// columns into registers, plane by plane, each warp releasing a plane's
+// slot when its reads of it are done; then it solves.  Sums rows are an
+// odd number of 16-byte words apart and the 8 threads of a quarter-warp
+// take 8 different rows, so the float4 row reads are conflict-free.
+//
+// Ordering: a consumer waits for a slot's fill only for the tile that
+// uses it, after the barrier of the previous tile, by which every earlier
+// fill of every slot has completed; the producer refills a slot only after
+// all eight warps released it.  So the parity waits cannot alias.  Every
+// wait is bounded: a consumer whose wait runs out skips the work, the
+// consumers agree at the barrier and leave with the batch error word set,
+// and the producer waits (bounded) for the copies it issued before it
+// leaves.
 constexpr int kWinConsumers = 256;
 constexpr int kWinThreads = kWinConsumers + 32;
-constexpr int kWinChunks = 3;
-constexpr size_t kWinSmemBlock = 112 * 1024;  // two blocks per SM
+constexpr size_t kWinSmemPair = 112 * 1024;  // two blocks per SM
+constexpr int kWinMaxSlots = 10;
+constexpr int kWinHdrs = 4;                   // tile headers in flight
+
+// A tile's geometry, written by the producer with the tile's first plane
+// copy (published to the consumers by that copy's mbarrier and the
+// consumers' barrier), so that consumer warps take no dependent global
+// loads per tile.  Header j mod kWinHdrs is rewritten for tile j + 4 only
+// after the slot of a plane of tile j + 2 was released, i.e. after every
+// consumer has finished tile j.
+struct WinTile {
+    int x0, y0, w, h, p, pad;
+    float2 *flow;
+};
+constexpr size_t kWinHdrOff = 2 * kWinMaxSlots * sizeof(uint64_t);
+constexpr size_t kWinSlotsOff = (kWinHdrOff + kWinHdrs * sizeof(WinTile) + 127) / 128 * 128;
 
 template <typename T, int R>
 struct WinGeom {
+    static constexpr bool inplace = sizeof(T) == 4;                    // sums overwrite the fp32 plane
     static constexpr int EPC = 16 / sizeof(T);                         // elements per 16 bytes
     static constexpr int XO = (R + EPC - 1) / EPC * EPC;               // box starts XO left of the tile
-    static constexpr int BW = (kWinTW + XO + R + EPC - 1) / EPC * EPC; // box width (elements)
     static constexpr int EH = kWinTH + 2 * R;
     static constexpr int EW = kWinTW + 2 * R;
-    static constexpr int CH = (kWinTH + kWinChunks - 1) / kWinChunks;  // outputs per column chunk
     static constexpr int SEG = 8;                                      // outputs per thread in a row
-    static constexpr int SV = (SEG + 2 * R + 3) / 4;                   // float4 words a thread reads per row
-    static constexpr int SW0 = EW > kWinTW - SEG + 4 * SV ? (EW + 3) / 4 * 4 : kWinTW - SEG + 4 * SV;
-    static constexpr int SW = (SW0 / 4) % 2 ? SW0 : SW0 + 4;           // sums row stride (floats)
+    static constexpr int SO = inplace ? XO - R : 0;                    // sums column of extended column 0
+    static constexpr int SV = (SO + SEG + 2 * R + 3) / 4;              // float4 words a thread reads per row
+    static constexpr int SNEED = kWinTW - SEG + 4 * SV;                // sums row span of the row reads
+    // Box width: the tile and its apron in whole 16-byte words; in place it
+    // also spans the row reads and is an odd number of 16-byte words.
+    static constexpr int BW0 = (kWinTW + XO + R + EPC - 1) / EPC * EPC;
+    static constexpr int BW1 = inplace && SNEED > BW0 ? SNEED : BW0;
+    static constexpr int BW = inplace && (BW1 / 4) % 2 == 0 ? BW1 + 4 : BW1;
+    static constexpr int SW0 = EW > SNEED ? (EW + 3) / 4 * 4 : SNEED;
+    static constexpr int SW = inplace ? BW : ((SW0 / 4) % 2 ? SW0 : SW0 + 4);  // sums row stride (floats)
     static constexpr size_t plane_bytes = (size_t)EH * BW * sizeof(T); // one TMA copy
-    static constexpr size_t slot_stride = (plane_bytes + 127) / 128 * 128;
-    static constexpr size_t sums_bytes = (size_t)kWinTH * SW * sizeof(float);
-    static constexpr size_t fixed = 128 + 2 * sums_bytes;
-    static constexpr int NS0 = (int)((kWinSmemBlock - fixed) / slot_stride);
-    static constexpr int NS = NS0 > 8 ? 8 : NS0;                       // ring slots
-    static constexpr size_t slots_off = 128;
-    static constexpr size_t sums_off = slots_off + NS * slot_stride;
-    static constexpr size_t smem = sums_off + 2 * sums_bytes;
+    static constexpr size_t data_bytes = (plane_bytes + 127) / 128 * 128;
+    static constexpr size_t sums_bytes = inplace ? 0 : ((size_t)kWinTH * SW * sizeof(float) + 127) / 128 * 128;
+    static constexpr size_t slot_stride = data_bytes + sums_bytes;
+    static constexpr int NS0 = (int)((kWinSmemPair - kWinSlotsOff) / slot_stride);
+    static constexpr int NS = NS0 > kWinMaxSlots ? kWinMaxSlots : NS0; // ring slots
+    static constexpr size_t slots_off = kWinSlotsOff;
+    static constexpr size_t smem = slots_off + NS * slot_stride;
     static_assert(NS >= 5, "a whole tile's planes in flight");
-    static_assert(kWinChunks * EW <= kWinConsumers, "one column chunk per consumer thread");
+    static_assert(5 * ((EW + 31) / 32) <= 2 * (kWinConsumers / 32), "at most two column pieces per consumer warp");
     static_assert((kWinTW / SEG) * kWinTH == kWinConsumers, "one row segment per consumer thread");
     static_assert(kWinConsumers == 256, "row-segment thread map assumes 8 warps");
+    static_assert(!inplace || (SO + EW <= BW && SNEED <= BW && EH >= kWinTH), "in-place sums fit the plane");
+    static_assert(inplace || (EW <= SW && SNEED <= SW), "sums rows span the columns and the row reads");
 };
 
 template <typename T, int R>
@@ -227,13 +254,16 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
                                                           int dst)
 {
     using G = WinGeom<T, R>;
-    constexpr int TW = kWinTW, TH = kWinTH, EW = G::EW, BW = G::BW, WN = 2 * R + 1;
-    constexpr int SEG = G::SEG, SW = G::SW, SV = G::SV, CH = G::CH, NS = G::NS;
+    constexpr int TW = kWinTW, TH = kWinTH, EW = G::EW, EH = G::EH, BW = G::BW, WN = 2 * R + 1;
+    constexpr int SEG = G::SEG, SW = G::SW, SV = G::SV, SO = G::SO, NS = G::NS;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw);
     uint64_t *empty = full + NS;
+    WinTile *hdr = reinterpret_cast<WinTile *>(smem_raw + kWinHdrOff);
     unsigned char *slots = smem_raw + G::slots_off;
-    float *sums = reinterpret_cast<float *>(smem_raw + G::sums_off);  // [2][TH][SW]
+    auto sums_of = [&](int slot) {
+        return reinterpret_cast<float *>(slots + slot * G::slot_stride + (G::inplace ? 0 : G::data_bytes));
+    };
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < NS; b++) {
@@ -257,7 +287,8 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
                 const int t = blockIdx.x + j * gridDim.x;
                 const int fi = find_frame(off, nfr, t);
                 const FrameDesc &F = bd->f[fi];
-                const int ntx = (F.lw[level] + TW - 1) / TW;
+                const int w = F.lw[level];
+                const int ntx = (w + TW - 1) / TW;
                 const int lt = t - __ldg(off + fi);
                 const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
                 const CUtensorMap *map = &F.gh_map[level];
@@ -268,6 +299,15 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
                         atomicExch(bd->err, kErrTmaTimeout);
                         ok = false;
                         break;
+                    }
+                    if (k == 0) {
+                        WinTile &ht = hdr[j % kWinHdrs];
+                        ht.x0 = x0;
+                        ht.y0 = y0;
+                        ht.w = w;
+                        ht.h = F.lh[level];
+                        ht.p = F.lp[level];
+                        ht.flow = F.flow[dst];
                     }
                     fence_proxy_async_smem();
                     mbar_expect_tx(&full[slot], (uint32_t)G::plane_bytes);
@@ -282,70 +322,76 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
 
     // ---- consumers
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    // column-sum item: chunk cc of ext column ex
-    const int cc = tid / EW, ex = tid - cc * EW;
-    const bool has_item = cc < kWinChunks;
-    const int cs = min(cc * CH, TH - CH);  // first output row of the chunk (the last one may overlap)
-    const int cw = cc * CH;                // rows below this are another chunk's to write
+    // column pieces wp and wp + 8: plane ck[u], the lane's extended column cx[u]
+    constexpr int PARTS = (EW + 31) / 32, PIECES = 5 * PARTS;
+    int ck[2], cx[2];
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int m = wp + u * (kWinConsumers / 32);
+        ck[u] = m < PIECES ? m / PARTS : 5;
+        cx[u] = (m - ck[u] * PARTS) * 32 + lane;
+    }
     // row-segment owner: quarter-warps span 8 rows
     const int r = (wp & 3) * 8 + (lane & 7), sg = (wp >> 2) * 4 + (lane >> 3);
-    int i = 0;
-    for (int j = 0; j < mine; j++) {
-        const int t = blockIdx.x + j * gridDim.x;
-        const int fi = find_frame(off, nfr, t);
-        const FrameDesc &F = bd->f[fi];
-        const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
-        const int ntx = (w + TW - 1) / TW;
-        const int lt = t - __ldg(off + fi);
-        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
+    int i = 0;  // ring index of the tile's plane 0
+    for (int j = 0; j < mine; j++, i += 5) {
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            if (ck[u] >= 5) break;
+            const int ii = i + ck[u];
+            const int slot = ii % NS;
+            ok = ok && mbar_wait(&full[slot], (uint32_t)((ii / NS) & 1));
+            if (!ok) break;
+            if (cx[u] >= EW) continue;
+            const T *col = reinterpret_cast<const T *>(slots + slot * G::slot_stride) + cx[u] + (G::XO - R);
+            float v[EH], sm[TH];
+#pragma unroll
+            for (int q = 0; q < EH; q++) v[q] = (float)col[q * BW];
+            box_sums<EH, WN>(v, sm);
+            float *dcol = sums_of(slot) + cx[u] + SO;
+#pragma unroll
+            for (int q = 0; q < TH; q++) dcol[q * SW] = sm[q];
+        }
+        // Generic-proxy writes to a slot precede the TMA refill of it.
+        if (G::inplace) fence_proxy_async_smem();
+        if (named_sync_or(1, kWinConsumers, !ok)) {
+            if (tid == 0) atomicExch(bd->err, kErrTmaTimeout);
+            return;
+        }
 
+        // horizontal sums of each plane for the thread's 8 outputs
         float acc[5][SEG];
 #pragma unroll
-        for (int k = 0; k < 5; k++, i++) {
-            const int slot = i % NS;
-            float *sb = sums + (i & 1) * (TH * SW);
-            const bool ok = mbar_wait(&full[slot], (uint32_t)((i / NS) & 1));
-            if (ok && has_item) {
-                const T *col = reinterpret_cast<const T *>(slots + slot * G::slot_stride) + cs * BW + ex + (G::XO - R);
-                float v[CH + 2 * R], sm[CH];
+        for (int k = 0; k < 5; k++) {
+            const int slot = (i + k) % NS;
+            const float4 *row = reinterpret_cast<const float4 *>(sums_of(slot) + r * SW + sg * SEG);
+            float v[4 * SV], hs[SEG];
 #pragma unroll
-                for (int q = 0; q < CH + 2 * R; q++) v[q] = (float)col[q * BW];
-                box_sums<CH + 2 * R, WN>(v, sm);
-                float *dcol = sb + cs * SW + ex;
-#pragma unroll
-                for (int q = 0; q < CH; q++)
-                    if (cs + q >= cw) dcol[q * SW] = sm[q];
+            for (int q = 0; q < SV; q++) {
+                const float4 u4 = row[q];
+                v[4 * q] = u4.x;
+                v[4 * q + 1] = u4.y;
+                v[4 * q + 2] = u4.z;
+                v[4 * q + 3] = u4.w;
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[slot]);
-            if (named_sync_or(1, kWinConsumers, !ok)) {
-                if (tid == 0) atomicExch(bd->err, kErrTmaTimeout);
-                return;
-            }
-            // horizontal sums of this plane for the thread's 8 outputs
-            const float4 *row = reinterpret_cast<const float4 *>(sb + r * SW + sg * SEG);
-            float v[4 * SV], sm[SEG];
+            const float(&vv)[SEG + 2 * R] = *reinterpret_cast<const float(*)[SEG + 2 * R]>(v + SO);
+            box_sums<SEG + 2 * R, WN>(vv, hs);
 #pragma unroll
-            for (int q = 0; q < SV; q++) {
-                const float4 u = row[q];
-                v[4 * q] = u.x;
-                v[4 * q + 1] = u.y;
-                v[4 * q + 2] = u.z;
-                v[4 * q + 3] = u.w;
-            }
-            const float(&vv)[SEG + 2 * R] = *reinterpret_cast<const float(*)[SEG + 2 * R]>(v);
-            box_sums<SEG + 2 * R, WN>(vv, sm);
-#pragma unroll
-            for (int q = 0; q < SEG; q++) acc[k][q] = sm[q];
+            for (int q = 0; q < SEG; q++) acc[k][q] = hs[q];
         }
 
-        const int gy = y0 + r, gxs = x0 + sg * SEG;
+        const WinTile &ht = hdr[j % kWinHdrs];
+        const int w = ht.w, h = ht.h;
+        const int gy = ht.y0 + r, gxs = ht.x0 + sg * SEG;
         if (gy < h && gxs < w) {
             // With c = the window's in-image pixel count, G_ = S_G / c and
             // h_ = S_h / c, so adj(G_) h_ / (det G_ + lambda) =
             // adj(S_G) S_h / (det S_G + lambda c^2): one division.
             const int cy = min(gy + R, h - 1) - max(gy - R, 0) + 1;
-            float2 *frow = F.flow[dst] + (size_t)gy * p + gxs;
+            float2 *frow = ht.flow + (size_t)gy * ht.p + gxs;
             const bool whole = gxs + SEG <= w;
 #pragma unroll
             for (int q = 0; q < SEG; q += 2) {
