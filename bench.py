@@ -553,7 +553,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        es = max(3, min(args.steps, 20))
+        es = max(3, min(args.steps, 60))
         er = run_e2e(F, wl, frames, es, args.warmup)
         barrier()
         e2e = {"value": job_throughput(er["frames"], ws, max_over_ranks(er["time_s"], ws, dev_name)), "unit": "frames/s",

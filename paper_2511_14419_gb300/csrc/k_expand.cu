@@ -32,18 +32,13 @@ namespace {
 template <typename T>
 struct LevelSrc {
     const uint8_t *raw;  // level 0: raw samples
-    const T *img;        // level > 0: pyramid image
+    const T *img;        // level > 0 (or denoised level 0): pyramid image
     int pitch;           // raw row pitch in bytes, or image pitch in elements
     int bpp;
     float scale;
-    __device__ __forceinline__ LevelSrc(const FrameDesc &F, int level)
+    __device__ __forceinline__ LevelSrc(const uint8_t *raw_, const T *img_, int pitch_, int bpp_, float scale_)
+        : raw(raw_), img(img_), pitch(pitch_), bpp(bpp_), scale(scale_)
     {
-        // level 0 is the raw frame, or its denoised image when one exists
-        img = static_cast<const T *>(F.pyr[level]);
-        raw = img ? nullptr : static_cast<const uint8_t *>(F.raw);
-        bpp = F.bpp;
-        scale = F.unit_scale;
-        pitch = raw ? F.raw_pitch : F.lp[level];
     }
     __device__ __forceinline__ float at(int x, int y) const
     {
@@ -57,6 +52,21 @@ struct LevelSrc {
 
 }  // namespace
 
+// Per-tile descriptor fields, gathered by one thread two tiles ahead into
+// shared memory (the other threads take no dependent global loads per
+// tile).
+template <typename T>
+struct ExpTile {
+    using T4 = typename Store<T>::T4;
+    const uint8_t *raw;  // level-0 raw samples (null when the level reads an image)
+    const T *img;        // pyramid image of the level
+    T4 *fq;
+    T *fb;
+    T *pnext;            // next pyramid level (null at the top)
+    float scale;
+    int x0, y0, w, h, p, pitch, bpp, staged, wn, hn, pn;
+};
+
 // One block per kExpTW x kExpTH tile (kExpTW = the block's 256 threads):
 // the tile plus a HALO apron (replicate border) is staged in shared memory
 // once; then each thread walks down its column, forming the three row
@@ -67,6 +77,12 @@ struct LevelSrc {
 // The next pyramid level's even samples are blurred from the same staged
 // tile: a row pass at even columns into a second buffer, then a column
 // pass at even rows.
+//
+// Level 0 from raw samples (16-byte aligned rows, width a multiple of 16
+// bytes): the next tile's rows (row-clamped, 16-byte chunks inside the
+// image) are copied with cp.async into one of two raw buffers while this
+// tile is expanded; the conversion to 8-bit units then applies the column
+// clamp from the staged copy.  Other levels and sources load directly.
 template <typename T, int NH>
 __global__ void __launch_bounds__(256, 4) k_expand(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
@@ -75,9 +91,12 @@ __global__ void __launch_bounds__(256, 4) k_expand(const BatchDesc *__restrict__
     constexpr int IW = TW + 2 * HALO, IH = TH + 2 * HALO;
     constexpr int BW = TW / 2, HR = IH / 2;
     constexpr int NLD = (IH * IW + TW - 1) / TW;  // staged elements per thread
+    constexpr int SRB = (TW + 2 * 8) * 2;         // raw row bytes: 16-bit samples, one chunk each side
     static_assert(TW == 256 && IW % 2 == 0 && IH % 2 == 0, "tile geometry");
+    static_assert(IH * BW * sizeof(float) <= (size_t)IH * SRB, "pyramid row buffer fits a raw buffer");
     __shared__ __align__(16) float s_in[IH][IW];
-    __shared__ float s_hb[IH][BW];
+    __shared__ __align__(16) uint8_t s_raw[2][IH][SRB];
+    __shared__ ExpTile<T> s_hdr[3];
     using ST = Store<T>;
     using T4 = typename ST::T4;
 
@@ -95,21 +114,86 @@ __global__ void __launch_bounds__(256, 4) k_expand(const BatchDesc *__restrict__
     const int total = __ldg(off + nfr);
     const bool pyr_next = level + 1 < mc.pyr_levels;
     const int tid = threadIdx.x;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+
+    auto fill_hdr = [&](int t, ExpTile<T> &H) {
+        if (t >= total) return;
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
-        const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
+        const int w = F.lw[level], h = F.lh[level];
         const int ntx = (w + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
-        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
-        // A per-tile constant is removed before the fit (the fit of a
-        // constant is that constant: A and b are unchanged) to keep the
-        // single-precision moments small.
-        const LevelSrc<T> src(F, level);
-        T4 *fq = static_cast<T4 *>(F.fq_cur[level]);
-        T *fb = static_cast<T *>(F.fb_cur[level]);
-        const float c0 = src.at(min(x0 + TW / 2, w - 1), min(y0 + TH / 2, h - 1));
-        {
+        H.x0 = (lt % ntx) * TW;
+        H.y0 = (lt / ntx) * TH;
+        H.w = w;
+        H.h = h;
+        H.p = F.lp[level];
+        // level 0 is the raw frame, or its denoised image when one exists
+        H.img = static_cast<const T *>(F.pyr[level]);
+        H.raw = H.img ? nullptr : static_cast<const uint8_t *>(F.raw);
+        H.bpp = F.bpp;
+        H.scale = F.unit_scale;
+        H.pitch = H.raw ? F.raw_pitch : F.lp[level];
+        H.fq = static_cast<T4 *>(F.fq_cur[level]);
+        H.fb = static_cast<T *>(F.fb_cur[level]);
+        H.pnext = pyr_next ? static_cast<T *>(F.pyr[level + 1]) : nullptr;
+        H.wn = pyr_next ? F.lw[level + 1] : 0;
+        H.hn = pyr_next ? F.lh[level + 1] : 0;
+        H.pn = pyr_next ? F.lp[level + 1] : 0;
+        H.staged = H.raw && (H.bpp == 1 || H.bpp == 2) &&
+                   ((reinterpret_cast<uintptr_t>(H.raw) | (uintptr_t)H.pitch | (uintptr_t)(w * H.bpp)) & 15) == 0;
+    };
+    // cp.async of a staged tile: rows clamped to the image, 16-byte chunks
+    // [x0 - CE, x0 + TW + CE) that lie inside it (CE samples per chunk)
+    auto issue_raw = [&](const ExpTile<T> &H, int buf) {
+        const int ce = 16 / H.bpp, nch = TW / ce + 2, xs = H.x0 - ce;
+        for (int i = tid; i < IH * nch; i += TW) {
+            const int r = i / nch, q = i - r * nch, gx = xs + q * ce;
+            if (gx < 0 || gx + ce > H.w) continue;
+            const int gy = clampi(H.y0 - HALO + r, 0, H.h - 1);
+            const uint8_t *src = H.raw + (size_t)gy * H.pitch + (size_t)gx * H.bpp;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(
+                             &s_raw[buf][r][q * 16])),
+                         "l"(src)
+                         : "memory");
+        }
+    };
+
+    if (tid == 0) {
+        fill_hdr(blockIdx.x, s_hdr[0]);
+        fill_hdr(blockIdx.x + gridDim.x, s_hdr[1]);
+    }
+    __syncthreads();
+    if ((int)blockIdx.x < total && s_hdr[0].staged) issue_raw(s_hdr[0], 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    int k = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, k++) {
+        const ExpTile<T> &H = s_hdr[k % 3];
+        const int w = H.w, h = H.h, p = H.p, x0 = H.x0, y0 = H.y0;
+        float c0;
+        if (H.staged) {
+            // this tile's copies, then the column clamp and the conversion
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            const int bpp = H.bpp, xs = x0 - 16 / bpp;
+            const float scale = H.scale;
+            const uint8_t *rb = &s_raw[k & 1][0][0];
+            auto raw_at = [&](int r, int gx) {
+                const int i = gx - xs;
+                return (bpp == 2 ? (float)reinterpret_cast<const uint16_t *>(rb + r * SRB)[i] : (float)rb[r * SRB + i]) *
+                       scale;
+            };
+            // A per-tile constant is removed before the fit (the fit of a
+            // constant is that constant: A and b are unchanged) to keep the
+            // single-precision moments small.
+            c0 = raw_at(HALO + TH / 2, min(x0 + TW / 2, w - 1));
+            for (int e = tid; e < IH * IW; e += TW) {
+                const int r = e / IW, cc = e - r * IW;
+                s_in[r][cc] = raw_at(r, clampi(x0 - HALO + cc, 0, w - 1)) - c0;
+            }
+        } else {
+            const LevelSrc<T> src(H.raw, H.img, H.pitch, H.bpp, H.scale);
+            c0 = src.at(min(x0 + TW / 2, w - 1), min(y0 + TH / 2, h - 1));
             // every load of the thread first, then the shared-memory stores
             float v[NLD];
 #pragma unroll
@@ -128,6 +212,16 @@ __global__ void __launch_bounds__(256, 4) k_expand(const BatchDesc *__restrict__
             }
         }
         __syncthreads();
+        // two tiles ahead: the header; one tile ahead: the raw copies (their
+        // buffer's last reader was the previous tile's conversion)
+        if (tid == 0) fill_hdr(t + 2 * gridDim.x, s_hdr[(k + 2) % 3]);
+        {
+            const ExpTile<T> &Hn = s_hdr[(k + 1) % 3];
+            if (t + (int)gridDim.x < total && Hn.staged) issue_raw(Hn, (k + 1) & 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
+        T4 *const fq = H.fq;
+        T *const fb = H.fb;
 
         // expansion: thread = column, walking down the rows
         {
@@ -178,29 +272,32 @@ __global__ void __launch_bounds__(256, 4) k_expand(const BatchDesc *__restrict__
         }
 
         if (pyr_next) {
-            // [1 4 6 4 1]/16 along rows at even columns (half the rows per thread)
-            const int k = tid & (BW - 1), r0 = (tid / BW) * HR;
+            // [1 4 6 4 1]/16 along rows at even columns (half the rows per
+            // thread), into this tile's raw buffer (its samples are converted)
+            float(*s_hb)[BW] = reinterpret_cast<float(*)[BW]>(&s_raw[k & 1][0][0]);
+            const int kk = tid & (BW - 1), r0 = (tid / BW) * HR;
 #pragma unroll
             for (int i = 0; i < HR; i++) {
-                const float *row = &s_in[r0 + i][HALO + 2 * k];
-                s_hb[r0 + i][k] = (6.f * row[0] + 4.f * (row[-1] + row[1]) + (row[-2] + row[2])) * (1.f / 16.f);
+                const float *row = &s_in[r0 + i][HALO + 2 * kk];
+                s_hb[r0 + i][kk] = (6.f * row[0] + 4.f * (row[-1] + row[1]) + (row[-2] + row[2])) * (1.f / 16.f);
             }
             __syncthreads();
             // ... and along columns at even rows
-            T *pdst = static_cast<T *>(F.pyr[level + 1]);
-            const int wn = F.lw[level + 1], hn = F.lh[level + 1], pn = F.lp[level + 1];
-            const int gi = x0 / 2 + k;
+            T *pdst = H.pnext;
+            const int wn = H.wn, hn = H.hn, pn = H.pn;
+            const int gi = x0 / 2 + kk;
 #pragma unroll
             for (int q = 0; q < TH / 4; q++) {
                 const int jj = (tid / BW) * (TH / 4) + q, gj = y0 / 2 + jj;
                 const int cr = HALO + 2 * jj;
-                const float vv = (6.f * s_hb[cr][k] + 4.f * (s_hb[cr - 1][k] + s_hb[cr + 1][k]) +
-                                  (s_hb[cr - 2][k] + s_hb[cr + 2][k])) * (1.f / 16.f);
+                const float vv = (6.f * s_hb[cr][kk] + 4.f * (s_hb[cr - 1][kk] + s_hb[cr + 1][kk]) +
+                                  (s_hb[cr - 2][kk] + s_hb[cr + 2][kk])) * (1.f / 16.f);
                 if (gi < wn && gj < hn) ST::st(pdst + (size_t)gj * pn + gi, vv + c0);
             }
         }
         __syncthreads();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 void launch_expand(const BatchDesc *bd, const MethodConsts &mc, int level, bool half, int grid, cudaStream_t s)
