@@ -48,13 +48,14 @@ constexpr float kA = -1.586134342059924f, kB = -0.052980118572961f, kG = 0.88291
 constexpr float kInvK = (float)(1.0 / 1.230174104914001);
 constexpr int kDwtHalo = 4;
 
-// Whole-sample symmetric extension of index i into [0, n).  One
-// reflection suffices when the apron is shorter than the signal; tiny
-// signals take the periodic form.
+// Whole-sample symmetric extension of index i into [0, n), for any i: one
+// reflection where it lands inside, else the periodic form (a tile's apron
+// reaches more than a signal length past the edge on small images).
 __device__ __forceinline__ int mirror(int i, int n)
 {
     if (i >= 0 && i < n) return i;
-    if (n > kDwtHalo) return i < 0 ? -i : 2 * (n - 1) - i;
+    if (i < 0 && -i < n) return -i;
+    if (i >= n && i <= 2 * (n - 1)) return 2 * (n - 1) - i;
     if (n == 1) return 0;
     const int period = 2 * (n - 1);
     i %= period;
@@ -141,10 +142,26 @@ __device__ __forceinline__ void mask_rule(const M (&m)[N], int e, M &lo, M &hi)
     hi = b;
 }
 
+// A tile's geometry and descriptor fields, gathered by one thread two
+// tiles ahead into shared memory, so the other threads take no dependent
+// global loads per tile.
+struct DwtTile {
+    const void *llin;        // previous level's low-low plane (levels > 1)
+    const uint8_t *mlin;     // ... and its mask
+    const uint8_t *fraw;     // level 1: raw samples
+    const uint8_t *fmask;    // level 1: pixel mask
+    int32_t *coeffs;
+    float *dbg_yf;
+    void *llout;             // this level's low-low plane
+    uint8_t *llmout;         // ... and its mask
+    int W, iw, ih, bw, bh, bx0, by0, raw_pitch, bpp, dc_off, staged, pad;
+};
+
 // Shared-memory plan of k_dwt: the vertically lifted tile s_x [EH][EW+1]
-// (sample type), the mask rows [NB][EH][MW] bytes and, at level 1, the
-// staged raw samples [2][EH][EW] (u16).  Level 1 double-buffers the mask
-// and samples so the next tile's copies run during this tile's lifting.
+// (sample type), the mask rows [NB][EH][MW] bytes, at level 1 the staged
+// raw samples [2][EH][EW] (u16), and three tile headers.  Level 1
+// double-buffers the mask and samples so the next tile's copies run during
+// this tile's lifting.
 template <int WAV, bool L1>
 struct DwtSmem {
     using V = typename std::conditional<WAV == 97, float, int>::type;
@@ -154,7 +171,8 @@ struct DwtSmem {
     static constexpr size_t x_bytes = (size_t)EH * (EW + 1) * sizeof(V);
     static constexpr size_t m_off = (x_bytes + 15) / 16 * 16;
     static constexpr size_t r_off = (m_off + (size_t)NB * EH * MW + 15) / 16 * 16;
-    static constexpr size_t bytes = r_off + (L1 ? (size_t)2 * EH * EW * sizeof(uint16_t) : 0);
+    static constexpr size_t h_off = (r_off + (L1 ? (size_t)2 * EH * EW * sizeof(uint16_t) : 0) + 15) / 16 * 16;
+    static constexpr size_t bytes = h_off + 3 * sizeof(DwtTile);
 };
 
 __device__ __forceinline__ void cp_async8(void *dst, const void *src)
@@ -182,49 +200,68 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
     V (*s_x)[EW + 1] = reinterpret_cast<V (*)[EW + 1]>(dsm);
     uint8_t *const s_mb = dsm + SM::m_off;                                  // [NB][EH][MW]
     uint16_t *const s_rb = reinterpret_cast<uint16_t *>(dsm + SM::r_off);  // [2][EH][EW] (level 1)
+    DwtTile *const s_hdr = reinterpret_cast<DwtTile *>(dsm + SM::h_off);    // [3]
 
     const int nfr = bd->nframes;
     const int *off = bd->dwt_off[level - 1];
     const int total = __ldg(off + nfr);
     const bool last = level == mc.dwt_levels;
 
-    // Level 1: the raw samples and mask bytes of an interior tile (no
-    // symmetric extension, no clipping) are copied to the staging buffers
-    // with cp.async, 8 and 4 bytes per copy.
-    auto interior_async = [&](const FrameDesc &F, int ix0, int iy0) {
-        if (!L1 || F.bpp != 2) return false;
-        if (ix0 < 0 || iy0 < 0 || ix0 + EW > F.W || iy0 + EH > F.H) return false;
-        return ((reinterpret_cast<uintptr_t>(F.dwt_raw) | (uintptr_t)F.raw_pitch) & 7) == 0 &&
-               ((reinterpret_cast<uintptr_t>(F.dwt_mask) | (uintptr_t)F.W) & 3) == 0;
-    };
-    auto tile_origin = [&](int t, int &fi, int &ix0, int &iy0) {
-        fi = find_frame(off, nfr, t);
+    // The header of tile t (thread 0).  Level 1: a tile's raw samples and
+    // mask bytes are copied to the staging buffers with cp.async, 8 and 4
+    // bytes per copy (4 samples, 4 mask bytes): sample rows through the
+    // symmetric extension, chunks outside the image left out (the vertical
+    // pass reads a column outside from its mirror image inside), mask
+    // chunks and rows outside the image zero.
+    auto fill_hdr = [&](int t, DwtTile &H) {
+        if (t >= total) return;
+        const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
-        const int bw = (F.W >> (level - 1)) >> 1;
-        const int ntx = (bw + TW - 1) / TW;
+        H.W = F.W;
+        H.iw = F.W >> (level - 1);
+        H.ih = F.H >> (level - 1);
+        H.bw = H.iw >> 1;
+        H.bh = H.ih >> 1;
+        const int ntx = (H.bw + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
-        ix0 = 2 * ((lt % ntx) * TW) - HALO;
-        iy0 = 2 * ((lt / ntx) * TH) - HALO;
+        H.bx0 = (lt % ntx) * TW;
+        H.by0 = (lt / ntx) * TH;
+        H.llin = F.ll[level % 2];
+        H.mlin = F.llm[level % 2];
+        H.fraw = static_cast<const uint8_t *>(F.dwt_raw);
+        H.fmask = F.dwt_mask;
+        H.raw_pitch = F.raw_pitch;
+        H.bpp = F.bpp;
+        H.dc_off = F.dc_off;
+        H.coeffs = F.dwt_coeffs;
+        H.dbg_yf = F.dwt_yf;
+        H.llout = F.ll[(level - 1) % 2];
+        H.llmout = F.llm[(level - 1) % 2];
+        H.staged = L1 && F.bpp == 2 && ((reinterpret_cast<uintptr_t>(F.dwt_raw) | (uintptr_t)F.raw_pitch) & 7) == 0 &&
+                   ((reinterpret_cast<uintptr_t>(F.dwt_mask) | (uintptr_t)F.W) & 3) == 0;
     };
-    auto issue_async = [&](const FrameDesc &F, int ix0, int iy0, int buf) {
+    auto issue_async = [&](const DwtTile &H, int buf) {
         constexpr int NQ = EW / 4;  // 8-byte sample chunks (and 4-byte mask chunks) per row
-        const uint8_t *raw = static_cast<const uint8_t *>(F.dwt_raw) + (size_t)iy0 * F.raw_pitch + (size_t)ix0 * 2;
-        const uint8_t *msk = F.dwt_mask + (size_t)iy0 * F.W + ix0;
+        const int ix0 = 2 * H.bx0 - HALO, iy0 = 2 * H.by0 - HALO;
         uint16_t *rb = s_rb + (size_t)buf * EH * EW;
         uint8_t *mb = s_mb + (size_t)buf * EH * MW;
         for (int i = threadIdx.x; i < EH * NQ; i += blockDim.x) {
             const int r = i / NQ, q = i - r * NQ;
-            cp_async8(rb + r * EW + 4 * q, raw + (size_t)r * F.raw_pitch + 8 * q);
-            cp_async4(mb + r * MW + 4 * q, msk + (size_t)r * F.W + 4 * q);
+            const int gy = iy0 + r, gx = ix0 + 4 * q;  // ix0 and W are multiples of 4
+            const bool xin = gx >= 0 && gx + 4 <= H.W;
+            if (xin) cp_async8(rb + r * EW + 4 * q, H.fraw + (size_t)mirror(gy, H.ih) * H.raw_pitch + (size_t)gx * 2);
+            if (xin && gy >= 0 && gy < H.ih) cp_async4(mb + r * MW + 4 * q, H.fmask + (size_t)gy * H.W + gx);
+            else *reinterpret_cast<uint32_t *>(mb + r * MW + 4 * q) = 0u;
         }
     };
+    if (threadIdx.x == 0) {
+        fill_hdr(blockIdx.x, s_hdr[0]);
+        fill_hdr(blockIdx.x + gridDim.x, s_hdr[1]);
+    }
+    __syncthreads();
     if (L1) {
         // prologue: the block's first tile
-        if ((int)blockIdx.x < total) {
-            int fi, ix0, iy0;
-            tile_origin(blockIdx.x, fi, ix0, iy0);
-            if (interior_async(bd->f[fi], ix0, iy0)) issue_async(bd->f[fi], ix0, iy0, 0);
-        }
+        if ((int)blockIdx.x < total && s_hdr[0].staged) issue_async(s_hdr[0], 0);
         cp_async_commit();
     }
 
@@ -233,37 +270,27 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         const int cur = L1 ? (k & 1) : 0;
         uint8_t *const s_m = s_mb + (size_t)cur * EH * MW;
         uint16_t *const s_r = s_rb + (size_t)cur * EH * EW;
-        const int fi = find_frame(off, nfr, t);
-        const FrameDesc &F = bd->f[fi];
-        const int W = F.W;
-        const int iw = F.W >> (level - 1), ih = F.H >> (level - 1);
-        const int bw = iw >> 1, bh = ih >> 1;
-        const int ntx = (bw + TW - 1) / TW;
-        const int lt = t - __ldg(off + fi);
-        const int bx0 = (lt % ntx) * TW, by0 = (lt / ntx) * TH;
+        const DwtTile &H = s_hdr[k % 3];
+        const int W = H.W, iw = H.iw, ih = H.ih, bw = H.bw, bh = H.bh, bx0 = H.bx0, by0 = H.by0;
         const int ix0 = 2 * bx0 - HALO, iy0 = 2 * by0 - HALO;
         // Descriptor fields in registers (the output stores below could
         // otherwise force their reloads).
-        const V *llin = static_cast<const V *>(F.ll[level % 2]);
-        const uint8_t *mlin = F.llm[level % 2];
-        const uint8_t *fraw = static_cast<const uint8_t *>(F.dwt_raw);
-        const uint8_t *fmask = F.dwt_mask;
-        const int raw_pitch = F.raw_pitch, bpp = F.bpp, dc_off = F.dc_off;
-        int32_t *const coeffs = F.dwt_coeffs;
-        float *const dbg_yf = F.dwt_yf;
-        V *const llout = static_cast<V *>(F.ll[(level - 1) % 2]);
-        uint8_t *const llmout = F.llm[(level - 1) % 2];
-        const bool staged = L1 && interior_async(F, ix0, iy0);
+        const V *llin = static_cast<const V *>(H.llin);
+        const uint8_t *mlin = H.mlin;
+        const uint8_t *fraw = H.fraw;
+        const uint8_t *fmask = H.fmask;
+        const int raw_pitch = H.raw_pitch, bpp = H.bpp, dc_off = H.dc_off;
+        int32_t *const coeffs = H.coeffs;
+        float *const dbg_yf = H.dbg_yf;
+        V *const llout = static_cast<V *>(H.llout);
+        uint8_t *const llmout = H.llmout;
+        const bool staged = L1 && H.staged;
 
         if (L1) {
             // start the next tile's copies into the other buffers (their last
             // reader, the previous tile's vertical pass, is behind a barrier)
-            const int tn = t + gridDim.x;
-            if (tn < total) {
-                int fn, nx0, ny0;
-                tile_origin(tn, fn, nx0, ny0);
-                if (interior_async(bd->f[fn], nx0, ny0)) issue_async(bd->f[fn], nx0, ny0, cur ^ 1);
-            }
+            const DwtTile &Hn = s_hdr[(k + 1) % 3];
+            if (t + (int)gridDim.x < total && Hn.staged) issue_async(Hn, cur ^ 1);
             cp_async_commit();
         }
 
@@ -341,6 +368,9 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         }
         if (L1) cp_async_wait_prior();  // this tile's staged copies have landed
         __syncthreads();
+        // two tiles ahead: its header (the slot's last reader was the
+        // previous tile, behind the barrier above)
+        if (threadIdx.x == 0) fill_hdr(t + 2 * gridDim.x, s_hdr[(k + 2) % 3]);
 
         // Vertical: threads [0, EW) lift one column each in registers (level
         // 1 from the staged samples, with the DC shift); the next EW/4
@@ -349,10 +379,13 @@ __global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd
         // rule, in place (the columns are private to their item).
         if (threadIdx.x < EW) {
             const int c = threadIdx.x;
+            // a staged column outside the image is read from its mirror image
+            // (clamped: columns that far out feed no stored output)
+            const int cs = staged ? clampi(mirror(ix0 + c, iw) - ix0, 0, EW - 1) : c;
             V x[EH];
 #pragma unroll
             for (int j = 0; j < EH; j++) {
-                if constexpr (L1) x[j] = (V)((int)s_r[j * EW + c] - dc_off);
+                if constexpr (L1) x[j] = (V)((int)s_r[j * EW + cs] - dc_off);
                 else x[j] = s_x[j][c];
             }
             lift<V, EH>(x);

@@ -94,6 +94,18 @@ def test_ragged_sizes(orc, h, w):
     _stagewise(orc, prev.numpy(), cur.numpy(), 8, g, **levels)
 
 
+@pytest.mark.parametrize("h,w,wav", [(16, 16, 97), (16, 16, 53), (72, 40, 97), (48, 64, 53), (200, 264, 97)])
+def test_ragged_sizes_u16(orc, h, w, wav):
+    """12-bit frames of ragged and tiny sizes: the staged 16-bit tile loads
+    of the expansion and of DWT level 1 at image borders (symmetric
+    extension of rows and columns, the mask clipped), including frames
+    narrower than a DWT tile's apron."""
+    seq = u16(sequence_u16(5000 + h * 7 + w, 2, h, w, 3))
+    levels = dict(pyr_levels=2, dwt_levels=3, wavelet=wav) if h > 16 else dict(pyr_levels=2, dwt_levels=2, wavelet=wav)
+    g = run_stream([seq[0], seq[1]], 12, **levels)[1]
+    _stagewise(orc, seq[0], seq[1], 12, g, **levels)
+
+
 @pytest.mark.parametrize("cfg", [
     dict(win_r=2),
     dict(win_r=10, poly_n_half=3, poly_sigma=1.5),
