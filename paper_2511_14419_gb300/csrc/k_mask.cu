@@ -19,6 +19,8 @@
 // (k+1)-th largest S; selecting on S lets the first pass run inside the
 // saliency kernel, before min and max are known.  Every normalised value
 // (threshold included) is computed by the same two IEEE operations.
+#include <mutex>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -101,31 +103,103 @@ struct BlockHist {
 // the saliency tolerance; the exact cut is taken on these same values).
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
-// Saliency S, min/max of S, histogram of the first radix digit.  One
-// thread per column of a kSalTW x kSalTH tile walks down its rows, keeping
-// M = |d| of the rows above, at and below in registers (the next row's
-// flow is read one row ahead); the horizontal neighbours come from the
-// adjacent lanes, and the first and last lane of each warp read their
-// outer neighbour themselves.  Columns past the right edge repeat the last
+// Saliency S, min/max of S, histogram of the first radix digit.  A
+// kSalTW x kSalTH tile is taken in row strips of kSalSub rows: the strip's
+// flow plus one row above and below (rows clamped to the image) and its
+// 16-byte-aligned column apron is copied with cp.async into one of two
+// shared-memory buffers while the previous strip is processed.  One thread
+// per column walks down the strip, keeping M = |d| of the rows above, at
+// and below in registers; the horizontal neighbours come from the adjacent
+// lanes, and the first and last lane of each warp read their outer
+// neighbour themselves.  Columns past the right edge repeat the last
 // column, rows above and below repeat the edge rows (replicate border).
-__global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ bd, MethodConsts mc)
+// One thread gathers each tile's descriptor fields two tiles ahead into a
+// shared-memory header.
+constexpr int kSalSub = 8;                       // rows per strip
+constexpr int kSalRows = kSalSub + 2;            // staged rows
+constexpr int kSalCols = kSalTW + 4;             // staged columns x0-2 .. x0+TW+2 (float2)
+
+struct SalTile {
+    const float2 *fl;
+    float *S;
+    float2 *dbg;
+    unsigned *red;
+    int x0, y0, w, h, p, fi;
+};
+
+struct SalSmem {
+    static constexpr size_t fl_bytes = (size_t)2 * kSalRows * kSalCols * sizeof(float2);
+    static constexpr size_t hist_off = fl_bytes;
+    static constexpr size_t mm_off = hist_off + kHistBins * sizeof(unsigned);
+    static constexpr size_t hdr_off = (mm_off + 2 * sizeof(unsigned) + 15) / 16 * 16;
+    static constexpr size_t bytes = hdr_off + 3 * sizeof(SalTile);
+};
+
+__global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
-    constexpr int TW = kSalTW, TH = kSalTH;
+    constexpr int TW = kSalTW, TH = kSalTH, SH = kSalSub, NSUB = TH / SH;
     static_assert(TW == 256, "one thread per tile column");
-    __shared__ unsigned s_hist[kHistBins];
-    __shared__ unsigned s_mm[2];
+    static_assert(TH % SH == 0, "whole strips");
+    extern __shared__ __align__(16) unsigned char ssm[];
+    float2 (*s_fl)[kSalRows][kSalCols] = reinterpret_cast<float2 (*)[kSalRows][kSalCols]>(ssm);
+    unsigned *const s_hist = reinterpret_cast<unsigned *>(ssm + SalSmem::hist_off);
+    unsigned *const s_mm = reinterpret_cast<unsigned *>(ssm + SalSmem::mm_off);
+    SalTile *const s_hdr = reinterpret_cast<SalTile *>(ssm + SalSmem::hdr_off);
     const int nfr = bd->nframes;
     const int *off = bd->sal_off;
     const int total = __ldg(off + nfr);
     const int buf = bd->final_flow_buf;
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31;
     const float wm = mc.alpha, wg = 1.f - mc.alpha;
     BlockHist bh{s_hist, s_mm};
     bh.with_minmax = true;
     unsigned mn = 0x7f800000u, mx = 0u;
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+
+    auto fill_hdr = [&](int t, SalTile &H) {
+        if (t >= total) return;
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
+        H.fi = fi;
+        H.fl = F.flow[buf];
+        H.S = F.S;
+        H.dbg = F.dbg_flow;
+        H.red = F.red;
+        H.w = F.W;
+        H.h = F.H;
+        H.p = F.lp[0];
+        const int ntx = (H.w + TW - 1) / TW;
+        const int lt = t - __ldg(off + fi);
+        H.x0 = (lt % ntx) * TW;
+        H.y0 = (lt / ntx) * TH;
+    };
+    // strip `sub` of a tile into buffer b: 16-byte chunks (two flow
+    // vectors; x0, the width and the row pitch are even) inside the image
+    auto issue = [&](const SalTile &H, int sub, int b) {
+        constexpr int NCH = kSalCols / 2;
+        for (int i = tid; i < kSalRows * NCH; i += TW) {
+            const int r = i / NCH, q = i - r * NCH;
+            const int gx = H.x0 - 2 + 2 * q;
+            if (gx < 0 || gx + 2 > H.w) continue;
+            const int gy = clampi(H.y0 + sub * SH - 1 + r, 0, H.h - 1);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(
+                             &s_fl[b][r][2 * q])),
+                         "l"(H.fl + (size_t)gy * H.p + gx)
+                         : "memory");
+        }
+    };
+
+    if (tid == 0) {
+        fill_hdr(blockIdx.x, s_hdr[0]);
+        fill_hdr(blockIdx.x + gridDim.x, s_hdr[1]);
+    }
+    __syncthreads();
+    if ((int)blockIdx.x < total) issue(s_hdr[0], 0, 0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    int k = 0, u = 0;  // tile and strip counters of the block
+    for (int t = blockIdx.x; t < total; t += gridDim.x, k++) {
+        const SalTile &H = s_hdr[k % 3];
+        const int fi = H.fi;
         if (fi != bh.frame) {
             // this thread's extrema belong to the frame being left
 #pragma unroll
@@ -141,58 +215,58 @@ __global__ void __launch_bounds__(256) k_saliency(const BatchDesc *__restrict__ 
             mx = 0u;
         }
         bh.begin(fi);
-        bh.target = F.red;
-        const int w = F.W, h = F.H, p = F.lp[0];
-        const int ntx = (w + TW - 1) / TW;
-        const int lt = t - __ldg(off + fi);
-        const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
-        const float2 *fl = F.flow[buf];
-        float *const Sp = F.S;
-        float2 *const dbg_flow = F.dbg_flow;
-        const int gx = x0 + (int)threadIdx.x;
-        const int cx = min(gx, w - 1);
-        // the outer neighbour column of the warp's first / last lane
-        const int ex = lane == 0 ? max(cx - 1, 0) : min(cx + 1, w - 1);
+        bh.target = H.red;
+        const int w = H.w, h = H.h, p = H.p, x0 = H.x0, y0 = H.y0;
+        float *const Sp = H.S;
+        float2 *const dbg_flow = H.dbg;
+        const int gx = x0 + tid;
+        // staged columns of the thread's pixel and of the warp's outer
+        // neighbours (clamped to the image)
+        const int cg = min(gx, w - 1);
+        const int cx = cg - (x0 - 2);
+        const int ex = (lane == 0 ? max(cg - 1, 0) : min(cg + 1, w - 1)) - (x0 - 2);
         const bool edge = lane == 0 || lane == 31;
-        auto mag = [&](int x, int y) {
-            const float2 v = __ldg(fl + (size_t)y * p + x);
-            return fast_sqrt(v.x * v.x + v.y * v.y);
-        };
-        float Mp = mag(cx, max(y0 - 1, 0)), Mc = mag(cx, y0);
-        float Ec = edge ? mag(ex, y0) : 0.f;
-        constexpr int RB = 8;  // rows whose flow is read ahead together
-        static_assert(TH % RB == 0, "row batches");
+        for (int sub = 0; sub < NSUB; sub++, u++) {
+            // this strip has landed; every thread is done with the other buffer
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+            if (sub == 0 && tid == 0) fill_hdr(t + 2 * (int)gridDim.x, s_hdr[(k + 2) % 3]);
+            if (sub + 1 < NSUB) issue(H, sub + 1, (u + 1) & 1);
+            else if (t + (int)gridDim.x < total) issue(s_hdr[(k + 1) % 3], 0, (u + 1) & 1);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+
+            const float2(*fl)[kSalCols] = s_fl[u & 1];
+            auto mag = [&](int r, int c) {
+                const float2 v = fl[r][c];
+                return fast_sqrt(v.x * v.x + v.y * v.y);
+            };
+            float Mp = mag(0, cx), Mc = mag(1, cx);
+            float Ec = edge ? mag(1, ex) : 0.f;
 #pragma unroll
-        for (int j0 = 0; j0 < TH; j0 += RB) {
-            float Mn[RB], En[RB];
-#pragma unroll
-            for (int k = 0; k < RB; k++) {
-                const int yn = min(y0 + j0 + k + 1, h - 1);
-                Mn[k] = mag(cx, yn);
-                En[k] = edge ? mag(ex, yn) : 0.f;
-            }
-#pragma unroll
-            for (int k = 0; k < RB; k++) {
-                const int gy = y0 + j0 + k;
+            for (int j = 0; j < SH; j++) {
+                const float Mn = mag(j + 2, cx);
+                const float En = edge ? mag(j + 2, ex) : 0.f;
+                const int gy = y0 + sub * SH + j;
                 float Ml = __shfl_up_sync(0xffffffffu, Mc, 1), Mr = __shfl_down_sync(0xffffffffu, Mc, 1);
                 if (lane == 0) Ml = Ec;
                 if (lane == 31) Mr = Ec;
                 if (gx < w && gy < h) {
-                    const float gxv = 0.5f * (Mr - Ml), gyv = 0.5f * (Mn[k] - Mp);
+                    const float gxv = 0.5f * (Mr - Ml), gyv = 0.5f * (Mn - Mp);
                     const float S = wm * Mc + wg * fast_sqrt(gxv * gxv + gyv * gyv);
                     Sp[(size_t)gy * p + gx] = S;
-                    if (dbg_flow) dbg_flow[(size_t)gy * w + gx] = __ldg(fl + (size_t)gy * p + gx);
+                    if (dbg_flow) dbg_flow[(size_t)gy * w + gx] = fl[j + 1][cx];
                     const unsigned b = __float_as_uint(S);
                     mn = min(mn, b);
                     mx = max(mx, b);
                     atomicAdd(&s_hist[b >> digit_shift(0)], 1u);
                 }
                 Mp = Mc;
-                Mc = Mn[k];
-                Ec = En[k];
+                Mc = Mn;
+                Ec = En;
             }
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
@@ -479,9 +553,26 @@ __global__ void __launch_bounds__(256) k_morph(const BatchDesc *__restrict__ bd,
 }
 
 void launch_frame_init(const BatchDesc *bd, int grid, cudaStream_t s) { k_frame_init<<<grid, 256, 0, s>>>(bd); }
+namespace {
+// k_saliency takes more than the default 48 KB of dynamic shared memory:
+// raise its limit once per device.
+void ensure_saliency_attr()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaFuncSetAttribute(k_saliency, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SalSmem::bytes);
+    done[dev] = true;
+}
+}  // namespace
+
 void launch_saliency(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s)
 {
-    k_saliency<<<grid, 256, 0, s>>>(bd, mc);
+    ensure_saliency_attr();
+    k_saliency<<<grid, 256, SalSmem::bytes, s>>>(bd, mc);
 }
 void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s) { k_select_pass<<<grid, 256, 0, s>>>(bd, pass); }
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s)
@@ -493,7 +584,8 @@ void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStr
 int occupancy_mask_kernels()
 {
     int a = 0, b = 0, c = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_saliency, 256, 0);
+    ensure_saliency_attr();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_saliency, 256, SalSmem::bytes);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_select_pass, 256, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_morph, 256, 0);
     return min(a, min(b, c));
