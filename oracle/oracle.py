@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "flowroi_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "orc_ebcot.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liborc.so")
 _lib = None
@@ -31,10 +32,10 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (plain IEEE double: no fast-math, no FMA
     contraction, so x86 and Arm builds round identically)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB_PATH) or any(os.path.getmtime(_LIB_PATH) < os.path.getmtime(f) for f in _SRCS):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-o", tmp, *_SRCS, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -92,6 +93,10 @@ def _declare(L):
         "orc_quantise_f64": (None, [_P, _I, _I, _I, _P, _P]),
         "orc_wavelet_mask": (None, [_P, _I, _I, _I, _I, _P]),
         "orc_roi_shift": (_I, [_P, _P, _I64, _I]),
+        "orc_mq_roundtrip": (ctypes.c_long, [_P, _P, ctypes.c_long, _P, _P]),
+        "orc_t1_encode": (_I, [_P, _I, _I, _I, _I, _P, ctypes.c_long, _P, _P, _P]),
+        "orc_t1_decode": (None, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _I]),
+        "orc_hull": (_I, [_I, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -428,6 +433,204 @@ def roi_shift(q: np.ndarray, cmask: np.ndarray, s: int) -> np.ndarray:
     if lib().orc_roi_shift(_ptr(a), _ptr(m), a.size, s) != 0:
         raise OverflowError("RoI up-shift overflows int32")
     return a
+
+
+# ------------------------------------------- embedded block coding (f4) --
+#
+# The JPEG2000 coder downstream of the front end (orc_ebcot.c): tier-1
+# coding of 64 x 64 code-blocks, rate control to a byte budget, a frame
+# container, and the decoder used for PSNR.
+
+CB = 64
+ORI_LL, ORI_HL, ORI_LH, ORI_HH = 0, 1, 2, 3
+_MAGIC = b"FRJ2"
+_HDR = 32
+_ENT = 16
+
+
+def mq_roundtrip(d: np.ndarray, cx: np.ndarray):
+    """MQ-encode decisions d in contexts cx (one terminated codeword) and
+    decode them back: (codeword bytes, decoded decisions)."""
+    d = _c(d, np.uint8)
+    cx = _c(cx, np.uint8)
+    code = np.zeros(2 * d.size + 16, np.uint8)
+    out = np.empty_like(d)
+    n = lib().orc_mq_roundtrip(_ptr(d), _ptr(cx), d.size, _ptr(code), _ptr(out))
+    return code[:n].copy(), out
+
+
+def t1_encode(q: np.ndarray, ori: int):
+    """Tier-1 coding of one code-block: (planes, pass lengths, pass
+    distortion decreases, bytes of all passes back to back)."""
+    q = _c(q, np.int32)
+    h, w = q.shape
+    cap = 8 * 64 * 64 * 96
+    out = np.empty(cap, np.uint8)
+    planes = ctypes.c_int(0)
+    plen = np.zeros(96, np.int32)
+    dist = np.zeros(96, np.float64)
+    n = lib().orc_t1_encode(_ptr(q), w, w, h, ori, _ptr(out), cap, ctypes.byref(planes), _ptr(plen), _ptr(dist))
+    if n < 0:
+        raise OverflowError("code-block output too large")
+    return planes.value, plen[:n].copy(), dist[:n].copy(), out[: int(plen[:n].sum())].copy()
+
+
+def t1_decode(code: np.ndarray, plen: np.ndarray, nkept: int, planes: int, w: int, h: int, ori: int,
+              midpoint: bool = True) -> np.ndarray:
+    code = _c(code, np.uint8)
+    plen = _c(plen, np.int32)
+    q = np.zeros((h, w), np.int32)
+    lib().orc_t1_decode(_ptr(code), _ptr(plen), nkept, planes, w, h, ori, int(midpoint), _ptr(q), w)
+    return q
+
+
+def codeblocks(w: int, h: int, levels: int):
+    """Code-blocks of a Mallat coefficient plane in codestream order: the
+    low-low band, then HL, LH, HH of each level from the coarsest; 64 x 64
+    blocks from each band's origin, in raster order.  Yields (band index,
+    orientation, x0, y0, width, height); band indices follow the
+    quantisation-step table (HL, LH, HH of level l at 3(l-1), +1, +2; low-low
+    at 3 levels)."""
+    out = []
+    bands = [(3 * levels, ORI_LL, 0, 0, w >> levels, h >> levels)]
+    for l in range(levels, 0, -1):
+        bw, bh = w >> l, h >> l
+        bands += [(3 * (l - 1), ORI_HL, bw, 0, bw, bh), (3 * (l - 1) + 1, ORI_LH, 0, bh, bw, bh),
+                  (3 * (l - 1) + 2, ORI_HH, bw, bh, bw, bh)]
+    for b, ori, bx, by, bw, bh in bands:
+        for y in range(0, bh, CB):
+            for x in range(0, bw, CB):
+                out.append((b, ori, bx + x, by + y, min(CB, bw - x), min(CB, bh - y)))
+    return out
+
+
+def hull(plen: np.ndarray, dist: np.ndarray):
+    """Lower convex hull of a code-block's truncation points: (pass counts,
+    slopes), slopes strictly decreasing (slope[0] unused)."""
+    n = len(plen)
+    R = np.zeros(n + 1, np.int64)
+    D = np.zeros(n + 1, np.float64)
+    for k in range(n):  # cumulative, in pass order
+        R[k + 1] = R[k] + int(plen[k])
+        D[k + 1] = D[k] + float(dist[k])
+    hk = np.zeros(n + 1, np.int32)
+    hs = np.zeros(n + 1, np.float64)
+    m = lib().orc_hull(n, _ptr(R), _ptr(D), _ptr(hk), _ptr(hs))
+    return hk[:m].copy(), hs[:m].copy(), R
+
+
+def pcrd(blocks, budget: int, iters: int = 64):
+    """Rate control: passes kept per code-block so that the kept pass bytes
+    fit `budget` (0: keep every pass).  The slope threshold lambda is found
+    by `iters` bisection steps on [0, 2 max slope + 1]; a block keeps the
+    passes up to its last hull point whose slope is >= lambda."""
+    hs = [hull(b["plen"], b["dist"]) for b in blocks]
+    full = sum(int(b["plen"].sum()) for b in blocks)
+    if budget <= 0 or full <= budget:
+        return [len(b["plen"]) for b in blocks]
+
+    def keep(lam):
+        ks, tot = [], 0
+        for hk, sl, R in hs:
+            j = 0
+            while j + 1 < len(hk) and sl[j + 1] >= lam:
+                j += 1
+            ks.append(int(hk[j]))
+            tot += int(R[hk[j]])
+        return ks, tot
+
+    lo = 0.0
+    hi = 2.0 * max([float(sl[1]) for hk, sl, R in hs if len(hk) > 1] + [0.0]) + 1.0
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if keep(mid)[1] <= budget:
+            hi = mid
+        else:
+            lo = mid
+    return keep(hi)[0]
+
+
+def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_depth: int, budget: int = 0):
+    """Tier-1 coding of every code-block of a Mallat plane, rate control to
+    `budget` bytes of pass data (0: lossless in the passes), and the frame
+    container: a 32-byte header, a 16-byte entry per code-block, then per
+    code-block the kept passes' 16-bit lengths and bytes.  Returns (bytes,
+    block records)."""
+    import struct
+    coeffs = _c(coeffs, np.int32)
+    h, w = coeffs.shape
+    blocks = []
+    for b, ori, x0, y0, cw, ch in codeblocks(w, h, levels):
+        planes, plen, dist, code = t1_encode(coeffs[y0:y0 + ch, x0:x0 + cw], ori)
+        blocks.append(dict(band=b, ori=ori, x0=x0, y0=y0, w=cw, h=ch, planes=planes, plen=plen, dist=dist,
+                           code=code))
+    nkeep = pcrd(blocks, budget)
+    data, table = [], []
+    off = 0
+    for blk, k in zip(blocks, nkeep):
+        blk["nkeep"] = k
+        body = np.asarray(blk["plen"][:k], "<u2").tobytes() + blk["code"][: int(blk["plen"][:k].sum())].tobytes()
+        table.append(struct.pack("<IHHBBBBBBH", off, blk["x0"], blk["y0"], blk["w"] - 1, blk["h"] - 1, blk["band"],
+                                 blk["planes"], len(blk["plen"]), k, 0))
+        data.append(body)
+        off += len(body)
+    hdr = struct.pack("<4sIIIBBBBIII", _MAGIC, 1, w, h, wavelet, levels, shift, bit_depth, len(blocks), off, 0)
+    return hdr + b"".join(table) + b"".join(data), blocks
+
+
+def decode_frame(stream: bytes, midpoint: bool = True) -> np.ndarray:
+    """The Mallat coefficient plane recovered from a frame container (kept
+    passes only; unknown low bits at the interval midpoint when
+    `midpoint`)."""
+    import struct
+    magic, ver, w, h, wav, levels, shift, bd, nb, nbytes, _ = struct.unpack_from("<4sIIIBBBBIII", stream, 0)
+    if magic != _MAGIC or ver != 1:
+        raise ValueError("not a frame container")
+    out = np.zeros((h, w), np.int32)
+    base = _HDR + nb * _ENT
+    oris = {b: o for b, o, *_ in codeblocks(w, h, levels)}
+    for i in range(nb):
+        off, x0, y0, cw1, ch1, band, planes, npass, k, _ = struct.unpack_from("<IHHBBBBBBH", stream, _HDR + i * _ENT)
+        p = base + off
+        plen = np.frombuffer(stream, "<u2", k, p).astype(np.int32)
+        code = np.frombuffer(stream, np.uint8, int(plen.sum()), p + 2 * k)
+        out[y0:y0 + ch1 + 1, x0:x0 + cw1 + 1] = t1_decode(code, plen, k, planes, cw1 + 1, ch1 + 1, oris[band],
+                                                          midpoint)
+    return out
+
+
+def unshift_dequantise(q: np.ndarray, cmask: np.ndarray, shift: int, levels: int, wavelet: int, bit_depth: int,
+                       delta_base: float = 1.0) -> np.ndarray:
+    """Inverse of the RoI up-shift (RoI coefficients, known from the
+    wavelet-domain mask, shifted back down) and of the quantiser (9/7: y =
+    q delta_b; 5/3: y = q), as the transform's input type."""
+    q = _c(q, np.int64)
+    m = _c(cmask, np.uint8) != 0
+    a = np.abs(q)
+    a = np.where(m, a >> shift, a)
+    q = np.sign(q) * a
+    if wavelet == 53:
+        return q.astype(np.int32)
+    _, delta, _, _ = delta_table(levels, bit_depth, delta_base)
+    h, w = q.shape
+    d = np.empty((h, w), np.float64)
+    for y in range(h):
+        for x in range(w):
+            d[y, x] = delta[subband_index(x, y, w, h, levels)]
+    return q.astype(np.float64) * d
+
+
+def reconstruct(y: np.ndarray, levels: int, wavelet: int, bit_depth: int) -> np.ndarray:
+    """Inverse DWT, inverse DC shift and clipping to the sample range."""
+    x = dwt2d(y, wavelet, levels, inverse=True)
+    x = np.rint(np.asarray(x, np.float64)) + 2.0 ** (bit_depth - 1)
+    return np.clip(x, 0, 2 ** bit_depth - 1).astype(np.int64)
+
+
+def psnr(a: np.ndarray, b: np.ndarray, bit_depth: int) -> float:
+    e = np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2)
+    peak = 2.0 ** bit_depth - 1
+    return float("inf") if e == 0 else 10.0 * np.log10(peak * peak / e)
 
 
 # ------------------------------------------------------------- pipeline --
