@@ -57,6 +57,11 @@ WORKLOADS = {
     # correlation of pyramid level 2 (512x512 FFTs)
     "register_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                              dwt_levels=5, wavelet=97, precision=32, seed_base=3000, register_frames=1, reg_level=2),
+    # the batched workload, each step's 16 frames also coded into
+    # rate-controlled containers of 1 bit per pixel of pass data (EBCOT tier-1,
+    # rate control, container)
+    "ebcot_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
     # four streams of the batched workload's frames (small case for profiler captures)
     "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
@@ -337,6 +342,58 @@ def run_e2e(F, wl, frames, steps, warmup):
     return res
 
 
+def run_codestream(F, wl, frames, steps, warmup):
+    """Device-resident pipeline steps, each followed by the coding of its
+    frames' coefficient planes into rate-controlled containers
+    (flowroi_encode_codestreams on device buffers).  Returns the wall time
+    of the timed steps, the time spent in the coder, and the containers'
+    mean size."""
+    import torch
+    cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
+               precision=wl["precision"], max_batch_frames=64, result_ring=8, flags=F.MANUAL,
+               device=torch.cuda.current_device())
+    S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
+    H, W, L = wl["h"], wl["w"], wl["dwt_levels"]
+    budget = int(wl["codestream_bpp"] * H * W / 8)
+    cap = F.flowroi_codestream_bound(W, H, L) // 4
+    coef = [torch.empty((H, W), dtype=torch.int32, device="cuda") for _ in range(S)]
+    outs = [torch.empty(cap, dtype=torch.uint8, device="cuda") for _ in range(S)]
+    jobs = [dict(coeffs=coef[s], out=outs[s], levels=L, wavelet=wl["wavelet"], shift=5, bit_depth=bd, budget=budget)
+            for s in range(S)]
+    res = {}
+    with F.Context(**cfg) as ctx:
+        t = 0
+        cs_time = 0.0
+        lens = []
+
+        def one_step(timed):
+            nonlocal t, cs_time
+            i = frame_index(t, n)
+            submit_all(F, ctx.h, [(s, frames[s][i], t, bd) for s in range(S)])
+            F.flowroi_step(ctx.h)
+            for s in range(S):
+                F.flowroi_get_coeffs(ctx.h, s, t, coef[s], -1)
+            t0 = time.perf_counter()
+            ls = F.flowroi_encode_codestreams(ctx.h, jobs)
+            if timed:
+                cs_time += time.perf_counter() - t0
+                lens.extend(ls)
+            t += 1
+
+        for _ in range(warmup + 1):
+            one_step(False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one_step(True)
+        torch.cuda.synchronize()
+        res["time_s"] = time.perf_counter() - t0
+    res["frames"] = steps * S
+    res["cs_time_s"] = cs_time
+    res["bpp"] = 8.0 * float(sum(lens)) / (len(lens) * H * W) if lens else None
+    return res
+
+
 def run_serving(F, wl, rate_fps: float, duration_s: float, burst_per_stream: int, seed: int = 7):
     """Serving through the public API with the scheduler thread: 64 streams
     of mixed resolution submit frames from pinned host memory, (1) as Poisson
@@ -530,6 +587,21 @@ def main():
                               "burst_frames_per_stream": args.burst, "phases": res}), flush=True)
         return
     frames = make_frames(wl, f"cuda:{local}")
+    if "codestream_bpp" in wl:
+        # pipeline + codestream measurement: its own JSON line (rank 0)
+        torch.cuda.synchronize()
+        cr = run_codestream(F, wl, frames, args.steps, args.warmup)
+        t_max = max_over_ranks(cr["time_s"], ws, "cpu")
+        if rank == 0:
+            print(json.dumps({"metric": "frames/s (flow+mask+DWT+codestream) at 1 GB300", "workload": args.workload,
+                              "value": job_throughput(cr["frames"], ws, t_max), "unit": "frames/s", "n_gpus": ws,
+                              "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": 1e3 * t_max / args.steps,
+                              "codestream_ms_per_step": 1e3 * cr["cs_time_s"] / args.steps,
+                              "codestream_target_bpp": wl["codestream_bpp"], "codestream_bpp": cr["bpp"],
+                              "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+                              "config": config_of(args.workload, wl)}), flush=True)
+        return
 
     def barrier():
         if ws > 1:

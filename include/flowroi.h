@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define FLOWROI_ABI_VERSION 2
+#define FLOWROI_ABI_VERSION 3
 
 /* Exported symbols (the library is built with hidden default visibility). */
 #if defined(__GNUC__)
@@ -69,6 +69,7 @@ extern "C" {
 #define FLOWROI_EDEVICE (-6)    /* a CUDA error was seen; the context is poisoned */
 #define FLOWROI_EGONE (-7)      /* result overwritten: the stream's result ring wrapped */
 #define FLOWROI_ENOTKEPT (-8)   /* intermediate requested without FLOWROI_KEEP_INTERMEDIATES */
+#define FLOWROI_ERANGE (-9)     /* output buffer too small, or a value outside the coder's range */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define FLOWROI_U8 1            /* 8-bit unsigned samples */
@@ -349,6 +350,61 @@ FLOWROI_API int flowroi_get_kernel_times(flowroi_ctx *ctx, flowroi_kernel_time *
 FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, int pitch_bytes, int dtype,
                                         int bit_depth, const uint8_t *mask, int wavelet, int levels,
                                         int scale_shift, const float *delta, int32_t *coeffs, void *cuda_stream);
+
+/* Embedded block coding of coefficient planes into frame containers.
+ *
+ * Paper: §Implementation details and Table 1 - the RoI-shifted JPEG2000
+ * coefficients are coded by a JPEG2000 coder and the codestream is cut to
+ * the target compression rate.  This is that coder's block coder and rate
+ * control, from the JPEG2000 Part 1 definitions: 64 x 64 code-blocks from
+ * each sub-band's origin; bit-plane coding passes (significance
+ * propagation, magnitude refinement, cleanup with run-length mode) with the
+ * MQ arithmetic coder, every pass terminated (its own byte segment);
+ * per-pass distortion decreases of the midpoint reconstruction on the
+ * quantised, RoI-shifted coefficients; rate control by the lower convex
+ * hull of each code-block's truncation points and a slope threshold found
+ * by bisection so that the kept pass bytes fit budget_bytes.
+ *
+ * Container (little-endian): a 32-byte header {"FRJ2", u32 version 1, u32
+ * width, u32 height, u8 wavelet, u8 levels, u8 shift, u8 bit_depth, u32
+ * code-blocks, u32 data bytes, u32 0}; per code-block a 16-byte entry {u32
+ * data offset, u16 x0, u16 y0 (in the plane), u8 width-1, u8 height-1, u8
+ * band (HL, LH, HH of level l at 3(l-1), +1, +2; low-low at 3 levels), u8
+ * bit-planes, u8 passes coded, u8 passes kept, u16 0}, in codestream order
+ * (low-low band, then HL, LH, HH of each level from the coarsest, raster
+ * order within a band); then the data: per code-block the kept passes'
+ * u16 lengths and their bytes.
+ *
+ * One job per frame:
+ *   coeffs        width x height int32 Mallat plane (the layout of
+ *                 flowroi_get_coeffs), magnitudes below 2^24
+ *   width, height multiples of 2^levels, at most 65535
+ *   levels        DWT levels of the plane, [1, 8]
+ *   wavelet, shift, bit_depth   recorded in the header (53 or 97, [0, 15],
+ *                 [1, 16])
+ *   budget_bytes  pass-data budget; <= 0 keeps every pass
+ *   out, out_cap  destination of the container and its capacity
+ *   out_len       set to the container's length (or, when it does not fit,
+ *                 to the length it needs, with FLOWROI_ERANGE)
+ * on_device: coeffs and out are device pointers of the context's device
+ * (else host pointers; the library copies).  Runs synchronously on a
+ * stream of its own with scratch memory allocated for the call (about
+ * 34 KB per code-block); n in [1, 64].  Returns FLOWROI_OK, FLOWROI_EINVAL
+ * (malformed job), FLOWROI_ENOMEM, FLOWROI_ERANGE (a container did not fit
+ * or a code-block exceeded the coder's limits) or FLOWROI_EDEVICE. */
+typedef struct {
+    const int32_t *coeffs;
+    int32_t width, height;
+    int32_t levels, wavelet, shift, bit_depth;
+    int64_t budget_bytes;
+    uint8_t *out;
+    uint64_t out_cap;
+    uint64_t out_len;
+} flowroi_cs_job;
+FLOWROI_API int flowroi_encode_codestreams(flowroi_ctx *ctx, int n, flowroi_cs_job *jobs, int on_device);
+/* A container capacity that always suffices for a width x height plane of
+ * `levels` levels (0 for a malformed geometry). */
+FLOWROI_API uint64_t flowroi_codestream_bound(int width, int height, int levels);
 
 /* Library ABI version (FLOWROI_ABI_VERSION). */
 FLOWROI_API int flowroi_abi_version(void);

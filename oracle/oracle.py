@@ -470,6 +470,8 @@ def t1_encode(q: np.ndarray, ori: int):
     plen = np.zeros(96, np.int32)
     dist = np.zeros(96, np.float64)
     n = lib().orc_t1_encode(_ptr(q), w, w, h, ori, _ptr(out), cap, ctypes.byref(planes), _ptr(plen), _ptr(dist))
+    if n == -2:
+        raise OverflowError("code-block magnitude of 2^24 or more")
     if n < 0:
         raise OverflowError("code-block output too large")
     return planes.value, plen[:n].copy(), dist[:n].copy(), out[: int(plen[:n].sum())].copy()

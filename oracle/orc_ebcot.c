@@ -366,12 +366,15 @@ static int64_t recon2(uint32_t m, int p)
     return 2 * (int64_t)((m >> p) << p) + (p > 0 ? ((int64_t)1 << p) : 0);
 }
 
-static double derr(uint32_t m, int p_before, int p_after)
+/* Decrease of the squared error (doubled units) when m's reconstruction
+ * goes from planes >= p_before known (p_before > 31: not yet significant)
+ * to planes >= p_after known.  Exact in int64 for m < 2^24. */
+static int64_t derr(uint32_t m, int p_before, int p_after)
 {
     const int64_t t = 2 * (int64_t)m;
     const int64_t eb = t - (p_before > 31 ? 0 : recon2(m, p_before));
     const int64_t ea = t - recon2(m, p_after);
-    return (double)(eb * eb - ea * ea);
+    return eb * eb - ea * ea;
 }
 
 /* Number of magnitude bit-planes of a code-block (0 when all zero). */
@@ -403,10 +406,11 @@ static void cb_load(orc_cb *b, const int32_t *q, int stride, int w, int h, int o
 /* Codes (enc) or decodes one pass of plane p.  type 0 = significance
  * propagation, 1 = magnitude refinement, 2 = cleanup.  Decoding sets bits
  * of b->m and the sign flags.  Returns the pass's distortion decrease
- * (encoding only). */
-static double cb_pass(orc_cb *b, int type, int p, orc_ctx *x, orc_mqe *e, orc_mqd *dd)
+ * (encoding only), an exact integer sum (so independent of the order of
+ * summation). */
+static int64_t cb_pass(orc_cb *b, int type, int p, orc_ctx *x, orc_mqe *e, orc_mqd *dd)
 {
-    double dd_sum = 0.0;
+    int64_t dd_sum = 0;
     const int enc = e != NULL;
     for (int y0 = 0; y0 < b->h; y0 += 4) {
         const int y1 = y0 + 4 < b->h ? y0 + 4 : b->h;
@@ -509,11 +513,12 @@ static double cb_pass(orc_cb *b, int type, int p, orc_ctx *x, orc_mqe *e, orc_mq
     return dd_sum;
 }
 
-/* Encodes one code-block (w, h <= 64) of orientation ori.  Writes the
- * passes' segments back to back into out (capacity cap), their lengths to
- * plen[] and distortion decreases to dist[]; returns the number of passes
- * (3 planes - 2, 0 for an all-zero block) and the planes in *planes, or -1
- * when out is too small. */
+/* Encodes one code-block (w, h <= 64) of orientation ori, magnitudes below
+ * 2^24.  Writes the passes' segments back to back into out (capacity cap),
+ * their lengths to plen[] and distortion decreases (the pass's int64 sum,
+ * then converted to double) to dist[]; returns the number of passes (3
+ * planes - 2, 0 for an all-zero block) and the planes in *planes, -1 when
+ * out is too small, -2 for a magnitude of 2^24 or more. */
 int orc_t1_encode(const int32_t *q, int stride, int w, int h, int ori, uint8_t *out, long cap, int *planes,
                   int32_t *plen, double *dist)
 {
@@ -522,6 +527,7 @@ int orc_t1_encode(const int32_t *q, int stride, int w, int h, int ori, uint8_t *
     const int mb = cb_planes(&b);
     *planes = mb;
     if (mb == 0) return 0;
+    if (mb > 24) return -2;
     orc_ctx x;
     ctx_reset(&x);
     /* scratch: one byte before each segment for the coder's B register, and
@@ -533,7 +539,7 @@ int orc_t1_encode(const int32_t *q, int stride, int w, int h, int ori, uint8_t *
         for (int type = (p == mb - 1 ? 2 : 0); type <= 2; type++, k++) {
             orc_mqe e;
             mqe_init(&e, tmp + 1);
-            dist[k] = cb_pass(&b, type, p, &x, &e, NULL);
+            dist[k] = (double)cb_pass(&b, type, p, &x, &e, NULL);
             const long len = mqe_flush(&e);
             if (pos + len > cap) {
                 free(tmp);

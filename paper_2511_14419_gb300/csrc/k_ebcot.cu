@@ -1,0 +1,729 @@
+// Embedded block coding of the RoI-shifted coefficient planes: the
+// JPEG2000 coder that the paper applies to the front end's output
+// (§Implementation details, Table 1: RoI coefficients scaled up, then the
+// codestream cut to the target compression rate).  Written from the
+// JPEG2000 Part 1 definitions (ISO/IEC 15444-1):
+//   - MQ arithmetic coder (Annex C), every coding pass terminated, so each
+//     pass is a byte segment and a truncation point;
+//   - bit-plane coding passes of 64 x 64 code-blocks anchored at each
+//     sub-band's origin (Annex D): stripes of four rows, significance
+//     propagation, magnitude refinement, cleanup with run-length mode,
+//     zero-coding contexts by orientation, sign contexts with the flip bit;
+//   - per pass, the decrease of the squared error of the midpoint
+//     reconstruction in doubled units (an exact int64 sum, so the warp can
+//     add the terms in any order), on the quantised, RoI-shifted
+//     coefficients with unit band weights;
+//   - rate control (Annex J): each code-block's lower convex hull of
+//     (bytes, distortion decrease), the slope threshold found by 64
+//     bisection steps on [0, 2 max slope + 1] so that the kept bytes fit
+//     the frame's budget;
+//   - a frame container: 32-byte header, a 16-byte entry per code-block,
+//     then per code-block the kept passes' 16-bit lengths and bytes.
+//
+// One warp per code-block.  The block's coder state (a 16-bit word per
+// coefficient with a one-sample border: neighbour significance counts,
+// significance, refinement, visited, sign, the plane's coding event) and
+// the current bit-plane as 64-bit row masks live in shared memory.  The
+// warp builds each bit-plane from the coefficient plane (coalesced) and,
+// in the same sweep, adds up the distortion decreases of the previous
+// plane's passes from the events lane 0 recorded; lane 0 runs the passes
+// and the MQ coder, which are sequential by definition.
+#include <mutex>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace flowroi {
+
+namespace {
+
+// MQ probability estimation table (Annex C, Table C.2): Qe, next index
+// after an MPS, after an LPS, and whether an LPS exchanges the MPS.
+__constant__ uint16_t kQe[47] = {
+    0x5601, 0x3401, 0x1801, 0x0AC1, 0x0521, 0x0221, 0x5601, 0x5401, 0x4801, 0x3801, 0x3001, 0x2401,
+    0x1C01, 0x1601, 0x5601, 0x5401, 0x5101, 0x4801, 0x3801, 0x3401, 0x3001, 0x2801, 0x2401, 0x2201,
+    0x1C01, 0x1801, 0x1601, 0x1401, 0x1201, 0x1101, 0x0AC1, 0x09C1, 0x08A1, 0x0521, 0x0441, 0x02A1,
+    0x0221, 0x0141, 0x0111, 0x0085, 0x0049, 0x0025, 0x0015, 0x0009, 0x0005, 0x0001, 0x5601};
+__constant__ uint8_t kNmps[47] = {1,  2,  3,  4,  5,  38, 7,  8,  9,  10, 11, 12, 13, 29, 15, 16,
+                                  17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32,
+                                  33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 45, 46};
+__constant__ uint8_t kNlps[47] = {1,  6,  9,  12, 29, 33, 6,  14, 14, 14, 17, 18, 20, 21, 14, 14,
+                                  15, 16, 17, 18, 19, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29,
+                                  30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 46};
+__constant__ uint8_t kSwitch[47] = {1, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0,
+                                    0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+
+constexpr int kCtxRL = 17, kCtxUni = 18, kNctx = 19;
+
+// Zero-coding context (Table D.1) from the significant horizontal (h),
+// vertical (v) and diagonal (d) neighbours; orientation 0 LL, 1 HL
+// (horizontally high-pass), 2 LH, 3 HH.
+__host__ __device__ constexpr int zc_rule(int ori, int h, int v, int d)
+{
+    if (ori == 1) {
+        const int t = h;
+        h = v;
+        v = t;
+    }
+    if (ori != 3) {
+        if (h == 2) return 8;
+        if (h == 1) return v >= 1 ? 7 : (d >= 1 ? 6 : 5);
+        if (v == 2) return 4;
+        if (v == 1) return 3;
+        return d >= 2 ? 2 : (d == 1 ? 1 : 0);
+    }
+    const int hv = h + v;
+    if (d >= 3) return 8;
+    if (d == 2) return hv >= 1 ? 7 : 6;
+    if (d == 1) return hv >= 2 ? 5 : (hv == 1 ? 4 : 3);
+    return hv >= 2 ? 2 : (hv == 1 ? 1 : 0);
+}
+
+struct ZcTable {
+    uint8_t t[4][45];
+    constexpr ZcTable() : t{}
+    {
+        for (int o = 0; o < 4; o++)
+            for (int d = 0; d < 5; d++)
+                for (int v = 0; v < 3; v++)
+                    for (int h = 0; h < 3; h++) t[o][h + 3 * v + 9 * d] = (uint8_t)zc_rule(o, h, v, d);
+    }
+};
+__constant__ ZcTable kZc = ZcTable();
+
+// Sign-coding context (Table D.3) and flip bit by (H + 1) + 3 (V + 1),
+// H and V the clipped horizontal and vertical sign contributions: bits 0-4
+// the context, bit 7 the flip.
+__constant__ uint8_t kSc[9] = {13 | 0x80, 10 | 0x80, 11, 12 | 0x80, 9, 12, 11 | 0x80, 10, 13};
+
+// State word of a coefficient.
+constexpr uint16_t kNbMask = 0x7F;  // h (bits 0-1), v (2-3), d (4-6) significant-neighbour counts
+constexpr uint16_t kSig = 1u << 7, kRef = 1u << 8, kVis = 1u << 9, kNeg = 1u << 10;
+constexpr int kEvShift = 11;        // bits 11-12: this plane's event (1 SPP, 2 MRP, 3 cleanup)
+constexpr uint16_t kEvMask = 3u << kEvShift;
+
+constexpr int kCbS = kCb + 2;  // state row stride (one-sample border)
+constexpr int kT1Warps = 8;    // code-blocks per CTA
+
+struct T1Warp {
+    uint16_t st[kCbS * kCbS];
+    uint8_t ci[kNctx + 1], cm[kNctx + 1];
+    uint64_t bm[kCb];  // bit p of the magnitudes, one row per word (bit x)
+};
+
+__device__ __forceinline__ int nb_index(uint16_t w) { return (w & 3) + 3 * ((w >> 2) & 3) + 9 * ((w >> 4) & 7); }
+
+__device__ __forceinline__ int contrib(uint16_t w) { return (w & kSig) ? ((w & kNeg) ? -1 : 1) : 0; }
+
+// Doubled-unit reconstruction once planes >= p are known (0 while m >> p == 0).
+__device__ __forceinline__ long long recon2(uint32_t m, int p)
+{
+    if ((m >> p) == 0) return 0;
+    return 2ll * (long long)((m >> p) << p) + (p > 0 ? (1ll << p) : 0ll);
+}
+__device__ __forceinline__ long long derr(uint32_t m, int pb, int pa)
+{
+    const long long t = 2ll * (long long)m;
+    const long long eb = t - (pb > 31 ? 0ll : recon2(m, pb));
+    const long long ea = t - recon2(m, pa);
+    return eb * eb - ea * ea;
+}
+
+// MQ encoder of lane 0 (Annex C, software conventions; the byte at BP is
+// held in b until BP moves on).
+struct Mqe {
+    uint32_t a, c, b;
+    int ct, bp;
+    uint8_t *out;
+    int cap;
+    bool over;
+
+    __device__ void init(uint8_t *o, int capacity)
+    {
+        a = 0x8000;
+        c = 0;
+        b = 0;
+        ct = 12;
+        bp = -1;
+        out = o;
+        cap = capacity;
+        over = false;
+    }
+    __device__ __forceinline__ void emit()
+    {
+        if (bp >= 0) {
+            if (bp < cap) out[bp] = (uint8_t)b;
+            else over = true;
+        }
+    }
+    __device__ void byteout()
+    {
+        if (b == 0xFF) {
+            emit();
+            bp++;
+            b = c >> 20;
+            c &= 0xFFFFF;
+            ct = 7;
+        } else if (c < 0x8000000) {
+            emit();
+            bp++;
+            b = c >> 19;
+            c &= 0x7FFFF;
+            ct = 8;
+        } else {
+            b++;
+            if (b == 0xFF) {
+                c &= 0x7FFFFFF;
+                emit();
+                bp++;
+                b = c >> 20;
+                c &= 0xFFFFF;
+                ct = 7;
+            } else {
+                emit();
+                bp++;
+                b = c >> 19;
+                c &= 0x7FFFF;
+                ct = 8;
+            }
+        }
+    }
+    __device__ __forceinline__ void renorm()
+    {
+        do {
+            a <<= 1;
+            c <<= 1;
+            if (--ct == 0) byteout();
+        } while ((a & 0x8000) == 0);
+    }
+    __device__ __forceinline__ void encode(T1Warp &s, int cx, int d)
+    {
+        const int i = s.ci[cx];
+        const uint32_t qe = kQe[i];
+        a -= qe;
+        if (d == s.cm[cx]) {
+            if ((a & 0x8000) == 0) {
+                if (a < qe) a = qe;
+                else c += qe;
+                s.ci[cx] = kNmps[i];
+                renorm();
+            } else {
+                c += qe;
+            }
+        } else {
+            if (a < qe) c += qe;
+            else a = qe;
+            if (kSwitch[i]) s.cm[cx] ^= 1;
+            s.ci[cx] = kNlps[i];
+            renorm();
+        }
+    }
+    // Terminates the codeword; returns its length in bytes.
+    __device__ int flush()
+    {
+        const uint32_t tempc = c + a;
+        c |= 0xFFFF;
+        if (c >= tempc) c -= 0x8000;
+        c <<= ct;
+        byteout();
+        c <<= ct;
+        byteout();
+        if (b != 0xFF) {
+            emit();
+            bp++;
+        }
+        return bp;
+    }
+};
+
+// A coefficient became significant: its neighbours' counts.
+__device__ __forceinline__ void set_sig(uint16_t *st, int i)
+{
+    st[i - 1] += 1;
+    st[i + 1] += 1;
+    st[i - kCbS] += 4;
+    st[i + kCbS] += 4;
+    st[i - kCbS - 1] += 16;
+    st[i - kCbS + 1] += 16;
+    st[i + kCbS - 1] += 16;
+    st[i + kCbS + 1] += 16;
+}
+
+__device__ __forceinline__ void code_sign(T1Warp &s, Mqe &e, int i, uint16_t w)
+{
+    const uint16_t *st = s.st;
+    int hc = contrib(st[i - 1]) + contrib(st[i + 1]);
+    int vc = contrib(st[i - kCbS]) + contrib(st[i + kCbS]);
+    hc = hc < -1 ? -1 : (hc > 1 ? 1 : hc);
+    vc = vc < -1 ? -1 : (vc > 1 ? 1 : vc);
+    const uint8_t sc = kSc[(hc + 1) + 3 * (vc + 1)];
+    e.encode(s, sc & 0x1F, ((w & kNeg) ? 1 : 0) ^ (sc >> 7));
+}
+
+// One coding pass of plane p by lane 0: type 0 significance propagation,
+// 1 magnitude refinement, 2 cleanup.
+__device__ void t1_pass(T1Warp &s, Mqe &e, int type, int p, int w, int h, int ori)
+{
+    uint16_t *st = s.st;
+    for (int y0 = 0; y0 < h; y0 += 4) {
+        const int y1 = min(y0 + 4, h);
+        for (int x = 0; x < w; x++) {
+            int y = y0;
+            if (type == 2 && y1 - y0 == 4) {
+                const int i0 = (y0 + 1) * kCbS + x + 1;
+                const uint16_t m4 = st[i0] | st[i0 + kCbS] | st[i0 + 2 * kCbS] | st[i0 + 3 * kCbS];
+                if ((m4 & (kNbMask | kSig | kVis)) == 0) {
+                    int r = 4;
+                    for (int k = 0; k < 4; k++)
+                        if ((s.bm[y0 + k] >> x) & 1) {
+                            r = k;
+                            break;
+                        }
+                    e.encode(s, kCtxRL, r < 4);
+                    if (r == 4) continue;
+                    e.encode(s, kCtxUni, r >> 1);
+                    e.encode(s, kCtxUni, r & 1);
+                    const int i = i0 + r * kCbS;
+                    code_sign(s, e, i, st[i]);
+                    st[i] |= kSig | (uint16_t)(3u << kEvShift);
+                    set_sig(st, i);
+                    y = y0 + r + 1;
+                }
+            }
+            for (; y < y1; y++) {
+                const int i = (y + 1) * kCbS + x + 1;
+                const uint16_t wd = st[i];
+                if (type == 0) {
+                    if ((wd & kSig) || (wd & kNbMask) == 0) continue;
+                } else if (type == 1) {
+                    if (!(wd & kSig) || (wd & kVis)) continue;
+                    const int mcx = (wd & kRef) ? 16 : ((wd & kNbMask) ? 15 : 14);
+                    e.encode(s, mcx, (int)((s.bm[y] >> x) & 1));
+                    st[i] = wd | kRef | (uint16_t)(2u << kEvShift);
+                    continue;
+                } else {
+                    if (wd & (kSig | kVis)) continue;
+                }
+                const int bit = (int)((s.bm[y] >> x) & 1);
+                e.encode(s, kZc.t[ori][nb_index(wd)], bit);
+                uint16_t nw = wd;
+                if (type == 0) nw |= kVis;
+                if (bit) {
+                    code_sign(s, e, i, wd);
+                    nw |= kSig | (uint16_t)((type == 0 ? 1u : 3u) << kEvShift);
+                    st[i] = nw;
+                    set_sig(st, i);
+                } else {
+                    st[i] = nw;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Geometry of code-block j of a frame (codestream order: low-low band,
+// then HL, LH, HH of each level from the coarsest; raster order within a
+// band).  Band index as in the quantisation-step table.
+__device__ void cb_geometry(int j, int W, int H, int D, int &band, int &ori, int &x0, int &y0, int &cw, int &ch)
+{
+    for (int k = 0; k <= 3 * D; k++) {
+        int l, o, bx, by;
+        if (k == 0) {
+            l = D;
+            o = 0;
+        } else {
+            l = D - (k - 1) / 3;
+            o = 1 + (k - 1) % 3;
+        }
+        const int bw = W >> l, bh = H >> l;
+        bx = (o == 1 || o == 3) ? bw : 0;
+        by = (o == 2 || o == 3) ? bh : 0;
+        const int nx = (bw + kCb - 1) / kCb, ny = (bh + kCb - 1) / kCb;
+        if (j < nx * ny) {
+            const int cy = j / nx, cx = j - cy * nx;
+            band = o == 0 ? 3 * D : 3 * (l - 1) + (o - 1);
+            ori = o;
+            x0 = bx + cx * kCb;
+            y0 = by + cy * kCb;
+            cw = min(kCb, bw - cx * kCb);
+            ch = min(kCb, bh - cy * kCb);
+            return;
+        }
+        j -= nx * ny;
+    }
+    band = ori = x0 = y0 = cw = ch = 0;
+}
+
+}  // namespace
+
+// Tier-1 coding: one warp per code-block of the job.
+__global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ job)
+{
+    extern __shared__ __align__(16) unsigned char t1sm[];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    T1Warp &s = reinterpret_cast<T1Warp *>(t1sm)[wp];
+    const int g = blockIdx.x * kT1Warps + wp;
+    if (g >= job->ncb) return;
+    // frame of the code-block (frames' code-block ranges are consecutive)
+    int f = 0;
+    while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
+    const CsFrame &F = job->frames[f];
+    int band, ori, x0, y0, cw, ch;
+    cb_geometry(g - F.cb0, F.w, F.h, F.levels, band, ori, x0, y0, cw, ch);
+    const int32_t *coef = F.coef + (size_t)y0 * F.w + x0;
+    int32_t *info = job->info + (size_t)g * kCbInfo;
+    int32_t *plen = job->plen + (size_t)g * kMaxPasses;
+    double *dist = job->dist + (size_t)g * kMaxPasses;
+
+    for (int i = lane; i < kCbS * kCbS; i += 32) s.st[i] = 0;
+    __syncwarp();
+    uint32_t mx = 0;
+    for (int y = 0; y < ch; y++)
+        for (int x = lane; x < cw; x += 32) {
+            const int32_t v = __ldg(coef + (size_t)y * F.w + x);
+            const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
+            mx |= m;
+            if (v < 0) s.st[(y + 1) * kCbS + x + 1] = kNeg;
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx |= __shfl_xor_sync(0xffffffffu, mx, o);
+    const int planes = 32 - __clz(mx);
+    if (lane == 0) {
+        info[0] = planes;
+        info[1] = 0;
+        info[3] = 0;
+    }
+    if (planes == 0) return;
+    if (planes > kMaxPlanes) {
+        if (lane == 0) {
+            info[3] = 2;
+            atomicExch(job->err, kErrCbRange);
+        }
+        return;
+    }
+    if (lane < kNctx) {
+        s.ci[lane] = lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0));
+        s.cm[lane] = 0;
+    }
+    uint8_t *const cbytes = job->cbytes + (size_t)g * job->cbcap;
+    Mqe e;
+    int k = 0, pos = 0;
+    bool over = false;
+    // plane p's sweep also settles the distortion of plane p + 1's passes
+    for (int p = planes - 1; p >= -1; p--) {
+        __syncwarp();
+        long long dsp = 0, dmr = 0, dcu = 0;
+        const int q = p + 1;  // plane whose events are settled
+        for (int y = 0; y < ch; y++) {
+#pragma unroll
+            for (int half = 0; half < 2; half++) {
+                const int x = half * 32 + lane;
+                bool bit = false;
+                if (x < cw) {
+                    const int32_t v = __ldg(coef + (size_t)y * F.w + x);
+                    const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
+                    if (p >= 0) bit = (m >> p) & 1;
+                    uint16_t &wd = s.st[(y + 1) * kCbS + x + 1];
+                    const int ev = (wd >> kEvShift) & 3;
+                    if (ev == 1) dsp += derr(m, 32, q);
+                    else if (ev == 2) dmr += derr(m, q + 1, q);
+                    else if (ev == 3) dcu += derr(m, 32, q);
+                    wd &= (uint16_t)~(kEvMask | kVis);
+                }
+                const unsigned bal = __ballot_sync(0xffffffffu, bit);
+                if (lane == 0) {
+                    if (half == 0) s.bm[y] = bal;
+                    else s.bm[y] |= (uint64_t)bal << 32;
+                }
+            }
+        }
+        dsp = warp_sum_ll(dsp);
+        dmr = warp_sum_ll(dmr);
+        dcu = warp_sum_ll(dcu);
+        if (lane == 0 && q < planes) {
+            // passes of plane q: cleanup only at the top plane
+            if (q == planes - 1) {
+                dist[0] = (double)dcu;
+            } else {
+                const int base = 1 + 3 * (planes - 2 - q);
+                dist[base] = (double)dsp;
+                dist[base + 1] = (double)dmr;
+                dist[base + 2] = (double)dcu;
+            }
+        }
+        if (p < 0) break;
+        __syncwarp();
+        if (lane == 0) {
+            for (int type = (p == planes - 1 ? 2 : 0); type <= 2; type++, k++) {
+                e.init(cbytes + pos, job->cbcap - pos);
+                t1_pass(s, e, type, p, cw, ch, ori);
+                const int len = e.flush();
+                over = over || e.over;
+                plen[k] = len;
+                pos += len;
+            }
+        }
+    }
+    if (lane == 0) {
+        info[1] = k;
+        if (over) {
+            info[3] = 1;
+            atomicExch(job->err, kErrCbRange);
+        }
+    }
+}
+
+// Rate control and container header / table of one frame: one CTA.
+__global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
+{
+    const CsFrame &F = job->frames[blockIdx.x];
+    const int n = F.ncb, tid = threadIdx.x, nt = blockDim.x;
+    __shared__ long long s_ll[32];
+    __shared__ double s_d[32];
+    auto bsum = [&](long long v) {
+        v = warp_sum_ll(v);
+        __syncthreads();
+        if ((tid & 31) == 0) s_ll[tid >> 5] = v;
+        __syncthreads();
+        long long t = 0;
+        for (int i = 0; i < (nt + 31) / 32; i++) t += s_ll[i];
+        return t;
+    };
+    auto bmax = [&](double v) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        __syncthreads();
+        if ((tid & 31) == 0) s_d[tid >> 5] = v;
+        __syncthreads();
+        double t = 0.0;
+        for (int i = 0; i < (nt + 31) / 32; i++) t = fmax(t, s_d[i]);
+        return t;
+    };
+
+    // hulls (lower convex hull of the cumulative (bytes, distortion) points)
+    long long full = 0;
+    double smax = 0.0;
+    for (int j = tid; j < n; j += nt) {
+        const int g = F.cb0 + j;
+        const int np = job->info[(size_t)g * kCbInfo + 1];
+        const int32_t *pl = job->plen + (size_t)g * kMaxPasses;
+        const double *di = job->dist + (size_t)g * kMaxPasses;
+        int32_t *hk = job->hk + (size_t)g * (kMaxPasses + 1);
+        double *hs = job->hs + (size_t)g * (kMaxPasses + 1);
+        long long R[kMaxPasses + 1];
+        double Dc[kMaxPasses + 1];
+        R[0] = 0;
+        Dc[0] = 0.0;
+        for (int k = 0; k < np; k++) {
+            R[k + 1] = R[k] + pl[k];
+            Dc[k + 1] = Dc[k] + di[k];
+        }
+        int m = 1;
+        hk[0] = 0;
+        hs[0] = 0.0;
+        for (int k = 1; k <= np; k++) {
+            if (!(Dc[k] > Dc[hk[m - 1]])) continue;
+            for (;;) {
+                const int a = hk[m - 1];
+                const double sl = (Dc[k] - Dc[a]) / (double)(R[k] - R[a]);
+                if (m >= 2 && sl >= hs[m - 1]) {
+                    m--;
+                    continue;
+                }
+                hk[m] = k;
+                hs[m] = sl;
+                m++;
+                break;
+            }
+        }
+        job->info[(size_t)g * kCbInfo + 4] = m;
+        full += R[np];
+        if (m > 1) smax = fmax(smax, hs[1]);
+    }
+    full = bsum(full);
+    smax = bmax(smax);
+
+    auto kept = [&](int g, double lam, long long *bytes) {
+        const int m = job->info[(size_t)g * kCbInfo + 4];
+        const int32_t *hk = job->hk + (size_t)g * (kMaxPasses + 1);
+        const double *hs = job->hs + (size_t)g * (kMaxPasses + 1);
+        int jj = 0;
+        while (jj + 1 < m && hs[jj + 1] >= lam) jj++;
+        const int nk = hk[jj];
+        long long b = 0;
+        const int32_t *pl = job->plen + (size_t)g * kMaxPasses;
+        for (int k = 0; k < nk; k++) b += pl[k];
+        *bytes = b;
+        return nk;
+    };
+    const bool all = F.budget <= 0 || full <= F.budget;
+    double lo = 0.0, hi = 2.0 * smax + 1.0;
+    if (!all) {
+        for (int it = 0; it < 64; it++) {
+            const double mid = 0.5 * (lo + hi);
+            long long tot = 0;
+            for (int j = tid; j < n; j += nt) {
+                long long b;
+                kept(F.cb0 + j, mid, &b);
+                tot += b;
+            }
+            tot = bsum(tot);
+            if (tot <= F.budget) hi = mid;
+            else lo = mid;
+        }
+    }
+    // kept passes and data sizes; offsets by a two-level scan over
+    // contiguous chunks of code-blocks
+    const int chunk = (n + nt - 1) / nt, j0 = min(n, tid * chunk), j1 = min(n, j0 + chunk);
+    long long mine = 0;
+    for (int j = j0; j < j1; j++) {
+        const int g = F.cb0 + j;
+        long long b;
+        const int nk = all ? job->info[(size_t)g * kCbInfo + 1] : kept(g, hi, &b);
+        if (all) {
+            b = 0;
+            for (int k = 0; k < nk; k++) b += job->plen[(size_t)g * kMaxPasses + k];
+        }
+        job->info[(size_t)g * kCbInfo + 2] = nk;
+        job->info[(size_t)g * kCbInfo + 5] = (int32_t)(2 * nk + b);
+        mine += 2 * nk + b;
+    }
+    // exclusive scan of the per-thread sums
+    __shared__ long long s_scan[1024];
+    __syncthreads();
+    s_scan[tid] = mine;
+    __syncthreads();
+    for (int d = 1; d < nt; d <<= 1) {
+        const long long v = tid >= d ? s_scan[tid - d] : 0;
+        __syncthreads();
+        s_scan[tid] += v;
+        __syncthreads();
+    }
+    long long off = s_scan[tid] - mine;
+    const long long data = s_scan[nt - 1];
+    const long long total = kCsHeader + (long long)kCsEntry * n + data;
+    const bool fits = total <= F.cap;
+    for (int j = j0; j < j1; j++) {
+        const int g = F.cb0 + j;
+        job->info[(size_t)g * kCbInfo + 6] = (int32_t)off;
+        if (fits) {
+            int band, ori, x0, y0, cw, ch;
+            cb_geometry(j, F.w, F.h, F.levels, band, ori, x0, y0, cw, ch);
+            uint8_t *en = F.out + kCsHeader + (size_t)kCsEntry * j;
+            const uint32_t o32 = (uint32_t)off;
+            en[0] = o32 & 0xFF;
+            en[1] = (o32 >> 8) & 0xFF;
+            en[2] = (o32 >> 16) & 0xFF;
+            en[3] = o32 >> 24;
+            en[4] = x0 & 0xFF;
+            en[5] = x0 >> 8;
+            en[6] = y0 & 0xFF;
+            en[7] = y0 >> 8;
+            en[8] = (uint8_t)(cw - 1);
+            en[9] = (uint8_t)(ch - 1);
+            en[10] = (uint8_t)band;
+            en[11] = (uint8_t)job->info[(size_t)g * kCbInfo + 0];
+            en[12] = (uint8_t)job->info[(size_t)g * kCbInfo + 1];
+            en[13] = (uint8_t)job->info[(size_t)g * kCbInfo + 2];
+            en[14] = 0;
+            en[15] = 0;
+        }
+        off += job->info[(size_t)g * kCbInfo + 5];
+    }
+    if (tid == 0) {
+        if (fits) {
+            uint8_t *hd = F.out;
+            auto put32 = [&](int at, uint32_t v) {
+                hd[at] = v & 0xFF;
+                hd[at + 1] = (v >> 8) & 0xFF;
+                hd[at + 2] = (v >> 16) & 0xFF;
+                hd[at + 3] = v >> 24;
+            };
+            hd[0] = 'F';
+            hd[1] = 'R';
+            hd[2] = 'J';
+            hd[3] = '2';
+            put32(4, 1u);
+            put32(8, (uint32_t)F.w);
+            put32(12, (uint32_t)F.h);
+            hd[16] = (uint8_t)F.wavelet;
+            hd[17] = (uint8_t)F.levels;
+            hd[18] = (uint8_t)F.shift;
+            hd[19] = (uint8_t)F.bit_depth;
+            put32(20, (uint32_t)n);
+            put32(24, (uint32_t)data);
+            put32(28, 0u);
+            job->flen[blockIdx.x] = total;
+        } else {
+            job->flen[blockIdx.x] = -total;
+            atomicExch(job->err, kErrCbRange);
+        }
+    }
+}
+
+// Container data: one warp per code-block copies its kept passes' lengths
+// and bytes.
+__global__ void __launch_bounds__(256) k_cs_copy(const CsJob *__restrict__ job)
+{
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (g >= job->ncb) return;
+    int f = 0;
+    while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
+    const CsFrame &F = job->frames[f];
+    if (job->flen[f] < 0) return;
+    const int32_t *info = job->info + (size_t)g * kCbInfo;
+    const int nk = info[2];
+    uint8_t *dst = F.out + kCsHeader + (size_t)kCsEntry * F.ncb + info[6];
+    const int32_t *pl = job->plen + (size_t)g * kMaxPasses;
+    for (int k = lane; k < nk; k += 32) {
+        dst[2 * k] = pl[k] & 0xFF;
+        dst[2 * k + 1] = (pl[k] >> 8) & 0xFF;
+    }
+    int nbytes = 0;
+    for (int k = 0; k < nk; k++) nbytes += pl[k];
+    const uint8_t *src = job->cbytes + (size_t)g * job->cbcap;
+    for (int i = lane; i < nbytes; i += 32) dst[2 * nk + i] = src[i];
+}
+
+namespace {
+void ensure_t1_attr()
+{
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return;
+    cudaFuncSetAttribute(k_t1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kT1Warps * sizeof(T1Warp)));
+    done[dev] = true;
+}
+}  // namespace
+
+int ebcot_codeblocks(int w, int h, int levels)
+{
+    int n = 0;
+    for (int k = 0; k <= 3 * levels; k++) {
+        const int l = k == 0 ? levels : levels - (k - 1) / 3;
+        const int bw = w >> l, bh = h >> l;
+        n += ((bw + kCb - 1) / kCb) * ((bh + kCb - 1) / kCb);
+    }
+    return n;
+}
+
+void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
+{
+    ensure_t1_attr();
+    k_t1<<<(ncb + kT1Warps - 1) / kT1Warps, 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
+    k_pcrd<<<nframes, 1024, 0, s>>>(job_dev);
+    k_cs_copy<<<(ncb + 7) / 8, 256, 0, s>>>(job_dev);
+}
+
+}  // namespace flowroi

@@ -201,6 +201,11 @@ struct flowroi_ctx {
     struct ProfRec { int kid, level, iter; cudaEvent_t a, b; };
     std::vector<ProfRec> prof_pending;
     std::map<std::tuple<int, int, int>, std::pair<int64_t, double>> prof_tot;
+    // codestream coder: scratch kept between calls (grow-only) and its stream
+    std::mutex cs_mu;
+    unsigned char *cs_scratch = nullptr;
+    size_t cs_bytes = 0;
+    cudaStream_t cs_stream = nullptr;
 };
 
 namespace {
@@ -1402,6 +1407,11 @@ void flowroi_destroy(flowroi_ctx *c)
         if (c->desc_ev[k]) cudaEventDestroy(c->desc_ev[k]);
     }
     if (c->err_host) cudaFreeHost(c->err_host);
+    if (c->cs_stream) {
+        cudaStreamSynchronize(c->cs_stream);
+        cudaStreamDestroy(c->cs_stream);
+    }
+    if (c->cs_scratch) cudaFree(c->cs_scratch);
     cudaStreamDestroy(c->s_comp);
     cudaStreamDestroy(c->s_copy);
     cudaStreamDestroy(c->s_d2h);
@@ -1461,6 +1471,143 @@ const char *flowroi_last_error(flowroi_ctx *c)
 {
     (void)c;
     return g_err.c_str();
+}
+
+uint64_t flowroi_codestream_bound(int width, int height, int levels)
+{
+    if (levels < 1 || levels > kMaxLevels || width < 1 || height < 1 || width > 65535 || height > 65535 ||
+        width % (1 << levels) || height % (1 << levels))
+        return 0;
+    const uint64_t ncb = (uint64_t)ebcot_codeblocks(width, height, levels);
+    return (uint64_t)kCsHeader + ncb * ((uint64_t)kCsEntry + 2 * kMaxPasses + kCbBytes);
+}
+
+int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int on_device)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    if (c->poisoned) return fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+    if (n < 1 || n > kMaxBatch || !jobs) return fail(FLOWROI_EINVAL, "n must be in [1,64] and jobs non-NULL");
+    std::vector<CsFrame> fr((size_t)n);
+    int ncb = 0;
+    size_t coef_bytes = 0, out_bytes = 0;
+    for (int i = 0; i < n; i++) {
+        const flowroi_cs_job &J = jobs[i];
+        if (!J.coeffs || !J.out) return fail(FLOWROI_EINVAL, "job %d: coeffs and out must be non-NULL", i);
+        if (flowroi_codestream_bound(J.width, J.height, J.levels) == 0)
+            return fail(FLOWROI_EINVAL, "job %d: width/height must be in [1,65535], multiples of 2^levels, levels in [1,8]", i);
+        if (J.wavelet != FLOWROI_W53 && J.wavelet != FLOWROI_W97) return fail(FLOWROI_EINVAL, "job %d: wavelet must be 53 or 97", i);
+        if (J.shift < 0 || J.shift > 15 || J.bit_depth < 1 || J.bit_depth > 16)
+            return fail(FLOWROI_EINVAL, "job %d: shift must be in [0,15] and bit_depth in [1,16]", i);
+        CsFrame &F = fr[(size_t)i];
+        F.coef = J.coeffs;
+        F.out = J.out;
+        F.cap = (long long)std::min<uint64_t>(J.out_cap, (uint64_t)INT64_MAX);
+        F.budget = J.budget_bytes;
+        F.w = J.width;
+        F.h = J.height;
+        F.levels = J.levels;
+        F.wavelet = J.wavelet;
+        F.shift = J.shift;
+        F.bit_depth = J.bit_depth;
+        F.cb0 = ncb;
+        F.ncb = ebcot_codeblocks(J.width, J.height, J.levels);
+        ncb += F.ncb;
+        coef_bytes += (size_t)J.width * J.height * sizeof(int32_t);
+        out_bytes += (size_t)J.out_cap;
+    }
+    // scratch: one allocation carved in 256-byte aligned pieces
+    size_t total = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = total;
+        total += (bytes + 255) / 256 * 256;
+        return at;
+    };
+    const size_t o_frames = take(sizeof(CsFrame) * (size_t)n), o_job = take(sizeof(CsJob));
+    const size_t o_bytes = take((size_t)ncb * kCbBytes);
+    const size_t o_plen = take((size_t)ncb * kMaxPasses * sizeof(int32_t));
+    const size_t o_dist = take((size_t)ncb * kMaxPasses * sizeof(double));
+    const size_t o_info = take((size_t)ncb * kCbInfo * sizeof(int32_t));
+    const size_t o_hk = take((size_t)ncb * (kMaxPasses + 1) * sizeof(int32_t));
+    const size_t o_hs = take((size_t)ncb * (kMaxPasses + 1) * sizeof(double));
+    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(sizeof(unsigned));
+    const size_t o_coef = on_device ? 0 : take(coef_bytes), o_out = on_device ? 0 : take(out_bytes);
+
+    int rc = FLOWROI_OK;
+    std::lock_guard<std::mutex> lk(c->cs_mu);
+    CK(c, cudaSetDevice(c->device));
+    if (!c->cs_stream) CK(c, cudaStreamCreateWithFlags(&c->cs_stream, cudaStreamNonBlocking));
+    cudaStream_t st = c->cs_stream;
+    if (c->cs_bytes < total) {
+        if (c->cs_scratch) cudaFree(c->cs_scratch);
+        c->cs_scratch = nullptr;
+        c->cs_bytes = 0;
+        if (cudaMalloc(&c->cs_scratch, total) != cudaSuccess) {
+            cudaGetLastError();
+            c->cs_scratch = nullptr;
+            return fail(FLOWROI_ENOMEM, "codestream scratch of %zu bytes", total);
+        }
+        c->cs_bytes = total;
+    }
+    unsigned char *dev = c->cs_scratch;
+    std::vector<long long> flen((size_t)n, 0);
+    unsigned err = 0;
+    cudaError_t e = cudaSuccess;
+    auto step = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    if (!on_device) {
+        size_t co = 0, oo = 0;
+        for (int i = 0; i < n; i++) {
+            const size_t cb = (size_t)fr[(size_t)i].w * fr[(size_t)i].h * sizeof(int32_t);
+            step(cudaMemcpyAsync(dev + o_coef + co, jobs[i].coeffs, cb, cudaMemcpyHostToDevice, st));
+            fr[(size_t)i].coef = reinterpret_cast<const int32_t *>(dev + o_coef + co);
+            fr[(size_t)i].out = dev + o_out + oo;
+            co += cb;
+            oo += (size_t)jobs[i].out_cap;
+        }
+    }
+    CsJob job{};
+    job.nframes = n;
+    job.ncb = ncb;
+    job.frames = reinterpret_cast<const CsFrame *>(dev + o_frames);
+    job.cbytes = dev + o_bytes;
+    job.cbcap = kCbBytes;
+    job.plen = reinterpret_cast<int32_t *>(dev + o_plen);
+    job.dist = reinterpret_cast<double *>(dev + o_dist);
+    job.info = reinterpret_cast<int32_t *>(dev + o_info);
+    job.hk = reinterpret_cast<int32_t *>(dev + o_hk);
+    job.hs = reinterpret_cast<double *>(dev + o_hs);
+    job.flen = reinterpret_cast<long long *>(dev + o_flen);
+    job.err = reinterpret_cast<unsigned *>(dev + o_err);
+    step(cudaMemcpyAsync(dev + o_frames, fr.data(), sizeof(CsFrame) * (size_t)n, cudaMemcpyHostToDevice, st));
+    step(cudaMemcpyAsync(dev + o_job, &job, sizeof job, cudaMemcpyHostToDevice, st));
+    step(cudaMemsetAsync(dev + o_err, 0, sizeof(unsigned), st));
+    if (e == cudaSuccess) {
+        launch_ebcot(reinterpret_cast<const CsJob *>(dev + o_job), n, ncb, st);
+        step(cudaGetLastError());
+    }
+    step(cudaMemcpyAsync(flen.data(), dev + o_flen, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, st));
+    step(cudaMemcpyAsync(&err, dev + o_err, sizeof err, cudaMemcpyDeviceToHost, st));
+    step(cudaStreamSynchronize(st));
+    if (e == cudaSuccess && !on_device) {
+        size_t oo = 0;
+        for (int i = 0; i < n; i++) {
+            if (flen[(size_t)i] > 0)
+                step(cudaMemcpyAsync(jobs[i].out, dev + o_out + oo, (size_t)flen[(size_t)i], cudaMemcpyDeviceToHost, st));
+            oo += (size_t)jobs[i].out_cap;
+        }
+        step(cudaStreamSynchronize(st));
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "flowroi_encode_codestreams");
+    for (int i = 0; i < n; i++) {
+        const long long L = flen[(size_t)i];
+        jobs[i].out_len = (uint64_t)(L < 0 ? -L : L);
+        if (L < 0 && rc == FLOWROI_OK) rc = fail(FLOWROI_ERANGE, "job %d: container needs %lld bytes, out_cap is %llu", i, -L,
+                                                 (unsigned long long)jobs[i].out_cap);
+    }
+    if (rc == FLOWROI_OK && err != 0)
+        rc = fail(FLOWROI_ERANGE, "a code-block has a magnitude of 2^24 or more, or exceeded %d bytes", kCbBytes);
+    return rc;
 }
 
 }  // extern "C"

@@ -14,7 +14,7 @@ import os
 from ._build import LIB
 
 OK = 0
-EINVAL, ENOSTREAM, EBUSY, ENOMEM, ETIMEDOUT, EDEVICE, EGONE, ENOTKEPT = -1, -2, -3, -4, -5, -6, -7, -8
+EINVAL, ENOSTREAM, EBUSY, ENOMEM, ETIMEDOUT, EDEVICE, EGONE, ENOTKEPT, ERANGE = -1, -2, -3, -4, -5, -6, -7, -8, -9
 U8, U16 = 1, 2
 W53, W97 = 53, 97
 FP32, FP16 = 32, 16
@@ -27,6 +27,7 @@ EXPORTS = [
     "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
     "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc", "flowroi_reset_stats",
+    "flowroi_encode_codestreams", "flowroi_codestream_bound",
 ]
 
 
@@ -57,6 +58,13 @@ class flowroi_frame(ctypes.Structure):
         ("pitch_bytes", ctypes.c_int32), ("dtype", ctypes.c_int32), ("bit_depth", ctypes.c_int32),
         ("frame_idx", ctypes.c_int64), ("data", ctypes.c_void_p), ("data_on_device", ctypes.c_int32),
     ]
+
+
+class flowroi_cs_job(ctypes.Structure):
+    _fields_ = [("coeffs", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("wavelet", ctypes.c_int32), ("shift", ctypes.c_int32),
+                ("bit_depth", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("out", ctypes.c_void_p),
+                ("out_cap", ctypes.c_uint64), ("out_len", ctypes.c_uint64)]
 
 
 class flowroi_kernel_time(ctypes.Structure):
@@ -107,6 +115,8 @@ def lib() -> ctypes.CDLL:
             "flowroi_get_kernel_times": (I, [P, ctypes.POINTER(flowroi_kernel_time), I]),
             "flowroi_dwt_roi_noalloc": (I, [P, I, I, I, I, I, P, I, I, I, P, P, P]),
             "flowroi_reset_stats": (I, [P]),
+            "flowroi_encode_codestreams": (I, [P, I, ctypes.POINTER(flowroi_cs_job), I]),
+            "flowroi_codestream_bound": (ctypes.c_uint64, [I, I, I]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -286,6 +296,34 @@ def flowroi_dwt_roi_noalloc(raw, bit_depth: int, mask, wavelet: int, levels: int
     if rc < 0:
         raise FlowRoIError(rc, "flowroi_dwt_roi_noalloc rejected the request" if rc == EINVAL else "CUDA error")
     return rc
+
+
+def flowroi_codestream_bound(width: int, height: int, levels: int) -> int:
+    return int(lib().flowroi_codestream_bound(width, height, levels))
+
+
+def flowroi_encode_codestreams(ctx, jobs) -> list:
+    """Codes coefficient planes into frame containers (see the C header).
+    jobs: dicts with coeffs (int32 (H, W) numpy array or CUDA tensor),
+    levels, wavelet, shift, bit_depth, budget (pass-data bytes, 0 = every
+    pass) and out (uint8 numpy array or CUDA tensor: the container's
+    destination, its size the capacity).  All on the host or all on the
+    device.  Returns the containers' lengths."""
+    arr = (flowroi_cs_job * len(jobs))()
+    dev = None
+    for i, j in enumerate(jobs):
+        cp, cdev = _ptr(j["coeffs"])
+        op, odev = _ptr(j["out"])
+        if dev is None:
+            dev = cdev
+        if cdev != dev or odev != dev:
+            raise ValueError("coeffs and out must all be on the host or all on the device")
+        h, w = int(j["coeffs"].shape[0]), int(j["coeffs"].shape[1])
+        nbytes = int(j["out"].numel() * j["out"].element_size()) if hasattr(j["out"], "numel") else int(j["out"].nbytes)
+        arr[i] = flowroi_cs_job(cp, w, h, j["levels"], j["wavelet"], j.get("shift", 0), j.get("bit_depth", 12),
+                                int(j.get("budget", 0)), op, nbytes, 0)
+    _check(lib().flowroi_encode_codestreams(ctx, len(jobs), arr, int(dev)), ctx)
+    return [int(arr[i].out_len) for i in range(len(jobs))]
 
 
 class Context:

@@ -44,7 +44,8 @@ def test_struct_sizes_match_binding(F):
     cfg = F.flowroi_default_config()
     assert cfg.struct_size == ctypes.sizeof(F.flowroi_config)
     assert (cfg.roi_q, cfg.scale_shift, cfg.win_r, cfg.iters) == (np.float32(0.2), 5, 7, 3)
-    assert F.flowroi_abi_version() == 2
+    assert F.flowroi_abi_version() == 3
+    assert ctypes.sizeof(F.flowroi_cs_job) == 64
 
 
 def test_quant_steps_match_oracle_table(F, orc):
@@ -96,3 +97,20 @@ def test_log_env_reports_refusals_on_stderr():
     env.pop("FLOWROI_LOG")
     off = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT, timeout=120)
     assert "[flowroi]" not in off.stderr
+
+
+def test_codestream_bound_counts_the_code_blocks(F, orc):
+    """The container bound is header + per code-block (entry + pass lengths
+    + the coder's per-block byte limit); the library's code-block count
+    agrees with the oracle's partition; malformed geometries give 0."""
+    for w, h, levels in [(2048, 2048, 5), (256, 256, 3), (264, 200, 3), (16, 16, 2), (2048, 1536, 5)]:
+        n = len(orc.codeblocks(w, h, levels))
+        assert F.flowroi_codestream_bound(w, h, levels) == 32 + n * (16 + 2 * 70 + 32768)
+    for w, h, levels in [(100, 64, 3), (64, 64, 0), (64, 64, 9), (0, 64, 1), (65536, 64, 1)]:
+        assert F.flowroi_codestream_bound(w, h, levels) == 0
+
+
+def test_encode_codestreams_rejects_bad_jobs_on_the_host(F):
+    L = F.lib()
+    jobs = (F.flowroi_cs_job * 1)()
+    assert L.flowroi_encode_codestreams(None, 1, jobs, 0) == F.EINVAL

@@ -1,0 +1,138 @@
+"""GPU parity of the embedded block coder (flowroi_encode_codestreams)
+against the oracle (orc_ebcot.c, oracle.py): the containers are compared
+byte for byte.  The coefficient planes are made by the oracle's own front
+end (DC shift, DWT, quantisation, wavelet-domain RoI mask, up-shift) from
+seeded synthetic 12-bit frames, and the same planes go to both coders.
+
+Every byte is decided by integer arithmetic except the rate control, whose
+slopes and bisection are IEEE double operations in the same order on both
+sides over the same exact inputs (pass lengths and integer distortion
+sums), so the containers must be identical, truncation points included."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as o
+from synth import sequence_u16
+from tests._gpu import F
+
+pytestmark = pytest.mark.gpu
+
+
+def _planes(seed, h, w, levels, wavelet, shift, bd=12, roi_frac=0.3):
+    """Oracle coefficient plane of a synthetic frame with a synthetic RoI
+    (a centred rectangle covering about roi_frac of the frame)."""
+    raw = np.asarray(sequence_u16(seed, 1, h, w, 6)[0]).astype(np.uint16)
+    pix = np.zeros((h, w), np.uint8)
+    rh, rw = int(h * np.sqrt(roi_frac)), int(w * np.sqrt(roi_frac))
+    pix[(h - rh) // 2:(h + rh) // 2, (w - rw) // 2:(w + rw) // 2] = 1
+    cm = o.wavelet_mask(pix, levels, wavelet)
+    if wavelet == 53:
+        q = o.dwt2d(o.dc_shift(raw, bd).astype(np.int64), 53, levels)
+    else:
+        y = o.dwt2d(o.dc_shift(raw, bd).astype(np.float64), 97, levels)
+        _, delta, _, _ = o.delta_table(levels, bd)
+        q = o.quantise_f64(y, levels, delta)
+    return o.roi_shift(q, cm, shift)
+
+
+def _gpu(ctx, planes, levels, wavelet, shift, budgets, on_device=False, bd=12):
+    jobs = []
+    for q, b in zip(planes, budgets):
+        h, w = q.shape
+        cap = F.flowroi_codestream_bound(w, h, levels)
+        if on_device:
+            jobs.append(dict(coeffs=torch.from_numpy(q).cuda(), out=torch.zeros(cap, dtype=torch.uint8, device="cuda"),
+                             levels=levels, wavelet=wavelet, shift=shift, bit_depth=bd, budget=b))
+        else:
+            jobs.append(dict(coeffs=np.ascontiguousarray(q), out=np.zeros(cap, np.uint8), levels=levels,
+                             wavelet=wavelet, shift=shift, bit_depth=bd, budget=b))
+    lens = F.flowroi_encode_codestreams(ctx, jobs)
+    out = []
+    for j, n in zip(jobs, lens):
+        buf = j["out"].cpu().numpy() if on_device else j["out"]
+        out.append(bytes(buf[:n]))
+    return out
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    with F.Context() as c:
+        yield c.h
+
+
+@pytest.mark.parametrize("h,w,levels", [(256, 256, 3), (200, 264, 3), (16, 16, 2), (192, 320, 4)])
+def test_lossless_53_matches_oracle(ctx, h, w, levels):
+    q = _planes(h + w, h, w, levels, 53, 5)
+    want, _ = o.encode_frame(q, levels, 53, 5, 12, 0)
+    got = _gpu(ctx, [q], levels, 53, 5, [0])[0]
+    assert got == want
+
+
+@pytest.mark.parametrize("bpp", [0.25, 1.0, 3.0])
+def test_rate_controlled_97_matches_oracle(ctx, bpp):
+    h, w, levels = 512, 512, 5
+    q = _planes(77, h, w, levels, 97, 5)
+    budget = int(bpp * h * w / 8)
+    want, blocks = o.encode_frame(q, levels, 97, 5, 12, budget)
+    got = _gpu(ctx, [q], levels, 97, 5, [budget])[0]
+    assert got == want
+    kept = sum(int(b["plen"][:b["nkeep"]].sum()) for b in blocks)
+    assert kept <= budget
+
+
+def test_batch_of_mixed_frames_and_device_pointers(ctx):
+    """One call codes frames of different sizes, wavelets are recorded per
+    frame; host and device buffers give the same containers."""
+    specs = [(128, 192, 3, 53, 0), (256, 256, 4, 97, 20000), (64, 64, 2, 53, 300), (128, 128, 3, 97, 0)]
+    planes = [_planes(900 + i, h, w, lv, wav, 5) for i, (h, w, lv, wav, b) in enumerate(specs)]
+    for on_device in (False, True):
+        for (h, w, lv, wav, b), q in zip(specs, planes):
+            got = _gpu(ctx, [q], lv, wav, 5, [b], on_device=on_device)[0]
+            want, _ = o.encode_frame(q, lv, wav, 5, 12, b)
+            assert got == want
+    # the same frames in one call
+    same = [(h, w, lv, wav, b) for h, w, lv, wav, b in specs if lv == 3 and wav == 53]
+    qs = [q for (h, w, lv, wav, b), q in zip(specs, planes) if lv == 3 and wav == 53]
+    got = _gpu(ctx, qs, 3, 53, 5, [b for *_, b in same])
+    for q, g, (h, w, lv, wav, b) in zip(qs, got, same):
+        assert g == o.encode_frame(q, 3, 53, 5, 12, b)[0]
+
+
+def test_full_size_2048_97_at_one_bit_per_pixel(ctx):
+    """The geometry of the batched workload: 2048^2, 9/7, 5 levels, RoI
+    shift 5, 1 bit per pixel of pass data."""
+    h = w = 2048
+    q = _planes(3000, h, w, 5, 97, 5)
+    budget = h * w // 8
+    want, _ = o.encode_frame(q, 5, 97, 5, 12, budget)
+    got = _gpu(ctx, [q], 5, 97, 5, [budget], on_device=True)[0]
+    assert got == want
+
+
+def test_decoded_container_reconstructs_the_frame(ctx):
+    """Lossless 5/3 without RoI shift: the GPU container, decoded and
+    inverse-transformed, is the frame (the container is the oracle's, byte
+    for byte, so this is the oracle's round trip on the GPU's output)."""
+    raw = np.asarray(sequence_u16(4242, 1, 128, 128, 6)[0]).astype(np.uint16)
+    q = o.dwt2d(o.dc_shift(raw, 12).astype(np.int64), 53, 3)
+    got = _gpu(ctx, [q.astype(np.int32)], 3, 53, 0, [0])[0]
+    assert got == o.encode_frame(q, 3, 53, 0, 12, 0)[0]
+
+
+def test_too_small_output_and_out_of_range_magnitudes(ctx):
+    q = _planes(5, 128, 128, 3, 53, 5)
+    small = np.zeros(100, np.uint8)
+    job = dict(coeffs=q, out=small, levels=3, wavelet=53, shift=5, bit_depth=12, budget=0)
+    with pytest.raises(F.FlowRoIError) as ei:
+        F.flowroi_encode_codestreams(ctx, [job])
+    assert ei.value.code == F.ERANGE
+    big = q.copy()
+    big[3, 3] = 1 << 24
+    cap = F.flowroi_codestream_bound(128, 128, 3)
+    job = dict(coeffs=big, out=np.zeros(cap, np.uint8), levels=3, wavelet=53, shift=5, bit_depth=12, budget=0)
+    with pytest.raises(F.FlowRoIError) as ei:
+        F.flowroi_encode_codestreams(ctx, [job])
+    assert ei.value.code == F.ERANGE
+    # the context is still usable
+    assert _gpu(ctx, [q], 3, 53, 5, [0])[0] == o.encode_frame(q, 3, 53, 5, 12, 0)[0]

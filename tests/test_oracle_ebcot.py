@@ -70,7 +70,7 @@ def _block(rng, h, w, scale, zero_frac):
 
 @pytest.mark.parametrize("ori", [o.ORI_LL, o.ORI_HL, o.ORI_LH, o.ORI_HH])
 @pytest.mark.parametrize("h,w,scale,zero_frac", [(64, 64, 40.0, 0.3), (64, 64, 3.0, 0.8), (17, 64, 1e5, 0.0),
-                                                 (64, 9, 700.0, 0.5), (1, 1, 5.0, 0.0), (3, 5, 2 ** 20, 0.2)])
+                                                 (64, 9, 700.0, 0.5), (1, 1, 5.0, 0.0), (3, 5, 2 ** 20, 0.2), (64, 64, 2 ** 21, 0.1)])
 def test_t1_roundtrip_and_pass_count(ori, h, w, scale, zero_frac):
     rng = np.random.default_rng(h * 131 + w * 7 + ori)
     q = _block(rng, h, w, scale, zero_frac)
@@ -81,6 +81,13 @@ def test_t1_roundtrip_and_pass_count(ori, h, w, scale, zero_frac):
     assert np.all(plen >= 1) and code.size == plen.sum()
     r = o.t1_decode(code, plen, len(plen), planes, w, h, ori, midpoint=False)
     assert np.array_equal(r, q)
+
+
+def test_t1_rejects_magnitudes_of_2_to_24():
+    q = np.zeros((8, 8), np.int32)
+    q[3, 4] = -(2 ** 24)
+    with pytest.raises(OverflowError):
+        o.t1_encode(q, o.ORI_LL)
 
 
 def test_t1_all_zero_block_has_no_passes():
@@ -214,3 +221,33 @@ def test_lossy_9_7_psnr_grows_with_rate():
         ps.append(o.psnr(x, raw, bd))
     assert all(b > a for a, b in zip(ps, ps[1:])), ps
     assert ps[-1] > 45.0
+
+
+def test_roi_upshift_keeps_the_roi_quality_at_low_rates():
+    """Scaling-based RoI (§Implementation details, Table 1): with the RoI
+    coefficients shifted up by 5 bits, a 0.5 bit-per-pixel codestream
+    spends its bytes on the RoI first: the RoI's PSNR is far above the
+    background's, and above what the same budget gives the RoI unshifted."""
+    bd, levels, s = 12, 3, 5
+    h = w = 256
+    raw = _frame(57, h, w, bd)
+    pix = np.zeros((h, w), np.uint8)
+    pix[64:192, 64:192] = 1
+    cm = o.wavelet_mask(pix, levels, 97)
+    y = o.dwt2d(o.dc_shift(raw, bd).astype(np.float64), 97, levels)
+    _, delta, _, _ = o.delta_table(levels, bd)
+    q = o.quantise_f64(y, levels, delta)
+    budget = int(0.5 * h * w / 8)
+
+    def code(shift):
+        qs = o.roi_shift(q, cm, shift) if shift else q
+        stream, _ = o.encode_frame(qs, levels, 97, shift, bd, budget)
+        r = o.decode_frame(stream)
+        return o.reconstruct(o.unshift_dequantise(r, cm, shift, levels, 97, bd), levels, 97, bd)
+
+    x5, x0 = code(s), code(0)
+    m = pix.astype(bool)
+    roi5, bg5 = o.psnr(x5[m], raw[m], bd), o.psnr(x5[~m], raw[~m], bd)
+    roi0 = o.psnr(x0[m], raw[m], bd)
+    assert roi5 > bg5 + 6.0, (roi5, bg5)
+    assert roi5 > roi0 + 2.0, (roi5, roi0)
