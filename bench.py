@@ -62,6 +62,9 @@ WORKLOADS = {
     # rate control, container)
     "ebcot_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                           dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
+    # four streams of it (small case for profiler captures of the coder)
+    "ebcot_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                         dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
     # four streams of the batched workload's frames (small case for profiler captures)
     "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000),

@@ -102,11 +102,14 @@ constexpr uint16_t kSig = 1u << 7, kRef = 1u << 8, kVis = 1u << 9, kNeg = 1u << 
 constexpr int kEvShift = 11;        // bits 11-12: this plane's event (1 SPP, 2 MRP, 3 cleanup)
 constexpr uint16_t kEvMask = 3u << kEvShift;
 
-constexpr int kCbS = kCb + 2;  // state row stride (one-sample border)
-constexpr int kT1Warps = 8;    // code-blocks per CTA
+// Column-major state words: (x, y) at (x + 1) * kColS + y + kRowOff, so a
+// stripe's four rows of a column are one aligned 64-bit word; x and y run
+// over the block plus a one-sample border.
+constexpr int kColS = 72, kRowOff = 4;
+constexpr int kT1Warps = 7;  // code-blocks per CTA (three CTAs per SM by shared memory)
 
 struct T1Warp {
-    uint16_t st[kCbS * kCbS];
+    uint16_t st[(kCb + 2) * kColS];
     uint8_t ci[kNctx + 1], cm[kNctx + 1];
     uint64_t bm[kCb];  // bit p of the magnitudes, one row per word (bit x)
 };
@@ -236,24 +239,27 @@ struct Mqe {
     }
 };
 
-// A coefficient became significant: its neighbours' counts.
+__device__ __forceinline__ int sti(int x, int y) { return (x + 1) * kColS + y + kRowOff; }
+
+// A coefficient became significant: its neighbours' counts (horizontal
+// neighbours are a column apart, vertical ones adjacent words).
 __device__ __forceinline__ void set_sig(uint16_t *st, int i)
 {
-    st[i - 1] += 1;
-    st[i + 1] += 1;
-    st[i - kCbS] += 4;
-    st[i + kCbS] += 4;
-    st[i - kCbS - 1] += 16;
-    st[i - kCbS + 1] += 16;
-    st[i + kCbS - 1] += 16;
-    st[i + kCbS + 1] += 16;
+    st[i - kColS] += 1;
+    st[i + kColS] += 1;
+    st[i - 1] += 4;
+    st[i + 1] += 4;
+    st[i - kColS - 1] += 16;
+    st[i - kColS + 1] += 16;
+    st[i + kColS - 1] += 16;
+    st[i + kColS + 1] += 16;
 }
 
 __device__ __forceinline__ void code_sign(T1Warp &s, Mqe &e, int i, uint16_t w)
 {
     const uint16_t *st = s.st;
-    int hc = contrib(st[i - 1]) + contrib(st[i + 1]);
-    int vc = contrib(st[i - kCbS]) + contrib(st[i + kCbS]);
+    int hc = contrib(st[i - kColS]) + contrib(st[i + kColS]);
+    int vc = contrib(st[i - 1]) + contrib(st[i + 1]);
     hc = hc < -1 ? -1 : (hc > 1 ? 1 : hc);
     vc = vc < -1 ? -1 : (vc > 1 ? 1 : vc);
     const uint8_t sc = kSc[(hc + 1) + 3 * (vc + 1)];
@@ -261,37 +267,53 @@ __device__ __forceinline__ void code_sign(T1Warp &s, Mqe &e, int i, uint16_t w)
 }
 
 // One coding pass of plane p by lane 0: type 0 significance propagation,
-// 1 magnitude refinement, 2 cleanup.
+// 1 magnitude refinement, 2 cleanup.  A stripe column's four state words
+// are read as one 64-bit word first: a column with no position to code in
+// this pass is skipped on it (no position of it can become one, since only
+// coding a position of the column changes the column's membership), and it
+// decides the run-length mode of the cleanup.
 __device__ void t1_pass(T1Warp &s, Mqe &e, int type, int p, int w, int h, int ori)
 {
+    (void)p;
     uint16_t *st = s.st;
+    constexpr uint64_t kRep = 0x0001000100010001ull;
     for (int y0 = 0; y0 < h; y0 += 4) {
-        const int y1 = min(y0 + 4, h);
+        const int nr = min(4, h - y0);
+        // 16-bit lanes of the stripe's rows that exist
+        const uint64_t rows = nr >= 4 ? ~0ull : ((1ull << (16 * nr)) - 1);
         for (int x = 0; x < w; x++) {
-            int y = y0;
-            if (type == 2 && y1 - y0 == 4) {
-                const int i0 = (y0 + 1) * kCbS + x + 1;
-                const uint16_t m4 = st[i0] | st[i0 + kCbS] | st[i0 + 2 * kCbS] | st[i0 + 3 * kCbS];
-                if ((m4 & (kNbMask | kSig | kVis)) == 0) {
-                    int r = 4;
-                    for (int k = 0; k < 4; k++)
-                        if ((s.bm[y0 + k] >> x) & 1) {
-                            r = k;
-                            break;
-                        }
-                    e.encode(s, kCtxRL, r < 4);
-                    if (r == 4) continue;
-                    e.encode(s, kCtxUni, r >> 1);
-                    e.encode(s, kCtxUni, r & 1);
-                    const int i = i0 + r * kCbS;
-                    code_sign(s, e, i, st[i]);
-                    st[i] |= kSig | (uint16_t)(3u << kEvShift);
-                    set_sig(st, i);
-                    y = y0 + r + 1;
-                }
+            const int i0 = sti(x, y0);
+            const uint64_t q4 = *reinterpret_cast<const uint64_t *>(st + i0) & rows;
+            const uint64_t sig4 = q4 & (kRep * kSig), vis4 = q4 & (kRep * kVis), nb4 = q4 & (kRep * kNbMask);
+            if (type == 0) {
+                // a lane with neighbours and without significance
+                const uint64_t has_nb = (nb4 + kRep * 0x7F) & (kRep * 0x80);  // bit 7 (= kSig) where nb != 0
+                if ((has_nb & ~sig4) == 0) continue;
+            } else if (type == 1) {
+                if ((sig4 & ~(vis4 >> 2)) == 0) continue;  // kVis = kSig << 2
+            } else if (((sig4 | (vis4 >> 2)) ^ (kRep * kSig & rows)) == 0) {
+                continue;  // every row significant or visited
             }
-            for (; y < y1; y++) {
-                const int i = (y + 1) * kCbS + x + 1;
+            int y = y0;
+            if (type == 2 && nr == 4 && (q4 & (kRep * (kNbMask | kSig | kVis))) == 0) {
+                // run-length mode: four uncoded, insignificant samples with
+                // all-zero neighbourhoods
+                int r = 4;
+#pragma unroll
+                for (int k = 3; k >= 0; k--)
+                    if ((s.bm[y0 + k] >> x) & 1) r = k;
+                e.encode(s, kCtxRL, r < 4);
+                if (r == 4) continue;
+                e.encode(s, kCtxUni, r >> 1);
+                e.encode(s, kCtxUni, r & 1);
+                const int i = i0 + r;
+                code_sign(s, e, i, st[i]);
+                st[i] |= kSig | (uint16_t)(3u << kEvShift);
+                set_sig(st, i);
+                y = y0 + r + 1;
+            }
+            for (; y < y0 + nr; y++) {
+                const int i = i0 + (y - y0);
                 const uint16_t wd = st[i];
                 if (type == 0) {
                     if ((wd & kSig) || (wd & kNbMask) == 0) continue;
@@ -382,7 +404,7 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
     int32_t *plen = job->plen + (size_t)g * kMaxPasses;
     double *dist = job->dist + (size_t)g * kMaxPasses;
 
-    for (int i = lane; i < kCbS * kCbS; i += 32) s.st[i] = 0;
+    for (int i = lane; i < (kCb + 2) * kColS; i += 32) s.st[i] = 0;
     __syncwarp();
     uint32_t mx = 0;
     for (int y = 0; y < ch; y++)
@@ -390,7 +412,7 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
             const int32_t v = __ldg(coef + (size_t)y * F.w + x);
             const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
             mx |= m;
-            if (v < 0) s.st[(y + 1) * kCbS + x + 1] = kNeg;
+            if (v < 0) s.st[sti(x, y)] = kNeg;
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx |= __shfl_xor_sync(0xffffffffu, mx, o);
@@ -430,7 +452,7 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
                     const int32_t v = __ldg(coef + (size_t)y * F.w + x);
                     const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
                     if (p >= 0) bit = (m >> p) & 1;
-                    uint16_t &wd = s.st[(y + 1) * kCbS + x + 1];
+                    uint16_t &wd = s.st[sti(x, y)];
                     const int ev = (wd >> kEvShift) & 3;
                     if (ev == 1) dsp += derr(m, 32, q);
                     else if (ev == 2) dmr += derr(m, q + 1, q);
