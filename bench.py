@@ -478,7 +478,9 @@ def run_serving(F, wl, rate_fps: float, duration_s: float, burst_per_stream: int
 
 def cpu_sample(wl, frames_cpu, budget_s=12.0, crop=512):
     """The oracle (as it stands, single-threaded) on crop pairs of the
-    workload; returns (frames/s scaled to full frames, seconds, crops)."""
+    workload (with the codestream workloads, each crop's coefficients also
+    coded at the workload's rate); returns (frames/s scaled to full
+    frames, seconds, crops)."""
     import numpy as np
 
     from oracle import oracle as O
@@ -490,8 +492,11 @@ def cpu_sample(wl, frames_cpu, budget_s=12.0, crop=512):
         a, b = frames_cpu[s]
         y0 = (k * 389) % (h - crop + 1) // 32 * 32
         x0 = (k * 613) % (w - crop + 1) // 32 * 32
-        O.frame(np.ascontiguousarray(a[y0:y0 + crop, x0:x0 + crop]), np.ascontiguousarray(b[y0:y0 + crop, x0:x0 + crop]),
-                wl["bit_depth"], p)
+        o = O.frame(np.ascontiguousarray(a[y0:y0 + crop, x0:x0 + crop]),
+                    np.ascontiguousarray(b[y0:y0 + crop, x0:x0 + crop]), wl["bit_depth"], p)
+        if "codestream_bpp" in wl:
+            O.encode_frame(o["coeffs"], wl["dwt_levels"], wl["wavelet"], p.scale_shift, wl["bit_depth"],
+                           int(wl["codestream_bpp"] * crop * crop / 8))
         done += 1
         k += 1
         el = time.perf_counter() - t0
@@ -595,6 +600,15 @@ def main():
         torch.cuda.synchronize()
         cr = run_codestream(F, wl, frames, args.steps, args.warmup)
         t_max = max_over_ranks(cr["time_s"], ws, "cpu")
+        cpu = None
+        if rank == 0 and ws == 1 and not args.no_cpu:
+            import numpy as np
+            fc = [(frames[s][0].cpu().numpy().view(np.uint16), frames[s][1].cpu().numpy().view(np.uint16))
+                  for s in range(min(2, wl["streams"]))]
+            fps_cpu, el, nc = cpu_sample(wl, fc)
+            cpu = {"value": fps_cpu, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                   "sample": f"{nc} crops of 512x512 from the workload's first frame pairs, flow to codestream "
+                             f"({el:.1f} s), time scaled to {wl['w']}x{wl['h']} frames by pixel count"}
         if rank == 0:
             print(json.dumps({"metric": "frames/s (flow+mask+DWT+codestream) at 1 GB300", "workload": args.workload,
                               "value": job_throughput(cr["frames"], ws, t_max), "unit": "frames/s", "n_gpus": ws,
@@ -603,7 +617,7 @@ def main():
                               "codestream_ms_per_step": 1e3 * cr["cs_time_s"] / args.steps,
                               "codestream_target_bpp": wl["codestream_bpp"], "codestream_bpp": cr["bpp"],
                               "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
-                              "config": config_of(args.workload, wl)}), flush=True)
+                              "config": config_of(args.workload, wl), "cpu_baseline": cpu}), flush=True)
         return
 
     def barrier():
