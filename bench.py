@@ -345,42 +345,35 @@ def run_e2e(F, wl, frames, steps, warmup):
     return res
 
 
-def run_codestream(F, wl, frames, steps, warmup):
-    """Device-resident pipeline steps, each followed by the coding of its
-    frames' coefficient planes into rate-controlled containers
-    (flowroi_encode_codestreams on device buffers).  Returns the wall time
-    of the timed steps, the time spent in the coder, and the containers'
-    mean size."""
+def run_codestream(F, wl, frames, steps, warmup, profile_steps=3):
+    """Device-resident steps of the stream path with the JPEG2000 coder on
+    (config.codestream_bpp): each batch's frames are coded into
+    rate-controlled containers inside the batch's launches, and every
+    frame's container is fetched (flowroi_get_codestream, device buffers).
+    Returns the wall time of the timed steps, the containers' mean size and
+    the per-kernel times of `profile_steps` further steps."""
     import torch
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
                precision=wl["precision"], max_batch_frames=64, result_ring=8, flags=F.MANUAL,
-               device=torch.cuda.current_device())
+               codestream_bpp=wl["codestream_bpp"], device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     H, W, L = wl["h"], wl["w"], wl["dwt_levels"]
-    budget = int(wl["codestream_bpp"] * H * W / 8)
     cap = F.flowroi_codestream_bound(W, H, L) // 4
-    coef = [torch.empty((H, W), dtype=torch.int32, device="cuda") for _ in range(S)]
     outs = [torch.empty(cap, dtype=torch.uint8, device="cuda") for _ in range(S)]
-    jobs = [dict(coeffs=coef[s], out=outs[s], levels=L, wavelet=wl["wavelet"], shift=5, bit_depth=bd, budget=budget)
-            for s in range(S)]
     res = {}
     with F.Context(**cfg) as ctx:
         t = 0
-        cs_time = 0.0
         lens = []
 
-        def one_step(timed):
-            nonlocal t, cs_time
+        def one_step(keep):
+            nonlocal t
             i = frame_index(t, n)
             submit_all(F, ctx.h, [(s, frames[s][i], t, bd) for s in range(S)])
             F.flowroi_step(ctx.h)
             for s in range(S):
-                F.flowroi_get_coeffs(ctx.h, s, t, coef[s], -1)
-            t0 = time.perf_counter()
-            ls = F.flowroi_encode_codestreams(ctx.h, jobs)
-            if timed:
-                cs_time += time.perf_counter() - t0
-                lens.extend(ls)
+                k = F.flowroi_get_codestream(ctx.h, s, t, outs[s], -1)
+                if keep:
+                    lens.append(k)
             t += 1
 
         for _ in range(warmup + 1):
@@ -391,9 +384,18 @@ def run_codestream(F, wl, frames, steps, warmup):
             one_step(True)
         torch.cuda.synchronize()
         res["time_s"] = time.perf_counter() - t0
+        F.flowroi_flush(ctx.h, -1)
+        F.flowroi_set_profiling(ctx.h, 1)
+        for _ in range(profile_steps):
+            one_step(False)
+        F.flowroi_flush(ctx.h, -1)
+        kt = F.flowroi_get_kernel_times(ctx.h)
+        F.flowroi_set_profiling(ctx.h, 0)
+        launches = F.flowroi_get_stats(ctx.h)["kernel_launches"]
     res["frames"] = steps * S
-    res["cs_time_s"] = cs_time
     res["bpp"] = 8.0 * float(sum(lens)) / (len(lens) * H * W) if lens else None
+    res["kernel_ms"] = {f"{k['name']}" + (f"[{k['level']}]" if k["level"] >= 0 else ""): round(k["total_ms"] / profile_steps, 4)
+                        for k in kt}
     return res
 
 
@@ -614,8 +616,9 @@ def main():
                               "value": job_throughput(cr["frames"], ws, t_max), "unit": "frames/s", "n_gpus": ws,
                               "steps": args.steps, "warmup": args.warmup,
                               "ms_per_step": 1e3 * t_max / args.steps,
-                              "codestream_ms_per_step": 1e3 * cr["cs_time_s"] / args.steps,
+                              "codestream_ms_per_step": cr["kernel_ms"].get("codestream"),
                               "codestream_target_bpp": wl["codestream_bpp"], "codestream_bpp": cr["bpp"],
+                              "kernel_avg_ms": cr["kernel_ms"],
                               "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
                               "config": config_of(args.workload, wl), "cpu_baseline": cpu}), flush=True)
         return

@@ -151,6 +151,13 @@ typedef struct flowroi_config {
      * reg_level, whose padded size must be at most 1024 per side. */
     int32_t register_frames;   /* 0 = off, 1 = on (0) */
     int32_t reg_level;         /* in [1, pyr_levels - 1] (2) */
+    /* JPEG2000 coder in the stream path (§Implementation details, Table 1:
+     * the codestream cut to a target compression rate): when > 0, every
+     * frame's coefficient plane is also coded into a rate-controlled
+     * container (the format of flowroi_encode_codestreams) of this many
+     * bits per pixel of pass data; fetch it with flowroi_get_codestream.
+     * 0 = off. (0) */
+    float codestream_bpp;
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and
@@ -402,6 +409,15 @@ typedef struct {
     uint64_t out_len;
 } flowroi_cs_job;
 FLOWROI_API int flowroi_encode_codestreams(flowroi_ctx *ctx, int n, flowroi_cs_job *jobs, int on_device);
+/* The container of a frame coded in the stream path (config.codestream_bpp
+ * > 0): waits like flowroi_get_coeffs, then copies the container (host or
+ * device out, capacity out_cap) and sets *out_len to its length.  A
+ * container that does not fit out_cap, or a frame whose coefficients the
+ * coder cannot take (a magnitude of 2^24 or more), returns FLOWROI_ERANGE
+ * (with *out_len the length it needs, or 0); FLOWROI_EINVAL when the
+ * coder is off. */
+FLOWROI_API int flowroi_get_codestream(flowroi_ctx *ctx, int64_t stream_id, int64_t frame_idx, uint8_t *out,
+                                       uint64_t out_cap, uint64_t *out_len, int out_on_device, int timeout_ms);
 /* A container capacity that always suffices for a width x height plane of
  * `levels` levels (0 for a malformed geometry). */
 FLOWROI_API uint64_t flowroi_codestream_bound(int width, int height, int levels);

@@ -68,6 +68,41 @@ struct MethodConsts {
     float den_lr;
 };
 
+// Embedded block coding (k_ebcot.cu): one frame of a coder job, with the
+// scratch of its code-blocks, and the job.
+constexpr int kCb = 64;                        // code-block side
+constexpr int kMaxPlanes = 24;                 // magnitudes below 2^24
+constexpr int kMaxPasses = 3 * kMaxPlanes - 2;
+constexpr int kCbInfo = 8;                     // per code-block: planes, passes, kept, status, hull size, data size, data offset
+constexpr int kCsHeader = 32, kCsEntry = 16;   // container header and per-code-block entry bytes
+constexpr unsigned kErrCbRange = 3u;           // error word: a code-block or container exceeded its buffer or range
+constexpr int kCbBytes = 32768;                // pass bytes a code-block may produce
+// device bytes of a code-block's scratch (pass bytes, lengths, distortions, info, hull)
+constexpr size_t kCbScratch = (size_t)kCbBytes + kMaxPasses * (4 + 8) + kCbInfo * 4 + (kMaxPasses + 1) * (4 + 8);
+
+struct CsFrame {
+    const int32_t *coef;  // Mallat plane, row pitch = w
+    uint8_t *out;         // container
+    long long cap;        // container capacity (bytes)
+    long long budget;     // pass-data budget (bytes); <= 0 keeps every pass
+    int w, h, levels, wavelet, shift, bit_depth;
+    int cb0, ncb;         // the frame's code-blocks in the job
+    // per code-block scratch of the frame, [ncb][...]
+    uint8_t *cbytes;      // [kCbBytes] pass bytes
+    int32_t *plen;        // [kMaxPasses]
+    double *dist;         // [kMaxPasses]
+    int32_t *info;        // [kCbInfo]
+    int32_t *hk;          // [kMaxPasses + 1] hull scratch
+    double *hs;           // [kMaxPasses + 1]
+    long long *flen;      // the container's length (negative: it needs that many bytes; -1: a code-block out of range)
+};
+struct CsJob {
+    int nframes, ncb;
+    const CsFrame *frames;  // device array [nframes]
+    int cbcap;              // kCbBytes
+    unsigned *err;          // error word, or null
+};
+
 // One frame of a batch.  Level geometry: lw/lh = level size, lp = pitch in
 // elements.  All planes of the previous frame of the same stream are read
 // through fq_prev / fb_prev.
@@ -112,6 +147,8 @@ struct FrameDesc {
     // predecessor's, and the correlation work plane
     int do_reg, reg_lnx, reg_lny;
     float2 *reg_cur, *reg_prev, *reg_work;
+    int do_cs;                      // the JPEG2000 target's coefficients are coded into a container
+    CsFrame cs;
     int n_adj;                      // per-frame masks ORed into dwt_mask (0: none, dwt_mask is the frame's own)
     const uint8_t *adj[2 * kMaxAdj + 1];
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
@@ -136,6 +173,8 @@ struct BatchDesc {
     int reg_col_off[kMaxBatch + 1];
     int reg_el_off[kMaxBatch + 1];
     FrameDesc f[kMaxBatch];
+    CsJob cs;                       // the batch's coder job over csf (frames with do_cs)
+    CsFrame csf[kMaxBatch];
 };
 
 #ifdef __CUDACC__

@@ -385,25 +385,26 @@ __device__ void cb_geometry(int j, int W, int H, int D, int &band, int &ori, int
 
 }  // namespace
 
-// Tier-1 coding: one warp per code-block of the job.
+// Tier-1 coding: one warp per code-block of the job (grid-stride).
 __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ job)
 {
     extern __shared__ __align__(16) unsigned char t1sm[];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     T1Warp &s = reinterpret_cast<T1Warp *>(t1sm)[wp];
-    const int g = blockIdx.x * kT1Warps + wp;
-    if (g >= job->ncb) return;
+    for (int g = blockIdx.x * kT1Warps + wp; g < job->ncb; g += gridDim.x * kT1Warps) {
     // frame of the code-block (frames' code-block ranges are consecutive)
     int f = 0;
     while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
     const CsFrame &F = job->frames[f];
+    const int jb = g - F.cb0;
     int band, ori, x0, y0, cw, ch;
-    cb_geometry(g - F.cb0, F.w, F.h, F.levels, band, ori, x0, y0, cw, ch);
+    cb_geometry(jb, F.w, F.h, F.levels, band, ori, x0, y0, cw, ch);
     const int32_t *coef = F.coef + (size_t)y0 * F.w + x0;
-    int32_t *info = job->info + (size_t)g * kCbInfo;
-    int32_t *plen = job->plen + (size_t)g * kMaxPasses;
-    double *dist = job->dist + (size_t)g * kMaxPasses;
+    int32_t *info = F.info + (size_t)jb * kCbInfo;
+    int32_t *plen = F.plen + (size_t)jb * kMaxPasses;
+    double *dist = F.dist + (size_t)jb * kMaxPasses;
 
+    __syncwarp();
     for (int i = lane; i < (kCb + 2) * kColS; i += 32) s.st[i] = 0;
     __syncwarp();
     uint32_t mx = 0;
@@ -422,19 +423,19 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
         info[1] = 0;
         info[3] = 0;
     }
-    if (planes == 0) return;
+    if (planes == 0) continue;
     if (planes > kMaxPlanes) {
         if (lane == 0) {
             info[3] = 2;
-            atomicExch(job->err, kErrCbRange);
+            if (job->err) atomicExch(job->err, kErrCbRange);
         }
-        return;
+        continue;
     }
     if (lane < kNctx) {
         s.ci[lane] = lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0));
         s.cm[lane] = 0;
     }
-    uint8_t *const cbytes = job->cbytes + (size_t)g * job->cbcap;
+    uint8_t *const cbytes = F.cbytes + (size_t)jb * job->cbcap;
     Mqe e;
     int k = 0, pos = 0;
     bool over = false;
@@ -497,18 +498,23 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
         info[1] = k;
         if (over) {
             info[3] = 1;
-            atomicExch(job->err, kErrCbRange);
+            if (job->err) atomicExch(job->err, kErrCbRange);
         }
+    }
+    __syncwarp();
     }
 }
 
-// Rate control and container header / table of one frame: one CTA.
+// Rate control and container header / table: one CTA per frame
+// (grid-stride over the job's frames).
 __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
 {
-    const CsFrame &F = job->frames[blockIdx.x];
-    const int n = F.ncb, tid = threadIdx.x, nt = blockDim.x;
     __shared__ long long s_ll[32];
     __shared__ double s_d[32];
+    __shared__ long long s_scan[1024];
+    for (int fi = blockIdx.x; fi < job->nframes; fi += gridDim.x) {
+    const CsFrame &F = job->frames[fi];
+    const int n = F.ncb, tid = threadIdx.x, nt = blockDim.x;
     auto bsum = [&](long long v) {
         v = warp_sum_ll(v);
         __syncthreads();
@@ -530,15 +536,16 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
     };
 
     // hulls (lower convex hull of the cumulative (bytes, distortion) points)
-    long long full = 0;
+    long long full = 0, bad = 0;
     double smax = 0.0;
     for (int j = tid; j < n; j += nt) {
-        const int g = F.cb0 + j;
-        const int np = job->info[(size_t)g * kCbInfo + 1];
-        const int32_t *pl = job->plen + (size_t)g * kMaxPasses;
-        const double *di = job->dist + (size_t)g * kMaxPasses;
-        int32_t *hk = job->hk + (size_t)g * (kMaxPasses + 1);
-        double *hs = job->hs + (size_t)g * (kMaxPasses + 1);
+        const int g = j;
+        const int np = F.info[(size_t)g * kCbInfo + 1];
+        if (F.info[(size_t)g * kCbInfo + 3] != 0) bad = 1;
+        const int32_t *pl = F.plen + (size_t)g * kMaxPasses;
+        const double *di = F.dist + (size_t)g * kMaxPasses;
+        int32_t *hk = F.hk + (size_t)g * (kMaxPasses + 1);
+        double *hs = F.hs + (size_t)g * (kMaxPasses + 1);
         long long R[kMaxPasses + 1];
         double Dc[kMaxPasses + 1];
         R[0] = 0;
@@ -565,22 +572,23 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
                 break;
             }
         }
-        job->info[(size_t)g * kCbInfo + 4] = m;
+        F.info[(size_t)g * kCbInfo + 4] = m;
         full += R[np];
         if (m > 1) smax = fmax(smax, hs[1]);
     }
     full = bsum(full);
     smax = bmax(smax);
+    bad = bsum(bad);
 
     auto kept = [&](int g, double lam, long long *bytes) {
-        const int m = job->info[(size_t)g * kCbInfo + 4];
-        const int32_t *hk = job->hk + (size_t)g * (kMaxPasses + 1);
-        const double *hs = job->hs + (size_t)g * (kMaxPasses + 1);
+        const int m = F.info[(size_t)g * kCbInfo + 4];
+        const int32_t *hk = F.hk + (size_t)g * (kMaxPasses + 1);
+        const double *hs = F.hs + (size_t)g * (kMaxPasses + 1);
         int jj = 0;
         while (jj + 1 < m && hs[jj + 1] >= lam) jj++;
         const int nk = hk[jj];
         long long b = 0;
-        const int32_t *pl = job->plen + (size_t)g * kMaxPasses;
+        const int32_t *pl = F.plen + (size_t)g * kMaxPasses;
         for (int k = 0; k < nk; k++) b += pl[k];
         *bytes = b;
         return nk;
@@ -593,7 +601,7 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
             long long tot = 0;
             for (int j = tid; j < n; j += nt) {
                 long long b;
-                kept(F.cb0 + j, mid, &b);
+                kept(j, mid, &b);
                 tot += b;
             }
             tot = bsum(tot);
@@ -606,19 +614,18 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
     const int chunk = (n + nt - 1) / nt, j0 = min(n, tid * chunk), j1 = min(n, j0 + chunk);
     long long mine = 0;
     for (int j = j0; j < j1; j++) {
-        const int g = F.cb0 + j;
+        const int g = j;
         long long b;
-        const int nk = all ? job->info[(size_t)g * kCbInfo + 1] : kept(g, hi, &b);
+        const int nk = all ? F.info[(size_t)g * kCbInfo + 1] : kept(g, hi, &b);
         if (all) {
             b = 0;
-            for (int k = 0; k < nk; k++) b += job->plen[(size_t)g * kMaxPasses + k];
+            for (int k = 0; k < nk; k++) b += F.plen[(size_t)g * kMaxPasses + k];
         }
-        job->info[(size_t)g * kCbInfo + 2] = nk;
-        job->info[(size_t)g * kCbInfo + 5] = (int32_t)(2 * nk + b);
+        F.info[(size_t)g * kCbInfo + 2] = nk;
+        F.info[(size_t)g * kCbInfo + 5] = (int32_t)(2 * nk + b);
         mine += 2 * nk + b;
     }
     // exclusive scan of the per-thread sums
-    __shared__ long long s_scan[1024];
     __syncthreads();
     s_scan[tid] = mine;
     __syncthreads();
@@ -631,10 +638,10 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
     long long off = s_scan[tid] - mine;
     const long long data = s_scan[nt - 1];
     const long long total = kCsHeader + (long long)kCsEntry * n + data;
-    const bool fits = total <= F.cap;
+    const bool fits = total <= F.cap && bad == 0;
     for (int j = j0; j < j1; j++) {
-        const int g = F.cb0 + j;
-        job->info[(size_t)g * kCbInfo + 6] = (int32_t)off;
+        const int g = j;
+        F.info[(size_t)g * kCbInfo + 6] = (int32_t)off;
         if (fits) {
             int band, ori, x0, y0, cw, ch;
             cb_geometry(j, F.w, F.h, F.levels, band, ori, x0, y0, cw, ch);
@@ -651,13 +658,13 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
             en[8] = (uint8_t)(cw - 1);
             en[9] = (uint8_t)(ch - 1);
             en[10] = (uint8_t)band;
-            en[11] = (uint8_t)job->info[(size_t)g * kCbInfo + 0];
-            en[12] = (uint8_t)job->info[(size_t)g * kCbInfo + 1];
-            en[13] = (uint8_t)job->info[(size_t)g * kCbInfo + 2];
+            en[11] = (uint8_t)F.info[(size_t)g * kCbInfo + 0];
+            en[12] = (uint8_t)F.info[(size_t)g * kCbInfo + 1];
+            en[13] = (uint8_t)F.info[(size_t)g * kCbInfo + 2];
             en[14] = 0;
             en[15] = 0;
         }
-        off += job->info[(size_t)g * kCbInfo + 5];
+        off += F.info[(size_t)g * kCbInfo + 5];
     }
     if (tid == 0) {
         if (fits) {
@@ -682,37 +689,41 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
             put32(20, (uint32_t)n);
             put32(24, (uint32_t)data);
             put32(28, 0u);
-            job->flen[blockIdx.x] = total;
+            *F.flen = total;
         } else {
-            job->flen[blockIdx.x] = -total;
-            atomicExch(job->err, kErrCbRange);
+            // did not fit (the length it needs), or a code-block out of range (-1)
+            *F.flen = bad ? -1 : -total;
+            if (job->err) atomicExch(job->err, kErrCbRange);
         }
+    }
+    __syncthreads();
     }
 }
 
 // Container data: one warp per code-block copies its kept passes' lengths
-// and bytes.
+// and bytes (grid-stride).
 __global__ void __launch_bounds__(256) k_cs_copy(const CsJob *__restrict__ job)
 {
     const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (g >= job->ncb) return;
-    int f = 0;
-    while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
-    const CsFrame &F = job->frames[f];
-    if (job->flen[f] < 0) return;
-    const int32_t *info = job->info + (size_t)g * kCbInfo;
-    const int nk = info[2];
-    uint8_t *dst = F.out + kCsHeader + (size_t)kCsEntry * F.ncb + info[6];
-    const int32_t *pl = job->plen + (size_t)g * kMaxPasses;
-    for (int k = lane; k < nk; k += 32) {
-        dst[2 * k] = pl[k] & 0xFF;
-        dst[2 * k + 1] = (pl[k] >> 8) & 0xFF;
+    for (int g = blockIdx.x * 8 + (threadIdx.x >> 5); g < job->ncb; g += gridDim.x * 8) {
+        int f = 0;
+        while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
+        const CsFrame &F = job->frames[f];
+        if (*F.flen < 0) continue;
+        const int j = g - F.cb0;
+        const int32_t *info = F.info + (size_t)j * kCbInfo;
+        const int nk = info[2];
+        uint8_t *dst = F.out + kCsHeader + (size_t)kCsEntry * F.ncb + info[6];
+        const int32_t *pl = F.plen + (size_t)j * kMaxPasses;
+        for (int k = lane; k < nk; k += 32) {
+            dst[2 * k] = pl[k] & 0xFF;
+            dst[2 * k + 1] = (pl[k] >> 8) & 0xFF;
+        }
+        int nbytes = 0;
+        for (int k = 0; k < nk; k++) nbytes += pl[k];
+        const uint8_t *src = F.cbytes + (size_t)j * job->cbcap;
+        for (int i = lane; i < nbytes; i += 32) dst[2 * nk + i] = src[i];
     }
-    int nbytes = 0;
-    for (int k = 0; k < nk; k++) nbytes += pl[k];
-    const uint8_t *src = job->cbytes + (size_t)g * job->cbcap;
-    for (int i = lane; i < nbytes; i += 32) dst[2 * nk + i] = src[i];
 }
 
 namespace {
@@ -743,9 +754,25 @@ int ebcot_codeblocks(int w, int h, int levels)
 void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
 {
     ensure_t1_attr();
-    k_t1<<<(ncb + kT1Warps - 1) / kT1Warps, 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
-    k_pcrd<<<nframes, 1024, 0, s>>>(job_dev);
-    k_cs_copy<<<(ncb + 7) / 8, 256, 0, s>>>(job_dev);
+    k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
+    k_pcrd<<<std::max(1, nframes), 1024, 0, s>>>(job_dev);
+    k_cs_copy<<<std::max(1, (ncb + 7) / 8), 256, 0, s>>>(job_dev);
+}
+
+void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, cudaStream_t s)
+{
+    ensure_t1_attr();
+    k_t1<<<grid_t1, 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
+    k_pcrd<<<kMaxBatch, 1024, 0, s>>>(job_dev);
+    k_cs_copy<<<grid_copy, 256, 0, s>>>(job_dev);
+}
+
+int occupancy_t1()
+{
+    ensure_t1_attr();
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t1, 32 * kT1Warps, kT1Warps * sizeof(T1Warp));
+    return b;
 }
 
 }  // namespace flowroi

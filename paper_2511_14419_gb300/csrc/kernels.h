@@ -51,38 +51,12 @@ bool morph_radius_supported(int r);
 bool denoise_radius_supported(int r);
 
 // Embedded block coding of coefficient planes into frame containers
-// (k_ebcot.cu).
-constexpr int kCb = 64;                        // code-block side
-constexpr int kMaxPlanes = 24;                 // magnitudes below 2^24
-constexpr int kMaxPasses = 3 * kMaxPlanes - 2;
-constexpr int kCbInfo = 8;                     // per code-block: planes, passes, kept, status, hull size, data size, data offset
-constexpr int kCsHeader = 32, kCsEntry = 16;   // container header and per-code-block entry bytes
-constexpr uint32_t kErrCbRange = 3u;           // error word: a code-block or container exceeded its buffer or range
-constexpr int kCbBytes = 32768;                // pass bytes a code-block may produce
-
-struct CsFrame {
-    const int32_t *coef;  // Mallat plane, row pitch = w
-    uint8_t *out;         // container
-    long long cap;        // container capacity (bytes)
-    long long budget;     // pass-data budget (bytes); <= 0 keeps every pass
-    int w, h, levels, wavelet, shift, bit_depth;
-    int cb0, ncb;         // the frame's code-blocks in the job
-};
-struct CsJob {
-    int nframes, ncb;
-    const CsFrame *frames;  // device array [nframes]
-    uint8_t *cbytes;        // [ncb][cbcap] pass bytes
-    int cbcap;
-    int32_t *plen;          // [ncb][kMaxPasses]
-    double *dist;           // [ncb][kMaxPasses]
-    int32_t *info;          // [ncb][kCbInfo]
-    int32_t *hk;            // [ncb][kMaxPasses + 1] hull scratch
-    double *hs;             // [ncb][kMaxPasses + 1]
-    long long *flen;        // [nframes] container length (negative: did not fit)
-    unsigned *err;          // error word
-};
+// (k_ebcot.cu); CsFrame, CsJob and the coder's constants are in common.cuh.
 int ebcot_codeblocks(int w, int h, int levels);
 void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s);
+// The same with fixed (persistent, grid-stride) grids, for captured graphs.
+void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, cudaStream_t s);
+int occupancy_t1();
 
 // 9/7 quantisation steps (host, double precision); see flowroi_quant_steps.
 int quant_steps(int levels, int bit_depth, double delta_base, float *delta, int *eps, int *mu, double *gain);

@@ -125,6 +125,8 @@ struct Entry {
     float *dbg_thr = nullptr;
     float *dbg_den = nullptr;
     float *dbg_drift = nullptr;
+    uint8_t *cs = nullptr;          // the coder's container (codestream_bpp > 0)
+    long long *cs_len = nullptr;    // its length (device)
 };
 
 struct Stream {
@@ -154,6 +156,10 @@ struct Stream {
     unsigned *red = nullptr;
     void *ll[2] = {};
     uint8_t *llm[2] = {};
+    // JPEG2000 coder (codestream_bpp > 0): code-block scratch, container geometry
+    char *cs_scratch = nullptr;
+    int cs_ncb = 0;
+    long long cs_cap = 0, cs_budget = 0;
 };
 
 struct BatchRec;
@@ -184,6 +190,7 @@ struct flowroi_ctx {
     int graph_launches = 0;
     int desc_next = 0;
     int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0, grid_mrg = 0, grid_reg = 0;
+    int grid_t1 = 0, grid_csc = 0;
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -267,6 +274,8 @@ int validate_config(const flowroi_config *c)
     if (c->denoise != 0 && c->denoise != 1) return fail(FLOWROI_EINVAL, "config.denoise must be 0 or 1");
     if (!denoise_radius_supported(c->den_radius)) return fail(FLOWROI_EINVAL, "config.den_radius must be in [1,3]");
     if (!(c->den_sigma_s > 0.f) || !(c->den_sigma_r > 0.f)) return fail(FLOWROI_EINVAL, "config.den_sigma_s/den_sigma_r must be > 0");
+    if (!(c->codestream_bpp >= 0.f && c->codestream_bpp <= 64.f))
+        return fail(FLOWROI_EINVAL, "config.codestream_bpp must be in [0, 64]");
     return FLOWROI_OK;
 }
 
@@ -379,6 +388,13 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
         s->ll[k] = take((npx / 4) * 4);
         s->llm[k] = reinterpret_cast<uint8_t *>(take(npx / 4));
     }
+    const bool cs_on = c->cfg.codestream_bpp > 0.f;
+    if (cs_on) {
+        s->cs_ncb = ebcot_codeblocks(s->W, s->H, c->cfg.dwt_levels);
+        s->cs_budget = (long long)std::floor((double)c->cfg.codestream_bpp * (double)npx / 8.0);
+        s->cs_cap = kCsHeader + (long long)s->cs_ncb * (kCsEntry + 2 * kMaxPasses) + s->cs_budget;
+        s->cs_scratch = take((size_t)s->cs_ncb * kCbScratch);
+    }
     for (int r = 0; r < R; r++) {
         Entry *e = s->ring[r].get();
         e->raw = take(npx * s->bpp);
@@ -393,6 +409,10 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
             e->dbg_thr = reinterpret_cast<float *>(take(sizeof(float)));
             e->dbg_den = c->cfg.denoise ? reinterpret_cast<float *>(take(npx * 4)) : nullptr;
             e->dbg_drift = c->cfg.register_frames ? reinterpret_cast<float *>(take(2 * sizeof(float))) : nullptr;
+        }
+        if (cs_on) {
+            e->cs = reinterpret_cast<uint8_t *>(take((size_t)s->cs_cap));
+            e->cs_len = reinterpret_cast<long long *>(take(sizeof(long long)));
         }
     }
     return align_up(off, 256);
@@ -479,6 +499,36 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
         F.dwt_mask = d->mask;
         F.dwt_coeffs = d->coeffs;
         F.dwt_yf = d->dbg_yf;
+        if (d->cs) {
+            // the coder takes the coefficients this batch's front end writes
+            F.do_cs = 1;
+            CsFrame &C = F.cs;
+            C.coef = d->coeffs;
+            C.out = d->cs;
+            C.cap = s->cs_cap;
+            C.budget = s->cs_budget;
+            C.w = s->W;
+            C.h = s->H;
+            C.levels = c->cfg.dwt_levels;
+            C.wavelet = c->cfg.wavelet;
+            C.shift = c->cfg.scale_shift;
+            C.bit_depth = s->bit_depth;
+            C.ncb = s->cs_ncb;
+            const size_t n = (size_t)s->cs_ncb;
+            char *b = s->cs_scratch;
+            C.cbytes = reinterpret_cast<uint8_t *>(b);
+            b += n * kCbBytes;
+            C.dist = reinterpret_cast<double *>(b);
+            b += n * kMaxPasses * sizeof(double);
+            C.hs = reinterpret_cast<double *>(b);
+            b += n * (kMaxPasses + 1) * sizeof(double);
+            C.plen = reinterpret_cast<int32_t *>(b);
+            b += n * kMaxPasses * sizeof(int32_t);
+            C.info = reinterpret_cast<int32_t *>(b);
+            b += n * kCbInfo * sizeof(int32_t);
+            C.hk = reinterpret_cast<int32_t *>(b);
+            C.flen = d->cs_len;
+        }
         const int k = c->cfg.adjacent;
         if (k > 0) {
             // own masks of frames d-k .. d+k that exist and have their flow launched
@@ -520,11 +570,24 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
         bd.reg_el_off[i + 1] = bd.reg_el_off[i] + (rnx * rny + register_unit() - 1) / register_unit();
         bd.frm_off[i + 1] = i + 1;
     }
+    // the coder's frames (those whose front end runs), code-blocks numbered in order
+    int m = 0, ncb = 0;
+    for (int i = 0; i < n; i++)
+        if (bd.f[i].do_cs) {
+            bd.csf[m] = bd.f[i].cs;
+            bd.csf[m].cb0 = ncb;
+            ncb += bd.csf[m].ncb;
+            m++;
+        }
+    bd.cs.nframes = m;
+    bd.cs.ncb = ncb;
+    bd.cs.cbcap = kCbBytes;
+    bd.cs.err = nullptr;
 }
 
 const char *const kKernelNames[] = {"frame_init", "expand", "update", "window", "saliency", "select_find", "select_pass",
-                                    "morph", "dwt", "denoise", "components", "merge", "register"};
-enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC, K_MERGE, K_REG };
+                                    "morph", "dwt", "denoise", "components", "merge", "register", "codestream"};
+enum KernelId { K_INIT = 0, K_EXPAND, K_UPDATE, K_WINDOW, K_SAL, K_FIND, K_PASS, K_MORPH, K_DWT, K_DENOISE, K_CC, K_MERGE, K_REG, K_CS };
 
 // Runs one launch, bracketed by an event pair when profiling.
 template <class Fn>
@@ -614,6 +677,11 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
         timed(c, st, prof, K_DWT, l, -1, [&] { launch_dwt(dd, mc, l, g(hd->dwt_off[l - 1][n], c->grid_dwt), st); });
         cnt++;
     }
+    if (c->cfg.codestream_bpp > 0.f) {
+        // tier-1 coding, rate control and containers of the batch's front-end frames
+        timed(c, st, prof, K_CS, -1, -1, [&] { launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_csc, st); });
+        cnt += 3;
+    }
     *nlaunch = cnt;
     return FLOWROI_OK;
 }
@@ -686,10 +754,15 @@ int step_locked(flowroi_ctx *c)
     hd.final_flow_buf = (nflow - 1) & 1;
     for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].s, sel[i].e, sel[i].d, hd.f[i]);
     fill_offsets(c, hd);
+    hd.cs.frames = c->desc_dev[k]->csf;
     for (auto &pk : sel)
         if (pk.e) CK(c, cudaStreamWaitEvent(c->s_comp, pk.e->uploaded, 0));
     const size_t bytes = offsetof(BatchDesc, f) + sizeof(FrameDesc) * sel.size();
     CK(c, cudaMemcpyAsync(c->desc_dev[k], c->desc_host[k], bytes, cudaMemcpyHostToDevice, c->s_comp));
+    if (c->cfg.codestream_bpp > 0.f) {
+        const size_t cs_bytes = offsetof(BatchDesc, csf) - offsetof(BatchDesc, cs) + sizeof(CsFrame) * (size_t)hd.cs.nframes;
+        CK(c, cudaMemcpyAsync(&c->desc_dev[k]->cs, &hd.cs, cs_bytes, cudaMemcpyHostToDevice, c->s_comp));
+    }
     CK(c, cudaEventRecord(c->desc_ev[k], c->s_comp));
     int nl = 0;
     if (c->plain || c->profiling) {
@@ -813,7 +886,7 @@ bool wait_done(flowroi_ctx *c, Entry *e, int timeout_ms)
 }
 
 int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, void *out, int out_on_device,
-               int timeout_ms)
+               int timeout_ms, uint64_t out_cap = 0, uint64_t *out_len = nullptr)
 {
     if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
     if (!out) return fail(FLOWROI_EINVAL, "out is NULL");
@@ -839,6 +912,7 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
         if (which == FLOWROI_I_DENOISED && !c->cfg.denoise) return fail(FLOWROI_EINVAL, "denoising is off (config.denoise)");
         if (which == FLOWROI_I_DRIFT && !c->cfg.register_frames)
             return fail(FLOWROI_EINVAL, "registration is off (config.register_frames)");
+        if (which == -2 && !(c->cfg.codestream_bpp > 0.f)) return fail(FLOWROI_EINVAL, "the coder is off (config.codestream_bpp)");
         e->readers++;
     }
     const bool ok = wait_done(c, e, timeout_ms);
@@ -860,6 +934,27 @@ int get_common(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, 
         case FLOWROI_I_THRESHOLD: src = e->dbg_thr; bytes = 4; break;
         case FLOWROI_I_DENOISED: src = e->dbg_den; bytes = npx * 4; break;
         case FLOWROI_I_DRIFT: src = e->dbg_drift; bytes = 2 * sizeof(float); break;
+        case -2: {
+            // the container: its length first
+            long long L = 0;
+            std::lock_guard<std::mutex> lk(c->d2h_mu);
+            cudaError_t ce = cudaMemcpyAsync(&L, e->cs_len, sizeof L, cudaMemcpyDeviceToHost, c->s_d2h);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->s_d2h);
+            if (ce != cudaSuccess) {
+                rc = cuda_fail(c, ce, "copy out");
+            } else if (L < 0) {
+                if (out_len) *out_len = 0;
+                rc = fail(FLOWROI_ERANGE, "frame %lld: a coefficient magnitude of 2^24 or more, or a code-block over %d bytes",
+                          (long long)frame_idx, kCbBytes);
+            } else {
+                if (out_len) *out_len = (uint64_t)L;
+                if ((uint64_t)L > out_cap) rc = fail(FLOWROI_ERANGE, "container of %lld bytes, out_cap is %llu", L,
+                                                      (unsigned long long)out_cap);
+                src = e->cs;
+                bytes = (size_t)L;
+            }
+            break;
+        }
         default: rc = fail(FLOWROI_EINVAL, "unknown intermediate %d", which); break;
         }
         if (rc == FLOWROI_OK && which >= FLOWROI_I_FLOW && !e->has_prev) {
@@ -973,6 +1068,7 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->adjacent = 0;
     cfg->register_frames = 0;
     cfg->reg_level = 2;
+    cfg->codestream_bpp = 0.f;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -1062,6 +1158,8 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     c->grid_cc = cfg->min_area > 1 ? std::max(1, occupancy_cc()) * c->num_sms : 0;
     c->grid_mrg = 8 * c->num_sms;
     c->grid_reg = cfg->register_frames ? std::max(1, occupancy_register()) * c->num_sms : 0;
+    c->grid_t1 = cfg->codestream_bpp > 0.f ? std::max(1, occupancy_t1()) * c->num_sms : 0;
+    c->grid_csc = 8 * c->num_sms;
     c->grid_frames = kMaxBatch;
     size_t freeb = 0, totalb = 0;
     CK(nullptr, cudaMemGetInfo(&freeb, &totalb));
@@ -1473,6 +1571,12 @@ const char *flowroi_last_error(flowroi_ctx *c)
     return g_err.c_str();
 }
 
+int flowroi_get_codestream(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, uint8_t *out, uint64_t out_cap,
+                           uint64_t *out_len, int out_on_device, int timeout_ms)
+{
+    return get_common(c, stream_id, frame_idx, -2, out, out_on_device, timeout_ms, out_cap, out_len);
+}
+
 uint64_t flowroi_codestream_bound(int width, int height, int levels)
 {
     if (levels < 1 || levels > kMaxLevels || width < 1 || height < 1 || width > 65535 || height > 65535 ||
@@ -1566,18 +1670,22 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
             oo += (size_t)jobs[i].out_cap;
         }
     }
+    for (int i = 0; i < n; i++) {
+        CsFrame &F = fr[(size_t)i];
+        const size_t b0 = (size_t)F.cb0;
+        F.cbytes = dev + o_bytes + b0 * kCbBytes;
+        F.plen = reinterpret_cast<int32_t *>(dev + o_plen) + b0 * kMaxPasses;
+        F.dist = reinterpret_cast<double *>(dev + o_dist) + b0 * kMaxPasses;
+        F.info = reinterpret_cast<int32_t *>(dev + o_info) + b0 * kCbInfo;
+        F.hk = reinterpret_cast<int32_t *>(dev + o_hk) + b0 * (kMaxPasses + 1);
+        F.hs = reinterpret_cast<double *>(dev + o_hs) + b0 * (kMaxPasses + 1);
+        F.flen = reinterpret_cast<long long *>(dev + o_flen) + i;
+    }
     CsJob job{};
     job.nframes = n;
     job.ncb = ncb;
     job.frames = reinterpret_cast<const CsFrame *>(dev + o_frames);
-    job.cbytes = dev + o_bytes;
     job.cbcap = kCbBytes;
-    job.plen = reinterpret_cast<int32_t *>(dev + o_plen);
-    job.dist = reinterpret_cast<double *>(dev + o_dist);
-    job.info = reinterpret_cast<int32_t *>(dev + o_info);
-    job.hk = reinterpret_cast<int32_t *>(dev + o_hk);
-    job.hs = reinterpret_cast<double *>(dev + o_hs);
-    job.flen = reinterpret_cast<long long *>(dev + o_flen);
     job.err = reinterpret_cast<unsigned *>(dev + o_err);
     step(cudaMemcpyAsync(dev + o_frames, fr.data(), sizeof(CsFrame) * (size_t)n, cudaMemcpyHostToDevice, st));
     step(cudaMemcpyAsync(dev + o_job, &job, sizeof job, cudaMemcpyHostToDevice, st));
@@ -1601,9 +1709,12 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     if (e != cudaSuccess) return cuda_fail(c, e, "flowroi_encode_codestreams");
     for (int i = 0; i < n; i++) {
         const long long L = flen[(size_t)i];
-        jobs[i].out_len = (uint64_t)(L < 0 ? -L : L);
-        if (L < 0 && rc == FLOWROI_OK) rc = fail(FLOWROI_ERANGE, "job %d: container needs %lld bytes, out_cap is %llu", i, -L,
-                                                 (unsigned long long)jobs[i].out_cap);
+        jobs[i].out_len = (uint64_t)(L == -1 ? 0 : (L < 0 ? -L : L));
+        if (L == -1 && rc == FLOWROI_OK)
+            rc = fail(FLOWROI_ERANGE, "job %d: a coefficient magnitude of 2^24 or more, or a code-block over %d bytes", i, kCbBytes);
+        else if (L < 0 && rc == FLOWROI_OK)
+            rc = fail(FLOWROI_ERANGE, "job %d: container needs %lld bytes, out_cap is %llu", i, -L,
+                      (unsigned long long)jobs[i].out_cap);
     }
     if (rc == FLOWROI_OK && err != 0)
         rc = fail(FLOWROI_ERANGE, "a code-block has a magnitude of 2^24 or more, or exceeded %d bytes", kCbBytes);

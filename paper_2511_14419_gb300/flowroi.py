@@ -27,7 +27,7 @@ EXPORTS = [
     "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
     "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc", "flowroi_reset_stats",
-    "flowroi_encode_codestreams", "flowroi_codestream_bound",
+    "flowroi_encode_codestreams", "flowroi_codestream_bound", "flowroi_get_codestream",
 ]
 
 
@@ -48,7 +48,7 @@ class flowroi_config(ctypes.Structure):
         ("flags", ctypes.c_uint32), ("device", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_uint64),
         ("denoise", ctypes.c_int32), ("den_radius", ctypes.c_int32), ("den_sigma_s", ctypes.c_float),
         ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32), ("adjacent", ctypes.c_int32),
-        ("register_frames", ctypes.c_int32), ("reg_level", ctypes.c_int32),
+        ("register_frames", ctypes.c_int32), ("reg_level", ctypes.c_int32), ("codestream_bpp", ctypes.c_float),
     ]
 
 
@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
             "flowroi_reset_stats": (I, [P]),
             "flowroi_encode_codestreams": (I, [P, I, ctypes.POINTER(flowroi_cs_job), I]),
             "flowroi_codestream_bound": (ctypes.c_uint64, [I, I, I]),
+            "flowroi_get_codestream": (I, [P, I64, I64, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), I, I]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -296,6 +297,17 @@ def flowroi_dwt_roi_noalloc(raw, bit_depth: int, mask, wavelet: int, levels: int
     if rc < 0:
         raise FlowRoIError(rc, "flowroi_dwt_roi_noalloc rejected the request" if rc == EINVAL else "CUDA error")
     return rc
+
+
+def flowroi_get_codestream(ctx, stream_id: int, frame_idx: int, out, timeout_ms: int = -1) -> int:
+    """Copies a frame's container (config.codestream_bpp > 0) into out (a
+    uint8 numpy array or CUDA tensor; its size is the capacity); returns
+    the container's length."""
+    p, dev = _ptr(out)
+    cap = int(out.numel() * out.element_size()) if hasattr(out, "numel") else int(out.nbytes)
+    n = ctypes.c_uint64(0)
+    _check(lib().flowroi_get_codestream(ctx, stream_id, frame_idx, p, cap, ctypes.byref(n), dev, timeout_ms), ctx)
+    return int(n.value)
 
 
 def flowroi_codestream_bound(width: int, height: int, levels: int) -> int:

@@ -136,3 +136,46 @@ def test_too_small_output_and_out_of_range_magnitudes(ctx):
     assert ei.value.code == F.ERANGE
     # the context is still usable
     assert _gpu(ctx, [q], 3, 53, 5, [0])[0] == o.encode_frame(q, 3, 53, 5, 12, 0)[0]
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_stream_path_codestreams_match_the_coder(plain):
+    """config.codestream_bpp: every frame's container from the stream path
+    (coded in the batch's launches, first frames included) equals the coder
+    applied to that frame's coefficient plane (whose parity with the oracle
+    the tests above establish)."""
+    h, w, S, n = 256, 320, 3, 3
+    flags = F.MANUAL | (F.PLAIN if plain else 0)
+    with F.Context(pyr_levels=3, dwt_levels=3, wavelet=97, codestream_bpp=1.0, flags=flags) as c:
+        seqs = [np.asarray(sequence_u16(700 + s, n, h, w, 8)).astype(np.uint16) for s in range(S)]
+        for t in range(n):
+            for s in range(S):
+                F.flowroi_submit_frame(c.h, s, seqs[s][t], t, 12)
+            F.flowroi_step(c.h)
+        F.flowroi_flush(c.h, 60000)
+        cap = F.flowroi_codestream_bound(w, h, 3)
+        for s in range(S):
+            for t in range(n):
+                coeffs = np.empty((h, w), np.int32)
+                F.flowroi_get_coeffs(c.h, s, t, coeffs, 10000)
+                out = np.zeros(cap, np.uint8)
+                k = F.flowroi_get_codestream(c.h, s, t, out, 10000)
+                want = np.zeros(cap, np.uint8)
+                m = F.flowroi_encode_codestreams(c.h, [dict(coeffs=coeffs, out=want, levels=3, wavelet=97, shift=5,
+                                                            bit_depth=12, budget=h * w // 8)])[0]
+                assert k == m and bytes(out[:k]) == bytes(want[:m]), (s, t)
+                dev = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+                assert F.flowroi_get_codestream(c.h, s, t, dev, 10000) == k
+                assert bytes(dev[:k].cpu().numpy()) == bytes(out[:k])
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_codestream(c.h, 0, 1, np.zeros(64, np.uint8), 10000)
+        assert ei.value.code == F.ERANGE
+
+
+def test_stream_path_codestream_off_is_einval():
+    with F.Context(pyr_levels=2, dwt_levels=2, flags=F.MANUAL) as c:
+        F.flowroi_submit_frame(c.h, 0, np.zeros((64, 64), np.uint16), 0, 12)
+        F.flowroi_flush(c.h, 60000)
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_codestream(c.h, 0, 0, np.zeros(1024, np.uint8), 10000)
+        assert ei.value.code == F.EINVAL
