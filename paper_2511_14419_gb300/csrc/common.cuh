@@ -101,6 +101,7 @@ struct CsJob {
     const CsFrame *frames;  // device array [nframes]
     int cbcap;              // kCbBytes
     unsigned *err;          // error word, or null
+    int *next;              // next code-block to take (zeroed before the coder runs)
 };
 
 // One frame of a batch.  Level geometry: lw/lh = level size, lp = pitch in
@@ -175,6 +176,7 @@ struct BatchDesc {
     FrameDesc f[kMaxBatch];
     CsJob cs;                       // the batch's coder job over csf (frames with do_cs)
     CsFrame csf[kMaxBatch];
+    int cs_next;                    // the coder's work counter
 };
 
 #ifdef __CUDACC__

@@ -385,13 +385,19 @@ __device__ void cb_geometry(int j, int W, int H, int D, int &band, int &ori, int
 
 }  // namespace
 
-// Tier-1 coding: one warp per code-block of the job (grid-stride).
+// Tier-1 coding: one warp per code-block of the job (taken dynamically).
 __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ job)
 {
     extern __shared__ __align__(16) unsigned char t1sm[];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     T1Warp &s = reinterpret_cast<T1Warp *>(t1sm)[wp];
-    for (int g = blockIdx.x * kT1Warps + wp; g < job->ncb; g += gridDim.x * kT1Warps) {
+    // code-blocks are taken in order from the job's counter, one per warp
+    // at a time: their costs differ by orders of magnitude
+    for (;;) {
+    int g = 0;
+    if (lane == 0) g = atomicAdd(job->next, 1);
+    g = __shfl_sync(0xffffffffu, g, 0);
+    if (g >= job->ncb) break;
     // frame of the code-block (frames' code-block ranges are consecutive)
     int f = 0;
     while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;

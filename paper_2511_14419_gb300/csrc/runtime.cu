@@ -679,7 +679,10 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     }
     if (c->cfg.codestream_bpp > 0.f) {
         // tier-1 coding, rate control and containers of the batch's front-end frames
-        timed(c, st, prof, K_CS, -1, -1, [&] { launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_csc, st); });
+        timed(c, st, prof, K_CS, -1, -1, [&] {
+            cudaMemsetAsync(const_cast<int *>(&dd->cs_next), 0, sizeof(int), st);
+            launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_csc, st);
+        });
         cnt += 3;
     }
     *nlaunch = cnt;
@@ -755,6 +758,7 @@ int step_locked(flowroi_ctx *c)
     for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].s, sel[i].e, sel[i].d, hd.f[i]);
     fill_offsets(c, hd);
     hd.cs.frames = c->desc_dev[k]->csf;
+    hd.cs.next = &c->desc_dev[k]->cs_next;
     for (auto &pk : sel)
         if (pk.e) CK(c, cudaStreamWaitEvent(c->s_comp, pk.e->uploaded, 0));
     const size_t bytes = offsetof(BatchDesc, f) + sizeof(FrameDesc) * sel.size();
@@ -1633,7 +1637,7 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     const size_t o_info = take((size_t)ncb * kCbInfo * sizeof(int32_t));
     const size_t o_hk = take((size_t)ncb * (kMaxPasses + 1) * sizeof(int32_t));
     const size_t o_hs = take((size_t)ncb * (kMaxPasses + 1) * sizeof(double));
-    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(sizeof(unsigned));
+    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(2 * sizeof(unsigned));
     const size_t o_coef = on_device ? 0 : take(coef_bytes), o_out = on_device ? 0 : take(out_bytes);
 
     int rc = FLOWROI_OK;
@@ -1687,9 +1691,10 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     job.frames = reinterpret_cast<const CsFrame *>(dev + o_frames);
     job.cbcap = kCbBytes;
     job.err = reinterpret_cast<unsigned *>(dev + o_err);
+    job.next = reinterpret_cast<int *>(dev + o_err) + 1;
     step(cudaMemcpyAsync(dev + o_frames, fr.data(), sizeof(CsFrame) * (size_t)n, cudaMemcpyHostToDevice, st));
     step(cudaMemcpyAsync(dev + o_job, &job, sizeof job, cudaMemcpyHostToDevice, st));
-    step(cudaMemsetAsync(dev + o_err, 0, sizeof(unsigned), st));
+    step(cudaMemsetAsync(dev + o_err, 0, 2 * sizeof(unsigned), st));
     if (e == cudaSuccess) {
         launch_ebcot(reinterpret_cast<const CsJob *>(dev + o_job), n, ncb, st);
         step(cudaGetLastError());
