@@ -38,20 +38,35 @@ namespace flowroi {
 namespace {
 
 // MQ probability estimation table (Annex C, Table C.2): Qe, next index
-// after an MPS, after an LPS, and whether an LPS exchanges the MPS.
-__constant__ uint16_t kQe[47] = {
-    0x5601, 0x3401, 0x1801, 0x0AC1, 0x0521, 0x0221, 0x5601, 0x5401, 0x4801, 0x3801, 0x3001, 0x2401,
-    0x1C01, 0x1601, 0x5601, 0x5401, 0x5101, 0x4801, 0x3801, 0x3401, 0x3001, 0x2801, 0x2401, 0x2201,
-    0x1C01, 0x1801, 0x1601, 0x1401, 0x1201, 0x1101, 0x0AC1, 0x09C1, 0x08A1, 0x0521, 0x0441, 0x02A1,
-    0x0221, 0x0141, 0x0111, 0x0085, 0x0049, 0x0025, 0x0015, 0x0009, 0x0005, 0x0001, 0x5601};
-__constant__ uint8_t kNmps[47] = {1,  2,  3,  4,  5,  38, 7,  8,  9,  10, 11, 12, 13, 29, 15, 16,
-                                  17, 18, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29, 30, 31, 32,
-                                  33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 44, 45, 45, 46};
-__constant__ uint8_t kNlps[47] = {1,  6,  9,  12, 29, 33, 6,  14, 14, 14, 17, 18, 20, 21, 14, 14,
-                                  15, 16, 17, 18, 19, 19, 20, 21, 22, 23, 24, 25, 26, 27, 28, 29,
-                                  30, 31, 32, 33, 34, 35, 36, 37, 38, 39, 40, 41, 42, 43, 46};
-__constant__ uint8_t kSwitch[47] = {1, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0,
-                                    0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+// after an MPS, after an LPS, and whether an LPS exchanges the MPS; packed
+// into one word per state for the coder (Qe bits 0-15, next-after-MPS
+// 16-21, next-after-LPS 22-27, exchange bit 28).
+struct MqRow {
+    uint16_t qe;
+    uint8_t nmps, nlps, sw;
+};
+constexpr MqRow kMqRows[47] = {
+    {0x5601, 1, 1, 1},   {0x3401, 2, 6, 0},   {0x1801, 3, 9, 0},   {0x0AC1, 4, 12, 0},  {0x0521, 5, 29, 0},
+    {0x0221, 38, 33, 0}, {0x5601, 7, 6, 1},   {0x5401, 8, 14, 0},  {0x4801, 9, 14, 0},  {0x3801, 10, 14, 0},
+    {0x3001, 11, 17, 0}, {0x2401, 12, 18, 0}, {0x1C01, 13, 20, 0}, {0x1601, 29, 21, 0}, {0x5601, 15, 14, 1},
+    {0x5401, 16, 14, 0}, {0x5101, 17, 15, 0}, {0x4801, 18, 16, 0}, {0x3801, 19, 17, 0}, {0x3401, 20, 18, 0},
+    {0x3001, 21, 19, 0}, {0x2801, 22, 19, 0}, {0x2401, 23, 20, 0}, {0x2201, 24, 21, 0}, {0x1C01, 25, 22, 0},
+    {0x1801, 26, 23, 0}, {0x1601, 27, 24, 0}, {0x1401, 28, 25, 0}, {0x1201, 29, 26, 0}, {0x1101, 30, 27, 0},
+    {0x0AC1, 31, 28, 0}, {0x09C1, 32, 29, 0}, {0x08A1, 33, 30, 0}, {0x0521, 34, 31, 0}, {0x0441, 35, 32, 0},
+    {0x02A1, 36, 33, 0}, {0x0221, 37, 34, 0}, {0x0141, 38, 35, 0}, {0x0111, 39, 36, 0}, {0x0085, 40, 37, 0},
+    {0x0049, 41, 38, 0}, {0x0025, 42, 39, 0}, {0x0015, 43, 40, 0}, {0x0009, 44, 41, 0}, {0x0005, 45, 42, 0},
+    {0x0001, 45, 43, 0}, {0x5601, 46, 46, 0},
+};
+struct MqTable {
+    uint32_t w[47];
+    constexpr MqTable() : w{}
+    {
+        for (int i = 0; i < 47; i++)
+            w[i] = kMqRows[i].qe | ((uint32_t)kMqRows[i].nmps << 16) | ((uint32_t)kMqRows[i].nlps << 22) |
+                   ((uint32_t)kMqRows[i].sw << 28);
+    }
+};
+__constant__ MqTable kMq = MqTable();
 
 constexpr int kCtxRL = 17, kCtxUni = 18, kNctx = 19;
 
@@ -110,7 +125,7 @@ constexpr int kT1Warps = 7;  // code-blocks per CTA (three CTAs per SM by shared
 
 struct T1Warp {
     uint16_t st[(kCb + 2) * kColS];
-    uint8_t ci[kNctx + 1], cm[kNctx + 1];
+    uint8_t cx[kNctx + 1];  // MQ context states: probability state << 1 | MPS
     uint64_t bm[kCb];  // bit p of the magnitudes, one row per word (bit x)
 };
 
@@ -201,14 +216,14 @@ struct Mqe {
     }
     __device__ __forceinline__ void encode(T1Warp &s, int cx, int d)
     {
-        const int i = s.ci[cx];
-        const uint32_t qe = kQe[i];
+        const uint32_t st8 = s.cx[cx], mps = st8 & 1u;
+        const uint32_t row = kMq.w[st8 >> 1], qe = row & 0xFFFFu;
         a -= qe;
-        if (d == s.cm[cx]) {
+        if ((uint32_t)d == mps) {
             if ((a & 0x8000) == 0) {
                 if (a < qe) a = qe;
                 else c += qe;
-                s.ci[cx] = kNmps[i];
+                s.cx[cx] = (uint8_t)((((row >> 16) & 63u) << 1) | mps);
                 renorm();
             } else {
                 c += qe;
@@ -216,8 +231,7 @@ struct Mqe {
         } else {
             if (a < qe) c += qe;
             else a = qe;
-            if (kSwitch[i]) s.cm[cx] ^= 1;
-            s.ci[cx] = kNlps[i];
+            s.cx[cx] = (uint8_t)((((row >> 22) & 63u) << 1) | (mps ^ (row >> 28)));
             renorm();
         }
     }
@@ -438,8 +452,7 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
         continue;
     }
     if (lane < kNctx) {
-        s.ci[lane] = lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0));
-        s.cm[lane] = 0;
+        s.cx[lane] = (uint8_t)((lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0))) << 1);
     }
     uint8_t *const cbytes = F.cbytes + (size_t)jb * job->cbcap;
     Mqe e;

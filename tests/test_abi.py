@@ -114,3 +114,6 @@ def test_encode_codestreams_rejects_bad_jobs_on_the_host(F):
     L = F.lib()
     jobs = (F.flowroi_cs_job * 1)()
     assert L.flowroi_encode_codestreams(None, 1, jobs, 0) == F.EINVAL
+    import ctypes
+    n = ctypes.c_uint64(0)
+    assert L.flowroi_get_codestream(None, 0, 0, jobs, 0, ctypes.byref(n), 0, 0) == F.EINVAL

@@ -138,15 +138,15 @@ def test_too_small_output_and_out_of_range_magnitudes(ctx):
     assert _gpu(ctx, [q], 3, 53, 5, [0])[0] == o.encode_frame(q, 3, 53, 5, 12, 0)[0]
 
 
-@pytest.mark.parametrize("plain", [False, True])
-def test_stream_path_codestreams_match_the_coder(plain):
+@pytest.mark.parametrize("plain,adjacent", [(False, 0), (True, 0), (False, 1)])
+def test_stream_path_codestreams_match_the_coder(plain, adjacent):
     """config.codestream_bpp: every frame's container from the stream path
     (coded in the batch's launches, first frames included) equals the coder
     applied to that frame's coefficient plane (whose parity with the oracle
     the tests above establish)."""
     h, w, S, n = 256, 320, 3, 3
     flags = F.MANUAL | (F.PLAIN if plain else 0)
-    with F.Context(pyr_levels=3, dwt_levels=3, wavelet=97, codestream_bpp=1.0, flags=flags) as c:
+    with F.Context(pyr_levels=3, dwt_levels=3, wavelet=97, codestream_bpp=1.0, flags=flags, adjacent=adjacent) as c:
         seqs = [np.asarray(sequence_u16(700 + s, n, h, w, 8)).astype(np.uint16) for s in range(S)]
         for t in range(n):
             for s in range(S):
@@ -179,3 +179,26 @@ def test_stream_path_codestream_off_is_einval():
         with pytest.raises(F.FlowRoIError) as ei:
             F.flowroi_get_codestream(c.h, 0, 0, np.zeros(1024, np.uint8), 10000)
         assert ei.value.code == F.EINVAL
+
+
+def test_stream_path_out_of_range_coefficients_are_erange():
+    """16-bit frames with a 15-bit RoI up-shift give magnitudes of 2^24 and
+    more: the frame's container is refused with FLOWROI_ERANGE, its
+    coefficients are still delivered, and the context keeps working."""
+    h = w = 128
+    rng = np.random.default_rng(5)
+    with F.Context(pyr_levels=2, dwt_levels=2, wavelet=53, scale_shift=15, codestream_bpp=2.0, flags=F.MANUAL) as c:
+        frames = [rng.integers(0, 65536, (h, w)).astype(np.uint16) for _ in range(3)]
+        for t, fr in enumerate(frames):
+            F.flowroi_submit_frame(c.h, 0, fr, t, 16)
+        F.flowroi_flush(c.h, 60000)
+        coeffs = np.empty((h, w), np.int32)
+        F.flowroi_get_coeffs(c.h, 0, 2, coeffs, 10000)
+        mask = np.empty((h, w), np.uint8)
+        F.flowroi_get_mask(c.h, 0, 2, mask, 10000)
+        assert mask.any() and np.abs(coeffs.astype(np.int64)).max() >= 1 << 24
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_get_codestream(c.h, 0, 2, np.zeros(F.flowroi_codestream_bound(w, h, 2), np.uint8), 10000)
+        assert ei.value.code == F.ERANGE
+        # the first frame has no RoI, so no shift: its container is there
+        assert F.flowroi_get_codestream(c.h, 0, 0, np.zeros(F.flowroi_codestream_bound(w, h, 2), np.uint8), 10000) > 0
