@@ -24,6 +24,7 @@ workload and prints the same metric.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -268,10 +269,13 @@ def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampl
         sampler = ClockSampler(sampler_device) if sampler_device is not None else None
         if sampler:
             sampler.__enter__()
+        gc.collect()
+        gc.disable()  # no collector pauses in the timed host loop
         e0.record(stream)
         for _ in range(steps):
             one_step()
         e1.record(stream)
+        gc.enable()
         F.flowroi_flush(ctx.h, -1)
         e1.synchronize()
         if sampler:
@@ -329,6 +333,8 @@ def run_e2e(F, wl, frames, steps, warmup):
             submit_step()
             fetch(t - 1)
         torch.cuda.synchronize()
+        gc.collect()
+        gc.disable()  # no collector pauses in the timed host loop
         t0 = time.perf_counter()
         for k in range(steps):
             submit_step()
@@ -336,6 +342,7 @@ def run_e2e(F, wl, frames, steps, warmup):
                 fetch(t - 2)
         fetch(t - 1)
         dt = time.perf_counter() - t0
+        gc.enable()
         st = F.flowroi_get_stats(ctx.h)
     res["time_s"] = dt
     res["frames"] = steps * S
@@ -645,7 +652,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        es = max(3, min(args.steps, 60))
+        es = max(3, min(args.steps, 200))
         er = run_e2e(F, wl, frames, es, args.warmup)
         barrier()
         e2e = {"value": job_throughput(er["frames"], ws, max_over_ranks(er["time_s"], ws, dev_name)), "unit": "frames/s",

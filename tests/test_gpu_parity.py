@@ -148,9 +148,12 @@ def test_full_size_2048_u16_97_batched(orc):
     _stagewise(orc, seq[0], seq[1], 12, g, **cfg)
 
 
-def test_fp16_storage_epe_and_iou(orc):
+@pytest.mark.parametrize("win_r", [7, 2, 10])
+def test_fp16_storage_epe_and_iou(orc, win_r):
+    """fp16 storage (the window kernel's separate fp32 sums areas, whose
+    ring depth depends on the window radius) against the FP64 oracle."""
     seq = u16(sequence_u16(3002, 2, 512, 512, 30))
-    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
+    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97, win_r=win_r)
     g = run_stream([seq[0], seq[1]], 12, precision=F.FP16, **cfg)[1]
     o = orc.frame(seq[0], seq[1], 12, oracle_params(orc, **cfg))
     d = g["flow"].transpose(2, 0, 1)
