@@ -395,8 +395,10 @@ FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, 
  *                 to the length it needs, with FLOWROI_ERANGE)
  * on_device: coeffs and out are device pointers of the context's device
  * (else host pointers; the library copies).  Runs synchronously on a
- * stream of its own with scratch memory allocated for the call (about
- * 34 KB per code-block); n in [1, 64].  Returns FLOWROI_OK, FLOWROI_EINVAL
+ * stream of its own (device inputs must be complete when the call is made:
+ * it does not wait on the caller's streams), with scratch memory that the
+ * context keeps between calls (about 34 KB per code-block of the largest
+ * call so far); n in [1, 64].  Returns FLOWROI_OK, FLOWROI_EINVAL
  * (malformed job), FLOWROI_ENOMEM, FLOWROI_ERANGE (a container did not fit
  * or a code-block exceeded the coder's limits) or FLOWROI_EDEVICE. */
 typedef struct {
