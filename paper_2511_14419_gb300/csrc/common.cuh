@@ -12,6 +12,7 @@ namespace flowroi {
 constexpr int kMaxLevels = 8;    // pyramid and DWT levels
 constexpr int kMaxBatch = 64;    // frames per batched launch
 constexpr int kHistBins = 2048;  // radix-select digit of 11 bits
+constexpr int kCandBlocks = 32;  // blocks per frame of the last radix digit
 constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
 
 // Tile shapes (output pixels per block) of each kernel family.
@@ -30,6 +31,7 @@ constexpr int kDwtTW = 64, kDwtTH = 16;   // DWT: band coefficients per block (p
 //   largest S whose normalised value is <= t_hat: mask0 = S > s*),
 //   [kRedHist .. +kHistBins) histogram of the current radix digit.
 constexpr int kRedMin = 0, kRedMax = 1, kRedPrefix = 2, kRedRank = 3, kRedTS = 4, kRedTHat = 5, kRedSStar = 6;
+constexpr int kRedCand = 7;  // S values left after the second digit, in FrameDesc::cand
 constexpr int kRedHist = 8;
 //   [kRedReg ..) registration: the level image's sum (double), max |X|
 //   (float bits), the correlation peak key (u64) and the drift (2 floats).
@@ -125,6 +127,7 @@ struct FrameDesc {
     float2 *flow[2];                // ping-pong flow buffers, level-0 capacity
     float *S;                       // saliency, pitch lp[0]
     unsigned *red;                  // reduction block (kRedWords)
+    unsigned *cand;                 // the S bits of the pixels the last digit pass reads (W*H words)
     uint8_t *mask;                  // result mask, W*H
     int32_t *coeffs;                // result coefficients, W*H (Mallat)
     float2 *dbg_flow;               // keep: level-0 flow, W*H (else null)

@@ -279,10 +279,12 @@ __global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict
     bh.flush();
 }
 
-// Histogram of radix digit `pass` (1 or 2) over the values whose higher
-// bits equal the prefix selected so far.  One thread per tile column: all
-// of its kSalTH loads are issued before any is tested.
-__global__ void __launch_bounds__(256) k_select_pass(const BatchDesc *__restrict__ bd, int pass)
+// Histogram of radix digit 1 over the values whose higher bits equal the
+// prefix selected so far.  One thread per tile column: all of its kSalTH
+// loads are issued before any is tested.  The matching values are also
+// appended to the frame's candidate list (one atomic per warp and tile), so
+// the last digit reads only them.
+__global__ void __launch_bounds__(256, 4) k_select_pass(const BatchDesc *__restrict__ bd, int pass)
 {
     constexpr int TW = kSalTW, TH = kSalTH;
     __shared__ unsigned s_hist[kHistBins];
@@ -292,6 +294,7 @@ __global__ void __launch_bounds__(256) k_select_pass(const BatchDesc *__restrict
     const int total = __ldg(off + nfr);
     const int sh = digit_shift(pass), hi = sh + digit_bits(pass);
     const unsigned dmask = (1u << digit_bits(pass)) - 1u;
+    const int lane = threadIdx.x & 31;
     BlockHist bh{s_hist, s_mm};
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
         const int fi = find_frame(off, nfr, t);
@@ -304,17 +307,61 @@ __global__ void __launch_bounds__(256) k_select_pass(const BatchDesc *__restrict
         const int x0 = (lt % ntx) * TW, y0 = (lt / ntx) * TH;
         const unsigned want = __ldg(F.red + kRedPrefix) >> hi;
         const int gx = x0 + (int)threadIdx.x;
-        if (gx >= w) continue;
-        const unsigned *col = reinterpret_cast<const unsigned *>(F.S) + (size_t)y0 * p + gx;
-        const int nr = min(TH, h - y0);
+        const int nr = gx < w ? min(TH, h - y0) : 0;
+        const unsigned *col = reinterpret_cast<const unsigned *>(F.S) + (size_t)y0 * p + min(gx, w - 1);
         unsigned v[TH];
 #pragma unroll
         for (int j = 0; j < TH; j++) v[j] = j < nr ? __ldg(col + (size_t)j * p) : 0u;
+        unsigned tot = 0;
 #pragma unroll
-        for (int j = 0; j < TH; j++)
-            if (j < nr && (v[j] >> hi) == want) atomicAdd(&s_hist[(v[j] >> sh) & dmask], 1u);
+        for (int j = 0; j < TH; j++) {
+            const bool hit = j < nr && (v[j] >> hi) == want;
+            if (hit) atomicAdd(&s_hist[(v[j] >> sh) & dmask], 1u);
+            tot += __popc(__ballot_sync(0xffffffffu, hit));
+        }
+        if (tot == 0) continue;  // warp-uniform
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(F.red + kRedCand, tot);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        // the row's matches are stored contiguously (the row's ballot again)
+        const unsigned below = (1u << lane) - 1u;
+#pragma unroll
+        for (int j = 0; j < TH; j++) {
+            const bool hit = j < nr && (v[j] >> hi) == want;
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (hit) F.cand[base + __popc(m & below)] = v[j];
+            base += __popc(m);
+        }
     }
     bh.flush();
+}
+
+// Histogram of the last radix digit over the frame's candidate list (the
+// values in the first digit's selected bin), counting those that are also in
+// the second digit's selected bin.  kCandBlocks blocks share a frame; the
+// grid (a multiple of kCandBlocks) strides over the frames.
+__global__ void __launch_bounds__(256) k_select_cand(const BatchDesc *__restrict__ bd)
+{
+    constexpr int NB = 1 << digit_bits(2);
+    __shared__ unsigned s_hist[NB];
+    const int part = blockIdx.x % kCandBlocks, fstride = gridDim.x / kCandBlocks;
+    const int sh = digit_shift(2), hi = sh + digit_bits(2);
+    for (int f = blockIdx.x / kCandBlocks; f < bd->nframes; f += fstride) {
+        const FrameDesc &F = bd->f[f];
+        if (!F.has_prev) continue;  // block-uniform
+        const unsigned want = F.red[kRedPrefix] >> hi;
+        const unsigned n = F.red[kRedCand];
+        for (int i = threadIdx.x; i < NB; i += blockDim.x) s_hist[i] = 0u;
+        __syncthreads();
+        for (unsigned i = part * blockDim.x + threadIdx.x; i < n; i += kCandBlocks * blockDim.x) {
+            const unsigned v = __ldg(F.cand + i);
+            if ((v >> hi) == want) atomicAdd(&s_hist[(v >> sh) & (NB - 1)], 1u);
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < NB; i += blockDim.x)
+            if (s_hist[i]) atomicAdd(F.red + kRedHist + i, s_hist[i]);
+        __syncthreads();
+    }
 }
 
 // One block per frame: locate the bin of the current digit that holds the
@@ -574,7 +621,11 @@ void launch_saliency(const BatchDesc *bd, const MethodConsts &mc, int grid, cuda
     ensure_saliency_attr();
     k_saliency<<<grid, 256, SalSmem::bytes, s>>>(bd, mc);
 }
-void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s) { k_select_pass<<<grid, 256, 0, s>>>(bd, pass); }
+void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s)
+{
+    if (pass == 1) k_select_pass<<<grid, 256, 0, s>>>(bd, pass);
+    else k_select_cand<<<grid, 256, 0, s>>>(bd);
+}
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s)
 {
     k_select_find<<<grid, 256, 0, s>>>(bd, mc, pass);

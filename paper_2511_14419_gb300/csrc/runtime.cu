@@ -154,6 +154,7 @@ struct Stream {
     float2 *reg_spec[2] = {}, *reg_work = nullptr; // spectra (by frame parity) and the correlation plane
     float *S = nullptr;
     unsigned *red = nullptr;
+    unsigned *cand = nullptr;  // select candidates (W*H words)
     void *ll[2] = {};
     uint8_t *llm[2] = {};
     // JPEG2000 coder (codestream_bpp > 0): code-block scratch, container geometry
@@ -373,6 +374,7 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
     for (int k = 0; k < 2; k++) s->flow[k] = reinterpret_cast<float2 *>(take((size_t)s->lp[0] * s->H * sizeof(float2)));
     s->S = reinterpret_cast<float *>(take((size_t)s->lp[0] * s->H * sizeof(float)));
     s->red = reinterpret_cast<unsigned *>(take(kRedWords * sizeof(unsigned)));
+    s->cand = reinterpret_cast<unsigned *>(take(npx * sizeof(unsigned)));
     if (c->cfg.min_area > 1)
         for (int k = 0; k < 3; k++) s->cc[k] = reinterpret_cast<int *>(take(npx * sizeof(int)));
     if (c->cfg.register_frames) {
@@ -467,6 +469,7 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
     F.flow[1] = s->flow[1];
     F.S = s->S;
     F.red = s->red;
+    F.cand = s->cand;
     F.cc_lab = s->cc[0];
     F.cc_cnt = s->cc[1];
     F.cc_area = s->cc[2];
@@ -655,8 +658,10 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
             }
         timed(c, st, prof, K_SAL, -1, -1, [&] { launch_saliency(dd, mc, g(hd->sal_off[n], c->grid_mask), st); });
         for (int pass = 0; pass < 3; pass++) {
-            if (pass > 0)
-                timed(c, st, prof, K_PASS, pass, -1, [&] { launch_select_pass(dd, pass, g(hd->sal_off[n], c->grid_mask), st); });
+            // pass 2 reads the candidates pass 1 kept: kCandBlocks blocks a frame
+            const int gp = pass == 1 ? g(hd->sal_off[n], c->grid_mask)
+                                     : (pl ? n * kCandBlocks : std::max(1, c->grid_mask / kCandBlocks) * kCandBlocks);
+            if (pass > 0) timed(c, st, prof, K_PASS, pass, -1, [&] { launch_select_pass(dd, pass, gp, st); });
             timed(c, st, prof, K_FIND, pass, -1, [&] { launch_select_find(dd, mc, pass, g(n, c->grid_frames), st); });
         }
         cnt += 6;
