@@ -48,3 +48,21 @@ def test_single_rank_is_identity():
     assert bench.max_over_ranks(3.0, 1, "cpu") == 3.0
     assert bench.job_throughput(16, 1, 2.0) == 8.0
     assert [bench.frame_index(t, 4) for t in range(8)] == [0, 1, 2, 3, 2, 1, 0, 1]
+
+
+def test_all_cores_oracle_sample_spawns_one_process_per_core():
+    """The all-cores CPU baseline: two spawned oracle processes on crops of
+    a small synthetic pair; the rate is the sum of the processes' rates,
+    scaled to the workload's frame size."""
+    import numpy as np
+
+    import bench
+    from synth import sequence_u16
+    seq = sequence_u16(11, 2, 128, 128, 6, device="cpu")
+    fc = [(seq[0].numpy().view(np.uint16), seq[1].numpy().view(np.uint16))]
+    wl = dict(h=128, w=128, bit_depth=12, pyr_levels=3, dwt_levels=3, wavelet=97)
+    fps, procs, n, el = bench.cpu_sample_parallel(wl, fc, procs=2, budget_s=0.2, crop=64, per_proc=2)
+    assert procs == 2 and n >= 2 and el >= 0.2
+    # two processes, each at least one 64x64 crop in at most el seconds
+    assert fps >= 2 * (64 * 64) / (128 * 128) / el * 0.5
+    assert fps > 0
