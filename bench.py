@@ -537,8 +537,11 @@ def _cpu_worker(job):
             return done, el
 
 
-def _cpu_worker_init():
-    from oracle import oracle  # noqa: F401  (loads the oracle's C library before the clock starts)
+def _cpu_proc(i, job, q):
+    try:
+        q.put((i, _cpu_worker(job)))
+    except Exception as e:  # reported to the parent, which gives up on the sample
+        q.put((i, f"{type(e).__name__}: {e}"))
 
 
 def cpu_sample_parallel(wl, frames_cpu, procs=None, budget_s=8.0, crop=512, per_proc=2):
@@ -548,27 +551,52 @@ def cpu_sample_parallel(wl, frames_cpu, procs=None, budget_s=8.0, crop=512, per_
     (frames/s scaled to full frames = the sum of the processes' rates,
     processes, crops done, seconds)."""
     import multiprocessing as mp
-    from concurrent.futures import ProcessPoolExecutor
+    import queue
 
     import numpy as np
     procs = procs or os.cpu_count() or 1
     h, w = wl["h"], wl["w"]
     jobs = []
-    for q in range(procs):
+    for pi in range(procs):
         crops = []
         for j in range(per_proc):
-            k = q * per_proc + j
+            k = pi * per_proc + j
             a, b = frames_cpu[k % len(frames_cpu)]
             y0 = (k * 389) % (h - crop + 1) // 32 * 32
             x0 = (k * 613) % (w - crop + 1) // 32 * 32
             crops.append((np.ascontiguousarray(a[y0:y0 + crop, x0:x0 + crop]),
                           np.ascontiguousarray(b[y0:y0 + crop, x0:x0 + crop])))
         jobs.append((crops, wl, budget_s))
-    # an executor, not a Pool: a worker that dies breaks the executor (an
-    # exception here) instead of being respawned forever
-    with ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn"), initializer=_cpu_worker_init) as ex:
-        futs = [ex.submit(_cpu_worker, j) for j in jobs]
-        res = [f.result(timeout=4 * budget_s + 120) for f in futs]
+    # plain processes and a queue: a worker that fails or dies ends the
+    # sample with an exception, and none outlives the deadline
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_cpu_proc, args=(i, j, q), daemon=True) for i, j in enumerate(jobs)]
+    for p in ps:
+        p.start()
+    out = {}
+    deadline = time.monotonic() + 4 * budget_s + 120
+    try:
+        while len(out) < len(ps):
+            try:
+                i, r = q.get(timeout=1.0)
+            except queue.Empty:
+                dead = [k for k, p in enumerate(ps) if k not in out and p.exitcode not in (None, 0)]
+                if dead:
+                    raise RuntimeError(f"oracle process {dead[0]} exited with {ps[dead[0]].exitcode}")
+                if time.monotonic() > deadline:
+                    raise TimeoutError("oracle processes did not finish")
+                continue
+            if isinstance(r, str):
+                raise RuntimeError(r)
+            out[i] = r
+    finally:
+        for p in ps:
+            p.join(timeout=5)
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=5)
+    res = [out[i] for i in range(len(ps))]
     px_per_s = sum(d * crop * crop / el for d, el in res)
     return px_per_s / (h * w), procs, sum(d for d, _ in res), max(el for _, el in res)
 

@@ -66,3 +66,19 @@ def test_all_cores_oracle_sample_spawns_one_process_per_core():
     # two processes, each at least one 64x64 crop in at most el seconds
     assert fps >= 2 * (64 * 64) / (128 * 128) / el * 0.5
     assert fps > 0
+
+
+def test_all_cores_oracle_sample_reports_a_failing_process():
+    """A worker whose oracle call fails ends the sample with an exception
+    (no respawn, no wait for the deadline)."""
+    import time
+
+    import numpy as np
+
+    import bench
+    fc = [(np.zeros((64, 64), np.uint16), np.zeros((64, 64), np.uint16))]
+    wl = dict(h=64, w=64, bit_depth=12, dwt_levels=2, wavelet=53)  # no pyr_levels: KeyError in the workers
+    t0 = time.monotonic()
+    with pytest.raises(RuntimeError, match="KeyError"):
+        bench.cpu_sample_parallel(wl, fc, procs=2, budget_s=0.1, crop=32, per_proc=1)
+    assert time.monotonic() - t0 < 60
