@@ -20,8 +20,12 @@
  *       (reversible 5/3 or irreversible 9/7), quantisation, and the up-shift
  *       of RoI coefficients by the scaling factor.
  *
- * EBCOT / rate control / codestream assembly are downstream consumers of
- * the coefficients and are not part of this library.
+ * Optionally (§Implementation details, Table 1 "compression rate") the
+ * coefficients are also coded: EBCOT tier-1 with the MQ coder, rate control
+ * to a byte budget, and a frame container of this library's own layout
+ * (flowroi_encode_codestreams, or config.codestream_bpp in the stream
+ * path).  The standard JPEG2000 codestream syntax (tier-2 packets, markers)
+ * is not produced.
  *
  * Every step runs in this library's CUDA kernels on one GPU; the host side
  * only validates, copies and schedules.  The library owns its device
@@ -98,8 +102,8 @@ extern "C" {
 
 /* ---- configuration ----------------------------------------------------- */
 /* Method parameters.  Table 1 of the paper names the user parameters (RoI
- * threshold, scaling factor, denoise, adjacent factor; compression rate
- * acts downstream).  The estimator constants are not
+ * threshold, scaling factor, denoise, adjacent factor, compression rate:
+ * codestream_bpp below).  The estimator constants are not
  * given by the paper; the defaults are the values this library documents
  * (pyramid 5 levels, 3 iterations, 15x15 box window, 5x5 expansion with
  * sigma 1.1, lambda 1e-3 in 8-bit units, opening radius 1, closing
@@ -304,9 +308,12 @@ FLOWROI_API int flowroi_compute_stream(flowroi_ctx *ctx, void **out);
  * rows (or a negative status).  Turning profiling off keeps the totals;
  * flowroi_set_profiling(ctx, 2) clears them and turns profiling on. */
 typedef struct flowroi_kernel_time {
-    char name[24];       /* "expand", "update", "window", "saliency", "select_pass", "select_find",
-                            "morph", "dwt", "frame_init" */
-    int32_t level;       /* pyramid level (expand, update, window), DWT level (dwt), digit pass, or -1 */
+    char name[24];       /* "frame_init", "expand", "update", "window", "saliency", "select_find",
+                            "select_pass" (digit 2 over the plane, digit 3 over its candidates),
+                            "morph", "dwt", "denoise", "components", "merge", "register",
+                            "codestream" (the coder's three kernels) */
+    int32_t level;       /* pyramid level (expand, update, window), DWT level (dwt), digit pass
+                            (select_*), step (components, register), or -1 */
     int32_t iter;        /* displacement iteration (update, window), else -1 */
     int64_t launches;
     double total_ms;
