@@ -94,6 +94,7 @@ def _declare(L):
         "orc_wavelet_mask": (None, [_P, _I, _I, _I, _I, _P]),
         "orc_roi_shift": (_I, [_P, _P, _I64, _I]),
         "orc_mq_roundtrip": (ctypes.c_long, [_P, _P, ctypes.c_long, _P, _P]),
+        "orc_mq_table": (_I, [_P, _P, _P, _P]),
         "orc_t1_encode": (_I, [_P, _I, _I, _I, _I, _P, ctypes.c_long, _P, _P, _P]),
         "orc_t1_decode": (None, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _I]),
         "orc_hull": (_I, [_I, _P, _P, _P, _P]),
@@ -457,6 +458,14 @@ def mq_roundtrip(d: np.ndarray, cx: np.ndarray):
     out = np.empty_like(d)
     n = lib().orc_mq_roundtrip(_ptr(d), _ptr(cx), d.size, _ptr(code), _ptr(out))
     return code[:n].copy(), out
+
+
+def mq_table():
+    """The MQ coder's probability states (JPEG2000 Part 1, Annex C, Table
+    C.2) as (qe, next after MPS, next after LPS, switch) int arrays."""
+    a = [np.zeros(47, np.int32) for _ in range(4)]
+    lib().orc_mq_table(*[_ptr(x) for x in a])
+    return tuple(a)
 
 
 def t1_encode(q: np.ndarray, ori: int):

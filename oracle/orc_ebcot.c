@@ -57,6 +57,18 @@ static const orc_mq_state MQ[47] = {
     {0x0001, 45, 43, 0}, {0x5601, 46, 46, 0},
 };
 
+/* The table as plain arrays (for the tests that check its structure). */
+int orc_mq_table(int32_t *qe, int32_t *nmps, int32_t *nlps, int32_t *sw)
+{
+    for (int i = 0; i < 47; i++) {
+        qe[i] = MQ[i].qe;
+        nmps[i] = MQ[i].nmps;
+        nlps[i] = MQ[i].nlps;
+        sw[i] = MQ[i].sw;
+    }
+    return 47;
+}
+
 enum { CTX_ZC = 0, CTX_SC = 9, CTX_MR = 14, CTX_RL = 17, CTX_UNI = 18, NCTX = 19 };
 
 /* context states: index into MQ and the more probable symbol */

@@ -251,3 +251,43 @@ def test_roi_upshift_keeps_the_roi_quality_at_low_rates():
     roi0 = o.psnr(x0[m], raw[m], bd)
     assert roi5 > bg5 + 6.0, (roi5, bg5)
     assert roi5 > roi0 + 2.0, (roi5, roi0)
+
+
+def test_mq_table_structure():
+    """The probability-state machine of the MQ coder (Annex C, Table C.2)
+    has a fixed shape, independent of the exact Qe values: two fast-attack
+    MPS chains (states 0-5 and 6-13) that join a steady chain (14-45, ending
+    in a self-loop), the MPS sense exchanged by an LPS only in the three
+    states whose estimate is 1/2 (0, 6, 14), an MPS always lowering the LPS
+    estimate Qe along a chain, an LPS never lowering it, and state 46 the
+    fixed uniform state that nothing enters.  A typo in a transition or an
+    out-of-order Qe breaks one of these even where the coder still decodes
+    its own output."""
+    qe, nmps, nlps, sw = o.mq_table()
+    assert len(qe) == 47
+    assert set(np.flatnonzero(sw)) == {0, 6, 14}
+    assert all(qe[i] == 0x5601 for i in (0, 6, 14, 46)) and qe.max() == 0x5601 and qe.min() > 0
+    # the uniform state
+    assert nmps[46] == 46 and nlps[46] == 46
+    assert 46 not in set(nmps[:46]) | set(nlps[:46])
+    # MPS chains
+    for i in range(46):
+        if i in (5, 13):
+            assert nmps[i] >= 14  # a fast-attack chain ends in the steady chain
+        elif i == 45:
+            assert nmps[i] == 45
+        else:
+            assert nmps[i] == i + 1
+        if i != 45:
+            assert qe[nmps[i]] < qe[i], i
+    # LPS transitions
+    for i in range(46):
+        if sw[i]:
+            assert nlps[i] in (i, i + 1)
+        else:
+            assert qe[nlps[i]] > qe[i], i
+        if i >= 6:
+            assert 14 <= nlps[i] <= 45 or (i < 14 and nlps[i] == 6)  # never back to a fast-attack chain
+        else:
+            assert nlps[i] >= 1
+    assert all(nlps[i] >= 6 for i in range(1, 6))
