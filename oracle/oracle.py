@@ -95,6 +95,7 @@ def _declare(L):
         "orc_roi_shift": (_I, [_P, _P, _I64, _I]),
         "orc_mq_roundtrip": (ctypes.c_long, [_P, _P, ctypes.c_long, _P, _P]),
         "orc_mq_table": (_I, [_P, _P, _P, _P]),
+        "orc_context_tables": (None, [_P, _P, _P]),
         "orc_t1_encode": (_I, [_P, _I, _I, _I, _I, _P, ctypes.c_long, _P, _P, _P]),
         "orc_t1_decode": (None, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _I]),
         "orc_hull": (_I, [_I, _P, _P, _P, _P]),
@@ -466,6 +467,19 @@ def mq_table():
     a = [np.zeros(47, np.int32) for _ in range(4)]
     lib().orc_mq_table(*[_ptr(x) for x in a])
     return tuple(a)
+
+
+def context_tables():
+    """The coding-pass context rules (Annex D, Tables D.1 and D.3): the
+    zero-coding label zc[ori, d, v, h] (ori 0 LL, 1 HL, 2 LH, 3 HH; h, v,
+    d the significant horizontal, vertical, diagonal neighbours), and the
+    sign-coding label and flip bit sc[vc + 1, hc + 1], flip[vc + 1, hc + 1]
+    (hc, vc the clipped sign contributions)."""
+    zc = np.zeros(4 * 45, np.int32)
+    sc = np.zeros(9, np.int32)
+    fl = np.zeros(9, np.int32)
+    lib().orc_context_tables(_ptr(zc), _ptr(sc), _ptr(fl))
+    return zc.reshape(4, 5, 3, 3), sc.reshape(3, 3), fl.reshape(3, 3)
 
 
 def t1_encode(q: np.ndarray, ori: int):

@@ -331,6 +331,23 @@ static void sc_context(int hc, int vc, int *cx, int *flip)
     else *cx = vc == 1 ? 10 : 9;
 }
 
+/* The context rules as tables (for the tests that check their structure):
+ * zc[ori * 45 + h + 3 v + 9 d], and sc / flip at (hc + 1) + 3 (vc + 1). */
+void orc_context_tables(int32_t *zc, int32_t *sc, int32_t *flip)
+{
+    for (int o = 0; o < 4; o++)
+        for (int d = 0; d < 5; d++)
+            for (int v = 0; v < 3; v++)
+                for (int h = 0; h < 3; h++) zc[o * 45 + h + 3 * v + 9 * d] = zc_context(o, h, v, d);
+    for (int vc = -1; vc <= 1; vc++)
+        for (int hc = -1; hc <= 1; hc++) {
+            int cx = 0, fl = 0;
+            sc_context(hc, vc, &cx, &fl);
+            sc[(hc + 1) + 3 * (vc + 1)] = cx;
+            flip[(hc + 1) + 3 * (vc + 1)] = fl;
+        }
+}
+
 /* Code-block coder state: magnitudes, signs and flags with a one-sample
  * border of zeros (neighbours outside the code-block are insignificant). */
 #define CB_MAX 64

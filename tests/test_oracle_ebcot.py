@@ -291,3 +291,30 @@ def test_mq_table_structure():
         else:
             assert nlps[i] >= 1
     assert all(nlps[i] >= 6 for i in range(1, 6))
+
+
+def test_context_rules_structure():
+    """Zero coding (Table D.1): labels 0..8, label 0 exactly for an
+    insignificant neighbourhood, every label used, the label never falling
+    when a neighbour becomes significant, HL the LH rule with horizontal
+    and vertical swapped, LL the same rule as LH, and HH driven by the
+    diagonals first.  Sign coding (Table D.3): labels 9..13, label 9 and no
+    flip for no contribution, and negating both contributions keeps the
+    label and flips the predicted sign."""
+    zc, sc, fl = o.context_tables()
+    for ori in range(4):
+        t = zc[ori]  # [d, v, h]
+        assert t.min() == 0 and t.max() == 8 and set(t.ravel()) == set(range(9))
+        assert (t == 0).sum() == 1 and t[0, 0, 0] == 0
+        assert (np.diff(t, axis=0) >= 0).all() and (np.diff(t, axis=1) >= 0).all() and (np.diff(t, axis=2) >= 0).all()
+    assert (zc[0] == zc[2]).all()
+    assert (zc[1] == zc[2].transpose(0, 2, 1)).all()
+    assert not (zc[1] == zc[2]).all()
+    # HH: the diagonal count dominates (one more diagonal outranks any h + v
+    # once d >= 1), LH: two horizontal neighbours give the top label
+    assert zc[3][3:].min() == 8 and zc[3][2].max() == 7 and (zc[2][:, :, 2] == 8).all()
+    assert set(sc.ravel()) == set(range(9, 14)) and sc[1, 1] == 9 and fl[1, 1] == 0
+    for v in range(3):
+        for h in range(3):
+            if (h, v) != (1, 1):
+                assert sc[v, h] == sc[2 - v, 2 - h] and fl[v, h] != fl[2 - v, 2 - h]
