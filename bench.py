@@ -672,6 +672,8 @@ def main():
     ap.add_argument("--serving-seconds", type=float, default=20.0)
     ap.add_argument("--burst", type=int, default=4, help="serving workload: frames per stream in the burst replay")
     args = ap.parse_args()
+    if not 1 <= args.burst <= 8:
+        ap.error("--burst must be in [1, 8]: the serving context keeps 8 results per stream")
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
     ws, rank, local = dist_env()

@@ -33,3 +33,9 @@ def test_reference_arm_other_ranks_exit_quietly():
     r = _run({"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_burst_larger_than_the_result_ring_is_refused_up_front():
+    r = subprocess.run([sys.executable, "bench.py", "--workload", "serving_64mixed", "--burst", "9"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 2 and "--burst" in r.stderr
