@@ -91,11 +91,44 @@ WORKLOADS = {
 #           fp16 10+8 = 18 B.
 KERNEL_BYTES = {("update", 32): (62.0, 68.0), ("update", 16): (32.0, 38.0),
                 ("window", 32): (28.0, 28.0), ("window", 16): (18.0, 18.0)}
+# Algorithmic bytes per pixel of one launch of the other kernels with a
+# roofline line (storage 32 / 16; `bpp` = bytes per raw sample):
+#   expand level 0: read the raw frame, write the five expansion fields and
+#           the next pyramid level (a quarter pixel): bpp + 5*4 + 4/4
+#           (fp16: bpp + 5*2 + 2/4);
+#   dwt level 1 (per frame pixel): read the raw sample and the RoI mask
+#           byte, write the three high bands' int32 coefficients (3/4 of the
+#           pixels) and the low-low band (a quarter: 4 B value + 1 B mask):
+#           bpp + 1 + 3 + 1 + 0.25.
+def other_bytes(name, storage, bpp):
+    if name == "expand":
+        return bpp + (5 * 4 + 1.0 if storage == 32 else 5 * 2 + 0.5)
+    if name == "dwt":
+        return bpp + 1 + 3 + 1 + 0.25
+    raise KeyError(name)
+
+
 # DRAM bytes (read + write) per level-0 pixel of one launch, measured by ncu
-# on the current kernels (profiles/k_update_level0_4x2048.md,
-# profiles/k_window_level0_4x2048.md: 4 frames, traffic proportional to
-# pixels); absent = not measured for the current build.
-KERNEL_TRAFFIC_PER_PX = {("update", 32): 66.5, ("window", 32): 27.0}
+# on 4 frames (profiles/*.md; traffic proportional to pixels), each with the
+# source file the kernel was built from and its SHA-256 prefix at the time of
+# the capture: a figure whose source has changed since is reported as null.
+KERNEL_TRAFFIC_PER_PX = {("update", 32): (66.5, "k_flow.cu", "1a0e59d8926c09fa"),
+                         ("window", 32): (27.0, "k_flow.cu", "1a0e59d8926c09fa")}
+
+
+def traffic_per_px(name, storage):
+    import hashlib
+    ent = KERNEL_TRAFFIC_PER_PX.get((name, storage))
+    if not ent:
+        return None
+    per_px, src, sha = ent
+    path = os.path.join(ROOT, "paper_2511_14419_gb300", "csrc", src)
+    try:
+        with open(path, "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return per_px if cur == sha else None
 
 
 def log(*a):
@@ -779,11 +812,23 @@ def main():
         ms = sum(k["total_ms"] for k in l0)
         nl = sum(k["launches"] for k in l0)
         achieved = byts / (ms / 1e3) / 1e9
-        tr = KERNEL_TRAFFIC_PER_PX.get((name, wl["precision"]))
+        tr = traffic_per_px(name, wl["precision"])
         roofs.append({"kernel": f"k_{name} level 0", "bound": "hbm", "achieved": achieved, "peak": peak,
                       "unit": "GB/s", "frac": achieved / peak, "peak_kind": f"of {peak_kind}",
                       "traffic": (tr * px) if tr else None, "algorithmic_bytes_per_launch": byts / nl,
                       "avg_launch_ms": ms / nl, "share_of_step": ms / tot})
+    for name, level, label in (("dwt", 1, "k_dwt level 1"), ("expand", 0, "k_expand level 0")):
+        ks = [k for k in kt if k["name"] == name and k["level"] == level]
+        if not ks:
+            continue
+        ms = sum(k["total_ms"] for k in ks)
+        nl = sum(k["launches"] for k in ks)
+        byts = other_bytes(name, wl["precision"], 2) * px
+        achieved = byts / (ms / nl / 1e3) / 1e9
+        tr = traffic_per_px(name, wl["precision"])
+        roofs.append({"kernel": label, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                      "frac": achieved / peak, "peak_kind": f"of {peak_kind}", "traffic": (tr * px) if tr else None,
+                      "algorithmic_bytes_per_launch": byts, "avg_launch_ms": ms / nl, "share_of_step": ms / tot})
     roofs.sort(key=lambda r: -r["share_of_step"])
     roof = roofs[0] if roofs else None
     kernels = {}

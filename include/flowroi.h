@@ -353,7 +353,11 @@ FLOWROI_API int flowroi_get_kernel_times(flowroi_ctx *ctx, flowroi_kernel_time *
  * Limits: width * height <= 2^20 pixels (the fixed array holds the low-low
  * planes of frames that large), width and height >= 16 and multiples of
  * 2^levels, levels in [1, 8].  Larger or malformed requests return
- * FLOWROI_EINVAL and queue nothing; a CUDA error returns FLOWROI_EDEVICE.
+ * FLOWROI_EINVAL and queue nothing.  A failed launch returns FLOWROI_EDEVICE:
+ * the launches before it (the descriptor and the DWT levels below the
+ * failing one) may already be queued, so coeffs is then undefined.  An
+ * error left pending by an earlier, unrelated CUDA call on the calling
+ * thread is cleared first and not reported here.
  *
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any

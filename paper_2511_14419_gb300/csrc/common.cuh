@@ -23,7 +23,10 @@ constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel
 constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
 constexpr int kSalTW = 256, kSalTH = 32;   // saliency, radix-select passes
 constexpr int kMorTW = 256, kMorTH = 64;  // threshold + opening + closing (8 words x 64 rows)
-constexpr int kDwtTW = 64, kDwtTH = 16;   // DWT: band coefficients per block (per band)
+constexpr int kDwtStrip = 60;             // DWT: band columns per warp unit (lanes 1..30, two each)
+constexpr int kDwtWarps = 4;              // DWT: warps (independent units) per block
+constexpr int kDwtMinBlocks = 5;          // DWT: resident blocks per SM the register budget is sized for
+constexpr int kDwtRing = 4;               // DWT: row pairs in a warp's staging ring (kDwtRing - 1 in flight)
 
 // Per-frame reduction block (device), one per frame slot.
 //   [0] min of S (float bits), [1] max of S, [2] select prefix,
@@ -59,6 +62,7 @@ struct MethodConsts {
     // JPEG2000 front end
     int wavelet, dwt_levels, shift;
     float delta[kMaxSubbands];
+    float rdelta[kMaxSubbands];  // float32 reciprocals of delta, rounded to nearest (the quantiser's divisor)
     // optional denoising of the flow input: bilateral radius; the weights
     // as powers of two, w = 2^-(den_ls[offset] + den_lr * (I(q) - I(p))^2),
     // den_ls = -log2 of the spatial weight over the (2 kDenMaxR + 1)^2
@@ -156,6 +160,7 @@ struct FrameDesc {
     int n_adj;                      // per-frame masks ORed into dwt_mask (0: none, dwt_mask is the frame's own)
     const uint8_t *adj[2 * kMaxAdj + 1];
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
+    int dwt_seg[kMaxLevels];        // DWT: band rows per warp unit at each level
     uint8_t *llm[2];                // their RoI masks
 };
 

@@ -10,8 +10,8 @@
 //            L[k] = x[2k]   + floor((H[k-1] + H[k] + 2) / 4)
 //       9/7: four lifting steps (alpha, beta, gamma, delta of the CDF 9/7
 //            factorisation), then low / K and high * K.
-//   - Quantisation (9/7): q = sign(y) floor(|y| / delta_b), decided in
-//     float (IEEE division); 5/3: q = y.
+//   - Quantisation (9/7): q = sign(y) floor(|y| / delta_b), the quotient
+//     rounded to float32 as an IEEE division would; 5/3: q = y.
 //   - A coefficient is RoI when its synthesis support meets the RoI:
 //       5/3: low k <- samples [2k-1, 2k+1], high k <- [2k-1, 2k+3]
 //       9/7: low k <- samples [2k-3, 2k+3], high k <- [2k-3, 2k+5]
@@ -19,19 +19,37 @@
 //     previous level's low-low mask (level 1: the pixel mask).
 //   - RoI coefficients: q <- sign(q) (|q| << s).
 //
-// Tile scheme: a block owns kDwtTW x kDwtTH coefficients of each of the
-// four bands of the level, i.e. a 2*TW x 2*TH input block plus a 4-sample
-// apron loaded with the symmetric extension (for the 4-step 9/7 cone;
-// 5/3 needs 2).  Each column of the extended tile is lifted in a thread's
-// registers; then each (row, 16-sample segment) is lifted in registers
-// from a 24-sample window of that row and its 8 low and 8 high
-// coefficients are quantised, shifted and stored.  Outputs come from window centres, which
-// depend only on in-window samples.  The low-low band goes to a temporary
-// plane for the next level (or, at the last level, into the coefficient
-// plane).  A batch entry's DWT codes the frame named by its dwt_* fields
-// (with an adjacent factor, an earlier frame than the one whose flow the
-// entry computes).
-#include <mutex>
+// Work decomposition: one warp per unit (frame, strip, segment), no shared
+// memory and no barriers.  A strip is 60 band columns: lane j (0..31) owns
+// the 4 input columns 2*bc..2*bc+3 with bc = 60*strip + 2*(j-1), so lanes
+// 0 and 31 hold the symmetric-extension apron of lanes 1..30, whose 2
+// low and 2 high band columns are stored.  A segment is `seg` band rows
+// (per frame and level, FrameDesc::dwt_seg).
+//   - Vertical: the warp walks its input rows in pairs (2n, 2n+1), one pair
+//     per step.  The pairs are staged by cp.async into a warp-private ring
+//     of kDwtRing pairs in shared memory, kDwtRing - 1 pairs ahead; each
+//     lane copies and later reads only its own columns, so no barrier is
+//     needed.  A lane whose columns lie outside the image on the left
+//     (right) copies the two aligned chunks holding their mirror images
+//     and permutes them when it reads.  Each column is
+//     lifted as a stream: the lifting steps of the 9/7 (5/3) factorisation
+//     run with a lag of two pairs (one pair), keeping five (three) values
+//     per column in registers, so each step completes one low and one
+//     high row.  The segment's first 2 (1) steps only fill the pipeline
+//     (the apron rows above it); rows outside the image are read from
+//     their mirror image.
+//   - Horizontal: each completed row is lifted across the warp, lane j
+//     holding (even, odd, even, odd) samples and taking its neighbours'
+//     from lanes j-1 and j+1 by shuffles.
+//   - Masks: mask words (4 columns as bytes) of the pairs needed by the
+//     vertical rule are kept ORed per pair; the horizontal rule works on a
+//     12-bit window of 4-bit column masks from lanes j-1, j, j+1.
+//   - Stores: per step, two 32-bit band coefficients per lane and band
+//     (8-byte stores), the low-low band to a temporary plane for the next
+//     level (or, at the last level, quantised into the coefficient plane).
+// A batch entry's DWT codes the frame named by its dwt_* fields (with an
+// adjacent factor, an earlier frame than the one whose flow the entry
+// computes).
 #include <type_traits>
 
 #include "common.cuh"
@@ -46,10 +64,12 @@ constexpr float kA = -1.586134342059924f, kB = -0.052980118572961f, kG = 0.88291
 // 1/K rounded to float: low samples are scaled by a product (one more
 // rounding than a division, far inside the 9/7 coefficient tolerance).
 constexpr float kInvK = (float)(1.0 / 1.230174104914001);
-constexpr int kDwtHalo = 4;
+constexpr unsigned kFull = 0xffffffffu;
+
+enum { kSrcU8 = 0, kSrcU16 = 1, kSrcLL = 2 };
 
 // Whole-sample symmetric extension of index i into [0, n), for any i: one
-// reflection where it lands inside, else the periodic form (a tile's apron
+// reflection where it lands inside, else the periodic form (a strip's apron
 // reaches more than a signal length past the edge on small images).
 __device__ __forceinline__ int mirror(int i, int n)
 {
@@ -63,485 +83,517 @@ __device__ __forceinline__ int mirror(int i, int n)
     return i <= n - 1 ? i : period - i;
 }
 
-template <typename V>
-__device__ __forceinline__ int32_t quantise(V y, float delta, int wav)
+// Four samples of one row, columns cx..cx+3, as loaded (u8: .x holds four
+// bytes; u16: .x, .y two samples each; low-low plane: one 32-bit value per
+// component).  Columns outside the image come from their mirror image.
+template <int SRC>
+__device__ __forceinline__ uint4 load_row(const unsigned char *row, int cx, int iw, bool vec)
 {
-    if constexpr (std::is_same<V, float>::value) {
-        const float a = __fdiv_rn(fabsf(y), delta);
-        const int32_t m = (int32_t)floorf(a);
-        return y < 0.f ? -m : m;
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if (vec && cx >= 0 && cx + 4 <= iw) {
+        if constexpr (SRC == kSrcU8) {
+            r.x = __ldg(reinterpret_cast<const unsigned *>(row + cx));
+        } else if constexpr (SRC == kSrcU16) {
+            const uint2 t = __ldg(reinterpret_cast<const uint2 *>(row + 2 * cx));
+            r.x = t.x;
+            r.y = t.y;
+        } else {
+            r = __ldg(reinterpret_cast<const uint4 *>(row + 4 * cx));
+        }
+        return r;
+    }
+    unsigned v[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int c = mirror(cx + k, iw);
+        if constexpr (SRC == kSrcU8) v[k] = __ldg(row + c);
+        else if constexpr (SRC == kSrcU16) v[k] = __ldg(reinterpret_cast<const unsigned short *>(row) + c);
+        else v[k] = __ldg(reinterpret_cast<const unsigned *>(row) + c);
+    }
+    if constexpr (SRC == kSrcU8) {
+        r.x = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+    } else if constexpr (SRC == kSrcU16) {
+        r.x = v[0] | (v[1] << 16);
+        r.y = v[2] | (v[3] << 16);
     } else {
-        (void)delta;
-        (void)wav;
-        return (int32_t)y;
+        r = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+    return r;
+}
+
+// Mask bytes of row y at columns cx..cx+3 (any nonzero byte is RoI); 0
+// outside the image (the support rules are clipped to the signal).
+__device__ __forceinline__ uint32_t load_mask(const uint8_t *base, int pitch, int y, int ih, int cx, int iw, bool vec)
+{
+    if (y < 0 || y >= ih) return 0u;
+    const uint8_t *row = base + (size_t)y * pitch;
+    if (vec && cx >= 0 && cx + 4 <= iw) return __ldg(reinterpret_cast<const unsigned *>(row + cx));
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int c = cx + k;
+        if (c >= 0 && c < iw && __ldg(row + c)) m |= 1u << (8 * k);
+    }
+    return m;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Bytes per lane and row of a source: 4 samples (u8 4, u16 8, float/int 16).
+template <int SRC> struct Chunk {
+    static constexpr int bytes = SRC == kSrcU8 ? 4 : (SRC == kSrcU16 ? 8 : 16);
+};
+
+template <int B>
+__device__ __forceinline__ void cp_async(void *dst, const void *src)
+{
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int SRC>
+__device__ __forceinline__ uint4 lds_chunk(const unsigned char *p)
+{
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
+    if constexpr (SRC == kSrcU8) {
+        r.x = *reinterpret_cast<const unsigned *>(p);
+    } else if constexpr (SRC == kSrcU16) {
+        const uint2 t = *reinterpret_cast<const uint2 *>(p);
+        r.x = t.x;
+        r.y = t.y;
+    } else {
+        r = *reinterpret_cast<const uint4 *>(p);
+    }
+    return r;
+}
+template <int SRC>
+__device__ __forceinline__ void sts_chunk(unsigned char *p, const uint4 &r)
+{
+    if constexpr (SRC == kSrcU8) *reinterpret_cast<unsigned *>(p) = r.x;
+    else if constexpr (SRC == kSrcU16) *reinterpret_cast<uint2 *>(p) = make_uint2(r.x, r.y);
+    else *reinterpret_cast<uint4 *>(p) = r;
+}
+
+// Lane kinds of a unit's source columns cx..cx+3.
+enum { kColPacked = 0, kColLeft = 1, kColRight = 2, kColNone = 3 };
+
+// Columns -4..-1 mirror to 4, 3, 2, 1 (chunks c0 = columns 0..3, c1 =
+// 4..7); columns iw..iw+3 mirror to iw-2..iw-5 (c0 = iw-8..iw-5, c1 =
+// iw-4..iw-1).
+template <int SRC>
+__device__ __forceinline__ uint4 mirror_chunks(const uint4 &c0, const uint4 &c1, bool left)
+{
+    uint4 r;
+    if constexpr (SRC == kSrcU8) {
+        r = make_uint4(__byte_perm(c0.x, c1.x, left ? 0x1234 : 0x3456), 0u, 0u, 0u);
+    } else if constexpr (SRC == kSrcU16) {
+        if (left) r = make_uint4(__byte_perm(c1.x, c0.y, 0x7610), __byte_perm(c0.y, c0.x, 0x7610), 0u, 0u);
+        else r = make_uint4(__byte_perm(c1.y, c1.x, 0x7610), __byte_perm(c1.x, c0.y, 0x7610), 0u, 0u);
+    } else {
+        r = left ? make_uint4(c1.x, c0.w, c0.z, c0.y) : make_uint4(c1.z, c1.y, c1.x, c0.w);
+    }
+    return r;
+}
+
+// Loaded samples -> the level's arithmetic type (level 1: DC-shifted).
+// A 16-bit sample u becomes a float exactly as the bit pattern
+// 0x4B000000 | u (= 2^23 + u) minus 2^23 + dc.
+template <int WAV, int SRC, typename V>
+__device__ __forceinline__ void to_vals(const uint4 &r, int dc, float dcf, V (&v)[4])
+{
+    if constexpr (SRC == kSrcLL) {
+        if constexpr (WAV == 97) {
+            v[0] = __uint_as_float(r.x), v[1] = __uint_as_float(r.y), v[2] = __uint_as_float(r.z), v[3] = __uint_as_float(r.w);
+        } else {
+            v[0] = (int)r.x, v[1] = (int)r.y, v[2] = (int)r.z, v[3] = (int)r.w;
+        }
+    } else if constexpr (WAV == 97) {
+        if constexpr (SRC == kSrcU8) {
+            v[0] = __uint_as_float(__byte_perm(r.x, 0x4B00u, 0x5440)) - dcf;
+            v[1] = __uint_as_float(__byte_perm(r.x, 0x4B00u, 0x5441)) - dcf;
+            v[2] = __uint_as_float(__byte_perm(r.x, 0x4B00u, 0x5442)) - dcf;
+            v[3] = __uint_as_float(__byte_perm(r.x, 0x4B00u, 0x5443)) - dcf;
+        } else {
+            v[0] = __uint_as_float(__byte_perm(r.x, 0x4B00u, 0x5410)) - dcf;
+            v[1] = __uint_as_float(__byte_perm(r.x, 0x4B00u, 0x5432)) - dcf;
+            v[2] = __uint_as_float(__byte_perm(r.y, 0x4B00u, 0x5410)) - dcf;
+            v[3] = __uint_as_float(__byte_perm(r.y, 0x4B00u, 0x5432)) - dcf;
+        }
+    } else {
+        if constexpr (SRC == kSrcU8) {
+            v[0] = (int)(r.x & 0xffu) - dc, v[1] = (int)((r.x >> 8) & 0xffu) - dc;
+            v[2] = (int)((r.x >> 16) & 0xffu) - dc, v[3] = (int)(r.x >> 24) - dc;
+        } else {
+            v[0] = (int)(r.x & 0xffffu) - dc, v[1] = (int)(r.x >> 16) - dc;
+            v[2] = (int)(r.y & 0xffffu) - dc, v[3] = (int)(r.y >> 16) - dc;
+        }
     }
 }
 
-__device__ __forceinline__ int32_t roi_up(int32_t q, int s) { return q < 0 ? -((-q) << s) : (q << s); }
+// 4 column masks (bytes, nonzero = RoI) -> bits 0..3.
+__device__ __forceinline__ uint32_t nibble(uint32_t w) { return ((__vcmpne4(w, 0u) & 0x01010101u) * 0x01020408u) >> 24; }
 
-__device__ __forceinline__ uint32_t smem_u32_dwt(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// The low-low plane's 32-bit words as the level's sample type.
-template <typename V>
-__device__ __forceinline__ V __int_as_float_or_int(uint32_t u)
+// Horizontal lifting of one row across the warp: this lane holds samples
+// (e0, o0, e1, o1) at columns 4j..4j+3; the even sample right of o1 is
+// lane j+1's e0, the odd sample left of e0 is lane j-1's o1.
+__device__ __forceinline__ void hlift(float &e0, float &o0, float &e1, float &o1)
 {
-    if constexpr (std::is_same<V, float>::value) return __uint_as_float(u);
-    else return (V)u;
+    o0 += kA * (e0 + e1);
+    o1 += kA * (e1 + __shfl_down_sync(kFull, e0, 1));
+    e0 += kB * (__shfl_up_sync(kFull, o1, 1) + o0);
+    e1 += kB * (o0 + o1);
+    o0 += kG * (e0 + e1);
+    o1 += kG * (e1 + __shfl_down_sync(kFull, e0, 1));
+    e0 += kD * (__shfl_up_sync(kFull, o1, 1) + o0);
+    e1 += kD * (o0 + o1);
+    e0 *= kInvK;
+    e1 *= kInvK;
+    o0 *= kK;
+    o1 *= kK;
+}
+__device__ __forceinline__ void hlift(int &e0, int &o0, int &e1, int &o1)
+{
+    o0 -= (e0 + e1) >> 1;
+    o1 -= (e1 + __shfl_down_sync(kFull, e0, 1)) >> 1;
+    e0 += (__shfl_up_sync(kFull, o1, 1) + o0 + 2) >> 2;
+    e1 += (o0 + o1 + 2) >> 2;
+}
+
+// Quantised, RoI-shifted coefficient.  9/7: floor(RN(|y| / d)) with RN
+// the float32 round-to-nearest quotient, formed from rd = RN(1/d) by one
+// residual correction (Markstein, "Computation of elementary functions on
+// the IBM RISC System/6000 processor", IBM J. Res. Dev. 34(1), 1990: with
+// rd the correctly rounded reciprocal and q0 within an ulp of the
+// quotient, q0 + (|y| - d q0) rd rounded once is the correctly rounded
+// quotient; the residual is exact in a fused multiply-add).  5/3: y itself.
+__device__ __forceinline__ int32_t qroi(float y, float d, float rd, bool roi, int s)
+{
+    const float a = fabsf(y);
+    const float q0 = __fmul_rn(a, rd);
+    const float e = __fmaf_rn(-q0, d, a);
+    const float q1 = __fmaf_rn(e, rd, q0);
+    const int32_t mag = __float2int_rd(q1) << (roi ? s : 0);
+    return y < 0.f ? -mag : mag;
+}
+__device__ __forceinline__ int32_t qroi(int y, float, float, bool roi, int s)
+{
+    return (int32_t)((uint32_t)y << (roi ? s : 0));
+}
+
+template <typename T>
+__device__ __forceinline__ bool aligned(const void *p, int n)
+{
+    return (reinterpret_cast<uintptr_t>(p) & (uintptr_t)(n - 1)) == 0;
+}
+
+// Stores a pair of adjacent values at p (8-byte store when allowed).
+template <typename T>
+__device__ __forceinline__ void st2(T *p, T a, T b, bool vec, bool both)
+{
+    if (vec) {
+        if constexpr (std::is_same<T, float>::value) *reinterpret_cast<float2 *>(p) = make_float2(a, b);
+        else *reinterpret_cast<int2 *>(p) = make_int2((int)a, (int)b);
+    } else {
+        p[0] = a;
+        if (both) p[1] = b;
+    }
+}
+
+// One unit: frame fi, unit index lt within the frame's units of this level.
+template <int WAV, int SRC>
+__device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts &mc, int level, int lt, int lane,
+                                         unsigned char *ring)
+{
+    using V = typename std::conditional<WAV == 97, float, int>::type;
+    constexpr int A = WAV == 97 ? 2 : 1;  // apron pairs above the segment = output lag in pairs
+    const int W = F.W;
+    const int iw = W >> (level - 1), ih = F.H >> (level - 1), bw = iw >> 1, bh = ih >> 1;
+    const int seg = F.dwt_seg[level - 1];
+    const int nst = (bw + kDwtStrip - 1) / kDwtStrip;
+    const int sgi = lt / nst, sti = lt - sgi * nst;
+    const int r0 = sgi * seg, r1 = min(r0 + seg, bh);  // band rows [r0, r1)
+    const int bc = sti * kDwtStrip + 2 * (lane - 1);    // first band column of this lane's outputs
+    const int cx = 2 * bc;                              // first of its 4 input columns
+    const bool last = level == mc.dwt_levels;
+    const bool outl = lane >= 1 && lane <= 30 && bc < bw;
+    const bool both = bc + 1 < bw;
+
+    // Sources: level 1 the raw frame and pixel mask, above it the previous
+    // level's low-low plane (pitch iw) and its mask.
+    const unsigned char *src;
+    size_t spitch;
+    const uint8_t *msrc;
+    int mpitch;
+    bool svec;
+    if constexpr (SRC == kSrcLL) {
+        src = static_cast<const unsigned char *>(F.ll[level % 2]);
+        spitch = (size_t)iw * 4;
+        msrc = F.llm[level % 2];
+        mpitch = iw;
+        svec = aligned<int>(src, 16) && (iw & 3) == 0;
+    } else {
+        src = static_cast<const unsigned char *>(F.dwt_raw);
+        spitch = (size_t)F.raw_pitch;
+        msrc = F.dwt_mask;
+        mpitch = W;
+        const int sa = SRC == kSrcU8 ? 4 : 8;
+        svec = aligned<int>(src, sa) && (F.raw_pitch & (sa - 1)) == 0;
+    }
+    const bool mvec = aligned<int>(msrc, 4) && (mpitch & 3) == 0;
+    const int dc = SRC == kSrcLL ? 0 : F.dc_off;
+    const float dcf = 8388608.f + (float)dc;
+
+    // Outputs.
+    int32_t *const coeffs = F.dwt_coeffs;
+    float *const yf = WAV == 97 ? F.dwt_yf : nullptr;
+    V *const llo = static_cast<V *>(F.ll[(level - 1) % 2]);
+    uint8_t *const llmo = F.llm[(level - 1) % 2];
+    const bool ovec = (bw & 1) == 0 && aligned<int>(coeffs, 8) && (!yf || aligned<int>(yf, 8)) &&
+                      (last || (aligned<int>(llo, 8) && aligned<int>(llmo, 2)));
+    const int b_ll = 3 * mc.dwt_levels, b_hl = 3 * (level - 1), b_lh = b_hl + 1, b_hh = b_hl + 2;
+    const float d_ll = mc.delta[b_ll], d_hl = mc.delta[b_hl], d_lh = mc.delta[b_lh], d_hh = mc.delta[b_hh];
+    const float r_ll = mc.rdelta[b_ll], r_hl = mc.rdelta[b_hl], r_lh = mc.rdelta[b_lh], r_hh = mc.rdelta[b_hh];
+    const int sh = mc.shift;
+    // horizontal rules on the 12-bit window (bit i = column 4j - 4 + i)
+    constexpr uint32_t kE0 = WAV == 97 ? 0x0FEu : 0x038u, kE1 = WAV == 97 ? 0x3F8u : 0x0E0u;
+    constexpr uint32_t kO0 = WAV == 97 ? 0x3FEu : 0x0F8u, kO1 = WAV == 97 ? 0xFF8u : 0x3E0u;
+
+    // Pipeline state per column (see the header).  9/7: the partial sums of
+    // lifting steps 1-4 that the next pair completes (x_odd + a x_even,
+    // x_even + b o1, o1 + g e2, e2 + d o3 of the rows above); 5/3: the
+    // previous pair and the last high sample.
+    V xe[4], xo[4], s1[4], s2[4], s3[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) xe[c] = xo[c] = s1[c] = s2[c] = s3[c] = (V)0;
+    // mask history: ORs of the last three pairs, odd rows of the last four
+    uint32_t p1 = 0, p2 = 0, p3 = 0, od1 = 0, od2 = 0, od3 = 0, od4 = 0;
+
+    // Staging kinds of this lane's columns (constant over the unit).
+    constexpr int CH = Chunk<SRC>::bytes, E = CH / 4;  // chunk bytes, bytes per sample
+    int kind;
+    bool sync_load = false;  // copied by plain loads at issue time (unaligned source, partial lanes)
+    if (cx >= 0 && cx + 4 <= iw) kind = kColPacked, sync_load = !svec;
+    else if (cx >= iw + 4) kind = kColNone;  // feeds no stored output
+    else if (svec && cx == -4 && iw >= 8) kind = kColLeft;
+    else if (svec && cx == iw && iw >= 8 && (iw & 3) == 0) kind = kColRight;
+    else kind = kColPacked, sync_load = true;
+    const bool mask_async = mvec && cx >= 0 && cx + 4 <= iw;
+    // ring layout: raw [kDwtRing][2 rows][2 chunks][32 lanes][CH], masks [kDwtRing][2 rows][32 lanes] words
+    unsigned char *const rraw = ring + lane * CH;
+    uint32_t *const rmask = reinterpret_cast<uint32_t *>(ring + kDwtRing * 4 * 32 * CH) + lane;
+
+    const int n0 = r0 - A, n1 = r1 - 1 + A;  // pair steps n0..n1
+    // Queues the copies of pair n (rows 2n, 2n+1) into its ring slot.
+    auto issue = [&](int n) {
+        const int slot = (n - n0) % kDwtRing;
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int y = 2 * n + h;
+            const unsigned char *rowp = src + (size_t)mirror(y, ih) * spitch;
+            unsigned char *d0 = rraw + (slot * 2 + h) * 2 * 32 * CH, *d1 = d0 + 32 * CH;
+            if (kind == kColPacked) {
+                if (!sync_load) cp_async<CH>(d0, rowp + (size_t)cx * E);
+                else sts_chunk<SRC>(d0, load_row<SRC>(rowp, cx, iw, false));
+            } else if (kind == kColLeft) {
+                cp_async<CH>(d0, rowp);
+                cp_async<CH>(d1, rowp + 4 * E);
+            } else if (kind == kColRight) {
+                cp_async<CH>(d0, rowp + (size_t)(iw - 8) * E);
+                cp_async<CH>(d1, rowp + (size_t)(iw - 4) * E);
+            }
+            uint32_t *md = rmask + (slot * 2 + h) * 32;
+            if (mask_async && y >= 0 && y < ih) cp_async<4>(md, msrc + (size_t)y * mpitch + cx);
+            else *md = load_mask(msrc, mpitch, y, ih, cx, iw, false);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int k = 0; k < kDwtRing - 1; k++) {
+        if (n0 + k <= n1) issue(n0 + k);
+        else cp_async_commit();
+    }
+#pragma unroll 1
+    for (int n = n0; n <= n1; n++) {
+        if (n + kDwtRing - 1 <= n1) issue(n + kDwtRing - 1);
+        else cp_async_commit();
+        cp_async_wait<kDwtRing - 1>();  // pair n has landed
+        const int slot = (n - n0) % kDwtRing;
+        uint4 ra, rb;
+        {
+            const unsigned char *q = rraw + slot * 2 * 2 * 32 * CH;
+            if (kind == kColPacked) {
+                ra = lds_chunk<SRC>(q);
+                rb = lds_chunk<SRC>(q + 2 * 32 * CH);
+            } else if (kind == kColNone) {
+                ra = rb = make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                ra = mirror_chunks<SRC>(lds_chunk<SRC>(q), lds_chunk<SRC>(q + 32 * CH), kind == kColLeft);
+                rb = mirror_chunks<SRC>(lds_chunk<SRC>(q + 2 * 32 * CH), lds_chunk<SRC>(q + 3 * 32 * CH), kind == kColLeft);
+            }
+        }
+        const uint32_t ma = rmask[slot * 2 * 32], mb = rmask[(slot * 2 + 1) * 32];
+        V e[4], o[4], lo[4], hi[4];
+        to_vals<WAV, SRC>(ra, dc, dcf, e);
+        to_vals<WAV, SRC>(rb, dc, dcf, o);
+        uint32_t lowm, highm;
+        const uint32_t pn = ma | mb;
+        if constexpr (WAV == 97) {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                // each lifting step's sum with its earlier operand is formed
+                // one step ahead, so four values per column carry over
+                const float O1 = s1[c] + kA * e[c];   // odd 2n-1, step 1
+                const float E2 = s2[c] + kB * O1;     // even 2n-2, step 2
+                const float O3 = s3[c] + kG * E2;     // odd 2n-3, step 3 (final)
+                const float E4 = xe[c] + kD * O3;     // even 2n-4, step 4 (final)
+                lo[c] = E4 * kInvK;
+                hi[c] = O3 * kK;
+                s1[c] = o[c] + kA * e[c];             // odd 2n+1 with its left even sample
+                s2[c] = e[c] + kB * O1;               // even 2n with its upper odd sample
+                s3[c] = O1 + kG * E2;                 // odd 2n-1 with its upper even sample
+                xe[c] = E2 + kD * O3;                 // even 2n-2 with its upper odd sample
+            }
+            // band row n-2: low from rows [2n-7, 2n-1], high from [2n-7, 2n+1]
+            lowm = od4 | p3 | p2 | p1;
+            highm = lowm | pn;
+            od4 = od3, od3 = od2, od2 = od1, od1 = mb;
+            p3 = p2, p2 = p1, p1 = pn;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; c++) {
+                const int H = xo[c] - ((xe[c] + e[c]) >> 1);      // odd 2n-1
+                const int L = xe[c] + ((s1[c] + H + 2) >> 2);     // even 2n-2
+                lo[c] = L;
+                hi[c] = H;
+                xe[c] = e[c];
+                xo[c] = o[c];
+                s1[c] = H;
+            }
+            // band row n-1: low from rows [2n-3, 2n-1], high from [2n-3, 2n+1]
+            lowm = od2 | p1;
+            highm = lowm | pn;
+            od2 = od1, od1 = mb;
+            p1 = pn;
+        }
+        const int m = n - A;  // band row completed by this step
+        if (m >= r0) {
+            hlift(lo[0], lo[1], lo[2], lo[3]);
+            hlift(hi[0], hi[1], hi[2], hi[3]);
+            const uint32_t nl = nibble(lowm), nh = nibble(highm);
+            const uint32_t pk = nl | (nh << 16);
+            const uint32_t pl = __shfl_up_sync(kFull, pk, 1), pr = __shfl_down_sync(kFull, pk, 1);
+            const uint32_t wl = (pl & 0xfu) | (nl << 4) | ((pr & 0xfu) << 8);
+            const uint32_t wh = ((pl >> 16) & 0xfu) | (nh << 4) | (((pr >> 16) & 0xfu) << 8);
+            if (outl) {
+                const size_t rl = (size_t)m * W, rh = (size_t)(bh + m) * W;
+                // vertical-low row: LL (even) and HL (odd)
+                st2<int32_t>(coeffs + rl + bw + bc, qroi(lo[1], d_hl, r_hl, wl & kO0, sh), qroi(lo[3], d_hl, r_hl, wl & kO1, sh),
+                             ovec, both);
+                if (last) {
+                    st2<int32_t>(coeffs + rl + bc, qroi(lo[0], d_ll, r_ll, wl & kE0, sh), qroi(lo[2], d_ll, r_ll, wl & kE1, sh),
+                                 ovec, both);
+                } else {
+                    st2<V>(llo + (size_t)m * bw + bc, lo[0], lo[2], ovec, both);
+                    const uint8_t m0 = (wl & kE0) ? 1 : 0, m1 = (wl & kE1) ? 1 : 0;
+                    if (ovec) {
+                        *reinterpret_cast<uint16_t *>(llmo + (size_t)m * bw + bc) = (uint16_t)(m0 | (m1 << 8));
+                    } else {
+                        llmo[(size_t)m * bw + bc] = m0;
+                        if (both) llmo[(size_t)m * bw + bc + 1] = m1;
+                    }
+                }
+                // vertical-high row: LH (even) and HH (odd)
+                st2<int32_t>(coeffs + rh + bc, qroi(hi[0], d_lh, r_lh, wh & kE0, sh), qroi(hi[2], d_lh, r_lh, wh & kE1, sh),
+                             ovec, both);
+                st2<int32_t>(coeffs + rh + bw + bc, qroi(hi[1], d_hh, r_hh, wh & kO0, sh), qroi(hi[3], d_hh, r_hh, wh & kO1, sh),
+                             ovec, both);
+                if constexpr (WAV == 97) {
+                    if (yf) {
+                        st2<float>(yf + rl + bw + bc, lo[1], lo[3], ovec, both);
+                        if (last) st2<float>(yf + rl + bc, lo[0], lo[2], ovec, both);
+                        st2<float>(yf + rh + bc, hi[0], hi[2], ovec, both);
+                        st2<float>(yf + rh + bw + bc, hi[1], hi[3], ovec, both);
+                    }
+                }
+            }
+        }
+    }
 }
 
 }  // namespace
 
-// One 1-D lifting pass over N register values (x[0] has even parity).
-// Only positions 1..N-2 are updated (their neighbours exist); the caller's
-// apron keeps the outputs it uses away from the stale ends.
-template <int N>
-__device__ __forceinline__ void lift97(float (&x)[N])
-{
-#pragma unroll
-    for (int i = 1; i < N - 1; i += 2) x[i] += kA * (x[i - 1] + x[i + 1]);
-#pragma unroll
-    for (int i = 2; i < N - 1; i += 2) x[i] += kB * (x[i - 1] + x[i + 1]);
-#pragma unroll
-    for (int i = 1; i < N - 1; i += 2) x[i] += kG * (x[i - 1] + x[i + 1]);
-#pragma unroll
-    for (int i = 2; i < N - 1; i += 2) x[i] += kD * (x[i - 1] + x[i + 1]);
-#pragma unroll
-    for (int i = 0; i < N; i++) x[i] *= (i & 1) ? kK : kInvK;
-}
-
-template <int N>
-__device__ __forceinline__ void lift53(int (&x)[N])
-{
-#pragma unroll
-    for (int i = 1; i < N - 1; i += 2) x[i] -= (x[i - 1] + x[i + 1]) >> 1;
-#pragma unroll
-    for (int i = 2; i < N - 1; i += 2) x[i] += (x[i - 1] + x[i + 1] + 2) >> 2;
-}
-
-template <typename V, int N>
-__device__ __forceinline__ void lift(V (&x)[N])
-{
-    if constexpr (std::is_same<V, float>::value) lift97<N>(x);
-    else lift53<N>(x);
-}
-
-// 1-D mask rule on a register window: low k from [2k+lo0, 2k+lo1], high k
-// from [2k+hi0, 2k+hi1] (relative to the window's even sample e = HALO+2k).
-// Applied to 0/1 bytes, or to words of four such bytes (four columns).
-template <int WAV, typename M, int N>
-__device__ __forceinline__ void mask_rule(const M (&m)[N], int e, M &lo, M &hi)
-{
-    constexpr int lo0 = WAV == 97 ? -3 : -1, lo1 = WAV == 97 ? 3 : 1;
-    constexpr int hi0 = WAV == 97 ? -3 : -1, hi1 = WAV == 97 ? 5 : 3;
-    M a = 0, b = 0;
-#pragma unroll
-    for (int d = lo0; d <= lo1; d++) a |= m[e + d];
-#pragma unroll
-    for (int d = hi0; d <= hi1; d++) b |= m[e + d];
-    lo = a;
-    hi = b;
-}
-
-// A tile's geometry and descriptor fields, gathered by one thread two
-// tiles ahead into shared memory, so the other threads take no dependent
-// global loads per tile.
-struct DwtTile {
-    const void *llin;        // previous level's low-low plane (levels > 1)
-    const uint8_t *mlin;     // ... and its mask
-    const uint8_t *fraw;     // level 1: raw samples
-    const uint8_t *fmask;    // level 1: pixel mask
-    int32_t *coeffs;
-    float *dbg_yf;
-    void *llout;             // this level's low-low plane
-    uint8_t *llmout;         // ... and its mask
-    int W, iw, ih, bw, bh, bx0, by0, raw_pitch, bpp, dc_off, staged, pad;
-};
-
-// Shared-memory plan of k_dwt: the vertically lifted tile s_x [EH][EW+1]
-// (sample type), the mask rows [NB][EH][MW] bytes, at level 1 the staged
-// raw samples [2][EH][EW] (u16), and three tile headers.  Level 1
-// double-buffers the mask and samples so the next tile's copies run during
-// this tile's lifting.
-template <int WAV, bool L1>
-struct DwtSmem {
-    using V = typename std::conditional<WAV == 97, float, int>::type;
-    static constexpr int EW = 2 * kDwtTW + 2 * kDwtHalo, EH = 2 * kDwtTH + 2 * kDwtHalo;  // 136 x 40
-    static constexpr int MW = EW + 4;                                                    // mask row stride
-    static constexpr int NB = L1 ? 2 : 1;
-    static constexpr size_t x_bytes = (size_t)EH * (EW + 1) * sizeof(V);
-    static constexpr size_t m_off = (x_bytes + 15) / 16 * 16;
-    static constexpr size_t r_off = (m_off + (size_t)NB * EH * MW + 15) / 16 * 16;
-    static constexpr size_t h_off = (r_off + (L1 ? (size_t)2 * EH * EW * sizeof(uint16_t) : 0) + 15) / 16 * 16;
-    static constexpr size_t bytes = h_off + 3 * sizeof(DwtTile);
-};
-
-__device__ __forceinline__ void cp_async8(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32_dwt(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void *dst, const void *src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32_dwt(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prior() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// Shared-memory ring of one warp: level 1 sized for 16-bit samples, higher
+// levels for 32-bit low-low values.
+__host__ __device__ constexpr int dwt_ring_bytes(bool l1) { return kDwtRing * 2 * (2 * 32 * (l1 ? 8 : 16) + 32 * 4); }
 
 template <int WAV, bool L1>
-__global__ void __launch_bounds__(256, 3) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
+__global__ void __launch_bounds__(32 * kDwtWarps, kDwtMinBlocks) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
-    using SM = DwtSmem<WAV, L1>;
-    using V = typename SM::V;
-    constexpr int TW = kDwtTW, TH = kDwtTH, HALO = kDwtHalo;
-    constexpr int EW = SM::EW, EH = SM::EH, MW = SM::MW;
-    constexpr int SEG = 8;                  // band outputs per row item
-    constexpr int RW = 2 * SEG + 2 * HALO;  // row window (24)
     extern __shared__ __align__(16) unsigned char dsm[];
-    V (*s_x)[EW + 1] = reinterpret_cast<V (*)[EW + 1]>(dsm);
-    uint8_t *const s_mb = dsm + SM::m_off;                                  // [NB][EH][MW]
-    uint16_t *const s_rb = reinterpret_cast<uint16_t *>(dsm + SM::r_off);  // [2][EH][EW] (level 1)
-    DwtTile *const s_hdr = reinterpret_cast<DwtTile *>(dsm + SM::h_off);    // [3]
-
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    unsigned char *const ring = dsm + (size_t)(threadIdx.x >> 5) * dwt_ring_bytes(L1);
     const int nfr = bd->nframes;
     const int *off = bd->dwt_off[level - 1];
     const int total = __ldg(off + nfr);
-    const bool last = level == mc.dwt_levels;
-
-    // The header of tile t (thread 0).  Level 1: a tile's raw samples and
-    // mask bytes are copied to the staging buffers with cp.async, 8 and 4
-    // bytes per copy (4 samples, 4 mask bytes): sample rows through the
-    // symmetric extension, chunks outside the image left out (the vertical
-    // pass reads a column outside from its mirror image inside), mask
-    // chunks and rows outside the image zero.
-    auto fill_hdr = [&](int t, DwtTile &H) {
-        if (t >= total) return;
-        const int fi = find_frame(off, nfr, t);
+    for (int u = blockIdx.x * wpb + (threadIdx.x >> 5); u < total; u += gridDim.x * wpb) {
+        const int fi = find_frame(off, nfr, u);
+        const int lt = u - __ldg(off + fi);
         const FrameDesc &F = bd->f[fi];
-        H.W = F.W;
-        H.iw = F.W >> (level - 1);
-        H.ih = F.H >> (level - 1);
-        H.bw = H.iw >> 1;
-        H.bh = H.ih >> 1;
-        const int ntx = (H.bw + TW - 1) / TW;
-        const int lt = t - __ldg(off + fi);
-        H.bx0 = (lt % ntx) * TW;
-        H.by0 = (lt / ntx) * TH;
-        H.llin = F.ll[level % 2];
-        H.mlin = F.llm[level % 2];
-        H.fraw = static_cast<const uint8_t *>(F.dwt_raw);
-        H.fmask = F.dwt_mask;
-        H.raw_pitch = F.raw_pitch;
-        H.bpp = F.bpp;
-        H.dc_off = F.dc_off;
-        H.coeffs = F.dwt_coeffs;
-        H.dbg_yf = F.dwt_yf;
-        H.llout = F.ll[(level - 1) % 2];
-        H.llmout = F.llm[(level - 1) % 2];
-        H.staged = L1 && F.bpp == 2 && ((reinterpret_cast<uintptr_t>(F.dwt_raw) | (uintptr_t)F.raw_pitch) & 7) == 0 &&
-                   ((reinterpret_cast<uintptr_t>(F.dwt_mask) | (uintptr_t)F.W) & 3) == 0;
-    };
-    auto issue_async = [&](const DwtTile &H, int buf) {
-        constexpr int NQ = EW / 4;  // 8-byte sample chunks (and 4-byte mask chunks) per row
-        const int ix0 = 2 * H.bx0 - HALO, iy0 = 2 * H.by0 - HALO;
-        uint16_t *rb = s_rb + (size_t)buf * EH * EW;
-        uint8_t *mb = s_mb + (size_t)buf * EH * MW;
-        for (int i = threadIdx.x; i < EH * NQ; i += blockDim.x) {
-            const int r = i / NQ, q = i - r * NQ;
-            const int gy = iy0 + r, gx = ix0 + 4 * q;  // ix0 and W are multiples of 4
-            const bool xin = gx >= 0 && gx + 4 <= H.W;
-            if (xin) cp_async8(rb + r * EW + 4 * q, H.fraw + (size_t)mirror(gy, H.ih) * H.raw_pitch + (size_t)gx * 2);
-            if (xin && gy >= 0 && gy < H.ih) cp_async4(mb + r * MW + 4 * q, H.fmask + (size_t)gy * H.W + gx);
-            else *reinterpret_cast<uint32_t *>(mb + r * MW + 4 * q) = 0u;
+        if constexpr (L1) {
+            if (F.bpp == 1) dwt_unit<WAV, kSrcU8>(F, mc, level, lt, lane, ring);
+            else dwt_unit<WAV, kSrcU16>(F, mc, level, lt, lane, ring);
+        } else {
+            dwt_unit<WAV, kSrcLL>(F, mc, level, lt, lane, ring);
         }
-    };
-    if (threadIdx.x == 0) {
-        fill_hdr(blockIdx.x, s_hdr[0]);
-        fill_hdr(blockIdx.x + gridDim.x, s_hdr[1]);
     }
-    __syncthreads();
-    if (L1) {
-        // prologue: the block's first tile
-        if ((int)blockIdx.x < total && s_hdr[0].staged) issue_async(s_hdr[0], 0);
-        cp_async_commit();
-    }
-
-    int k = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, k++) {
-        const int cur = L1 ? (k & 1) : 0;
-        uint8_t *const s_m = s_mb + (size_t)cur * EH * MW;
-        uint16_t *const s_r = s_rb + (size_t)cur * EH * EW;
-        const DwtTile &H = s_hdr[k % 3];
-        const int W = H.W, iw = H.iw, ih = H.ih, bw = H.bw, bh = H.bh, bx0 = H.bx0, by0 = H.by0;
-        const int ix0 = 2 * bx0 - HALO, iy0 = 2 * by0 - HALO;
-        // Descriptor fields in registers (the output stores below could
-        // otherwise force their reloads).
-        const V *llin = static_cast<const V *>(H.llin);
-        const uint8_t *mlin = H.mlin;
-        const uint8_t *fraw = H.fraw;
-        const uint8_t *fmask = H.fmask;
-        const int raw_pitch = H.raw_pitch, bpp = H.bpp, dc_off = H.dc_off;
-        int32_t *const coeffs = H.coeffs;
-        float *const dbg_yf = H.dbg_yf;
-        V *const llout = static_cast<V *>(H.llout);
-        uint8_t *const llmout = H.llmout;
-        const bool staged = L1 && H.staged;
-
-        if (L1) {
-            // start the next tile's copies into the other buffers (their last
-            // reader, the previous tile's vertical pass, is behind a barrier)
-            const DwtTile &Hn = s_hdr[(k + 1) % 3];
-            if (t + (int)gridDim.x < total && Hn.staged) issue_async(Hn, cur ^ 1);
-            cp_async_commit();
-        }
-
-        if (!staged) {
-            // Samples with symmetric extension, mask clipped (0 outside).
-            // Two adjacent columns per item (ix0 is even, so an in-range pair
-            // is one aligned 2-sample / 2-byte load); a thread issues all of
-            // its items' loads before any shared-memory store, holding level-1
-            // sample pairs packed in one word and every mask pair in one word.
-            const bool xin = ix0 >= 0 && ix0 + EW <= iw;
-            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-            constexpr int NR = (EH + 7) / 8, NP = (EW / 2 + 31) / 32;
-            constexpr int NV = L1 ? 1 : 2;  // registers per sample pair
-            uint32_t sv[NR][NP][NV];
-            uint32_t mm[NR][NP];
-#pragma unroll
-            for (int i = 0; i < NR; i++) {
-                const int r = warp + 8 * i;
-                const int gy = iy0 + r, my = mirror(gy, ih);
-                const bool rin = gy >= 0 && gy < ih;
-                const uint8_t *mrow = L1 ? fmask + (size_t)gy * W : mlin + (size_t)gy * iw;
-#pragma unroll
-                for (int j = 0; j < NP; j++) {
-                    const int c = 2 * (lane + 32 * j), gx = ix0 + c;
-#pragma unroll
-                    for (int e = 0; e < NV; e++) sv[i][j][e] = 0u;
-                    mm[i][j] = 0u;
-                    if (r >= EH || c >= EW) continue;
-                    if constexpr (L1) {
-                        const uint8_t *row = fraw + (size_t)my * raw_pitch;
-                        if (xin && bpp == 2) {
-                            sv[i][j][0] = __ldg(reinterpret_cast<const unsigned *>(row) + (gx >> 1));
-                        } else {
-                            const int m0 = mirror(gx, iw), m1 = mirror(gx + 1, iw);
-                            const uint32_t r0 = bpp == 1 ? __ldg(row + m0) : __ldg(reinterpret_cast<const uint16_t *>(row) + m0);
-                            const uint32_t r1 = bpp == 1 ? __ldg(row + m1) : __ldg(reinterpret_cast<const uint16_t *>(row) + m1);
-                            sv[i][j][0] = r0 | (r1 << 16);
-                        }
-                    } else {
-                        const uint32_t *row = reinterpret_cast<const uint32_t *>(llin) + (size_t)my * iw;
-                        if (xin) {
-                            const uint2 pr = __ldg(reinterpret_cast<const uint2 *>(row + gx));
-                            sv[i][j][0] = pr.x;
-                            sv[i][j][1] = pr.y;
-                        } else {
-                            sv[i][j][0] = __ldg(row + mirror(gx, iw));
-                            sv[i][j][1] = __ldg(row + mirror(gx + 1, iw));
-                        }
-                    }
-                    if (rin) {
-                        if (xin) {
-                            mm[i][j] = __ldg(reinterpret_cast<const unsigned short *>(mrow + gx));
-                        } else {
-                            const uint32_t m0 = gx >= 0 && gx < iw ? __ldg(mrow + gx) : 0;
-                            const uint32_t m1 = gx + 1 >= 0 && gx + 1 < iw ? __ldg(mrow + gx + 1) : 0;
-                            mm[i][j] = m0 | (m1 << 8);
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < NR; i++)
-#pragma unroll
-                for (int j = 0; j < NP; j++) {
-                    const int r = warp + 8 * i, c = 2 * (lane + 32 * j);
-                    if (r >= EH || c >= EW) continue;
-                    if constexpr (L1) {
-                        *reinterpret_cast<uint32_t *>(s_r + r * EW + c) = sv[i][j][0];
-                    } else {
-                        s_x[r][c] = __int_as_float_or_int<V>(sv[i][j][0]);
-                        s_x[r][c + 1] = __int_as_float_or_int<V>(sv[i][j][1]);
-                    }
-                    *reinterpret_cast<uint16_t *>(s_m + r * MW + c) = (uint16_t)mm[i][j];
-                }
-        }
-        if (L1) cp_async_wait_prior();  // this tile's staged copies have landed
-        __syncthreads();
-        // two tiles ahead: its header (the slot's last reader was the
-        // previous tile, behind the barrier above)
-        if (threadIdx.x == 0) fill_hdr(t + 2 * gridDim.x, s_hdr[(k + 2) % 3]);
-
-        // Vertical: threads [0, EW) lift one column each in registers (level
-        // 1 from the staged samples, with the DC shift); the next EW/4
-        // threads turn four columns of the mask at a time (the byte lanes of
-        // a word, made 0/1 first) into (low, high) row masks with the 1-D
-        // rule, in place (the columns are private to their item).
-        if (threadIdx.x < EW) {
-            const int c = threadIdx.x;
-            // a staged column outside the image is read from its mirror image
-            // (clamped: columns that far out feed no stored output)
-            const int cs = staged ? clampi(mirror(ix0 + c, iw) - ix0, 0, EW - 1) : c;
-            V x[EH];
-#pragma unroll
-            for (int j = 0; j < EH; j++) {
-                if constexpr (L1) x[j] = (V)((int)s_r[j * EW + cs] - dc_off);
-                else x[j] = s_x[j][c];
-            }
-            lift<V, EH>(x);
-#pragma unroll
-            for (int j = 0; j < EH; j++) s_x[j][c] = x[j];
-        } else if (threadIdx.x < EW + EW / 4) {
-            const int c = 4 * (threadIdx.x - EW);
-            uint32_t m[EH];
-#pragma unroll
-            for (int j = 0; j < EH; j++)
-                m[j] = __vcmpne4(*reinterpret_cast<const uint32_t *>(s_m + j * MW + c), 0u) & 0x01010101u;
-#pragma unroll
-            for (int kk = 0; kk < TH; kk++) {
-                uint32_t lo, hi;
-                mask_rule<WAV>(m, HALO + 2 * kk, lo, hi);
-                *reinterpret_cast<uint32_t *>(s_m + (HALO + 2 * kk) * MW + c) = lo;      // even rows: low-vertical mask
-                *reinterpret_cast<uint32_t *>(s_m + (HALO + 2 * kk + 1) * MW + c) = hi;  // odd rows: high-vertical mask
-            }
-        }
-        __syncthreads();
-
-        // Horizontal: one (output row, 16-sample segment) per thread.
-        {
-            // a warp takes 16 consecutive rows x 2 segments: with the odd row
-            // stride of s_x its 32 window reads fall in 32 different banks
-            static_assert(2 * TH == 32 && TW / SEG == 8, "row-item map");
-            const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-            const int rr = (wq & 1) * 16 + (lane & 15), sg = (wq >> 1) * 2 + (lane >> 4);  // rr in [0, 2*TH)
-            const int row = HALO + rr;         // even: low-vertical row, odd: high
-            const int gj = by0 + (rr >> 1);
-            const int c0 = sg * 2 * SEG;       // window start (covers its apron)
-            if (rr < 2 * TH && gj < bh) {
-                V x[RW];
-#pragma unroll
-                for (int j = 0; j < RW; j++) x[j] = s_x[row][c0 + j];
-                // the RW mask bytes (0/1) of the window as bits 0..RW-1
-                uint32_t mb = 0;
-#pragma unroll
-                for (int q = 0; q < RW / 4; q++) {
-                    const uint32_t wq = *reinterpret_cast<const uint32_t *>(&s_m[row * MW + c0 + 4 * q]);
-                    mb |= ((wq * 0x01020408u) >> 24 & 0xfu) << (4 * q);
-                }
-                lift<V, RW>(x);
-                const bool vhigh = rr & 1;
-                const int b_lo = vhigh ? 3 * (level - 1) + 1 : 3 * mc.dwt_levels;  // LH or LL
-                const int b_hi = vhigh ? 3 * (level - 1) + 2 : 3 * (level - 1);    // HH or HL
-                const float d_lo = mc.delta[b_lo], d_hi = mc.delta[b_hi];
-                const int ylo = vhigh ? bh + gj : gj;
-                // the 1-D rule on bits: low k <- [e+lo0, e+lo1], high k <- [e+hi0, e+hi1], e = HALO+2k
-                constexpr int lo0 = WAV == 97 ? -3 : -1, lo1 = WAV == 97 ? 3 : 1;
-                constexpr int hi0 = WAV == 97 ? -3 : -1, hi1 = WAV == 97 ? 5 : 3;
-                constexpr uint32_t lom = (1u << (lo1 - lo0 + 1)) - 1u, him = (1u << (hi1 - hi0 + 1)) - 1u;
-                int32_t qh[SEG], ql[SEG];
-#pragma unroll
-                for (int k = 0; k < SEG; k++) {
-                    const bool mlo = (mb >> (HALO + 2 * k + lo0)) & lom;
-                    const bool mhi = (mb >> (HALO + 2 * k + hi0)) & him;
-                    const V ylo_v = x[HALO + 2 * k], yhi_v = x[HALO + 2 * k + 1];
-                    const int32_t a = quantise(yhi_v, d_hi, WAV);
-                    qh[k] = mhi ? roi_up(a, mc.shift) : a;
-                    const int32_t b = quantise(ylo_v, d_lo, WAV);
-                    ql[k] = mlo ? roi_up(b, mc.shift) : b;
-                }
-                const int gi0 = bx0 + sg * SEG;
-                const bool lo_band = vhigh || last;  // low horizontal band to the coefficients (LH or LL)
-                int32_t *const ph = coeffs + (size_t)ylo * W + bw + gi0;
-                int32_t *const pl = coeffs + (size_t)ylo * W + gi0;
-                if (gi0 + SEG <= bw && (bw & 3) == 0) {
-#pragma unroll
-                    for (int k = 0; k < SEG; k += 4) {
-                        *reinterpret_cast<int4 *>(ph + k) = make_int4(qh[k], qh[k + 1], qh[k + 2], qh[k + 3]);
-                        if (lo_band) *reinterpret_cast<int4 *>(pl + k) = make_int4(ql[k], ql[k + 1], ql[k + 2], ql[k + 3]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < SEG; k++) {
-                        if (gi0 + k >= bw) break;
-                        ph[k] = qh[k];
-                        if (lo_band) pl[k] = ql[k];
-                    }
-                }
-                if (!lo_band) {
-#pragma unroll
-                    for (int k = 0; k < SEG; k++) {
-                        if (gi0 + k >= bw) break;
-                        llout[(size_t)gj * bw + gi0 + k] = x[HALO + 2 * k];
-                        llmout[(size_t)gj * bw + gi0 + k] = (mb >> (HALO + 2 * k + lo0)) & lom ? 1 : 0;
-                    }
-                }
-                if constexpr (WAV == 97) {
-                    if (dbg_yf) {
-#pragma unroll
-                        for (int k = 0; k < SEG; k++) {
-                            if (gi0 + k >= bw) break;
-                            dbg_yf[(size_t)ylo * W + bw + gi0 + k] = x[HALO + 2 * k + 1];
-                            if (lo_band) dbg_yf[(size_t)ylo * W + gi0 + k] = x[HALO + 2 * k];
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-    if (L1) cp_async_wait_all();
 }
 
-namespace {
-
-// The kernels take more than the default 48 KB of dynamic shared memory:
-// raise their limit once per device.
-template <int WAV, bool L1>
-void dwt_attr()
+int dwt_default_seg(int bw, int bh)
 {
-    cudaFuncSetAttribute(k_dwt<WAV, L1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DwtSmem<WAV, L1>::bytes);
+    (void)bw;
+    // Short units where a level has few rows: a unit's first steps only
+    // fill its lifting pipeline, and a warp walks its rows one pair at a time.
+    return bh >= 1024 ? 32 : (bh >= 256 ? 16 : 8);
 }
 
-void ensure_dwt_attrs()
+int dwt_units(int bw, int bh, int seg)
 {
-    static std::mutex mu;
-    static bool done[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done[dev]) return;
-    dwt_attr<97, true>();
-    dwt_attr<97, false>();
-    dwt_attr<53, true>();
-    dwt_attr<53, false>();
-    done[dev] = true;
+    if (bw <= 0 || bh <= 0) return 0;
+    return ((bw + kDwtStrip - 1) / kDwtStrip) * ((bh + seg - 1) / seg);
 }
 
-}  // namespace
+int dwt_grid(int units, int persistent_blocks)
+{
+    const int need = (units + kDwtWarps - 1) / kDwtWarps;
+    return need < persistent_blocks ? (need > 0 ? need : 1) : persistent_blocks;
+}
 
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s)
 {
-    ensure_dwt_attrs();
     if (mc.wavelet == 97) {
-        if (level == 1) k_dwt<97, true><<<grid, 256, DwtSmem<97, true>::bytes, s>>>(bd, mc, level);
-        else k_dwt<97, false><<<grid, 256, DwtSmem<97, false>::bytes, s>>>(bd, mc, level);
+        if (level == 1) k_dwt<97, true><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true), s>>>(bd, mc, level);
+        else k_dwt<97, false><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false), s>>>(bd, mc, level);
     } else {
-        if (level == 1) k_dwt<53, true><<<grid, 256, DwtSmem<53, true>::bytes, s>>>(bd, mc, level);
-        else k_dwt<53, false><<<grid, 256, DwtSmem<53, false>::bytes, s>>>(bd, mc, level);
+        if (level == 1) k_dwt<53, true><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true), s>>>(bd, mc, level);
+        else k_dwt<53, false><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false), s>>>(bd, mc, level);
     }
 }
 
 int occupancy_dwt(int wavelet)
 {
-    // the level-1 kernel (staging buffers) bounds the occupancy
-    ensure_dwt_attrs();
     int a = 0, b = 0;
     if (wavelet == 97) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true>, 256, DwtSmem<97, true>::bytes);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false>, 256, DwtSmem<97, false>::bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false));
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true>, 256, DwtSmem<53, true>::bytes);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false>, 256, DwtSmem<53, false>::bytes);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false));
     }
     return a < b ? a : b;
 }

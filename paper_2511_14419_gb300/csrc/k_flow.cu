@@ -1,5 +1,6 @@
 // Farneback displacement estimation: one iteration at one pyramid level,
-// fused (update, box window, 2x2 solve) in one pass over a tile.
+// as two kernels (per-pixel update of G and h, then box window and 2x2
+// solve).
 //
 // Paper: §Optical flow extraction (dense Farneback flow between adjacent
 // frames).  With f1 = the current frame and f2 = its predecessor, and a

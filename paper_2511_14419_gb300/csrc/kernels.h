@@ -19,6 +19,11 @@ void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s)
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
 void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
+// DWT work units (one warp each) of a level whose bands are bw x bh, with
+// seg band rows per unit; blocks needed for `units` (at most the persistent grid).
+int dwt_units(int bw, int bh, int seg);
+int dwt_default_seg(int bw, int bh);  // band rows per unit when no tile table entry applies
+int dwt_grid(int units, int persistent_blocks);
 // Registration to the predecessor: steps 0-7 (level-image sum, row and
 // column FFTs, cross-power spectrum, inverse FFTs, peak, drift).
 void launch_register(const BatchDesc *bd, const MethodConsts &mc, bool half, int step, int grid, cudaStream_t s);

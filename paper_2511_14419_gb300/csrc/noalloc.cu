@@ -112,7 +112,11 @@ extern "C" int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, i
     mc.shift = scale_shift;
     for (int b = 0; b < kMaxSubbands; b++) mc.delta[b] = 1.f;
     if (wavelet == FLOWROI_W97)
-        for (int b = 0; b <= 3 * levels; b++) mc.delta[b] = delta[b];
+        for (int b = 0; b <= 3 * levels; b++) {
+            if (!(delta[b] > 0.f) || !(delta[b] < 1e30f)) return FLOWROI_EINVAL;
+            mc.delta[b] = delta[b];
+        }
+    for (int b = 0; b < kMaxSubbands; b++) mc.rdelta[b] = 1.f / mc.delta[b];  // IEEE float division: rounded to nearest
 
     NaDesc nd;
     memset(&nd, 0, sizeof nd);
@@ -135,12 +139,19 @@ extern "C" int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, i
     F.llm[0] = base + kNaDescBytes + 2 * kNaLLBytes;
     F.llm[1] = base + kNaDescBytes + 2 * kNaLLBytes + kNaLLMBytes;
     for (int l = 1; l <= levels; l++) {
-        const int bw = width >> l, bh = height >> l;
-        nd.tiles[l - 1] = ((bw + kDwtTW - 1) / kDwtTW) * ((bh + kDwtTH - 1) / kDwtTH);
+        F.dwt_seg[l - 1] = dwt_default_seg(width >> l, height >> l);
+        nd.tiles[l - 1] = dwt_units(width >> l, height >> l, F.dwt_seg[l - 1]);
     }
     BatchDesc *bdd = reinterpret_cast<BatchDesc *>(base);
+    // An error left pending by an earlier, unrelated call on this thread
+    // would otherwise be reported as this call's; a launch that fails stops
+    // the sequence there (the levels after it are not queued).
+    cudaGetLastError();
     k_na_desc<<<1, 128, 0, st>>>(nd, bdd);
-    for (int l = 1; l <= levels; l++) launch_dwt(bdd, mc, l, nd.tiles[l - 1], st);
     if (cudaGetLastError() != cudaSuccess) return FLOWROI_EDEVICE;
+    for (int l = 1; l <= levels; l++) {
+        launch_dwt(bdd, mc, l, dwt_grid(nd.tiles[l - 1], 1 << 20), st);
+        if (cudaGetLastError() != cudaSuccess) return FLOWROI_EDEVICE;
+    }
     return FLOWROI_OK;
 }

@@ -475,6 +475,7 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
     F.cc_area = s->cc[2];
     F.ll[0] = s->ll[0];
     F.ll[1] = s->ll[1];
+    for (int l = 0; l < kMaxLevels; l++) F.dwt_seg[l] = dwt_default_seg(s->W >> (l + 1), s->H >> (l + 1));
     F.llm[0] = s->llm[0];
     F.llm[1] = s->llm[1];
     if (e && c->cfg.register_frames) {
@@ -563,7 +564,8 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
             bd.win_off[l][i + 1] = bd.win_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kWinTW, kWinTH) : 0);
         }
         for (int l = 1; l <= D; l++)
-            bd.dwt_off[l - 1][i + 1] = bd.dwt_off[l - 1][i] + (F.do_dwt ? tiles(F.W >> l, F.H >> l, kDwtTW, kDwtTH) : 0);
+            bd.dwt_off[l - 1][i + 1] =
+                bd.dwt_off[l - 1][i] + (F.do_dwt ? dwt_units(F.W >> l, F.H >> l, F.dwt_seg[l - 1]) : 0);
         bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
         bd.mor_off[i + 1] = bd.mor_off[i] + (F.do_flow ? tiles(F.W, F.H, kMorTW, kMorTH) : 0);
         bd.mrg_off[i + 1] = bd.mrg_off[i] + (F.n_adj > 0 ? (int)(((size_t)F.W * F.H + 4095) / 4096) : 0);
@@ -679,7 +681,9 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
         cnt++;
     }
     for (int l = 1; l <= D; l++) {
-        timed(c, st, prof, K_DWT, l, -1, [&] { launch_dwt(dd, mc, l, g(hd->dwt_off[l - 1][n], c->grid_dwt), st); });
+        timed(c, st, prof, K_DWT, l, -1, [&] {
+            launch_dwt(dd, mc, l, pl ? dwt_grid(hd->dwt_off[l - 1][n], c->grid_dwt) : c->grid_dwt, st);
+        });
         cnt++;
     }
     if (c->cfg.codestream_bpp > 0.f) {
@@ -1133,6 +1137,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     for (int b = 0; b < kMaxSubbands; b++) mc.delta[b] = 1.f;
     if (cfg->wavelet == FLOWROI_W97 && quant_steps(cfg->dwt_levels, 12, cfg->delta_base, mc.delta, nullptr, nullptr, nullptr) != 0)
         return fail(FLOWROI_EINVAL, "config.delta_base gives quantisation steps out of range");
+    for (int b = 0; b < kMaxSubbands; b++) mc.rdelta[b] = 1.f / mc.delta[b];  // IEEE float division: rounded to nearest
 
     flowroi_ctx *cp = c.get();
     CK(nullptr, cudaSetDevice(c->device));

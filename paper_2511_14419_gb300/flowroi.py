@@ -278,19 +278,47 @@ def flowroi_get_kernel_times(ctx, cap: int = 256) -> list:
 def flowroi_dwt_roi_noalloc(raw, bit_depth: int, mask, wavelet: int, levels: int, scale_shift: int, delta,
                             coeffs, stream: int = 0, pitch_bytes: int = 0) -> int:
     """JPEG2000 front end of one frame with no allocation (see the C header).
-    raw / mask / coeffs: CUDA tensors (H, W); delta: host float32 array or
-    None (5/3); stream: cudaStream_t handle as an int (0 = default)."""
+    raw: CUDA tensor (H, W) of 1- or 2-byte samples, contiguous or with
+    padded rows (unit column stride; its row stride gives the pitch unless
+    pitch_bytes is passed); mask: uint8 or bool CUDA tensor (H, W); coeffs:
+    int32 CUDA tensor (H, W); delta: host float32 array of 3*levels+1 steps,
+    or None (5/3); stream: cudaStream_t handle as an int (0 = default).
+    Every shape, dtype and size is checked here before the library is
+    called: a smaller mask or coefficient buffer would otherwise be read or
+    written past its end on the device."""
+    import torch
+    if raw.dim() != 2 or mask.dim() != 2 or coeffs.dim() != 2:
+        raise ValueError("raw, mask and coeffs must be 2-D (H, W) tensors")
+    if not (raw.is_cuda and mask.is_cuda and coeffs.is_cuda):
+        raise ValueError("raw, mask and coeffs must be device tensors")
     h, w = int(raw.shape[0]), int(raw.shape[1])
     esz = raw.element_size()
-    rp, rdev = _ptr(raw)
-    mp_, mdev = _ptr(mask)
-    cp, cdev = _ptr(coeffs)
-    if not (rdev and mdev and cdev):
-        raise ValueError("raw, mask and coeffs must be device tensors")
+    if esz not in (1, 2) or raw.is_floating_point():
+        raise ValueError("raw must hold 1- or 2-byte integer samples")
+    if tuple(mask.shape) != (h, w) or tuple(coeffs.shape) != (h, w):
+        raise ValueError(f"mask {tuple(mask.shape)} and coeffs {tuple(coeffs.shape)} must both be {(h, w)}")
+    if mask.dtype not in (torch.uint8, torch.bool):
+        raise ValueError("mask must be uint8 (or bool)")
+    if coeffs.dtype != torch.int32:
+        raise ValueError("coeffs must be int32")
+    mp_, _ = _ptr(mask)
+    cp, _ = _ptr(coeffs)
+    if raw.is_contiguous():
+        rp = raw.data_ptr()
+    else:
+        if raw.stride(1) != 1 or raw.stride(0) < w:
+            raise ValueError("raw must have unit column stride and rows at least W samples apart")
+        rp = raw.data_ptr()
+        if not pitch_bytes:
+            pitch_bytes = raw.stride(0) * esz
+    if pitch_bytes and pitch_bytes < w * esz:
+        raise ValueError("pitch_bytes smaller than a row")
     dp = None
     if delta is not None:
         import numpy as np
         delta = np.ascontiguousarray(delta, dtype=np.float32)
+        if delta.size < 3 * levels + 1:
+            raise ValueError(f"delta needs 3*levels+1 = {3 * levels + 1} steps")
         dp = delta.ctypes.data
     rc = lib().flowroi_dwt_roi_noalloc(rp, w, h, pitch_bytes, U8 if esz == 1 else U16, bit_depth, mp_, wavelet, levels,
                                        scale_shift, dp, cp, stream or None)

@@ -55,6 +55,52 @@ def test_noalloc_matches_streaming_path_on_two_calls():
     assert np.array_equal(out2.cpu().numpy(), ref2)
 
 
+def test_noalloc_allocates_nothing_across_repeated_calls():
+    """The entry point's promise: no device allocation.  torch's allocator
+    counters stay flat across a run of calls (the library's own cudaMalloc
+    calls would not show there, but none exist on this path; the wrapper
+    allocates no tensor either), and the result is the same every time."""
+    prev, cur = pair_u8(seed=4242)
+    mask, ref = _streaming_path([prev.numpy(), cur.numpy()], 8, F.W53, 3)
+    raw = cur.cuda()
+    out = torch.empty((256, 256), dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    a0, r0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(20):
+        F.flowroi_dwt_roi_noalloc(raw, 8, mask, F.W53, 3, 5, None, out)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == a0 and torch.cuda.memory_reserved() == r0
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("pad", [2, 4])
+def test_noalloc_pitched_rows(pad):
+    """Rows of a wider 16-bit tensor (row pitch (W + pad) * 2 bytes: 4-byte
+    aligned with pad 2, 8-byte aligned with pad 4), bit-exact with the
+    streaming path's coefficients of the same frame."""
+    seq = u16(sequence_u16(4545 + pad, 2, 256, 512, 20))
+    mask, ref = _streaming_path([seq[0], seq[1]], 12, F.W97, 5)
+    delta, _, _, _ = F.flowroi_quant_steps(5, 12, 1.0)
+    wide = torch.zeros((256, 512 + pad), dtype=torch.int16, device="cuda")
+    wide[:, :512] = torch.from_numpy(seq[1].view(np.int16).copy()).cuda()
+    out = torch.full((256, 512), -7, dtype=torch.int32, device="cuda")
+    F.flowroi_dwt_roi_noalloc(wide[:, :512], 12, mask, F.W97, 5, 5, delta, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_noalloc_frame_at_the_size_limit():
+    """A 2048 x 512 frame (2^20 pixels, the largest the fixed array holds):
+    its low-low planes fill the array."""
+    seq = u16(sequence_u16(4646, 2, 512, 2048, 40))
+    mask, ref = _streaming_path([seq[0], seq[1]], 12, F.W53, 5)
+    raw = torch.from_numpy(seq[1].view(np.int16).copy()).cuda()
+    out = torch.full((512, 2048), -7, dtype=torch.int32, device="cuda")
+    F.flowroi_dwt_roi_noalloc(raw, 12, mask, F.W53, 5, 5, None, out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
 def test_noalloc_rejects_oversize_and_malformed_requests():
     raw = torch.zeros((2048, 1024), dtype=torch.int16, device="cuda")   # 2^21 pixels > 2^20
     mask = torch.zeros((2048, 1024), dtype=torch.uint8, device="cuda")
@@ -62,9 +108,6 @@ def test_noalloc_rejects_oversize_and_malformed_requests():
     with pytest.raises(F.FlowRoIError) as ei:
         F.flowroi_dwt_roi_noalloc(raw, 12, mask, F.W53, 3, 5, None, out)
     assert ei.value.code == F.EINVAL
-    small = (raw[:64, :48], mask[:64, :48], out[:64, :48])
-    with pytest.raises(ValueError):  # not contiguous
-        F.flowroi_dwt_roi_noalloc(*small[:1], 12, small[1], F.W53, 3, 5, None, small[2])
     raw_ok = torch.zeros((64, 40), dtype=torch.int16, device="cuda")   # 40 not a multiple of 2^4
     with pytest.raises(F.FlowRoIError) as ei:
         F.flowroi_dwt_roi_noalloc(raw_ok, 12, torch.zeros((64, 40), dtype=torch.uint8, device="cuda"), F.W53, 4, 5,
@@ -74,3 +117,14 @@ def test_noalloc_rejects_oversize_and_malformed_requests():
         F.flowroi_dwt_roi_noalloc(raw_ok[:, :32].contiguous(), 12, torch.zeros((64, 32), dtype=torch.uint8, device="cuda"),
                                   F.W97, 3, 5, None, torch.zeros((64, 32), dtype=torch.int32, device="cuda"))
     assert ei.value.code == F.EINVAL
+    # malformed buffers are refused before the library is called: a mask or
+    # coefficient buffer smaller than the frame, the wrong dtypes, 4-byte samples
+    r = torch.zeros((64, 64), dtype=torch.int16, device="cuda")
+    m = torch.zeros((64, 64), dtype=torch.uint8, device="cuda")
+    c = torch.zeros((64, 64), dtype=torch.int32, device="cuda")
+    for args in ((r, m[:32], c), (r, m, c[:, :32].contiguous()), (r, m, c.to(torch.int16)), (r, m.to(torch.int32), c),
+                 (r.to(torch.int32), m, c), (r.float(), m, c)):
+        with pytest.raises(ValueError):
+            F.flowroi_dwt_roi_noalloc(args[0], 12, args[1], F.W53, 3, 5, None, args[2])
+    with pytest.raises(ValueError):  # too few quantisation steps
+        F.flowroi_dwt_roi_noalloc(r, 12, m, F.W97, 3, 5, np.ones(5, np.float32), c)
