@@ -131,6 +131,29 @@ def traffic_per_px(name, storage):
     return per_px if cur == sha else None
 
 
+# Tile table the contexts are created with (set in main: --tiles; by default
+# the committed table for the workload's storage type, if there is one).
+TILE_TABLE = None
+
+
+def default_tiles(storage):
+    path = os.path.join(ROOT, "paper_2511_14419_gb300", "tiles", f"gb300_fp{storage}.json")
+    return path if os.path.exists(path) else None
+
+
+def tile_kw():
+    return {"tile_table": TILE_TABLE} if TILE_TABLE else {}
+
+
+def tiles_desc():
+    if not TILE_TABLE:
+        return "built-in shapes"
+    import hashlib
+    with open(TILE_TABLE, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:12]
+    return f"{os.path.relpath(TILE_TABLE, ROOT)} (sha256 {sha})"
+
+
 def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
@@ -278,7 +301,7 @@ def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampl
                reg_level=wl.get("reg_level", 2), flags=F.MANUAL | (F.PLAIN if plain else 0), device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     res = {}
-    with F.Context(**cfg) as ctx:
+    with F.Context(**cfg, **tile_kw()) as ctx:
         stream = torch.cuda.ExternalStream(F.flowroi_compute_stream(ctx.h))
         t = 0
 
@@ -346,7 +369,7 @@ def run_e2e(F, wl, frames, steps, warmup):
                reg_level=wl.get("reg_level", 2), flags=F.MANUAL,
                device=torch.cuda.current_device())
     res = {}
-    with F.Context(**cfg) as ctx:
+    with F.Context(**cfg, **tile_kw()) as ctx:
         t = 0
 
         def submit_step():
@@ -404,7 +427,7 @@ def run_codestream(F, wl, frames, steps, warmup, profile_steps=3):
     cap = F.flowroi_codestream_bound(W, H, L) // 4
     outs = [torch.empty(cap, dtype=torch.uint8, device="cuda") for _ in range(S)]
     res = {}
-    with F.Context(**cfg) as ctx:
+    with F.Context(**cfg, **tile_kw()) as ctx:
         t = 0
         lens = []
 
@@ -467,7 +490,7 @@ def run_serving(F, wl, rate_fps: float, duration_s: float, burst_per_stream: int
     out = {}
     masks = {sz: torch.empty(sz, dtype=torch.uint8).pin_memory() for sz in set(sizes)}
     coefs = {sz: torch.empty(sz, dtype=torch.int32).pin_memory() for sz in set(sizes)}
-    with F.Context(**cfg) as ctx:
+    with F.Context(**cfg, **tile_kw()) as ctx:
         nxt = [0] * S
         pending = []  # (stream, frame index)
 
@@ -687,7 +710,7 @@ def config_of(name, wl):
             "pyr_levels": wl["pyr_levels"], "dwt": f"{wl['wavelet'] // 10}/{wl['wavelet'] % 10} x{wl['dwt_levels']}",
             "storage": "fp16" if wl["precision"] == 16 else "fp32", "denoise": bool(wl.get("denoise", 0)),
             "min_area": wl.get("min_area", 0), "register": bool(wl.get("register_frames", 0)),
-            "l2": "inputs larger than L2 (each step touches ~2.5 GB of frames and fields)"}
+            "l2": "inputs larger than L2 (each step touches ~2.5 GB of frames and fields)", "tiles": tiles_desc()}
 
 
 def main():
@@ -697,6 +720,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="batched_16x2048", choices=sorted(WORKLOADS))
+    ap.add_argument("--tiles", default="default",
+                    help="tile table JSON for every context: a path, 'none' (built-in shapes) or 'default' "
+                         "(the committed table for the workload's storage type, if any)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
@@ -709,6 +735,11 @@ def main():
         ap.error("--burst must be in [1, 8]: the serving context keeps 8 results per stream")
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
+    global TILE_TABLE
+    if args.tiles == "default":
+        TILE_TABLE = default_tiles(wl["precision"])
+    elif args.tiles != "none":
+        TILE_TABLE = os.path.abspath(args.tiles)
     ws, rank, local = dist_env()
     if args.impl == "reference":
         reference_arm(args, wl, ws, rank)
@@ -730,7 +761,7 @@ def main():
             print(json.dumps({"metric": METRIC, "workload": args.workload, "n_gpus": ws, "data": "synthetic",
                               "streams": wl["streams"], "sizes": wl["sizes"],
                               "poisson_rate_fps": args.serving_rate, "poisson_seconds": args.serving_seconds,
-                              "burst_frames_per_stream": args.burst, "phases": res}), flush=True)
+                              "burst_frames_per_stream": args.burst, "tiles": tiles_desc(), "phases": res}), flush=True)
         return
     frames = make_frames(wl, f"cuda:{local}")
     if "codestream_bpp" in wl:

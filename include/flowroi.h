@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define FLOWROI_ABI_VERSION 3
+#define FLOWROI_ABI_VERSION 4
 
 /* Exported symbols (the library is built with hidden default visibility). */
 #if defined(__GNUC__)
@@ -162,6 +162,11 @@ typedef struct flowroi_config {
      * bits per pixel of pass data; fetch it with flowroi_get_codestream.
      * 0 = off. (0) */
     float codestream_bpp;
+    /* Tile table (launch and tile shapes per frame width class, see
+     * flowroi_autotune): path of a JSON file read at create, or NULL for
+     * the built-in shapes.  Not a method parameter: results do not depend
+     * on it, only the time they take.  (NULL) */
+    const char *tile_table;
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and
@@ -434,6 +439,49 @@ FLOWROI_API int flowroi_get_codestream(flowroi_ctx *ctx, int64_t stream_id, int6
 /* A container capacity that always suffices for a width x height plane of
  * `levels` levels (0 for a malformed geometry). */
 FLOWROI_API uint64_t flowroi_codestream_bound(int width, int height, int levels);
+
+/* ---- tile shapes -------------------------------------------------------
+ * The paper has no counterpart: these calls choose how the kernels cut
+ * their work, not what they compute (every choice gives bit-identical
+ * results).  A tile table is JSON text:
+ *   {"format": "flowroi-tiles-1", "device": "...", "entries": [ENTRY, ...]}
+ * with ENTRY one of (storage 32 or 16; w the width class 256, 512, 1024,
+ * 2048, 4096 or 8192 that holds the frames of level-0 width <= w and
+ * > w/2, the last one every wider frame):
+ *   {"param": "dwt_seg", "w": W, "storage": S, "level": l, "value": v}
+ *        DWT band rows per warp unit at level l, v in [4, 256]
+ *   {"param": "update_rows", "storage": S, "value": v}
+ *        rows per thread of a displacement-update tile column, 4 or 8
+ *   {"param": "saliency_rows", "w": W, "storage": S, "value": v}
+ *        rows of a saliency tile, a multiple of 8 up to 128
+ *   {"param": "blocks_per_sm", "kernel": K, "storage": S, "value": v}
+ *        persistent grid of K (expand, update, window, mask, dwt): min(v,
+ *        occupancy) blocks per SM, v in [1, 32]
+ *   {"param": "dwt_variant", "storage": S, "value": v}
+ *        register budget of the DWT kernel: 5 or 6 resident blocks per SM
+ * (entries may also carry "ms", ignored).  Shapes without an entry keep
+ * the built-in choice.  Per-width entries apply to each frame of a batch
+ * by its own width; the others to the context.
+ *
+ * flowroi_tiles_check: validates a table (no device needed); FLOWROI_OK or
+ * FLOWROI_EINVAL with a message in err (caller-owned, err_cap bytes).
+ * flowroi_set_tiles: replaces ctx's table (NULL = built-in shapes); waits
+ * for the context's queued work, and its captured graphs are rebuilt at
+ * the next batch.  FLOWROI_EINVAL on a malformed table (ctx unchanged).
+ * flowroi_get_tiles: ctx's table as JSON into out (cap bytes, NUL
+ * included); *out_len = its length; FLOWROI_ERANGE when it does not fit.
+ * flowroi_autotune: times candidate shapes on synthetic 12-bit frames of
+ * each of the nsizes sizes (`streams` streams per batch, `steps` batches
+ * per candidate) with cfg's method settings on cfg's device, by coordinate
+ * descent on the summed device time of the kernels each shape affects,
+ * and writes the chosen table (JSON) into out; *out_len = its length
+ * (FLOWROI_ERANGE when out_cap is too small).  Takes seconds to minutes
+ * and the device memory of `streams` streams of the largest size. */
+FLOWROI_API int flowroi_tiles_check(const char *json, char *err, uint64_t err_cap);
+FLOWROI_API int flowroi_set_tiles(flowroi_ctx *ctx, const char *json);
+FLOWROI_API int flowroi_get_tiles(flowroi_ctx *ctx, char *out, uint64_t cap, uint64_t *out_len);
+FLOWROI_API int flowroi_autotune(const flowroi_config *cfg, int nsizes, const int *widths, const int *heights,
+                                 int streams, int steps, char *out, uint64_t out_cap, uint64_t *out_len);
 
 /* Library ABI version (FLOWROI_ABI_VERSION). */
 FLOWROI_API int flowroi_abi_version(void);

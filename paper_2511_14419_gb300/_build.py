@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libflowroi.so")
-SOURCES = ["runtime.cu", "k_expand.cu", "k_flow.cu", "k_mask.cu", "k_dwt.cu", "k_denoise.cu", "k_cc.cu", "k_reg.cu", "quant_steps.cu", "noalloc.cu", "k_ebcot.cu"]
+SOURCES = ["runtime.cu", "k_expand.cu", "k_flow.cu", "k_mask.cu", "k_dwt.cu", "k_denoise.cu", "k_cc.cu", "k_reg.cu", "quant_steps.cu", "noalloc.cu", "k_ebcot.cu", "tiles.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

@@ -21,11 +21,11 @@ constexpr int kMaxAdj = 4;                 // largest adjacent factor (masks of 
 constexpr int kExpTW = 256, kExpTH = 16;   // pyramid + polynomial expansion
 constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
 constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
-constexpr int kSalTW = 256, kSalTH = 32;   // saliency, radix-select passes
+constexpr int kSalTW = 256, kSalTH = 32;   // radix-select passes (saliency: kSalSub-row strips, per frame)
+constexpr int kSalSub = 8;                 // saliency: rows per staged strip
 constexpr int kMorTW = 256, kMorTH = 64;  // threshold + opening + closing (8 words x 64 rows)
 constexpr int kDwtStrip = 60;             // DWT: band columns per warp unit (lanes 1..30, two each)
 constexpr int kDwtWarps = 4;              // DWT: warps (independent units) per block
-constexpr int kDwtMinBlocks = 5;          // DWT: resident blocks per SM the register budget is sized for
 constexpr int kDwtRing = 4;               // DWT: row pairs in a warp's staging ring (kDwtRing - 1 in flight)
 
 // Per-frame reduction block (device), one per frame slot.
@@ -161,6 +161,7 @@ struct FrameDesc {
     const uint8_t *adj[2 * kMaxAdj + 1];
     void *ll[2];                    // DWT low-low temporaries ((W/2)*(H/2) elements)
     int dwt_seg[kMaxLevels];        // DWT: band rows per warp unit at each level
+    int sal_strips;                 // saliency: tiles of kSalSub x sal_strips rows
     uint8_t *llm[2];                // their RoI masks
 };
 
@@ -174,7 +175,8 @@ struct BatchDesc {
     int flow_off[kMaxLevels][kMaxBatch + 1];   // update tiles
     int win_off[kMaxLevels][kMaxBatch + 1];    // window tiles
     int dwt_off[kMaxLevels][kMaxBatch + 1];
-    int sal_off[kMaxBatch + 1];     // frames with a predecessor only
+    int sal_off[kMaxBatch + 1];     // frames with a predecessor only (kSalTW x kSalTH tiles)
+    int sal2_off[kMaxBatch + 1];    // the saliency kernel's own tiles (kSalTW x kSalSub * sal_strips)
     int mor_off[kMaxBatch + 1];     // every flow frame
     int frm_off[kMaxBatch + 1];     // one unit per frame (init / select-find)
     int mrg_off[kMaxBatch + 1];     // adjacent-mask merge: 4096-byte units of entries with n_adj > 0

@@ -71,26 +71,33 @@ enum { kSrcU8 = 0, kSrcU16 = 1, kSrcLL = 2 };
 // Whole-sample symmetric extension of index i into [0, n), for any i: one
 // reflection where it lands inside, else the periodic form (a strip's apron
 // reaches more than a signal length past the edge on small images).
-__device__ __forceinline__ int mirror(int i, int n)
+__device__ __noinline__ int mirror_far(int i, int n)
 {
-    if (i >= 0 && i < n) return i;
-    if (i < 0 && -i < n) return -i;
-    if (i >= n && i <= 2 * (n - 1)) return 2 * (n - 1) - i;
     if (n == 1) return 0;
     const int period = 2 * (n - 1);
     i %= period;
     if (i < 0) i += period;
     return i <= n - 1 ? i : period - i;
 }
+__device__ __forceinline__ int mirror(int i, int n)
+{
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && -i < n) return -i;
+    if (i >= n && i <= 2 * (n - 1)) return 2 * (n - 1) - i;
+    return mirror_far(i, n);
+}
 
 // Four samples of one row, columns cx..cx+3, as loaded (u8: .x holds four
 // bytes; u16: .x, .y two samples each; low-low plane: one 32-bit value per
 // component).  Columns outside the image come from their mirror image.
 template <int SRC>
+__device__ __noinline__ uint4 load_row_slow(const unsigned char *row, int cx, int iw);
+template <int SRC>
 __device__ __forceinline__ uint4 load_row(const unsigned char *row, int cx, int iw, bool vec)
 {
     uint4 r = make_uint4(0u, 0u, 0u, 0u);
-    if (vec && cx >= 0 && cx + 4 <= iw) {
+    if (!(vec && cx >= 0 && cx + 4 <= iw)) return load_row_slow<SRC>(row, cx, iw);
+    {
         if constexpr (SRC == kSrcU8) {
             r.x = __ldg(reinterpret_cast<const unsigned *>(row + cx));
         } else if constexpr (SRC == kSrcU16) {
@@ -102,6 +109,11 @@ __device__ __forceinline__ uint4 load_row(const unsigned char *row, int cx, int 
         }
         return r;
     }
+}
+template <int SRC>
+__device__ __noinline__ uint4 load_row_slow(const unsigned char *row, int cx, int iw)
+{
+    uint4 r = make_uint4(0u, 0u, 0u, 0u);
     unsigned v[4];
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -123,11 +135,8 @@ __device__ __forceinline__ uint4 load_row(const unsigned char *row, int cx, int 
 
 // Mask bytes of row y at columns cx..cx+3 (any nonzero byte is RoI); 0
 // outside the image (the support rules are clipped to the signal).
-__device__ __forceinline__ uint32_t load_mask(const uint8_t *base, int pitch, int y, int ih, int cx, int iw, bool vec)
+__device__ __noinline__ uint32_t load_mask_slow(const uint8_t *row, int cx, int iw)
 {
-    if (y < 0 || y >= ih) return 0u;
-    const uint8_t *row = base + (size_t)y * pitch;
-    if (vec && cx >= 0 && cx + 4 <= iw) return __ldg(reinterpret_cast<const unsigned *>(row + cx));
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 4; k++) {
@@ -135,6 +144,13 @@ __device__ __forceinline__ uint32_t load_mask(const uint8_t *base, int pitch, in
         if (c >= 0 && c < iw && __ldg(row + c)) m |= 1u << (8 * k);
     }
     return m;
+}
+__device__ __forceinline__ uint32_t load_mask(const uint8_t *base, int pitch, int y, int ih, int cx, int iw, bool vec)
+{
+    if (y < 0 || y >= ih || cx + 4 <= 0 || cx >= iw) return 0u;
+    const uint8_t *row = base + (size_t)y * pitch;
+    if (vec && cx >= 0 && cx + 4 <= iw) return __ldg(reinterpret_cast<const unsigned *>(row + cx));
+    return load_mask_slow(row, cx, iw);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -236,7 +252,15 @@ __device__ __forceinline__ void to_vals(const uint4 &r, int dc, float dcf, V (&v
 }
 
 // 4 column masks (bytes, nonzero = RoI) -> bits 0..3.
-__device__ __forceinline__ uint32_t nibble(uint32_t w) { return ((__vcmpne4(w, 0u) & 0x01010101u) * 0x01020408u) >> 24; }
+__device__ __forceinline__ uint32_t nibble(uint32_t w)
+{
+    // bit 7 of each byte becomes "byte != 0": its low 7 bits plus 0x7f
+    // carry into bit 7 exactly when they are nonzero, and never beyond
+    // the byte (at most 0x7f + 0x7f); OR-ing the byte keeps a set bit 7.
+    // The four bit 7s are then gathered into bits 0..3 by one multiply.
+    const uint32_t t = (((w & 0x7f7f7f7fu) + 0x7f7f7f7fu) | w) & 0x80808080u;
+    return ((t >> 7) * 0x01020408u) >> 24;
+}
 
 // Horizontal lifting of one row across the warp: this lane holds samples
 // (e0, o0, e1, o1) at columns 4j..4j+3; the even sample right of o1 is
@@ -359,6 +383,8 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
     const float d_ll = mc.delta[b_ll], d_hl = mc.delta[b_hl], d_lh = mc.delta[b_lh], d_hh = mc.delta[b_hh];
     const float r_ll = mc.rdelta[b_ll], r_hl = mc.rdelta[b_hl], r_lh = mc.rdelta[b_lh], r_hh = mc.rdelta[b_hh];
     const int sh = mc.shift;
+    const int ohl = bw + bc;                  // column of this lane's high-horizontal outputs
+    const size_t hoff = (size_t)bh * W;       // offset of the vertical-high half of the plane
     // horizontal rules on the 12-bit window (bit i = column 4j - 4 + i)
     constexpr uint32_t kE0 = WAV == 97 ? 0x0FEu : 0x038u, kE1 = WAV == 97 ? 0x3F8u : 0x0E0u;
     constexpr uint32_t kO0 = WAV == 97 ? 0x3FEu : 0x0F8u, kO1 = WAV == 97 ? 0xFF8u : 0x3E0u;
@@ -389,8 +415,10 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
 
     const int n0 = r0 - A, n1 = r1 - 1 + A;  // pair steps n0..n1
     // Queues the copies of pair n (rows 2n, 2n+1) into its ring slot.
+    int islot = 0, cslot = 0;  // ring slots of the next pair to issue and to consume
     auto issue = [&](int n) {
-        const int slot = (n - n0) % kDwtRing;
+        const int slot = islot;
+        islot = islot == kDwtRing - 1 ? 0 : islot + 1;
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int y = 2 * n + h;
@@ -412,7 +440,7 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
         }
         cp_async_commit();
     };
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < kDwtRing - 1; k++) {
         if (n0 + k <= n1) issue(n0 + k);
         else cp_async_commit();
@@ -422,7 +450,8 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
         if (n + kDwtRing - 1 <= n1) issue(n + kDwtRing - 1);
         else cp_async_commit();
         cp_async_wait<kDwtRing - 1>();  // pair n has landed
-        const int slot = (n - n0) % kDwtRing;
+        const int slot = cslot;
+        cslot = cslot == kDwtRing - 1 ? 0 : cslot + 1;
         uint4 ra, rb;
         {
             const unsigned char *q = rraw + slot * 2 * 2 * 32 * CH;
@@ -490,34 +519,37 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
             const uint32_t wl = (pl & 0xfu) | (nl << 4) | ((pr & 0xfu) << 8);
             const uint32_t wh = ((pl >> 16) & 0xfu) | (nh << 4) | (((pr >> 16) & 0xfu) << 8);
             if (outl) {
-                const size_t rl = (size_t)m * W, rh = (size_t)(bh + m) * W;
+                int32_t *const cl = coeffs + (size_t)m * W;  // band row m of the vertical-low half
+                int32_t *const ch = cl + hoff;               // ... and of the vertical-high half
                 // vertical-low row: LL (even) and HL (odd)
-                st2<int32_t>(coeffs + rl + bw + bc, qroi(lo[1], d_hl, r_hl, wl & kO0, sh), qroi(lo[3], d_hl, r_hl, wl & kO1, sh),
-                             ovec, both);
+                st2<int32_t>(cl + ohl, qroi(lo[1], d_hl, r_hl, wl & kO0, sh), qroi(lo[3], d_hl, r_hl, wl & kO1, sh), ovec,
+                             both);
                 if (last) {
-                    st2<int32_t>(coeffs + rl + bc, qroi(lo[0], d_ll, r_ll, wl & kE0, sh), qroi(lo[2], d_ll, r_ll, wl & kE1, sh),
-                                 ovec, both);
+                    st2<int32_t>(cl + bc, qroi(lo[0], d_ll, r_ll, wl & kE0, sh), qroi(lo[2], d_ll, r_ll, wl & kE1, sh), ovec,
+                                 both);
                 } else {
-                    st2<V>(llo + (size_t)m * bw + bc, lo[0], lo[2], ovec, both);
+                    const size_t lo_at = (size_t)m * bw + bc;
+                    st2<V>(llo + lo_at, lo[0], lo[2], ovec, both);
                     const uint8_t m0 = (wl & kE0) ? 1 : 0, m1 = (wl & kE1) ? 1 : 0;
                     if (ovec) {
-                        *reinterpret_cast<uint16_t *>(llmo + (size_t)m * bw + bc) = (uint16_t)(m0 | (m1 << 8));
+                        *reinterpret_cast<uint16_t *>(llmo + lo_at) = (uint16_t)(m0 | (m1 << 8));
                     } else {
-                        llmo[(size_t)m * bw + bc] = m0;
-                        if (both) llmo[(size_t)m * bw + bc + 1] = m1;
+                        llmo[lo_at] = m0;
+                        if (both) llmo[lo_at + 1] = m1;
                     }
                 }
                 // vertical-high row: LH (even) and HH (odd)
-                st2<int32_t>(coeffs + rh + bc, qroi(hi[0], d_lh, r_lh, wh & kE0, sh), qroi(hi[2], d_lh, r_lh, wh & kE1, sh),
-                             ovec, both);
-                st2<int32_t>(coeffs + rh + bw + bc, qroi(hi[1], d_hh, r_hh, wh & kO0, sh), qroi(hi[3], d_hh, r_hh, wh & kO1, sh),
-                             ovec, both);
+                st2<int32_t>(ch + bc, qroi(hi[0], d_lh, r_lh, wh & kE0, sh), qroi(hi[2], d_lh, r_lh, wh & kE1, sh), ovec,
+                             both);
+                st2<int32_t>(ch + ohl, qroi(hi[1], d_hh, r_hh, wh & kO0, sh), qroi(hi[3], d_hh, r_hh, wh & kO1, sh), ovec,
+                             both);
                 if constexpr (WAV == 97) {
                     if (yf) {
-                        st2<float>(yf + rl + bw + bc, lo[1], lo[3], ovec, both);
-                        if (last) st2<float>(yf + rl + bc, lo[0], lo[2], ovec, both);
-                        st2<float>(yf + rh + bc, hi[0], hi[2], ovec, both);
-                        st2<float>(yf + rh + bw + bc, hi[1], hi[3], ovec, both);
+                        float *const fl = yf + (size_t)m * W, *const fh = fl + hoff;
+                        st2<float>(fl + ohl, lo[1], lo[3], ovec, both);
+                        if (last) st2<float>(fl + bc, lo[0], lo[2], ovec, both);
+                        st2<float>(fh + bc, hi[0], hi[2], ovec, both);
+                        st2<float>(fh + ohl, hi[1], hi[3], ovec, both);
                     }
                 }
             }
@@ -531,8 +563,10 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
 // levels for 32-bit low-low values.
 __host__ __device__ constexpr int dwt_ring_bytes(bool l1) { return kDwtRing * 2 * (2 * 32 * (l1 ? 8 : 16) + 32 * 4); }
 
-template <int WAV, bool L1>
-__global__ void __launch_bounds__(32 * kDwtWarps, kDwtMinBlocks) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
+// MB: resident blocks per SM the register budget is sized for (5: no
+// spills; 6: more warps, a few spilled values).
+template <int WAV, bool L1, int MB>
+__global__ void __launch_bounds__(32 * kDwtWarps, MB) k_dwt(const BatchDesc *__restrict__ bd, MethodConsts mc, int level)
 {
     extern __shared__ __align__(16) unsigned char dsm[];
     const int lane = threadIdx.x & 31;
@@ -574,28 +608,42 @@ int dwt_grid(int units, int persistent_blocks)
     return need < persistent_blocks ? (need > 0 ? need : 1) : persistent_blocks;
 }
 
-void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s)
+namespace {
+template <int MB>
+void launch_dwt_mb(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s)
 {
     if (mc.wavelet == 97) {
-        if (level == 1) k_dwt<97, true><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true), s>>>(bd, mc, level);
-        else k_dwt<97, false><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false), s>>>(bd, mc, level);
+        if (level == 1) k_dwt<97, true, MB><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true), s>>>(bd, mc, level);
+        else k_dwt<97, false, MB><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false), s>>>(bd, mc, level);
     } else {
-        if (level == 1) k_dwt<53, true><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true), s>>>(bd, mc, level);
-        else k_dwt<53, false><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false), s>>>(bd, mc, level);
+        if (level == 1) k_dwt<53, true, MB><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true), s>>>(bd, mc, level);
+        else k_dwt<53, false, MB><<<grid, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false), s>>>(bd, mc, level);
     }
 }
-
-int occupancy_dwt(int wavelet)
+template <int MB>
+int occupancy_dwt_mb(int wavelet)
 {
     int a = 0, b = 0;
     if (wavelet == 97) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<97, true, MB>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<97, false, MB>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false));
     } else {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_dwt<53, true, MB>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(true));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_dwt<53, false, MB>, 32 * kDwtWarps, kDwtWarps * dwt_ring_bytes(false));
     }
     return a < b ? a : b;
+}
+}  // namespace
+
+void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, int variant, cudaStream_t s)
+{
+    if (variant == 6) launch_dwt_mb<6>(bd, mc, level, grid, s);
+    else launch_dwt_mb<5>(bd, mc, level, grid, s);
+}
+
+int occupancy_dwt(int wavelet, int variant)
+{
+    return variant == 6 ? occupancy_dwt_mb<6>(wavelet) : occupancy_dwt_mb<5>(wavelet);
 }
 
 }  // namespace flowroi

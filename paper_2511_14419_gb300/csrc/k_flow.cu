@@ -70,13 +70,14 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 
 // ---------------------------------------------------------------- update
 // Per pixel G = A^T A and h = A^T db (5 values) into five planes.  One
-// thread owns a column of kUpdRows rows of a 256-wide row band, so its
-// loads for those pixels are in flight together; no shared memory, full
-// occupancy hides the gather latency.
-template <typename T>
+// thread owns a column of ROWS rows of a 256-wide row band (ROWS = kUpdRows
+// or a tile table's choice), so its loads for those pixels are in flight
+// together; no shared memory, full occupancy hides the gather latency.
+template <typename T, int ROWS>
 __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int iter,
                                               int src)
 {
+    constexpr int kUpdRows = ROWS;
     using ST = Store<T>;
     using T4 = typename ST::T4;
     const int nfr = bd->nframes;
@@ -440,11 +441,16 @@ static int occ_window_t()
 
 #define FLOWROI_FLOW_RADII(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10)
 
-void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int grid,
-                   cudaStream_t s)
+void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int rows,
+                   int grid, cudaStream_t s)
 {
-    if (half) k_update<__half><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
-    else k_update<float><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+    if (rows == 8) {
+        if (half) k_update<__half, 8><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+        else k_update<float, 8><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+    } else {
+        if (half) k_update<__half, kUpdRows><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+        else k_update<float, kUpdRows><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+    }
 }
 
 int window_box(bool half, int win_r, int *xo, int *bw, int *eh)
@@ -475,11 +481,16 @@ void launch_window(const BatchDesc *bd, const MethodConsts &mc, int level, int d
     }
 }
 
-int occupancy_update(bool half)
+int occupancy_update(bool half, int rows)
 {
     int b = 0;
-    if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half>, 256, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float>, 256, 0);
+    if (rows == 8) {
+        if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half, 8>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float, 8>, 256, 0);
+    } else {
+        if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half, kUpdRows>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float, kUpdRows>, 256, 0);
+    }
     return b;
 }
 

@@ -104,7 +104,8 @@ struct BlockHist {
 __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
 // Saliency S, min/max of S, histogram of the first radix digit.  A
-// kSalTW x kSalTH tile is taken in row strips of kSalSub rows: the strip's
+// kSalTW x (kSalSub x FrameDesc::sal_strips) tile is taken in row strips of
+// kSalSub rows (its own tiling, BatchDesc::sal2_off): the strip's
 // flow plus one row above and below (rows clamped to the image) and its
 // 16-byte-aligned column apron is copied with cp.async into one of two
 // shared-memory buffers while the previous strip is processed.  One thread
@@ -115,7 +116,6 @@ __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrt
 // column, rows above and below repeat the edge rows (replicate border).
 // One thread gathers each tile's descriptor fields two tiles ahead into a
 // shared-memory header.
-constexpr int kSalSub = 8;                       // rows per strip
 constexpr int kSalRows = kSalSub + 2;            // staged rows
 constexpr int kSalCols = kSalTW + 4;             // staged columns x0-2 .. x0+TW+2 (float2)
 
@@ -124,7 +124,7 @@ struct SalTile {
     float *S;
     float2 *dbg;
     unsigned *red;
-    int x0, y0, w, h, p, fi;
+    int x0, y0, w, h, p, fi, nsub, pad;
 };
 
 struct SalSmem {
@@ -137,16 +137,15 @@ struct SalSmem {
 
 __global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
-    constexpr int TW = kSalTW, TH = kSalTH, SH = kSalSub, NSUB = TH / SH;
+    constexpr int TW = kSalTW, SH = kSalSub;
     static_assert(TW == 256, "one thread per tile column");
-    static_assert(TH % SH == 0, "whole strips");
     extern __shared__ __align__(16) unsigned char ssm[];
     float2 (*s_fl)[kSalRows][kSalCols] = reinterpret_cast<float2 (*)[kSalRows][kSalCols]>(ssm);
     unsigned *const s_hist = reinterpret_cast<unsigned *>(ssm + SalSmem::hist_off);
     unsigned *const s_mm = reinterpret_cast<unsigned *>(ssm + SalSmem::mm_off);
     SalTile *const s_hdr = reinterpret_cast<SalTile *>(ssm + SalSmem::hdr_off);
     const int nfr = bd->nframes;
-    const int *off = bd->sal_off;
+    const int *off = bd->sal2_off;
     const int total = __ldg(off + nfr);
     const int buf = bd->final_flow_buf;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -169,8 +168,9 @@ __global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict
         H.p = F.lp[0];
         const int ntx = (H.w + TW - 1) / TW;
         const int lt = t - __ldg(off + fi);
+        H.nsub = F.sal_strips;
         H.x0 = (lt % ntx) * TW;
-        H.y0 = (lt / ntx) * TH;
+        H.y0 = (lt / ntx) * SH * H.nsub;
     };
     // strip `sub` of a tile into buffer b: 16-byte chunks (two flow
     // vectors; x0, the width and the row pitch are even) inside the image
@@ -226,12 +226,13 @@ __global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict
         const int cx = cg - (x0 - 2);
         const int ex = (lane == 0 ? max(cg - 1, 0) : min(cg + 1, w - 1)) - (x0 - 2);
         const bool edge = lane == 0 || lane == 31;
-        for (int sub = 0; sub < NSUB; sub++, u++) {
+        const int nsub = H.nsub;
+        for (int sub = 0; sub < nsub; sub++, u++) {
             // this strip has landed; every thread is done with the other buffer
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();
             if (sub == 0 && tid == 0) fill_hdr(t + 2 * (int)gridDim.x, s_hdr[(k + 2) % 3]);
-            if (sub + 1 < NSUB) issue(H, sub + 1, (u + 1) & 1);
+            if (sub + 1 < nsub) issue(H, sub + 1, (u + 1) & 1);
             else if (t + (int)gridDim.x < total) issue(s_hdr[(k + 1) % 3], 0, (u + 1) & 1);
             asm volatile("cp.async.commit_group;" ::: "memory");
 

@@ -10,15 +10,17 @@
 namespace flowroi {
 
 void launch_expand(const BatchDesc *bd, const MethodConsts &mc, int level, bool half, int grid, cudaStream_t s);
-void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int grid,
-                   cudaStream_t s);
+// rows: rows per thread of a tile column (kUpdRows or 8)
+void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int rows,
+                   int grid, cudaStream_t s);
 void launch_window(const BatchDesc *bd, const MethodConsts &mc, int level, int dst, bool half, int grid, cudaStream_t s);
 void launch_frame_init(const BatchDesc *bd, int grid, cudaStream_t s);
 void launch_saliency(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
 void launch_select_pass(const BatchDesc *bd, int pass, int grid, cudaStream_t s);
 void launch_select_find(const BatchDesc *bd, const MethodConsts &mc, int pass, int grid, cudaStream_t s);
 void launch_morph(const BatchDesc *bd, const MethodConsts &mc, int grid, cudaStream_t s);
-void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, cudaStream_t s);
+// variant: the register budget's resident blocks per SM (5 or 6)
+void launch_dwt(const BatchDesc *bd, const MethodConsts &mc, int level, int grid, int variant, cudaStream_t s);
 // DWT work units (one warp each) of a level whose bands are bw x bh, with
 // seg band rows per unit; blocks needed for `units` (at most the persistent grid).
 int dwt_units(int bw, int bh, int seg);
@@ -42,12 +44,12 @@ void launch_denoise(const BatchDesc *bd, const MethodConsts &mc, bool half, int 
 // Resident blocks per SM (also sets any shared-memory attribute the kernel
 // needs; call once per device before the first launch).
 int occupancy_expand(bool half, int n_half);
-int occupancy_update(bool half);
+int occupancy_update(bool half, int rows);
 // TMA box of the window kernel: it starts xo elements left of a tile, bw wide, eh rows.
 int window_box(bool half, int win_r, int *xo, int *bw, int *eh);
 int occupancy_window(bool half, int win_r);
 int occupancy_mask_kernels();
-int occupancy_dwt(int wavelet);
+int occupancy_dwt(int wavelet, int variant);
 int occupancy_denoise(bool half, int radius);
 int occupancy_cc();
 

@@ -150,7 +150,7 @@ extern "C" int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, i
     k_na_desc<<<1, 128, 0, st>>>(nd, bdd);
     if (cudaGetLastError() != cudaSuccess) return FLOWROI_EDEVICE;
     for (int l = 1; l <= levels; l++) {
-        launch_dwt(bdd, mc, l, dwt_grid(nd.tiles[l - 1], 1 << 20), st);
+        launch_dwt(bdd, mc, l, dwt_grid(nd.tiles[l - 1], 1 << 20), 5, st);
         if (cudaGetLastError() != cudaSuccess) return FLOWROI_EDEVICE;
     }
     return FLOWROI_OK;

@@ -46,6 +46,7 @@
 #include "../../include/flowroi.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "tiles.h"
 #include "tma.cuh"
 
 using namespace flowroi;
@@ -192,6 +193,10 @@ struct flowroi_ctx {
     int desc_next = 0;
     int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0, grid_mrg = 0, grid_reg = 0;
     int grid_t1 = 0, grid_csc = 0;
+    int occ[TK_COUNT] = {};         // resident blocks per SM of the tunable persistent kernels
+    int dwt_variant = 5;            // DWT register budget in use (resident blocks per SM)
+    int upd_rows = kUpdRows;        // rows per thread of the update kernel's tile columns
+    TileTable tiles{};              // launch and tile shapes (flowroi_set_tiles / config.tile_table)
     int inflight = 0;               // guarded by cmu
     int max_inflight = 2;
     bool work_flag = false;         // guarded by cmu
@@ -243,6 +248,21 @@ int cuda_fail(flowroi_ctx *c, cudaError_t e, const char *what)
     } while (0)
 
 // ------------------------------------------------------------ validation --
+bool read_text_file(const char *path, std::string &out)
+{
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return false;
+    char buf[4096];
+    size_t n;
+    out.clear();
+    while ((n = std::fread(buf, 1, sizeof buf, f)) > 0) {
+        out.append(buf, n);
+        if (out.size() > (1u << 20)) break;
+    }
+    std::fclose(f);
+    return out.size() <= (1u << 20);
+}
+
 int validate_config(const flowroi_config *c)
 {
     if (!c) return fail(FLOWROI_EINVAL, "config is NULL");
@@ -277,6 +297,13 @@ int validate_config(const flowroi_config *c)
     if (!(c->den_sigma_s > 0.f) || !(c->den_sigma_r > 0.f)) return fail(FLOWROI_EINVAL, "config.den_sigma_s/den_sigma_r must be > 0");
     if (!(c->codestream_bpp >= 0.f && c->codestream_bpp <= 64.f))
         return fail(FLOWROI_EINVAL, "config.codestream_bpp must be in [0, 64]");
+    if (c->tile_table) {
+        std::string text, err;
+        TileTable t;
+        tiles_clear(t);
+        if (!read_text_file(c->tile_table, text)) return fail(FLOWROI_EINVAL, "config.tile_table: cannot read %s", c->tile_table);
+        if (!tiles_parse(text.c_str(), t, err)) return fail(FLOWROI_EINVAL, "config.tile_table %s: %s", c->tile_table, err.c_str());
+    }
     return FLOWROI_OK;
 }
 
@@ -475,7 +502,9 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
     F.cc_area = s->cc[2];
     F.ll[0] = s->ll[0];
     F.ll[1] = s->ll[1];
-    for (int l = 0; l < kMaxLevels; l++) F.dwt_seg[l] = dwt_default_seg(s->W >> (l + 1), s->H >> (l + 1));
+    for (int l = 0; l < kMaxLevels; l++)
+        F.dwt_seg[l] = tiles_dwt_seg(c->tiles, c->half, s->W, l + 1, s->W >> (l + 1), s->H >> (l + 1));
+    F.sal_strips = tiles_saliency_strips(c->tiles, c->half, s->W);
     F.llm[0] = s->llm[0];
     F.llm[1] = s->llm[1];
     if (e && c->cfg.register_frames) {
@@ -546,6 +575,28 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
     }
 }
 
+
+// Persistent grids and the DWT variant from the context's tile table.
+void apply_context_tiles(flowroi_ctx *c)
+{
+    const int sh = c->half ? 1 : 0;
+    const int dv = c->tiles.dwt_variant[sh];
+    c->dwt_variant = dv == 6 ? 6 : 5;
+    c->occ[TK_DWT] = occupancy_dwt(c->cfg.wavelet, c->dwt_variant);
+    c->upd_rows = c->tiles.update_rows[sh] == 8 ? 8 : kUpdRows;
+    c->occ[TK_UPDATE] = occupancy_update(c->half, c->upd_rows);
+    auto grid = [&](int k) {
+        const int occ = std::max(1, c->occ[k]);
+        const int want = c->tiles.blocks_per_sm[sh][k];
+        return (want > 0 ? std::min(want, occ) : occ) * c->num_sms;
+    };
+    c->grid_exp = grid(TK_EXPAND);
+    c->grid_upd = grid(TK_UPDATE);
+    c->grid_win = grid(TK_WINDOW);
+    c->grid_mask = grid(TK_MASK);
+    c->grid_dwt = grid(TK_DWT);
+}
+
 // Prefix tables of the batch (also the exact grids of the plain path).
 void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
 {
@@ -554,19 +605,20 @@ void fill_offsets(flowroi_ctx *c, BatchDesc &bd)
     for (int l = 0; l < kMaxLevels; l++) {
         bd.exp_off[l][0] = bd.flow_off[l][0] = bd.win_off[l][0] = bd.dwt_off[l][0] = 0;
     }
-    bd.sal_off[0] = bd.mor_off[0] = bd.frm_off[0] = bd.mrg_off[0] = 0;
+    bd.sal_off[0] = bd.sal2_off[0] = bd.mor_off[0] = bd.frm_off[0] = bd.mrg_off[0] = 0;
     bd.reg_row_off[0] = bd.reg_col_off[0] = bd.reg_el_off[0] = 0;
     for (int i = 0; i < n; i++) {
         const FrameDesc &F = bd.f[i];
         for (int l = 0; l < L; l++) {
             bd.exp_off[l][i + 1] = bd.exp_off[l][i] + (F.do_flow ? tiles(F.lw[l], F.lh[l], kExpTW, kExpTH) : 0);
-            bd.flow_off[l][i + 1] = bd.flow_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kUpdTW, kUpdRows) : 0);
+            bd.flow_off[l][i + 1] = bd.flow_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kUpdTW, c->upd_rows) : 0);
             bd.win_off[l][i + 1] = bd.win_off[l][i] + (F.has_prev ? tiles(F.lw[l], F.lh[l], kWinTW, kWinTH) : 0);
         }
         for (int l = 1; l <= D; l++)
             bd.dwt_off[l - 1][i + 1] =
                 bd.dwt_off[l - 1][i] + (F.do_dwt ? dwt_units(F.W >> l, F.H >> l, F.dwt_seg[l - 1]) : 0);
         bd.sal_off[i + 1] = bd.sal_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalTH) : 0);
+        bd.sal2_off[i + 1] = bd.sal2_off[i] + (F.has_prev ? tiles(F.W, F.H, kSalTW, kSalSub * F.sal_strips) : 0);
         bd.mor_off[i + 1] = bd.mor_off[i] + (F.do_flow ? tiles(F.W, F.H, kMorTW, kMorTH) : 0);
         bd.mrg_off[i + 1] = bd.mrg_off[i] + (F.n_adj > 0 ? (int)(((size_t)F.W * F.H + 4095) / 4096) : 0);
         const int rnx = F.do_reg ? 1 << F.reg_lnx : 0, rny = F.do_reg ? 1 << F.reg_lny : 0;
@@ -651,14 +703,14 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
             for (int it = 0; it < I; it++, k++) {
                 const int dst = k & 1;
                 timed(c, st, prof, K_UPDATE, l, it, [&] {
-                    launch_update(dd, mc, l, it, dst ^ 1, c->half, g(hd->flow_off[l][n], c->grid_upd), st);
+                    launch_update(dd, mc, l, it, dst ^ 1, c->half, c->upd_rows, g(hd->flow_off[l][n], c->grid_upd), st);
                 });
                 timed(c, st, prof, K_WINDOW, l, it, [&] {
                     launch_window(dd, mc, l, dst, c->half, g(hd->win_off[l][n], c->grid_win), st);
                 });
                 cnt += 2;
             }
-        timed(c, st, prof, K_SAL, -1, -1, [&] { launch_saliency(dd, mc, g(hd->sal_off[n], c->grid_mask), st); });
+        timed(c, st, prof, K_SAL, -1, -1, [&] { launch_saliency(dd, mc, g(hd->sal2_off[n], c->grid_mask), st); });
         for (int pass = 0; pass < 3; pass++) {
             // pass 2 reads the candidates pass 1 kept: kCandBlocks blocks a frame
             const int gp = pass == 1 ? g(hd->sal_off[n], c->grid_mask)
@@ -682,7 +734,7 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     }
     for (int l = 1; l <= D; l++) {
         timed(c, st, prof, K_DWT, l, -1, [&] {
-            launch_dwt(dd, mc, l, pl ? dwt_grid(hd->dwt_off[l - 1][n], c->grid_dwt) : c->grid_dwt, st);
+            launch_dwt(dd, mc, l, pl ? dwt_grid(hd->dwt_off[l - 1][n], c->grid_dwt) : c->grid_dwt, c->dwt_variant, st);
         });
         cnt++;
     }
@@ -1157,17 +1209,18 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     *c->err_host = 0u;
     CK(nullptr, cudaHostGetDevicePointer(reinterpret_cast<void **>(&c->err_dev), c->err_host, 0));
     if (!tma_available()) return fail(FLOWROI_EDEVICE, "cuTensorMapEncodeTiled is not available from the driver");
-    const int oe = occupancy_expand(c->half, cfg->poly_n_half);
-    const int ou = occupancy_update(c->half);
-    const int ow = occupancy_window(c->half, cfg->win_r);
-    const int om = occupancy_mask_kernels();
-    const int od = occupancy_dwt(cfg->wavelet);
+    if (cfg->tile_table) {
+        std::string text, err;
+        if (!read_text_file(cfg->tile_table, text)) return fail(FLOWROI_EINVAL, "config.tile_table: cannot read %s", cfg->tile_table);
+        if (!tiles_parse(text.c_str(), c->tiles, err))
+            return fail(FLOWROI_EINVAL, "config.tile_table %s: %s", cfg->tile_table, err.c_str());
+    }
+    c->cfg.tile_table = nullptr;  // the caller's string is not kept
+    c->occ[TK_EXPAND] = occupancy_expand(c->half, cfg->poly_n_half);
+    c->occ[TK_WINDOW] = occupancy_window(c->half, cfg->win_r);
+    c->occ[TK_MASK] = occupancy_mask_kernels();
+    apply_context_tiles(c.get());
     CK(nullptr, cudaGetLastError());
-    c->grid_exp = std::max(1, oe) * c->num_sms;
-    c->grid_upd = std::max(1, ou) * c->num_sms;
-    c->grid_win = std::max(1, ow) * c->num_sms;
-    c->grid_mask = std::max(1, om) * c->num_sms;
-    c->grid_dwt = std::max(1, od) * c->num_sms;
     c->grid_den = cfg->denoise ? std::max(1, occupancy_denoise(c->half, cfg->den_radius)) * c->num_sms : 0;
     c->grid_cc = cfg->min_area > 1 ? std::max(1, occupancy_cc()) * c->num_sms : 0;
     c->grid_mrg = 8 * c->num_sms;
@@ -1535,6 +1588,45 @@ int flowroi_compute_stream(flowroi_ctx *c, void **out)
 {
     if (!c || !out) return fail(FLOWROI_EINVAL, "ctx or out is NULL");
     *out = (void *)c->s_comp;
+    return FLOWROI_OK;
+}
+
+int flowroi_set_tiles(flowroi_ctx *c, const char *json)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    TileTable t;
+    tiles_clear(t);
+    std::string err;
+    if (json && !tiles_parse(json, t, err)) return fail(FLOWROI_EINVAL, "tile table: %s", err.c_str());
+    cudaSetDevice(c->device);
+    std::lock_guard<std::mutex> lk(c->mu);
+    // queued batches replay graphs captured with the old shapes: let them finish
+    CK(c, cudaStreamSynchronize(c->s_comp));
+    for (int g = 0; g < flowroi_ctx::kDesc; g++)
+        if (c->graph[g]) {
+            cudaGraphExecDestroy(c->graph[g]);
+            c->graph[g] = nullptr;
+        }
+    c->tiles = t;
+    apply_context_tiles(c);
+    CK(c, cudaGetLastError());
+    return FLOWROI_OK;
+}
+
+int flowroi_get_tiles(flowroi_ctx *c, char *out, uint64_t cap, uint64_t *out_len)
+{
+    if (!c || !out_len) return fail(FLOWROI_EINVAL, "ctx or out_len is NULL");
+    std::string j;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        cudaDeviceProp prop;
+        const bool named = cudaGetDeviceProperties(&prop, c->device) == cudaSuccess;
+        j = tiles_json(c->tiles, named ? prop.name : nullptr);
+    }
+    *out_len = j.size();
+    if (!out || cap < j.size() + 1) return fail(FLOWROI_ERANGE, "tile table of %zu bytes, cap is %llu", j.size(),
+                                                (unsigned long long)cap);
+    std::memcpy(out, j.c_str(), j.size() + 1);
     return FLOWROI_OK;
 }
 

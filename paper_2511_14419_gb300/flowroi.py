@@ -28,6 +28,7 @@ EXPORTS = [
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
     "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc", "flowroi_reset_stats",
     "flowroi_encode_codestreams", "flowroi_codestream_bound", "flowroi_get_codestream",
+    "flowroi_tiles_check", "flowroi_set_tiles", "flowroi_get_tiles", "flowroi_autotune",
 ]
 
 
@@ -49,6 +50,7 @@ class flowroi_config(ctypes.Structure):
         ("denoise", ctypes.c_int32), ("den_radius", ctypes.c_int32), ("den_sigma_s", ctypes.c_float),
         ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32), ("adjacent", ctypes.c_int32),
         ("register_frames", ctypes.c_int32), ("reg_level", ctypes.c_int32), ("codestream_bpp", ctypes.c_float),
+        ("tile_table", ctypes.c_char_p),
     ]
 
 
@@ -118,6 +120,11 @@ def lib() -> ctypes.CDLL:
             "flowroi_encode_codestreams": (I, [P, I, ctypes.POINTER(flowroi_cs_job), I]),
             "flowroi_codestream_bound": (ctypes.c_uint64, [I, I, I]),
             "flowroi_get_codestream": (I, [P, I64, I64, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), I, I]),
+            "flowroi_tiles_check": (I, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_uint64]),
+            "flowroi_set_tiles": (I, [P, ctypes.c_char_p]),
+            "flowroi_get_tiles": (I, [P, ctypes.c_char_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
+            "flowroi_autotune": (I, [ctypes.POINTER(flowroi_config), I, ctypes.POINTER(I), ctypes.POINTER(I), I, I,
+                                     ctypes.c_char_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]),
         }
         for name, (res, args) in sigs.items():
             fn = getattr(L, name)
@@ -155,6 +162,8 @@ def flowroi_default_config(**overrides) -> flowroi_config:
     cfg = flowroi_config()
     lib().flowroi_default_config(ctypes.byref(cfg))
     for k, v in overrides.items():
+        if k == "tile_table" and isinstance(v, str):
+            v = v.encode()
         setattr(cfg, "lambda_" if k == "lam" else k, v)
     return cfg
 
@@ -364,6 +373,37 @@ def flowroi_encode_codestreams(ctx, jobs) -> list:
                                 int(j.get("budget", 0)), op, nbytes, 0)
     _check(lib().flowroi_encode_codestreams(ctx, len(jobs), arr, int(dev)), ctx)
     return [int(arr[i].out_len) for i in range(len(jobs))]
+
+
+def flowroi_tiles_check(json_text: str) -> str:
+    """'' when the tile table is valid, else the reason (no device used)."""
+    err = ctypes.create_string_buffer(512)
+    rc = lib().flowroi_tiles_check(json_text.encode(), err, len(err))
+    return "" if rc == OK else (err.value.decode(errors="replace") or "invalid")
+
+
+def flowroi_set_tiles(ctx, json_text) -> int:
+    return _check(lib().flowroi_set_tiles(ctx, json_text.encode() if json_text is not None else None), ctx)
+
+
+def flowroi_get_tiles(ctx) -> str:
+    n = ctypes.c_uint64(0)
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check(lib().flowroi_get_tiles(ctx, buf, len(buf), ctypes.byref(n)), ctx)
+    return buf.value.decode()
+
+
+def flowroi_autotune(cfg: flowroi_config, sizes, streams: int, steps: int) -> str:
+    """Runs the tile search (see the C header) for frame sizes [(w, h), ...]
+    and returns the chosen table as JSON text."""
+    ws = (ctypes.c_int * len(sizes))(*[int(w) for w, _ in sizes])
+    hs = (ctypes.c_int * len(sizes))(*[int(h) for _, h in sizes])
+    n = ctypes.c_uint64(0)
+    buf = ctypes.create_string_buffer(1 << 16)
+    rc = lib().flowroi_autotune(ctypes.byref(cfg), len(sizes), ws, hs, streams, steps, buf, len(buf), ctypes.byref(n))
+    if rc < 0:
+        raise FlowRoIError(rc, "flowroi_autotune failed (its reason is on stderr)")
+    return buf.value.decode()
 
 
 class Context:
