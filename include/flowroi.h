@@ -451,7 +451,8 @@ FLOWROI_API uint64_t flowroi_codestream_bound(int width, int height, int levels)
  *   {"param": "dwt_seg", "w": W, "storage": S, "level": l, "value": v}
  *        DWT band rows per warp unit at level l, v in [4, 256]
  *   {"param": "update_rows", "storage": S, "value": v}
- *        rows per thread of a displacement-update tile column, 4 or 8
+ *        rows of a displacement-update tile (4, 8, 16 or 32), which
+ *        a block takes 4 at a time
  *   {"param": "saliency_rows", "w": W, "storage": S, "value": v}
  *        rows of a saliency tile, a multiple of 8 up to 128
  *   {"param": "blocks_per_sm", "kernel": K, "storage": S, "value": v}

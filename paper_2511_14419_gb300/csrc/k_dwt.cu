@@ -61,9 +61,12 @@ namespace {
 
 constexpr float kA = -1.586134342059924f, kB = -0.052980118572961f, kG = 0.882911075530934f,
                 kD = 0.443506852043971f, kK = 1.230174104914001f;
-// 1/K rounded to float: low samples are scaled by a product (one more
-// rounding than a division, far inside the 9/7 coefficient tolerance).
-constexpr float kInvK = (float)(1.0 / 1.230174104914001);
+// The normalisation (low / K, high * K in each direction) is applied once
+// per 2-D band: HL and LH carry K / K = 1, LL 1/K^2, HH K^2 (each a float
+// rounded from the double product; one rounding per coefficient instead of
+// two, far inside the 9/7 coefficient tolerance).
+constexpr float kInvK2 = (float)(1.0 / (1.230174104914001 * 1.230174104914001));
+constexpr float kK2 = (float)(1.230174104914001 * 1.230174104914001);
 constexpr unsigned kFull = 0xffffffffu;
 
 enum { kSrcU8 = 0, kSrcU16 = 1, kSrcLL = 2 };
@@ -264,7 +267,8 @@ __device__ __forceinline__ uint32_t nibble(uint32_t w)
 
 // Horizontal lifting of one row across the warp: this lane holds samples
 // (e0, o0, e1, o1) at columns 4j..4j+3; the even sample right of o1 is
-// lane j+1's e0, the odd sample left of e0 is lane j-1's o1.
+// lane j+1's e0, the odd sample left of e0 is lane j-1's o1.  9/7: the four
+// lifting steps only; the caller applies the band's normalisation.
 __device__ __forceinline__ void hlift(float &e0, float &o0, float &e1, float &o1)
 {
     o0 += kA * (e0 + e1);
@@ -275,10 +279,6 @@ __device__ __forceinline__ void hlift(float &e0, float &o0, float &e1, float &o1
     o1 += kG * (e1 + __shfl_down_sync(kFull, e0, 1));
     e0 += kD * (__shfl_up_sync(kFull, o1, 1) + o0);
     e1 += kD * (o0 + o1);
-    e0 *= kInvK;
-    e1 *= kInvK;
-    o0 *= kK;
-    o1 *= kK;
 }
 __device__ __forceinline__ void hlift(int &e0, int &o0, int &e1, int &o1)
 {
@@ -480,8 +480,8 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
                 const float E2 = s2[c] + kB * O1;     // even 2n-2, step 2
                 const float O3 = s3[c] + kG * E2;     // odd 2n-3, step 3 (final)
                 const float E4 = xe[c] + kD * O3;     // even 2n-4, step 4 (final)
-                lo[c] = E4 * kInvK;
-                hi[c] = O3 * kK;
+                lo[c] = E4;  // normalised per band after the rows are lifted
+                hi[c] = O3;
                 s1[c] = o[c] + kA * e[c];             // odd 2n+1 with its left even sample
                 s2[c] = e[c] + kB * O1;               // even 2n with its upper odd sample
                 s3[c] = O1 + kG * E2;                 // odd 2n-1 with its upper even sample
@@ -513,6 +513,12 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
         if (m >= r0) {
             hlift(lo[0], lo[1], lo[2], lo[3]);
             hlift(hi[0], hi[1], hi[2], hi[3]);
+            if constexpr (WAV == 97) {
+                lo[0] *= kInvK2;  // LL
+                lo[2] *= kInvK2;
+                hi[1] *= kK2;     // HH
+                hi[3] *= kK2;
+            }
             const uint32_t nl = nibble(lowm), nh = nibble(highm);
             const uint32_t pk = nl | (nh << 16);
             const uint32_t pl = __shfl_up_sync(kFull, pk, 1), pr = __shfl_down_sync(kFull, pk, 1);

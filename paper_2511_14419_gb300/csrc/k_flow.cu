@@ -69,15 +69,17 @@ __device__ __forceinline__ float diff_of_products(float a, float b, float c, flo
 }  // namespace
 
 // ---------------------------------------------------------------- update
-// Per pixel G = A^T A and h = A^T db (5 values) into five planes.  One
-// thread owns a column of ROWS rows of a 256-wide row band (ROWS = kUpdRows
-// or a tile table's choice), so its loads for those pixels are in flight
-// together; no shared memory, full occupancy hides the gather latency.
-template <typename T, int ROWS>
+// Per pixel G = A^T A and h = A^T db (5 values) into five planes.  A tile
+// is 256 columns x (kUpdRows x GROUPS) rows; one thread owns a column of it
+// and takes its rows kUpdRows at a time, so the loads of those pixels are
+// in flight together; no shared memory, full occupancy hides the gather
+// latency.  With GROUPS > 1 a block walks consecutive rows, whose bilinear
+// reads of the predecessor's fields overlap (L1 hits instead of L2
+// requests); the tile table chooses GROUPS per context.
+template <typename T, int GROUPS>
 __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd, MethodConsts mc, int level, int iter,
                                               int src)
 {
-    constexpr int kUpdRows = ROWS;
     using ST = Store<T>;
     using T4 = typename ST::T4;
     const int nfr = bd->nframes;
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
         const int w = F.lw[level], h = F.lh[level], p = F.lp[level];
         const int ntx = (w + kUpdTW - 1) / kUpdTW;
         const int lt = t - __ldg(off + fi);
-        const int gx = (lt % ntx) * kUpdTW + threadIdx.x, y0 = (lt / ntx) * kUpdRows;
+        const int gx = (lt % ntx) * kUpdTW + threadIdx.x, ty0 = (lt / ntx) * kUpdRows * GROUPS;
         if (gx >= w) continue;
         const T4 *q1 = static_cast<const T4 *>(F.fq_cur[level]);
         const T *b1p = static_cast<const T *>(F.fb_cur[level]);
@@ -106,6 +108,10 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
             oy = __uint_as_float(__ldg(F.red + kRedRegDrift + 1)) * sc;
         }
         const size_t plane = (size_t)p * h;
+#pragma unroll 1
+        for (int grp = 0; grp < GROUPS; grp++) {
+        const int y0 = ty0 + grp * kUpdRows;
+        if (GROUPS > 1 && y0 >= h) break;
         float ddx[kUpdRows], ddy[kUpdRows];
 #pragma unroll
         for (int j = 0; j < kUpdRows; j++) {
@@ -163,6 +169,7 @@ __global__ void __launch_bounds__(256) k_update(const BatchDesc *__restrict__ bd
             ST::st(gh + 2 * plane + o, a12 * a12 + a22 * a22);
             ST::st(gh + 3 * plane + o, a11 * db1 + a12 * db2);
             ST::st(gh + 4 * plane + o, a12 * db1 + a22 * db2);
+        }
         }
     }
 }
@@ -444,12 +451,19 @@ static int occ_window_t()
 void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int rows,
                    int grid, cudaStream_t s)
 {
-    if (rows == 8) {
-        if (half) k_update<__half, 8><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
-        else k_update<float, 8><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
-    } else {
-        if (half) k_update<__half, kUpdRows><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
-        else k_update<float, kUpdRows><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+    switch (rows) {
+#define CASE(G)                                                                              \
+    case kUpdRows * G:                                                                       \
+        if (half) k_update<__half, G><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);         \
+        else k_update<float, G><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);               \
+        break;
+        CASE(2)
+        CASE(4)
+        CASE(8)
+#undef CASE
+    default:
+        if (half) k_update<__half, 1><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
+        else k_update<float, 1><<<grid, 256, 0, s>>>(bd, mc, level, iter, src);
     }
 }
 
@@ -484,12 +498,19 @@ void launch_window(const BatchDesc *bd, const MethodConsts &mc, int level, int d
 int occupancy_update(bool half, int rows)
 {
     int b = 0;
-    if (rows == 8) {
-        if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half, 8>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float, 8>, 256, 0);
-    } else {
-        if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half, kUpdRows>, 256, 0);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float, kUpdRows>, 256, 0);
+    switch (rows) {
+#define CASE(G)                                                                                            \
+    case kUpdRows * G:                                                                                     \
+        if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half, G>, 256, 0);           \
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float, G>, 256, 0);                 \
+        break;
+        CASE(2)
+        CASE(4)
+        CASE(8)
+#undef CASE
+    default:
+        if (half) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<__half, 1>, 256, 0);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_update<float, 1>, 256, 0);
     }
     return b;
 }

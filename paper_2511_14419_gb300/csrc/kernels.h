@@ -10,7 +10,7 @@
 namespace flowroi {
 
 void launch_expand(const BatchDesc *bd, const MethodConsts &mc, int level, bool half, int grid, cudaStream_t s);
-// rows: rows per thread of a tile column (kUpdRows or 8)
+// rows: rows of a tile (kUpdRows x 1, 2, 4 or 8), taken kUpdRows at a time
 void launch_update(const BatchDesc *bd, const MethodConsts &mc, int level, int iter, int src, bool half, int rows,
                    int grid, cudaStream_t s);
 void launch_window(const BatchDesc *bd, const MethodConsts &mc, int level, int dst, bool half, int grid, cudaStream_t s);

@@ -583,7 +583,7 @@ void apply_context_tiles(flowroi_ctx *c)
     const int dv = c->tiles.dwt_variant[sh];
     c->dwt_variant = dv == 6 ? 6 : 5;
     c->occ[TK_DWT] = occupancy_dwt(c->cfg.wavelet, c->dwt_variant);
-    c->upd_rows = c->tiles.update_rows[sh] == 8 ? 8 : kUpdRows;
+    c->upd_rows = c->tiles.update_rows[sh] > 0 ? c->tiles.update_rows[sh] : kUpdRows;
     c->occ[TK_UPDATE] = occupancy_update(c->half, c->upd_rows);
     auto grid = [&](int k) {
         const int occ = std::max(1, c->occ[k]);

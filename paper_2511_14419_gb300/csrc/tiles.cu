@@ -298,8 +298,8 @@ bool tiles_parse(const char *json, TileTable &t, std::string &err)
             }
             n.saliency_rows[sh][c] = value;
         } else if (param == "update_rows") {
-            if (value != 4 && value != 8) {
-                err = std::string(where) + "update_rows must be 4 or 8";
+            if (value != 4 && value != 8 && value != 16 && value != 32) {
+                err = std::string(where) + "update_rows must be 4, 8, 16 or 32";
                 return false;
             }
             n.update_rows[sh] = value;
@@ -553,7 +553,7 @@ struct Tuner {
         if (!setup(r, w, h)) return false;
         const int sh = half ? 1 : 0;
         if (!search(r, {5, 6}, {{"dwt", -1}}, [&](int v) { best.dwt_variant[sh] = v; })) return false;
-        if (!search(r, {4, 8}, {{"update", -1}}, [&](int v) { best.update_rows[sh] = v; })) return false;
+        if (!search(r, {4, 8, 16, 32}, {{"update", -1}}, [&](int v) { best.update_rows[sh] = v; })) return false;
         const int occ[TK_COUNT] = {occupancy_expand(half, cfg->poly_n_half),
                                    occupancy_update(half, best.update_rows[sh] ? best.update_rows[sh] : kUpdRows),
                                    occupancy_window(half, cfg->win_r), occupancy_mask_kernels(),

@@ -31,7 +31,7 @@ struct TileTable {
     // per context [storage]; 0 = built-in default
     int blocks_per_sm[2][TK_COUNT];         // persistent grid = min(this, occupancy) x SMs
     int dwt_variant[2];                     // DWT register budget: 5 or 6 resident blocks per SM
-    int update_rows[2];                     // rows per thread of a k_update tile column: 4 or 8
+    int update_rows[2];                     // rows of a k_update tile: 4, 8, 16 or 32 (taken 4 at a time)
 };
 
 void tiles_clear(TileTable &t);

@@ -27,12 +27,12 @@ def _all_widths(param, value, storage=32, **extra):
 
 TABLE_A = _table(
     [e for l in range(1, 6) for e in _all_widths("dwt_seg", 8, level=l)]
-    + [dict(param="update_rows", storage=32, value=8)] + _all_widths("saliency_rows", 64)
+    + [dict(param="update_rows", storage=32, value=32)] + _all_widths("saliency_rows", 64)
     + [dict(param="blocks_per_sm", kernel=k, storage=32, value=1) for k in ("expand", "update", "window", "mask", "dwt")]
     + [dict(param="dwt_variant", storage=32, value=6)])
 TABLE_B = _table(
     [e for l in range(1, 6) for e in _all_widths("dwt_seg", 64 if l == 1 else 12, level=l)]
-    + [dict(param="update_rows", storage=32, value=4)] + _all_widths("saliency_rows", 16)
+    + [dict(param="update_rows", storage=32, value=8)] + _all_widths("saliency_rows", 16)
     + [dict(param="blocks_per_sm", kernel=k, storage=32, value=2) for k in ("expand", "update", "window", "mask", "dwt")]
     + [dict(param="dwt_variant", storage=32, value=5)])
 

@@ -53,7 +53,7 @@ def test_valid_tables_are_accepted(F):
     (_table({"param": "dwt_seg", "w": 2048, "storage": 32, "level": 9, "value": 32}), "level"),
     (_table({"param": "dwt_seg", "w": 2000, "storage": 32, "level": 1, "value": 32}), "w must"),
     (_table({"param": "dwt_seg", "w": 2048, "storage": 8, "level": 1, "value": 32}), "storage"),
-    (_table({"param": "update_rows", "storage": 32, "value": 6}), "4 or 8"),
+    (_table({"param": "update_rows", "storage": 32, "value": 6}), "4, 8, 16 or 32"),
     (_table({"param": "saliency_rows", "w": 2048, "storage": 32, "value": 12}), "multiple of 8"),
     (_table({"param": "saliency_rows", "w": 2048, "storage": 32, "value": 8.5}), "integer"),
     (_table({"param": "blocks_per_sm", "kernel": "nope", "storage": 32, "value": 2}), "kernel"),
