@@ -574,6 +574,21 @@ def cpu_sample(wl, frames_cpu, budget_s=12.0, crop=512):
     return px_per_s / (h * w), el, done
 
 
+def cpu_full_frames(wl, frames_cpu, n=1):
+    """The oracle (single-threaded) on n whole frame pairs of the workload
+    (no crop, no scaling); returns (frames/s, seconds)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    p = O.Params(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"])
+    t0 = time.perf_counter()
+    for k in range(n):
+        a, b = frames_cpu[k % len(frames_cpu)]
+        O.frame(np.ascontiguousarray(a), np.ascontiguousarray(b), wl["bit_depth"], p)
+    el = time.perf_counter() - t0
+    return n / el, el
+
+
 def _cpu_worker(job):
     """One process of the all-cores oracle sample: the oracle on its crop
     pairs, round robin, for budget_s seconds (at least one crop)."""
@@ -880,6 +895,11 @@ def main():
             cpu_all = cpu_parallel_line(wl, fc)
         except Exception as e:  # the single-threaded figure stands on its own
             cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
+        ff, fel = cpu_full_frames(wl, fc, 1)
+        cpu_full = {"value": ff, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                    "sample": f"1 whole {wl['w']}x{wl['h']} frame pair of the workload ({fel:.1f} s), no crop, no scaling"}
+    else:
+        cpu_full = None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -887,7 +907,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": config_of(args.workload, wl), "e2e": e2e, "gpu_launches": dev["launches"],
                 "plain_fps": plain, "latency": latency, "clocks": dev.get("clocks"), "roofline": roof,
-                "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "kernel_avg_ms": kernels,
+                "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "cpu_baseline_full_frame": cpu_full,
+                "kernel_avg_ms": kernels,
                 "roofline_other": roofs[1:]}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -90,6 +90,15 @@ extern "C" {
                                            one grid per frame, no CUDA graphs */
 #define FLOWROI_MANUAL 0x4u             /* no scheduler thread: the caller launches batches
                                            with flowroi_step (deterministic batch makeup) */
+/* Test only: exercise the failure path of the bounded device waits and
+ * loops without a fault.  Every batch run under one of these flags sets the
+ * error word and poisons the context (FLOWROI_EDEVICE; the device and other
+ * contexts stay usable); results of those batches are not valid. */
+#define FLOWROI_TEST_EXPIRE_TMA 0x100u  /* the window kernel's producer (block 0,
+                                           level 0) never issues its first tile's
+                                           copies; TMA waits give up after 2^12 polls */
+#define FLOWROI_TEST_EXPIRE_LOOP 0x200u /* union-find loops of the component filter
+                                           (config.min_area > 1) give up after 1 step */
 
 /* flowroi_get_intermediate: `which` */
 #define FLOWROI_I_FLOW 1        /* float[2*W*H]: level-0 flow (dx, dy) interleaved */

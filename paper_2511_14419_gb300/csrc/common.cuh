@@ -14,6 +14,9 @@ constexpr int kMaxBatch = 64;    // frames per batched launch
 constexpr int kHistBins = 2048;  // radix-select digit of 11 bits
 constexpr int kCandBlocks = 32;  // blocks per frame of the last radix digit
 constexpr int kMaxSubbands = 3 * kMaxLevels + 1;
+constexpr int kLoopLimit = 1 << 24;          // union-find loop steps before a loop gives up
+constexpr unsigned kTestTmaSpin = 1u << 12;  // FLOWROI_TEST_EXPIRE_TMA: polls of a bounded TMA wait
+constexpr int kTestLoopLimit = 1;            // FLOWROI_TEST_EXPIRE_LOOP: union-find loop steps
 
 // Tile shapes (output pixels per block) of each kernel family.
 constexpr int kDenMaxR = 3;                // largest bilateral radius of the optional denoising
@@ -171,6 +174,9 @@ struct BatchDesc {
     int nframes;
     int final_flow_buf;             // ping-pong index holding the level-0 flow
     unsigned *err;                  // error word (mapped host memory); kernels set it on a failed wait
+    unsigned tma_spin;              // polls of a bounded TMA wait before it gives up
+    int loop_limit;                 // steps of a bounded union-find loop before it gives up
+    int test_skip_tile;             // test only: the level-0 window producer of block 0 skips its first tile's copies
     int exp_off[kMaxLevels][kMaxBatch + 1];
     int flow_off[kMaxLevels][kMaxBatch + 1];   // update tiles
     int win_off[kMaxLevels][kMaxBatch + 1];    // window tiles

@@ -32,13 +32,12 @@ namespace {
 constexpr int kCcTW = kSalTW, kCcTH = kSalTH;
 constexpr int kCcN = kCcTW * kCcTH;
 constexpr unsigned kErrCcLoop = 2u;  // error word: a union-find loop ran out
-constexpr int kCcLimit = 1 << 24;
 
 // Root of x, halving the path on the way (a non-root's parent may be
 // replaced by any ancestor: roots are only ever linked, never unlinked).
-__device__ __forceinline__ int find_s(int *P, int x, bool &bad)
+__device__ __forceinline__ int find_s(int *P, int x, bool &bad, int lim)
 {
-    for (int k = 0; k < kCcLimit; k++) {
+    for (int k = 0; k < lim; k++) {
         const int p = P[x];
         if (p == x) return x;
         const int gp = P[p];
@@ -49,11 +48,11 @@ __device__ __forceinline__ int find_s(int *P, int x, bool &bad)
     return x;
 }
 
-__device__ __forceinline__ void union_s(int *P, int a, int b, bool &bad)
+__device__ __forceinline__ void union_s(int *P, int a, int b, bool &bad, int lim)
 {
-    for (int k = 0; k < kCcLimit; k++) {
-        a = find_s(P, a, bad);
-        b = find_s(P, b, bad);
+    for (int k = 0; k < lim; k++) {
+        a = find_s(P, a, bad, lim);
+        b = find_s(P, b, bad, lim);
         if (a == b || bad) return;
         if (a < b) {
             const int t = a;
@@ -69,10 +68,10 @@ __device__ __forceinline__ void union_s(int *P, int a, int b, bool &bad)
 
 // The same on the frame's label array in global memory (volatile reads:
 // other blocks link roots concurrently).
-__device__ __forceinline__ int find_g(int *L, int x, bool &bad)
+__device__ __forceinline__ int find_g(int *L, int x, bool &bad, int lim)
 {
     volatile int *V = L;
-    for (int k = 0; k < kCcLimit; k++) {
+    for (int k = 0; k < lim; k++) {
         const int p = V[x];
         if (p == x) return x;
         const int gp = V[p];
@@ -84,9 +83,9 @@ __device__ __forceinline__ int find_g(int *L, int x, bool &bad)
 }
 
 // Root of x once no union runs any more (read-only path).
-__device__ __forceinline__ int find_ro(const int *L, int x, bool &bad)
+__device__ __forceinline__ int find_ro(const int *L, int x, bool &bad, int lim)
 {
-    for (int k = 0; k < kCcLimit; k++) {
+    for (int k = 0; k < lim; k++) {
         const int p = __ldg(L + x);
         if (p == x) return x;
         x = p;
@@ -95,11 +94,11 @@ __device__ __forceinline__ int find_ro(const int *L, int x, bool &bad)
     return x;
 }
 
-__device__ __forceinline__ void union_g(int *L, int a, int b, bool &bad)
+__device__ __forceinline__ void union_g(int *L, int a, int b, bool &bad, int lim)
 {
-    for (int k = 0; k < kCcLimit; k++) {
-        a = find_g(L, a, bad);
-        b = find_g(L, b, bad);
+    for (int k = 0; k < lim; k++) {
+        a = find_g(L, a, bad, lim);
+        b = find_g(L, b, bad, lim);
         if (a == b || bad) return;
         if (a < b) {
             const int t = a;
@@ -139,6 +138,7 @@ __device__ __forceinline__ CcTile cc_tile(const BatchDesc *bd, int t)
 // 1. tile-local labelling (shared memory: parents, then the counts)
 __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ bd)
 {
+    const int lim = bd->loop_limit;
     __shared__ int P[kCcN];  // parent (local index), -1 = background; then the count of each local root
     const int total = __ldg(bd->sal_off + bd->nframes);
     const int c = threadIdx.x;
@@ -165,19 +165,19 @@ __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ 
             const bool n = r > 0 && P[u] >= 0;
             const bool wst = c > 0 && P[i - 1] >= 0;
             if (n) {
-                union_s(P, i, u, bad);
+                union_s(P, i, u, bad, lim);
                 continue;
             }
-            if (wst) union_s(P, i, i - 1, bad);
-            else if (r > 0 && c > 0 && P[u - 1] >= 0) union_s(P, i, u - 1, bad);
-            if (r > 0 && c + 1 < kCcTW && P[u + 1] >= 0) union_s(P, i, u + 1, bad);
+            if (wst) union_s(P, i, i - 1, bad, lim);
+            else if (r > 0 && c > 0 && P[u - 1] >= 0) union_s(P, i, u - 1, bad, lim);
+            if (r > 0 && c + 1 < kCcTW && P[u + 1] >= 0) union_s(P, i, u + 1, bad, lim);
         }
         __syncthreads();
         int root[kCcTH];
 #pragma unroll
         for (int r = 0; r < kCcTH; r++) {
             const int i = r * kCcTW + c;
-            root[r] = P[i] >= 0 ? find_s(P, i, bad) : -1;
+            root[r] = P[i] >= 0 ? find_s(P, i, bad, lim) : -1;
         }
         __syncthreads();  // every find is done: the parents are not needed any more
 #pragma unroll
@@ -222,6 +222,7 @@ __global__ void __launch_bounds__(256) k_cc_local(const BatchDesc *__restrict__ 
 // 2. unions across the top and left tile borders
 __global__ void __launch_bounds__(256) k_cc_merge(const BatchDesc *__restrict__ bd)
 {
+    const int lim = bd->loop_limit;
     const int total = __ldg(bd->sal_off + bd->nframes);
     bool bad = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -238,7 +239,7 @@ __global__ void __launch_bounds__(256) k_cc_merge(const BatchDesc *__restrict__ 
                         const int qx = gx + dx;
                         if (qx < 0 || qx >= w) continue;
                         const int q = (gy - 1) * w + qx;
-                        if (L[q] >= 0) union_g(L, L[p], L[q], bad);
+                        if (L[q] >= 0) union_g(L, L[p], L[q], bad, lim);
                     }
             }
         }
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(256) k_cc_merge(const BatchDesc *__restrict__ 
                         const int qy = gy + dy;
                         if (qy < 0 || qy >= h) continue;
                         const int q = qy * w + gx - 1;
-                        if (L[q] >= 0) union_g(L, L[p], L[q], bad);
+                        if (L[q] >= 0) union_g(L, L[p], L[q], bad, lim);
                     }
             }
         }
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(256) k_cc_merge(const BatchDesc *__restrict__ 
 // column's counts are all read before any root is looked up)
 __global__ void __launch_bounds__(256) k_cc_count(const BatchDesc *__restrict__ bd)
 {
+    const int lim = bd->loop_limit;
     const int total = __ldg(bd->sal_off + bd->nframes);
     bool bad = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(256) k_cc_count(const BatchDesc *__restrict__ 
             const int r = __ffs(rows) - 1;
             rows &= rows - 1u;
             const int g = (T.y0 + r) * T.w + gx;
-            const int root = find_g(L, g, bad);
+            const int root = find_g(L, g, bad, lim);
             L[g] = root;  // the filter reaches the root in one step (root <= g)
             atomicAdd(A + root, __ldg(C + g));
         }
@@ -295,6 +297,7 @@ __global__ void __launch_bounds__(256) k_cc_count(const BatchDesc *__restrict__ 
 // labels, roots and areas are read in three batches.
 __global__ void __launch_bounds__(256) k_cc_filter(const BatchDesc *__restrict__ bd, MethodConsts mc)
 {
+    const int lim = bd->loop_limit;
     const int total = __ldg(bd->sal_off + bd->nframes);
     bool bad = false;
     for (int t = blockIdx.x; t < total; t += gridDim.x) {
@@ -312,7 +315,7 @@ __global__ void __launch_bounds__(256) k_cc_filter(const BatchDesc *__restrict__
             if (rt[r] >= 0) rt[r] = __ldg(L + rt[r]);
 #pragma unroll
         for (int r = 0; r < kCcTH; r++)
-            if (rt[r] >= 0 && __ldg(L + rt[r]) != rt[r]) rt[r] = find_ro(L, rt[r], bad);  // not expected
+            if (rt[r] >= 0 && __ldg(L + rt[r]) != rt[r]) rt[r] = find_ro(L, rt[r], bad, lim);  // not expected
 #pragma unroll
         for (int r = 0; r < kCcTH; r++)
             if (rt[r] >= 0 && __ldg(A + rt[r]) < mc.min_area) mask[(size_t)(T.y0 + r) * T.w + gx] = 0;

@@ -292,7 +292,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
         if (threadIdx.x == kWinConsumers) {
             int i = 0;
             bool ok = true;
+            const uint32_t spin = bd->tma_spin;
             for (int j = 0; j < mine && ok; j++) {
+                // test only (FLOWROI_TEST_EXPIRE_TMA): this tile's copies are
+                // never issued, so the waits for them run out
+                const bool skip = bd->test_skip_tile && level == 0 && blockIdx.x == 0 && j == 0;
                 const int t = blockIdx.x + j * gridDim.x;
                 const int fi = find_frame(off, nfr, t);
                 const FrameDesc &F = bd->f[fi];
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
                 tensormap_acquire(map);
                 for (int k = 0; k < 5; k++, i++) {
                     const int slot = i % NS;
-                    if (i >= NS && !mbar_wait(&empty[slot], (uint32_t)((i / NS - 1) & 1))) {
+                    if (i >= NS && !mbar_wait(&empty[slot], (uint32_t)((i / NS - 1) & 1), spin)) {
                         atomicExch(bd->err, kErrTmaTimeout);
                         ok = false;
                         break;
@@ -318,13 +322,14 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
                         ht.p = F.lp[level];
                         ht.flow = F.flow[dst];
                     }
+                    if (skip) continue;
                     fence_proxy_async_smem();
                     mbar_expect_tx(&full[slot], (uint32_t)G::plane_bytes);
                     tma_load_3d(slots + slot * G::slot_stride, map, x0 - G::XO, y0 - R, k, &full[slot]);
                 }
             }
             // No copy may still be writing shared memory when the block leaves.
-            for (int q = i - NS < 0 ? 0 : i - NS; q < i; q++) mbar_wait(&full[q % NS], (uint32_t)((q / NS) & 1));
+            for (int q = i - NS < 0 ? 0 : i - NS; q < i; q++) mbar_wait(&full[q % NS], (uint32_t)((q / NS) & 1), spin);
         }
         return;
     }
@@ -343,6 +348,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
     // row-segment owner: quarter-warps span 8 rows
     const int r = (wp & 3) * 8 + (lane & 7), sg = (wp >> 2) * 4 + (lane >> 3);
     int i = 0;  // ring index of the tile's plane 0
+    const uint32_t spin = bd->tma_spin;
     for (int j = 0; j < mine; j++, i += 5) {
         bool ok = true;
 #pragma unroll
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_window(const BatchDesc *__re
             if (ck[u] >= 5) break;
             const int ii = i + ck[u];
             const int slot = ii % NS;
-            ok = ok && mbar_wait(&full[slot], (uint32_t)((ii / NS) & 1));
+            ok = ok && mbar_wait(&full[slot], (uint32_t)((ii / NS) & 1), spin);
             if (!ok) break;
             if (cx[u] >= EW) continue;
             const T *col = reinterpret_cast<const T *>(slots + slot * G::slot_stride) + cx[u] + (G::XO - R);

@@ -284,7 +284,9 @@ int validate_config(const flowroi_config *c)
     if (!(c->delta_base > 0.f)) return fail(FLOWROI_EINVAL, "config.delta_base must be > 0");
     if (c->max_batch_frames < 1 || c->max_batch_frames > kMaxBatch) return fail(FLOWROI_EINVAL, "config.max_batch_frames must be in [1,64]");
     if (c->result_ring < 2 || c->result_ring > 16) return fail(FLOWROI_EINVAL, "config.result_ring must be in [2,16]");
-    if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL)) return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
+    if (c->flags & ~(FLOWROI_KEEP_INTERMEDIATES | FLOWROI_PLAIN | FLOWROI_MANUAL | FLOWROI_TEST_EXPIRE_TMA |
+                     FLOWROI_TEST_EXPIRE_LOOP))
+        return fail(FLOWROI_EINVAL, "config.flags has unknown bits");
     if (c->min_area < 0 || c->min_area > (1 << 20)) return fail(FLOWROI_EINVAL, "config.min_area must be in [0, 2^20]");
     if (c->adjacent < 0 || c->adjacent > kMaxAdj) return fail(FLOWROI_EINVAL, "config.adjacent must be in [0,4]");
     if (c->register_frames != 0 && c->register_frames != 1) return fail(FLOWROI_EINVAL, "config.register_frames must be 0 or 1");
@@ -814,6 +816,9 @@ int step_locked(flowroi_ctx *c)
     BatchDesc &hd = *c->desc_host[k];
     hd.nframes = (int)sel.size();
     hd.err = c->err_dev;
+    hd.tma_spin = (c->cfg.flags & FLOWROI_TEST_EXPIRE_TMA) ? kTestTmaSpin : kTmaSpinLimit;
+    hd.loop_limit = (c->cfg.flags & FLOWROI_TEST_EXPIRE_LOOP) ? kTestLoopLimit : kLoopLimit;
+    hd.test_skip_tile = (c->cfg.flags & FLOWROI_TEST_EXPIRE_TMA) ? 1 : 0;
     const int nflow = c->cfg.pyr_levels * c->cfg.iters;
     hd.final_flow_buf = (nflow - 1) & 1;
     for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].s, sel[i].e, sel[i].d, hd.f[i]);

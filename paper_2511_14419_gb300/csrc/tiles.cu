@@ -427,7 +427,8 @@ struct Tuner {
     bool setup(Run &r, int w, int h)
     {
         flowroi_config c2 = *cfg;
-        c2.flags = (cfg->flags | FLOWROI_MANUAL) & ~(unsigned)(FLOWROI_PLAIN | FLOWROI_KEEP_INTERMEDIATES);
+        c2.flags = (cfg->flags | FLOWROI_MANUAL) & ~(unsigned)(FLOWROI_PLAIN | FLOWROI_KEEP_INTERMEDIATES | FLOWROI_TEST_EXPIRE_TMA |
+                                                             FLOWROI_TEST_EXPIRE_LOOP);
         c2.tile_table = nullptr;
         c2.max_batch_frames = std::max(cfg->max_batch_frames, streams);
         c2.codestream_bpp = 0.f;

@@ -72,10 +72,11 @@ __device__ __forceinline__ bool named_sync_or(int id, int nthreads, bool p)
     return r != 0;
 }
 
-// Bounded wait for phase `parity` of the mbarrier; true when it completed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// Bounded wait (at most `limit` polls) for phase `parity` of the mbarrier;
+// true when it completed.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32_t limit)
 {
-    for (uint32_t i = 0; i < kTmaSpinLimit; i++) {
+    for (uint32_t i = 0; i < limit; i++) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

@@ -19,6 +19,7 @@ U8, U16 = 1, 2
 W53, W97 = 53, 97
 FP32, FP16 = 32, 16
 KEEP_INTERMEDIATES, PLAIN, MANUAL = 0x1, 0x2, 0x4
+TEST_EXPIRE_TMA, TEST_EXPIRE_LOOP = 0x100, 0x200
 I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD, I_DENOISED, I_DRIFT = 1, 2, 3, 4, 5, 6, 7
 
 EXPORTS = [

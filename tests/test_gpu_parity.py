@@ -138,10 +138,12 @@ def test_pair_512_u16_97(orc):
     _stagewise(orc, seq[0], seq[1], 12, g, **cfg)
 
 
-def test_full_size_2048_u16_97_batched(orc):
+def test_full_size_2048_u16_97(orc):
     """Frame geometry and settings of the 16 x 2048^2 batched workload
-    (5-level pyramid, 9/7 DWT 5 levels), through the batched, graph-replayed
-    path, one pair checked against the oracle at full size."""
+    (5-level pyramid, 9/7 DWT 5 levels), one stream through the captured
+    graph path, one pair checked against the oracle at full size (the full
+    16-frame batch is checked against frames run alone in
+    test_batch_invariance_16x2048)."""
     seq = u16(sequence_u16(3000, 2, 2048, 2048, 200))
     cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
     g = run_stream([seq[0], seq[1]], 12, **cfg)[1]
@@ -199,3 +201,27 @@ def test_fp16_storage_2048_epe_and_iou_vs_fp64(orc):
           f"fp16 EPE {res['fp16'][0]:.3e} max {res['fp16'][1]:.3e} IoU {res['fp16'][2]:.5f}")
     assert res["fp32"][1] <= FLOW_TOL
     assert res["fp16"][0] < 0.05 and res["fp16"][2] > 0.9
+
+
+def test_batch_invariance_16x2048():
+    """The headline batch: 16 streams of 2048^2 12-bit frames (the bench
+    workload's first two frames per stream), each frame index one batch of
+    16 through the captured graph; streams 0, 7 and 15 are bit-identical to
+    the same streams run alone."""
+    S = 16
+    seqs = [sequence_u16(3000 + s, 2, 2048, 2048, 200, device="cuda") for s in range(S)]
+    cfg = dict(pyr_levels=5, dwt_levels=5, wavelet=97)
+    got = {}
+    with F.Context(flags=F.MANUAL, **cfg) as ctx:
+        for t in range(2):
+            for s in range(S):
+                F.flowroi_submit_frame(ctx.h, s, seqs[s][t], t, 12)
+            assert F.flowroi_step(ctx.h) == S
+            F.flowroi_flush(ctx.h, 120000)
+        for s in (0, 7, 15):
+            got[s] = fetch(ctx.h, s, 1, 2048, 2048, keep=False, wavelet=97)
+    for s in (0, 7, 15):
+        alone = run_stream([u16(seqs[s][0].cpu()), u16(seqs[s][1].cpu())], 12, keep=False, **cfg)[1]
+        assert np.array_equal(got[s]["mask"], alone["mask"]), s
+        assert np.array_equal(got[s]["coeffs"], alone["coeffs"]), s
+        assert got[s]["mask"].sum() > 0

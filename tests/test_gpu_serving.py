@@ -3,6 +3,9 @@ invariance (a frame's results are bit-identical alone, in a mixed batch of
 streams of different resolutions, on the plain per-frame path and under the
 continuously batching scheduler thread), admission by HBM budget, result
 ring eviction, bounded waits and argument errors."""
+import threading
+import time
+
 import numpy as np
 import pytest
 
@@ -158,3 +161,66 @@ def test_many_streams_and_frames_in_flight():
         F.flowroi_flush(ctx.h, 60000)
         st = F.flowroi_get_stats(ctx.h)
         assert st["frames_done"] == 96 and st["batches"] >= 6
+
+
+def test_admission_while_batches_are_in_flight():
+    """A stream refused for lack of HBM budget (EBUSY) is admitted without a
+    flush once another thread ends a stream, while the scheduler thread keeps
+    a third stream's batches going; the late stream's results, and the busy
+    stream's, equal the same streams run alone."""
+    cfg = dict(pyr_levels=4, dwt_levels=4, wavelet=97)
+    A = u16(sequence_u16(7001, 3, 512, 512, 20))
+    B = u16(sequence_u16(7002, 10, 512, 512, 20))
+    C = u16(sequence_u16(7003, 3, 512, 512, 20))
+    alone_B = run_stream([B[t] for t in range(10)], 12, keep=False, **cfg)
+    alone_C = run_stream([C[t] for t in range(3)], 12, keep=False, **cfg)
+    with F.Context(flags=F.MANUAL, **cfg) as probe:
+        F.flowroi_submit_frame(probe.h, 0, A[0], 0, 12)
+        one = F.flowroi_get_stats(probe.h)["bytes_admitted"]
+
+    def submit_retry(ctx, sid, fr, idx):
+        for _ in range(20000):
+            try:
+                return F.flowroi_submit_frame(ctx.h, sid, fr, idx, 12)
+            except F.FlowRoIError as e:
+                if e.code != F.EBUSY:
+                    raise
+                time.sleep(0.0005)
+        raise TimeoutError("submission stayed refused")
+
+    with F.Context(hbm_budget_bytes=int(2.5 * one), result_ring=8, **cfg) as ctx:  # scheduler thread
+        for t in range(3):
+            F.flowroi_submit_frame(ctx.h, 1, A[t], t, 12)
+        for t in range(3):
+            F.flowroi_submit_frame(ctx.h, 2, B[t], t, 12)
+        with pytest.raises(F.FlowRoIError) as ei:
+            F.flowroi_submit_frame(ctx.h, 3, C[0], 0, 12)
+        assert ei.value.code == F.EBUSY
+        errs = []
+
+        def ender():
+            try:
+                fetch(ctx.h, 1, 2, 512, 512, keep=False, wavelet=97)
+                for t in range(3, 6):  # more of B's frames queued while A ends
+                    submit_retry(ctx, 2, B[t], t)
+                F.flowroi_end_stream(ctx.h, 1)
+            except Exception as e:  # reported by the main thread
+                errs.append(e)
+
+        th = threading.Thread(target=ender)
+        th.start()
+        submit_retry(ctx, 3, C[0], 0)  # admitted once A's budget is returned; no flush
+        for t in range(6, 10):
+            submit_retry(ctx, 2, B[t], t)
+        for t in (1, 2):
+            submit_retry(ctx, 3, C[t], t)
+        th.join(60)
+        assert not th.is_alive() and not errs, errs
+        for t in range(3):
+            got = fetch(ctx.h, 3, t, 512, 512, keep=False, wavelet=97, timeout_ms=60000)
+            assert np.array_equal(got["mask"], alone_C[t]["mask"]) and np.array_equal(got["coeffs"], alone_C[t]["coeffs"])
+        for t in (8, 9):
+            got = fetch(ctx.h, 2, t, 512, 512, keep=False, wavelet=97, timeout_ms=60000)
+            assert np.array_equal(got["mask"], alone_B[t]["mask"]) and np.array_equal(got["coeffs"], alone_B[t]["coeffs"])
+        st = F.flowroi_get_stats(ctx.h)
+        assert st["admissions_refused"] >= 1 and st["streams_admitted"] == 2  # B and C (A ended)
