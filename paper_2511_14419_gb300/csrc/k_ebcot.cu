@@ -26,8 +26,19 @@
 // the current bit-plane as 64-bit row masks live in shared memory.  The
 // warp builds each bit-plane from the coefficient plane (coalesced) and,
 // in the same sweep, adds up the distortion decreases of the previous
-// plane's passes from the events lane 0 recorded; lane 0 runs the passes
-// and the MQ coder, which are sequential by definition.
+// plane's passes from the events the passes recorded.  The passes go
+// stripe by stripe:
+//   - magnitude refinement: its members, contexts and decisions depend only
+//     on state fixed before the pass, so the whole warp forms the stripe's
+//     (context, bit) symbols in scan order into a shared-memory queue and
+//     lane 0 only runs the MQ coder over it;
+//   - significance propagation and cleanup: the warp forms the stripe's
+//     candidate columns by ballot; lane 0 walks them in order and codes
+//     their samples (sequential by definition: a sample that becomes
+//     significant changes its neighbours' contexts; in the significance
+//     pass it makes the next column a candidate).
+// The MQ coder keeps each context's probability-table row and MPS in one
+// shared-memory word and renormalises by count-leading-zeros.
 #include <mutex>
 
 #include "common.cuh"
@@ -94,17 +105,6 @@ __host__ __device__ constexpr int zc_rule(int ori, int h, int v, int d)
     return hv >= 2 ? 2 : (hv == 1 ? 1 : 0);
 }
 
-struct ZcTable {
-    uint8_t t[4][45];
-    constexpr ZcTable() : t{}
-    {
-        for (int o = 0; o < 4; o++)
-            for (int d = 0; d < 5; d++)
-                for (int v = 0; v < 3; v++)
-                    for (int h = 0; h < 3; h++) t[o][h + 3 * v + 9 * d] = (uint8_t)zc_rule(o, h, v, d);
-    }
-};
-__constant__ ZcTable kZc = ZcTable();
 
 // Sign-coding context (Table D.3) and flip bit by (H + 1) + 3 (V + 1),
 // H and V the clipped horizontal and vertical sign contributions: bits 0-4
@@ -125,11 +125,10 @@ constexpr int kT1Warps = 7;  // code-blocks per CTA (three CTAs per SM by shared
 
 struct T1Warp {
     uint16_t st[(kCb + 2) * kColS];
-    uint8_t cx[kNctx + 1];  // MQ context states: probability state << 1 | MPS
-    uint64_t bm[kCb];  // bit p of the magnitudes, one row per word (bit x)
+    uint32_t cxw[kNctx + 1];  // MQ contexts: the state's table row (kMq word) | MPS << 31
+    uint64_t bm[kCb];         // bit p of the magnitudes, one row per word (bit x)
+    uint8_t mq[4 * kCb];      // a stripe's refinement symbols: (context - 14) << 1 | bit
 };
-
-__device__ __forceinline__ int nb_index(uint16_t w) { return (w & 3) + 3 * ((w >> 2) & 3) + 9 * ((w >> 4) & 7); }
 
 __device__ __forceinline__ int contrib(uint16_t w) { return (w & kSig) ? ((w & kNeg) ? -1 : 1) : 0; }
 
@@ -156,7 +155,7 @@ struct Mqe {
     int cap;
     bool over;
 
-    __device__ void init(uint8_t *o, int capacity)
+    __device__ __forceinline__ void init(uint8_t *o, int capacity)
     {
         a = 0x8000;
         c = 0;
@@ -174,7 +173,7 @@ struct Mqe {
             else over = true;
         }
     }
-    __device__ void byteout()
+    __device__ __forceinline__ void byteout()
     {
         if (b == 0xFF) {
             emit();
@@ -206,37 +205,42 @@ struct Mqe {
             }
         }
     }
+    // Doubles A (and C) until A >= 0x8000, handing out a byte whenever CT
+    // reaches zero: the one-bit-at-a-time loop of the definition, taken in
+    // runs of min(remaining shifts, CT) bits (1 <= A < 0x8000 here).
     __device__ __forceinline__ void renorm()
     {
-        do {
-            a <<= 1;
-            c <<= 1;
-            if (--ct == 0) byteout();
-        } while ((a & 0x8000) == 0);
+        int n = __clz(a) - 16;
+        while (n > 0) {
+            const int k = n < ct ? n : ct;
+            a <<= k;
+            c <<= k;
+            ct -= k;
+            n -= k;
+            if (ct == 0) byteout();
+        }
     }
-    __device__ __forceinline__ void encode(T1Warp &s, int cx, int d)
+    __device__ __forceinline__ void encode(uint32_t *cxw, int cx, int d)
     {
-        const uint32_t st8 = s.cx[cx], mps = st8 & 1u;
-        const uint32_t row = kMq.w[st8 >> 1], qe = row & 0xFFFFu;
+        const uint32_t w = cxw[cx], qe = w & 0xFFFFu, mps = w >> 31;
         a -= qe;
         if ((uint32_t)d == mps) {
-            if ((a & 0x8000) == 0) {
-                if (a < qe) a = qe;
-                else c += qe;
-                s.cx[cx] = (uint8_t)((((row >> 16) & 63u) << 1) | mps);
-                renorm();
-            } else {
+            if (a & 0x8000) {
                 c += qe;
+                return;
             }
+            if (a < qe) a = qe;
+            else c += qe;
+            cxw[cx] = kMq.w[(w >> 16) & 63u] | (mps << 31);
         } else {
             if (a < qe) c += qe;
             else a = qe;
-            s.cx[cx] = (uint8_t)((((row >> 22) & 63u) << 1) | (mps ^ (row >> 28)));
-            renorm();
+            cxw[cx] = kMq.w[(w >> 22) & 63u] | ((mps ^ ((w >> 28) & 1u)) << 31);
         }
+        renorm();
     }
     // Terminates the codeword; returns its length in bytes.
-    __device__ int flush()
+    __device__ __forceinline__ int flush()
     {
         const uint32_t tempc = c + a;
         c |= 0xFFFF;
@@ -277,83 +281,137 @@ __device__ __forceinline__ void code_sign(T1Warp &s, Mqe &e, int i, uint16_t w)
     hc = hc < -1 ? -1 : (hc > 1 ? 1 : hc);
     vc = vc < -1 ? -1 : (vc > 1 ? 1 : vc);
     const uint8_t sc = kSc[(hc + 1) + 3 * (vc + 1)];
-    e.encode(s, sc & 0x1F, ((w & kNeg) ? 1 : 0) ^ (sc >> 7));
+    e.encode(s.cxw, sc & 0x1F, ((w & kNeg) ? 1 : 0) ^ (sc >> 7));
 }
 
-// One coding pass of plane p by lane 0: type 0 significance propagation,
-// 1 magnitude refinement, 2 cleanup.  A stripe column's four state words
-// are read as one 64-bit word first: a column with no position to code in
-// this pass is skipped on it (no position of it can become one, since only
-// coding a position of the column changes the column's membership), and it
-// decides the run-length mode of the cleanup.
-__device__ void t1_pass(T1Warp &s, Mqe &e, int type, int p, int w, int h, int ori)
+// One coding pass of the current plane by the warp: type 0 significance
+// propagation, 1 magnitude refinement, 2 cleanup (see the file header);
+// e is lane 0's coder.  zc: the zero-coding contexts of the block's
+// orientation by the state word's neighbour bits (0-6).  A stripe
+// column's four state words are one 64-bit word.
+__device__ __forceinline__ void t1_pass(T1Warp &s, Mqe &e, int type, int w, int h, const uint8_t *zc, int lane)
 {
-    (void)p;
     uint16_t *st = s.st;
     constexpr uint64_t kRep = 0x0001000100010001ull;
     for (int y0 = 0; y0 < h; y0 += 4) {
         const int nr = min(4, h - y0);
         // 16-bit lanes of the stripe's rows that exist
         const uint64_t rows = nr >= 4 ? ~0ull : ((1ull << (16 * nr)) - 1);
-        for (int x = 0; x < w; x++) {
-            const int i0 = sti(x, y0);
-            const uint64_t q4 = *reinterpret_cast<const uint64_t *>(st + i0) & rows;
-            const uint64_t sig4 = q4 & (kRep * kSig), vis4 = q4 & (kRep * kVis), nb4 = q4 & (kRep * kNbMask);
-            if (type == 0) {
-                // a lane with neighbours and without significance
-                const uint64_t has_nb = (nb4 + kRep * 0x7F) & (kRep * 0x80);  // bit 7 (= kSig) where nb != 0
-                if ((has_nb & ~sig4) == 0) continue;
-            } else if (type == 1) {
-                if ((sig4 & ~(vis4 >> 2)) == 0) continue;  // kVis = kSig << 2
-            } else if (((sig4 | (vis4 >> 2)) ^ (kRep * kSig & rows)) == 0) {
-                continue;  // every row significant or visited
-            }
-            int y = y0;
-            if (type == 2 && nr == 4 && (q4 & (kRep * (kNbMask | kSig | kVis))) == 0) {
-                // run-length mode: four uncoded, insignificant samples with
-                // all-zero neighbourhoods
-                int r = 4;
+        if (type == 1) {
+            // refinement: every lane forms its columns' symbols (columns
+            // lane and lane + 32, rows in order), placed in scan order by a
+            // prefix sum over the lanes of each half
+            int total = 0;
 #pragma unroll
-                for (int k = 3; k >= 0; k--)
-                    if ((s.bm[y0 + k] >> x) & 1) r = k;
-                e.encode(s, kCtxRL, r < 4);
-                if (r == 4) continue;
-                e.encode(s, kCtxUni, r >> 1);
-                e.encode(s, kCtxUni, r & 1);
-                const int i = i0 + r;
-                code_sign(s, e, i, st[i]);
-                st[i] |= kSig | (uint16_t)(3u << kEvShift);
-                set_sig(st, i);
-                y = y0 + r + 1;
+            for (int half = 0; half < 2; half++) {
+                const int x = half * 32 + lane;
+                uint32_t q = 0;  // up to four 3-bit symbols
+                int n = 0;
+                if (x < w) {
+                    const int i0 = sti(x, y0);
+                    for (int r = 0; r < nr; r++) {
+                        const uint16_t wd = st[i0 + r];
+                        if (!(wd & kSig) || (wd & kVis)) continue;
+                        const uint32_t ctx = (wd & kRef) ? 2u : ((wd & kNbMask) ? 1u : 0u);
+                        const uint32_t bit = (uint32_t)(s.bm[y0 + r] >> x) & 1u;
+                        q |= ((ctx << 1) | bit) << (3 * n);
+                        n++;
+                        st[i0 + r] = wd | kRef | (uint16_t)(2u << kEvShift);
+                    }
+                }
+                int incl = n;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int at = total + incl - n;
+                for (int k = 0; k < n; k++) s.mq[at + k] = (uint8_t)((q >> (3 * k)) & 7u);
+                total += __shfl_sync(0xffffffffu, incl, 31);
             }
-            for (; y < y0 + nr; y++) {
-                const int i = i0 + (y - y0);
-                const uint16_t wd = st[i];
+            __syncwarp();
+            if (lane == 0)
+                for (int k = 0; k < total; k++) {
+                    const uint32_t q = s.mq[k];
+                    e.encode(s.cxw, 14 + (int)(q >> 1), (int)(q & 1u));
+                }
+            __syncwarp();
+            continue;
+        }
+        // candidate columns: significance pass, a row with neighbours and
+        // without significance; cleanup, a row neither significant nor visited
+        uint64_t cand = 0;
+#pragma unroll
+        for (int half = 0; half < 2; half++) {
+            const int x = half * 32 + lane;
+            bool c = false;
+            if (x < w) {
+                const uint64_t q4 = *reinterpret_cast<const uint64_t *>(st + sti(x, y0)) & rows;
+                const uint64_t sig4 = q4 & (kRep * kSig), vis4 = q4 & (kRep * kVis), nb4 = q4 & (kRep * kNbMask);
                 if (type == 0) {
-                    if ((wd & kSig) || (wd & kNbMask) == 0) continue;
-                } else if (type == 1) {
-                    if (!(wd & kSig) || (wd & kVis)) continue;
-                    const int mcx = (wd & kRef) ? 16 : ((wd & kNbMask) ? 15 : 14);
-                    e.encode(s, mcx, (int)((s.bm[y] >> x) & 1));
-                    st[i] = wd | kRef | (uint16_t)(2u << kEvShift);
-                    continue;
+                    const uint64_t has_nb = (nb4 + kRep * 0x7F) & (kRep * 0x80);  // bit 7 (= kSig) where nb != 0
+                    c = (has_nb & ~sig4) != 0;
                 } else {
-                    if (wd & (kSig | kVis)) continue;
+                    c = ((sig4 | (vis4 >> 2)) ^ (kRep * kSig & rows)) != 0;  // kVis = kSig << 2
                 }
-                const int bit = (int)((s.bm[y] >> x) & 1);
-                e.encode(s, kZc.t[ori][nb_index(wd)], bit);
-                uint16_t nw = wd;
-                if (type == 0) nw |= kVis;
-                if (bit) {
-                    code_sign(s, e, i, wd);
-                    nw |= kSig | (uint16_t)((type == 0 ? 1u : 3u) << kEvShift);
-                    st[i] = nw;
-                    set_sig(st, i);
-                } else {
-                    st[i] = nw;
+            }
+            cand |= (uint64_t)__ballot_sync(0xffffffffu, c) << (32 * half);
+        }
+        if (lane == 0) {
+            while (cand) {
+                const int x = __ffsll((long long)cand) - 1;
+                cand &= cand - 1;
+                const int i0 = sti(x, y0);
+                bool newsig = false;
+                int y = y0;
+                if (type == 2 && nr == 4) {
+                    const uint64_t q4 = *reinterpret_cast<const uint64_t *>(st + i0);
+                    if ((q4 & (kRep * (kNbMask | kSig | kVis))) == 0) {
+                        // run-length mode: four uncoded, insignificant samples
+                        // with all-zero neighbourhoods
+                        int r = 4;
+#pragma unroll
+                        for (int k = 3; k >= 0; k--)
+                            if ((s.bm[y0 + k] >> x) & 1) r = k;
+                        e.encode(s.cxw, kCtxRL, r < 4);
+                        if (r == 4) continue;
+                        e.encode(s.cxw, kCtxUni, r >> 1);
+                        e.encode(s.cxw, kCtxUni, r & 1);
+                        const int i = i0 + r;
+                        code_sign(s, e, i, st[i]);
+                        st[i] |= kSig | (uint16_t)(3u << kEvShift);
+                        set_sig(st, i);
+                        y = y0 + r + 1;
+                    }
                 }
+                for (; y < y0 + nr; y++) {
+                    const int i = i0 + (y - y0);
+                    const uint16_t wd = st[i];
+                    if (type == 0) {
+                        if ((wd & kSig) || (wd & kNbMask) == 0) continue;
+                    } else {
+                        if (wd & (kSig | kVis)) continue;
+                    }
+                    const int bit = (int)((s.bm[y] >> x) & 1);
+                    e.encode(s.cxw, zc[wd & kNbMask], bit);
+                    uint16_t nw = wd;
+                    if (type == 0) nw |= kVis;
+                    if (bit) {
+                        code_sign(s, e, i, wd);
+                        nw |= kSig | (uint16_t)((type == 0 ? 1u : 3u) << kEvShift);
+                        st[i] = nw;
+                        set_sig(st, i);
+                        newsig = true;
+                    } else {
+                        st[i] = nw;
+                    }
+                }
+                // a new significance gives the next column's samples a
+                // neighbour: it joins the significance pass's candidates
+                if (type == 0 && newsig && x + 1 < w) cand |= 1ull << (x + 1);
             }
         }
+        __syncwarp();
     }
 }
 
@@ -400,11 +458,18 @@ __device__ void cb_geometry(int j, int W, int H, int D, int &band, int &ori, int
 }  // namespace
 
 // Tier-1 coding: one warp per code-block of the job (taken dynamically).
-__global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ job)
+__global__ void __launch_bounds__(32 * kT1Warps, 3) k_t1(const CsJob *__restrict__ job)
 {
     extern __shared__ __align__(16) unsigned char t1sm[];
+    __shared__ uint8_t s_zc[4][128];  // zero-coding context by orientation and the state word's bits 0-6
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     T1Warp &s = reinterpret_cast<T1Warp *>(t1sm)[wp];
+    for (int i = threadIdx.x; i < 4 * 128; i += blockDim.x) {
+        const int o = i >> 7, b = i & 127;
+        // counts beyond their range (h, v > 2, d > 4) never occur
+        s_zc[o][b] = (uint8_t)zc_rule(o, min(b & 3, 2), min((b >> 2) & 3, 2), min(b >> 4, 4));
+    }
+    __syncthreads();
     // code-blocks are taken in order from the job's counter, one per warp
     // at a time: their costs differ by orders of magnitude
     for (;;) {
@@ -451,9 +516,7 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
         }
         continue;
     }
-    if (lane < kNctx) {
-        s.cx[lane] = (uint8_t)((lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0))) << 1);
-    }
+    if (lane < kNctx) s.cxw[lane] = kMq.w[lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0))];
     uint8_t *const cbytes = F.cbytes + (size_t)jb * job->cbcap;
     Mqe e;
     int k = 0, pos = 0;
@@ -502,10 +565,10 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
         }
         if (p < 0) break;
         __syncwarp();
-        if (lane == 0) {
-            for (int type = (p == planes - 1 ? 2 : 0); type <= 2; type++, k++) {
-                e.init(cbytes + pos, job->cbcap - pos);
-                t1_pass(s, e, type, p, cw, ch, ori);
+        for (int type = (p == planes - 1 ? 2 : 0); type <= 2; type++, k++) {
+            if (lane == 0) e.init(cbytes + pos, job->cbcap - pos);
+            t1_pass(s, e, type, cw, ch, s_zc[ori], lane);
+            if (lane == 0) {
                 const int len = e.flush();
                 over = over || e.over;
                 plen[k] = len;
