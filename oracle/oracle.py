@@ -575,12 +575,14 @@ def pcrd(blocks, budget: int, iters: int = 64):
     return keep(hi)[0]
 
 
-def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_depth: int, budget: int = 0):
+def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_depth: int, budget: int = 0,
+                 fmt: str = "container", delta_base: float = 1.0):
     """Tier-1 coding of every code-block of a Mallat plane, rate control to
     `budget` bytes of pass data (0: lossless in the passes), and the frame
     container: a 32-byte header, a 16-byte entry per code-block, then per
-    code-block the kept passes' 16-bit lengths and bytes.  Returns (bytes,
-    block records)."""
+    code-block the kept passes' 16-bit lengths and bytes; with fmt="j2c" a
+    JPEG2000 Part 1 codestream of the same kept passes instead
+    (codestream_j2c).  Returns (bytes, block records)."""
     import struct
     coeffs = _c(coeffs, np.int32)
     h, w = coeffs.shape
@@ -599,8 +601,199 @@ def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_
                                  blk["planes"], len(blk["plen"]), k, 0))
         data.append(body)
         off += len(body)
+    if fmt == "j2c":
+        return codestream_j2c(blocks, w, h, levels, wavelet, bit_depth, delta_base), blocks
     hdr = struct.pack("<4sIIIBBBBIII", _MAGIC, 1, w, h, wavelet, levels, shift, bit_depth, len(blocks), off, 0)
     return hdr + b"".join(table) + b"".join(data), blocks
+
+
+# ------------------------------------------- JPEG2000 Part 1 codestream --
+# ISO/IEC 15444-1: Annex A (markers), Annex B (tier-2: packets, tag trees,
+# packet headers), Annex E (the quantisation exponents and M_b).  One tile,
+# one component, one quality layer, LRCP progression, no precinct
+# partition (one precinct per resolution: one packet per resolution),
+# 64 x 64 code-blocks, code-block style "termination on each coding pass",
+# no RGN marker: Part 1 signals only the maximum-shift RoI method, so the
+# scaling-based RoI travels in the coefficients themselves (a Part 1
+# decoder returns the up-shifted coefficients; undoing the shift needs the
+# RoI mask, as the scaling method does).
+
+
+class _BitWriter:
+    """Packet-header bits, most significant first; a byte that follows a
+    0xFF byte carries only 7 bits (its MSB is 0), and the header never ends
+    on 0xFF (Annex B.10.1)."""
+
+    def __init__(self):
+        self.out = bytearray()
+        self.cur = 0
+        self.n = 0
+        self.cap = 8
+
+    def put(self, b: int):
+        self.cur = (self.cur << 1) | (b & 1)
+        self.n += 1
+        if self.n == self.cap:
+            self.out.append(self.cur)
+            self.cap = 7 if self.cur == 0xFF else 8
+            self.cur = 0
+            self.n = 0
+
+    def put_bits(self, v: int, nbits: int):
+        for i in range(nbits - 1, -1, -1):
+            self.put((v >> i) & 1)
+
+    def flush(self) -> bytes:
+        if self.n:
+            self.out.append(self.cur << (self.cap - self.n))
+            self.n = 0
+        if self.out and self.out[-1] == 0xFF:
+            self.out.append(0)
+        return bytes(self.out)
+
+
+class _TagTree:
+    """Tag tree over a nx x ny grid of leaves (Annex B.10.2): every node
+    holds the minimum of the leaves below it; a leaf's value is sent as the
+    path from the root down, each node's value in excess of its parent's as
+    0 bits closed by a 1 bit, and only up to a threshold; what a node has
+    already sent is remembered (low bound, known)."""
+
+    def __init__(self, nx: int, ny: int, values):
+        self.levels = []
+        w, h = nx, ny
+        while True:
+            self.levels.append((w, h))
+            if w == 1 and h == 1:
+                break
+            w, h = (w + 1) // 2, (h + 1) // 2
+        big = 1 << 30
+        self.val = [[big] * (lw * lh) for lw, lh in self.levels]
+        self.low = [[0] * (lw * lh) for lw, lh in self.levels]
+        self.known = [[False] * (lw * lh) for lw, lh in self.levels]
+        for y in range(ny):
+            for x in range(nx):
+                v = values[y * nx + x]
+                xx, yy = x, y
+                for l, (lw, lh) in enumerate(self.levels):
+                    i = yy * lw + xx
+                    self.val[l][i] = min(self.val[l][i], v)
+                    xx, yy = xx // 2, yy // 2
+
+    def encode(self, bw: _BitWriter, x: int, y: int, threshold: int):
+        path = []
+        xx, yy = x, y
+        for l, (lw, lh) in enumerate(self.levels):
+            path.append((l, yy * lw + xx))
+            xx, yy = xx // 2, yy // 2
+        low = 0
+        for l, i in reversed(path):  # root first
+            low = max(low, self.low[l][i])
+            while low < threshold:
+                if low >= self.val[l][i]:
+                    if not self.known[l][i]:
+                        bw.put(1)
+                        self.known[l][i] = True
+                    break
+                bw.put(0)
+                low += 1
+            self.low[l][i] = low
+
+
+def _passes_codeword(bw: _BitWriter, n: int):
+    """Number of coding passes included (Annex B.10.6, Table B.4)."""
+    if n == 1:
+        bw.put(0)
+    elif n == 2:
+        bw.put_bits(0b10, 2)
+    elif n <= 5:
+        bw.put_bits(0b1100 | (n - 3), 4)
+    elif n <= 36:
+        bw.put_bits(0b1111, 4)
+        bw.put_bits(n - 6, 5)
+    elif n <= 164:
+        bw.put_bits(0b111111111, 9)
+        bw.put_bits(n - 37, 7)
+    else:
+        raise ValueError("more than 164 coding passes")
+
+
+def band_exponents(levels: int, wavelet: int, bit_depth: int, delta_base: float = 1.0):
+    """(eps, mu) per band of the quantisation-step table's index: 9/7 the
+    steps' JPEG2000 form; 5/3 (no quantisation) eps = bit depth + log2 of
+    the band's nominal gain (0 LL, 1 HL and LH, 2 HH), mu = 0."""
+    nb = 3 * levels + 1
+    if wavelet == 97:
+        _, _, e, m = delta_table(levels, bit_depth, delta_base)
+        return [int(v) for v in e], [int(v) for v in m]
+    eps = [bit_depth + (0 if b == 3 * levels else (1 if b % 3 < 2 else 2)) for b in range(nb)]
+    return eps, [0] * nb
+
+
+def codestream_j2c(blocks, w: int, h: int, levels: int, wavelet: int, bit_depth: int,
+                   delta_base: float = 1.0) -> bytes:
+    """A JPEG2000 Part 1 codestream of one frame from its code-blocks' kept
+    passes (encode_frame's block records with 'nkeep').  The guard bits G are
+    the fewest (at least 1) for which every block's bit-planes fit the
+    band's M_b = G + eps_b - 1 (Annex E.1); more than 7 cannot be signalled."""
+    import struct
+    eps, mu = band_exponents(levels, wavelet, bit_depth, delta_base)
+    need = [blk["planes"] - eps[blk["band"]] + 1 for blk in blocks if blk["planes"] > 0]
+    G = max([1] + need)
+    if G > 7:
+        raise ValueError("coefficient bit-planes beyond what 7 guard bits signal")
+    # band order of QCD and of the packets: LL_D, then HL, LH, HH of D .. 1
+    order = [3 * levels] + [3 * (l - 1) + o for l in range(levels, 0, -1) for o in range(3)]
+    cs = bytearray(b"\xff\x4f")  # SOC
+    cs += struct.pack(">HHHIIIIIIIIHBBB", 0xFF51, 41, 0, w, h, 0, 0, w, h, 0, 0, 1, bit_depth - 1, 1, 1)  # SIZ
+    cs += struct.pack(">HHBBHBBBBBB", 0xFF52, 12, 0, 0, 1, 0, levels, 4, 4, 0x04, 1 if wavelet == 53 else 0)  # COD
+    if wavelet == 53:
+        cs += struct.pack(">HHB", 0xFF5C, 3 + len(order), G << 5) + bytes(eps[b] << 3 for b in order)
+    else:
+        cs += struct.pack(">HHB", 0xFF5C, 3 + 2 * len(order), (G << 5) | 2)
+        cs += b"".join(struct.pack(">H", (eps[b] << 11) | mu[b]) for b in order)
+    # packets, one per resolution: LL_D, then (HL, LH, HH) of level D .. 1
+    byband = {}
+    for blk in blocks:
+        byband.setdefault(blk["band"], []).append(blk)
+    res = [[3 * levels]] + [[3 * (l - 1), 3 * (l - 1) + 1, 3 * (l - 1) + 2] for l in range(levels, 0, -1)]
+    data = bytearray()
+    for bands in res:
+        bw = _BitWriter()
+        body = bytearray()
+        if not any(blk["nkeep"] > 0 for b in bands for blk in byband.get(b, [])):
+            bw.put(0)  # empty packet
+        else:
+            bw.put(1)
+            for b in bands:
+                bl = byband.get(b, [])
+                if not bl:
+                    continue
+                x0s = sorted({blk["x0"] for blk in bl})
+                y0s = sorted({blk["y0"] for blk in bl})
+                nx, ny = len(x0s), len(y0s)
+                Mb = G + eps[b] - 1
+                incl = _TagTree(nx, ny, [0 if blk["nkeep"] > 0 else 1 for blk in bl])
+                zbp = _TagTree(nx, ny, [Mb - blk["planes"] for blk in bl])
+                for j, blk in enumerate(bl):
+                    cx, cy = j % nx, j // nx
+                    incl.encode(bw, cx, cy, 1)
+                    n = blk["nkeep"]
+                    if n == 0:
+                        continue
+                    zbp.encode(bw, cx, cy, 1 << 30)
+                    _passes_codeword(bw, n)
+                    lens = [int(v) for v in blk["plen"][:n]]
+                    need_bits = max(max(1, L.bit_length()) for L in lens)
+                    k = max(0, need_bits - 3)  # Lblock starts at 3
+                    bw.put_bits((1 << (k + 1)) - 2, k + 1)  # k ones, then a zero
+                    for L in lens:  # one codeword segment per pass
+                        bw.put_bits(L, 3 + k)
+                    body += blk["code"][: sum(lens)].tobytes()
+        data += bw.flush() + body
+    psot = 12 + 2 + len(data)
+    cs += struct.pack(">HHHIBB", 0xFF90, 10, 0, psot, 0, 1) + b"\xff\x93" + data + b"\xff\xd9"
+    return bytes(cs)
 
 
 def decode_frame(stream: bytes, midpoint: bool = True) -> np.ndarray:
