@@ -64,6 +64,9 @@ WORKLOADS = {
     # rate control, container)
     "ebcot_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                           dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
+    # the same with JPEG2000 Part 1 codestreams instead of containers
+    "j2c_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                        dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0, codestream_format=1),
     # four streams of it (small case for profiler captures of the coder)
     "ebcot_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
@@ -421,7 +424,8 @@ def run_codestream(F, wl, frames, steps, warmup, profile_steps=3):
     import torch
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
                precision=wl["precision"], max_batch_frames=64, result_ring=8, flags=F.MANUAL,
-               codestream_bpp=wl["codestream_bpp"], device=torch.cuda.current_device())
+               codestream_bpp=wl["codestream_bpp"], codestream_format=wl.get("codestream_format", 0),
+               device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     H, W, L = wl["h"], wl["w"], wl["dwt_levels"]
     cap = F.flowroi_codestream_bound(W, H, L) // 4

@@ -83,6 +83,10 @@ extern "C" {
 #define FLOWROI_FP32 32         /* pyramid and expansion fields stored in float */
 #define FLOWROI_FP16 16         /* ... stored in half, all arithmetic in float */
 
+/* codestream formats (flowroi_config.codestream_format, flowroi_cs_job.format) */
+#define FLOWROI_CS_CONTAINER 0  /* the library's frame container (layout below) */
+#define FLOWROI_CS_J2C 1        /* JPEG2000 Part 1 codestream (ISO/IEC 15444-1) */
+
 /* flowroi_config.flags */
 #define FLOWROI_KEEP_INTERMEDIATES 0x1u /* keep flow, saliency, pre-morphology mask and
                                            (9/7) float coefficients per result slot */
@@ -171,6 +175,10 @@ typedef struct flowroi_config {
      * bits per pixel of pass data; fetch it with flowroi_get_codestream.
      * 0 = off. (0) */
     float codestream_bpp;
+    /* Format of those codestreams: FLOWROI_CS_CONTAINER (the library's
+     * frame container) or FLOWROI_CS_J2C (a JPEG2000 Part 1 codestream, see
+     * flowroi_encode_codestreams).  (FLOWROI_CS_CONTAINER) */
+    int32_t codestream_format;
     /* Tile table (launch and tile shapes per frame width class, see
      * flowroi_autotune): path of a JSON file read at create, or NULL for
      * the built-in shapes.  Not a method parameter: results do not depend
@@ -407,6 +415,24 @@ FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, 
  * order within a band); then the data: per code-block the kept passes'
  * u16 lengths and their bytes.
  *
+ * JPEG2000 Part 1 codestream (format FLOWROI_CS_J2C; ISO/IEC 15444-1, the
+ * same kept passes): SOC; SIZ (one tile of the whole frame, one unsigned
+ * component of bit_depth bits); COD (LRCP, one quality layer, no
+ * multi-component transform, `levels` decomposition levels, 64 x 64
+ * code-blocks, code-block style "termination on each coding pass",
+ * transform 5/3 reversible or 9/7 irreversible, no precinct partition);
+ * QCD (5/3: no quantisation, exponent bit_depth + the band's log2 gain;
+ * 9/7: scalar expounded, each band's (exponent, mantissa) of the steps
+ * flowroi_quant_steps gives for the context's delta_base; guard bits the
+ * fewest, 1 to 7, that make every code-block's bit-planes fit); one
+ * tile-part (SOT, SOD) of one packet per resolution level (packet headers
+ * with inclusion and zero-bit-plane tag trees, pass counts, Lblock and one
+ * length per pass); EOC.  No RGN marker: Part 1 signals only the
+ * maximum-shift RoI method, so the RoI coefficients' up-shift by `shift`
+ * bits stays in the data; a Part 1 decoder returns the shifted
+ * coefficients, and undoing the shift needs the RoI mask.  A frame whose
+ * bit-planes would need more than 7 guard bits gets FLOWROI_ERANGE.
+ *
  * One job per frame:
  *   coeffs        width x height int32 Mallat plane (the layout of
  *                 flowroi_get_coeffs), magnitudes below 2^24
@@ -415,7 +441,8 @@ FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, 
  *   wavelet, shift, bit_depth   recorded in the header (53 or 97, [0, 15],
  *                 [1, 16])
  *   budget_bytes  pass-data budget; <= 0 keeps every pass
- *   out, out_cap  destination of the container and its capacity
+ *   out, out_cap  destination of the codestream and its capacity
+ *   format        FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C
  *   out_len       set to the container's length (or, when it does not fit,
  *                 to the length it needs, with FLOWROI_ERANGE)
  * on_device: coeffs and out are device pointers of the context's device
@@ -434,6 +461,8 @@ typedef struct {
     uint8_t *out;
     uint64_t out_cap;
     uint64_t out_len;
+    int32_t format;      /* FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C */
+    int32_t reserved;    /* 0 */
 } flowroi_cs_job;
 FLOWROI_API int flowroi_encode_codestreams(flowroi_ctx *ctx, int n, flowroi_cs_job *jobs, int on_device);
 /* The container of a frame coded in the stream path (config.codestream_bpp

@@ -84,6 +84,10 @@ constexpr int kMaxPlanes = 24;                 // magnitudes below 2^24
 constexpr int kMaxPasses = 3 * kMaxPlanes - 2;
 constexpr int kCbInfo = 8;                     // per code-block: planes, passes, kept, status, hull size, data size, data offset
 constexpr int kCsHeader = 32, kCsEntry = 16;   // container header and per-code-block entry bytes
+// JPEG2000 codestream: bytes of the markers (with 3 x 8 + 1 bands) and of
+// a code-block's packet-header bits at most (tag-tree paths, pass count,
+// Lblock, 70 lengths of up to 16 bits, one stuffed bit per byte)
+constexpr int kJ2cHeader = 256, kJ2cPerBlock = 192;
 constexpr unsigned kErrCbRange = 3u;           // error word: a code-block or container exceeded its buffer or range
 constexpr int kCbBytes = 32768;                // pass bytes a code-block may produce
 // device bytes of a code-block's scratch (pass bytes, lengths, distortions, info, hull)
@@ -104,6 +108,10 @@ struct CsFrame {
     int32_t *hk;          // [kMaxPasses + 1] hull scratch
     double *hs;           // [kMaxPasses + 1]
     long long *flen;      // the container's length (negative: it needs that many bytes; -1: a code-block out of range)
+    int format;           // 0: the library's frame container, 1: JPEG2000 Part 1 codestream
+    int pad_;
+    uint8_t eps[kMaxSubbands];   // 1: the bands' quantisation exponents (table index as delta[])
+    uint16_t mu[kMaxSubbands];   // 1: and mantissas (9/7)
 };
 struct CsJob {
     int nframes, ncb;

@@ -720,7 +720,8 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
     long long off = s_scan[tid] - mine;
     const long long data = s_scan[nt - 1];
     const long long total = kCsHeader + (long long)kCsEntry * n + data;
-    const bool fits = total <= F.cap && bad == 0;
+    const bool container = F.format == 0;  // else k_j2c writes the frame
+    const bool fits = container && total <= F.cap && bad == 0;
     for (int j = j0; j < j1; j++) {
         const int g = j;
         F.info[(size_t)g * kCbInfo + 6] = (int32_t)off;
@@ -748,7 +749,7 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
         }
         off += F.info[(size_t)g * kCbInfo + 5];
     }
-    if (tid == 0) {
+    if (tid == 0 && container) {
         if (fits) {
             uint8_t *hd = F.out;
             auto put32 = [&](int at, uint32_t v) {
@@ -791,7 +792,7 @@ __global__ void __launch_bounds__(256) k_cs_copy(const CsJob *__restrict__ job)
         int f = 0;
         while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
         const CsFrame &F = job->frames[f];
-        if (*F.flen < 0) continue;
+        if (F.format != 0 || *F.flen < 0) continue;
         const int j = g - F.cb0;
         const int32_t *info = F.info + (size_t)j * kCbInfo;
         const int nk = info[2];
@@ -805,6 +806,312 @@ __global__ void __launch_bounds__(256) k_cs_copy(const CsJob *__restrict__ job)
         for (int k = 0; k < nk; k++) nbytes += pl[k];
         const uint8_t *src = F.cbytes + (size_t)j * job->cbcap;
         for (int i = lane; i < nbytes; i += 32) dst[2 * nk + i] = src[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// JPEG2000 Part 1 codestream of a frame (CsFrame::format 1) from its
+// code-blocks' kept passes (ISO/IEC 15444-1 Annex A markers, Annex B
+// packets): SOC, SIZ, COD, QCD, one tile-part (SOT, SOD) holding one packet
+// per resolution (one layer, LRCP, no precinct partition), EOC.  A packet
+// header codes, per band and code-block in raster order, its inclusion and
+// its missing most significant bit-planes with two tag trees, the number of
+// passes (Table B.4), the Lblock increment and one length per pass (every
+// pass is a terminated codeword segment); a byte after 0xFF carries 7 bits
+// and a header never ends on 0xFF.  No RGN marker: Part 1 signals only the
+// maximum-shift RoI, so the scaling-based up-shift stays in the data.  The
+// guard bits are the fewest (at least 1) that make every block's bit-planes
+// fit M_b = G + eps_b - 1; more than 7 cannot be signalled (length -1).
+
+namespace {
+
+// Packet-header bits of lane 0, written straight into the output.
+struct HdrBits {
+    uint8_t *out;
+    long long cap, pos;
+    uint32_t cur, last;
+    int n, room, nbytes;
+    bool over;
+    __device__ __forceinline__ void init(uint8_t *o, long long c, long long p)
+    {
+        out = o;
+        cap = c;
+        pos = p;
+        cur = last = 0;
+        n = nbytes = 0;
+        room = 8;
+        over = false;
+    }
+    __device__ __forceinline__ void emit(uint32_t b)
+    {
+        if (pos < cap) out[pos] = (uint8_t)b;
+        else over = true;
+        pos++;
+        nbytes++;
+        last = b;
+    }
+    __device__ __forceinline__ void put(int b)
+    {
+        cur = (cur << 1) | (uint32_t)(b & 1);
+        if (++n == room) {
+            emit(cur);
+            room = cur == 0xFF ? 7 : 8;
+            cur = 0;
+            n = 0;
+        }
+    }
+    __device__ __forceinline__ void put_bits(uint32_t v, int k)
+    {
+        for (int i = k - 1; i >= 0; i--) put((int)((v >> i) & 1u));
+    }
+    __device__ __forceinline__ void flush()
+    {
+        if (n) {
+            emit(cur << (room - n));
+            n = 0;
+        }
+        if (nbytes && last == 0xFF) emit(0);
+    }
+};
+
+// A tag tree over nx x ny leaves in global scratch: per node its value
+// (the least leaf below it) and its state (low bound, bit 31: known).
+struct TagTree {
+    int *val, *st;
+    int nlev, lw[20], off[20];
+    __device__ void build(int *mem, int nx, int ny)
+    {
+        int w = nx, h = ny, o = 0;
+        nlev = 0;
+        for (;;) {
+            lw[nlev] = w;
+            off[nlev] = o;
+            o += w * h;
+            nlev++;
+            if (w == 1 && h == 1) break;
+            w = (w + 1) >> 1;
+            h = (h + 1) >> 1;
+        }
+        val = mem;
+        st = mem + o;
+        for (int i = 0; i < o; i++) {
+            val[i] = 0x3fffffff;
+            st[i] = 0;
+        }
+    }
+    __device__ int nodes() const { return off[nlev - 1] + 1; }
+    __device__ void set(int x, int y, int v)
+    {
+        for (int l = 0; l < nlev; l++) {
+            int &t = val[off[l] + (y >> l) * lw[l] + (x >> l)];
+            if (v < t) t = v;
+        }
+    }
+    __device__ void encode(HdrBits &bw, int x, int y, int threshold)
+    {
+        int low = 0;
+        for (int l = nlev - 1; l >= 0; l--) {
+            const int i = off[l] + (y >> l) * lw[l] + (x >> l);
+            bool known = st[i] < 0;
+            const int nl = st[i] & 0x7fffffff;
+            if (low < nl) low = nl;
+            while (low < threshold) {
+                if (low >= val[i]) {
+                    if (!known) {
+                        bw.put(1);
+                        known = true;
+                    }
+                    break;
+                }
+                bw.put(0);
+                low++;
+            }
+            st[i] = low | (known ? (int)0x80000000 : 0);
+        }
+    }
+};
+
+__device__ __forceinline__ void passes_codeword(HdrBits &bw, int n)
+{
+    if (n == 1) bw.put(0);
+    else if (n == 2) bw.put_bits(2u, 2);
+    else if (n <= 5) bw.put_bits(12u | (uint32_t)(n - 3), 4);
+    else if (n <= 36) {
+        bw.put_bits(15u, 4);
+        bw.put_bits((uint32_t)(n - 6), 5);
+    } else {
+        bw.put_bits(511u, 9);
+        bw.put_bits((uint32_t)(n - 37), 7);
+    }
+}
+
+__device__ __forceinline__ int bit_length(uint32_t v) { return v ? 32 - __clz(v) : 0; }
+
+}  // namespace
+
+// One warp per frame (grid-stride over the job's frames with format 1).
+__global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
+{
+    const int lane = threadIdx.x;
+    for (int fi = blockIdx.x; fi < job->nframes; fi += gridDim.x) {
+        const CsFrame &F = job->frames[fi];
+        if (F.format != 1) continue;
+        const int n = F.ncb, D = F.levels, W = F.w, H = F.h;
+        uint8_t *const out = F.out;
+        const long long cap = F.cap;
+        // guard bits, and code-blocks out of the coder's range
+        int need = 1, bad = 0;
+        for (int j = lane; j < n; j += 32) {
+            const int32_t *in = F.info + (size_t)j * kCbInfo;
+            if (in[3] != 0) bad = 1;
+            if (in[0] > 0) {
+                int band, ori, x0, y0, cw, ch;
+                cb_geometry(j, W, H, D, band, ori, x0, y0, cw, ch);
+                need = max(need, in[0] - (int)F.eps[band] + 1);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            need = max(need, __shfl_xor_sync(0xffffffffu, need, o));
+            bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+        }
+        if (bad || need > 7) {
+            if (lane == 0) {
+                *F.flen = -1;
+                if (job->err) atomicExch(job->err, kErrCbRange);
+            }
+            continue;
+        }
+        const int G = need;
+        long long pos = 0, sot = 0;
+        bool over = false;
+        if (lane == 0) {
+            auto b8 = [&](uint32_t v) {
+                if (pos < cap) out[pos] = (uint8_t)v;
+                else over = true;
+                pos++;
+            };
+            auto b16 = [&](uint32_t v) { b8(v >> 8); b8(v & 0xFF); };
+            auto b32 = [&](uint32_t v) { b16(v >> 16); b16(v & 0xFFFF); };
+            b16(0xFF4F);                                      // SOC
+            b16(0xFF51); b16(41); b16(0);                     // SIZ: Lsiz, Rsiz
+            b32((uint32_t)W); b32((uint32_t)H); b32(0); b32(0);  // image size, offset
+            b32((uint32_t)W); b32((uint32_t)H); b32(0); b32(0);  // one tile
+            b16(1); b8((uint32_t)(F.bit_depth - 1)); b8(1); b8(1);  // one unsigned component
+            b16(0xFF52); b16(12); b8(0); b8(0); b16(1); b8(0);  // COD: LRCP, one layer, no MCT
+            b8((uint32_t)D); b8(4); b8(4); b8(0x04); b8(F.wavelet == 53 ? 1 : 0);
+            const int nb = 3 * D + 1;
+            b16(0xFF5C);                                      // QCD
+            if (F.wavelet == 53) {
+                b16((uint32_t)(3 + nb));
+                b8((uint32_t)G << 5);
+                b8((uint32_t)F.eps[3 * D] << 3);
+                for (int l = D; l >= 1; l--)
+                    for (int o = 0; o < 3; o++) b8((uint32_t)F.eps[3 * (l - 1) + o] << 3);
+            } else {
+                b16((uint32_t)(3 + 2 * nb));
+                b8(((uint32_t)G << 5) | 2u);
+                b16(((uint32_t)F.eps[3 * D] << 11) | F.mu[3 * D]);
+                for (int l = D; l >= 1; l--)
+                    for (int o = 0; o < 3; o++) {
+                        const int b = 3 * (l - 1) + o;
+                        b16(((uint32_t)F.eps[b] << 11) | F.mu[b]);
+                    }
+            }
+            sot = pos;
+            b16(0xFF90); b16(10); b16(0); b32(0); b8(0); b8(1);  // SOT (Psot filled below)
+            b16(0xFF93);                                      // SOD
+        }
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        // packets: resolution 0 holds the low-low band, resolution r the
+        // HL, LH, HH bands of level D - r + 1; their code-blocks follow one
+        // another in the frame's code-block order
+        int j0 = 0;
+        int *const tt_mem = F.hk;  // the hulls' scratch, free once rate control is done
+        for (int r = 0; r <= D; r++) {
+            const int nbands = r == 0 ? 1 : 3, l = r == 0 ? D : D - r + 1;
+            const int bw = W >> l, bh = H >> l;
+            const int nx = (bw + kCb - 1) / kCb, ny = (bh + kCb - 1) / kCb, per = nx * ny;
+            const int j1 = j0 + nbands * per;
+            int any = 0;
+            for (int j = j0 + lane; j < j1; j += 32) any |= F.info[(size_t)j * kCbInfo + 2] > 0;
+            any = __any_sync(0xffffffffu, any);
+            if (lane == 0) {
+                HdrBits bits;
+                bits.init(out, cap, pos);
+                if (!any) {
+                    bits.put(0);
+                } else {
+                    bits.put(1);
+                    for (int k = 0; k < nbands; k++) {
+                        const int band = r == 0 ? 3 * D : 3 * (l - 1) + k;
+                        const int Mb = G + (int)F.eps[band] - 1;
+                        const int jb = j0 + k * per;
+                        TagTree incl, zbp;
+                        incl.build(tt_mem, nx, ny);
+                        zbp.build(tt_mem + 2 * incl.nodes(), nx, ny);
+                        for (int q = 0; q < per; q++) {
+                            const int32_t *in = F.info + (size_t)(jb + q) * kCbInfo;
+                            incl.set(q % nx, q / nx, in[2] > 0 ? 0 : 1);
+                            zbp.set(q % nx, q / nx, Mb - in[0]);
+                        }
+                        for (int q = 0; q < per; q++) {
+                            const int j = jb + q;
+                            const int32_t *in = F.info + (size_t)j * kCbInfo;
+                            const int cx = q % nx, cy = q / nx;
+                            incl.encode(bits, cx, cy, 1);
+                            const int nk = in[2];
+                            if (nk == 0) continue;
+                            zbp.encode(bits, cx, cy, 0x3fffffff);
+                            passes_codeword(bits, nk);
+                            const int32_t *pl = F.plen + (size_t)j * kMaxPasses;
+                            int nbits = 1;
+                            for (int t = 0; t < nk; t++) nbits = max(nbits, bit_length((uint32_t)pl[t]));
+                            const int inc = max(0, nbits - 3);  // Lblock starts at 3
+                            for (int t = 0; t < inc; t++) bits.put(1);
+                            bits.put(0);
+                            for (int t = 0; t < nk; t++) bits.put_bits((uint32_t)pl[t], 3 + inc);
+                        }
+                    }
+                }
+                bits.flush();
+                pos = bits.pos;
+                over = over || bits.over;
+            }
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            // bodies: the included blocks' kept pass bytes, in header order
+            for (int j = j0; j < j1; j++) {
+                const int32_t *in = F.info + (size_t)j * kCbInfo;
+                const int nk = in[2];
+                if (nk == 0) continue;
+                const int nbytes = in[5] - 2 * nk;
+                const uint8_t *src = F.cbytes + (size_t)j * job->cbcap;
+                for (int i = lane; i < nbytes; i += 32)
+                    if (pos + i < cap) out[pos + i] = src[i];
+                pos += nbytes;
+            }
+            j0 = j1;
+        }
+        if (lane == 0) {
+            if (pos + 2 <= cap) {
+                out[pos] = 0xFF;
+                out[pos + 1] = 0xD9;  // EOC
+            }
+            pos += 2;
+            over = over || pos > cap;
+            if (!over) {
+                const uint32_t psot = (uint32_t)(pos - 2 - sot);
+                out[sot + 6] = (uint8_t)(psot >> 24);
+                out[sot + 7] = (uint8_t)(psot >> 16);
+                out[sot + 8] = (uint8_t)(psot >> 8);
+                out[sot + 9] = (uint8_t)psot;
+                *F.flen = pos;
+            } else {
+                *F.flen = -pos;  // the length it needs
+                if (job->err) atomicExch(job->err, kErrCbRange);
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -839,6 +1146,7 @@ void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
     k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
     k_pcrd<<<std::max(1, nframes), 1024, 0, s>>>(job_dev);
     k_cs_copy<<<std::max(1, (ncb + 7) / 8), 256, 0, s>>>(job_dev);
+    k_j2c<<<std::max(1, nframes), 32, 0, s>>>(job_dev);
 }
 
 void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, cudaStream_t s)
@@ -847,6 +1155,7 @@ void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, c
     k_t1<<<grid_t1, 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
     k_pcrd<<<kMaxBatch, 1024, 0, s>>>(job_dev);
     k_cs_copy<<<grid_copy, 256, 0, s>>>(job_dev);
+    k_j2c<<<kMaxBatch, 32, 0, s>>>(job_dev);
 }
 
 int occupancy_t1()

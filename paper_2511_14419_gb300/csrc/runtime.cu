@@ -162,6 +162,8 @@ struct Stream {
     char *cs_scratch = nullptr;
     int cs_ncb = 0;
     long long cs_cap = 0, cs_budget = 0;
+    uint8_t cs_eps[kMaxSubbands] = {};   // the bands' quantisation exponents and mantissas (JPEG2000 codestream)
+    uint16_t cs_mu[kMaxSubbands] = {};
 };
 
 struct BatchRec;
@@ -248,6 +250,29 @@ int cuda_fail(flowroi_ctx *c, cudaError_t e, const char *what)
     } while (0)
 
 // ------------------------------------------------------------ validation --
+// The bands' exponents and mantissas of a JPEG2000 codestream (table index
+// as the quantisation steps): 9/7 the steps' (eps, mu); 5/3 (no
+// quantisation) eps = bit depth + log2 of the band's nominal gain (0 LL,
+// 1 HL and LH, 2 HH), mu = 0.
+bool band_exponents(int levels, int wavelet, int bit_depth, float delta_base, uint8_t *eps, uint16_t *mu)
+{
+    std::memset(eps, 0, kMaxSubbands);
+    std::memset(mu, 0, kMaxSubbands * sizeof(uint16_t));
+    const int nb = 3 * levels + 1;
+    if (wavelet == FLOWROI_W97) {
+        int e[kMaxSubbands], m[kMaxSubbands];
+        if (quant_steps(levels, bit_depth, delta_base, nullptr, e, m, nullptr) != 0) return false;
+        for (int b = 0; b < nb; b++) {
+            if (e[b] < 0 || e[b] > 31) return false;
+            eps[b] = (uint8_t)e[b];
+            mu[b] = (uint16_t)m[b];
+        }
+    } else {
+        for (int b = 0; b < nb; b++) eps[b] = (uint8_t)(bit_depth + (b == 3 * levels ? 0 : (b % 3 < 2 ? 1 : 2)));
+    }
+    return true;
+}
+
 bool read_text_file(const char *path, std::string &out)
 {
     FILE *f = std::fopen(path, "rb");
@@ -299,6 +324,8 @@ int validate_config(const flowroi_config *c)
     if (!(c->den_sigma_s > 0.f) || !(c->den_sigma_r > 0.f)) return fail(FLOWROI_EINVAL, "config.den_sigma_s/den_sigma_r must be > 0");
     if (!(c->codestream_bpp >= 0.f && c->codestream_bpp <= 64.f))
         return fail(FLOWROI_EINVAL, "config.codestream_bpp must be in [0, 64]");
+    if (c->codestream_format != FLOWROI_CS_CONTAINER && c->codestream_format != FLOWROI_CS_J2C)
+        return fail(FLOWROI_EINVAL, "config.codestream_format must be FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C");
     if (c->tile_table) {
         std::string text, err;
         TileTable t;
@@ -423,7 +450,10 @@ size_t plan_stream(flowroi_ctx *c, Stream *s, char *base)
     if (cs_on) {
         s->cs_ncb = ebcot_codeblocks(s->W, s->H, c->cfg.dwt_levels);
         s->cs_budget = (long long)std::floor((double)c->cfg.codestream_bpp * (double)npx / 8.0);
-        s->cs_cap = kCsHeader + (long long)s->cs_ncb * (kCsEntry + 2 * kMaxPasses) + s->cs_budget;
+        s->cs_cap = c->cfg.codestream_format == FLOWROI_CS_J2C
+                        ? kJ2cHeader + (long long)s->cs_ncb * kJ2cPerBlock + s->cs_budget
+                        : kCsHeader + (long long)s->cs_ncb * (kCsEntry + 2 * kMaxPasses) + s->cs_budget;
+        band_exponents(c->cfg.dwt_levels, c->cfg.wavelet, s->bit_depth, c->cfg.delta_base, s->cs_eps, s->cs_mu);
         s->cs_scratch = take((size_t)s->cs_ncb * kCbScratch);
     }
     for (int r = 0; r < R; r++) {
@@ -563,6 +593,9 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
             b += n * kCbInfo * sizeof(int32_t);
             C.hk = reinterpret_cast<int32_t *>(b);
             C.flen = d->cs_len;
+            C.format = c->cfg.codestream_format;
+            std::memcpy(C.eps, s->cs_eps, sizeof C.eps);
+            std::memcpy(C.mu, s->cs_mu, sizeof C.mu);
         }
         const int k = c->cfg.adjacent;
         if (k > 0) {
@@ -746,7 +779,7 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
             cudaMemsetAsync(const_cast<int *>(&dd->cs_next), 0, sizeof(int), st);
             launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_csc, st);
         });
-        cnt += 3;
+        cnt += 4;
     }
     *nlaunch = cnt;
     return FLOWROI_OK;
@@ -1139,6 +1172,7 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->register_frames = 0;
     cfg->reg_level = 2;
     cfg->codestream_bpp = 0.f;
+    cfg->codestream_format = FLOWROI_CS_CONTAINER;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -1694,7 +1728,8 @@ uint64_t flowroi_codestream_bound(int width, int height, int levels)
         width % (1 << levels) || height % (1 << levels))
         return 0;
     const uint64_t ncb = (uint64_t)ebcot_codeblocks(width, height, levels);
-    return (uint64_t)kCsHeader + ncb * ((uint64_t)kCsEntry + 2 * kMaxPasses + kCbBytes);
+    // the larger of the two formats' bounds (the codestream's)
+    return (uint64_t)kJ2cHeader + ncb * ((uint64_t)kJ2cPerBlock + kCbBytes);
 }
 
 int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int on_device)
@@ -1724,6 +1759,11 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
         F.wavelet = J.wavelet;
         F.shift = J.shift;
         F.bit_depth = J.bit_depth;
+        if (J.format != FLOWROI_CS_CONTAINER && J.format != FLOWROI_CS_J2C)
+            return fail(FLOWROI_EINVAL, "job %d: format must be FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C", i);
+        F.format = J.format;
+        if (J.format == FLOWROI_CS_J2C && !band_exponents(J.levels, J.wavelet, J.bit_depth, c->cfg.delta_base, F.eps, F.mu))
+            return fail(FLOWROI_EINVAL, "job %d: quantisation steps out of range for bit_depth %d", i, J.bit_depth);
         F.cb0 = ncb;
         F.ncb = ebcot_codeblocks(J.width, J.height, J.levels);
         ncb += F.ncb;

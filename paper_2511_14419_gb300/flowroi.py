@@ -20,6 +20,7 @@ W53, W97 = 53, 97
 FP32, FP16 = 32, 16
 KEEP_INTERMEDIATES, PLAIN, MANUAL = 0x1, 0x2, 0x4
 TEST_EXPIRE_TMA, TEST_EXPIRE_LOOP = 0x100, 0x200
+CS_CONTAINER, CS_J2C = 0, 1
 I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD, I_DENOISED, I_DRIFT = 1, 2, 3, 4, 5, 6, 7
 
 EXPORTS = [
@@ -51,7 +52,7 @@ class flowroi_config(ctypes.Structure):
         ("denoise", ctypes.c_int32), ("den_radius", ctypes.c_int32), ("den_sigma_s", ctypes.c_float),
         ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32), ("adjacent", ctypes.c_int32),
         ("register_frames", ctypes.c_int32), ("reg_level", ctypes.c_int32), ("codestream_bpp", ctypes.c_float),
-        ("tile_table", ctypes.c_char_p),
+        ("codestream_format", ctypes.c_int32), ("tile_table", ctypes.c_char_p),
     ]
 
 
@@ -67,7 +68,8 @@ class flowroi_cs_job(ctypes.Structure):
     _fields_ = [("coeffs", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("wavelet", ctypes.c_int32), ("shift", ctypes.c_int32),
                 ("bit_depth", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("out", ctypes.c_void_p),
-                ("out_cap", ctypes.c_uint64), ("out_len", ctypes.c_uint64)]
+                ("out_cap", ctypes.c_uint64), ("out_len", ctypes.c_uint64), ("format", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class flowroi_kernel_time(ctypes.Structure):
@@ -353,12 +355,13 @@ def flowroi_codestream_bound(width: int, height: int, levels: int) -> int:
 
 
 def flowroi_encode_codestreams(ctx, jobs) -> list:
-    """Codes coefficient planes into frame containers (see the C header).
-    jobs: dicts with coeffs (int32 (H, W) numpy array or CUDA tensor),
-    levels, wavelet, shift, bit_depth, budget (pass-data bytes, 0 = every
-    pass) and out (uint8 numpy array or CUDA tensor: the container's
-    destination, its size the capacity).  All on the host or all on the
-    device.  Returns the containers' lengths."""
+    """Codes coefficient planes into frame containers or JPEG2000
+    codestreams (see the C header).  jobs: dicts with coeffs (int32 (H, W)
+    numpy array or CUDA tensor), levels, wavelet, shift, bit_depth, budget
+    (pass-data bytes, 0 = every pass), format (CS_CONTAINER or CS_J2C) and
+    out (uint8 numpy array or CUDA tensor: the destination, its size the
+    capacity).  All on the host or all on the device.  Returns the
+    lengths."""
     arr = (flowroi_cs_job * len(jobs))()
     dev = None
     for i, j in enumerate(jobs):
@@ -371,7 +374,7 @@ def flowroi_encode_codestreams(ctx, jobs) -> list:
         h, w = int(j["coeffs"].shape[0]), int(j["coeffs"].shape[1])
         nbytes = int(j["out"].numel() * j["out"].element_size()) if hasattr(j["out"], "numel") else int(j["out"].nbytes)
         arr[i] = flowroi_cs_job(cp, w, h, j["levels"], j["wavelet"], j.get("shift", 0), j.get("bit_depth", 12),
-                                int(j.get("budget", 0)), op, nbytes, 0)
+                                int(j.get("budget", 0)), op, nbytes, 0, int(j.get("format", CS_CONTAINER)), 0)
     _check(lib().flowroi_encode_codestreams(ctx, len(jobs), arr, int(dev)), ctx)
     return [int(arr[i].out_len) for i in range(len(jobs))]
 

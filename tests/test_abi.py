@@ -45,7 +45,7 @@ def test_struct_sizes_match_binding(F):
     assert cfg.struct_size == ctypes.sizeof(F.flowroi_config)
     assert (cfg.roi_q, cfg.scale_shift, cfg.win_r, cfg.iters) == (np.float32(0.2), 5, 7, 3)
     assert F.flowroi_abi_version() == 4
-    assert ctypes.sizeof(F.flowroi_cs_job) == 64
+    assert ctypes.sizeof(F.flowroi_cs_job) == 72
 
 
 def test_quant_steps_match_oracle_table(F, orc):
@@ -100,12 +100,17 @@ def test_log_env_reports_refusals_on_stderr():
 
 
 def test_codestream_bound_counts_the_code_blocks(F, orc):
-    """The container bound is header + per code-block (entry + pass lengths
-    + the coder's per-block byte limit); the library's code-block count
-    agrees with the oracle's partition; malformed geometries give 0."""
+    """The bound covers both formats: the JPEG2000 codestream's markers
+    (256 bytes) + per code-block its packet-header bits (at most 192 bytes)
+    and the coder's per-block byte limit, which exceeds the container's
+    header + per code-block entry, pass lengths and bytes; the library's
+    code-block count agrees with the oracle's partition; malformed
+    geometries give 0."""
     for w, h, levels in [(2048, 2048, 5), (256, 256, 3), (264, 200, 3), (16, 16, 2), (2048, 1536, 5)]:
         n = len(orc.codeblocks(w, h, levels))
-        assert F.flowroi_codestream_bound(w, h, levels) == 32 + n * (16 + 2 * 70 + 32768)
+        b = F.flowroi_codestream_bound(w, h, levels)
+        assert b == 256 + n * (192 + 32768)
+        assert b >= 32 + n * (16 + 2 * 70 + 32768)
     for w, h, levels in [(100, 64, 3), (64, 64, 0), (64, 64, 9), (0, 64, 1), (65536, 64, 1)]:
         assert F.flowroi_codestream_bound(w, h, levels) == 0
 

@@ -15,6 +15,7 @@ import torch
 from oracle import oracle as o
 from synth import sequence_u16
 from tests._gpu import F
+from tests.test_oracle_codestream import _container_blocks, parse
 
 pytestmark = pytest.mark.gpu
 
@@ -36,17 +37,17 @@ def _planes(seed, h, w, levels, wavelet, shift, bd=12, roi_frac=0.3):
     return o.roi_shift(q, cm, shift)
 
 
-def _gpu(ctx, planes, levels, wavelet, shift, budgets, on_device=False, bd=12):
+def _gpu(ctx, planes, levels, wavelet, shift, budgets, on_device=False, bd=12, fmt=0):
     jobs = []
     for q, b in zip(planes, budgets):
         h, w = q.shape
         cap = F.flowroi_codestream_bound(w, h, levels)
         if on_device:
             jobs.append(dict(coeffs=torch.from_numpy(q).cuda(), out=torch.zeros(cap, dtype=torch.uint8, device="cuda"),
-                             levels=levels, wavelet=wavelet, shift=shift, bit_depth=bd, budget=b))
+                             levels=levels, wavelet=wavelet, shift=shift, bit_depth=bd, budget=b, format=fmt))
         else:
             jobs.append(dict(coeffs=np.ascontiguousarray(q), out=np.zeros(cap, np.uint8), levels=levels,
-                             wavelet=wavelet, shift=shift, bit_depth=bd, budget=b))
+                             wavelet=wavelet, shift=shift, bit_depth=bd, budget=b, format=fmt))
     lens = F.flowroi_encode_codestreams(ctx, jobs)
     out = []
     for j, n in zip(jobs, lens):
@@ -202,3 +203,56 @@ def test_stream_path_out_of_range_coefficients_are_erange():
         assert ei.value.code == F.ERANGE
         # the first frame has no RoI, so no shift: its container is there
         assert F.flowroi_get_codestream(c.h, 0, 0, np.zeros(F.flowroi_codestream_bound(w, h, 2), np.uint8), 10000) > 0
+
+
+# ------------------------------------------------ JPEG2000 codestreams --
+
+@pytest.mark.parametrize("h,w,levels,wavelet,bpp", [(256, 256, 3, 53, 0.0), (200, 264, 3, 97, 1.0),
+                                                     (16, 16, 2, 53, 0.0), (512, 512, 5, 97, 0.25),
+                                                     (192, 320, 4, 97, 3.0)])
+def test_j2c_codestream_matches_oracle(ctx, h, w, levels, wavelet, bpp):
+    """format CS_J2C: the GPU's JPEG2000 Part 1 codestream equals the
+    oracle's byte for byte, and the independent parser reads back the same
+    passes as the container of the same frame."""
+    q = _planes(h * 3 + w + levels, h, w, levels, wavelet, 5)
+    budget = int(bpp * h * w / 8)
+    want, _ = o.encode_frame(q, levels, wavelet, 5, 12, budget, fmt="j2c")
+    got = _gpu(ctx, [q], levels, wavelet, 5, [budget], fmt=F.CS_J2C)[0]
+    assert got == want
+    cont = _gpu(ctx, [q], levels, wavelet, 5, [budget])[0]
+    assert parse(got)["blocks"] == _container_blocks(cont)
+
+
+def test_j2c_full_size_2048_97_at_one_bit_per_pixel(ctx):
+    h = w = 2048
+    q = _planes(3000, h, w, 5, 97, 5)
+    budget = h * w // 8
+    want, _ = o.encode_frame(q, 5, 97, 5, 12, budget, fmt="j2c")
+    got = _gpu(ctx, [q], 5, 97, 5, [budget], on_device=True, fmt=F.CS_J2C)[0]
+    assert got == want
+
+
+def test_j2c_in_the_stream_path():
+    """config.codestream_format = CS_J2C: each frame's codestream from the
+    stream path equals the coder's codestream of that frame's coefficients,
+    and it parses."""
+    h, w, S, n = 256, 320, 2, 3
+    with F.Context(pyr_levels=3, dwt_levels=3, wavelet=97, codestream_bpp=1.0, codestream_format=F.CS_J2C,
+                   flags=F.MANUAL) as c:
+        seqs = [np.asarray(sequence_u16(710 + s, n, h, w, 8)).astype(np.uint16) for s in range(S)]
+        for t in range(n):
+            for s in range(S):
+                F.flowroi_submit_frame(c.h, s, seqs[s][t], t, 12)
+            F.flowroi_step(c.h)
+        F.flowroi_flush(c.h, 60000)
+        cap = F.flowroi_codestream_bound(w, h, 3)
+        for s in range(S):
+            for t in range(n):
+                coeffs = np.empty((h, w), np.int32)
+                F.flowroi_get_coeffs(c.h, s, t, coeffs, 10000)
+                out = np.zeros(cap, np.uint8)
+                k = F.flowroi_get_codestream(c.h, s, t, out, 10000)
+                want, _ = o.encode_frame(coeffs, 3, 97, 5, 12, h * w // 8, fmt="j2c")
+                assert bytes(out[:k]) == want, (s, t)
+                info = parse(want)
+                assert (info["w"], info["h"], info["levels"]) == (w, h, 3)
