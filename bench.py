@@ -70,6 +70,9 @@ WORKLOADS = {
     # four streams of it (small case for profiler captures of the coder)
     "ebcot_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
+    # four streams with fp16 storage (small case for profiler captures)
+    "small_fp16_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                              dwt_levels=5, wavelet=97, precision=16, seed_base=3000),
     # four streams of the batched workload's frames (small case for profiler captures)
     "small_4x2048": dict(streams=4, frames=4, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                          dwt_levels=5, wavelet=97, precision=32, seed_base=3000),
@@ -112,11 +115,15 @@ def other_bytes(name, storage, bpp):
 
 
 # DRAM bytes (read + write) per level-0 pixel of one launch, measured by ncu
-# on 4 frames (profiles/*.md; traffic proportional to pixels), each with the
-# source file the kernel was built from and its SHA-256 prefix at the time of
-# the capture: a figure whose source has changed since is reported as null.
-KERNEL_TRAFFIC_PER_PX = {("update", 32): (66.5, "k_flow.cu", "1a0e59d8926c09fa"),
-                         ("window", 32): (27.0, "k_flow.cu", "1a0e59d8926c09fa")}
+# on 4 frames (profiles/launch_traffic_small_4x2048.md; traffic proportional
+# to pixels; the update figure averages its three level-0 launches), each
+# with the source file the kernel was built from and its SHA-256 prefix at
+# the time of the capture: a figure whose source has changed since is
+# reported as null.
+KERNEL_TRAFFIC_PER_PX = {("update", 32): (64.26, "k_flow.cu", "05226eafcefe7118"),
+                         ("window", 32): (27.25, "k_flow.cu", "05226eafcefe7118"),
+                         ("expand", 32): (19.16, "k_expand.cu", "83e2d4444934406d"),
+                         ("dwt", 32): (4.13, "k_dwt.cu", "d491d8afc89994db")}
 
 
 def traffic_per_px(name, storage):
