@@ -540,7 +540,9 @@ struct Tuner {
         for (int l = 1; l <= cfg->dwt_levels; l++) {
             const int bh = h >> l;
             std::vector<int> cands;
-            for (int v : {8, 12, 16, 24, 32, 48, 64})
+            // fine steps: the unit count against the resident warps decides
+            // how full the last wave of units is
+            for (int v : {8, 10, 12, 14, 16, 18, 20, 22, 24, 28, 32, 40, 48, 64})
                 if (v <= std::max(8, bh)) cands.push_back(v);
             if (!search(r, cands, {{"dwt", l}}, [&](int v) { best.dwt_seg[sh][c][l - 1] = v; })) return false;
         }
