@@ -171,6 +171,14 @@ __device__ __forceinline__ void cp_async(void *dst, const void *src)
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(src), "n"(B) : "memory");
 }
+template <int B>
+__device__ __forceinline__ void cp_async_s(uint32_t dst, const void *src)
+{
+    if constexpr (B == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(B) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -416,9 +424,26 @@ __device__ __forceinline__ void dwt_unit(const FrameDesc &F, const MethodConsts 
     const int n0 = r0 - A, n1 = r1 - 1 + A;  // pair steps n0..n1
     // Queues the copies of pair n (rows 2n, 2n+1) into its ring slot.
     int islot = 0, cslot = 0;  // ring slots of the next pair to issue and to consume
+    // common case: this lane's columns inside the image, aligned sources:
+    // column pointers and shared-space addresses kept, four copies a pair
+    const bool fast = kind == kColPacked && !sync_load && mask_async;
+    const unsigned char *const scol = src + (size_t)cx * E;
+    const uint8_t *const mcol = msrc + cx;
+    const uint32_t rraw_s = smem_u32(rraw), rmask_s = smem_u32(rmask);
     auto issue = [&](int n) {
         const int slot = islot;
         islot = islot == kDwtRing - 1 ? 0 : islot + 1;
+        if (fast && n >= 0 && 2 * n + 1 < ih) {
+            const unsigned char *r0 = scol + (size_t)(2 * n) * spitch;
+            const uint8_t *m0 = mcol + (size_t)(2 * n) * mpitch;
+            const uint32_t d = rraw_s + (uint32_t)(slot * 2 * 2 * 32 * CH), dm = rmask_s + (uint32_t)(slot * 2 * 32 * 4);
+            cp_async_s<CH>(d, r0);
+            cp_async_s<CH>(d + 2 * 32 * CH, r0 + spitch);
+            cp_async_s<4>(dm, m0);
+            cp_async_s<4>(dm + 32 * 4, m0 + mpitch);
+            cp_async_commit();
+            return;
+        }
 #pragma unroll
         for (int h = 0; h < 2; h++) {
             const int y = 2 * n + h;
