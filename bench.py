@@ -123,7 +123,7 @@ def other_bytes(name, storage, bpp):
 KERNEL_TRAFFIC_PER_PX = {("update", 32): (64.26, "k_flow.cu", "05226eafcefe7118"),
                          ("window", 32): (27.25, "k_flow.cu", "05226eafcefe7118"),
                          ("expand", 32): (19.16, "k_expand.cu", "83e2d4444934406d"),
-                         ("dwt", 32): (4.13, "k_dwt.cu", "d491d8afc89994db")}
+                         ("dwt", 32): (4.03, "k_dwt.cu", "48cdef260a22e4fa")}
 
 
 def traffic_per_px(name, storage):
