@@ -90,8 +90,24 @@ constexpr int kCsHeader = 32, kCsEntry = 16;   // container header and per-code-
 constexpr int kJ2cHeader = 256, kJ2cPerBlock = 192;
 constexpr unsigned kErrCbRange = 3u;           // error word: a code-block or container exceeded its buffer or range
 constexpr int kCbBytes = 32768;                // pass bytes a code-block may produce
-// device bytes of a code-block's scratch (pass bytes, lengths, distortions, info, hull)
-constexpr size_t kCbScratch = (size_t)kCbBytes + kMaxPasses * (4 + 8) + kCbInfo * 4 + (kMaxPasses + 1) * (4 + 8);
+// Coding decisions a code-block's passes may produce, one byte each
+// (context << 1 | decision): per bit-plane and stripe column at most six
+// that are not signs (four samples, or run-length mode's run symbol, two
+// position symbols and the three samples below), and one sign per sample
+// over all planes.
+constexpr int kSymCap = kMaxPlanes * 6 * (kCb * kCb / 4) + kCb * kCb;
+// Bytes of a code-block's pass-byte region: each pass is first coded into
+// a slot of floor(S / 7) + 3 bytes (S its renormalisation shifts; a pass of
+// L bytes has S <= 8 L + 12), and the slots of a block whose passes fit
+// kCbBytes sum to less than 8/7 kCbBytes + 5 per pass; then moved down to
+// be contiguous.
+constexpr int kCbRegion = 40960;
+constexpr int kMqWords = 20;  // a pass's starting MQ context states (19 contexts, padded)
+// device bytes of a code-block's scratch (pass bytes, decision stream and
+// per-pass counts, lengths, distortions, context states and slot table,
+// info, hull)
+constexpr size_t kCbScratch = (size_t)kCbRegion + (size_t)kSymCap + kMaxPasses * (4 + 4 + 8 + 4 * kMqWords + 16) +
+                              kCbInfo * 4 + (kMaxPasses + 1) * (4 + 8);
 
 struct CsFrame {
     const int32_t *coef;  // Mallat plane, row pitch = w
@@ -101,8 +117,12 @@ struct CsFrame {
     int w, h, levels, wavelet, shift, bit_depth;
     int cb0, ncb;         // the frame's code-blocks in the job
     // per code-block scratch of the frame, [ncb][...]
-    uint8_t *cbytes;      // [kCbBytes] pass bytes
+    uint8_t *cbytes;      // [kCbRegion] pass bytes (the first kCbBytes hold them back to back)
     int32_t *plen;        // [kMaxPasses]
+    uint8_t *sym;         // [kSymCap] the passes' coding decisions, in coding order
+    int32_t *nsym;        // [kMaxPasses] decisions per pass
+    uint32_t *mqs;        // [kMaxPasses][kMqWords] MQ context states at each pass's start
+    int4 *ptab;           // [kMaxPasses] per pass: first decision, slot offset, slot bytes
     double *dist;         // [kMaxPasses]
     int32_t *info;        // [kCbInfo]
     int32_t *hk;          // [kMaxPasses + 1] hull scratch
@@ -118,7 +138,7 @@ struct CsJob {
     const CsFrame *frames;  // device array [nframes]
     int cbcap;              // kCbBytes
     unsigned *err;          // error word, or null
-    int *next;              // next code-block to take (zeroed before the coder runs)
+    int *next;              // work counters, zeroed before the coder runs: [0] modelling, [1] MQ states, [2] MQ passes
 };
 
 // One frame of a batch.  Level geometry: lw/lh = level size, lp = pitch in
@@ -200,7 +220,7 @@ struct BatchDesc {
     FrameDesc f[kMaxBatch];
     CsJob cs;                       // the batch's coder job over csf (frames with do_cs)
     CsFrame csf[kMaxBatch];
-    int cs_next;                    // the coder's work counter
+    int cs_next[3];                 // the coder's work counters
 };
 
 #ifdef __CUDACC__

@@ -20,26 +20,29 @@
 //   - a frame container: 32-byte header, a 16-byte entry per code-block,
 //     then per code-block the kept passes' 16-bit lengths and bytes.
 //
-// One warp per code-block.  The block's coder state (a 16-bit word per
-// coefficient with a one-sample border: neighbour significance counts,
-// significance, refinement, visited, sign, the plane's coding event) and
-// the current bit-plane as 64-bit row masks live in shared memory.  The
-// warp builds each bit-plane from the coefficient plane (coalesced) and,
-// in the same sweep, adds up the distortion decreases of the previous
-// plane's passes from the events the passes recorded.  The passes go
-// stripe by stripe:
-//   - magnitude refinement: its members, contexts and decisions depend only
-//     on state fixed before the pass, so the whole warp forms the stripe's
-//     (context, bit) symbols in scan order into a shared-memory queue and
-//     lane 0 only runs the MQ coder over it;
-//   - significance propagation and cleanup: the warp forms the stripe's
-//     candidate columns by ballot; lane 0 walks them in order and codes
-//     their samples (sequential by definition: a sample that becomes
-//     significant changes its neighbours' contexts; in the significance
-//     pass it makes the next column a candidate).
-// The MQ coder keeps each context's probability-table row and MPS in one
-// shared-memory word and renormalises by count-leading-zeros.
-#include <mutex>
+// Tier-1 coding runs as four kernels, so that no long sequential chain
+// waits on another:
+//   - k_t1, context modelling, one warp per code-block.  Which samples each
+//     pass codes, in which context, and with which decision depends only on
+//     the coefficients and the passes before, not on the arithmetic coder,
+//     so the warp forms all of a block's (context, decision) pairs in
+//     coding order and writes them out, pass by pass.  Lane l holds the
+//     block's columns 2l and 2l + 1 as 64-bit column words of every state
+//     (significance, sign, refined, visited, the plane's bit, the plane's
+//     new significances); a stripe's contexts come from six-row windows of
+//     the lane's and its neighbours' columns (shuffles).  The significance
+//     pass's chain (a sample turning significant makes the next ones in the
+//     scan candidates) is solved per stripe by rounds across the lanes; the
+//     cleanup pass's new significances are known at once.  The same warp
+//     builds each bit-plane and adds up the distortion decreases.
+//   - k_t1_mq, one thread per code-block: the MQ coder's interval register
+//     and context states over the block's decisions (the one chain that
+//     runs through all passes), recording each pass's starting context
+//     states and a byte bound for its codeword;
+//   - k_t1_mqc, one thread per pass: each pass, a terminated codeword of
+//     its own, coded from its starting context states into its slot;
+//   - k_t1_pack, one warp per code-block: the codewords moved to be back to
+//     back.
 
 #include "common.cuh"
 #include "kernels.h"
@@ -105,32 +108,22 @@ __host__ __device__ constexpr int zc_rule(int ori, int h, int v, int d)
     return hv >= 2 ? 2 : (hv == 1 ? 1 : 0);
 }
 
+// Sign-coding context and flip (Table D.3) by (H + 1) + 3 (V + 1), H and V
+// the clipped horizontal and vertical sign contributions; four bits an
+// entry: the context minus 9 (bits 0-2) and the flip (bit 3).
+constexpr uint64_t sc_packed()
+{
+    constexpr int ctx[9] = {13, 10, 11, 12, 9, 12, 11, 10, 13};
+    constexpr int flip[9] = {1, 1, 0, 1, 0, 0, 1, 0, 0};
+    uint64_t v = 0;
+    for (int i = 0; i < 9; i++) v |= (uint64_t)((ctx[i] - 9) | (flip[i] << 3)) << (4 * i);
+    return v;
+}
+constexpr uint64_t kScPacked = sc_packed();
 
-// Sign-coding context (Table D.3) and flip bit by (H + 1) + 3 (V + 1),
-// H and V the clipped horizontal and vertical sign contributions: bits 0-4
-// the context, bit 7 the flip.
-__constant__ uint8_t kSc[9] = {13 | 0x80, 10 | 0x80, 11, 12 | 0x80, 9, 12, 11 | 0x80, 10, 13};
-
-// State word of a coefficient.
-constexpr uint16_t kNbMask = 0x7F;  // h (bits 0-1), v (2-3), d (4-6) significant-neighbour counts
-constexpr uint16_t kSig = 1u << 7, kRef = 1u << 8, kVis = 1u << 9, kNeg = 1u << 10;
-constexpr int kEvShift = 11;        // bits 11-12: this plane's event (1 SPP, 2 MRP, 3 cleanup)
-constexpr uint16_t kEvMask = 3u << kEvShift;
-
-// Column-major state words: (x, y) at (x + 1) * kColS + y + kRowOff, so a
-// stripe's four rows of a column are one aligned 64-bit word; x and y run
-// over the block plus a one-sample border.
-constexpr int kColS = 72, kRowOff = 4;
-constexpr int kT1Warps = 7;  // code-blocks per CTA (three CTAs per SM by shared memory)
-
-struct T1Warp {
-    uint16_t st[(kCb + 2) * kColS];
-    uint32_t cxw[kNctx + 1];  // MQ contexts: the state's table row (kMq word) | MPS << 31
-    uint64_t bm[kCb];         // bit p of the magnitudes, one row per word (bit x)
-    uint8_t mq[4 * kCb];      // a stripe's refinement symbols: (context - 14) << 1 | bit
-};
-
-__device__ __forceinline__ int contrib(uint16_t w) { return (w & kSig) ? ((w & kNeg) ? -1 : 1) : 0; }
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kT1Warps = 8;     // code-blocks (one a warp) per CTA of the modelling kernel
+constexpr int kMqThreads = 64;  // code-blocks (one a thread) per CTA of the MQ kernel
 
 // Doubled-unit reconstruction once planes >= p are known (0 while m >> p == 0).
 __device__ __forceinline__ long long recon2(uint32_t m, int p)
@@ -146,8 +139,8 @@ __device__ __forceinline__ long long derr(uint32_t m, int pb, int pa)
     return eb * eb - ea * ea;
 }
 
-// MQ encoder of lane 0 (Annex C, software conventions; the byte at BP is
-// held in b until BP moves on).
+// MQ encoder of one thread (Annex C, software conventions; the byte at BP
+// is held in b until BP moves on).
 struct Mqe {
     uint32_t a, c, b;
     int ct, bp;
@@ -199,7 +192,7 @@ struct Mqe {
             } else {
                 emit();
                 bp++;
-                b = c >> 19;
+                b = (c >> 19) & 0xFFu;  // the carry (bit 27) went into the byte before
                 c &= 0x7FFFF;
                 ct = 8;
             }
@@ -220,22 +213,24 @@ struct Mqe {
             if (ct == 0) byteout();
         }
     }
-    __device__ __forceinline__ void encode(uint32_t *cxw, int cx, int d)
+    // One decision d in the context whose word (the state's table row |
+    // MPS << 31) is cw; tab: the table rows by state index.
+    __device__ __forceinline__ void encode(uint32_t &cw, const uint32_t *tab, uint32_t d)
     {
-        const uint32_t w = cxw[cx], qe = w & 0xFFFFu, mps = w >> 31;
+        const uint32_t w = cw, qe = w & 0xFFFFu, mps = w >> 31;
         a -= qe;
-        if ((uint32_t)d == mps) {
+        if (d == mps) {
             if (a & 0x8000) {
                 c += qe;
                 return;
             }
             if (a < qe) a = qe;
             else c += qe;
-            cxw[cx] = kMq.w[(w >> 16) & 63u] | (mps << 31);
+            cw = tab[(w >> 16) & 63u] | (mps << 31);
         } else {
             if (a < qe) c += qe;
             else a = qe;
-            cxw[cx] = kMq.w[(w >> 22) & 63u] | ((mps ^ ((w >> 28) & 1u)) << 31);
+            cw = tab[(w >> 22) & 63u] | ((mps ^ ((w >> 28) & 1u)) << 31);
         }
         renorm();
     }
@@ -257,162 +252,255 @@ struct Mqe {
     }
 };
 
-__device__ __forceinline__ int sti(int x, int y) { return (x + 1) * kColS + y + kRowOff; }
+// ---------------------------------------------------------------------------
+// Context modelling by column words.  Lane l of a block's warp holds the
+// block's columns x = 2l and 2l + 1 as 64-bit words (bit y = row y) of each
+// state: significance, sign, refined, visited in this plane's significance
+// pass, the current plane's magnitude bit, and this plane's new
+// significances by pass (for the distortion).  A stripe (rows y0 .. y0 + 3)
+// is modelled from windows of six rows (y0 - 1 .. y0 + 4) by four columns
+// (2l - 1 .. 2l + 2): byte j of a window holds column 2l - 1 + j, bit R of
+// that byte row y0 - 1 + R.  The lane's own columns are bytes 1 and 2.
 
-// A coefficient became significant: its neighbours' counts (horizontal
-// neighbours are a column apart, vertical ones adjacent words).
-__device__ __forceinline__ void set_sig(uint16_t *st, int i)
+// Rows y0 - 1 .. y0 + 4 of a column word (rows outside the block are 0).
+__device__ __forceinline__ uint32_t rows6(uint64_t c, int y0)
 {
-    st[i - kColS] += 1;
-    st[i + kColS] += 1;
-    st[i - 1] += 4;
-    st[i + 1] += 4;
-    st[i - kColS - 1] += 16;
-    st[i - kColS + 1] += 16;
-    st[i + kColS - 1] += 16;
-    st[i + kColS + 1] += 16;
+    return (uint32_t)(y0 == 0 ? (c << 1) : (c >> (y0 - 1))) & 0x3Fu;
+}
+// Rows y0 .. y0 + 3.
+__device__ __forceinline__ uint32_t rows4(uint64_t c, int y0) { return (uint32_t)(c >> y0) & 0xFu; }
+
+// A stripe window from the lane's two column values (c0: column 2l) and
+// its neighbours' (columns 2l - 1 and 2l + 2 do not exist at the edges).
+__device__ __forceinline__ uint32_t window(uint32_t c0, uint32_t c1, int lane)
+{
+    const uint32_t own = c0 | (c1 << 8);
+    const uint32_t l = __shfl_up_sync(kFull, own, 1) >> 8;
+    const uint32_t r = __shfl_down_sync(kFull, own, 1) & 0xFFu;
+    return (lane == 0 ? 0u : l) | (own << 8) | (lane == 31 ? 0u : r << 24);
 }
 
-__device__ __forceinline__ void code_sign(T1Warp &s, Mqe &e, int i, uint16_t w)
+// Stripe rows (bits 0-3) of own column j (1 or 2) with at least one of
+// the eight neighbours set in window B.
+__device__ __forceinline__ uint32_t any_nb(uint32_t B, int j)
 {
-    const uint16_t *st = s.st;
-    int hc = contrib(st[i - kColS]) + contrib(st[i + kColS]);
-    int vc = contrib(st[i - 1]) + contrib(st[i + 1]);
-    hc = hc < -1 ? -1 : (hc > 1 ? 1 : hc);
-    vc = vc < -1 ? -1 : (vc > 1 ? 1 : vc);
-    const uint8_t sc = kSc[(hc + 1) + 3 * (vc + 1)];
-    e.encode(s.cxw, sc & 0x1F, ((w & kNeg) ? 1 : 0) ^ (sc >> 7));
+    const uint32_t D = B | (B << 1) | (B >> 1);  // each column dilated along y
+    const uint32_t c = B >> (8 * j);
+    return (((D >> (8 * (j - 1))) | (D >> (8 * (j + 1))) | (c << 1) | (c >> 1)) >> 1) & 0xFu;
 }
 
-// One coding pass of the current plane by the warp: type 0 significance
-// propagation, 1 magnitude refinement, 2 cleanup (see the file header);
-// e is lane 0's coder.  zc: the zero-coding contexts of the block's
-// orientation by the state word's neighbour bits (0-6).  A stripe
-// column's four state words are one 64-bit word.
-__device__ __forceinline__ void t1_pass(T1Warp &s, Mqe &e, int type, int w, int h, const uint8_t *zc, int lane)
+// Zero-coding index (h | v << 2 | d << 4: significant horizontal, vertical
+// and diagonal neighbours) of the sample at window row R of own column j,
+// when the samples before it in scan order (the column to the left, the
+// rows above) are seen in A and the ones after it in B.
+__device__ __forceinline__ uint32_t nb_index(uint32_t A, uint32_t B, int j, int R)
 {
-    uint16_t *st = s.st;
-    constexpr uint64_t kRep = 0x0001000100010001ull;
-    for (int y0 = 0; y0 < h; y0 += 4) {
-        const int nr = min(4, h - y0);
-        // 16-bit lanes of the stripe's rows that exist
-        const uint64_t rows = nr >= 4 ? ~0ull : ((1ull << (16 * nr)) - 1);
-        if (type == 1) {
-            // refinement: every lane forms its columns' symbols (columns
-            // lane and lane + 32, rows in order), placed in scan order by a
-            // prefix sum over the lanes of each half
-            int total = 0;
+    const int l = 8 * (j - 1) + R, m = 8 * j + R, r = 8 * (j + 1) + R;
+    const uint32_t h = ((A >> l) & 1u) + ((B >> r) & 1u);
+    const uint32_t v = ((A >> (m - 1)) & 1u) + ((B >> (m + 1)) & 1u);
+    const uint32_t d = ((A >> (l - 1)) & 1u) + ((A >> (l + 1)) & 1u) + ((B >> (r - 1)) & 1u) + ((B >> (r + 1)) & 1u);
+    return h | (v << 2) | (d << 4);
+}
+
+// Sign-coding decision ((context << 1) | bit) of the sample at window row R
+// of own column j whose sign is neg; N: the sign window.
+__device__ __forceinline__ uint32_t sign_symbol(uint32_t A, uint32_t B, uint32_t N, int j, int R, uint32_t neg)
+{
+    const int l = 8 * (j - 1) + R, m = 8 * j + R, r = 8 * (j + 1) + R;
+    auto ct = [N](uint32_t W, int k) -> int { return ((W >> k) & 1u) ? (((N >> k) & 1u) ? -1 : 1) : 0; };
+    int h = ct(A, l) + ct(B, r), v = ct(A, m - 1) + ct(B, m + 1);
+    h = h < -1 ? -1 : (h > 1 ? 1 : h);
+    v = v < -1 ? -1 : (v > 1 ? 1 : v);
+    const uint32_t e = (uint32_t)(kScPacked >> (4 * ((h + 1) + 3 * (v + 1)))) & 0xFu;
+    return ((9u + (e & 7u)) << 1) | (neg ^ (e >> 3));
+}
+
+// Exclusive prefix sum of v over the warp; total: the sum over all lanes.
+__device__ __forceinline__ int warp_excl(int v, int lane, int &total)
+{
+    int incl = v;
 #pragma unroll
-            for (int half = 0; half < 2; half++) {
-                const int x = half * 32 + lane;
-                uint32_t q = 0;  // up to four 3-bit symbols
-                int n = 0;
-                if (x < w) {
-                    const int i0 = sti(x, y0);
-                    for (int r = 0; r < nr; r++) {
-                        const uint16_t wd = st[i0 + r];
-                        if (!(wd & kSig) || (wd & kVis)) continue;
-                        const uint32_t ctx = (wd & kRef) ? 2u : ((wd & kNbMask) ? 1u : 0u);
-                        const uint32_t bit = (uint32_t)(s.bm[y0 + r] >> x) & 1u;
-                        q |= ((ctx << 1) | bit) << (3 * n);
-                        n++;
-                        st[i0 + r] = wd | kRef | (uint16_t)(2u << kEvShift);
-                    }
-                }
-                int incl = n;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                const int at = total + incl - n;
-                for (int k = 0; k < n; k++) s.mq[at + k] = (uint8_t)((q >> (3 * k)) & 7u);
-                total += __shfl_sync(0xffffffffu, incl, 31);
-            }
-            __syncwarp();
-            if (lane == 0)
-                for (int k = 0; k < total; k++) {
-                    const uint32_t q = s.mq[k];
-                    e.encode(s.cxw, 14 + (int)(q >> 1), (int)(q & 1u));
-                }
-            __syncwarp();
-            continue;
-        }
-        // candidate columns: significance pass, a row with neighbours and
-        // without significance; cleanup, a row neither significant nor visited
-        uint64_t cand = 0;
-#pragma unroll
-        for (int half = 0; half < 2; half++) {
-            const int x = half * 32 + lane;
-            bool c = false;
-            if (x < w) {
-                const uint64_t q4 = *reinterpret_cast<const uint64_t *>(st + sti(x, y0)) & rows;
-                const uint64_t sig4 = q4 & (kRep * kSig), vis4 = q4 & (kRep * kVis), nb4 = q4 & (kRep * kNbMask);
-                if (type == 0) {
-                    const uint64_t has_nb = (nb4 + kRep * 0x7F) & (kRep * 0x80);  // bit 7 (= kSig) where nb != 0
-                    c = (has_nb & ~sig4) != 0;
-                } else {
-                    c = ((sig4 | (vis4 >> 2)) ^ (kRep * kSig & rows)) != 0;  // kVis = kSig << 2
-                }
-            }
-            cand |= (uint64_t)__ballot_sync(0xffffffffu, c) << (32 * half);
-        }
-        if (lane == 0) {
-            while (cand) {
-                const int x = __ffsll((long long)cand) - 1;
-                cand &= cand - 1;
-                const int i0 = sti(x, y0);
-                bool newsig = false;
-                int y = y0;
-                if (type == 2 && nr == 4) {
-                    const uint64_t q4 = *reinterpret_cast<const uint64_t *>(st + i0);
-                    if ((q4 & (kRep * (kNbMask | kSig | kVis))) == 0) {
-                        // run-length mode: four uncoded, insignificant samples
-                        // with all-zero neighbourhoods
-                        int r = 4;
-#pragma unroll
-                        for (int k = 3; k >= 0; k--)
-                            if ((s.bm[y0 + k] >> x) & 1) r = k;
-                        e.encode(s.cxw, kCtxRL, r < 4);
-                        if (r == 4) continue;
-                        e.encode(s.cxw, kCtxUni, r >> 1);
-                        e.encode(s.cxw, kCtxUni, r & 1);
-                        const int i = i0 + r;
-                        code_sign(s, e, i, st[i]);
-                        st[i] |= kSig | (uint16_t)(3u << kEvShift);
-                        set_sig(st, i);
-                        y = y0 + r + 1;
-                    }
-                }
-                for (; y < y0 + nr; y++) {
-                    const int i = i0 + (y - y0);
-                    const uint16_t wd = st[i];
-                    if (type == 0) {
-                        if ((wd & kSig) || (wd & kNbMask) == 0) continue;
-                    } else {
-                        if (wd & (kSig | kVis)) continue;
-                    }
-                    const int bit = (int)((s.bm[y] >> x) & 1);
-                    e.encode(s.cxw, zc[wd & kNbMask], bit);
-                    uint16_t nw = wd;
-                    if (type == 0) nw |= kVis;
-                    if (bit) {
-                        code_sign(s, e, i, wd);
-                        nw |= kSig | (uint16_t)((type == 0 ? 1u : 3u) << kEvShift);
-                        st[i] = nw;
-                        set_sig(st, i);
-                        newsig = true;
-                    } else {
-                        st[i] = nw;
-                    }
-                }
-                // a new significance gives the next column's samples a
-                // neighbour: it joins the significance pass's candidates
-                if (type == 0 && newsig && x + 1 < w) cand |= 1ull << (x + 1);
-            }
-        }
-        __syncwarp();
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
     }
+    total = __shfl_sync(kFull, incl, 31);
+    return incl - v;
+}
+
+// Decisions of one own column (j) of a stripe, in scan order: the coded
+// rows c (zero coding, then the sign where the sample turns significant,
+// rows n); with rl, run-length mode first (the run decision, and where a
+// sample of the column turns significant, its row in two uniform
+// decisions and its sign; the rows below it then coded one by one).
+struct StripeCtx {
+    uint32_t A, B, N;
+    int y0;
+    const uint8_t *zc;
+};
+__device__ __forceinline__ int col_count(uint32_t c, uint32_t n, bool rl)
+{
+    if (!rl) return __popc(c) + __popc(n);
+    if (!n) return 1;
+    const uint32_t below = (0xEu << (__ffs(n) - 1)) & 0xFu;
+    return 4 + __popc(c & below) + __popc(n & below);
+}
+__device__ __forceinline__ void col_emit(uint8_t *&o, const StripeCtx &S, int j, uint32_t c, uint32_t n, bool rl,
+                                         uint64_t ng)
+{
+    uint32_t rest = c;
+    if (rl) {
+        *o++ = (uint8_t)((kCtxRL << 1) | (n != 0 ? 1 : 0));
+        if (!n) return;
+        const int r = __ffs(n) - 1;
+        *o++ = (uint8_t)((kCtxUni << 1) | (r >> 1));
+        *o++ = (uint8_t)((kCtxUni << 1) | (r & 1));
+        *o++ = (uint8_t)sign_symbol(S.A, S.B, S.N, j, r + 1, (uint32_t)(ng >> (S.y0 + r)) & 1u);
+        rest = c & (0xEu << r) & 0xFu;
+    }
+    for (uint32_t m = rest; m; m &= m - 1) {
+        const int r = __ffs(m) - 1;
+        const uint32_t nb = (n >> r) & 1u;
+        *o++ = (uint8_t)((S.zc[nb_index(S.A, S.B, j, r + 1)] << 1) | nb);
+        if (nb) *o++ = (uint8_t)sign_symbol(S.A, S.B, S.N, j, r + 1, (uint32_t)(ng >> (S.y0 + r)) & 1u);
+    }
+}
+
+// The block state of a lane (its two columns).
+struct Cols {
+    uint64_t sig[2], neg[2], ref[2], vis[2], bm[2], nsp[2], ncu[2];
+};
+
+__device__ __forceinline__ uint32_t dil4(uint32_t p) { return (p | (p << 1) | (p >> 1)) & 0xFu; }
+// Seeds s spread down the column through the rows of u.
+__device__ __forceinline__ uint32_t fill_down(uint32_t s, uint32_t u)
+{
+    s |= (s << 1) & u;
+    s |= (s << 1) & u;
+    s |= (s << 1) & u;
+    return s;
+}
+
+// Significance propagation over stripe y0: writes the stripe's decisions
+// at out (room bytes left) and returns their number.  A sample is coded
+// when it is insignificant and has a significant neighbour at its turn, so
+// a sample turning significant makes later ones in the scan (the next
+// column, the rows below) candidates: the warp finds the new significances
+// of each column from those of the column before it (ex: the rows and
+// columns that exist), iterating until no lane's left column changes
+// (one lane more is settled per round, so at most 33 rounds).
+__device__ __forceinline__ int t1_spp(Cols &s, int y0, uint32_t ex0, uint32_t ex1, int lane, const uint8_t *zc,
+                                      uint8_t *out, int room, bool &ovf)
+{
+    const uint32_t B = window(rows6(s.sig[0], y0), rows6(s.sig[1], y0), lane);
+    const uint32_t f0 = ~(B >> 9) & ex0, f1 = ~(B >> 17) & ex1;  // insignificant samples
+    const uint32_t b0 = any_nb(B, 1) & f0, b1 = any_nb(B, 2) & f1;
+    if (!__any_sync(kFull, (b0 | b1) != 0u)) return 0;
+    const uint32_t u0 = rows4(s.bm[0], y0) & f0, u1 = rows4(s.bm[1], y0) & f1;
+    uint32_t pin = 0, t0 = 0, t1 = 0, n0 = 0, n1 = 0;
+    for (int it = 0; it <= 32; it++) {
+        t0 = b0 | (dil4(pin) & f0);
+        n0 = fill_down(t0 & u0, u0);
+        t1 = b1 | (dil4(n0) & f1);
+        n1 = fill_down(t1 & u1, u1);
+        uint32_t pn = __shfl_up_sync(kFull, n1, 1);
+        if (lane == 0) pn = 0;
+        const bool moved = pn != pin;
+        pin = pn;
+        if (!__any_sync(kFull, moved)) break;
+    }
+    const uint32_t c0 = (t0 | (n0 << 1)) & f0, c1 = (t1 | (n1 << 1)) & f1;
+    StripeCtx S;
+    S.B = B;
+    S.A = B | (pin << 1) | (n0 << 9) | (n1 << 17);
+    S.N = __any_sync(kFull, (n0 | n1) != 0u) ? window(rows6(s.neg[0], y0), rows6(s.neg[1], y0), lane) : 0u;
+    S.y0 = y0;
+    S.zc = zc;
+    int total;
+    const int at = warp_excl(col_count(c0, n0, false) + col_count(c1, n1, false), lane, total);
+    if (total > room) {
+        ovf = true;
+    } else {
+        uint8_t *o = out + at;
+        col_emit(o, S, 1, c0, n0, false, s.neg[0]);
+        col_emit(o, S, 2, c1, n1, false, s.neg[1]);
+    }
+    s.sig[0] |= (uint64_t)n0 << y0;
+    s.sig[1] |= (uint64_t)n1 << y0;
+    s.nsp[0] |= (uint64_t)n0 << y0;
+    s.nsp[1] |= (uint64_t)n1 << y0;
+    s.vis[0] |= (uint64_t)c0 << y0;
+    s.vis[1] |= (uint64_t)c1 << y0;
+    return total;
+}
+
+// Magnitude refinement over stripe y0: the samples significant before this
+// plane; context 16 after their first refinement, else 15 or 14 by whether
+// any neighbour is significant.
+__device__ __forceinline__ int t1_mrp(Cols &s, int y0, int lane, uint8_t *out, int room, bool &ovf)
+{
+    const uint32_t B = window(rows6(s.sig[0], y0), rows6(s.sig[1], y0), lane);
+    const uint32_t m0 = (B >> 9) & ~rows4(s.vis[0], y0) & 0xFu, m1 = (B >> 17) & ~rows4(s.vis[1], y0) & 0xFu;
+    if (!__any_sync(kFull, (m0 | m1) != 0u)) return 0;
+    int total;
+    const int at = warp_excl(__popc(m0) + __popc(m1), lane, total);
+    if (total > room) {
+        ovf = true;
+    } else {
+        uint8_t *o = out + at;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            const uint32_t a = any_nb(B, c + 1), rf = rows4(s.ref[c], y0), v = rows4(s.bm[c], y0);
+            for (uint32_t m = c ? m1 : m0; m; m &= m - 1) {
+                const int r = __ffs(m) - 1;
+                const uint32_t ctx = ((rf >> r) & 1u) ? 16u : (((a >> r) & 1u) ? 15u : 14u);
+                *o++ = (uint8_t)((ctx << 1) | ((v >> r) & 1u));
+            }
+        }
+    }
+    s.ref[0] |= (uint64_t)m0 << y0;
+    s.ref[1] |= (uint64_t)m1 << y0;
+    return total;
+}
+
+// Cleanup over stripe y0: every sample neither significant nor visited is
+// coded, so the new significances are known at once; a full column of
+// such samples whose neighbourhood is insignificant at its turn is coded
+// in run-length mode.
+__device__ __forceinline__ int t1_cup(Cols &s, int y0, uint32_t ex0, uint32_t ex1, int lane, const uint8_t *zc,
+                                      uint8_t *out, int room, bool &ovf)
+{
+    const uint32_t B = window(rows6(s.sig[0], y0), rows6(s.sig[1], y0), lane);
+    const uint32_t c0 = ~(B >> 9) & ~rows4(s.vis[0], y0) & ex0, c1 = ~(B >> 17) & ~rows4(s.vis[1], y0) & ex1;
+    if (!__any_sync(kFull, (c0 | c1) != 0u)) return 0;
+    const uint32_t n0 = c0 & rows4(s.bm[0], y0), n1 = c1 & rows4(s.bm[1], y0);
+    uint32_t pl = __shfl_up_sync(kFull, n1, 1);
+    if (lane == 0) pl = 0;
+    StripeCtx S;
+    S.B = B;
+    S.A = B | (pl << 1) | (n0 << 9) | (n1 << 17);
+    S.N = __any_sync(kFull, (n0 | n1) != 0u) ? window(rows6(s.neg[0], y0), rows6(s.neg[1], y0), lane) : 0u;
+    S.y0 = y0;
+    S.zc = zc;
+    // run-length mode: four uncoded samples (a full stripe) and no
+    // significant neighbour (the left column as it stands, the own and the
+    // right column as before this pass)
+    const bool rl0 = c0 == 0xFu && (S.A & 0x3Fu) == 0u && ((B >> 8) & 0x3Fu) == 0u && ((B >> 16) & 0x3Fu) == 0u;
+    const bool rl1 = c1 == 0xFu && ((S.A >> 8) & 0x3Fu) == 0u && ((B >> 16) & 0x3Fu) == 0u && ((B >> 24) & 0x3Fu) == 0u;
+    int total;
+    const int at = warp_excl(col_count(c0, n0, rl0) + col_count(c1, n1, rl1), lane, total);
+    if (total > room) {
+        ovf = true;
+    } else {
+        uint8_t *o = out + at;
+        col_emit(o, S, 1, c0, n0, rl0, s.neg[0]);
+        col_emit(o, S, 2, c1, n1, rl1, s.neg[1]);
+    }
+    s.sig[0] |= (uint64_t)n0 << y0;
+    s.sig[1] |= (uint64_t)n1 << y0;
+    s.ncu[0] |= (uint64_t)n0 << y0;
+    s.ncu[1] |= (uint64_t)n1 << y0;
+    return total;
 }
 
 __device__ __forceinline__ long long warp_sum_ll(long long v)
@@ -457,51 +545,54 @@ __device__ void cb_geometry(int j, int W, int H, int D, int &band, int &ori, int
 
 }  // namespace
 
-// Tier-1 coding: one warp per code-block of the job (taken dynamically).
-__global__ void __launch_bounds__(32 * kT1Warps, 3) k_t1(const CsJob *__restrict__ job)
+// Tier-1 context modelling: one warp per code-block of the job (taken
+// dynamically: their costs differ by orders of magnitude).  Writes the
+// block's decisions pass by pass (sym, nsym), its plane count and pass
+// count (info 0, 1; info 3 = 2 for magnitudes of 2^24 or more) and the
+// passes' distortion decreases.
+__global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ job)
 {
-    extern __shared__ __align__(16) unsigned char t1sm[];
-    __shared__ uint8_t s_zc[4][128];  // zero-coding context by orientation and the state word's bits 0-6
-    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    T1Warp &s = reinterpret_cast<T1Warp *>(t1sm)[wp];
+    __shared__ uint8_t s_zc[4][128];  // zero-coding context by orientation and zero-coding index
+    const int lane = threadIdx.x & 31;
     for (int i = threadIdx.x; i < 4 * 128; i += blockDim.x) {
         const int o = i >> 7, b = i & 127;
         // counts beyond their range (h, v > 2, d > 4) never occur
         s_zc[o][b] = (uint8_t)zc_rule(o, min(b & 3, 2), min((b >> 2) & 3, 2), min(b >> 4, 4));
     }
     __syncthreads();
-    // code-blocks are taken in order from the job's counter, one per warp
-    // at a time: their costs differ by orders of magnitude
     for (;;) {
     int g = 0;
     if (lane == 0) g = atomicAdd(job->next, 1);
-    g = __shfl_sync(0xffffffffu, g, 0);
+    g = __shfl_sync(kFull, g, 0);
     if (g >= job->ncb) break;
     // frame of the code-block (frames' code-block ranges are consecutive)
     int f = 0;
     while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
     const CsFrame &F = job->frames[f];
     const int jb = g - F.cb0;
-    int band, ori, x0, y0, cw, ch;
-    cb_geometry(jb, F.w, F.h, F.levels, band, ori, x0, y0, cw, ch);
-    const int32_t *coef = F.coef + (size_t)y0 * F.w + x0;
+    int band, ori, x0, y0b, cw, ch;
+    cb_geometry(jb, F.w, F.h, F.levels, band, ori, x0, y0b, cw, ch);
+    const int32_t *coef = F.coef + (size_t)y0b * F.w + x0;
     int32_t *info = F.info + (size_t)jb * kCbInfo;
-    int32_t *plen = F.plen + (size_t)jb * kMaxPasses;
     double *dist = F.dist + (size_t)jb * kMaxPasses;
+    int32_t *nsym = F.nsym + (size_t)jb * kMaxPasses;
+    uint8_t *const sym = F.sym + (size_t)jb * kSymCap;
+    const uint8_t *zc = s_zc[ori];
+    const bool has0 = 2 * lane < cw, has1 = 2 * lane + 1 < cw;
+    const int32_t *col = coef + 2 * lane;
 
-    __syncwarp();
-    for (int i = lane; i < (kCb + 2) * kColS; i += 32) s.st[i] = 0;
-    __syncwarp();
-    uint32_t mx = 0;
-    for (int y = 0; y < ch; y++)
-        for (int x = lane; x < cw; x += 32) {
-            const int32_t v = __ldg(coef + (size_t)y * F.w + x);
-            const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
-            mx |= m;
-            if (v < 0) s.st[sti(x, y)] = kNeg;
-        }
+    Cols s;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx |= __shfl_xor_sync(0xffffffffu, mx, o);
+    for (int c = 0; c < 2; c++) s.sig[c] = s.neg[c] = s.ref[c] = s.vis[c] = s.bm[c] = s.nsp[c] = s.ncu[c] = 0;
+    uint32_t mx = 0;
+    for (int y = 0; y < ch; y++) {
+        const int32_t v0 = has0 ? __ldg(col + (size_t)y * F.w) : 0, v1 = has1 ? __ldg(col + (size_t)y * F.w + 1) : 0;
+        mx |= (uint32_t)(v0 < 0 ? -(long long)v0 : v0) | (uint32_t)(v1 < 0 ? -(long long)v1 : v1);
+        s.neg[0] |= (uint64_t)(v0 < 0) << y;
+        s.neg[1] |= (uint64_t)(v1 < 0) << y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx |= __shfl_xor_sync(kFull, mx, o);
     const int planes = 32 - __clz(mx);
     if (lane == 0) {
         info[0] = planes;
@@ -516,37 +607,28 @@ __global__ void __launch_bounds__(32 * kT1Warps, 3) k_t1(const CsJob *__restrict
         }
         continue;
     }
-    if (lane < kNctx) s.cxw[lane] = kMq.w[lane == 0 ? 4 : (lane == kCtxRL ? 3 : (lane == kCtxUni ? 46 : 0))];
-    uint8_t *const cbytes = F.cbytes + (size_t)jb * job->cbcap;
-    Mqe e;
     int k = 0, pos = 0;
-    bool over = false;
+    bool ovf = false;
     // plane p's sweep also settles the distortion of plane p + 1's passes
     for (int p = planes - 1; p >= -1; p--) {
-        __syncwarp();
         long long dsp = 0, dmr = 0, dcu = 0;
-        const int q = p + 1;  // plane whose events are settled
-        for (int y = 0; y < ch; y++) {
+        const int q = p + 1;  // plane whose passes are settled
+        uint64_t before[2];   // significant before plane q
 #pragma unroll
-            for (int half = 0; half < 2; half++) {
-                const int x = half * 32 + lane;
-                bool bit = false;
-                if (x < cw) {
-                    const int32_t v = __ldg(coef + (size_t)y * F.w + x);
-                    const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
-                    if (p >= 0) bit = (m >> p) & 1;
-                    uint16_t &wd = s.st[sti(x, y)];
-                    const int ev = (wd >> kEvShift) & 3;
-                    if (ev == 1) dsp += derr(m, 32, q);
-                    else if (ev == 2) dmr += derr(m, q + 1, q);
-                    else if (ev == 3) dcu += derr(m, 32, q);
-                    wd &= (uint16_t)~(kEvMask | kVis);
-                }
-                const unsigned bal = __ballot_sync(0xffffffffu, bit);
-                if (lane == 0) {
-                    if (half == 0) s.bm[y] = bal;
-                    else s.bm[y] |= (uint64_t)bal << 32;
-                }
+        for (int c = 0; c < 2; c++) {
+            before[c] = s.sig[c] & ~(s.nsp[c] | s.ncu[c]);
+            s.bm[c] = 0;
+        }
+        for (int y = 0; y < ch; y++) {
+            const int32_t v0 = has0 ? __ldg(col + (size_t)y * F.w) : 0, v1 = has1 ? __ldg(col + (size_t)y * F.w + 1) : 0;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                const int32_t v = c ? v1 : v0;
+                const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
+                if (p >= 0) s.bm[c] |= (uint64_t)((m >> p) & 1u) << y;
+                if ((s.nsp[c] >> y) & 1u) dsp += derr(m, 32, q);
+                else if ((before[c] >> y) & 1u) dmr += derr(m, q + 1, q);
+                else if ((s.ncu[c] >> y) & 1u) dcu += derr(m, 32, q);
             }
         }
         dsp = warp_sum_ll(dsp);
@@ -564,26 +646,259 @@ __global__ void __launch_bounds__(32 * kT1Warps, 3) k_t1(const CsJob *__restrict
             }
         }
         if (p < 0) break;
-        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 2; c++) s.vis[c] = s.nsp[c] = s.ncu[c] = 0;
         for (int type = (p == planes - 1 ? 2 : 0); type <= 2; type++, k++) {
-            if (lane == 0) e.init(cbytes + pos, job->cbcap - pos);
-            t1_pass(s, e, type, cw, ch, s_zc[ori], lane);
-            if (lane == 0) {
-                const int len = e.flush();
-                over = over || e.over;
-                plen[k] = len;
-                pos += len;
+            int n = 0;  // decisions of this pass
+            for (int y0 = 0; y0 < ch; y0 += 4) {
+                const uint32_t rr = ch - y0 >= 4 ? 0xFu : ((1u << (ch - y0)) - 1u);
+                const uint32_t ex0 = has0 ? rr : 0u, ex1 = has1 ? rr : 0u;
+                uint8_t *const out = sym + pos + n;
+                const int room = kSymCap - pos - n;
+                if (type == 0) n += t1_spp(s, y0, ex0, ex1, lane, zc, out, room, ovf);
+                else if (type == 1) n += t1_mrp(s, y0, lane, out, room, ovf);
+                else n += t1_cup(s, y0, ex0, ex1, lane, zc, out, room, ovf);
             }
+            if (lane == 0) nsym[k] = n;
+            pos += n;
         }
     }
     if (lane == 0) {
         info[1] = k;
-        if (over) {
+        if (ovf) {
             info[3] = 1;
             if (job->err) atomicExch(job->err, kErrCbRange);
         }
     }
-    __syncwarp();
+    }
+}
+
+// Reads a code-block's decisions in order from 16-byte pieces, the next
+// piece loaded ahead (decision streams start 16-byte aligned and hold
+// kSymCap bytes).
+struct DecReader {
+    const uint4 *p;
+    uint4 cur, nxt;
+    int i;
+    __device__ __forceinline__ void start(const uint8_t *sym, int at)
+    {
+        p = reinterpret_cast<const uint4 *>(sym);
+        i = at;
+        const int pc = at >> 4;
+        const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+        cur = pc * 16 < kSymCap ? __ldg(p + pc) : z;  // at == kSymCap: an empty pass at the end
+        nxt = (pc + 1) * 16 < kSymCap ? __ldg(p + pc + 1) : z;
+    }
+    __device__ __forceinline__ uint32_t next()
+    {
+        const int ws = (i >> 2) & 3;
+        const uint32_t w = ws == 0 ? cur.x : (ws == 1 ? cur.y : (ws == 2 ? cur.z : cur.w));
+        const uint32_t d = (w >> ((i & 3) * 8)) & 0xFFu;
+        i++;
+        if ((i & 15) == 0) {
+            cur = nxt;
+            if (i + 16 < kSymCap) nxt = __ldg(p + (i >> 4) + 1);
+        }
+        return d;
+    }
+};
+
+__device__ __forceinline__ void mq_init_contexts(uint32_t (*cx)[kMqThreads], int t, const uint32_t *tab)
+{
+    for (int c = 0; c < kNctx; c++) cx[c][t] = tab[c == 0 ? 4 : (c == kCtxRL ? 3 : (c == kCtxUni ? 46 : 0))];
+}
+
+__device__ __forceinline__ int cb_frame(const CsJob *job, int g)
+{
+    int f = 0;
+    while (f + 1 < job->nframes && job->frames[f + 1].cb0 <= g) f++;
+    return f;
+}
+
+// MQ coding, first stage: one thread per code-block (taken dynamically)
+// runs the interval register and the context states over all of the
+// block's decisions (Annex C: the state of a context moves on only at a
+// renormalisation, which depends on the interval alone, not on the code
+// register), recording each pass's starting context states and the slot
+// its codeword is given: floor(S / 7) + 3 bytes for S renormalisation
+// shifts (the first byte leaves after 12 shifts, each later one after 7 or
+// 8, and the termination adds two).  Branch-free per decision: both next
+// states are looked up before the renormalisation is known, and the next
+// decision's context word is loaded ahead (and forwarded when it is the
+// same context).
+__global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ job)
+{
+    __shared__ uint32_t s_cx[32][kMqThreads];  // the contexts of each thread's code-block
+    __shared__ uint32_t s_tab[64];             // the probability table rows
+    const int t = threadIdx.x;
+    for (int i = t; i < 64; i += blockDim.x) s_tab[i] = i < 47 ? kMq.w[i] : 0u;
+    __syncthreads();
+    for (;;) {
+        const int g = atomicAdd(job->next + 1, 1);
+        if (g >= job->ncb) break;
+        const CsFrame &F = job->frames[cb_frame(job, g)];
+        const int jb = g - F.cb0;
+        int32_t *info = F.info + (size_t)jb * kCbInfo;
+        const int np = info[1];
+        if (info[3] != 0 || np <= 0) continue;
+        const int32_t *nsym = F.nsym + (size_t)jb * kMaxPasses;
+        int4 *ptab = F.ptab + (size_t)jb * kMaxPasses;
+        uint32_t *mqs = F.mqs + (size_t)jb * kMaxPasses * kMqWords;
+        int total = 0;
+        bool over = false;
+        for (int k = 0; k < np; k++) {
+            const int n = nsym[k];
+            if (n < 0 || n > kSymCap - total) over = true;  // never: the model bounds its decisions
+            else total += n;
+        }
+        int off = 0;
+        if (!over) {
+            mq_init_contexts(s_cx, t, s_tab);
+            for (int c = 0; c < kNctx; c++) mqs[c] = s_cx[c][t];
+            DecReader rd;
+            rd.start(F.sym + (size_t)jb * kSymCap, 0);
+            // one loop over all of the block's decisions (the pass
+            // boundaries inside it), so that the threads of a warp do not
+            // wait for each other at every pass
+            int k = 0, i = 0, start = 0, end = nsym[0], S = 0;
+            uint32_t a = 0x8000;
+            uint32_t d = total > 0 ? rd.next() : 0u;
+            uint32_t w = s_cx[(d >> 1) & 31u][t];
+            for (;;) {
+                if (i == end) {
+                    ptab[k] = make_int4(start, off, S / 7 + 3, 0);
+                    off += S / 7 + 3;
+                    if (++k == np) break;
+                    for (int c = 0; c < kNctx; c++) mqs[k * kMqWords + c] = s_cx[c][t];
+                    start = i;
+                    end = i + nsym[k];
+                    a = 0x8000;
+                    S = 0;
+                    continue;
+                }
+                const uint32_t cx = (d >> 1) & 31u;
+                const uint32_t d2 = i + 1 < total ? rd.next() : 0u;
+                const uint32_t cx2 = (d2 >> 1) & 31u;
+                const uint32_t w2 = s_cx[cx2][t];  // stale when cx2 == cx: forwarded below
+                const uint32_t qe = w & 0xFFFFu, mps = w >> 31;
+                const uint32_t tm = s_tab[(w >> 16) & 63u], tl = s_tab[(w >> 22) & 63u];
+                const uint32_t a1 = a - qe;
+                const bool is_mps = (d & 1u) == mps;
+                const bool keep = is_mps && (a1 & 0x8000u);
+                const bool xchg = a1 < qe;
+                const uint32_t a2 = is_mps != xchg ? a1 : qe;  // a1 whenever keep
+                const int sh = __clz(a2) - 16;                 // 0 whenever keep
+                a = a2 << sh;
+                S += sh;
+                const uint32_t wn =
+                    keep ? w : (is_mps ? (tm | (mps << 31)) : (tl | ((mps ^ ((w >> 28) & 1u)) << 31)));
+                s_cx[cx][t] = wn;
+                w = cx2 == cx ? wn : w2;
+                d = d2;
+                i++;
+            }
+        }
+        if (over || off > kCbRegion) {
+            // the passes need more than kCbBytes (see kCbRegion)
+            info[3] = 1;
+            if (job->err) atomicExch(job->err, kErrCbRange);
+        }
+    }
+}
+
+// MQ coding, second stage: one thread per (code-block, pass), taken
+// dynamically: every pass is a terminated codeword of its own, so with its
+// starting context states it is coded apart from the others, into its
+// slot.
+__global__ void __launch_bounds__(kMqThreads) k_t1_mqc(const CsJob *__restrict__ job)
+{
+    __shared__ uint32_t s_cx[32][kMqThreads];
+    __shared__ uint32_t s_tab[64];
+    const int t = threadIdx.x;
+    for (int i = t; i < 64; i += blockDim.x) s_tab[i] = i < 47 ? kMq.w[i] : 0u;
+    __syncthreads();
+    const int items = job->ncb * kMaxPasses;
+    for (;;) {
+        const int u = atomicAdd(job->next + 2, 1);
+        if (u >= items) break;
+        // pass-major: a warp's threads take the same pass of neighbouring
+        // code-blocks, of similar lengths
+        const int k = u / job->ncb, g = u - k * job->ncb;
+        const CsFrame &F = job->frames[cb_frame(job, g)];
+        const int jb = g - F.cb0;
+        int32_t *info = F.info + (size_t)jb * kCbInfo;
+        if (info[3] != 0 || k >= info[1]) continue;
+        const int4 pt = F.ptab[(size_t)jb * kMaxPasses + k];
+        const int n = F.nsym[(size_t)jb * kMaxPasses + k];
+        const uint32_t *mqs = F.mqs + ((size_t)jb * kMaxPasses + k) * kMqWords;
+        for (int c = 0; c < kNctx; c++) s_cx[c][t] = mqs[c];
+        DecReader rd;
+        rd.start(F.sym + (size_t)jb * kSymCap, pt.x);
+        Mqe e;
+        e.init(F.cbytes + (size_t)jb * kCbRegion + pt.y, pt.z);
+        for (int j = 0; j < n; j++) {
+            const uint32_t d = rd.next();
+            e.encode(s_cx[(d >> 1) & 31u][t], s_tab, d & 1u);
+        }
+        const int len = e.flush();
+        F.plen[(size_t)jb * kMaxPasses + k] = len;
+        if (e.over) {  // never: the slot bounds the codeword
+            info[3] = 1;
+            if (job->err) atomicExch(job->err, kErrCbRange);
+        }
+    }
+}
+
+// Moves each code-block's pass codewords from their slots to be back to
+// back from the start of its region (one warp per code-block; a block
+// whose passes exceed kCbBytes gets info 3 = 1).  Slots only move down
+// and each 256-byte piece is read whole before it is written, so the move
+// is in place.
+__global__ void __launch_bounds__(256) k_t1_pack(const CsJob *__restrict__ job)
+{
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = w0; g < job->ncb; g += nw) {
+        const CsFrame &F = job->frames[cb_frame(job, g)];
+        const int jb = g - F.cb0;
+        int32_t *info = F.info + (size_t)jb * kCbInfo;
+        const int np = info[1];
+        if (info[3] != 0 || np <= 0) continue;
+        const int32_t *plen = F.plen + (size_t)jb * kMaxPasses;
+        const int4 *ptab = F.ptab + (size_t)jb * kMaxPasses;
+        uint8_t *const region = F.cbytes + (size_t)jb * kCbRegion;
+        int total = 0;
+        for (int k = lane; k < np; k += 32) total += plen[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(kFull, total, o);
+        if (total > job->cbcap) {
+            if (lane == 0) {
+                info[3] = 1;
+                if (job->err) atomicExch(job->err, kErrCbRange);
+            }
+            continue;
+        }
+        int dst = 0;
+        for (int k = 0; k < np; k++) {
+            const int len = plen[k], src = ptab[k].y;
+            if (src != dst)
+                for (int o = 0; o < len; o += 256) {
+                    uint8_t v[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int at = o + q * 32 + lane;
+                        v[q] = at < len ? region[src + at] : (uint8_t)0;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const int at = o + q * 32 + lane;
+                        if (at < len) region[dst + at] = v[q];
+                    }
+                    __syncwarp();
+                }
+            dst += len;
+        }
     }
 }
 
@@ -804,7 +1119,7 @@ __global__ void __launch_bounds__(256) k_cs_copy(const CsJob *__restrict__ job)
         }
         int nbytes = 0;
         for (int k = 0; k < nk; k++) nbytes += pl[k];
-        const uint8_t *src = F.cbytes + (size_t)j * job->cbcap;
+        const uint8_t *src = F.cbytes + (size_t)j * kCbRegion;
         for (int i = lane; i < nbytes; i += 32) dst[2 * nk + i] = src[i];
     }
 }
@@ -1085,7 +1400,7 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
                 const int nk = in[2];
                 if (nk == 0) continue;
                 const int nbytes = in[5] - 2 * nk;
-                const uint8_t *src = F.cbytes + (size_t)j * job->cbcap;
+                const uint8_t *src = F.cbytes + (size_t)j * kCbRegion;
                 for (int i = lane; i < nbytes; i += 32)
                     if (pos + i < cap) out[pos + i] = src[i];
                 pos += nbytes;
@@ -1115,20 +1430,6 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
     }
 }
 
-namespace {
-void ensure_t1_attr()
-{
-    static std::mutex mu;
-    static bool done[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
-    std::lock_guard<std::mutex> lk(mu);
-    if (done[dev]) return;
-    cudaFuncSetAttribute(k_t1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kT1Warps * sizeof(T1Warp)));
-    done[dev] = true;
-}
-}  // namespace
-
 int ebcot_codeblocks(int w, int h, int levels)
 {
     int n = 0;
@@ -1142,17 +1443,22 @@ int ebcot_codeblocks(int w, int h, int levels)
 
 void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
 {
-    ensure_t1_attr();
-    k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
+    const long long items = (long long)ncb * kMaxPasses;
+    k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, 0, s>>>(job_dev);
+    k_t1_mq<<<std::max(1, (ncb + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
+    k_t1_mqc<<<(int)std::min<long long>(4096, (items + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
+    k_t1_pack<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
     k_pcrd<<<std::max(1, nframes), 1024, 0, s>>>(job_dev);
     k_cs_copy<<<std::max(1, (ncb + 7) / 8), 256, 0, s>>>(job_dev);
     k_j2c<<<std::max(1, nframes), 32, 0, s>>>(job_dev);
 }
 
-void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, cudaStream_t s)
+void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, cudaStream_t s)
 {
-    ensure_t1_attr();
-    k_t1<<<grid_t1, 32 * kT1Warps, kT1Warps * sizeof(T1Warp), s>>>(job_dev);
+    k_t1<<<grid_t1, 32 * kT1Warps, 0, s>>>(job_dev);
+    k_t1_mq<<<grid_mq, kMqThreads, 0, s>>>(job_dev);
+    k_t1_mqc<<<4 * grid_mq, kMqThreads, 0, s>>>(job_dev);
+    k_t1_pack<<<grid_copy, 256, 0, s>>>(job_dev);
     k_pcrd<<<kMaxBatch, 1024, 0, s>>>(job_dev);
     k_cs_copy<<<grid_copy, 256, 0, s>>>(job_dev);
     k_j2c<<<kMaxBatch, 32, 0, s>>>(job_dev);
@@ -1160,9 +1466,8 @@ void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, c
 
 int occupancy_t1()
 {
-    ensure_t1_attr();
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t1, 32 * kT1Warps, kT1Warps * sizeof(T1Warp));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_t1, 32 * kT1Warps, 0);
     return b;
 }
 

@@ -62,7 +62,7 @@ bool denoise_radius_supported(int r);
 int ebcot_codeblocks(int w, int h, int levels);
 void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s);
 // The same with fixed (persistent, grid-stride) grids, for captured graphs.
-void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_copy, cudaStream_t s);
+void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, cudaStream_t s);
 int occupancy_t1();
 
 // 9/7 quantisation steps (host, double precision); see flowroi_quant_steps.

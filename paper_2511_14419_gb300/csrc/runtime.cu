@@ -194,7 +194,7 @@ struct flowroi_ctx {
     int graph_launches = 0;
     int desc_next = 0;
     int grid_exp = 0, grid_upd = 0, grid_win = 0, grid_mask = 0, grid_dwt = 0, grid_frames = 0, grid_den = 0, grid_cc = 0, grid_mrg = 0, grid_reg = 0;
-    int grid_t1 = 0, grid_csc = 0;
+    int grid_t1 = 0, grid_mq = 0, grid_csc = 0;
     int occ[TK_COUNT] = {};         // resident blocks per SM of the tunable persistent kernels
     int dwt_variant = 5;            // DWT register budget in use (resident blocks per SM)
     int upd_rows = kUpdRows;        // rows per thread of the update kernel's tile columns
@@ -582,12 +582,20 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
             const size_t n = (size_t)s->cs_ncb;
             char *b = s->cs_scratch;
             C.cbytes = reinterpret_cast<uint8_t *>(b);
-            b += n * kCbBytes;
+            b += n * kCbRegion;
+            C.sym = reinterpret_cast<uint8_t *>(b);  // 16-byte aligned: the MQ coder reads it in 16-byte pieces
+            b += n * kSymCap;
+            C.ptab = reinterpret_cast<int4 *>(b);
+            b += n * kMaxPasses * sizeof(int4);
+            C.mqs = reinterpret_cast<uint32_t *>(b);
+            b += n * kMaxPasses * kMqWords * sizeof(uint32_t);
             C.dist = reinterpret_cast<double *>(b);
             b += n * kMaxPasses * sizeof(double);
             C.hs = reinterpret_cast<double *>(b);
             b += n * (kMaxPasses + 1) * sizeof(double);
             C.plen = reinterpret_cast<int32_t *>(b);
+            b += n * kMaxPasses * sizeof(int32_t);
+            C.nsym = reinterpret_cast<int32_t *>(b);
             b += n * kMaxPasses * sizeof(int32_t);
             C.info = reinterpret_cast<int32_t *>(b);
             b += n * kCbInfo * sizeof(int32_t);
@@ -776,10 +784,10 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
     if (c->cfg.codestream_bpp > 0.f) {
         // tier-1 coding, rate control and containers of the batch's front-end frames
         timed(c, st, prof, K_CS, -1, -1, [&] {
-            cudaMemsetAsync(const_cast<int *>(&dd->cs_next), 0, sizeof(int), st);
-            launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_csc, st);
+            cudaMemsetAsync(const_cast<int *>(dd->cs_next), 0, sizeof dd->cs_next, st);
+            launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_mq, c->grid_csc, st);
         });
-        cnt += 4;
+        cnt += 7;
     }
     *nlaunch = cnt;
     return FLOWROI_OK;
@@ -857,7 +865,7 @@ int step_locked(flowroi_ctx *c)
     for (size_t i = 0; i < sel.size(); i++) fill_frame(c, sel[i].s, sel[i].e, sel[i].d, hd.f[i]);
     fill_offsets(c, hd);
     hd.cs.frames = c->desc_dev[k]->csf;
-    hd.cs.next = &c->desc_dev[k]->cs_next;
+    hd.cs.next = c->desc_dev[k]->cs_next;
     for (auto &pk : sel)
         if (pk.e) CK(c, cudaStreamWaitEvent(c->s_comp, pk.e->uploaded, 0));
     const size_t bytes = offsetof(BatchDesc, f) + sizeof(FrameDesc) * sel.size();
@@ -1265,6 +1273,7 @@ int flowroi_create(const flowroi_config *cfg, flowroi_ctx **out)
     c->grid_mrg = 8 * c->num_sms;
     c->grid_reg = cfg->register_frames ? std::max(1, occupancy_register()) * c->num_sms : 0;
     c->grid_t1 = cfg->codestream_bpp > 0.f ? std::max(1, occupancy_t1()) * c->num_sms : 0;
+    c->grid_mq = 4 * c->num_sms;
     c->grid_csc = 8 * c->num_sms;
     c->grid_frames = kMaxBatch;
     size_t freeb = 0, totalb = 0;
@@ -1778,13 +1787,17 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
         return at;
     };
     const size_t o_frames = take(sizeof(CsFrame) * (size_t)n), o_job = take(sizeof(CsJob));
-    const size_t o_bytes = take((size_t)ncb * kCbBytes);
+    const size_t o_bytes = take((size_t)ncb * kCbRegion);
     const size_t o_plen = take((size_t)ncb * kMaxPasses * sizeof(int32_t));
+    const size_t o_nsym = take((size_t)ncb * kMaxPasses * sizeof(int32_t));
+    const size_t o_ptab = take((size_t)ncb * kMaxPasses * sizeof(int4));
+    const size_t o_mqs = take((size_t)ncb * kMaxPasses * kMqWords * sizeof(uint32_t));
+    const size_t o_sym = take((size_t)ncb * kSymCap);
     const size_t o_dist = take((size_t)ncb * kMaxPasses * sizeof(double));
     const size_t o_info = take((size_t)ncb * kCbInfo * sizeof(int32_t));
     const size_t o_hk = take((size_t)ncb * (kMaxPasses + 1) * sizeof(int32_t));
     const size_t o_hs = take((size_t)ncb * (kMaxPasses + 1) * sizeof(double));
-    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(2 * sizeof(unsigned));
+    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(4 * sizeof(unsigned));
     const size_t o_coef = on_device ? 0 : take(coef_bytes), o_out = on_device ? 0 : take(out_bytes);
 
     int rc = FLOWROI_OK;
@@ -1824,8 +1837,12 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     for (int i = 0; i < n; i++) {
         CsFrame &F = fr[(size_t)i];
         const size_t b0 = (size_t)F.cb0;
-        F.cbytes = dev + o_bytes + b0 * kCbBytes;
+        F.cbytes = dev + o_bytes + b0 * kCbRegion;
         F.plen = reinterpret_cast<int32_t *>(dev + o_plen) + b0 * kMaxPasses;
+        F.nsym = reinterpret_cast<int32_t *>(dev + o_nsym) + b0 * kMaxPasses;
+        F.ptab = reinterpret_cast<int4 *>(dev + o_ptab) + b0 * kMaxPasses;
+        F.mqs = reinterpret_cast<uint32_t *>(dev + o_mqs) + b0 * kMaxPasses * kMqWords;
+        F.sym = dev + o_sym + b0 * kSymCap;
         F.dist = reinterpret_cast<double *>(dev + o_dist) + b0 * kMaxPasses;
         F.info = reinterpret_cast<int32_t *>(dev + o_info) + b0 * kCbInfo;
         F.hk = reinterpret_cast<int32_t *>(dev + o_hk) + b0 * (kMaxPasses + 1);
@@ -1841,7 +1858,7 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     job.next = reinterpret_cast<int *>(dev + o_err) + 1;
     step(cudaMemcpyAsync(dev + o_frames, fr.data(), sizeof(CsFrame) * (size_t)n, cudaMemcpyHostToDevice, st));
     step(cudaMemcpyAsync(dev + o_job, &job, sizeof job, cudaMemcpyHostToDevice, st));
-    step(cudaMemsetAsync(dev + o_err, 0, 2 * sizeof(unsigned), st));
+    step(cudaMemsetAsync(dev + o_err, 0, 4 * sizeof(unsigned), st));
     if (e == cudaSuccess) {
         launch_ebcot(reinterpret_cast<const CsJob *>(dev + o_job), n, ncb, st);
         step(cudaGetLastError());
