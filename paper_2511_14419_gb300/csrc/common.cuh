@@ -94,8 +94,8 @@ constexpr int kCbBytes = 32768;                // pass bytes a code-block may pr
 // (context << 1 | decision): per bit-plane and stripe column at most six
 // that are not signs (four samples, or run-length mode's run symbol, two
 // position symbols and the three samples below), and one sign per sample
-// over all planes.
-constexpr int kSymCap = kMaxPlanes * 6 * (kCb * kCb / 4) + kCb * kCb;
+// over all planes; each pass starts 16-byte aligned.
+constexpr int kSymCap = kMaxPlanes * 6 * (kCb * kCb / 4) + kCb * kCb + 16 * kMaxPasses;
 // Bytes of a code-block's pass-byte region: each pass is first coded into
 // a slot of floor(S / 7) + 3 bytes (S its renormalisation shifts; a pass of
 // L bytes has S <= 8 L + 12), and the slots of a block whose passes fit

@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
                 else n += t1_cup(s, y0, ex0, ex1, lane, zc, out, room, ovf);
             }
             if (lane == 0) nsym[k] = n;
-            pos += n;
+            pos = (pos + n + 15) & ~15;  // the next pass starts 16-byte aligned
         }
     }
     if (lane == 0) {
@@ -715,17 +715,49 @@ __device__ __forceinline__ int cb_frame(const CsJob *job, int g)
     return f;
 }
 
-// MQ coding, first stage: one thread per code-block (taken dynamically)
-// runs the interval register and the context states over all of the
-// block's decisions (Annex C: the state of a context moves on only at a
-// renormalisation, which depends on the interval alone, not on the code
-// register), recording each pass's starting context states and the slot
-// its codeword is given: floor(S / 7) + 3 bytes for S renormalisation
-// shifts (the first byte leaves after 12 shifts, each later one after 7 or
-// 8, and the termination adds two).  Branch-free per decision: both next
-// states are looked up before the renormalisation is known, and the next
-// decision's context word is loaded ahead (and forwarded when it is the
-// same context).
+// One decision d of the MQ coder's interval register a and context states
+// (Annex C), without the code register: a context's state moves on only
+// at a renormalisation, and that depends on the interval alone.  w: the
+// context word of d (the state's table row | MPS << 31), returned as that
+// of the next decision d2 (loaded ahead; forwarded when it is the same
+// context); S counts the renormalisation shifts.  Branch-free: both next
+// states are looked up before the renormalisation is known.
+__device__ __forceinline__ void mq_state_step(uint32_t d, uint32_t d2, uint32_t (*cx)[kMqThreads], int t,
+                                              const uint32_t *tab, uint32_t &w, uint32_t &a, int &S)
+{
+    const uint32_t c1 = (d >> 1) & 31u, c2 = (d2 >> 1) & 31u;
+    const uint32_t w2 = cx[c2][t];  // stale when c2 == c1: forwarded below
+    const uint32_t qe = w & 0xFFFFu, mps = w >> 31;
+    const uint32_t tm = tab[(w >> 16) & 63u], tl = tab[(w >> 22) & 63u];
+    const uint32_t a1 = a - qe;
+    const bool is_mps = (d & 1u) == mps;
+    const bool xchg = a1 < qe;
+    const uint32_t a2 = is_mps != xchg ? a1 : qe;  // a1 when the MPS leaves a >= 0x8000
+    const int sh = __clz(a2) - 16;                 // 0 exactly then
+    a = a2 << sh;
+    S += sh;
+    const uint32_t wr = is_mps ? (tm | (mps << 31)) : (tl | ((mps ^ ((w >> 28) & 1u)) << 31));
+    const uint32_t wn = sh > 0 ? wr : w;
+    cx[c1][t] = wn;
+    w = c2 == c1 ? wn : w2;
+}
+
+__device__ __forceinline__ uint32_t piece_byte(const uint4 &v, int q)
+{
+    const uint32_t x = q < 4 ? v.x : (q < 8 ? v.y : (q < 12 ? v.z : v.w));
+    return (x >> ((q & 3) * 8)) & 0xFFu;
+}
+
+// MQ coding, first stage: the interval register and context states over a
+// code-block's decisions, recording each pass's starting context states
+// and the slot its codeword is given: floor(S / 7) + 3 bytes for S
+// renormalisation shifts (the first byte leaves after 12 shifts, each
+// later one after 7 or 8, and the termination adds two).  The refinement
+// passes use contexts 14-16 only and the other passes never do, and every
+// pass starts a fresh interval, so a block is two independent chains: one
+// thread takes the refinement passes, another the significance and
+// cleanup passes.  Decisions are read 16 at a time (each pass's start is
+// 16-byte aligned) with the next 16 loaded ahead.
 __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ job)
 {
     __shared__ uint32_t s_cx[32][kMqThreads];  // the contexts of each thread's code-block
@@ -734,8 +766,10 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ 
     for (int i = t; i < 64; i += blockDim.x) s_tab[i] = i < 47 ? kMq.w[i] : 0u;
     __syncthreads();
     for (;;) {
-        const int g = atomicAdd(job->next + 1, 1);
-        if (g >= job->ncb) break;
+        const int u = atomicAdd(job->next + 1, 1);
+        if (u >= 2 * job->ncb) break;
+        const int g = u >> 1;
+        const bool mrp = (u & 1) != 0;  // this thread's chain: the refinement passes
         const CsFrame &F = job->frames[cb_frame(job, g)];
         const int jb = g - F.cb0;
         int32_t *info = F.info + (size_t)jb * kCbInfo;
@@ -744,62 +778,71 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ 
         const int32_t *nsym = F.nsym + (size_t)jb * kMaxPasses;
         int4 *ptab = F.ptab + (size_t)jb * kMaxPasses;
         uint32_t *mqs = F.mqs + (size_t)jb * kMaxPasses * kMqWords;
-        int total = 0;
-        bool over = false;
+        const uint8_t *sym = F.sym + (size_t)jb * kSymCap;
+        mq_init_contexts(s_cx, t, s_tab);
+        int pos = 0;
         for (int k = 0; k < np; k++) {
             const int n = nsym[k];
-            if (n < 0 || n > kSymCap - total) over = true;  // never: the model bounds its decisions
-            else total += n;
-        }
-        int off = 0;
-        if (!over) {
-            mq_init_contexts(s_cx, t, s_tab);
-            for (int c = 0; c < kNctx; c++) mqs[c] = s_cx[c][t];
-            DecReader rd;
-            rd.start(F.sym + (size_t)jb * kSymCap, 0);
-            // one loop over all of the block's decisions (the pass
-            // boundaries inside it), so that the threads of a warp do not
-            // wait for each other at every pass
-            int k = 0, i = 0, start = 0, end = nsym[0], S = 0;
-            uint32_t a = 0x8000;
-            uint32_t d = total > 0 ? rd.next() : 0u;
-            uint32_t w = s_cx[(d >> 1) & 31u][t];
-            for (;;) {
-                if (i == end) {
-                    ptab[k] = make_int4(start, off, S / 7 + 3, 0);
-                    off += S / 7 + 3;
-                    if (++k == np) break;
-                    for (int c = 0; c < kNctx; c++) mqs[k * kMqWords + c] = s_cx[c][t];
-                    start = i;
-                    end = i + nsym[k];
-                    a = 0x8000;
-                    S = 0;
-                    continue;
-                }
-                const uint32_t cx = (d >> 1) & 31u;
-                const uint32_t d2 = i + 1 < total ? rd.next() : 0u;
-                const uint32_t cx2 = (d2 >> 1) & 31u;
-                const uint32_t w2 = s_cx[cx2][t];  // stale when cx2 == cx: forwarded below
-                const uint32_t qe = w & 0xFFFFu, mps = w >> 31;
-                const uint32_t tm = s_tab[(w >> 16) & 63u], tl = s_tab[(w >> 22) & 63u];
-                const uint32_t a1 = a - qe;
-                const bool is_mps = (d & 1u) == mps;
-                const bool keep = is_mps && (a1 & 0x8000u);
-                const bool xchg = a1 < qe;
-                const uint32_t a2 = is_mps != xchg ? a1 : qe;  // a1 whenever keep
-                const int sh = __clz(a2) - 16;                 // 0 whenever keep
-                a = a2 << sh;
-                S += sh;
-                const uint32_t wn =
-                    keep ? w : (is_mps ? (tm | (mps << 31)) : (tl | ((mps ^ ((w >> 28) & 1u)) << 31)));
-                s_cx[cx][t] = wn;
-                w = cx2 == cx ? wn : w2;
-                d = d2;
-                i++;
+            if (n < 0 || n > kSymCap - pos) {  // never: the model bounds its decisions
+                info[3] = 1;
+                break;
             }
+            const int s0 = pos;
+            pos = (pos + n + 15) & ~15;
+            if ((k % 3 == 2) != mrp) continue;  // the other chain's pass
+            for (int c = 0; c < kNctx; c++) mqs[k * kMqWords + c] = s_cx[c][t];
+            uint32_t a = 0x8000;
+            int S = 0;
+            if (n > 0) {
+                const uint4 *pp = reinterpret_cast<const uint4 *>(sym + s0);
+                const int npc = (n + 15) >> 4;
+                uint4 cur = __ldg(pp);
+                uint32_t w = s_cx[(cur.x >> 1) & 31u][t];
+                for (int b = 0; b < npc; b++) {
+                    const uint4 nx = b + 1 < npc ? __ldg(pp + b + 1) : make_uint4(0u, 0u, 0u, 0u);
+                    const int rem = n - 16 * b;
+                    if (rem > 16) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++)
+                            mq_state_step(piece_byte(cur, q), q < 15 ? piece_byte(cur, q + 1) : (nx.x & 0xFFu), s_cx,
+                                          t, s_tab, w, a, S);
+                    } else {
+                        for (int q = 0; q < rem; q++)
+                            mq_state_step(piece_byte(cur, q), q + 1 < rem ? piece_byte(cur, q + 1) : 0u, s_cx, t, s_tab,
+                                          w, a, S);
+                    }
+                    cur = nx;
+                }
+            }
+            ptab[k] = make_int4(s0, 0, S / 7 + 3, 0);
         }
-        if (over || off > kCbRegion) {
-            // the passes need more than kCbBytes (see kCbRegion)
+    }
+}
+
+// Slot offsets of each code-block's pass codewords (one warp per block):
+// the passes' slots back to back; a block whose slots exceed kCbRegion
+// needs more than kCbBytes (see kCbRegion) and gets info 3 = 1.
+__global__ void __launch_bounds__(256) k_t1_slots(const CsJob *__restrict__ job)
+{
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = w0; g < job->ncb; g += nw) {
+        const CsFrame &F = job->frames[cb_frame(job, g)];
+        const int jb = g - F.cb0;
+        int32_t *info = F.info + (size_t)jb * kCbInfo;
+        const int np = info[1];
+        if (info[3] != 0 || np <= 0) continue;
+        int4 *ptab = F.ptab + (size_t)jb * kMaxPasses;
+        int base = 0;
+        for (int k0 = 0; k0 < np; k0 += 32) {
+            const int k = k0 + lane;
+            const int z = k < np ? ptab[k].z : 0;
+            int total;
+            const int at = warp_excl(z, lane, total);
+            if (k < np) ptab[k].y = base + at;
+            base += total;
+        }
+        if (base > kCbRegion && lane == 0) {
             info[3] = 1;
             if (job->err) atomicExch(job->err, kErrCbRange);
         }
@@ -830,6 +873,10 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mqc(const CsJob *__restrict__
         if (info[3] != 0 || k >= info[1]) continue;
         const int4 pt = F.ptab[(size_t)jb * kMaxPasses + k];
         const int n = F.nsym[(size_t)jb * kMaxPasses + k];
+        if (pt.x < 0 || n < 0 || n > kSymCap - pt.x || pt.y < 0 || pt.z < 0 || pt.z > kCbRegion - pt.y) {
+            info[3] = 1;  // never: the first stage and the slot offsets bound these
+            continue;
+        }
         const uint32_t *mqs = F.mqs + ((size_t)jb * kMaxPasses + k) * kMqWords;
         for (int c = 0; c < kNctx; c++) s_cx[c][t] = mqs[c];
         DecReader rd;
@@ -1445,7 +1492,8 @@ void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
 {
     const long long items = (long long)ncb * kMaxPasses;
     k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, 0, s>>>(job_dev);
-    k_t1_mq<<<std::max(1, (ncb + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
+    k_t1_mq<<<std::max(1, (2 * ncb + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
+    k_t1_slots<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
     k_t1_mqc<<<(int)std::min<long long>(4096, (items + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
     k_t1_pack<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
     k_pcrd<<<std::max(1, nframes), 1024, 0, s>>>(job_dev);
@@ -1457,6 +1505,7 @@ void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int
 {
     k_t1<<<grid_t1, 32 * kT1Warps, 0, s>>>(job_dev);
     k_t1_mq<<<grid_mq, kMqThreads, 0, s>>>(job_dev);
+    k_t1_slots<<<grid_copy, 256, 0, s>>>(job_dev);
     k_t1_mqc<<<4 * grid_mq, kMqThreads, 0, s>>>(job_dev);
     k_t1_pack<<<grid_copy, 256, 0, s>>>(job_dev);
     k_pcrd<<<kMaxBatch, 1024, 0, s>>>(job_dev);
