@@ -243,13 +243,33 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def rank_streams(route, n_streams: int, ws: int, rank: int) -> list:
+    """The stream ids this rank serves: the first n_streams ids (0, 1, 2,
+    ...) that route(sid, ws) sends to this rank (the library's stream ->
+    device routing), so every rank has n_streams streams and no stream is on
+    two ranks."""
+    out, sid = [], 0
+    while len(out) < n_streams:
+        if sid > 1000 * n_streams * ws:
+            raise RuntimeError("stream routing sends too few streams to rank %d" % rank)
+        if route(sid, ws) == rank:
+            out.append(sid)
+        sid += 1
+    return out
+
+
+def sid_of(wl, s: int) -> int:
+    """Stream id of the workload's s-th stream on this rank."""
+    return wl["sids"][s] if "sids" in wl else s
+
+
 def make_frames(wl, device):
     import torch
 
     from synth import sequence_u16
     frames = []
     for s in range(wl["streams"]):
-        frames.append(sequence_u16(wl["seed_base"] + s, wl["frames"], wl["h"], wl["w"], wl["blobs"],
+        frames.append(sequence_u16(wl["seed_base"] + sid_of(wl, s), wl["frames"], wl["h"], wl["w"], wl["blobs"],
                                    device=device))
     torch.cuda.synchronize()
     return frames
@@ -318,7 +338,7 @@ def run_device(F, wl, frames, steps, warmup, plain=False, profile_steps=0, sampl
         def one_step():
             nonlocal t
             i = frame_index(t, n)
-            submit_all(F, ctx.h, [(s, frames[s][i], t, bd) for s in range(S)])
+            submit_all(F, ctx.h, [(sid_of(wl, s), frames[s][i], t, bd) for s in range(S)])
             if plain:
                 while F.flowroi_step(ctx.h) > 0:
                     pass
@@ -385,14 +405,14 @@ def run_e2e(F, wl, frames, steps, warmup):
         def submit_step():
             nonlocal t
             i = frame_index(t, nh)
-            submit_all(F, ctx.h, [(s, host[s][i], t, bd) for s in range(S)])
+            submit_all(F, ctx.h, [(sid_of(wl, s), host[s][i], t, bd) for s in range(S)])
             F.flowroi_step(ctx.h)
             t += 1
 
         def fetch(step):
             for s in range(S):
-                F.flowroi_get_mask(ctx.h, s, step, masks[s], -1)
-                F.flowroi_get_coeffs(ctx.h, s, step, coefs[s], -1)
+                F.flowroi_get_mask(ctx.h, sid_of(wl, s), step, masks[s], -1)
+                F.flowroi_get_coeffs(ctx.h, sid_of(wl, s), step, coefs[s], -1)
 
         submit_step()
         fetch(0)
@@ -445,10 +465,10 @@ def run_codestream(F, wl, frames, steps, warmup, profile_steps=3):
         def one_step(keep):
             nonlocal t
             i = frame_index(t, n)
-            submit_all(F, ctx.h, [(s, frames[s][i], t, bd) for s in range(S)])
+            submit_all(F, ctx.h, [(sid_of(wl, s), frames[s][i], t, bd) for s in range(S)])
             F.flowroi_step(ctx.h)
             for s in range(S):
-                k = F.flowroi_get_codestream(ctx.h, s, t, outs[s], -1)
+                k = F.flowroi_get_codestream(ctx.h, sid_of(wl, s), t, outs[s], -1)
                 if keep:
                     lens.append(k)
             t += 1
@@ -780,6 +800,8 @@ def main():
     torch.cuda.set_device(local)
     if ws > 1:
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    # this rank's streams: stream -> device routing (one device per rank)
+    wl = dict(wl, sids=rank_streams(F.flowroi_route, wl["streams"], ws, rank))
     if "sizes" in wl:
         # serving measurement: its own JSON line (rank 0), not the throughput line
         res = run_serving(F, wl, args.serving_rate, args.serving_seconds, args.burst)

@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define FLOWROI_ABI_VERSION 4
+#define FLOWROI_ABI_VERSION 5
 
 /* Exported symbols (the library is built with hidden default visibility). */
 #if defined(__GNUC__)
@@ -521,6 +521,17 @@ FLOWROI_API int flowroi_set_tiles(flowroi_ctx *ctx, const char *json);
 FLOWROI_API int flowroi_get_tiles(flowroi_ctx *ctx, char *out, uint64_t cap, uint64_t *out_len);
 FLOWROI_API int flowroi_autotune(const flowroi_config *cfg, int nsizes, const int *widths, const int *heights,
                                  int streams, int steps, char *out, uint64_t out_cap, uint64_t *out_len);
+
+/* Stream -> device routing for several devices, one context each (streams
+ * are independent: a stream's state is its own previous frame, so the path
+ * shards by stream with no exchange between devices).  Returns the device
+ * index in [0, n_devices) of stream_id: Lamping and Veach's jump consistent
+ * hash ("A Fast, Minimal Memory, Consistent Hash Algorithm", 2014) of the
+ * id after the splitmix64 finaliser.  The same id always maps to the same
+ * device; going from n to n + 1 devices moves a stream only to the new
+ * device, and about 1/(n + 1) of them.  Host only, no device call, thread
+ * safe.  n_devices == 0: returns UINT32_MAX. */
+FLOWROI_API uint32_t flowroi_route(int64_t stream_id, uint32_t n_devices);
 
 /* Library ABI version (FLOWROI_ABI_VERSION). */
 FLOWROI_API int flowroi_abi_version(void);

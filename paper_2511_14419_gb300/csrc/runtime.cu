@@ -1146,6 +1146,24 @@ extern "C" {
 
 int flowroi_abi_version(void) { return FLOWROI_ABI_VERSION; }
 
+uint32_t flowroi_route(int64_t stream_id, uint32_t n_devices)
+{
+    if (n_devices == 0) return UINT32_MAX;
+    // splitmix64 finaliser: consecutive ids become unrelated keys
+    uint64_t key = (uint64_t)stream_id + 0x9E3779B97F4A7C15ull;
+    key = (key ^ (key >> 30)) * 0xBF58476D1CE4E5B9ull;
+    key = (key ^ (key >> 27)) * 0x94D049BB133111EBull;
+    key ^= key >> 31;
+    // jump consistent hash: the last bucket the key jumps to below n_devices
+    int64_t b = -1, j = 0;
+    while (j < (int64_t)n_devices) {
+        b = j;
+        key = key * 2862933555777941757ull + 1;
+        j = (int64_t)((double)(b + 1) * ((double)(1ll << 31) / (double)((key >> 33) + 1)));
+    }
+    return (uint32_t)b;
+}
+
 void flowroi_default_config(flowroi_config *cfg)
 {
     if (!cfg) return;

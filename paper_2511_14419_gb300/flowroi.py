@@ -30,7 +30,7 @@ EXPORTS = [
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
     "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc", "flowroi_reset_stats",
     "flowroi_encode_codestreams", "flowroi_codestream_bound", "flowroi_get_codestream",
-    "flowroi_tiles_check", "flowroi_set_tiles", "flowroi_get_tiles", "flowroi_autotune",
+    "flowroi_tiles_check", "flowroi_set_tiles", "flowroi_get_tiles", "flowroi_autotune", "flowroi_route",
 ]
 
 
@@ -122,6 +122,7 @@ def lib() -> ctypes.CDLL:
             "flowroi_reset_stats": (I, [P]),
             "flowroi_encode_codestreams": (I, [P, I, ctypes.POINTER(flowroi_cs_job), I]),
             "flowroi_codestream_bound": (ctypes.c_uint64, [I, I, I]),
+            "flowroi_route": (ctypes.c_uint32, [I64, ctypes.c_uint32]),
             "flowroi_get_codestream": (I, [P, I64, I64, P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), I, I]),
             "flowroi_tiles_check": (I, [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_uint64]),
             "flowroi_set_tiles": (I, [P, ctypes.c_char_p]),
@@ -352,6 +353,59 @@ def flowroi_get_codestream(ctx, stream_id: int, frame_idx: int, out, timeout_ms:
 
 def flowroi_codestream_bound(width: int, height: int, levels: int) -> int:
     return int(lib().flowroi_codestream_bound(width, height, levels))
+
+
+def flowroi_route(stream_id: int, n_devices: int) -> int:
+    """Device index of a stream among n_devices (see the C header)."""
+    if n_devices < 1:
+        raise ValueError("n_devices must be >= 1")
+    return int(lib().flowroi_route(int(stream_id), int(n_devices)))
+
+
+class Router:
+    """One context per device, streams routed by flowroi_route: submit and
+    fetch calls take a stream id and go to that stream's context.  Only
+    dispatch lives here; every call is the C ABI's.  make_context(device)
+    builds a device's context (default: Context(device=device, **cfg))."""
+
+    def __init__(self, n_devices: int, make_context=None, **cfg):
+        if n_devices < 1:
+            raise ValueError("n_devices must be >= 1")
+        self.n = n_devices
+        self._make = make_context or (lambda d: Context(device=d, **cfg))
+        self._ctx = {}
+
+    def device_of(self, stream_id: int) -> int:
+        return flowroi_route(stream_id, self.n)
+
+    def context(self, stream_id: int):
+        d = self.device_of(stream_id)
+        if d not in self._ctx:
+            self._ctx[d] = self._make(d)
+        return self._ctx[d]
+
+    def submit_frame(self, stream_id: int, frame, frame_idx: int, bit_depth: int) -> int:
+        c = self.context(stream_id)
+        return flowroi_submit_frame(c.h, stream_id, frame, frame_idx, bit_depth)
+
+    def get_mask(self, stream_id: int, frame_idx: int, out, timeout_ms: int = 60000) -> int:
+        c = self.context(stream_id)
+        return flowroi_get_mask(c.h, stream_id, frame_idx, out, timeout_ms)
+
+    def flush(self, timeout_ms: int = 60000) -> None:
+        for c in self._ctx.values():
+            flowroi_flush(c.h, timeout_ms)
+
+    def close(self) -> None:
+        for c in self._ctx.values():
+            c.close()
+        self._ctx = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def flowroi_encode_codestreams(ctx, jobs) -> list:

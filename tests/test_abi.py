@@ -44,7 +44,7 @@ def test_struct_sizes_match_binding(F):
     cfg = F.flowroi_default_config()
     assert cfg.struct_size == ctypes.sizeof(F.flowroi_config)
     assert (cfg.roi_q, cfg.scale_shift, cfg.win_r, cfg.iters) == (np.float32(0.2), 5, 7, 3)
-    assert F.flowroi_abi_version() == 4
+    assert F.flowroi_abi_version() == 5
     assert ctypes.sizeof(F.flowroi_cs_job) == 72
 
 

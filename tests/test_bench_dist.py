@@ -82,3 +82,41 @@ def test_all_cores_oracle_sample_reports_a_failing_process():
     with pytest.raises(RuntimeError, match="KeyError"):
         bench.cpu_sample_parallel(wl, fc, procs=2, budget_s=0.1, crop=32, per_proc=1)
     assert time.monotonic() - t0 < 60
+
+
+def _route_worker(rank, ws, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    import bench
+    from paper_2511_14419_gb300 import flowroi as F
+    mine = bench.rank_streams(F.flowroi_route, 16, ws, rank)
+    every = [None] * ws
+    dist.all_gather_object(every, mine)
+    q.put((rank, mine, every))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_ranks_take_disjoint_routed_stream_sets_gloo():
+    """Each rank of a 2-rank job serves the 16 streams the library routes to
+    it; the ranks agree on the split and no stream is served twice."""
+    ws = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_route_worker, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(ws)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    from paper_2511_14419_gb300 import flowroi as F
+    views = {rank: every for rank, _, every in out}
+    assert views[0] == views[1]
+    sets = views[0]
+    assert all(len(s) == 16 for s in sets)
+    assert not set(sets[0]) & set(sets[1])
+    for r, ids in enumerate(sets):
+        assert all(F.flowroi_route(i, ws) == r for i in ids)
