@@ -125,18 +125,23 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kT1Warps = 8;     // code-blocks (one a warp) per CTA of the modelling kernel
 constexpr int kMqThreads = 64;  // code-blocks (one a thread) per CTA of the MQ kernel
 
-// Doubled-unit reconstruction once planes >= p are known (0 while m >> p == 0).
-__device__ __forceinline__ long long recon2(uint32_t m, int p)
+// Doubled-unit reconstruction once planes >= p are known (0 while m >> p
+// == 0); below 2^26 for magnitudes below 2^24.
+__device__ __forceinline__ int recon2(uint32_t m, int p)
 {
-    if ((m >> p) == 0) return 0;
-    return 2ll * (long long)((m >> p) << p) + (p > 0 ? (1ll << p) : 0ll);
+    const uint32_t hi = m >> p;
+    return hi == 0 ? 0 : (int)(2u * (hi << p) + (p > 0 ? (1u << p) : 0u));
 }
+// Decrease of the squared doubled-unit error when the reconstruction moves
+// from planes >= pb (pb > 31: nothing known yet) to planes >= pa; both
+// errors are below 2^26 in magnitude, so each square is one widening
+// product and the difference is exact.
 __device__ __forceinline__ long long derr(uint32_t m, int pb, int pa)
 {
-    const long long t = 2ll * (long long)m;
-    const long long eb = t - (pb > 31 ? 0ll : recon2(m, pb));
-    const long long ea = t - recon2(m, pa);
-    return eb * eb - ea * ea;
+    const int t = 2 * (int)m;
+    const int eb = t - (pb > 31 ? 0 : recon2(m, pb));
+    const int ea = t - recon2(m, pa);
+    return (long long)eb * eb - (long long)ea * ea;
 }
 
 // MQ encoder of one thread (Annex C, software conventions; the byte at BP
@@ -289,19 +294,6 @@ __device__ __forceinline__ uint32_t any_nb(uint32_t B, int j)
     return (((D >> (8 * (j - 1))) | (D >> (8 * (j + 1))) | (c << 1) | (c >> 1)) >> 1) & 0xFu;
 }
 
-// Zero-coding index (h | v << 2 | d << 4: significant horizontal, vertical
-// and diagonal neighbours) of the sample at window row R of own column j,
-// when the samples before it in scan order (the column to the left, the
-// rows above) are seen in A and the ones after it in B.
-__device__ __forceinline__ uint32_t nb_index(uint32_t A, uint32_t B, int j, int R)
-{
-    const int l = 8 * (j - 1) + R, m = 8 * j + R, r = 8 * (j + 1) + R;
-    const uint32_t h = ((A >> l) & 1u) + ((B >> r) & 1u);
-    const uint32_t v = ((A >> (m - 1)) & 1u) + ((B >> (m + 1)) & 1u);
-    const uint32_t d = ((A >> (l - 1)) & 1u) + ((A >> (l + 1)) & 1u) + ((B >> (r - 1)) & 1u) + ((B >> (r + 1)) & 1u);
-    return h | (v << 2) | (d << 4);
-}
-
 // Sign-coding decision ((context << 1) | bit) of the sample at window row R
 // of own column j whose sign is neg; N: the sign window.
 __device__ __forceinline__ uint32_t sign_symbol(uint32_t A, uint32_t B, uint32_t N, int j, int R, uint32_t neg)
@@ -345,6 +337,23 @@ __device__ __forceinline__ int col_count(uint32_t c, uint32_t n, bool rl)
     const uint32_t below = (0xEu << (__ffs(n) - 1)) & 0xFu;
     return 4 + __popc(c & below) + __popc(n & below);
 }
+// Zero-coding indices (h | v << 2 | d << 4: significant horizontal,
+// vertical and diagonal neighbours) of the four stripe rows of own column j
+// at once, one byte per row, when the samples before a sample in scan order
+// (the column to the left, the rows above) are seen in A and the ones after
+// it in B: each neighbour's row bits are spread to the rows' bytes by a
+// multiply (bit i to bit 8i; no two terms meet), then counted bytewise (at
+// most 2 + 8 + 64, so no carries).
+__device__ __forceinline__ uint32_t spread4(uint32_t x) { return (x * 0x00204081u) & 0x01010101u; }
+__device__ __forceinline__ uint32_t zc_word(uint32_t A, uint32_t B, int j)
+{
+    const uint32_t L = (A >> (8 * (j - 1))) & 0x3Fu, Ca = (A >> (8 * j)) & 0x3Fu, Cb = (B >> (8 * j)) & 0x3Fu,
+                   R = (B >> (8 * (j + 1))) & 0x3Fu;
+    const uint32_t h = spread4((L >> 1) & 0xFu) + spread4((R >> 1) & 0xFu);
+    const uint32_t v = spread4(Ca & 0xFu) + spread4((Cb >> 2) & 0xFu);
+    const uint32_t d = spread4(L & 0xFu) + spread4((L >> 2) & 0xFu) + spread4(R & 0xFu) + spread4((R >> 2) & 0xFu);
+    return h + 4u * v + 16u * d;
+}
 __device__ __forceinline__ void col_emit(uint8_t *&o, const StripeCtx &S, int j, uint32_t c, uint32_t n, bool rl,
                                          uint64_t ng)
 {
@@ -358,10 +367,12 @@ __device__ __forceinline__ void col_emit(uint8_t *&o, const StripeCtx &S, int j,
         *o++ = (uint8_t)sign_symbol(S.A, S.B, S.N, j, r + 1, (uint32_t)(ng >> (S.y0 + r)) & 1u);
         rest = c & (0xEu << r) & 0xFu;
     }
+    if (!rest) return;
+    const uint32_t zw = zc_word(S.A, S.B, j);
     for (uint32_t m = rest; m; m &= m - 1) {
         const int r = __ffs(m) - 1;
         const uint32_t nb = (n >> r) & 1u;
-        *o++ = (uint8_t)((S.zc[nb_index(S.A, S.B, j, r + 1)] << 1) | nb);
+        *o++ = (uint8_t)((S.zc[(zw >> (8 * r)) & 0x7Fu] << 1) | nb);
         if (nb) *o++ = (uint8_t)sign_symbol(S.A, S.B, S.N, j, r + 1, (uint32_t)(ng >> (S.y0 + r)) & 1u);
     }
 }
@@ -619,17 +630,36 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
             before[c] = s.sig[c] & ~(s.nsp[c] | s.ncu[c]);
             s.bm[c] = 0;
         }
-        for (int y = 0; y < ch; y++) {
-            const int32_t v0 = has0 ? __ldg(col + (size_t)y * F.w) : 0, v1 = has1 ? __ldg(col + (size_t)y * F.w + 1) : 0;
+        // rows in two halves of 32, so that the row bits are 32-bit shifts
+        for (int ya = 0; ya < ch; ya += 32) {
+            const int yb = min(ch, ya + 32);
+            uint32_t e1[2], e2[2], e3[2], bw[2] = {0u, 0u};
 #pragma unroll
             for (int c = 0; c < 2; c++) {
-                const int32_t v = c ? v1 : v0;
-                const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
-                if (p >= 0) s.bm[c] |= (uint64_t)((m >> p) & 1u) << y;
-                if ((s.nsp[c] >> y) & 1u) dsp += derr(m, 32, q);
-                else if ((before[c] >> y) & 1u) dmr += derr(m, q + 1, q);
-                else if ((s.ncu[c] >> y) & 1u) dcu += derr(m, 32, q);
+                e1[c] = (uint32_t)(s.nsp[c] >> ya);
+                e2[c] = (uint32_t)(before[c] >> ya);
+                e3[c] = (uint32_t)(s.ncu[c] >> ya);
             }
+            for (int y = ya; y < yb; y++) {
+                const int b = y - ya;
+                const int32_t v0 = has0 ? __ldg(col + (size_t)y * F.w) : 0,
+                              v1 = has1 ? __ldg(col + (size_t)y * F.w + 1) : 0;
+#pragma unroll
+                for (int c = 0; c < 2; c++) {
+                    const int32_t v = c ? v1 : v0;
+                    const uint32_t m = v < 0 ? (uint32_t)(-(long long)v) : (uint32_t)v;
+                    if (p >= 0) bw[c] |= ((m >> p) & 1u) << b;
+                    const uint32_t a1 = (e1[c] >> b) & 1u, a2 = (e2[c] >> b) & 1u, a3 = (e3[c] >> b) & 1u;
+                    if (a1 | a2 | a3) {  // this plane's passes coded the sample: one event each
+                        const long long d = derr(m, a2 ? q + 1 : 32, q);
+                        if (a1) dsp += d;
+                        else if (a2) dmr += d;
+                        else dcu += d;
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 2; c++) s.bm[c] |= (uint64_t)bw[c] << ya;
         }
         dsp = warp_sum_ll(dsp);
         dmr = warp_sum_ll(dmr);
@@ -860,17 +890,23 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mqc(const CsJob *__restrict__
     const int t = threadIdx.x;
     for (int i = t; i < 64; i += blockDim.x) s_tab[i] = i < 47 ? kMq.w[i] : 0u;
     __syncthreads();
-    const int items = job->ncb * kMaxPasses;
+    const int items = job->ncb * 3 * kMaxPlanes;
     for (;;) {
         const int u = atomicAdd(job->next + 2, 1);
         if (u >= items) break;
-        // pass-major: a warp's threads take the same pass of neighbouring
-        // code-blocks, of similar lengths
-        const int k = u / job->ncb, g = u - k * job->ncb;
+        // items ordered by (bit-plane counted from 0, pass type), then
+        // code-block: a warp's threads take the same kind of pass on the
+        // same plane of neighbouring code-blocks, of similar lengths
+        const int kk = u / job->ncb, g = u - kk * job->ncb;
+        const int pl = kk / 3, type = kk - 3 * pl;  // type 0 significance, 1 refinement, 2 cleanup
         const CsFrame &F = job->frames[cb_frame(job, g)];
         const int jb = g - F.cb0;
         int32_t *info = F.info + (size_t)jb * kCbInfo;
-        if (info[3] != 0 || k >= info[1]) continue;
+        const int planes = info[0];
+        if (info[3] != 0 || info[1] <= 0 || pl >= planes || (pl == planes - 1 && type != 2)) continue;
+        // pass index: the top plane has its cleanup pass only
+        const int k = pl == planes - 1 ? 0 : 1 + 3 * (planes - 2 - pl) + type;
+        if (k >= info[1]) continue;
         const int4 pt = F.ptab[(size_t)jb * kMaxPasses + k];
         const int n = F.nsym[(size_t)jb * kMaxPasses + k];
         if (pt.x < 0 || n < 0 || n > kSymCap - pt.x || pt.y < 0 || pt.z < 0 || pt.z > kCbRegion - pt.y) {
@@ -1490,7 +1526,7 @@ int ebcot_codeblocks(int w, int h, int levels)
 
 void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
 {
-    const long long items = (long long)ncb * kMaxPasses;
+    const long long items = (long long)ncb * 3 * kMaxPlanes;
     k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, 0, s>>>(job_dev);
     k_t1_mq<<<std::max(1, (2 * ncb + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
     k_t1_slots<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
