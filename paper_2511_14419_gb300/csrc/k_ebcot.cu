@@ -772,6 +772,30 @@ __device__ __forceinline__ void mq_state_step(uint32_t d, uint32_t d2, uint32_t 
     w = c2 == c1 ? wn : w2;
 }
 
+// The same for the refinement passes' chain, whose three contexts (14-16)
+// stay in registers (w3), so that no context word goes through shared
+// memory.
+__device__ __forceinline__ void mq_state_step_mr(uint32_t d, uint32_t (&w3)[3], const uint32_t *tab, uint32_t &a,
+                                                 int &S)
+{
+    const uint32_t c = ((d >> 1) - 14u) & 3u;  // 0, 1, 2 (3 never occurs)
+    const uint32_t w = c == 0 ? w3[0] : (c == 1 ? w3[1] : w3[2]);
+    const uint32_t qe = w & 0xFFFFu, mps = w >> 31;
+    const uint32_t tm = tab[(w >> 16) & 63u], tl = tab[(w >> 22) & 63u];
+    const uint32_t a1 = a - qe;
+    const bool is_mps = (d & 1u) == mps;
+    const bool xchg = a1 < qe;
+    const uint32_t a2 = is_mps != xchg ? a1 : qe;
+    const int sh = __clz(a2) - 16;
+    a = a2 << sh;
+    S += sh;
+    const uint32_t wr = is_mps ? (tm | (mps << 31)) : (tl | ((mps ^ ((w >> 28) & 1u)) << 31));
+    const uint32_t wn = sh > 0 ? wr : w;
+    w3[0] = c == 0 ? wn : w3[0];
+    w3[1] = c == 1 ? wn : w3[1];
+    w3[2] = c == 2 ? wn : w3[2];
+}
+
 __device__ __forceinline__ uint32_t piece_byte(const uint4 &v, int q)
 {
     const uint32_t x = q < 4 ? v.x : (q < 8 ? v.y : (q < 12 ? v.z : v.w));
@@ -798,8 +822,10 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ 
     for (;;) {
         const int u = atomicAdd(job->next + 1, 1);
         if (u >= 2 * job->ncb) break;
-        const int g = u >> 1;
-        const bool mrp = (u & 1) != 0;  // this thread's chain: the refinement passes
+        // the refinement chains first, then the others, so that a warp's
+        // threads run one kind of chain
+        const bool mrp = u < job->ncb;  // this thread's chain: the refinement passes
+        const int g = mrp ? u : u - job->ncb;
         const CsFrame &F = job->frames[cb_frame(job, g)];
         const int jb = g - F.cb0;
         int32_t *info = F.info + (size_t)jb * kCbInfo;
@@ -823,7 +849,26 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ 
             for (int c = 0; c < kNctx; c++) mqs[k * kMqWords + c] = s_cx[c][t];
             uint32_t a = 0x8000;
             int S = 0;
-            if (n > 0) {
+            if (n > 0 && mrp) {
+                const uint4 *pp = reinterpret_cast<const uint4 *>(sym + s0);
+                const int npc = (n + 15) >> 4;
+                uint4 cur = __ldg(pp);
+                uint32_t w3[3] = {s_cx[14][t], s_cx[15][t], s_cx[16][t]};
+                for (int b = 0; b < npc; b++) {
+                    const uint4 nx = b + 1 < npc ? __ldg(pp + b + 1) : make_uint4(0u, 0u, 0u, 0u);
+                    const int rem = n - 16 * b;
+                    if (rem >= 16) {
+#pragma unroll
+                        for (int q = 0; q < 16; q++) mq_state_step_mr(piece_byte(cur, q), w3, s_tab, a, S);
+                    } else {
+                        for (int q = 0; q < rem; q++) mq_state_step_mr(piece_byte(cur, q), w3, s_tab, a, S);
+                    }
+                    cur = nx;
+                }
+                s_cx[14][t] = w3[0];
+                s_cx[15][t] = w3[1];
+                s_cx[16][t] = w3[2];
+            } else if (n > 0) {
                 const uint4 *pp = reinterpret_cast<const uint4 *>(sym + s0);
                 const int npc = (n + 15) >> 4;
                 uint4 cur = __ldg(pp);
