@@ -121,6 +121,31 @@ def test_decoded_container_reconstructs_the_frame(ctx):
     assert got == o.encode_frame(q, 3, 53, 0, 12, 0)[0]
 
 
+@pytest.mark.parametrize("kind", ["dense", "sparse"])
+def test_largest_magnitudes_24_planes_match_oracle(ctx, kind):
+    """Code-blocks at the largest magnitudes the coder accepts (below 2^24:
+    24 bit-planes, 70 passes).  Dense noise makes the most decisions per
+    block, so the decision streams and the codeword slots come nearest their
+    bounds; sparse spikes among zeros make long run-length stretches in
+    every plane.  Lossless and rate-controlled containers byte-identical to
+    the oracle's."""
+    rng = np.random.default_rng(2424 if kind == "dense" else 2425)
+    h = w = 128
+    top = (1 << 24) - 1
+    if kind == "dense":
+        q = rng.integers(-top, top + 1, size=(h, w)).astype(np.int32)
+    else:
+        q = np.zeros((h, w), np.int32)
+        idx = rng.choice(h * w, 300, replace=False)
+        q.flat[idx] = rng.integers(-top, top + 1, size=idx.size)
+    q[0, 0], q[-1, -1] = top, -top
+    assert np.abs(q.astype(np.int64)).max() == top
+    for budget in (0, h * w // 4):
+        want, _ = o.encode_frame(q, 2, 53, 5, 12, budget)
+        got = _gpu(ctx, [q], 2, 53, 5, [budget])[0]
+        assert got == want
+
+
 def test_too_small_output_and_out_of_range_magnitudes(ctx):
     q = _planes(5, 128, 128, 3, 53, 5)
     small = np.zeros(100, np.uint8)
