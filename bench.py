@@ -115,8 +115,9 @@ def other_bytes(name, storage, bpp):
 
 
 # DRAM bytes (read + write) per level-0 pixel of one launch, measured by ncu
-# on 4 frames (profiles/launch_traffic_small_4x2048.md; traffic proportional
-# to pixels; the update figure averages its three level-0 launches), each
+# (dram__bytes_read.sum + dram__bytes_write.sum) on 4 frames of the same
+# workload (traffic proportional to pixels; the update figure averages its
+# three level-0 launches), each
 # with the source file the kernel was built from and its SHA-256 prefix at
 # the time of the capture: a figure whose source has changed since is
 # reported as null.
