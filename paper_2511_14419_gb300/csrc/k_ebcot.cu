@@ -1272,16 +1272,18 @@ namespace {
 struct HdrBits {
     uint8_t *out;
     long long cap, pos;
-    uint32_t cur, last;
-    int n, room, nbytes;
+    uint64_t acc;  // bits not yet emitted (the low `nacc` bits, first bit highest)
+    uint32_t last;
+    int nacc, room, nbytes;
     bool over;
     __device__ __forceinline__ void init(uint8_t *o, long long c, long long p)
     {
         out = o;
         cap = c;
         pos = p;
-        cur = last = 0;
-        n = nbytes = 0;
+        acc = 0;
+        last = 0;
+        nacc = nbytes = 0;
         room = 8;
         over = false;
     }
@@ -1293,41 +1295,46 @@ struct HdrBits {
         nbytes++;
         last = b;
     }
-    __device__ __forceinline__ void put(int b)
-    {
-        cur = (cur << 1) | (uint32_t)(b & 1);
-        if (++n == room) {
-            emit(cur);
-            room = cur == 0xFF ? 7 : 8;
-            cur = 0;
-            n = 0;
-        }
-    }
+    // Appends the k (<= 32) low bits of v, first bit highest; every byte
+    // holds 8 bits, or 7 after a 0xFF byte (bit stuffing).
     __device__ __forceinline__ void put_bits(uint32_t v, int k)
     {
-        for (int i = k - 1; i >= 0; i--) put((int)((v >> i) & 1u));
+        acc = (acc << k) | (uint64_t)(k == 32 ? v : (v & ((1u << k) - 1u)));
+        nacc += k;
+        while (nacc >= room) {
+            const uint32_t b = (uint32_t)(acc >> (nacc - room)) & ((1u << room) - 1u);
+            nacc -= room;
+            emit(b);
+            room = b == 0xFF ? 7 : 8;
+        }
     }
+    __device__ __forceinline__ void put(int b) { put_bits((uint32_t)(b & 1), 1); }
     __device__ __forceinline__ void flush()
     {
-        if (n) {
-            emit(cur << (room - n));
-            n = 0;
+        if (nacc) {
+            emit((uint32_t)(acc & ((1u << nacc) - 1u)) << (room - nacc));
+            nacc = 0;
         }
         if (nbytes && last == 0xFF) emit(0);
     }
 };
 
-// A tag tree over nx x ny leaves in global scratch: per node its value
-// (the least leaf below it) and its state (low bound, bit 31: known).
+constexpr int kJ2cSmemInts = 12 * 1024;  // k_j2c's tag trees in shared memory: up to 3072 nodes a tree
+
+// A tag tree over nx x ny leaves (in shared memory, or global scratch for
+// large bands): per node its value (the least leaf below it) and its
+// state (low bound, bit 31: known).
 struct TagTree {
     int *val, *st;
-    int nlev, lw[20], off[20];
-    __device__ void build(int *mem, int nx, int ny)
+    int nlev, lw[20], lh[20], off[20];
+    // node layout of an nx x ny tree (every lane computes the same)
+    __device__ void layout(int *mem, int nx, int ny)
     {
         int w = nx, h = ny, o = 0;
         nlev = 0;
         for (;;) {
             lw[nlev] = w;
+            lh[nlev] = h;
             off[nlev] = o;
             o += w * h;
             nlev++;
@@ -1337,18 +1344,31 @@ struct TagTree {
         }
         val = mem;
         st = mem + o;
-        for (int i = 0; i < o; i++) {
-            val[i] = 0x3fffffff;
-            st[i] = 0;
-        }
     }
     __device__ int nodes() const { return off[nlev - 1] + 1; }
-    __device__ void set(int x, int y, int v)
+    // By the warp: leaf q (x = q % nx, y = q / nx) takes leaf(q), each node
+    // above the least of its children, every state cleared.
+    template <class Leaf>
+    __device__ void build(int lane, Leaf leaf)
     {
-        for (int l = 0; l < nlev; l++) {
-            int &t = val[off[l] + (y >> l) * lw[l] + (x >> l)];
-            if (v < t) t = v;
+        const int o = nodes();
+        for (int i = lane; i < o; i += 32) st[i] = 0;
+        for (int q = lane; q < lw[0] * lh[0]; q += 32) val[q] = leaf(q);
+        for (int l = 1; l < nlev; l++) {
+            __syncwarp();
+            const int w = lw[l], h = lh[l], pw = lw[l - 1], ph = lh[l - 1];
+            for (int q = lane; q < w * h; q += 32) {
+                const int x = q % w, y = q / w;
+                int v = 0x3fffffff;
+                for (int dy = 0; dy < 2; dy++)
+                    for (int dx = 0; dx < 2; dx++) {
+                        const int cx = 2 * x + dx, cy = 2 * y + dy;
+                        if (cx < pw && cy < ph) v = min(v, val[off[l - 1] + cy * pw + cx]);
+                    }
+                val[off[l] + q] = v;
+            }
         }
+        __syncwarp();
     }
     __device__ void encode(HdrBits &bw, int x, int y, int threshold)
     {
@@ -1374,7 +1394,34 @@ struct TagTree {
     }
 };
 
-__device__ __forceinline__ void passes_codeword(HdrBits &bw, int n)
+// A code-block's header bits after its tag-tree bits (pass count, Lblock
+// increment, segment lengths): independent of the other blocks, so formed
+// by the lanes in parallel into words (MSB first, no stuffing; lane 0
+// appends them through HdrBits, which stuffs).
+struct TailBits {
+    uint32_t *w;
+    uint32_t cur;
+    int n;
+    __device__ __forceinline__ void put(int b)
+    {
+        cur = (cur << 1) | (uint32_t)(b & 1);
+        if ((++n & 31) == 0) {
+            w[(n >> 5) - 1] = cur;
+            cur = 0;
+        }
+    }
+    __device__ __forceinline__ void put_bits(uint32_t v, int k)
+    {
+        for (int i = k - 1; i >= 0; i--) put((int)((v >> i) & 1u));
+    }
+    __device__ __forceinline__ void finish()
+    {
+        if (n & 31) w[n >> 5] = cur << (32 - (n & 31));
+    }
+};
+
+template <class Bits>
+__device__ __forceinline__ void passes_codeword(Bits &bw, int n)
 {
     if (n == 1) bw.put(0);
     else if (n == 2) bw.put_bits(2u, 2);
@@ -1466,11 +1513,33 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
             b16(0xFF93);                                      // SOD
         }
         pos = __shfl_sync(0xffffffffu, pos, 0);
+        // every included block's header bits after its tag-tree bits, by the
+        // lanes (into the block's hull-slope scratch, free once rate control
+        // is done): word 0 the bit count, then the bits
+        for (int j = lane; j < n; j += 32) {
+            const int32_t *in = F.info + (size_t)j * kCbInfo;
+            uint32_t *tw = reinterpret_cast<uint32_t *>(F.hs + (size_t)j * (kMaxPasses + 1));
+            const int nk = in[2];
+            TailBits tb{tw + 1, 0u, 0};
+            if (nk > 0) {
+                passes_codeword(tb, nk);
+                const int32_t *pl = F.plen + (size_t)j * kMaxPasses;
+                int nbits = 1;
+                for (int t = 0; t < nk; t++) nbits = max(nbits, bit_length((uint32_t)pl[t]));
+                const int inc = max(0, nbits - 3);  // Lblock starts at 3
+                for (int t = 0; t < inc; t++) tb.put(1);
+                tb.put(0);
+                for (int t = 0; t < nk; t++) tb.put_bits((uint32_t)pl[t], 3 + inc);
+                tb.finish();
+            }
+            tw[0] = (uint32_t)tb.n;
+        }
+        __syncwarp();
         // packets: resolution 0 holds the low-low band, resolution r the
         // HL, LH, HH bands of level D - r + 1; their code-blocks follow one
         // another in the frame's code-block order
+        extern __shared__ int j2c_smem[];
         int j0 = 0;
-        int *const tt_mem = F.hk;  // the hulls' scratch, free once rate control is done
         for (int r = 0; r <= D; r++) {
             const int nbands = r == 0 ? 1 : 3, l = r == 0 ? D : D - r + 1;
             const int bw = W >> l, bh = H >> l;
@@ -1479,59 +1548,75 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
             int any = 0;
             for (int j = j0 + lane; j < j1; j += 32) any |= F.info[(size_t)j * kCbInfo + 2] > 0;
             any = __any_sync(0xffffffffu, any);
+            HdrBits bits;
             if (lane == 0) {
-                HdrBits bits;
                 bits.init(out, cap, pos);
-                if (!any) {
-                    bits.put(0);
-                } else {
-                    bits.put(1);
-                    for (int k = 0; k < nbands; k++) {
-                        const int band = r == 0 ? 3 * D : 3 * (l - 1) + k;
-                        const int Mb = G + (int)F.eps[band] - 1;
-                        const int jb = j0 + k * per;
-                        TagTree incl, zbp;
-                        incl.build(tt_mem, nx, ny);
-                        zbp.build(tt_mem + 2 * incl.nodes(), nx, ny);
+                bits.put(any ? 1 : 0);
+            }
+            if (any) {
+                for (int k = 0; k < nbands; k++) {
+                    const int band = r == 0 ? 3 * D : 3 * (l - 1) + k;
+                    const int Mb = G + (int)F.eps[band] - 1;
+                    const int jb = j0 + k * per;
+                    // the band's two tag trees: in shared memory when they fit
+                    TagTree incl, zbp;
+                    incl.layout(j2c_smem, nx, ny);
+                    int *mem = 4 * incl.nodes() <= kJ2cSmemInts ? j2c_smem : F.hk;
+                    incl.layout(mem, nx, ny);
+                    zbp.layout(mem + 2 * incl.nodes(), nx, ny);
+                    incl.build(lane, [&](int q) { return F.info[(size_t)(jb + q) * kCbInfo + 2] > 0 ? 0 : 1; });
+                    zbp.build(lane, [&](int q) { return Mb - F.info[(size_t)(jb + q) * kCbInfo + 0]; });
+                    if (lane == 0) {
+                        auto tail = [&](int q) {
+                            return reinterpret_cast<const uint32_t *>(F.hs + (size_t)(jb + q) * (kMaxPasses + 1));
+                        };
+                        // the next block's tail count and first two words loaded ahead
+                        uint32_t nbq = tail(0)[0], w0 = tail(0)[1], w1 = tail(0)[2];
                         for (int q = 0; q < per; q++) {
-                            const int32_t *in = F.info + (size_t)(jb + q) * kCbInfo;
-                            incl.set(q % nx, q / nx, in[2] > 0 ? 0 : 1);
-                            zbp.set(q % nx, q / nx, Mb - in[0]);
-                        }
-                        for (int q = 0; q < per; q++) {
-                            const int j = jb + q;
-                            const int32_t *in = F.info + (size_t)j * kCbInfo;
+                            uint32_t nbn = 0, w0n = 0, w1n = 0;
+                            if (q + 1 < per) {
+                                const uint32_t *tn = tail(q + 1);
+                                nbn = tn[0];
+                                w0n = tn[1];
+                                w1n = tn[2];
+                            }
                             const int cx = q % nx, cy = q / nx;
                             incl.encode(bits, cx, cy, 1);
-                            const int nk = in[2];
-                            if (nk == 0) continue;
-                            zbp.encode(bits, cx, cy, 0x3fffffff);
-                            passes_codeword(bits, nk);
-                            const int32_t *pl = F.plen + (size_t)j * kMaxPasses;
-                            int nbits = 1;
-                            for (int t = 0; t < nk; t++) nbits = max(nbits, bit_length((uint32_t)pl[t]));
-                            const int inc = max(0, nbits - 3);  // Lblock starts at 3
-                            for (int t = 0; t < inc; t++) bits.put(1);
-                            bits.put(0);
-                            for (int t = 0; t < nk; t++) bits.put_bits((uint32_t)pl[t], 3 + inc);
+                            const int nb = (int)nbq;
+                            if (nb > 0) {  // included
+                                zbp.encode(bits, cx, cy, 0x3fffffff);
+                                const uint32_t *tw = tail(q);
+                                for (int i = 0; i < nb; i += 32) {
+                                    const int kk = min(32, nb - i);
+                                    const uint32_t word = i == 0 ? w0 : (i == 32 ? w1 : tw[1 + (i >> 5)]);
+                                    bits.put_bits(word >> (32 - kk), kk);
+                                }
+                            }
+                            nbq = nbn;
+                            w0 = w0n;
+                            w1 = w1n;
                         }
                     }
+                    __syncwarp();
                 }
+            }
+            if (lane == 0) {
                 bits.flush();
                 pos = bits.pos;
                 over = over || bits.over;
             }
             pos = __shfl_sync(0xffffffffu, pos, 0);
-            // bodies: the included blocks' kept pass bytes, in header order
-            for (int j = j0; j < j1; j++) {
-                const int32_t *in = F.info + (size_t)j * kCbInfo;
-                const int nk = in[2];
-                if (nk == 0) continue;
-                const int nbytes = in[5] - 2 * nk;
-                const uint8_t *src = F.cbytes + (size_t)j * kCbRegion;
-                for (int i = lane; i < nbytes; i += 32)
-                    if (pos + i < cap) out[pos + i] = src[i];
-                pos += nbytes;
+            // bodies: the included blocks' kept pass bytes, in header order;
+            // their offsets here, the copies by k_j2c_copy
+            for (int jc = j0; jc < j1; jc += 32) {
+                const int j = jc + lane;
+                int nbytes = 0;
+                int32_t *in = F.info + (size_t)j * kCbInfo;
+                if (j < j1 && in[2] > 0) nbytes = in[5] - 2 * in[2];
+                int total;
+                const int at = warp_excl(nbytes, lane, total);
+                if (j < j1) in[7] = (int32_t)(pos + at);
+                pos += total;
             }
             j0 = j1;
         }
@@ -1558,6 +1643,28 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
     }
 }
 
+// Copies the included code-blocks' kept pass bytes into their frames'
+// JPEG2000 codestreams at the offsets k_j2c placed them (one warp per
+// code-block); frames whose codestream did not fit are left alone.
+__global__ void __launch_bounds__(256) k_j2c_copy(const CsJob *__restrict__ job)
+{
+    const int lane = threadIdx.x & 31;
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int g = w0; g < job->ncb; g += nw) {
+        const CsFrame &F = job->frames[cb_frame(job, g)];
+        if (F.format != 1 || *F.flen <= 0) continue;
+        const int jb = g - F.cb0;
+        const int32_t *in = F.info + (size_t)jb * kCbInfo;
+        const int nk = in[2];
+        if (nk <= 0) continue;
+        const int nbytes = in[5] - 2 * nk;
+        const uint8_t *src = F.cbytes + (size_t)jb * kCbRegion;
+        uint8_t *dst = F.out + in[7];
+#pragma unroll 4
+        for (int i = lane; i < nbytes; i += 32) dst[i] = src[i];
+    }
+}
+
 int ebcot_codeblocks(int w, int h, int levels)
 {
     int n = 0;
@@ -1579,7 +1686,8 @@ void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
     k_t1_pack<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
     k_pcrd<<<std::max(1, nframes), 1024, 0, s>>>(job_dev);
     k_cs_copy<<<std::max(1, (ncb + 7) / 8), 256, 0, s>>>(job_dev);
-    k_j2c<<<std::max(1, nframes), 32, 0, s>>>(job_dev);
+    k_j2c<<<std::max(1, nframes), 32, kJ2cSmemInts * sizeof(int), s>>>(job_dev);
+    k_j2c_copy<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
 }
 
 void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, cudaStream_t s)
@@ -1591,7 +1699,8 @@ void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int
     k_t1_pack<<<grid_copy, 256, 0, s>>>(job_dev);
     k_pcrd<<<kMaxBatch, 1024, 0, s>>>(job_dev);
     k_cs_copy<<<grid_copy, 256, 0, s>>>(job_dev);
-    k_j2c<<<kMaxBatch, 32, 0, s>>>(job_dev);
+    k_j2c<<<kMaxBatch, 32, kJ2cSmemInts * sizeof(int), s>>>(job_dev);
+    k_j2c_copy<<<grid_copy, 256, 0, s>>>(job_dev);
 }
 
 int occupancy_t1()

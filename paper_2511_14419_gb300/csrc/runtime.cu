@@ -787,7 +787,7 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
             cudaMemsetAsync(const_cast<int *>(dd->cs_next), 0, sizeof dd->cs_next, st);
             launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_mq, c->grid_csc, st);
         });
-        cnt += 8;
+        cnt += 9;
     }
     *nlaunch = cnt;
     return FLOWROI_OK;
