@@ -17,10 +17,12 @@
 //     (bytes, distortion decrease), the slope threshold found by 64
 //     bisection steps on [0, 2 max slope + 1] so that the kept bytes fit
 //     the frame's budget;
-//   - a frame container: 32-byte header, a 16-byte entry per code-block,
-//     then per code-block the kept passes' 16-bit lengths and bytes.
+//   - the frame as this library's container (32-byte header, a 16-byte
+//     entry per code-block, then per code-block the kept passes' 16-bit
+//     lengths and bytes) or as a JPEG2000 Part 1 codestream (Annex A
+//     markers, Annex B packets with tag trees).
 //
-// Tier-1 coding runs as four kernels, so that no long sequential chain
+// Tier-1 coding runs as five kernels, so that no long sequential chain
 // waits on another:
 //   - k_t1, context modelling, one warp per code-block.  Which samples each
 //     pass codes, in which context, and with which decision depends only on
@@ -35,14 +37,19 @@
 //     scan candidates) is solved per stripe by rounds across the lanes; the
 //     cleanup pass's new significances are known at once.  The same warp
 //     builds each bit-plane and adds up the distortion decreases.
-//   - k_t1_mq, one thread per code-block: the MQ coder's interval register
-//     and context states over the block's decisions (the one chain that
-//     runs through all passes), recording each pass's starting context
-//     states and a byte bound for its codeword;
+//   - k_t1_mq, two threads per code-block: the MQ coder's interval
+//     register and context states over the block's decisions (the one
+//     chain that runs through all passes; the refinement passes' contexts
+//     and the others' form two independent chains), recording each pass's
+//     starting context states and a byte bound for its codeword;
+//   - k_t1_slots, one warp per code-block: the codewords' slot offsets;
 //   - k_t1_mqc, one thread per pass: each pass, a terminated codeword of
 //     its own, coded from its starting context states into its slot;
 //   - k_t1_pack, one warp per code-block: the codewords moved to be back to
 //     back.
+// Then k_pcrd (rate control, one CTA per frame), and the output: k_cs_copy
+// (container bodies) or k_j2c (codestream markers and packet headers, one
+// warp per frame) and k_j2c_copy (codestream bodies).
 
 #include "common.cuh"
 #include "kernels.h"
