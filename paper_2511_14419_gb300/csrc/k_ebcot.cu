@@ -1330,57 +1330,70 @@ constexpr int kJ2cSmemInts = 12 * 1024;  // k_j2c's tag trees in shared memory: 
 
 // A tag tree over nx x ny leaves (in shared memory, or global scratch for
 // large bands): per node its value (the least leaf below it) and its
-// state (low bound, bit 31: known).
+// state (low bound, bit 31: known).  The level loops run over a fixed
+// maximum, so the per-level geometry stays in registers.
+constexpr int kTTMax = 16;  // levels: bands up to 2^15 code-blocks a side
 struct TagTree {
     int *val, *st;
-    int nlev, lw[20], lh[20], off[20];
+    int nlev, nn, lw[kTTMax], lh[kTTMax], off[kTTMax];
     // node layout of an nx x ny tree (every lane computes the same)
-    __device__ void layout(int *mem, int nx, int ny)
+    __device__ __forceinline__ void layout(int *mem, int nx, int ny)
     {
         int w = nx, h = ny, o = 0;
-        nlev = 0;
-        for (;;) {
-            lw[nlev] = w;
-            lh[nlev] = h;
-            off[nlev] = o;
-            o += w * h;
-            nlev++;
-            if (w == 1 && h == 1) break;
+        bool done = false;
+        nlev = kTTMax;
+#pragma unroll
+        for (int l = 0; l < kTTMax; l++) {
+            lw[l] = w;
+            lh[l] = h;
+            off[l] = o;
+            if (!done) {
+                o += w * h;
+                if (w == 1 && h == 1) {
+                    nlev = l + 1;
+                    done = true;
+                }
+            }
             w = (w + 1) >> 1;
             h = (h + 1) >> 1;
         }
+        nn = o;
         val = mem;
         st = mem + o;
     }
-    __device__ int nodes() const { return off[nlev - 1] + 1; }
+    __device__ __forceinline__ int nodes() const { return nn; }
     // By the warp: leaf q (x = q % nx, y = q / nx) takes leaf(q), each node
     // above the least of its children, every state cleared.
     template <class Leaf>
-    __device__ void build(int lane, Leaf leaf)
+    __device__ __forceinline__ void build(int lane, Leaf leaf)
     {
-        const int o = nodes();
-        for (int i = lane; i < o; i += 32) st[i] = 0;
+        for (int i = lane; i < nn; i += 32) st[i] = 0;
         for (int q = lane; q < lw[0] * lh[0]; q += 32) val[q] = leaf(q);
-        for (int l = 1; l < nlev; l++) {
+#pragma unroll
+        for (int l = 1; l < kTTMax; l++) {
+            if (l >= nlev) break;
             __syncwarp();
-            const int w = lw[l], h = lh[l], pw = lw[l - 1], ph = lh[l - 1];
+            const int w = lw[l], h = lh[l], pw = lw[l - 1], ph = lh[l - 1], po = off[l - 1], o = off[l];
             for (int q = lane; q < w * h; q += 32) {
                 const int x = q % w, y = q / w;
                 int v = 0x3fffffff;
                 for (int dy = 0; dy < 2; dy++)
                     for (int dx = 0; dx < 2; dx++) {
                         const int cx = 2 * x + dx, cy = 2 * y + dy;
-                        if (cx < pw && cy < ph) v = min(v, val[off[l - 1] + cy * pw + cx]);
+                        if (cx < pw && cy < ph) v = min(v, val[po + cy * pw + cx]);
                     }
-                val[off[l] + q] = v;
+                val[o + q] = v;
             }
         }
         __syncwarp();
     }
-    __device__ void encode(HdrBits &bw, int x, int y, int threshold)
+    template <class Bits>
+    __device__ __forceinline__ void encode(Bits &bw, int x, int y, int threshold)
     {
         int low = 0;
-        for (int l = nlev - 1; l >= 0; l--) {
+#pragma unroll
+        for (int l = kTTMax - 1; l >= 0; l--) {
+            if (l >= nlev) continue;
             const int i = off[l] + (y >> l) * lw[l] + (x >> l);
             bool known = st[i] < 0;
             const int nl = st[i] & 0x7fffffff;
@@ -1401,29 +1414,34 @@ struct TagTree {
     }
 };
 
-// A code-block's header bits after its tag-tree bits (pass count, Lblock
-// increment, segment lengths): independent of the other blocks, so formed
-// by the lanes in parallel into words (MSB first, no stuffing; lane 0
-// appends them through HdrBits, which stuffs).
-struct TailBits {
+// Header bits without stuffing, into 32-bit words (first bit highest):
+// a code-block's bits after its tag-tree bits (pass count, Lblock
+// increment, segment lengths), or a band's whole header bits, formed apart
+// and later appended through HdrBits, which stuffs.
+struct RawBits {
     uint32_t *w;
-    uint32_t cur;
-    int n;
-    __device__ __forceinline__ void put(int b)
+    uint64_t acc;
+    int nacc, n;  // pending bits, bits so far
+    __device__ __forceinline__ void init(uint32_t *words)
     {
-        cur = (cur << 1) | (uint32_t)(b & 1);
-        if ((++n & 31) == 0) {
-            w[(n >> 5) - 1] = cur;
-            cur = 0;
-        }
+        w = words;
+        acc = 0;
+        nacc = n = 0;
     }
     __device__ __forceinline__ void put_bits(uint32_t v, int k)
     {
-        for (int i = k - 1; i >= 0; i--) put((int)((v >> i) & 1u));
+        acc = (acc << k) | (uint64_t)(k == 32 ? v : (v & ((1u << k) - 1u)));
+        nacc += k;
+        n += k;
+        if (nacc >= 32) {
+            w[(n - nacc) >> 5] = (uint32_t)(acc >> (nacc - 32));
+            nacc -= 32;
+        }
     }
+    __device__ __forceinline__ void put(int b) { put_bits((uint32_t)(b & 1), 1); }
     __device__ __forceinline__ void finish()
     {
-        if (n & 31) w[n >> 5] = cur << (32 - (n & 31));
+        if (nacc) w[(n - nacc) >> 5] = (uint32_t)(acc << (32 - nacc));
     }
 };
 
@@ -1527,7 +1545,8 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
             const int32_t *in = F.info + (size_t)j * kCbInfo;
             uint32_t *tw = reinterpret_cast<uint32_t *>(F.hs + (size_t)j * (kMaxPasses + 1));
             const int nk = in[2];
-            TailBits tb{tw + 1, 0u, 0};
+            RawBits tb;
+            tb.init(tw + 1);
             if (nk > 0) {
                 passes_codeword(tb, nk);
                 const int32_t *pl = F.plen + (size_t)j * kMaxPasses;
@@ -1546,6 +1565,103 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
         // HL, LH, HH bands of level D - r + 1; their code-blocks follow one
         // another in the frame's code-block order
         extern __shared__ int j2c_smem[];
+        // Each band's header bits (its packet's part after the `any` bit),
+        // coded by one lane per band into its code-blocks' hull scratch
+        // (free once rate control is done), when every band's tag trees fit
+        // in shared memory; lane 0 then only appends them, stuffing.
+        const int NU = 1 + 3 * D;  // bands: the low-low band, then HL, LH, HH from the coarsest level
+        auto unit = [&](int u, int &nx, int &ny, int &jb, int &band) {
+            int jj = 0;
+            for (int r = 0; r <= D; r++) {
+                const int nb = r == 0 ? 1 : 3, l = r == 0 ? D : D - r + 1;
+                const int ux = ((W >> l) + kCb - 1) / kCb, uy = ((H >> l) + kCb - 1) / kCb;
+                const int u0 = r == 0 ? 0 : 1 + 3 * (r - 1);
+                if (u < u0 + nb) {
+                    const int k = u - u0;
+                    nx = ux;
+                    ny = uy;
+                    jb = jj + k * ux * uy;
+                    band = r == 0 ? 3 * D : 3 * (l - 1) + k;
+                    return;
+                }
+                jj += nb * ux * uy;
+            }
+        };
+        int need_smem = NU;
+        for (int u = 0; u < NU; u++) {
+            int ux, uy, ujb, ub;
+            unit(u, ux, uy, ujb, ub);
+            TagTree tt;
+            tt.layout(j2c_smem, ux, uy);
+            need_smem += 4 * tt.nodes();
+        }
+        const bool par = need_smem <= kJ2cSmemInts;
+        int *const ubits = j2c_smem;
+        auto ubuf = [&](int jb) { return reinterpret_cast<uint32_t *>(F.hk + (size_t)jb * (kMaxPasses + 1)); };
+        if (par) {
+            int toff = NU;
+            for (int u = 0; u < NU; u++) {
+                int ux, uy, ujb, ub;
+                unit(u, ux, uy, ujb, ub);
+                const int Mb = G + (int)F.eps[ub] - 1;
+                TagTree incl, zbp;
+                incl.layout(j2c_smem + toff, ux, uy);
+                zbp.layout(j2c_smem + toff + 2 * incl.nodes(), ux, uy);
+                incl.build(lane, [&](int q) { return F.info[(size_t)(ujb + q) * kCbInfo + 2] > 0 ? 0 : 1; });
+                zbp.build(lane, [&](int q) { return Mb - F.info[(size_t)(ujb + q) * kCbInfo + 0]; });
+                toff += 4 * incl.nodes();
+            }
+            if (lane < NU) {
+                int ux, uy, ujb, ub;
+                unit(lane, ux, uy, ujb, ub);
+                int to = NU;
+                for (int u = 0; u < lane; u++) {
+                    int vx, vy, vjb, vb;
+                    unit(u, vx, vy, vjb, vb);
+                    TagTree tt;
+                    tt.layout(j2c_smem, vx, vy);
+                    to += 4 * tt.nodes();
+                }
+                TagTree incl, zbp;
+                incl.layout(j2c_smem + to, ux, uy);
+                zbp.layout(j2c_smem + to + 2 * incl.nodes(), ux, uy);
+                RawBits raw;
+                raw.init(ubuf(ujb));
+                auto tail = [&](int q) {
+                    return reinterpret_cast<const uint32_t *>(F.hs + (size_t)(ujb + q) * (kMaxPasses + 1));
+                };
+                // the next block's tail count and first two words loaded ahead
+                const int per_u = ux * uy;
+                uint32_t nbq = tail(0)[0], w0 = tail(0)[1], w1 = tail(0)[2];
+                for (int q = 0; q < per_u; q++) {
+                    uint32_t nbn = 0, w0n = 0, w1n = 0;
+                    if (q + 1 < per_u) {
+                        const uint32_t *tn = tail(q + 1);
+                        nbn = tn[0];
+                        w0n = tn[1];
+                        w1n = tn[2];
+                    }
+                    const int cx = q % ux, cy = q / ux;
+                    incl.encode(raw, cx, cy, 1);
+                    const int nb = (int)nbq;
+                    if (nb > 0) {  // included
+                        zbp.encode(raw, cx, cy, 0x3fffffff);
+                        const uint32_t *tw = tail(q);
+                        for (int i = 0; i < nb; i += 32) {
+                            const int kk = min(32, nb - i);
+                            const uint32_t word = i == 0 ? w0 : (i == 32 ? w1 : tw[1 + (i >> 5)]);
+                            raw.put_bits(word >> (32 - kk), kk);
+                        }
+                    }
+                    nbq = nbn;
+                    w0 = w0n;
+                    w1 = w1n;
+                }
+                raw.finish();
+                ubits[lane] = raw.n;
+            }
+            __syncwarp();
+        }
         int j0 = 0;
         for (int r = 0; r <= D; r++) {
             const int nbands = r == 0 ? 1 : 3, l = r == 0 ? D : D - r + 1;
@@ -1560,7 +1676,18 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
                 bits.init(out, cap, pos);
                 bits.put(any ? 1 : 0);
             }
-            if (any) {
+            if (any && par) {
+                if (lane == 0)
+                    for (int k = 0; k < nbands; k++) {
+                        const int u = r == 0 ? 0 : 1 + 3 * (r - 1) + k;
+                        const uint32_t *rw = ubuf(j0 + k * per);
+                        const int nb = ubits[u];
+                        for (int i = 0; i < nb; i += 32) {
+                            const int kk = min(32, nb - i);
+                            bits.put_bits(rw[i >> 5] >> (32 - kk), kk);
+                        }
+                    }
+            } else if (any) {
                 for (int k = 0; k < nbands; k++) {
                     const int band = r == 0 ? 3 * D : 3 * (l - 1) + k;
                     const int Mb = G + (int)F.eps[band] - 1;

@@ -257,6 +257,21 @@ def test_j2c_full_size_2048_97_at_one_bit_per_pixel(ctx):
     assert got == want
 
 
+def test_j2c_large_bands_tag_trees_in_global_scratch(ctx):
+    """A 6144^2 frame at one level: each band has 48 x 48 code-blocks, whose
+    tag trees no longer fit the writer's shared memory, so every band is
+    written with its trees in global scratch.  Sparse coefficients keep the
+    coding short."""
+    h = w = 6144
+    rng = np.random.default_rng(6144)
+    q = np.zeros((h, w), np.int32)
+    idx = rng.choice(h * w, 1500, replace=False)
+    q.flat[idx] = rng.integers(-3000, 3001, size=idx.size)
+    want, _ = o.encode_frame(q, 1, 53, 5, 12, 0, fmt="j2c")
+    got = _gpu(ctx, [q], 1, 53, 5, [0], on_device=True, fmt=F.CS_J2C)[0]
+    assert got == want
+
+
 def test_j2c_in_the_stream_path():
     """config.codestream_format = CS_J2C: each frame's codestream from the
     stream path equals the coder's codestream of that frame's coefficients,
