@@ -1086,19 +1086,22 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
             R[k + 1] = R[k] + pl[k];
             Dc[k + 1] = Dc[k] + di[k];
         }
+        // hull point i: its pass count in bits 0-7 and the bytes of those
+        // passes above (below 2^23: a block over kCbBytes is bad anyway)
+        auto pack = [&](int k) { return k | (int)(min(R[k], (long long)((1 << 23) - 1)) << 8); };
         int m = 1;
         hk[0] = 0;
         hs[0] = 0.0;
         for (int k = 1; k <= np; k++) {
-            if (!(Dc[k] > Dc[hk[m - 1]])) continue;
+            if (!(Dc[k] > Dc[hk[m - 1] & 0xFF])) continue;
             for (;;) {
-                const int a = hk[m - 1];
+                const int a = hk[m - 1] & 0xFF;
                 const double sl = (Dc[k] - Dc[a]) / (double)(R[k] - R[a]);
                 if (m >= 2 && sl >= hs[m - 1]) {
                     m--;
                     continue;
                 }
-                hk[m] = k;
+                hk[m] = pack(k);
                 hs[m] = sl;
                 m++;
                 break;
@@ -1112,18 +1115,22 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
     smax = bmax(smax);
     bad = bsum(bad);
 
+    // The last hull point whose slope is at least lam: the slopes fall
+    // strictly along the hull, so a binary search makes the same
+    // comparisons' decision as a scan from the start.
     auto kept = [&](int g, double lam, long long *bytes) {
         const int m = F.info[(size_t)g * kCbInfo + 4];
         const int32_t *hk = F.hk + (size_t)g * (kMaxPasses + 1);
         const double *hs = F.hs + (size_t)g * (kMaxPasses + 1);
-        int jj = 0;
-        while (jj + 1 < m && hs[jj + 1] >= lam) jj++;
-        const int nk = hk[jj];
-        long long b = 0;
-        const int32_t *pl = F.plen + (size_t)g * kMaxPasses;
-        for (int k = 0; k < nk; k++) b += pl[k];
-        *bytes = b;
-        return nk;
+        int a = 0, z = m - 1;  // hs[1..a] >= lam, hs[z+1..] < lam
+        while (a < z) {
+            const int mid = (a + z + 1) >> 1;
+            if (hs[mid] >= lam) a = mid;
+            else z = mid - 1;
+        }
+        const int h = hk[a];
+        *bytes = h >> 8;
+        return h & 0xFF;
     };
     const bool all = F.budget <= 0 || full <= F.budget;
     double lo = 0.0, hi = 2.0 * smax + 1.0;
