@@ -188,16 +188,20 @@ __global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict
         }
     };
 
+    // the block's tiles: one contiguous run, so that its histogram changes
+    // frame (clear and flush) rarely
+    const int run = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t0 = min(total, (int)blockIdx.x * run), t1 = min(total, t0 + run);
     if (tid == 0) {
-        fill_hdr(blockIdx.x, s_hdr[0]);
-        fill_hdr(blockIdx.x + gridDim.x, s_hdr[1]);
+        if (t0 < t1) fill_hdr(t0, s_hdr[0]);
+        if (t0 + 1 < t1) fill_hdr(t0 + 1, s_hdr[1]);
     }
     __syncthreads();
-    if ((int)blockIdx.x < total) issue(s_hdr[0], 0, 0);
+    if (t0 < t1) issue(s_hdr[0], 0, 0);
     asm volatile("cp.async.commit_group;" ::: "memory");
 
     int k = 0, u = 0;  // tile and strip counters of the block
-    for (int t = blockIdx.x; t < total; t += gridDim.x, k++) {
+    for (int t = t0; t < t1; t++, k++) {
         const SalTile &H = s_hdr[k % 3];
         const int fi = H.fi;
         if (fi != bh.frame) {
@@ -231,9 +235,9 @@ __global__ void __launch_bounds__(256, 4) k_saliency(const BatchDesc *__restrict
             // this strip has landed; every thread is done with the other buffer
             asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();
-            if (sub == 0 && tid == 0) fill_hdr(t + 2 * (int)gridDim.x, s_hdr[(k + 2) % 3]);
+            if (sub == 0 && tid == 0 && t + 2 < t1) fill_hdr(t + 2, s_hdr[(k + 2) % 3]);
             if (sub + 1 < nsub) issue(H, sub + 1, (u + 1) & 1);
-            else if (t + (int)gridDim.x < total) issue(s_hdr[(k + 1) % 3], 0, (u + 1) & 1);
+            else if (t + 1 < t1) issue(s_hdr[(k + 1) % 3], 0, (u + 1) & 1);
             asm volatile("cp.async.commit_group;" ::: "memory");
 
             const float2(*fl)[kSalCols] = s_fl[u & 1];
@@ -297,7 +301,10 @@ __global__ void __launch_bounds__(256, 4) k_select_pass(const BatchDesc *__restr
     const unsigned dmask = (1u << digit_bits(pass)) - 1u;
     const int lane = threadIdx.x & 31;
     BlockHist bh{s_hist, s_mm};
-    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+    // the block's tiles: one contiguous run (its histogram changes frame rarely)
+    const int run = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int t0 = min(total, (int)blockIdx.x * run), t1 = min(total, t0 + run);
+    for (int t = t0; t < t1; t++) {
         const int fi = find_frame(off, nfr, t);
         const FrameDesc &F = bd->f[fi];
         bh.begin(fi);
