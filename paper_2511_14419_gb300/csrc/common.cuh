@@ -23,7 +23,7 @@ constexpr int kDenMaxR = 3;                // largest bilateral radius of the op
 constexpr int kMaxAdj = 4;                 // largest adjacent factor (masks of frames t-k..t+k merged)
 constexpr int kExpTW = 256, kExpTH = 16;   // pyramid + polynomial expansion
 constexpr int kUpdTW = 256, kUpdRows = 4; // displacement update (G, h per pixel)
-constexpr int kWinTW = 64, kWinTH = 32;   // box window + 2x2 solve
+constexpr int kWinTW = 64, kWinTH = 64;   // box window + 2x2 solve
 constexpr int kSalTW = 256, kSalTH = 32;   // radix-select passes (saliency: kSalSub-row strips, per frame)
 constexpr int kSalSub = 8;                 // saliency: rows per staged strip
 constexpr int kMorTW = 256, kMorTH = 64;  // threshold + opening + closing (8 words x 64 rows)

@@ -167,6 +167,27 @@ def test_fp16_storage_epe_and_iou(orc, win_r):
     assert np.array_equal(orc.morph(g["mask0"], p.r_open, p.r_close), g["mask"])
 
 
+@pytest.mark.parametrize("prec,win_r", [("fp32", 2), ("fp32", 5), ("fp32", 10), ("fp16", 10)])
+def test_window_ring_several_tiles_per_block(orc, prec, win_r):
+    """Window radii whose plane rings differ in depth (in fp32, how many of
+    a tile's planes are column-summed at the end of the previous tile's
+    iteration: all five at r = 2, four at r = 5, two at r = 10), on a
+    2048 x 1024 pair: 512 level-0 tiles of 64 x 64, so every persistent
+    block takes several tiles in turn and runs the hand-over between them."""
+    seq = u16(sequence_u16(3100 + win_r, 2, 1024, 2048, 100))
+    cfg = dict(pyr_levels=3, dwt_levels=3, wavelet=97, win_r=win_r)
+    if prec == "fp32":
+        g = run_stream([seq[0], seq[1]], 12, **cfg)[1]
+        _stagewise(orc, seq[0], seq[1], 12, g, **cfg)
+        return
+    g = run_stream([seq[0], seq[1]], 12, precision=F.FP16, **cfg)[1]
+    o = orc.frame(seq[0], seq[1], 12, oracle_params(orc, **cfg))
+    d = g["flow"].transpose(2, 0, 1)
+    epe = np.hypot(d[0] - o["flow"][0], d[1] - o["flow"][1]).mean()
+    iou = (g["mask"] & o["mask"]).sum() / max(1, (g["mask"] | o["mask"]).sum())
+    assert epe < 0.05 and iou > 0.9, (epe, iou)
+
+
 def test_device_pointer_io_matches_host_io():
     prev, cur = pair_u8(seed=77, h=128, w=128, n_blobs=5)
     host = run_stream([prev.numpy(), cur.numpy()], 8, keep=False)[1]
