@@ -96,8 +96,8 @@ def _declare(L):
         "orc_mq_roundtrip": (ctypes.c_long, [_P, _P, ctypes.c_long, _P, _P]),
         "orc_mq_table": (_I, [_P, _P, _P, _P]),
         "orc_context_tables": (None, [_P, _P, _P]),
-        "orc_t1_encode": (_I, [_P, _I, _I, _I, _I, _P, ctypes.c_long, _P, _P, _P]),
-        "orc_t1_decode": (None, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _I]),
+        "orc_t1_encode": (_I, [_P, _I, _I, _I, _I, _P, ctypes.c_long, _P, _P, _P, _I]),
+        "orc_t1_decode": (None, [_P, _P, _I, _I, _I, _I, _I, _I, _P, _I, _I]),
         "orc_hull": (_I, [_I, _P, _P, _P, _P]),
     }
     for name, (res, args) in sig.items():
@@ -482,9 +482,10 @@ def context_tables():
     return zc.reshape(4, 5, 3, 3), sc.reshape(3, 3), fl.reshape(3, 3)
 
 
-def t1_encode(q: np.ndarray, ori: int):
+def t1_encode(q: np.ndarray, ori: int, reset: bool = False):
     """Tier-1 coding of one code-block: (planes, pass lengths, pass
-    distortion decreases, bytes of all passes back to back)."""
+    distortion decreases, bytes of all passes back to back).  Every pass is
+    terminated; with `reset` the contexts also restart at every pass."""
     q = _c(q, np.int32)
     h, w = q.shape
     cap = 8 * 64 * 64 * 96
@@ -492,7 +493,8 @@ def t1_encode(q: np.ndarray, ori: int):
     planes = ctypes.c_int(0)
     plen = np.zeros(96, np.int32)
     dist = np.zeros(96, np.float64)
-    n = lib().orc_t1_encode(_ptr(q), w, w, h, ori, _ptr(out), cap, ctypes.byref(planes), _ptr(plen), _ptr(dist))
+    n = lib().orc_t1_encode(_ptr(q), w, w, h, ori, _ptr(out), cap, ctypes.byref(planes), _ptr(plen), _ptr(dist),
+                            int(reset))
     if n == -2:
         raise OverflowError("code-block magnitude of 2^24 or more")
     if n < 0:
@@ -501,11 +503,11 @@ def t1_encode(q: np.ndarray, ori: int):
 
 
 def t1_decode(code: np.ndarray, plen: np.ndarray, nkept: int, planes: int, w: int, h: int, ori: int,
-              midpoint: bool = True) -> np.ndarray:
+              midpoint: bool = True, reset: bool = False) -> np.ndarray:
     code = _c(code, np.uint8)
     plen = _c(plen, np.int32)
     q = np.zeros((h, w), np.int32)
-    lib().orc_t1_decode(_ptr(code), _ptr(plen), nkept, planes, w, h, ori, int(midpoint), _ptr(q), w)
+    lib().orc_t1_decode(_ptr(code), _ptr(plen), nkept, planes, w, h, ori, int(midpoint), _ptr(q), w, int(reset))
     return q
 
 
@@ -576,19 +578,21 @@ def pcrd(blocks, budget: int, iters: int = 64):
 
 
 def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_depth: int, budget: int = 0,
-                 fmt: str = "container", delta_base: float = 1.0):
+                 fmt: str = "container", delta_base: float = 1.0, reset: bool = False):
     """Tier-1 coding of every code-block of a Mallat plane, rate control to
     `budget` bytes of pass data (0: lossless in the passes), and the frame
     container: a 32-byte header, a 16-byte entry per code-block, then per
     code-block the kept passes' 16-bit lengths and bytes; with fmt="j2c" a
     JPEG2000 Part 1 codestream of the same kept passes instead
-    (codestream_j2c).  Returns (bytes, block records)."""
+    (codestream_j2c).  With `reset` every block is coded with its contexts
+    reset at every pass (the header's flags word, bit 0; COD's code-block
+    style).  Returns (bytes, block records)."""
     import struct
     coeffs = _c(coeffs, np.int32)
     h, w = coeffs.shape
     blocks = []
     for b, ori, x0, y0, cw, ch in codeblocks(w, h, levels):
-        planes, plen, dist, code = t1_encode(coeffs[y0:y0 + ch, x0:x0 + cw], ori)
+        planes, plen, dist, code = t1_encode(coeffs[y0:y0 + ch, x0:x0 + cw], ori, reset)
         blocks.append(dict(band=b, ori=ori, x0=x0, y0=y0, w=cw, h=ch, planes=planes, plen=plen, dist=dist,
                            code=code))
     nkeep = pcrd(blocks, budget)
@@ -602,8 +606,9 @@ def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_
         data.append(body)
         off += len(body)
     if fmt == "j2c":
-        return codestream_j2c(blocks, w, h, levels, wavelet, bit_depth, delta_base), blocks
-    hdr = struct.pack("<4sIIIBBBBIII", _MAGIC, 1, w, h, wavelet, levels, shift, bit_depth, len(blocks), off, 0)
+        return codestream_j2c(blocks, w, h, levels, wavelet, bit_depth, delta_base, reset), blocks
+    hdr = struct.pack("<4sIIIBBBBIII", _MAGIC, 1, w, h, wavelet, levels, shift, bit_depth, len(blocks), off,
+                      1 if reset else 0)
     return hdr + b"".join(table) + b"".join(data), blocks
 
 
@@ -612,7 +617,9 @@ def encode_frame(coeffs: np.ndarray, levels: int, wavelet: int, shift: int, bit_
 # packet headers), Annex E (the quantisation exponents and M_b).  One tile,
 # one component, one quality layer, LRCP progression, no precinct
 # partition (one precinct per resolution: one packet per resolution),
-# 64 x 64 code-blocks, code-block style "termination on each coding pass",
+# 64 x 64 code-blocks, code-block style "termination on each coding pass"
+# (byte 0x04; with reset also "reset context probabilities on coding pass
+# boundaries", 0x02: the style byte's bits, Annex A.6.1),
 # no RGN marker: Part 1 signals only the maximum-shift RoI method, so the
 # scaling-based RoI travels in the coefficients themselves (a Part 1
 # decoder returns the up-shifted coefficients; undoing the shift needs the
@@ -731,7 +738,7 @@ def band_exponents(levels: int, wavelet: int, bit_depth: int, delta_base: float 
 
 
 def codestream_j2c(blocks, w: int, h: int, levels: int, wavelet: int, bit_depth: int,
-                   delta_base: float = 1.0) -> bytes:
+                   delta_base: float = 1.0, reset: bool = False) -> bytes:
     """A JPEG2000 Part 1 codestream of one frame from its code-blocks' kept
     passes (encode_frame's block records with 'nkeep').  The guard bits G are
     the fewest (at least 1) for which every block's bit-planes fit the
@@ -746,7 +753,8 @@ def codestream_j2c(blocks, w: int, h: int, levels: int, wavelet: int, bit_depth:
     order = [3 * levels] + [3 * (l - 1) + o for l in range(levels, 0, -1) for o in range(3)]
     cs = bytearray(b"\xff\x4f")  # SOC
     cs += struct.pack(">HHHIIIIIIIIHBBB", 0xFF51, 41, 0, w, h, 0, 0, w, h, 0, 0, 1, bit_depth - 1, 1, 1)  # SIZ
-    cs += struct.pack(">HHBBHBBBBBB", 0xFF52, 12, 0, 0, 1, 0, levels, 4, 4, 0x04, 1 if wavelet == 53 else 0)  # COD
+    style = 0x04 | (0x02 if reset else 0)
+    cs += struct.pack(">HHBBHBBBBBB", 0xFF52, 12, 0, 0, 1, 0, levels, 4, 4, style, 1 if wavelet == 53 else 0)  # COD
     if wavelet == 53:
         cs += struct.pack(">HHB", 0xFF5C, 3 + len(order), G << 5) + bytes(eps[b] << 3 for b in order)
     else:
@@ -799,11 +807,13 @@ def codestream_j2c(blocks, w: int, h: int, levels: int, wavelet: int, bit_depth:
 def decode_frame(stream: bytes, midpoint: bool = True) -> np.ndarray:
     """The Mallat coefficient plane recovered from a frame container (kept
     passes only; unknown low bits at the interval midpoint when
-    `midpoint`)."""
+    `midpoint`; the blocks decoded with their contexts reset at every pass
+    when the header's flags word has bit 0 set)."""
     import struct
-    magic, ver, w, h, wav, levels, shift, bd, nb, nbytes, _ = struct.unpack_from("<4sIIIBBBBIII", stream, 0)
-    if magic != _MAGIC or ver != 1:
+    magic, ver, w, h, wav, levels, shift, bd, nb, nbytes, flags = struct.unpack_from("<4sIIIBBBBIII", stream, 0)
+    if magic != _MAGIC or ver != 1 or flags & ~1:
         raise ValueError("not a frame container")
+    reset = bool(flags & 1)
     out = np.zeros((h, w), np.int32)
     base = _HDR + nb * _ENT
     oris = {b: o for b, o, *_ in codeblocks(w, h, levels)}
@@ -813,7 +823,7 @@ def decode_frame(stream: bytes, midpoint: bool = True) -> np.ndarray:
         plen = np.frombuffer(stream, "<u2", k, p).astype(np.int32)
         code = np.frombuffer(stream, np.uint8, int(plen.sum()), p + 2 * k)
         out[y0:y0 + ch1 + 1, x0:x0 + cw1 + 1] = t1_decode(code, plen, k, planes, cw1 + 1, ch1 + 1, oris[band],
-                                                          midpoint)
+                                                          midpoint, reset)
     return out
 
 

@@ -547,9 +547,15 @@ static int64_t cb_pass(orc_cb *b, int type, int p, orc_ctx *x, orc_mqe *e, orc_m
  * their lengths to plen[] and distortion decreases (the pass's int64 sum,
  * then converted to double) to dist[]; returns the number of passes (3
  * planes - 2, 0 for an all-zero block) and the planes in *planes, -1 when
- * out is too small, -2 for a magnitude of 2^24 or more. */
+ * out is too small, -2 for a magnitude of 2^24 or more.  Every pass is
+ * terminated (the code-block style option "termination on each coding
+ * pass"); with reset the context states also return to their initial
+ * values at the start of every pass (the option "reset context
+ * probabilities on coding pass boundaries"), else they carry from pass to
+ * pass.  Both options are signalled in the code-block style byte of the
+ * COD marker (Annex A.6.1). */
 int orc_t1_encode(const int32_t *q, int stride, int w, int h, int ori, uint8_t *out, long cap, int *planes,
-                  int32_t *plen, double *dist)
+                  int32_t *plen, double *dist, int reset)
 {
     static orc_cb b;
     cb_load(&b, q, stride, w, h, ori);
@@ -568,6 +574,7 @@ int orc_t1_encode(const int32_t *q, int stride, int w, int h, int ori, uint8_t *
         for (int type = (p == mb - 1 ? 2 : 0); type <= 2; type++, k++) {
             orc_mqe e;
             mqe_init(&e, tmp + 1);
+            if (reset) ctx_reset(&x);
             dist[k] = (double)cb_pass(&b, type, p, &x, &e, NULL);
             const long len = mqe_flush(&e);
             if (pos + len > cap) {
@@ -588,9 +595,10 @@ int orc_t1_encode(const int32_t *q, int stride, int w, int h, int ori, uint8_t *
  * a significant coefficient whose bits are known down to plane p is set to
  * the middle of its interval (the known bits plus 2^(p-1), p > 0): the
  * reconstruction whose squared error the encoder's distortion decreases
- * account for; without it, to the known bits. */
+ * account for; without it, to the known bits.  reset: the block was coded
+ * with the contexts reset at every pass. */
 void orc_t1_decode(const uint8_t *code, const int32_t *plen, int nkept, int planes, int w, int h, int ori,
-                   int midpoint, int32_t *q, int stride)
+                   int midpoint, int32_t *q, int stride, int reset)
 {
     static orc_cb b;
     memset(&b, 0, sizeof b);
@@ -606,6 +614,7 @@ void orc_t1_decode(const uint8_t *code, const int32_t *plen, int nkept, int plan
         for (int type = (p == planes - 1 ? 2 : 0); type <= 2 && k < nkept; type++, k++) {
             orc_mqd d;
             mqd_init(&d, code + pos, plen[k]);
+            if (reset) ctx_reset(&x);
             cb_pass(&b, type, p, &x, NULL, &d);
             pos += plen[k];
         }

@@ -106,8 +106,11 @@ def parse(cs: bytes, levels_expected=None):
             info.update(w=w, h=h, bit_depth=(ss & 0x7F) + 1)
         elif m == 0xFF52:
             scod, prog, nl, mct, D, xcb, ycb, style, tr = struct.unpack(">BBHBBBBBB", seg)
-            assert (scod, prog, nl, mct, xcb, ycb, style, L) == (0, 0, 1, 0, 4, 4, 0x04, 12)
-            info.update(levels=D, wavelet=53 if tr == 1 else 97)
+            assert (scod, prog, nl, mct, xcb, ycb, L) == (0, 0, 1, 0, 4, 4, 12)
+            # code-block style byte: termination on each coding pass (0x04),
+            # optionally with the contexts reset on pass boundaries (0x02)
+            assert style in (0x04, 0x06)
+            info.update(levels=D, wavelet=53 if tr == 1 else 97, style=style)
         elif m == 0xFF5C:
             sq = seg[0]
             info["guard"] = sq >> 5
@@ -220,6 +223,28 @@ def test_lossless_53_frame_decodes_back_from_the_codestream():
     cont, _ = O.encode_frame(q, 3, 53, 5, 12, 0)
     assert info["blocks"] == _container_blocks(cont)
     assert np.array_equal(O.decode_frame(cont), q)
+
+
+@pytest.mark.parametrize("wavelet,budget", [(53, 0), (97, 6000)])
+def test_reset_style_codestream_and_container(wavelet, budget):
+    """Contexts reset at every pass: the container's flags word is 1 and
+    COD's code-block style byte 0x06; the codestream carries the container's
+    passes, the container decodes back (lossless 5/3), and the same frame
+    without the reset has flags 0, style 0x04 and the same pass counts kept
+    when every pass is kept."""
+    q = _frame(11 + wavelet, 192, 256, 8.0)
+    cont, blocks = O.encode_frame(q, 3, wavelet, 5, 12, budget, reset=True)
+    cs, _ = O.encode_frame(q, 3, wavelet, 5, 12, budget, fmt="j2c", reset=True)
+    assert struct.unpack_from("<I", cont, 28)[0] == 1
+    info = parse(cs)
+    assert info["style"] == 0x06
+    assert info["blocks"] == _container_blocks(cont)
+    cont0, blocks0 = O.encode_frame(q, 3, wavelet, 5, 12, budget)
+    cs0, _ = O.encode_frame(q, 3, wavelet, 5, 12, budget, fmt="j2c")
+    assert struct.unpack_from("<I", cont0, 28)[0] == 0 and parse(cs0)["style"] == 0x04
+    if budget == 0:
+        assert [b["nkeep"] for b in blocks] == [b["nkeep"] for b in blocks0]
+        assert np.array_equal(O.decode_frame(cont), q)
 
 
 def test_all_zero_frame_gives_empty_packets():

@@ -113,6 +113,66 @@ def test_t1_distortion_decreases_match_the_decoder(ori):
     assert np.all(dist >= 0)
 
 
+@pytest.mark.parametrize("ori", [o.ORI_LL, o.ORI_HL, o.ORI_LH, o.ORI_HH])
+@pytest.mark.parametrize("h,w,scale,zero_frac", [(64, 64, 300.0, 0.3), (64, 64, 3.0, 0.8), (17, 40, 2 ** 20, 0.1)])
+def test_t1_reset_codes_the_same_decisions(ori, h, w, scale, zero_frac):
+    """Resetting the contexts at every pass changes how the MQ coder codes
+    each pass's decisions, never which decisions are coded: so the passes'
+    distortion decreases are those of the carried-contexts coder, decoding
+    the first k passes of either stream gives the same coefficients for
+    every k, and the first pass (which starts from the initial states either
+    way) is the same codeword.  A later pass that starts from learned states
+    gives a different codeword, and a reset stream decoded with carried
+    contexts does not come back."""
+    rng = np.random.default_rng(h * 17 + w + ori)
+    q = _block(rng, h, w, scale, zero_frac)
+    planes, plen, dist, code = o.t1_encode(q, ori)
+    planes_r, plen_r, dist_r, code_r = o.t1_encode(q, ori, reset=True)
+    assert planes_r == planes and len(plen_r) == len(plen)
+    assert np.array_equal(dist_r, dist)
+    for k in range(len(plen) + 1):
+        a = o.t1_decode(code, plen, k, planes, w, h, ori, midpoint=False)
+        b = o.t1_decode(code_r, plen_r, k, planes, w, h, ori, midpoint=False, reset=True)
+        assert np.array_equal(a, b), k
+    assert np.array_equal(b, q)
+    assert plen_r[0] == plen[0] and bytes(code_r[:plen[0]]) == bytes(code[:plen[0]])
+    ends, ends_r = np.cumsum(plen), np.cumsum(plen_r)
+    assert any(bytes(code[ends[k - 1]:ends[k]]) != bytes(code_r[ends_r[k - 1]:ends_r[k]]) for k in range(1, len(plen)))
+    wrong = o.t1_decode(code_r, plen_r, len(plen_r), planes, w, h, ori, midpoint=False)
+    assert not np.array_equal(wrong, q)
+
+
+def test_t1_reset_passes_are_independent_codewords():
+    """With the contexts reset and every pass terminated, a pass's codeword
+    depends only on that pass's decisions: two blocks whose top bit-planes
+    differ but whose lower planes (and significance by then) agree give the
+    same codewords for the passes of those lower planes.  Block b is block a
+    with one already-significant coefficient's top bits changed, which
+    changes the decisions of the top passes only (its refinement bits
+    there) and, with carried contexts, the states every later pass starts
+    from."""
+    rng = np.random.default_rng(7)
+    a = _block(rng, 64, 64, 200.0, 0.4)
+    a[5, 9] = 4000   # 12 planes; planes 0..9 of the others stay below 2^10
+    b = a.copy()
+    b[5, 9] = 4000 ^ (1 << 10)   # 2976: same top plane (11), bit 10 flipped
+    assert int(np.abs(a).max()).bit_length() == int(np.abs(b).max()).bit_length() == 12
+    assert int(np.abs(np.delete(a.ravel(), 5 * 64 + 9)).max()) < 1 << 10
+    pa, la, _, ca = o.t1_encode(a, o.ORI_HH, reset=True)
+    pb, lb, _, cb = o.t1_encode(b, o.ORI_HH, reset=True)
+    ea, eb = np.concatenate([[0], np.cumsum(la)]), np.concatenate([[0], np.cumsum(lb)])
+    # pass index of plane p's significance pass: 1 + 3 (planes - 2 - p)
+    first_same = 1 + 3 * (pa - 2 - 9)
+    for k in range(first_same, len(la)):
+        assert bytes(ca[ea[k]:ea[k + 1]]) == bytes(cb[eb[k]:eb[k + 1]]), k
+    kr = 1 + 3 * (pa - 2 - 10) + 1   # plane 10's refinement pass: one decision, 1 in a, 0 in b
+    assert bytes(ca[ea[kr]:ea[kr + 1]]) != bytes(cb[eb[kr]:eb[kr + 1]])
+    _, lc, _, cc = o.t1_encode(a, o.ORI_HH)
+    _, ld, _, cd = o.t1_encode(b, o.ORI_HH)
+    ec, ed = np.concatenate([[0], np.cumsum(lc)]), np.concatenate([[0], np.cumsum(ld)])
+    assert any(bytes(cc[ec[k]:ec[k + 1]]) != bytes(cd[ed[k]:ed[k + 1]]) for k in range(first_same, len(lc)))
+
+
 def _frame(seed, h, w, bd=12):
     return np.asarray(sequence_u16(seed, 1, h, w, 6)[0]).astype(np.uint16)
 
