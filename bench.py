@@ -64,6 +64,12 @@ WORKLOADS = {
     # rate control, container)
     "ebcot_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                           dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0),
+    # the same with the coder's contexts reset at every pass (code-block style
+    # 0x02 with per-pass termination: no chain of context states through a
+    # code-block, every pass's MQ states formed apart)
+    "ebcot_reset_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
+                                dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0,
+                                codestream_reset=1),
     # the same with JPEG2000 Part 1 codestreams instead of containers
     "j2c_16x2048": dict(streams=16, frames=32, h=2048, w=2048, blobs=200, bit_depth=12, pyr_levels=5,
                         dwt_levels=5, wavelet=97, precision=32, seed_base=3000, codestream_bpp=1.0, codestream_format=1),
@@ -453,7 +459,7 @@ def run_codestream(F, wl, frames, steps, warmup, profile_steps=3):
     cfg = dict(pyr_levels=wl["pyr_levels"], dwt_levels=wl["dwt_levels"], wavelet=wl["wavelet"],
                precision=wl["precision"], max_batch_frames=64, result_ring=8, flags=F.MANUAL,
                codestream_bpp=wl["codestream_bpp"], codestream_format=wl.get("codestream_format", 0),
-               device=torch.cuda.current_device())
+               codestream_reset=wl.get("codestream_reset", 0), device=torch.cuda.current_device())
     S, n, bd = wl["streams"], wl["frames"], wl["bit_depth"]
     H, W, L = wl["h"], wl["w"], wl["dwt_levels"]
     cap = F.flowroi_codestream_bound(W, H, L) // 4
@@ -596,7 +602,7 @@ def cpu_sample(wl, frames_cpu, budget_s=12.0, crop=512):
                     np.ascontiguousarray(b[y0:y0 + crop, x0:x0 + crop]), wl["bit_depth"], p)
         if "codestream_bpp" in wl:
             O.encode_frame(o["coeffs"], wl["dwt_levels"], wl["wavelet"], p.scale_shift, wl["bit_depth"],
-                           int(wl["codestream_bpp"] * crop * crop / 8))
+                           int(wl["codestream_bpp"] * crop * crop / 8), reset=bool(wl.get("codestream_reset", 0)))
         done += 1
         k += 1
         el = time.perf_counter() - t0
@@ -633,7 +639,8 @@ def _cpu_worker(job):
         o = O.frame(a, b, wl["bit_depth"], p)
         if "codestream_bpp" in wl:
             O.encode_frame(o["coeffs"], wl["dwt_levels"], wl["wavelet"], p.scale_shift, wl["bit_depth"],
-                           int(wl["codestream_bpp"] * a.shape[0] * a.shape[1] / 8))
+                           int(wl["codestream_bpp"] * a.shape[0] * a.shape[1] / 8),
+                           reset=bool(wl.get("codestream_reset", 0)))
         done += 1
         el = time.perf_counter() - t0
         if el >= budget_s:
@@ -838,6 +845,8 @@ def main():
                               "ms_per_step": 1e3 * t_max / args.steps,
                               "codestream_ms_per_step": cr["kernel_ms"].get("codestream"),
                               "codestream_target_bpp": wl["codestream_bpp"], "codestream_bpp": cr["bpp"],
+                              "codestream_contexts": "reset at every pass" if wl.get("codestream_reset")
+                              else "carried from pass to pass",
                               "kernel_avg_ms": cr["kernel_ms"],
                               "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
                               "config": config_of(args.workload, wl), "cpu_baseline": cpu,

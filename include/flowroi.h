@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define FLOWROI_ABI_VERSION 5
+#define FLOWROI_ABI_VERSION 6
 
 /* Exported symbols (the library is built with hidden default visibility). */
 #if defined(__GNUC__)
@@ -184,6 +184,15 @@ typedef struct flowroi_config {
      * the built-in shapes.  Not a method parameter: results do not depend
      * on it, only the time they take.  (NULL) */
     const char *tile_table;
+    /* Code-block style of those codestreams: 0 = every pass terminated, the
+     * MQ coder's context states carried from pass to pass; 1 = also reset
+     * the context states at every pass (JPEG2000 Part 1's code-block style
+     * option "reset context probabilities on coding pass boundaries", COD
+     * style byte 0x06 instead of 0x04, the container's flags word 1).  With
+     * reset every pass is coded apart from the others, so no chain of
+     * context states runs through a code-block; the passes cost a few more
+     * bytes each, while their contexts learn again.  (0) */
+    int32_t codestream_reset;
 } flowroi_config;
 
 /* One input frame.  Frames of a stream keep their width, height, dtype and
@@ -407,7 +416,8 @@ FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, 
  *
  * Container (little-endian): a 32-byte header {"FRJ2", u32 version 1, u32
  * width, u32 height, u8 wavelet, u8 levels, u8 shift, u8 bit_depth, u32
- * code-blocks, u32 data bytes, u32 0}; per code-block a 16-byte entry {u32
+ * code-blocks, u32 data bytes, u32 flags (bit 0: the contexts were reset at
+ * every pass)}; per code-block a 16-byte entry {u32
  * data offset, u16 x0, u16 y0 (in the plane), u8 width-1, u8 height-1, u8
  * band (HL, LH, HH of level l at 3(l-1), +1, +2; low-low at 3 levels), u8
  * bit-planes, u8 passes coded, u8 passes kept, u16 0}, in codestream order
@@ -419,7 +429,8 @@ FLOWROI_API int flowroi_dwt_roi_noalloc(const void *raw, int width, int height, 
  * same kept passes): SOC; SIZ (one tile of the whole frame, one unsigned
  * component of bit_depth bits); COD (LRCP, one quality layer, no
  * multi-component transform, `levels` decomposition levels, 64 x 64
- * code-blocks, code-block style "termination on each coding pass",
+ * code-blocks, code-block style "termination on each coding pass" (and
+ * "reset context probabilities on coding pass boundaries" with reset),
  * transform 5/3 reversible or 9/7 irreversible, no precinct partition);
  * QCD (5/3: no quantisation, exponent bit_depth + the band's log2 gain;
  * 9/7: scalar expounded, each band's (exponent, mantissa) of the steps
@@ -462,7 +473,7 @@ typedef struct {
     uint64_t out_cap;
     uint64_t out_len;
     int32_t format;      /* FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C */
-    int32_t reserved;    /* 0 */
+    int32_t reset;       /* 0 or 1: the code-block style of config.codestream_reset */
 } flowroi_cs_job;
 FLOWROI_API int flowroi_encode_codestreams(flowroi_ctx *ctx, int n, flowroi_cs_job *jobs, int on_device);
 /* The container of a frame coded in the stream path (config.codestream_bpp

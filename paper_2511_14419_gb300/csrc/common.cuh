@@ -129,7 +129,7 @@ struct CsFrame {
     double *hs;           // [kMaxPasses + 1]
     long long *flen;      // the container's length (negative: it needs that many bytes; -1: a code-block out of range)
     int format;           // 0: the library's frame container, 1: JPEG2000 Part 1 codestream
-    int pad_;
+    int reset;            // 1: the MQ contexts reset at every pass (code-block style 0x02)
     uint8_t eps[kMaxSubbands];   // 1: the bands' quantisation exponents (table index as delta[])
     uint16_t mu[kMaxSubbands];   // 1: and mantissas (9/7)
 };
@@ -138,7 +138,8 @@ struct CsJob {
     const CsFrame *frames;  // device array [nframes]
     int cbcap;              // kCbBytes
     unsigned *err;          // error word, or null
-    int *next;              // work counters, zeroed before the coder runs: [0] modelling, [1] MQ states, [2] MQ passes
+    int *next;              // work counters, zeroed before the coder runs: [0] modelling, [1] MQ state chains,
+                            // [2] MQ codewords, [3] MQ states of passes coded apart (reset)
 };
 
 // One frame of a batch.  Level geometry: lw/lh = level size, lp = pitch in
@@ -220,7 +221,7 @@ struct BatchDesc {
     FrameDesc f[kMaxBatch];
     CsJob cs;                       // the batch's coder job over csf (frames with do_cs)
     CsFrame csf[kMaxBatch];
-    int cs_next[3];                 // the coder's work counters
+    int cs_next[4];                 // the coder's work counters
 };
 
 #ifdef __CUDACC__

@@ -696,7 +696,11 @@ __global__ void __launch_bounds__(32 * kT1Warps) k_t1(const CsJob *__restrict__ 
                 else if (type == 1) n += t1_mrp(s, y0, lane, out, room, ovf);
                 else n += t1_cup(s, y0, ex0, ex1, lane, zc, out, room, ovf);
             }
-            if (lane == 0) nsym[k] = n;
+            if (lane == 0) {
+                nsym[k] = n;
+                // passes coded apart take their first decision from here
+                if (F.reset) F.ptab[(size_t)jb * kMaxPasses + k].x = pos;
+            }
             pos = (pos + n + 15) & ~15;  // the next pass starts 16-byte aligned
         }
     }
@@ -809,6 +813,57 @@ __device__ __forceinline__ uint32_t piece_byte(const uint4 &v, int q)
     return (x >> ((q & 3) * 8)) & 0xFFu;
 }
 
+// Renormalisation shifts S of one pass's n decisions (sym 16-byte aligned,
+// read 16 at a time with the next 16 loaded ahead) from a fresh interval
+// and the context states in s_cx[.][t], which it leaves at their end
+// states; mrp: a refinement pass, whose three contexts (14-16) stay in
+// registers on the way.
+__device__ __forceinline__ int pass_shifts(const uint8_t *sym, int n, bool mrp, uint32_t (*s_cx)[kMqThreads], int t,
+                                           const uint32_t *s_tab)
+{
+    uint32_t a = 0x8000;
+    int S = 0;
+    if (n <= 0) return 0;
+    const uint4 *pp = reinterpret_cast<const uint4 *>(sym);
+    const int npc = (n + 15) >> 4;
+    uint4 cur = __ldg(pp);
+    if (mrp) {
+        uint32_t w3[3] = {s_cx[14][t], s_cx[15][t], s_cx[16][t]};
+        for (int b = 0; b < npc; b++) {
+            const uint4 nx = b + 1 < npc ? __ldg(pp + b + 1) : make_uint4(0u, 0u, 0u, 0u);
+            const int rem = n - 16 * b;
+            if (rem >= 16) {
+#pragma unroll
+                for (int q = 0; q < 16; q++) mq_state_step_mr(piece_byte(cur, q), w3, s_tab, a, S);
+            } else {
+                for (int q = 0; q < rem; q++) mq_state_step_mr(piece_byte(cur, q), w3, s_tab, a, S);
+            }
+            cur = nx;
+        }
+        s_cx[14][t] = w3[0];
+        s_cx[15][t] = w3[1];
+        s_cx[16][t] = w3[2];
+    } else {
+        uint32_t w = s_cx[(cur.x >> 1) & 31u][t];
+        for (int b = 0; b < npc; b++) {
+            const uint4 nx = b + 1 < npc ? __ldg(pp + b + 1) : make_uint4(0u, 0u, 0u, 0u);
+            const int rem = n - 16 * b;
+            if (rem > 16) {
+#pragma unroll
+                for (int q = 0; q < 16; q++)
+                    mq_state_step(piece_byte(cur, q), q < 15 ? piece_byte(cur, q + 1) : (nx.x & 0xFFu), s_cx, t, s_tab,
+                                  w, a, S);
+            } else {
+                for (int q = 0; q < rem; q++)
+                    mq_state_step(piece_byte(cur, q), q + 1 < rem ? piece_byte(cur, q + 1) : 0u, s_cx, t, s_tab, w, a,
+                                  S);
+            }
+            cur = nx;
+        }
+    }
+    return S;
+}
+
 // MQ coding, first stage: the interval register and context states over a
 // code-block's decisions, recording each pass's starting context states
 // and the slot its codeword is given: floor(S / 7) + 3 bytes for S
@@ -817,8 +872,8 @@ __device__ __forceinline__ uint32_t piece_byte(const uint4 &v, int q)
 // passes use contexts 14-16 only and the other passes never do, and every
 // pass starts a fresh interval, so a block is two independent chains: one
 // thread takes the refinement passes, another the significance and
-// cleanup passes.  Decisions are read 16 at a time (each pass's start is
-// 16-byte aligned) with the next 16 loaded ahead.
+// cleanup passes.  Blocks whose contexts reset at every pass are left to
+// k_t1_mq_pass.
 __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ job)
 {
     __shared__ uint32_t s_cx[32][kMqThreads];  // the contexts of each thread's code-block
@@ -834,6 +889,7 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ 
         const bool mrp = u < job->ncb;  // this thread's chain: the refinement passes
         const int g = mrp ? u : u - job->ncb;
         const CsFrame &F = job->frames[cb_frame(job, g)];
+        if (F.reset) continue;
         const int jb = g - F.cb0;
         int32_t *info = F.info + (size_t)jb * kCbInfo;
         const int np = info[1];
@@ -854,50 +910,48 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mq(const CsJob *__restrict__ 
             pos = (pos + n + 15) & ~15;
             if ((k % 3 == 2) != mrp) continue;  // the other chain's pass
             for (int c = 0; c < kNctx; c++) mqs[k * kMqWords + c] = s_cx[c][t];
-            uint32_t a = 0x8000;
-            int S = 0;
-            if (n > 0 && mrp) {
-                const uint4 *pp = reinterpret_cast<const uint4 *>(sym + s0);
-                const int npc = (n + 15) >> 4;
-                uint4 cur = __ldg(pp);
-                uint32_t w3[3] = {s_cx[14][t], s_cx[15][t], s_cx[16][t]};
-                for (int b = 0; b < npc; b++) {
-                    const uint4 nx = b + 1 < npc ? __ldg(pp + b + 1) : make_uint4(0u, 0u, 0u, 0u);
-                    const int rem = n - 16 * b;
-                    if (rem >= 16) {
-#pragma unroll
-                        for (int q = 0; q < 16; q++) mq_state_step_mr(piece_byte(cur, q), w3, s_tab, a, S);
-                    } else {
-                        for (int q = 0; q < rem; q++) mq_state_step_mr(piece_byte(cur, q), w3, s_tab, a, S);
-                    }
-                    cur = nx;
-                }
-                s_cx[14][t] = w3[0];
-                s_cx[15][t] = w3[1];
-                s_cx[16][t] = w3[2];
-            } else if (n > 0) {
-                const uint4 *pp = reinterpret_cast<const uint4 *>(sym + s0);
-                const int npc = (n + 15) >> 4;
-                uint4 cur = __ldg(pp);
-                uint32_t w = s_cx[(cur.x >> 1) & 31u][t];
-                for (int b = 0; b < npc; b++) {
-                    const uint4 nx = b + 1 < npc ? __ldg(pp + b + 1) : make_uint4(0u, 0u, 0u, 0u);
-                    const int rem = n - 16 * b;
-                    if (rem > 16) {
-#pragma unroll
-                        for (int q = 0; q < 16; q++)
-                            mq_state_step(piece_byte(cur, q), q < 15 ? piece_byte(cur, q + 1) : (nx.x & 0xFFu), s_cx,
-                                          t, s_tab, w, a, S);
-                    } else {
-                        for (int q = 0; q < rem; q++)
-                            mq_state_step(piece_byte(cur, q), q + 1 < rem ? piece_byte(cur, q + 1) : 0u, s_cx, t, s_tab,
-                                          w, a, S);
-                    }
-                    cur = nx;
-                }
-            }
+            const int S = pass_shifts(sym + s0, n, mrp, s_cx, t, s_tab);
             ptab[k] = make_int4(s0, 0, S / 7 + 3, 0);
         }
+    }
+}
+
+// The same stage for code-blocks whose contexts reset at every pass: each
+// pass starts from the initial context states and a fresh interval, so
+// its slot bound is a short chain of its own.  One thread per (code-block,
+// pass), items ordered like k_t1_mqc's (by bit-plane and pass type, then
+// code-block), so that a warp's threads run like passes of neighbouring
+// blocks; each pass's first decision was recorded by k_t1.
+__global__ void __launch_bounds__(kMqThreads) k_t1_mq_pass(const CsJob *__restrict__ job)
+{
+    __shared__ uint32_t s_cx[32][kMqThreads];
+    __shared__ uint32_t s_tab[64];
+    const int t = threadIdx.x;
+    for (int i = t; i < 64; i += blockDim.x) s_tab[i] = i < 47 ? kMq.w[i] : 0u;
+    __syncthreads();
+    const int items = job->ncb * 3 * kMaxPlanes;
+    for (;;) {
+        const int u = atomicAdd(job->next + 3, 1);
+        if (u >= items) break;
+        const int kk = u / job->ncb, g = u - kk * job->ncb;
+        const int pl = kk / 3, type = kk - 3 * pl;  // type 0 significance, 1 refinement, 2 cleanup
+        const CsFrame &F = job->frames[cb_frame(job, g)];
+        if (!F.reset) continue;
+        const int jb = g - F.cb0;
+        int32_t *info = F.info + (size_t)jb * kCbInfo;
+        const int planes = info[0];
+        if (info[3] != 0 || info[1] <= 0 || pl >= planes || (pl == planes - 1 && type != 2)) continue;
+        const int k = pl == planes - 1 ? 0 : 1 + 3 * (planes - 2 - pl) + type;
+        if (k >= info[1]) continue;
+        int4 *pt = F.ptab + (size_t)jb * kMaxPasses + k;
+        const int s0 = pt->x, n = F.nsym[(size_t)jb * kMaxPasses + k];
+        if (s0 < 0 || (s0 & 15) != 0 || n < 0 || n > kSymCap - s0) {
+            info[3] = 1;  // never: the model bounds its decisions and aligns each pass
+            continue;
+        }
+        mq_init_contexts(s_cx, t, s_tab);
+        const int S = pass_shifts(F.sym + (size_t)jb * kSymCap + s0, n, type == 1, s_cx, t, s_tab);
+        pt->z = S / 7 + 3;
     }
 }
 
@@ -965,8 +1019,12 @@ __global__ void __launch_bounds__(kMqThreads) k_t1_mqc(const CsJob *__restrict__
             info[3] = 1;  // never: the first stage and the slot offsets bound these
             continue;
         }
-        const uint32_t *mqs = F.mqs + ((size_t)jb * kMaxPasses + k) * kMqWords;
-        for (int c = 0; c < kNctx; c++) s_cx[c][t] = mqs[c];
+        if (F.reset) {
+            mq_init_contexts(s_cx, t, s_tab);
+        } else {
+            const uint32_t *mqs = F.mqs + ((size_t)jb * kMaxPasses + k) * kMqWords;
+            for (int c = 0; c < kNctx; c++) s_cx[c][t] = mqs[c];
+        }
         DecReader rd;
         rd.start(F.sym + (size_t)jb * kSymCap, pt.x);
         Mqe e;
@@ -1228,7 +1286,7 @@ __global__ void __launch_bounds__(1024) k_pcrd(const CsJob *__restrict__ job)
             hd[19] = (uint8_t)F.bit_depth;
             put32(20, (uint32_t)n);
             put32(24, (uint32_t)data);
-            put32(28, 0u);
+            put32(28, F.reset ? 1u : 0u);  // flags: bit 0, contexts reset at every pass
             *F.flen = total;
         } else {
             // did not fit (the length it needs), or a code-block out of range (-1)
@@ -1521,7 +1579,7 @@ __global__ void __launch_bounds__(32) k_j2c(const CsJob *__restrict__ job)
             b32((uint32_t)W); b32((uint32_t)H); b32(0); b32(0);  // one tile
             b16(1); b8((uint32_t)(F.bit_depth - 1)); b8(1); b8(1);  // one unsigned component
             b16(0xFF52); b16(12); b8(0); b8(0); b16(1); b8(0);  // COD: LRCP, one layer, no MCT
-            b8((uint32_t)D); b8(4); b8(4); b8(0x04); b8(F.wavelet == 53 ? 1 : 0);
+            b8((uint32_t)D); b8(4); b8(4); b8(F.reset ? 0x06 : 0x04); b8(F.wavelet == 53 ? 1 : 0);
             const int nb = 3 * D + 1;
             b16(0xFF5C);                                      // QCD
             if (F.wavelet == 53) {
@@ -1817,11 +1875,13 @@ int ebcot_codeblocks(int w, int h, int levels)
     return n;
 }
 
-void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
+void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, bool chains, bool passes, cudaStream_t s)
 {
     const long long items = (long long)ncb * 3 * kMaxPlanes;
     k_t1<<<std::max(1, (ncb + kT1Warps - 1) / kT1Warps), 32 * kT1Warps, 0, s>>>(job_dev);
-    k_t1_mq<<<std::max(1, (2 * ncb + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
+    if (chains) k_t1_mq<<<std::max(1, (2 * ncb + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
+    if (passes)
+        k_t1_mq_pass<<<(int)std::min<long long>(4096, (items + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
     k_t1_slots<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
     k_t1_mqc<<<(int)std::min<long long>(4096, (items + kMqThreads - 1) / kMqThreads), kMqThreads, 0, s>>>(job_dev);
     k_t1_pack<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
@@ -1831,10 +1891,11 @@ void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s)
     k_j2c_copy<<<std::max(1, std::min(1024, (ncb + 7) / 8)), 256, 0, s>>>(job_dev);
 }
 
-void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, cudaStream_t s)
+void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, bool reset, cudaStream_t s)
 {
     k_t1<<<grid_t1, 32 * kT1Warps, 0, s>>>(job_dev);
-    k_t1_mq<<<grid_mq, kMqThreads, 0, s>>>(job_dev);
+    if (reset) k_t1_mq_pass<<<4 * grid_mq, kMqThreads, 0, s>>>(job_dev);
+    else k_t1_mq<<<grid_mq, kMqThreads, 0, s>>>(job_dev);
     k_t1_slots<<<grid_copy, 256, 0, s>>>(job_dev);
     k_t1_mqc<<<4 * grid_mq, kMqThreads, 0, s>>>(job_dev);
     k_t1_pack<<<grid_copy, 256, 0, s>>>(job_dev);

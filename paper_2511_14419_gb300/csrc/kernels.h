@@ -60,9 +60,11 @@ bool denoise_radius_supported(int r);
 // Embedded block coding of coefficient planes into frame containers
 // (k_ebcot.cu); CsFrame, CsJob and the coder's constants are in common.cuh.
 int ebcot_codeblocks(int w, int h, int levels);
-void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, cudaStream_t s);
+// chains: some frame carries its contexts from pass to pass; passes: some
+// frame resets them at every pass (each launches its own MQ state stage).
+void launch_ebcot(const CsJob *job_dev, int nframes, int ncb, bool chains, bool passes, cudaStream_t s);
 // The same with fixed (persistent, grid-stride) grids, for captured graphs.
-void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, cudaStream_t s);
+void launch_ebcot_persistent(const CsJob *job_dev, int grid_t1, int grid_mq, int grid_copy, bool reset, cudaStream_t s);
 int occupancy_t1();
 
 // 9/7 quantisation steps (host, double precision); see flowroi_quant_steps.

@@ -326,6 +326,8 @@ int validate_config(const flowroi_config *c)
         return fail(FLOWROI_EINVAL, "config.codestream_bpp must be in [0, 64]");
     if (c->codestream_format != FLOWROI_CS_CONTAINER && c->codestream_format != FLOWROI_CS_J2C)
         return fail(FLOWROI_EINVAL, "config.codestream_format must be FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C");
+    if (c->codestream_reset != 0 && c->codestream_reset != 1)
+        return fail(FLOWROI_EINVAL, "config.codestream_reset must be 0 or 1");
     if (c->tile_table) {
         std::string text, err;
         TileTable t;
@@ -602,6 +604,7 @@ void fill_frame(flowroi_ctx *c, Stream *s, Entry *e, Entry *d, FrameDesc &F)
             C.hk = reinterpret_cast<int32_t *>(b);
             C.flen = d->cs_len;
             C.format = c->cfg.codestream_format;
+            C.reset = c->cfg.codestream_reset;
             std::memcpy(C.eps, s->cs_eps, sizeof C.eps);
             std::memcpy(C.mu, s->cs_mu, sizeof C.mu);
         }
@@ -785,7 +788,7 @@ int enqueue_pipeline(flowroi_ctx *c, const BatchDesc *dd, const BatchDesc *hd, c
         // tier-1 coding, rate control and containers of the batch's front-end frames
         timed(c, st, prof, K_CS, -1, -1, [&] {
             cudaMemsetAsync(const_cast<int *>(dd->cs_next), 0, sizeof dd->cs_next, st);
-            launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_mq, c->grid_csc, st);
+            launch_ebcot_persistent(&dd->cs, c->grid_t1, c->grid_mq, c->grid_csc, c->cfg.codestream_reset != 0, st);
         });
         cnt += 9;
     }
@@ -1199,6 +1202,7 @@ void flowroi_default_config(flowroi_config *cfg)
     cfg->reg_level = 2;
     cfg->codestream_bpp = 0.f;
     cfg->codestream_format = FLOWROI_CS_CONTAINER;
+    cfg->codestream_reset = 0;
 }
 
 int flowroi_quant_steps(int levels, int bit_depth, float delta_base, float *delta, int32_t *eps, int32_t *mu,
@@ -1767,6 +1771,7 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     std::vector<CsFrame> fr((size_t)n);
     int ncb = 0;
     size_t coef_bytes = 0, out_bytes = 0;
+    bool any_reset = false, any_carry = false;  // code-block styles present: the launches they need
     for (int i = 0; i < n; i++) {
         const flowroi_cs_job &J = jobs[i];
         if (!J.coeffs || !J.out) return fail(FLOWROI_EINVAL, "job %d: coeffs and out must be non-NULL", i);
@@ -1789,6 +1794,9 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
         if (J.format != FLOWROI_CS_CONTAINER && J.format != FLOWROI_CS_J2C)
             return fail(FLOWROI_EINVAL, "job %d: format must be FLOWROI_CS_CONTAINER or FLOWROI_CS_J2C", i);
         F.format = J.format;
+        if (J.reset != 0 && J.reset != 1) return fail(FLOWROI_EINVAL, "job %d: reset must be 0 or 1", i);
+        F.reset = J.reset;
+        (J.reset ? any_reset : any_carry) = true;
         if (J.format == FLOWROI_CS_J2C && !band_exponents(J.levels, J.wavelet, J.bit_depth, c->cfg.delta_base, F.eps, F.mu))
             return fail(FLOWROI_EINVAL, "job %d: quantisation steps out of range for bit_depth %d", i, J.bit_depth);
         F.cb0 = ncb;
@@ -1815,7 +1823,7 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     const size_t o_info = take((size_t)ncb * kCbInfo * sizeof(int32_t));
     const size_t o_hk = take((size_t)ncb * (kMaxPasses + 1) * sizeof(int32_t));
     const size_t o_hs = take((size_t)ncb * (kMaxPasses + 1) * sizeof(double));
-    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(4 * sizeof(unsigned));
+    const size_t o_flen = take((size_t)n * sizeof(long long)), o_err = take(5 * sizeof(unsigned));
     const size_t o_coef = on_device ? 0 : take(coef_bytes), o_out = on_device ? 0 : take(out_bytes);
 
     int rc = FLOWROI_OK;
@@ -1876,9 +1884,9 @@ int flowroi_encode_codestreams(flowroi_ctx *c, int n, flowroi_cs_job *jobs, int 
     job.next = reinterpret_cast<int *>(dev + o_err) + 1;
     step(cudaMemcpyAsync(dev + o_frames, fr.data(), sizeof(CsFrame) * (size_t)n, cudaMemcpyHostToDevice, st));
     step(cudaMemcpyAsync(dev + o_job, &job, sizeof job, cudaMemcpyHostToDevice, st));
-    step(cudaMemsetAsync(dev + o_err, 0, 4 * sizeof(unsigned), st));
+    step(cudaMemsetAsync(dev + o_err, 0, 5 * sizeof(unsigned), st));
     if (e == cudaSuccess) {
-        launch_ebcot(reinterpret_cast<const CsJob *>(dev + o_job), n, ncb, st);
+        launch_ebcot(reinterpret_cast<const CsJob *>(dev + o_job), n, ncb, any_carry, any_reset, st);
         step(cudaGetLastError());
     }
     step(cudaMemcpyAsync(flen.data(), dev + o_flen, sizeof(long long) * (size_t)n, cudaMemcpyDeviceToHost, st));

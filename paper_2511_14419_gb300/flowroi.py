@@ -53,6 +53,7 @@ class flowroi_config(ctypes.Structure):
         ("den_sigma_r", ctypes.c_float), ("min_area", ctypes.c_int32), ("adjacent", ctypes.c_int32),
         ("register_frames", ctypes.c_int32), ("reg_level", ctypes.c_int32), ("codestream_bpp", ctypes.c_float),
         ("codestream_format", ctypes.c_int32), ("tile_table", ctypes.c_char_p),
+        ("codestream_reset", ctypes.c_int32),
     ]
 
 
@@ -69,7 +70,7 @@ class flowroi_cs_job(ctypes.Structure):
                 ("levels", ctypes.c_int32), ("wavelet", ctypes.c_int32), ("shift", ctypes.c_int32),
                 ("bit_depth", ctypes.c_int32), ("budget_bytes", ctypes.c_int64), ("out", ctypes.c_void_p),
                 ("out_cap", ctypes.c_uint64), ("out_len", ctypes.c_uint64), ("format", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("reset", ctypes.c_int32)]
 
 
 class flowroi_kernel_time(ctypes.Structure):
@@ -412,10 +413,10 @@ def flowroi_encode_codestreams(ctx, jobs) -> list:
     """Codes coefficient planes into frame containers or JPEG2000
     codestreams (see the C header).  jobs: dicts with coeffs (int32 (H, W)
     numpy array or CUDA tensor), levels, wavelet, shift, bit_depth, budget
-    (pass-data bytes, 0 = every pass), format (CS_CONTAINER or CS_J2C) and
-    out (uint8 numpy array or CUDA tensor: the destination, its size the
-    capacity).  All on the host or all on the device.  Returns the
-    lengths."""
+    (pass-data bytes, 0 = every pass), format (CS_CONTAINER or CS_J2C),
+    reset (0 or 1: contexts reset at every pass) and out (uint8 numpy array
+    or CUDA tensor: the destination, its size the capacity).  All on the
+    host or all on the device.  Returns the lengths."""
     arr = (flowroi_cs_job * len(jobs))()
     dev = None
     for i, j in enumerate(jobs):
@@ -428,7 +429,8 @@ def flowroi_encode_codestreams(ctx, jobs) -> list:
         h, w = int(j["coeffs"].shape[0]), int(j["coeffs"].shape[1])
         nbytes = int(j["out"].numel() * j["out"].element_size()) if hasattr(j["out"], "numel") else int(j["out"].nbytes)
         arr[i] = flowroi_cs_job(cp, w, h, j["levels"], j["wavelet"], j.get("shift", 0), j.get("bit_depth", 12),
-                                int(j.get("budget", 0)), op, nbytes, 0, int(j.get("format", CS_CONTAINER)), 0)
+                                int(j.get("budget", 0)), op, nbytes, 0, int(j.get("format", CS_CONTAINER)),
+                                int(j.get("reset", 0)))
     _check(lib().flowroi_encode_codestreams(ctx, len(jobs), arr, int(dev)), ctx)
     return [int(arr[i].out_len) for i in range(len(jobs))]
 

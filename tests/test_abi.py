@@ -44,7 +44,7 @@ def test_struct_sizes_match_binding(F):
     cfg = F.flowroi_default_config()
     assert cfg.struct_size == ctypes.sizeof(F.flowroi_config)
     assert (cfg.roi_q, cfg.scale_shift, cfg.win_r, cfg.iters) == (np.float32(0.2), 5, 7, 3)
-    assert F.flowroi_abi_version() == 5
+    assert F.flowroi_abi_version() == 6
     assert ctypes.sizeof(F.flowroi_cs_job) == 72
 
 
@@ -59,7 +59,7 @@ def test_quant_steps_match_oracle_table(F, orc):
 def test_config_validation_is_host_side(F):
     bad = [dict(roi_q=0.0), dict(roi_q=1.0), dict(wavelet=44), dict(win_r=1), dict(win_r=11), dict(poly_n_half=4),
            dict(lam=0.0), dict(r_open=5), dict(precision=8), dict(max_batch_frames=0), dict(result_ring=1),
-           dict(dwt_levels=9), dict(scale_shift=16), dict(flags=0x80)]
+           dict(dwt_levels=9), dict(scale_shift=16), dict(flags=0x80), dict(codestream_reset=2)]
     for kw in bad:
         cfg = F.flowroi_default_config(**kw)
         with pytest.raises(F.FlowRoIError) as ei:

@@ -37,17 +37,18 @@ def _planes(seed, h, w, levels, wavelet, shift, bd=12, roi_frac=0.3):
     return o.roi_shift(q, cm, shift)
 
 
-def _gpu(ctx, planes, levels, wavelet, shift, budgets, on_device=False, bd=12, fmt=0):
+def _gpu(ctx, planes, levels, wavelet, shift, budgets, on_device=False, bd=12, fmt=0, resets=None):
     jobs = []
-    for q, b in zip(planes, budgets):
+    for i, (q, b) in enumerate(zip(planes, budgets)):
         h, w = q.shape
         cap = F.flowroi_codestream_bound(w, h, levels)
+        r = resets[i] if resets else 0
         if on_device:
             jobs.append(dict(coeffs=torch.from_numpy(q).cuda(), out=torch.zeros(cap, dtype=torch.uint8, device="cuda"),
-                             levels=levels, wavelet=wavelet, shift=shift, bit_depth=bd, budget=b, format=fmt))
+                             levels=levels, wavelet=wavelet, shift=shift, bit_depth=bd, budget=b, format=fmt, reset=r))
         else:
             jobs.append(dict(coeffs=np.ascontiguousarray(q), out=np.zeros(cap, np.uint8), levels=levels,
-                             wavelet=wavelet, shift=shift, bit_depth=bd, budget=b, format=fmt))
+                             wavelet=wavelet, shift=shift, bit_depth=bd, budget=b, format=fmt, reset=r))
     lens = F.flowroi_encode_codestreams(ctx, jobs)
     out = []
     for j, n in zip(jobs, lens):
@@ -296,3 +297,62 @@ def test_j2c_in_the_stream_path():
                 assert bytes(out[:k]) == want, (s, t)
                 info = parse(want)
                 assert (info["w"], info["h"], info["levels"]) == (w, h, 3)
+
+
+# ------------------------------- contexts reset at every pass (style 0x02) --
+
+@pytest.mark.parametrize("h,w,levels,wavelet,bpp,fmt", [(256, 256, 3, 53, 0.0, 0), (200, 264, 3, 97, 1.0, 0),
+                                                         (512, 512, 5, 97, 0.25, 1), (192, 320, 4, 53, 0.0, 1)])
+def test_reset_style_matches_oracle(ctx, h, w, levels, wavelet, bpp, fmt):
+    """reset = 1: every pass coded from the initial context states (the
+    per-pass MQ state stage instead of the per-block chains), containers
+    and codestreams byte for byte the oracle's."""
+    q = _planes(h * 5 + w + levels, h, w, levels, wavelet, 5)
+    budget = int(bpp * h * w / 8)
+    want, _ = o.encode_frame(q, levels, wavelet, 5, 12, budget, fmt="j2c" if fmt else "container", reset=True)
+    got = _gpu(ctx, [q], levels, wavelet, 5, [budget], fmt=fmt, resets=[1])[0]
+    assert got == want
+
+
+def test_reset_and_carried_styles_in_one_call(ctx):
+    """Frames of both styles in one call: both MQ state stages run, each on
+    its own frames, and every container is the oracle's."""
+    qs = [_planes(900 + i, 192, 256, 3, 97, 5) for i in range(4)]
+    resets = [1, 0, 0, 1]
+    budgets = [6000, 6000, 0, 0]
+    got = _gpu(ctx, qs, 3, 97, 5, budgets, resets=resets)
+    for q, b, r, g in zip(qs, budgets, resets, got):
+        assert g == o.encode_frame(q, 3, 97, 5, 12, b, reset=bool(r))[0]
+
+
+def test_reset_full_size_2048_97_at_one_bit_per_pixel(ctx):
+    h = w = 2048
+    q = _planes(3001, h, w, 5, 97, 5)
+    budget = h * w // 8
+    want, _ = o.encode_frame(q, 5, 97, 5, 12, budget, reset=True)
+    got = _gpu(ctx, [q], 5, 97, 5, [budget], on_device=True, resets=[1])[0]
+    assert got == want
+
+
+def test_reset_in_the_stream_path():
+    """config.codestream_reset = 1 in the stream path (captured launches):
+    each frame's container is the oracle's coding of that frame's
+    coefficients with the contexts reset at every pass."""
+    h, w, S, n = 256, 320, 2, 3
+    with F.Context(pyr_levels=3, dwt_levels=3, wavelet=97, codestream_bpp=1.0, codestream_reset=1,
+                   flags=F.MANUAL) as c:
+        seqs = [np.asarray(sequence_u16(730 + s, n, h, w, 8)).astype(np.uint16) for s in range(S)]
+        for t in range(n):
+            for s in range(S):
+                F.flowroi_submit_frame(c.h, s, seqs[s][t], t, 12)
+            F.flowroi_step(c.h)
+        F.flowroi_flush(c.h, 60000)
+        cap = F.flowroi_codestream_bound(w, h, 3)
+        for s in range(S):
+            for t in range(n):
+                coeffs = np.empty((h, w), np.int32)
+                F.flowroi_get_coeffs(c.h, s, t, coeffs, 10000)
+                out = np.zeros(cap, np.uint8)
+                k = F.flowroi_get_codestream(c.h, s, t, out, 10000)
+                want, _ = o.encode_frame(coeffs, 3, 97, 5, 12, h * w // 8, reset=True)
+                assert bytes(out[:k]) == want, (s, t)
