@@ -42,9 +42,13 @@
 //     chain that runs through all passes; the refinement passes' contexts
 //     and the others' form two independent chains), recording each pass's
 //     starting context states and a byte bound for its codeword;
+//     With the contexts reset at every pass (code-block style 0x02, an
+//     option) no state runs from pass to pass, and k_t1_mq_pass, one thread
+//     per (code-block, pass), takes this stage instead;
 //   - k_t1_slots, one warp per code-block: the codewords' slot offsets;
 //   - k_t1_mqc, one thread per pass: each pass, a terminated codeword of
-//     its own, coded from its starting context states into its slot;
+//     its own, coded from its starting context states (the initial ones
+//     with reset) into its slot;
 //   - k_t1_pack, one warp per code-block: the codewords moved to be back to
 //     back.
 // Then k_pcrd (rate control, one CTA per frame), and the output: k_cs_copy
