@@ -230,25 +230,33 @@ struct Mqe {
         }
     }
     // One decision d in the context whose word (the state's table row |
-    // MPS << 31) is cw; tab: the table rows by state index.
+    // MPS << 31) is cw; tab: the table rows by state index.  The coded
+    // sub-interval is picked by selects: the upper one (A - Qe, C + Qe)
+    // when the decision is the MPS and no conditional exchange applies, or
+    // it is the LPS and one does; else the lower one (Qe).  A renormalises
+    // exactly when it falls below 0x8000 (never for an MPS that leaves it
+    // there), and the shift stays within CT, with no byte handed out, for
+    // most decisions, so the threads of a warp (coding different passes)
+    // branch apart only at a byte-out.
     __device__ __forceinline__ void encode(uint32_t &cw, const uint32_t *tab, uint32_t d)
     {
         const uint32_t w = cw, qe = w & 0xFFFFu, mps = w >> 31;
-        a -= qe;
-        if (d == mps) {
-            if (a & 0x8000) {
-                c += qe;
-                return;
+        const uint32_t a1 = a - qe;
+        const bool is_mps = d == mps;
+        const bool up = is_mps != (a1 < qe);
+        a = up ? a1 : qe;
+        c += up ? qe : 0u;
+        const int n = __clz(a) - 16;
+        if (n > 0) {
+            cw = is_mps ? (tab[(w >> 16) & 63u] | (mps << 31)) : (tab[(w >> 22) & 63u] | ((mps ^ ((w >> 28) & 1u)) << 31));
+            if (n < ct) {
+                a <<= n;
+                c <<= n;
+                ct -= n;
+            } else {
+                renorm();
             }
-            if (a < qe) a = qe;
-            else c += qe;
-            cw = tab[(w >> 16) & 63u] | (mps << 31);
-        } else {
-            if (a < qe) c += qe;
-            else a = qe;
-            cw = tab[(w >> 22) & 63u] | ((mps ^ ((w >> 28) & 1u)) << 31);
         }
-        renorm();
     }
     // Terminates the codeword; returns its length in bytes.
     __device__ __forceinline__ int flush()
