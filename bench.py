@@ -417,9 +417,9 @@ def run_e2e(F, wl, frames, steps, warmup):
             t += 1
 
         def fetch(step):
-            for s in range(S):
-                F.flowroi_get_mask(ctx.h, sid_of(wl, s), step, masks[s], -1)
-                F.flowroi_get_coeffs(ctx.h, sid_of(wl, s), step, coefs[s], -1)
+            # every stream's mask and coefficients of the step in one call
+            # (the copies back to back, one wait)
+            F.flowroi_get_results(ctx.h, [(sid_of(wl, s), step, masks[s], coefs[s]) for s in range(S)], -1)
 
         submit_step()
         fetch(0)

@@ -282,6 +282,24 @@ FLOWROI_API int flowroi_get_mask(flowroi_ctx *ctx, int64_t stream_id, int64_t fr
 FLOWROI_API int flowroi_get_coeffs(flowroi_ctx *ctx, int64_t stream_id, int64_t frame_idx, int32_t *out,
                        int out_on_device, int timeout_ms);
 
+/* The masks and coefficients of n frames in one call (one step's
+ * results of a batch of wells): frame frame_idx[k] of stream
+ * stream_ids[k] into masks[k] (W*H bytes, as flowroi_get_mask) and
+ * coeffs[k] (W*H int32, as flowroi_get_coeffs); masks or coeffs, or an
+ * element of either, may be NULL to skip that output.  Each frame is
+ * waited for like flowroi_get_mask (at most timeout_ms each, < 0: no
+ * limit); then every copy is queued back to back on the library's
+ * copy-out stream and waited for once (one wait per batch instead of two
+ * per frame).  status[k] (if status is not NULL) receives frame k's result
+ * (FLOWROI_OK, FLOWROI_ETIMEDOUT, FLOWROI_EGONE, FLOWROI_ENOSTREAM, ...);
+ * a failed frame's outputs are not written, and the other frames are still
+ * copied.  Returns FLOWROI_OK when every frame's outputs were written, else
+ * the first failing frame's code; FLOWROI_EINVAL for a NULL ctx, n < 0 or
+ * NULL stream_ids / frame_idx, with nothing copied. */
+FLOWROI_API int flowroi_get_results(flowroi_ctx *ctx, int n, const int64_t *stream_ids, const int64_t *frame_idx,
+                                    uint8_t *const *masks, int32_t *const *coeffs, int out_on_device, int timeout_ms,
+                                    int *status);
+
 /* Copy out an intermediate of (stream_id, frame_idx) (`which`: one of
  * FLOWROI_I_*, sizes as listed there) for inspection and tests.  Needs
  * FLOWROI_KEEP_INTERMEDIATES (else FLOWROI_ENOTKEPT).  A first frame has

@@ -1467,6 +1467,83 @@ int flowroi_get_coeffs(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int
     return get_common(c, stream_id, frame_idx, -1, out, out_on_device, timeout_ms);
 }
 
+int flowroi_get_results(flowroi_ctx *c, int n, const int64_t *stream_ids, const int64_t *frame_idx, uint8_t *const *masks,
+                        int32_t *const *coeffs, int out_on_device, int timeout_ms, int *status)
+{
+    if (!c) return fail(FLOWROI_EINVAL, "ctx is NULL");
+    if (n < 0 || (n > 0 && (!stream_ids || !frame_idx))) return fail(FLOWROI_EINVAL, "n < 0 or a NULL array");
+    cudaSetDevice(c->device);
+    std::vector<Entry *> held((size_t)n, nullptr);
+    std::vector<size_t> npx((size_t)n, 0);
+    std::vector<int> rc((size_t)n, FLOWROI_OK);
+    // look up and hold every frame (its ring slot is not reused while held)
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (int k = 0; k < n; k++) {
+            if (c->poisoned) {
+                rc[(size_t)k] = fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str());
+                continue;
+            }
+            auto it = c->streams.find(stream_ids[k]);
+            if (it == c->streams.end()) {
+                rc[(size_t)k] = fail(FLOWROI_ENOSTREAM, "unknown stream %lld", (long long)stream_ids[k]);
+                continue;
+            }
+            Stream *s = it->second.get();
+            Entry *e = find_entry(s, frame_idx[k]);
+            if (!e) {
+                rc[(size_t)k] = s->any_frame && frame_idx[k] <= s->last_frame_idx
+                                    ? fail(FLOWROI_EGONE, "frame %lld of stream %lld is no longer held",
+                                           (long long)frame_idx[k], (long long)stream_ids[k])
+                                    : fail(FLOWROI_ENOSTREAM, "frame %lld of stream %lld was not submitted",
+                                           (long long)frame_idx[k], (long long)stream_ids[k]);
+                continue;
+            }
+            e->readers++;
+            held[(size_t)k] = e;
+            npx[(size_t)k] = (size_t)s->W * s->H;
+        }
+    }
+    for (int k = 0; k < n; k++) {
+        Entry *e = held[(size_t)k];
+        if (e && !wait_done(c, e, timeout_ms))
+            rc[(size_t)k] = c->poisoned ? fail(FLOWROI_EDEVICE, "context poisoned: %s", c->poison_msg.c_str())
+                                        : fail(FLOWROI_ETIMEDOUT, "frame %lld not finished within %d ms",
+                                               (long long)frame_idx[k], timeout_ms);
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->d2h_mu);
+        const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        cudaError_t ce = cudaSuccess;
+        int queued = 0;
+        for (int k = 0; k < n && ce == cudaSuccess; k++) {
+            Entry *e = held[(size_t)k];
+            if (!e || rc[(size_t)k] != FLOWROI_OK) continue;
+            if (masks && masks[k]) ce = cudaMemcpyAsync(masks[k], e->mask, npx[(size_t)k], kind, c->s_d2h), queued++;
+            if (ce == cudaSuccess && coeffs && coeffs[k])
+                ce = cudaMemcpyAsync(coeffs[k], e->coeffs, npx[(size_t)k] * 4, kind, c->s_d2h), queued++;
+        }
+        if (ce == cudaSuccess && queued) ce = cudaStreamSynchronize(c->s_d2h);
+        if (ce != cudaSuccess) {
+            const int code = cuda_fail(c, ce, "copy out");
+            for (int k = 0; k < n; k++)
+                if (held[(size_t)k] && rc[(size_t)k] == FLOWROI_OK) rc[(size_t)k] = code;
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (Entry *e : held)
+            if (e) e->readers--;
+    }
+    if (!c->manual) wake_scheduler(c);
+    int first = FLOWROI_OK;
+    for (int k = 0; k < n; k++) {
+        if (status) status[k] = rc[(size_t)k];
+        if (first == FLOWROI_OK) first = rc[(size_t)k];
+    }
+    return first;
+}
+
 int flowroi_get_intermediate(flowroi_ctx *c, int64_t stream_id, int64_t frame_idx, int which, void *out, int out_on_device,
                              int timeout_ms)
 {

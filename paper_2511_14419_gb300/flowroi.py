@@ -25,7 +25,7 @@ I_FLOW, I_SALIENCY, I_MASK0, I_COEFF_F32, I_THRESHOLD, I_DENOISED, I_DRIFT = 1, 
 
 EXPORTS = [
     "flowroi_abi_version", "flowroi_default_config", "flowroi_create", "flowroi_submit_frame", "flowroi_submit_frames",
-    "flowroi_step", "flowroi_get_mask", "flowroi_get_coeffs", "flowroi_get_intermediate",
+    "flowroi_step", "flowroi_get_mask", "flowroi_get_coeffs", "flowroi_get_results", "flowroi_get_intermediate",
     "flowroi_flush", "flowroi_end_stream", "flowroi_get_stats", "flowroi_destroy",
     "flowroi_last_error", "flowroi_quant_steps", "flowroi_compute_stream", "flowroi_set_profiling",
     "flowroi_get_kernel_times", "flowroi_dwt_roi_noalloc", "flowroi_reset_stats",
@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
             "flowroi_step": (I, [P]),
             "flowroi_get_mask": (I, [P, I64, I64, P, I, I]),
             "flowroi_get_coeffs": (I, [P, I64, I64, P, I, I]),
+            "flowroi_get_results": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(P),
+                                        ctypes.POINTER(P), I, I, ctypes.POINTER(I)]),
             "flowroi_get_intermediate": (I, [P, I64, I64, I, P, I, I]),
             "flowroi_flush": (I, [P, I]),
             "flowroi_end_stream": (I, [P, I64]),
@@ -224,6 +226,33 @@ def flowroi_get_mask(ctx, stream_id: int, frame_idx: int, out, timeout_ms: int =
 def flowroi_get_coeffs(ctx, stream_id: int, frame_idx: int, out, timeout_ms: int = -1) -> int:
     p, dev = _ptr(out)
     return _check(lib().flowroi_get_coeffs(ctx, stream_id, frame_idx, p, dev, timeout_ms), ctx)
+
+
+def flowroi_get_results(ctx, items, timeout_ms: int = -1) -> list:
+    """Masks and coefficients of several frames in one call (see the C
+    header): items = [(stream_id, frame_idx, mask_out, coeffs_out)], each
+    output a contiguous array or tensor, or None to skip it; all outputs on
+    the host or all on the device.  Returns the per-frame status codes;
+    raises FlowRoIError with the first failing frame's code."""
+    n = len(items)
+    ids = (ctypes.c_int64 * max(n, 1))(*[int(it[0]) for it in items])
+    fis = (ctypes.c_int64 * max(n, 1))(*[int(it[1]) for it in items])
+    mp = (ctypes.c_void_p * max(n, 1))()
+    cp = (ctypes.c_void_p * max(n, 1))()
+    dev = None
+    for k, (_, _, m, c) in enumerate(items):
+        for arr, dst in ((m, mp), (c, cp)):
+            if arr is None:
+                continue
+            p, d = _ptr(arr)
+            if dev is None:
+                dev = d
+            elif d != dev:
+                raise ValueError("outputs must all be on the host or all on the device")
+            dst[k] = p
+    st = (ctypes.c_int * max(n, 1))()
+    _check(lib().flowroi_get_results(ctx, n, ids, fis, mp, cp, int(dev or 0), timeout_ms, st), ctx)
+    return list(st)[:n]
 
 
 def flowroi_get_intermediate(ctx, stream_id: int, frame_idx: int, which: int, out, timeout_ms: int = -1) -> int:

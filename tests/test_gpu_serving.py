@@ -77,6 +77,60 @@ def test_batch_submit_matches_per_frame_submit_and_stops_at_a_refusal():
         assert F.lib().flowroi_submit_frames(ctx.h, -1, None, None, None) == F.EINVAL
 
 
+def test_get_results_matches_the_per_frame_getters():
+    """flowroi_get_results: the masks and coefficients of several streams'
+    frames in one call equal flowroi_get_mask / flowroi_get_coeffs frame by
+    frame, into host and into device buffers; a skipped output stays
+    untouched; a frame that cannot be read (unknown stream, a frame not
+    submitted) gets its own status while the others are still copied."""
+    import torch
+    cfg = dict(pyr_levels=3, dwt_levels=3, wavelet=97)
+    streams = _streams()
+    with F.Context(flags=F.MANUAL, **cfg) as ctx:
+        for t in range(2):
+            F.flowroi_submit_frames(ctx.h, [(sid, frames[t], t, bd) for sid, frames, bd in streams])
+            F.flowroi_step(ctx.h)
+        F.flowroi_flush(ctx.h, 60000)
+        want = {}
+        for sid, frames, bd in streams:
+            h, w = frames[1].shape
+            m, c = np.empty((h, w), np.uint8), np.empty((h, w), np.int32)
+            F.flowroi_get_mask(ctx.h, sid, 1, m)
+            F.flowroi_get_coeffs(ctx.h, sid, 1, c)
+            want[sid] = (m, c)
+        outs = {sid: (np.full(frames[1].shape, 7, np.uint8), np.full(frames[1].shape, 7, np.int32))
+                for sid, frames, bd in streams}
+        st = F.flowroi_get_results(ctx.h, [(sid, 1, outs[sid][0], outs[sid][1]) for sid, _, _ in streams])
+        assert st == [F.OK] * len(streams)
+        for sid in want:
+            assert np.array_equal(outs[sid][0], want[sid][0]) and np.array_equal(outs[sid][1], want[sid][1])
+        # device outputs, coefficients only for the first stream
+        dev = {sid: (torch.zeros(frames[1].shape, dtype=torch.uint8, device="cuda"),
+                     torch.zeros(frames[1].shape, dtype=torch.int32, device="cuda")) for sid, frames, bd in streams}
+        items = [(sid, 1, None if sid == 0 else dev[sid][0], dev[sid][1]) for sid, _, _ in streams]
+        assert F.flowroi_get_results(ctx.h, items) == [F.OK] * len(streams)
+        for sid in want:
+            assert np.array_equal(dev[sid][1].cpu().numpy(), want[sid][1])
+            if sid == 0:
+                assert not dev[sid][0].any()
+            else:
+                assert np.array_equal(dev[sid][0].cpu().numpy(), want[sid][0])
+        # per-frame failures: the readable frames are still copied
+        sid1, fr1, _ = streams[1]
+        m1 = np.zeros(fr1[1].shape, np.uint8)
+        import ctypes
+        ids = (ctypes.c_int64 * 3)(999, sid1, sid1)
+        fis = (ctypes.c_int64 * 3)(1, 1, 5)
+        mp = (ctypes.c_void_p * 3)(None, m1.ctypes.data, None)
+        cp = (ctypes.c_void_p * 3)()
+        st = (ctypes.c_int * 3)()
+        rc = F.lib().flowroi_get_results(ctx.h, 3, ids, fis, mp, cp, 0, 1000, st)
+        assert rc == F.ENOSTREAM and list(st) == [F.ENOSTREAM, F.OK, F.ENOSTREAM]
+        assert np.array_equal(m1, want[sid1][0])
+        assert F.lib().flowroi_get_results(ctx.h, -1, None, None, None, None, 0, 0, None) == F.EINVAL
+        assert F.flowroi_get_results(ctx.h, []) == []
+
+
 def test_scheduler_thread_matches_manual():
     streams = _streams()
     manual = {sid: run_stream(frames, bd, keep=False)[1] for sid, frames, bd in streams}
