@@ -115,6 +115,12 @@ def test_codestream_bound_counts_the_code_blocks(F, orc):
         assert F.flowroi_codestream_bound(w, h, levels) == 0
 
 
+def test_get_results_rejects_bad_arguments_on_the_host(F):
+    L = F.lib()
+    assert L.flowroi_get_results(None, 1, None, None, None, None, 0, 0, None) == F.EINVAL
+    assert "ctx is NULL" in F.flowroi_last_error(None)
+
+
 def test_encode_codestreams_rejects_bad_jobs_on_the_host(F):
     L = F.lib()
     jobs = (F.flowroi_cs_job * 1)()
