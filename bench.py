@@ -122,15 +122,19 @@ def other_bytes(name, storage, bpp):
 
 # DRAM bytes (read + write) per level-0 pixel of one launch, measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on 4 frames of the same
-# workload (traffic proportional to pixels; the update figure averages its
-# three level-0 launches), each
+# workload (traffic proportional to pixels; the fp32 update figure averages
+# its three level-0 launches, the fp16 ones are single launches: update
+# iteration 1, window, expansion), each
 # with the source file the kernel was built from and its SHA-256 prefix at
 # the time of the capture: a figure whose source has changed since is
 # reported as null.
 KERNEL_TRAFFIC_PER_PX = {("update", 32): (64.26, "k_flow.cu", "c9219d3d2d871711"),
                          ("window", 32): (26.06, "k_flow.cu", "c9219d3d2d871711"),
                          ("expand", 32): (19.16, "k_expand.cu", "83e2d4444934406d"),
-                         ("dwt", 32): (4.03, "k_dwt.cu", "48cdef260a22e4fa")}
+                         ("dwt", 32): (4.03, "k_dwt.cu", "48cdef260a22e4fa"),
+                         ("update", 16): (37.35, "k_flow.cu", "c9219d3d2d871711"),
+                         ("window", 16): (15.25, "k_flow.cu", "c9219d3d2d871711"),
+                         ("expand", 16): (8.91, "k_expand.cu", "83e2d4444934406d")}
 
 
 def traffic_per_px(name, storage):
